@@ -1,0 +1,178 @@
+"""Outer solvers for min_u 1/2 ||A u - b||^2 + alpha TV(u)  (Eq. 5), FP64 oracle.
+
+f(x) = 1/2 ||A x - b||^2 (gradient A^T (A x - b)), g = alpha TV (+ the indicator of
+x >= 0 when ``nonneg``).  Every prox of g is the warm-started fixed-iteration inner
+solver ``tv.fgp_prox`` (Section 3.1); each solver keeps one dual field across its
+prox calls.  Coins come from ``coin.coin``.
+
+Each solver returns a dict with the final iterates, the objective F(x_{k+1}) after
+every outer iteration, the coin of every iteration and the number of prox calls.
+"""
+
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import coin as coin_mod
+from . import tv
+from .operators import LinearOp
+
+
+@dataclass
+class Problem:
+    """min_u 1/2 ||A u - b||^2 + alpha TV(u) [+ indicator(u >= 0)]."""
+    A: LinearOp
+    b: np.ndarray
+    alpha: float
+    shape: tuple
+    nonneg: bool = False
+
+    def grad_f(self, x):
+        return self.A.adjoint(self.A.forward(x) - self.b)
+
+    def objective(self, x):
+        r = self.A.forward(x) - self.b
+        return 0.5 * float(np.sum(r * r)) + self.alpha * tv.tv(x)
+
+
+def _prox_g(prob: Problem, v, step, n_inner, dual):
+    """prox_{step * g}(v) with g = alpha TV: FGP with lam = step * alpha."""
+    return tv.fgp_prox(v, step * prob.alpha, n_inner, dual, prob.nonneg)
+
+
+def pgd(prob: Problem, x0, gamma, K, n_inner, record=True):
+    """Algorithm 2: x_{k+1} = prox_{gamma g}(x_k - gamma grad f(x_k))."""
+    x = np.array(x0, dtype=np.float64)
+    dual = None
+    obj = []
+    for _ in range(K):
+        x, dual = _prox_g(prob, x - gamma * prob.grad_f(x), gamma, n_inner, dual)
+        if record:
+            obj.append(prob.objective(x))
+    return dict(x=x, dual=dual, objective=obj, coins=[1] * K, prox_calls=K)
+
+
+def proxskip(prob: Problem, x0, gamma, p, seed, K, n_inner, h0=None, record=True,
+             on_prox=None):
+    """Algorithm 4 (ProxSkip).
+
+    x^_{k+1} = x_k - gamma (grad f(x_k) - h_k);
+    if theta_k = 1: x_{k+1} = prox_{(gamma/p) g}(x^_{k+1} - (gamma/p) h_k)
+    else:          x_{k+1} = x^_{k+1};
+    h_{k+1} = h_k + (p/gamma)(x_{k+1} - x^_{k+1}).
+    ``on_prox(k, x, h, dual)`` is called after each executed prox (for tests).
+    """
+    x = np.array(x0, dtype=np.float64)
+    h = np.zeros_like(x) if h0 is None else np.array(h0, dtype=np.float64)
+    dual = None
+    obj, coins = [], []
+    n_prox = 0
+    for k in range(K):
+        x_hat = x - gamma * (prob.grad_f(x) - h)
+        theta = coin_mod.coin(seed, p, k)
+        coins.append(theta)
+        if theta:
+            x_new, dual = _prox_g(prob, x_hat - (gamma / p) * h, gamma / p, n_inner, dual)
+            n_prox += 1
+        else:
+            x_new = x_hat
+        h = h + (p / gamma) * (x_new - x_hat)
+        x = x_new
+        if theta and on_prox is not None:
+            on_prox(k, x, h, dual)
+        if record:
+            obj.append(prob.objective(x))
+    return dict(x=x, h=h, dual=dual, objective=obj, coins=coins, prox_calls=n_prox)
+
+
+def fista(prob: Problem, x0, gamma, K, n_inner, record=True):
+    """Algorithm 3 (FISTA) in Beck and Teboulle's form.
+
+    x_{k+1} = prox_{gamma g}(y_k - gamma grad f(y_k)); t_{k+1} = (1 + sqrt(1 + 4 t_k^2))/2;
+    y_{k+1} = x_{k+1} + ((t_k - 1)/t_{k+1}) (x_{k+1} - x_k); y_0 = x_0, t_0 = 1.
+    """
+    x = np.array(x0, dtype=np.float64)
+    y = x.copy()
+    t = 1.0
+    dual = None
+    obj = []
+    for _ in range(K):
+        x_new, dual = _prox_g(prob, y - gamma * prob.grad_f(y), gamma, n_inner, dual)
+        t_new = (1.0 + math.sqrt(1.0 + 4.0 * t * t)) / 2.0
+        y = x_new + ((t - 1.0) / t_new) * (x_new - x)
+        x, t = x_new, t_new
+        if record:
+            obj.append(prob.objective(x))
+    return dict(x=x, dual=dual, objective=obj, coins=[1] * K, prox_calls=K)
+
+
+def prox_fconj(v, tau, b):
+    """prox_{tau f*}(v) for f = 1/2 ||. - b||^2, through Moreau's identity.
+
+    prox_{tau f*}(v) = v - tau prox_{f/tau}(v / tau), and prox_{f/tau}(w) minimises
+    1/2 ||x - w||^2 + (1/(2 tau)) ||x - b||^2, i.e. x = (tau w + b) / (tau + 1).
+    """
+    w = v / tau
+    return v - tau * (tau * w + b) / (tau + 1.0)
+
+
+def pdhg(prob: Problem, x0, y0, sigma, tau, K, n_inner, record=True, on_iter=None):
+    """Implicit PDHG for f(K x) + g(x) with K = A, f = 1/2 ||. - b||^2, g = alpha TV.
+
+    Written with the step naming of Algorithm 6 (sigma primal, tau dual):
+    x_{k+1} = prox_{sigma g}(x_k - sigma K^T y_k); x-bar = 2 x_{k+1} - x_k;
+    y_{k+1} = prox_{tau f*}(y_k + tau K x-bar).
+    ``on_iter(k, x_k, y_k, x_{k+1}, y_{k+1})`` is called after every iteration (for tests).
+    """
+    x = np.array(x0, dtype=np.float64)
+    y = np.array(y0, dtype=np.float64)
+    dual = None
+    obj = []
+    for _ in range(K):
+        x_new, dual = _prox_g(prob, x - sigma * prob.A.adjoint(y), sigma, n_inner, dual)
+        x_bar = 2.0 * x_new - x
+        y_new = prox_fconj(y + tau * prob.A.forward(x_bar), tau, prob.b)
+        if on_iter is not None:
+            on_iter(_, x, y, x_new, y_new)
+        x, y = x_new, y_new
+        if record:
+            obj.append(prob.objective(x))
+    return dict(x=x, y=y, dual=dual, objective=obj, coins=[1] * K, prox_calls=K)
+
+
+def pdhgskip2(prob: Problem, x0, y0, sigma, tau, p, seed, K, n_inner, h0=None,
+              record=True, on_prox=None):
+    """Algorithm 6 (PDHGSkip-2), with the index reading
+    h_{k+1} = h_k + (p/sigma)(x_{k+1} - x^_k) and y_{k+1} = prox_{tau f*}(y_k + tau K x-bar_{k+1}):
+
+    x^_k = x_k - sigma (K^T y_k - h_k);
+    if theta_k = 1: x_{k+1} = prox_{(sigma/p) g}(x^_k - (sigma/p) h_k) else x_{k+1} = x^_k;
+    x-bar_{k+1} = 2 x_{k+1} - x_k.
+    """
+    x = np.array(x0, dtype=np.float64)
+    y = np.array(y0, dtype=np.float64)
+    h = np.zeros_like(x) if h0 is None else np.array(h0, dtype=np.float64)
+    dual = None
+    obj, coins = [], []
+    n_prox = 0
+    for k in range(K):
+        x_hat = x - sigma * (prob.A.adjoint(y) - h)
+        theta = coin_mod.coin(seed, p, k)
+        coins.append(theta)
+        if theta:
+            x_new, dual = _prox_g(prob, x_hat - (sigma / p) * h, sigma / p, n_inner, dual)
+            n_prox += 1
+        else:
+            x_new = x_hat
+        x_bar = 2.0 * x_new - x
+        y = prox_fconj(y + tau * prob.A.forward(x_bar), tau, prob.b)
+        h = h + (p / sigma) * (x_new - x_hat)
+        x = x_new
+        if theta and on_prox is not None:
+            on_prox(k, x, h, dual)
+        if record:
+            obj.append(prob.objective(x))
+    return dict(x=x, y=y, h=h, dual=dual, objective=obj, coins=coins, prox_calls=n_prox)

@@ -1,0 +1,171 @@
+"""Pins of the oracle's outer solvers (Algorithms 2, 3, 4, 6 and implicit PDHG).
+
+* ProxSkip with p = 1 is PGD and PDHGSkip-2 with p = 1 is PDHG (the prox argument
+  x^ - gamma h equals x - gamma grad f(x)): compared iterate for iterate against the
+  separately written PGD / PDHG.
+* After every executed prox (no constraint) h = alpha div p_N, since
+  h + (p/gamma)(x+ - x^) = (p/gamma) lam div p_N with lam = (gamma/p) alpha.
+* Between prox events h does not change.
+* All solvers reach the closed-form two-pixel minimiser, and on a small deblurring
+  problem PGD, FISTA and PDHG agree on the minimum.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import coin, operators, solvers, tv
+
+
+def _deblur_problem(n=12, seed=0, alpha=0.05, nonneg=False):
+    g = np.random.default_rng(seed)
+    truth = np.zeros((n, n))
+    truth[2:7, 3:9] = 1.0
+    truth[6:10, 1:5] = 0.5
+    A = operators.blur_op(1.5)
+    b = A.forward(truth) + 0.01 * g.standard_normal((n, n))
+    return solvers.Problem(A, b, alpha, (n, n), nonneg)
+
+
+def _denoise_problem(n=10, seed=1, alpha=0.1):
+    g = np.random.default_rng(seed)
+    truth = np.zeros((n, n))
+    truth[3:8, 2:6] = 1.0
+    b = truth + 0.1 * g.standard_normal((n, n))
+    return solvers.Problem(operators.identity_op(), b, alpha, (n, n))
+
+
+def _ct_problem(N=12, seed=2, alpha=0.02):
+    geom = operators.ParallelBeam.unit_square(N, 16, 17)
+    A = operators.ct_op(geom)
+    g = np.random.default_rng(seed)
+    truth = np.zeros((N, N))
+    truth[3:9, 4:8] = 0.4
+    b = A.forward(truth) + 0.001 * g.standard_normal((16, 17))
+    return solvers.Problem(A, b, alpha, (N, N)), geom
+
+
+@pytest.mark.parametrize("make", [_deblur_problem, _denoise_problem])
+def test_proxskip_p1_equals_pgd(make):
+    prob = make()
+    a = solvers.pgd(prob, prob.b, 1.0, 25, 7)
+    b = solvers.proxskip(prob, prob.b, 1.0, 1.0, 3, 25, 7)
+    assert b["prox_calls"] == 25
+    np.testing.assert_allclose(b["x"], a["x"], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(b["objective"], a["objective"], rtol=1e-12)
+
+
+def test_pdhgskip_p1_equals_pdhg():
+    prob, geom = _ct_problem()
+    L = 0.0
+    # sigma = tau = 0.99/||A||
+    from oracle.power import power_method
+    L = power_method(lambda x: prob.A.adjoint(prob.A.forward(x)), prob.shape, 300)
+    st = 0.99 / math.sqrt(L)
+    y0 = np.zeros_like(prob.b)
+    a = solvers.pdhg(prob, np.zeros(prob.shape), y0, st, st, 20, 6)
+    b = solvers.pdhgskip2(prob, np.zeros(prob.shape), y0, st, st, 1.0, 5, 20, 6)
+    np.testing.assert_allclose(b["x"], a["x"], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(b["y"], a["y"], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("p", [0.5, 0.2])
+def test_proxskip_control_variate_identity(p):
+    prob = _deblur_problem(seed=3)
+    gamma = 1.0
+    seen = []
+
+    def check(k, x, h, dual):
+        seen.append(k)
+        np.testing.assert_allclose(h, prob.alpha * tv.div(dual), rtol=0, atol=1e-12)
+
+    out = solvers.proxskip(prob, prob.b, gamma, p, 11, 40, 5, on_prox=check)
+    assert len(seen) == out["prox_calls"] == sum(out["coins"]) > 0
+    assert out["coins"] == coin.schedule(11, p, 40)
+
+
+def test_pdhgskip_control_variate_identity():
+    prob, _ = _ct_problem()
+    seen = []
+
+    def check(k, x, h, dual):
+        seen.append(k)
+        np.testing.assert_allclose(h, prob.alpha * tv.div(dual), rtol=0, atol=1e-12)
+
+    out = solvers.pdhgskip2(prob, np.zeros(prob.shape), np.zeros_like(prob.b), 0.3, 0.3, 0.3, 4, 30, 5,
+                            on_prox=check)
+    assert len(seen) == out["prox_calls"] > 0
+
+
+def test_h_constant_between_prox_events():
+    prob = _denoise_problem()
+    p, seed, K = 0.3, 21, 30
+    sched = coin.schedule(seed, p, K)
+    hs = []
+    for k in range(1, K + 1):
+        hs.append(solvers.proxskip(prob, prob.b, 1.0, p, seed, k, 4, record=False)["h"])
+    for k in range(1, K):
+        if not sched[k]:
+            np.testing.assert_array_equal(hs[k], hs[k - 1])
+
+
+def _two_pixel(b1, b2, alpha):
+    if abs(b1 - b2) <= 2 * alpha:
+        return np.array([[(b1 + b2) / 2] * 2])
+    s = math.copysign(1.0, b2 - b1)
+    return np.array([[b1 + s * alpha, b2 - s * alpha]])
+
+
+@pytest.mark.parametrize("b1,b2,alpha", [(0.0, 1.0, 0.2), (0.4, 0.5, 0.1)])
+def test_solvers_reach_two_pixel_minimiser(b1, b2, alpha):
+    """A = I on a 1 x 2 image: the minimiser of Eq. 5 is the two-pixel TV prox of b."""
+    b = np.array([[b1, b2]])
+    prob = solvers.Problem(operators.identity_op(), b, alpha, (1, 2))
+    expect = _two_pixel(b1, b2, alpha)
+    x0 = np.zeros_like(b)
+    outs = [
+        solvers.pgd(prob, x0, 1.0, 30, 60)["x"],
+        solvers.fista(prob, x0, 0.5, 200, 60)["x"],
+        solvers.proxskip(prob, x0, 0.5, 0.5, 1, 400, 60)["x"],
+        solvers.pdhg(prob, x0, np.zeros_like(b), 0.5, 0.5, 600, 60)["x"],
+        solvers.pdhgskip2(prob, x0, np.zeros_like(b), 0.5, 0.5, 0.5, 2, 1500, 60)["x"],
+    ]
+    for x in outs:
+        np.testing.assert_allclose(x, expect, atol=1e-7)
+
+
+def test_deblur_solvers_agree_on_minimum():
+    """PGD, FISTA and PDHG (three different iterations) reach the same minimum value."""
+    prob = _deblur_problem(n=10, alpha=0.03)
+    x0 = prob.b.copy()
+    f_pgd = solvers.pgd(prob, x0, 1.0, 1500, 30)["objective"][-1]
+    f_fista = solvers.fista(prob, x0, 1.0, 600, 30)["objective"][-1]
+    f_pdhg = solvers.pdhg(prob, x0, np.zeros_like(prob.b), 0.99, 0.99, 3000, 30)["objective"][-1]
+    assert abs(f_pgd - f_fista) <= 1e-8 * f_fista
+    assert abs(f_pdhg - f_fista) <= 1e-8 * f_fista
+
+
+def test_pdhg_residual_decreases():
+    """The PDHG fixed-point residual, averaged over windows, decreases."""
+    from oracle.power import power_method
+    prob, _ = _ct_problem(N=10)
+    L = power_method(lambda x: prob.A.adjoint(prob.A.forward(x)), prob.shape, 300)
+    st = 0.95 / math.sqrt(L)
+    res = []
+
+    def rec(k, x, y, xn, yn):
+        res.append(np.linalg.norm((x - xn) / st - prob.A.adjoint(y - yn))
+                   + np.linalg.norm((y - yn) / st - prob.A.forward(x - xn)))
+
+    solvers.pdhg(prob, np.zeros(prob.shape), np.zeros_like(prob.b), st, st, 60, 20, record=False, on_iter=rec)
+    w = np.array(res).reshape(6, 10).mean(axis=1)
+    assert np.all(np.diff(w) < 0)
+
+
+def test_objective_closed_form():
+    """F(x) = 1/2 ||A x - b||^2 + alpha TV(x) on a step image with A = I, b = 0."""
+    x = np.zeros((5, 8))
+    x[:, 3:] = 2.0
+    prob = solvers.Problem(operators.identity_op(), np.zeros_like(x), 0.1, x.shape)
+    assert prob.objective(x) == pytest.approx(0.5 * 4.0 * 25 + 0.1 * 2.0 * 5, rel=1e-15)
