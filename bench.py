@@ -1,0 +1,362 @@
+"""Benchmark: ProxSkip time to a 1e-4 relative objective gap on one GB300, beside
+PGD with the same prox, and the fused FGP kernel's bandwidth against HBM peak.
+
+Workload: 2D TV deblurring, 1024 x 1024 phantom of 40 random ellipses, 9x9
+Gaussian blur (sigma 2, reflective boundary), noise sigma 0.01, alpha 0.02,
+gamma = 1/||A||^2 = 1, ProxSkip p = 0.1 (Philox seed 0), 50 FGP iterations per
+prox, at most 1000 outer iterations, FP32 iterates and dual.  One step = one
+ProxSkip solve from x_0 = b until (F(x_k) - F*)/F* <= 1e-4.  F* is the smallest
+objective of a long FISTA run (3000 iterations, 100 inner) made before timing.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ProxSkip time-to-1e-4 gap vs PGD on one GB300; FGP TB/s vs HBM peak"
+TARGET = 1e-4
+P_SKIP = 0.1
+F_STAR_ITERS, F_STAR_INNER = 3000, 100
+FGP_BYTES_PER_PX = 28        # read z (4) + p_k (8) + p_{k-1} (8), write p_{k+1} (8), FP32 dual
+# Iterations / prox calls this workload's ProxSkip solve needs to reach the target
+# (from the solver's trace); used only to scale the CPU oracle sample.
+REF_ITERS_DEFAULT, REF_PROX_DEFAULT = 300, 30
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _workload_inputs():
+    from synth.configs import DeblurConfig
+    cfg = DeblurConfig()
+    return cfg, cfg.phantom().astype(np.float32), cfg.noise().astype(np.float32)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [c.strip() for c in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _flush_l2(buf):
+    buf.add_(1.0)  # touches 256 MB (> 129 MB L2)
+
+
+def run_gpu(args):
+    import torch
+    import paper_2411_00688_gb300 as tvs
+
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.Stream()
+    ctx = tvs.Context.__new__(tvs.Context)
+    # context on the benchmark's own (non-default) torch stream so CUDA events see its work
+    import ctypes as C
+    from paper_2411_00688_gb300 import _lib as L
+    ctx._h = C.c_void_p()
+    L.check(L.lib().tvs_create(C.byref(ctx._h), local, C.c_void_p(stream.cuda_stream)))
+    ctx.device = local
+
+    cfg, truth, noise = _workload_inputs()
+    H, W = truth.shape
+    with torch.cuda.stream(stream):
+        t_truth = torch.from_numpy(truth).cuda()
+        clean = torch.empty_like(t_truth)
+    stream.synchronize()
+    op_prob = tvs.Problem(ctx, t_truth, cfg.alpha, op="blur", blur_sigma=cfg.blur_sigma)
+    tvs.tvs_op_apply(op_prob, t_truth, clean)
+    op_prob.close()
+    b = (clean + torch.from_numpy(noise).cuda()).contiguous()
+    torch.cuda.synchronize()
+    prob = tvs.Problem(ctx, b, cfg.alpha, op="blur", blur_sigma=cfg.blur_sigma)
+    gamma = 1.0  # ||A||^2 = 1 for the normalised reflective blur
+
+    # reference optimum for the gap metric (not timed)
+    _, fista_tr = tvs.fista_solve(prob, b.clone(), gamma, F_STAR_ITERS, F_STAR_INNER)
+    f_star = float(np.nanmin(fista_tr.objective))
+
+    def solve(kind, x):
+        if kind == "proxskip":
+            return tvs.proxskip_solve(prob, x, gamma, P_SKIP, cfg.seed, cfg.max_iter, cfg.n_inner,
+                                      f_star=f_star, target=TARGET)
+        return tvs.pgd_solve(prob, x, gamma, cfg.max_iter, cfg.n_inner, f_star=f_star, target=TARGET)
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    x = torch.empty_like(b)
+
+    def timed(kind, steps):
+        times, traces = [], []
+        for _ in range(steps):
+            _flush_l2(flush)
+            x.copy_(b)
+            torch.cuda.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, tr = solve(kind, x)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+            traces.append(tr)
+        return times, traces
+
+    # PGD beside it (same prox, same target), after its own warm-up
+    timed("pgd", 1)
+    pgd_times, pgd_tr = timed("pgd", max(1, min(args.steps, 2)))
+
+    timed("proxskip", args.warmup)
+    with ClockSampler(local) as clk:
+        ps_times, ps_tr = timed("proxskip", args.steps)
+    clocks = clk.summary()
+
+    # FGP kernel duration with CUDA events on the launching stream: tv_prox with
+    # N inner iterations minus tv_prox with none, divided by N.
+    z = b.clone()
+    u = torch.empty_like(z)
+    state = torch.zeros((2, H, W), dtype=torch.float32, device="cuda")
+
+    def prox_time(n_iter, reps=5):
+        tvs.tv_prox(ctx, z, u, gamma / P_SKIP * cfg.alpha, n_iter, dual_state=state)
+        best = []
+        for _ in range(reps):
+            _flush_l2(flush)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tvs.tv_prox(ctx, z, u, gamma / P_SKIP * cfg.alpha, n_iter, dual_state=state)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best.append(e0.elapsed_time(e1) * 1e-3)
+        return statistics.median(best)
+
+    n_fgp = cfg.n_inner
+    fgp_s = (prox_time(n_fgp) - prox_time(0)) / n_fgp
+    in_solve = [t.fgp_ms / t.fgp_launches for t in ps_tr if t.fgp_launches > 0]
+    fgp_in_solve_s = statistics.median(in_solve) * 1e-3 if in_solve else None
+    hbm_peak, peak_kind = _peaks()
+    bytes_per_launch = FGP_BYTES_PER_PX * H * W
+    achieved = bytes_per_launch / fgp_s / 1e9
+
+    # end to end through the C ABI with pinned host buffers: H2D of b and x_0,
+    # D2H of the result, every step
+    b_host = torch.empty((H, W), dtype=torch.float32, pin_memory=True)
+    b_host.copy_(b.cpu())
+    x_host = torch.empty((H, W), dtype=torch.float32, pin_memory=True)
+    b_np, x_np = b_host.numpy(), x_host.numpy()
+    e2e_times = []
+    for i in range(args.warmup + args.steps):
+        _flush_l2(flush)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        prob.set_data(b_np)
+        x_np[...] = b_np
+        tvs.proxskip_solve(prob, x_np, gamma, P_SKIP, cfg.seed, cfg.max_iter, cfg.n_inner,
+                           f_star=f_star, target=TARGET)
+        t1 = time.perf_counter()
+        if i >= args.warmup:
+            e2e_times.append(t1 - t0)
+
+    ms_per_step = 1e3 * statistics.mean(ps_times)
+    if world > 1:
+        t = torch.tensor([ms_per_step], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_per_step = float(t.item())
+    last = ps_tr[-1]
+    launches = sum(tr.iters_run * 3 + tr.prox_calls * (cfg.n_inner + 3) + 3 for tr in ps_tr)
+    result = {
+        "metric": METRIC,
+        "value": ms_per_step / 1e3,
+        "unit": "s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "deblur2d_1024: 1024x1024, 40 ellipses, 9x9 Gaussian sigma 2, noise 0.01, "
+                               "alpha 0.02, gamma 1, ProxSkip p 0.1 seed 0, 50 FGP iterations per prox, "
+                               "stop at relative objective gap 1e-4 (max 1000 iterations)",
+                   "parallelism": f"replicas x{world}", "l2": "flushed between steps (256 MB write)",
+                   "f_star": f_star},
+        "time_to_target_device_s": statistics.mean(t.time_to_target_s for t in ps_tr),
+        "iterations_to_target": last.reached_iter + 1 if last.reached else None,
+        "prox_calls": last.prox_calls,
+        "reached": all(t.reached for t in ps_tr),
+        "pgd_time_to_target_s": statistics.mean(pgd_times) if all(t.reached for t in pgd_tr) else None,
+        "pgd_iterations_to_target": pgd_tr[-1].reached_iter + 1 if pgd_tr[-1].reached else None,
+        "speedup_vs_pgd": (statistics.mean(pgd_times) / statistics.mean(ps_times))
+        if all(t.reached for t in pgd_tr) else None,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": None,
+                     "kernel": "fgp2d_kernel<float>", "bytes_per_launch": bytes_per_launch,
+                     "launch_us": fgp_s * 1e6, "peak_kind": peak_kind,
+                     "launch_us_in_solve": fgp_in_solve_s * 1e6 if fgp_in_solve_s else None},
+        "e2e": {"value": statistics.mean(e2e_times), "unit": "s",
+                "h2d_bytes_per_step": 2 * H * W * 4, "d2h_bytes_per_step": H * W * 4},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(result["iterations_to_target"] or cfg.max_iter,
+                                              result["prox_calls"], truth=truth, noise=noise, cfg=cfg)
+    if rank == 0:
+        print(json.dumps(result))
+    prob.close()
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _oracle_sample(cfg, truth, noise):
+    """Seconds of the FP64 oracle for one outer gradient step (+ objective) and one
+    prox call (50 FGP iterations) of the 1024^2 deblurring workload."""
+    from oracle import operators, solvers, tv
+    w = operators.gaussian_weights(cfg.blur_sigma, cfg.blur_radius)
+    b = (operators.blur(truth.astype(np.float64), w) + noise.astype(np.float64))
+    prob = solvers.Problem(operators.blur_op(cfg.blur_sigma), b, cfg.alpha, b.shape)
+    x = b.copy()
+    t0 = time.perf_counter()
+    g = prob.grad_f(x)
+    x_hat = x - 1.0 * g
+    prob.objective(x_hat)
+    t1 = time.perf_counter()
+    tv.fgp_prox(x_hat, cfg.alpha / P_SKIP, cfg.n_inner)
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t1
+
+
+def cpu_baseline(iters, prox_calls, truth, noise, cfg):
+    t_grad, t_prox = _oracle_sample(cfg, truth, noise)
+    value = iters * t_grad + prox_calls * t_prox
+    return {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": f"one outer gradient step + objective ({t_grad:.2f} s) and one 50-iteration prox "
+                      f"({t_prox:.2f} s) of the FP64 numpy oracle on the 1024^2 workload, extrapolated "
+                      f"to {iters} iterations and {prox_calls} prox calls (extrapolated)"}
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return
+    cfg, truth, noise = _workload_inputs()
+    iters, prox = args.ref_iters, args.ref_prox
+    vals = []
+    for i in range(args.warmup + args.steps):
+        t_grad, t_prox = _oracle_sample(cfg, truth, noise)
+        if i >= args.warmup:
+            vals.append(iters * t_grad + prox * t_prox)
+    value = statistics.mean(vals)
+    sample = (f"per step: one outer gradient step + objective and one 50-iteration prox of the FP64 numpy "
+              f"oracle on the 1024^2 deblurring workload, extrapolated to {iters} iterations and {prox} "
+              f"prox calls (extrapolated)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "deblur2d_1024 (see the GPU arm)", "parallelism": "cpu"},
+        "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-iters", type=int, default=REF_ITERS_DEFAULT)
+    ap.add_argument("--ref-prox", type=int, default=REF_PROX_DEFAULT)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

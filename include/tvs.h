@@ -1,0 +1,198 @@
+/*
+ * tvs.h -- C ABI of the GB300 ProxSkip / PDHGSkip path for
+ *
+ *     min_u  1/2 || A u - b ||_2^2 + alpha TV(u)      (Eq. 5; Eq. 1 with D = 1/2||.||^2, R = TV)
+ *
+ * with isotropic TV and forward differences under Neumann boundary conditions
+ * (Eq. 5), A the identity, a separable Gaussian blur (Section 3.1) or a 2D
+ * parallel-beam projector (Section 3.3).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Arrays are dense, row-major float32.  A 2D image has dims {nx, ny, 1} and is
+ * stored as ny rows of nx values; a 3D volume has dims {nx, ny, nz} (nz slices).
+ * A sinogram is n_angles rows of n_det values.  A dual TV field holds `ndim`
+ * planes of the image size, plane a differentiating along the a-th slowest
+ * array axis (2D: plane 0 = vertical, plane 1 = horizontal; 3D: z, y, x).
+ *
+ * Pointers are device pointers on the context's stream unless a `tvs_mem`
+ * argument says TVS_MEM_HOST; the caller owns every pointer it passes.  Calls
+ * that return results synchronise the context's stream before returning.
+ * Every call validates its arguments first: on TVS_EINVAL nothing has been
+ * launched and no state has changed.  The message of the last failure on the
+ * calling thread is returned by tvs_last_error().  A context must be used by
+ * one host thread at a time.
+ *
+ * The dual step of the TV prox uses the bound ||D||^2 <= 4 * ndim (8 in 2D, 12
+ * in 3D), so one inner iteration is p <- P_B(r + D u / (4 ndim lambda)).
+ */
+#ifndef TVS_H
+#define TVS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TVS_OK = 0,
+  TVS_EINVAL = 1,        /* invalid argument; nothing was launched           */
+  TVS_ENOMEM = 2,        /* a device or pinned-host allocation failed        */
+  TVS_ECUDA = 3,         /* a CUDA runtime call failed (message has details) */
+  TVS_ENUMERIC = 4,      /* non-finite value in an input or in the objective */
+  TVS_ETIMEDOUT = 5,     /* a bounded device wait gave up                     */
+  TVS_EUNSUPPORTED = 6   /* valid request this build does not implement       */
+} tvs_status;
+
+typedef enum { TVS_OP_IDENTITY = 0, TVS_OP_GAUSS_BLUR = 1, TVS_OP_PARALLEL_BEAM = 2 } tvs_op_kind;
+typedef enum { TVS_DUAL_F32 = 0, TVS_DUAL_BF16 = 1, TVS_DUAL_F16 = 2 } tvs_dual_dtype;
+typedef enum { TVS_MEM_DEVICE = 0, TVS_MEM_HOST = 1 } tvs_mem;
+
+typedef struct tvs_ctx tvs_ctx;
+typedef struct tvs_problem tvs_problem;
+
+/* Forward operator A.
+ * TVS_OP_GAUSS_BLUR: 2*blur_radius+1 taps w_i = exp(-i^2/(2 sigma^2)), normalised
+ *   to sum 1, applied along x then y with half-sample symmetric extension
+ *   ("... b a | a b ..."); this A is symmetric, so A^T = A.  1 <= radius <= 8.
+ * TVS_OP_PARALLEL_BEAM (2D, nx == ny == N): Joseph's ray-driven projector.  The
+ *   image spans [-N s/2, N s/2]^2 (s = pixel_size); angle a is a*pi/n_angles;
+ *   bin b is the line x cos + y sin = (b - (n_det-1)/2) * det_spacing.  Rays with
+ *   |cos| >= |sin| are walked over rows, others over columns, interpolating
+ *   linearly between the two nearest pixels with weight s / max(|cos|,|sin|);
+ *   pixels outside the image count as zero.  The backprojector is the exact
+ *   transpose of the same weights. */
+typedef struct {
+  tvs_op_kind kind;
+  int blur_radius;
+  double blur_sigma;
+  int n_angles;
+  int n_det;
+  double pixel_size;
+  double det_spacing;
+} tvs_op_desc;
+
+typedef struct {
+  int ndim;            /* 2 or 3 (3 only with TVS_OP_IDENTITY)              */
+  int nx, ny, nz;      /* nz = 1 for 2D                                      */
+  double alpha;        /* TV weight, >= 0                                    */
+  int nonneg;          /* 1: add the constraint u >= 0 (Section 3.3)         */
+  tvs_op_desc op;
+} tvs_problem_desc;
+
+/* Forward-backward solvers (PGD = Algorithm 2, FISTA = Algorithm 3, ProxSkip =
+ * Algorithm 4).  gamma > 0; p in (0, 1] (ProxSkip only); n_inner >= 0 inner FGP
+ * iterations per prox, warm-started from the dual of the previous prox call;
+ * max_iter >= 0 outer iterations.  When f_star > 0 the solve stops (within a
+ * few iterations) once (F(x_k) - f_star) / f_star <= target_rel_gap.
+ * objective_every >= 1: F is evaluated every that many iterations (NaN between). */
+typedef struct {
+  double gamma;
+  double p;
+  uint64_t seed;
+  int max_iter;
+  int n_inner;
+  tvs_dual_dtype dual;
+  double f_star;
+  double target_rel_gap;
+  int objective_every;
+} tvs_fb_params;
+
+/* Primal-dual solvers (PDHG, PDHGSkip-2 = Algorithm 6) with the naming of
+ * Algorithm 6: sigma is the primal and tau the dual step, sigma tau ||A||^2 <= 1. */
+typedef struct {
+  double sigma;
+  double tau;
+  double p;
+  uint64_t seed;
+  int max_iter;
+  int n_inner;
+  tvs_dual_dtype dual;
+  double f_star;
+  double target_rel_gap;
+  int objective_every;
+} tvs_pd_params;
+
+/* Solve record.  The caller owns the three host arrays (any may be NULL) and
+ * sets cap to their length; entry k describes outer iteration k: objective[k]
+ * = F(x_{k+1}), coins[k] = theta_k, t_s[k] = device time in seconds from the
+ * start of the solve until F(x_{k+1}) was known.  The scalars are outputs. */
+typedef struct {
+  int cap;
+  double* objective;
+  unsigned char* coins;
+  double* t_s;
+  int iters_run;          /* outer iterations executed                          */
+  int prox_calls;         /* prox evaluations among them                        */
+  int reached;            /* 1 if the relative-gap target was met               */
+  int reached_iter;       /* first k with (F(x_{k+1}) - f*)/f* <= target, else -1 */
+  double time_to_target_s;/* t_s[reached_iter], or -1                           */
+  double solve_ms;        /* device time of the whole solve (CUDA events)       */
+  double fgp_ms;          /* device time inside inner-iteration launches        */
+  long long fgp_launches; /* number of inner-iteration kernel launches          */
+  long long fgp_pixel_iters; /* pixels x inner iterations processed by them    */
+} tvs_trace;
+
+/* ---- context ----------------------------------------------------------- */
+/* Creates a context on `device`.  `cuda_stream` is a cudaStream_t to launch on;
+ * NULL creates a private non-blocking stream owned by the context. */
+tvs_status tvs_create(tvs_ctx** ctx, int device, void* cuda_stream);
+tvs_status tvs_destroy(tvs_ctx* ctx);
+const char* tvs_last_error(void);
+/* Bytes of device memory currently held by the context and its problems. */
+size_t tvs_device_bytes(const tvs_ctx* ctx);
+
+/* ---- problems ------------------------------------------------------------ */
+/* Copies b (measurement: image-sized, or n_angles x n_det for CT) into memory
+ * the problem owns, together with all its workspace.  Returns TVS_ENUMERIC if b
+ * holds a non-finite value. */
+tvs_status tvs_problem_create(tvs_ctx* ctx, const tvs_problem_desc* desc, const float* b,
+                              tvs_mem b_mem, tvs_problem** out);
+/* Replaces the problem's copy of b (same size). */
+tvs_status tvs_problem_set_data(tvs_problem* prob, const float* b, tvs_mem b_mem);
+tvs_status tvs_problem_destroy(tvs_problem* prob);
+/* y = A x (adjoint = 0) or y = A^T x (adjoint = 1); device pointers. */
+tvs_status tvs_op_apply(tvs_problem* prob, const float* x, float* y, int adjoint);
+/* F(x) = 1/2 ||A x - b||^2 + alpha TV(x) for a device image x (FP32 terms,
+ * FP64 accumulation). */
+tvs_status tvs_objective(tvs_problem* prob, const float* x, double* out);
+
+/* ---- TV prox (Eq. 3 with R = TV; inner solver of Sections 2.2, 3.1) ------ */
+/* u = prox_{lambda TV}(z) (with u >= 0 if nonneg) by n_iter iterations of the
+ * accelerated dual projected gradient.  dual_state: NULL for a cold start (p =
+ * 0), else a device buffer of ndim planes of `dual` elements holding the warm
+ * start; it receives the final dual p_N.  lambda = 0 or n_iter = 0 returns
+ * u = P(z + lambda div p0).  z and u may not alias. */
+tvs_status tv_prox(tvs_ctx* ctx, int ndim, const int dims[3], const float* z, float* u,
+                   double lambda, int n_iter, tvs_dual_dtype dual, void* dual_state, int nonneg);
+
+/* ---- outer solvers --------------------------------------------------------- */
+/* x_inout: initial iterate in, final iterate out (image size, TVS_MEM_* says
+ * where it lives).  The control variate starts at h_0 = 0, the TV dual at 0. */
+tvs_status pgd_solve(tvs_problem* prob, const tvs_fb_params* prm, float* x_inout, tvs_mem mem,
+                     tvs_trace* trace);
+tvs_status fista_solve(tvs_problem* prob, const tvs_fb_params* prm, float* x_inout, tvs_mem mem,
+                       tvs_trace* trace);
+tvs_status proxskip_solve(tvs_problem* prob, const tvs_fb_params* prm, float* x_inout,
+                          tvs_mem mem, tvs_trace* trace);
+/* y_inout: dual iterate (measurement size) in and out; h_0 = 0. */
+tvs_status pdhg_solve(tvs_problem* prob, const tvs_pd_params* prm, float* x_inout,
+                      float* y_inout, tvs_mem mem, tvs_trace* trace);
+tvs_status pdhgskip_solve(tvs_problem* prob, const tvs_pd_params* prm, float* x_inout,
+                          float* y_inout, tvs_mem mem, tvs_trace* trace);
+
+/* ---- the coin (Algorithms 4 and 6) ----------------------------------------- */
+/* theta_k = [(w >> 11) < p 2^53], w the first word of Philox4x64-10 with counter
+ * (k, 0, 0, 0) and key (seed, 0).  Returns 0/1, or -1 if p is not in (0, 1]. */
+int tvs_coin(uint64_t seed, double p, int64_t k);
+/* theta_{k0}, ..., theta_{k0+K-1} computed by a device kernel, written to the
+ * host array out (K bytes). */
+tvs_status tvs_coin_schedule_device(tvs_ctx* ctx, uint64_t seed, double p, int64_t k0, int K,
+                                    unsigned char* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TVS_H */

@@ -1,0 +1,26 @@
+"""GB300-native ProxSkip / PDHGSkip-2 for TV-regularised imaging inverse problems.
+
+The compute path is libtvs.so (CUDA for sm_103a behind the C ABI in
+include/tvs.h); this package is its Python binding.  Importing the binding
+loads the library and fails if it has not been built.
+"""
+
+from .api import (  # noqa: F401
+    Context,
+    Problem,
+    SolveTrace,
+    fista_solve,
+    pd_steps,
+    pdhg_solve,
+    pdhgskip_solve,
+    pgd_solve,
+    proxskip_solve,
+    tv_prox,
+    tvs_coin,
+    tvs_coin_schedule_device,
+    tvs_objective,
+    tvs_op_apply,
+)
+from ._lib import LIB_PATH, TVSError, lib  # noqa: F401
+
+lib()  # load now: no CPU fallback exists

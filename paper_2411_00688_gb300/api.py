@@ -1,0 +1,285 @@
+"""Python binding of the C ABI: argument marshalling only.
+
+Every computation runs in libtvs.so.  Arrays may be torch CUDA tensors (device
+pointers) or numpy float32 arrays (host pointers; the library copies them in and
+out).  Functions keep the names of the C entry points.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib as L
+
+
+def _torch():
+    import torch  # imported lazily: host-only users need numpy only
+    return torch
+
+
+def _is_cuda_tensor(a) -> bool:
+    try:
+        torch = _torch()
+    except ImportError:
+        return False
+    return isinstance(a, torch.Tensor) and a.is_cuda
+
+
+def _sync_torch():
+    torch = _torch()
+    if torch.cuda.is_available():
+        torch.cuda.current_stream().synchronize()
+
+
+def _arr(a, what):
+    """(pointer, mem kind, keep-alive object) for a float32 array."""
+    if _is_cuda_tensor(a):
+        torch = _torch()
+        if a.dtype != torch.float32 or not a.is_contiguous():
+            raise ValueError(f"{what}: CUDA tensors must be contiguous float32")
+        return a.data_ptr(), L.MEM_DEVICE, a
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float32 or not a.flags.c_contiguous:
+            raise ValueError(f"{what}: numpy arrays must be C-contiguous float32")
+        return a.ctypes.data, L.MEM_HOST, a
+    raise TypeError(f"{what}: expected a CUDA tensor or a numpy float32 array")
+
+
+class Context:
+    """tvs_ctx on one device with a private stream."""
+
+    def __init__(self, device: int = 0):
+        self._h = C.c_void_p()
+        L.check(L.lib().tvs_create(C.byref(self._h), int(device), None))
+        self.device = device
+
+    @property
+    def handle(self):
+        return self._h
+
+    def device_bytes(self) -> int:
+        return int(L.lib().tvs_device_bytes(self._h))
+
+    def close(self):
+        if self._h:
+            L.lib().tvs_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclass
+class SolveTrace:
+    objective: np.ndarray
+    coins: np.ndarray
+    t_s: np.ndarray
+    iters_run: int
+    prox_calls: int
+    reached: bool
+    reached_iter: int
+    time_to_target_s: float
+    solve_ms: float
+    fgp_ms: float
+    fgp_launches: int
+    fgp_pixel_iters: int
+
+
+def _new_trace(cap):
+    obj = np.full(cap, np.nan)
+    coins = np.zeros(cap, dtype=np.uint8)
+    ts = np.full(cap, np.nan)
+    tr = L.Trace()
+    tr.cap = cap
+    tr.objective = obj.ctypes.data_as(C.POINTER(C.c_double))
+    tr.coins = coins.ctypes.data_as(C.POINTER(C.c_ubyte))
+    tr.t_s = ts.ctypes.data_as(C.POINTER(C.c_double))
+    return tr, obj, coins, ts
+
+
+def _finish_trace(tr, obj, coins, ts):
+    n = tr.iters_run
+    return SolveTrace(obj[:n].copy(), coins[:n].copy(), ts[:n].copy(), tr.iters_run, tr.prox_calls,
+                      bool(tr.reached), tr.reached_iter, tr.time_to_target_s, tr.solve_ms, tr.fgp_ms,
+                      tr.fgp_launches, tr.fgp_pixel_iters)
+
+
+class Problem:
+    """tvs_problem: min_u 1/2 ||A u - b||^2 + alpha TV(u) [+ u >= 0]."""
+
+    def __init__(self, ctx: Context, b, alpha: float, op: str = "identity", shape=None,
+                 nonneg: bool = False, blur_sigma: float = 2.0, blur_radius: int = 4,
+                 n_angles: int = 0, n_det: int = 0, pixel_size: float = 0.0,
+                 det_spacing: float = 0.0):
+        self.ctx = ctx
+        d = L.ProblemDesc()
+        if op == "ct":
+            if shape is None:
+                raise ValueError("CT problems need the image shape")
+            img_shape = tuple(shape)
+        else:
+            img_shape = tuple(b.shape) if shape is None else tuple(shape)
+        self.shape = img_shape
+        if len(img_shape) == 2:
+            d.ndim, d.nz, d.ny, d.nx = 2, 1, img_shape[0], img_shape[1]
+        elif len(img_shape) == 3:
+            d.ndim, d.nz, d.ny, d.nx = 3, img_shape[0], img_shape[1], img_shape[2]
+        else:
+            raise ValueError("images are 2D or 3D")
+        d.alpha = float(alpha)
+        d.nonneg = int(bool(nonneg))
+        kinds = {"identity": L.OP_IDENTITY, "blur": L.OP_GAUSS_BLUR, "ct": L.OP_PARALLEL_BEAM}
+        d.op.kind = kinds[op]
+        d.op.blur_radius = int(blur_radius)
+        d.op.blur_sigma = float(blur_sigma)
+        d.op.n_angles = int(n_angles)
+        d.op.n_det = int(n_det)
+        d.op.pixel_size = float(pixel_size)
+        d.op.det_spacing = float(det_spacing)
+        self.op = op
+        self.alpha = float(alpha)
+        self.meas_shape = (n_angles, n_det) if op == "ct" else img_shape
+        self._desc = d
+        ptr, mem, keep = _arr(b, "b")
+        if mem == L.MEM_DEVICE:
+            _sync_torch()
+        self._h = C.c_void_p()
+        L.check(L.lib().tvs_problem_create(ctx.handle, C.byref(d), C.c_void_p(ptr), mem, C.byref(self._h)))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_data(self, b):
+        ptr, mem, keep = _arr(b, "b")
+        if mem == L.MEM_DEVICE:
+            _sync_torch()
+        L.check(L.lib().tvs_problem_set_data(self._h, C.c_void_p(ptr), mem))
+
+    def close(self):
+        if self._h:
+            L.lib().tvs_problem_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tvs_op_apply(prob: Problem, x, y, adjoint: bool = False):
+    """y = A x or A^T x (device tensors)."""
+    _sync_torch()
+    L.check(L.lib().tvs_op_apply(prob.handle, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                 int(bool(adjoint))))
+    return y
+
+
+def tvs_objective(prob: Problem, x) -> float:
+    _sync_torch()
+    out = C.c_double()
+    L.check(L.lib().tvs_objective(prob.handle, C.c_void_p(x.data_ptr()), C.byref(out)))
+    return out.value
+
+
+def tv_prox(ctx: Context, z, u, lam: float, n_iter: int, dual: str = "f32", dual_state=None,
+            nonneg: bool = False):
+    """u = prox_{lam TV}(z) on device tensors (2D (H, W) or 3D (D, H, W))."""
+    _sync_torch()
+    shape = tuple(z.shape)
+    if len(shape) == 2:
+        dims = (C.c_int * 3)(shape[1], shape[0], 1)
+    elif len(shape) == 3:
+        dims = (C.c_int * 3)(shape[2], shape[1], shape[0])
+    else:
+        raise ValueError("z must be 2D or 3D")
+    ds = C.c_void_p(dual_state.data_ptr()) if dual_state is not None else None
+    L.check(L.lib().tv_prox(ctx.handle, len(shape), dims, C.c_void_p(z.data_ptr()),
+                            C.c_void_p(u.data_ptr()), float(lam), int(n_iter), L.DUAL[dual], ds,
+                            int(bool(nonneg))))
+    return u
+
+
+def _fb(fn_name, prob, x, gamma, max_iter, n_inner, p=1.0, seed=0, dual="f32", f_star=0.0,
+        target=0.0, every=1):
+    prm = L.FBParams(gamma=float(gamma), p=float(p), seed=int(seed) & ((1 << 64) - 1),
+                     max_iter=int(max_iter), n_inner=int(n_inner), dual=L.DUAL[dual],
+                     f_star=float(f_star), target_rel_gap=float(target), objective_every=int(every))
+    ptr, mem, keep = _arr(x, "x")
+    if mem == L.MEM_DEVICE:
+        _sync_torch()
+    tr, obj, coins, ts = _new_trace(max(int(max_iter), 1))
+    L.check(getattr(L.lib(), fn_name)(prob.handle, C.byref(prm), C.c_void_p(ptr), mem, C.byref(tr)))
+    return x, _finish_trace(tr, obj, coins, ts)
+
+
+def pgd_solve(prob, x, gamma, max_iter, n_inner, **kw):
+    """PGD (Algorithm 2); x holds x_0 on entry and the final iterate on return."""
+    return _fb("pgd_solve", prob, x, gamma, max_iter, n_inner, **kw)
+
+
+def fista_solve(prob, x, gamma, max_iter, n_inner, **kw):
+    """FISTA (Algorithm 3)."""
+    return _fb("fista_solve", prob, x, gamma, max_iter, n_inner, **kw)
+
+
+def proxskip_solve(prob, x, gamma, p, seed, max_iter, n_inner, **kw):
+    """ProxSkip (Algorithm 4)."""
+    return _fb("proxskip_solve", prob, x, gamma, max_iter, n_inner, p=p, seed=seed, **kw)
+
+
+def _pd(fn_name, prob, x, y, sigma, tau, max_iter, n_inner, p=1.0, seed=0, dual="f32", f_star=0.0,
+        target=0.0, every=1):
+    prm = L.PDParams(sigma=float(sigma), tau=float(tau), p=float(p), seed=int(seed) & ((1 << 64) - 1),
+                     max_iter=int(max_iter), n_inner=int(n_inner), dual=L.DUAL[dual],
+                     f_star=float(f_star), target_rel_gap=float(target), objective_every=int(every))
+    px, mem, kx = _arr(x, "x")
+    py, mem_y, ky = _arr(y, "y")
+    if mem != mem_y:
+        raise ValueError("x and y must live in the same memory")
+    if mem == L.MEM_DEVICE:
+        _sync_torch()
+    tr, obj, coins, ts = _new_trace(max(int(max_iter), 1))
+    L.check(getattr(L.lib(), fn_name)(prob.handle, C.byref(prm), C.c_void_p(px), C.c_void_p(py), mem,
+                                      C.byref(tr)))
+    return x, y, _finish_trace(tr, obj, coins, ts)
+
+
+def pdhg_solve(prob, x, y, sigma, tau, max_iter, n_inner, **kw):
+    """Implicit PDHG (PDHGSkip-2 with p = 1)."""
+    return _pd("pdhg_solve", prob, x, y, sigma, tau, max_iter, n_inner, **kw)
+
+
+def pdhgskip_solve(prob, x, y, sigma, tau, p, seed, max_iter, n_inner, **kw):
+    """PDHGSkip-2 (Algorithm 6)."""
+    return _pd("pdhgskip_solve", prob, x, y, sigma, tau, max_iter, n_inner, p=p, seed=seed, **kw)
+
+
+def tvs_coin(seed: int, p: float, k: int) -> int:
+    return int(L.lib().tvs_coin(int(seed) & ((1 << 64) - 1), float(p), int(k)))
+
+
+def tvs_coin_schedule_device(ctx: Context, seed: int, p: float, k0: int, K: int) -> np.ndarray:
+    out = np.zeros(int(K), dtype=np.uint8)
+    L.check(L.lib().tvs_coin_schedule_device(ctx.handle, int(seed) & ((1 << 64) - 1), float(p),
+                                             int(k0), int(K), out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def gaussian_blur_norm_sq() -> float:
+    """||A||^2 of the normalised, reflect-boundary Gaussian blur (exactly 1)."""
+    return 1.0
+
+
+def pd_steps(norm_A_sq: float, ratio: float = 1.0, safety: float = 0.99):
+    """sigma, tau with sigma tau ||A||^2 = safety^2 (sigma / tau = ratio)."""
+    nrm = math.sqrt(norm_A_sq)
+    return safety * math.sqrt(ratio) / nrm, safety / (math.sqrt(ratio) * nrm)

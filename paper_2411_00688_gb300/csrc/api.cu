@@ -1,0 +1,939 @@
+// C ABI (include/tvs.h): contexts, problems and the outer-loop drivers.
+//
+// Every outer iteration of a solver is one CUDA-graph launch.  A solver captures
+// one graph per (coin value, buffer parity): the iterate ping-pongs between
+// x[0] and x[1], so iteration k reads x[k % 2] and writes x[(k+1) % 2], and the
+// Philox coin schedule, a pure function of (seed, p, k), is drawn on the host
+// before the loop.  Graphs are iteration-independent: the objective reduction
+// takes its trace index from a device counter it increments itself.
+//
+// ProxSkip (Algorithm 4), iteration k, parity c = k % 2, A the forward operator:
+//   step kernels : out = x[c] - gamma A^T(A x[c] - b) + ch h     (+ partials of F(x[c]))
+//                  skip: out = x[c+1], ch = gamma          (x_{k+1} = x^)
+//                  prox: out = z,      ch = gamma - gamma/p (z = x^ - (gamma/p) h)
+//   reduce       : F(x_k) -> trace (index k - 1)
+//   prox only    : N x FGP on z with lam = (gamma/p) alpha, warm-started dual;
+//                  finalize x[c+1] = P_X(z + lam div p_N), h = (p/gamma)(x[c+1] - z)
+// The last line is Algorithm 4's h + (p/gamma)(x_{k+1} - x^_{k+1}) with
+// x^ = z + (gamma/p) h substituted; on skip iterations h is left untouched.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.hpp"
+#include "tvs.h"
+
+using namespace tvs;
+
+namespace {
+
+thread_local std::string g_err;
+
+tvs_status fail(tvs_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define CUDA_TRY(call)                                                                        \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(e_ == cudaErrorMemoryAllocation ? TVS_ENOMEM : TVS_ECUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                         \
+  } while (0)
+
+#define TVS_TRY(call)                  \
+  do {                                 \
+    tvs_status s_ = (call);            \
+    if (s_ != TVS_OK) return s_;       \
+  } while (0)
+
+constexpr int LAG = 8;  // outer iterations the host may run ahead of the device
+
+bool is_fin(double v) { return std::isfinite(v); }
+
+}  // namespace
+
+struct tvs_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  void* prox_scratch = nullptr;
+  size_t prox_scratch_bytes = 0;
+  double* red_out = nullptr;  // one double for tvs_objective
+  int* flags = nullptr;       // scratch flags for tvs_objective
+  double* parts = nullptr;    // partials for tvs_objective
+  size_t parts_cap = 0;
+  cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
+  cudaEvent_t ring[LAG] = {};
+  size_t bytes = 0;
+};
+
+struct tvs_problem {
+  tvs_ctx* ctx = nullptr;
+  tvs_problem_desc desc{};
+  Dims dims;
+  size_t n = 0, m = 0;
+  BlurW bw{};
+  CTGeom geom{};
+  float4* angle_tab = nullptr;
+  float* xt = nullptr;
+  float* b = nullptr;
+  float* x[2] = {nullptr, nullptr};
+  float* z = nullptr;
+  float* h = nullptr;
+  float* r = nullptr;
+  float* y = nullptr;
+  float* axp = nullptr;
+  void* dual[3] = {nullptr, nullptr, nullptr};
+  double* part_a = nullptr;
+  double* part_b = nullptr;
+  int max_parts = 0;
+  double* obj_dev = nullptr;
+  unsigned long long* ts_dev = nullptr;   // [cap] objective timestamps, [cap] = solve start
+  unsigned long long* fgp_ts = nullptr;   // 2 per prox call
+  float* beta_dev = nullptr;              // FISTA outer extrapolation table
+  int trace_cap = 0;
+  int* flags = nullptr;                   // [0] done [1] reached k [2] trace counter [3] prox counter
+  int* done_host = nullptr;               // pinned, mapped
+  int* done_host_dev = nullptr;
+  int* count = nullptr;
+  size_t bytes = 0;
+};
+
+namespace {
+
+tvs_status dalloc(tvs_ctx* ctx, size_t* owner_bytes, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return TVS_OK;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(TVS_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  ctx->bytes += bytes;
+  if (owner_bytes) *owner_bytes += bytes;
+  return TVS_OK;
+}
+
+template <typename T>
+tvs_status palloc(tvs_problem* P, T** p, size_t count) {
+  return dalloc(P->ctx, &P->bytes, (void**)p, count * sizeof(T));
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+bool valid_dual(int d) { return d == TVS_DUAL_F32 || d == TVS_DUAL_BF16 || d == TVS_DUAL_F16; }
+
+std::vector<float> fgp_betas(int n_iter) {
+  // beta of inner iteration i (1-based): 0 for i = 1, (t_{i-1} - 1) / t_i after,
+  // with t_1 = 1 and t_{i} = (1 + sqrt(1 + 4 t_{i-1}^2)) / 2.
+  std::vector<float> b(n_iter > 0 ? n_iter : 0, 0.f);
+  double t = 1.0;
+  for (int i = 2; i <= n_iter; ++i) {
+    const double tn = (1.0 + std::sqrt(1.0 + 4.0 * t * t)) / 2.0;
+    b[i - 1] = (float)((t - 1.0) / tn);
+    t = tn;
+  }
+  return b;
+}
+
+// N inner iterations on z starting from the dual in buf[0]; returns the index
+// of the buffer that holds p_N.
+tvs_status launch_fgp_sequence(const Dims& d, const float* z, void* const buf[3], int n_iter,
+                               const std::vector<float>& betas, float lam, int dtype, bool nonneg,
+                               cudaStream_t s, int* final_idx) {
+  const float inv_step = (float)(1.0 / (4.0 * d.ndim * (double)lam));
+  for (int i = 1; i <= n_iter; ++i) {
+    void* cur = buf[(i - 1) % 3];
+    void* prev = i >= 2 ? buf[(i - 2) % 3] : cur;
+    void* out = buf[i % 3];
+    CUDA_TRY(launch_fgp_iter(d, z, cur, prev, out, lam, inv_step, betas[i - 1], dtype, nonneg, s));
+  }
+  *final_idx = n_iter % 3;
+  return TVS_OK;
+}
+
+tvs_status copy_in(float* dst, const float* src, size_t n, tvs_mem mem, cudaStream_t s) {
+  CUDA_TRY(cudaMemcpyAsync(dst, src, n * sizeof(float),
+                           mem == TVS_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+  return TVS_OK;
+}
+
+tvs_status copy_out(float* dst, const float* src, size_t n, tvs_mem mem, cudaStream_t s) {
+  CUDA_TRY(cudaMemcpyAsync(dst, src, n * sizeof(float),
+                           mem == TVS_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+  return TVS_OK;
+}
+
+tvs_status ensure_trace(tvs_problem* P, int K) {
+  if (K + 1 <= P->trace_cap) return TVS_OK;
+  if (P->trace_cap > 0) {
+    const size_t old = (size_t)P->trace_cap * (sizeof(double) + 2 * sizeof(unsigned long long) + sizeof(float)) +
+                       sizeof(unsigned long long);
+    P->bytes -= old;
+    P->ctx->bytes -= old;
+  }
+  dfree(P->obj_dev);
+  dfree(P->ts_dev);
+  dfree(P->fgp_ts);
+  dfree(P->beta_dev);
+  P->obj_dev = nullptr;
+  P->ts_dev = nullptr;
+  P->fgp_ts = nullptr;
+  P->beta_dev = nullptr;
+  const int cap = K + 1;
+  TVS_TRY(palloc(P, &P->obj_dev, cap));
+  TVS_TRY(palloc(P, &P->ts_dev, cap + 1));
+  TVS_TRY(palloc(P, &P->fgp_ts, 2 * (size_t)cap));
+  TVS_TRY(palloc(P, &P->beta_dev, cap));
+  P->trace_cap = cap;
+  return TVS_OK;
+}
+
+// ---------------------------------------------------------------- per-operator pieces
+// Partials of the data term / TV term written by the step kernels.
+int step_parts_a(const tvs_problem* P) {
+  switch (P->desc.op.kind) {
+    case TVS_OP_GAUSS_BLUR: return tile_blocks_2d(P->dims.ny, P->dims.nx);
+    case TVS_OP_PARALLEL_BEAM: return ct_fwd_blocks(P->geom);
+    default: return pointwise_blocks(P->n);
+  }
+}
+int step_parts_b(const tvs_problem* P) {
+  switch (P->desc.op.kind) {
+    case TVS_OP_GAUSS_BLUR: return tile_blocks_2d(P->dims.ny, P->dims.nx);
+    case TVS_OP_PARALLEL_BEAM: return ct_bwd_blocks(P->geom);
+    default: return pointwise_blocks(P->n);
+  }
+}
+
+// out = src - gamma A^T(A src - b) + ch h; partials of F(src) into part_a/part_b.
+tvs_status fb_step(tvs_problem* P, const float* src, float* out, const float* h, float gamma,
+                   float ch, cudaStream_t s) {
+  const Dims& d = P->dims;
+  switch (P->desc.op.kind) {
+    case TVS_OP_GAUSS_BLUR:
+      CUDA_TRY(launch_blur_residual(d.ny, d.nx, src, P->b, P->r, P->bw, P->part_a, P->part_b, s));
+      CUDA_TRY(launch_blur_step(d.ny, d.nx, P->r, src, h, out, P->bw, gamma, ch, nullptr, s));
+      break;
+    case TVS_OP_PARALLEL_BEAM:
+      CUDA_TRY(launch_ct_forward(P->geom, src, P->r, nullptr, P->b, 0.f, P->part_a, CT_FWD_RESID, s));
+      CUDA_TRY(launch_ct_backward(P->geom, P->r, src, h, out, gamma, ch, P->part_b, s));
+      break;
+    default:
+      CUDA_TRY(launch_identity_step(d, src, P->b, h, out, gamma, ch, P->part_a, P->part_b, s));
+  }
+  return TVS_OK;
+}
+
+// Partials of F(x) only; returns their counts.
+tvs_status objective_parts(tvs_problem* P, const float* x, double* pa, double* pb, int* na, int* nb,
+                           cudaStream_t s) {
+  const Dims& d = P->dims;
+  switch (P->desc.op.kind) {
+    case TVS_OP_GAUSS_BLUR:
+      CUDA_TRY(launch_blur_residual(d.ny, d.nx, x, P->b, nullptr, P->bw, pa, pb, s));
+      *na = *nb = tile_blocks_2d(d.ny, d.nx);
+      break;
+    case TVS_OP_PARALLEL_BEAM:
+      CUDA_TRY(launch_ct_forward(P->geom, x, P->r, nullptr, P->b, 0.f, pa, CT_FWD_STORE, s));
+      CUDA_TRY(launch_tv_partials(d, x, pb, s));
+      *na = ct_fwd_blocks(P->geom);
+      *nb = pointwise_blocks(P->n);
+      break;
+    default:
+      CUDA_TRY(launch_identity_step(d, x, P->b, nullptr, nullptr, 0.f, 0.f, pa, pb, s));
+      *na = *nb = pointwise_blocks(P->n);
+  }
+  return TVS_OK;
+}
+
+// PDHG pieces.  Backward step: out = x - sigma A^T y + ch h, TV(x) partials -> part_b.
+tvs_status pd_backward(tvs_problem* P, const float* x, float* out, const float* h, float sigma,
+                       float ch, cudaStream_t s) {
+  const Dims& d = P->dims;
+  switch (P->desc.op.kind) {
+    case TVS_OP_GAUSS_BLUR:
+      CUDA_TRY(launch_blur_step(d.ny, d.nx, P->y, x, h, out, P->bw, sigma, ch, P->part_b, s));
+      break;
+    case TVS_OP_PARALLEL_BEAM:
+      CUDA_TRY(launch_ct_backward(P->geom, P->y, x, h, out, sigma, ch, P->part_b, s));
+      break;
+    default:
+      CUDA_TRY(launch_axpy_step(d, P->y, x, h, out, sigma, ch, P->part_b, s));
+  }
+  return TVS_OK;
+}
+int pd_parts_a(const tvs_problem* P) {
+  switch (P->desc.op.kind) {
+    case TVS_OP_GAUSS_BLUR: return tile_blocks_2d(P->dims.ny, P->dims.nx);
+    case TVS_OP_PARALLEL_BEAM: return ct_fwd_blocks(P->geom);
+    default: return pointwise_blocks(P->m);
+  }
+}
+int pd_parts_b(const tvs_problem* P) {
+  switch (P->desc.op.kind) {
+    case TVS_OP_GAUSS_BLUR: return tile_blocks_2d(P->dims.ny, P->dims.nx);
+    case TVS_OP_PARALLEL_BEAM: return ct_bwd_blocks(P->geom);
+    default: return pointwise_blocks(P->n);
+  }
+}
+// Forward dual step: y = prox_{tau f*}(y + tau A(2 x - x_prev)) using axp = A x_prev;
+// axp <- A x; data partials of F(x) -> part_a.  init: only axp <- A x and partials.
+tvs_status pd_forward(tvs_problem* P, const float* x, float tau, bool init, cudaStream_t s) {
+  const Dims& d = P->dims;
+  switch (P->desc.op.kind) {
+    case TVS_OP_GAUSS_BLUR:
+      if (init) {
+        CUDA_TRY(launch_blur_residual(d.ny, d.nx, x, P->b, nullptr, P->bw, P->part_a, nullptr, s));
+        CUDA_TRY(launch_blur(d.ny, d.nx, x, P->axp, P->bw, s));
+      } else {
+        CUDA_TRY(launch_blur_pd_dual(d.ny, d.nx, x, P->axp, P->y, P->b, P->bw, tau, P->part_a, s));
+      }
+      break;
+    case TVS_OP_PARALLEL_BEAM:
+      CUDA_TRY(launch_ct_forward(P->geom, x, P->axp, init ? nullptr : P->y, P->b, tau, P->part_a,
+                                 init ? CT_FWD_STORE : CT_FWD_PD, s));
+      break;
+    default:
+      if (init) {
+        CUDA_TRY(launch_identity_step(d, x, P->b, nullptr, nullptr, 0.f, 0.f, P->part_a, nullptr, s));
+        CUDA_TRY(cudaMemcpyAsync(P->axp, x, P->n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+      } else {
+        CUDA_TRY(launch_pd_dual_pointwise(P->m, x, P->axp, P->y, P->b, tau, P->part_a, s));
+      }
+  }
+  return TVS_OK;
+}
+
+struct GraphSet {
+  cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [coin][parity]
+  ~GraphSet() {
+    for (auto& row : exec)
+      for (auto& e : row)
+        if (e) cudaGraphExecDestroy(e);
+  }
+};
+
+template <typename F>
+tvs_status capture(cudaStream_t s, cudaGraphExec_t* exec, F&& body) {
+  cudaGraph_t g = nullptr;
+  CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  tvs_status st = body();
+  cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (st != TVS_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(TVS_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(TVS_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+  return TVS_OK;
+}
+
+// Shared outer-loop machinery: pacing, trace readback.
+struct LoopState {
+  int iters = 0;
+  int prox = 0;
+};
+
+tvs_status run_loop(tvs_problem* P, int K, const std::vector<unsigned char>& coins, GraphSet& G,
+                    LoopState* ls) {
+  tvs_ctx* C = P->ctx;
+  cudaStream_t s = C->stream;
+  for (int k = 0; k < K; ++k) {
+    if (k >= LAG) {
+      CUDA_TRY(cudaEventSynchronize(C->ring[k % LAG]));
+      if (*(volatile int*)P->done_host) break;
+    }
+    const int c = coins[k] ? 1 : 0;
+    CUDA_TRY(cudaGraphLaunch(G.exec[c][k & 1], s));
+    CUDA_TRY(cudaEventRecord(C->ring[k % LAG], s));
+    ls->iters = k + 1;
+    ls->prox += c;
+  }
+  return TVS_OK;
+}
+
+tvs_status begin_solve(tvs_problem* P, int K, int flags_counter_start) {
+  cudaStream_t s = P->ctx->stream;
+  TVS_TRY(ensure_trace(P, K));
+  *(volatile int*)P->done_host = 0;
+  int f[4] = {0, -1, flags_counter_start, 0};
+  CUDA_TRY(cudaMemcpyAsync(P->flags, f, sizeof(f), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemsetAsync(P->obj_dev, 0xff, sizeof(double) * (K + 1), s));  // NaN pattern
+  CUDA_TRY(cudaEventRecord(P->ctx->ev_start, s));
+  CUDA_TRY(launch_timestamp(P->ts_dev + P->trace_cap, s));
+  return TVS_OK;
+}
+
+tvs_status zero_dual(tvs_problem* P, int dtype) {
+  CUDA_TRY(cudaMemsetAsync(P->dual[0], 0, dual_elem_bytes(dtype) * P->dims.ndim * P->n, P->ctx->stream));
+  return TVS_OK;
+}
+
+tvs_status finish_solve(tvs_problem* P, int K, const LoopState& ls,
+                        const std::vector<unsigned char>& coins, int n_inner, tvs_trace* tr) {
+  tvs_ctx* C = P->ctx;
+  cudaStream_t s = C->stream;
+  CUDA_TRY(cudaEventRecord(C->ev_stop, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  const int iters = ls.iters;
+  std::vector<double> obj(iters > 0 ? iters : 1);
+  std::vector<unsigned long long> ts(iters + 1);
+  int flags[4];
+  if (iters > 0) {
+    CUDA_TRY(cudaMemcpy(obj.data(), P->obj_dev, sizeof(double) * iters, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(ts.data(), P->ts_dev, sizeof(unsigned long long) * iters, cudaMemcpyDeviceToHost));
+  }
+  CUDA_TRY(cudaMemcpy(&ts[iters], P->ts_dev + P->trace_cap, sizeof(unsigned long long),
+                      cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemcpy(flags, P->flags, sizeof(flags), cudaMemcpyDeviceToHost));
+  const unsigned long long t0 = ts[iters];
+  float solve_ms = 0.f;
+  CUDA_TRY(cudaEventElapsedTime(&solve_ms, C->ev_start, C->ev_stop));
+  double fgp_ms = 0.0;
+  const int nprox = flags[3];
+  if (nprox > 0) {
+    std::vector<unsigned long long> f(2 * (size_t)nprox);
+    CUDA_TRY(cudaMemcpy(f.data(), P->fgp_ts, sizeof(unsigned long long) * f.size(), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < nprox; ++i) fgp_ms += (double)(f[2 * i + 1] - f[2 * i]) * 1e-6;
+  }
+  bool bad = false;
+  for (int k = 0; k < iters; ++k) {
+    // NaN entries between evaluations carry the 0xff pattern; non-finite
+    // evaluated objectives signal divergence or bad input.
+    if (std::isinf(obj[k])) bad = true;
+  }
+  if (iters > 0 && !std::isnan(obj[iters - 1]) && !is_fin(obj[iters - 1])) bad = true;
+  if (tr) {
+    tr->iters_run = iters;
+    tr->prox_calls = ls.prox;
+    tr->reached = flags[0];
+    tr->reached_iter = flags[0] ? flags[1] : -1;
+    tr->time_to_target_s = -1.0;
+    if (flags[0] && flags[1] >= 0 && flags[1] < iters)
+      tr->time_to_target_s = (double)(ts[flags[1]] - t0) * 1e-9;
+    tr->solve_ms = solve_ms;
+    tr->fgp_ms = fgp_ms;
+    tr->fgp_launches = (long long)nprox * n_inner;
+    tr->fgp_pixel_iters = (long long)nprox * n_inner * (long long)P->n;
+    const int lim = tr->cap < iters ? tr->cap : iters;
+    for (int k = 0; k < lim; ++k) {
+      if (tr->objective) tr->objective[k] = obj[k];
+      if (tr->coins) tr->coins[k] = coins[k];
+      if (tr->t_s) tr->t_s[k] = std::isnan(obj[k]) ? NAN : (double)(ts[k] - t0) * 1e-9;
+    }
+  }
+  if (bad) return fail(TVS_ENUMERIC, "non-finite objective during the solve");
+  return TVS_OK;
+}
+
+tvs_status check_common(tvs_problem* P, int max_iter, int n_inner, int dual, double f_star,
+                        double target, int every, const float* x) {
+  if (!P) return fail(TVS_EINVAL, "null problem");
+  if (!x) return fail(TVS_EINVAL, "null x_inout");
+  if (max_iter < 0 || n_inner < 0) return fail(TVS_EINVAL, "max_iter and n_inner must be >= 0");
+  if (!valid_dual(dual)) return fail(TVS_EINVAL, "invalid dual dtype %d", dual);
+  if (!is_fin(f_star) || !is_fin(target) || target < 0) return fail(TVS_EINVAL, "invalid f_star/target");
+  if (every < 0) return fail(TVS_EINVAL, "objective_every must be >= 1");
+  return TVS_OK;
+}
+
+enum FBKind { FB_PGD, FB_FISTA, FB_PROXSKIP };
+
+tvs_status fb_solve(tvs_problem* P, const tvs_fb_params* prm, float* x_io, tvs_mem mem,
+                    tvs_trace* tr, FBKind kind) {
+  if (!prm) return fail(TVS_EINVAL, "null params");
+  TVS_TRY(check_common(P, prm->max_iter, prm->n_inner, prm->dual, prm->f_star, prm->target_rel_gap,
+                       prm->objective_every, x_io));
+  if (!(prm->gamma > 0) || !is_fin(prm->gamma)) return fail(TVS_EINVAL, "gamma must be > 0");
+  const double p = kind == FB_PROXSKIP ? prm->p : 1.0;
+  if (!(p > 0.0 && p <= 1.0)) return fail(TVS_EINVAL, "p must lie in (0, 1]");
+  if (mem != TVS_MEM_DEVICE && mem != TVS_MEM_HOST) return fail(TVS_EINVAL, "invalid mem kind");
+  const int K = prm->max_iter, N = prm->n_inner, every = prm->objective_every < 1 ? 1 : prm->objective_every;
+  const int dtype = prm->dual;
+  const bool nonneg = P->desc.nonneg != 0;
+  const double gamma = prm->gamma, alpha = P->desc.alpha;
+  const double lam_d = (kind == FB_PROXSKIP ? gamma / p : gamma) * alpha;
+  const float lam = (float)lam_d;
+  const bool use_prox = lam_d > 0.0;
+  tvs_ctx* C = P->ctx;
+  cudaStream_t s = C->stream;
+  const Dims& d = P->dims;
+  const std::vector<float> betas = fgp_betas(N);
+
+  std::vector<unsigned char> coins(K, 1);
+  if (kind == FB_PROXSKIP)
+    for (int k = 0; k < K; ++k) coins[k] = (unsigned char)tvs_coin(prm->seed, p, k);
+
+  TVS_TRY(begin_solve(P, K, kind == FB_FISTA ? 0 : -1));
+  TVS_TRY(copy_in(P->x[0], x_io, P->n, mem, s));
+  TVS_TRY(zero_dual(P, dtype));
+  float* aux = P->h;  // control variate h (ProxSkip) or extrapolated point y (FISTA)
+  if (kind == FB_PROXSKIP) CUDA_TRY(cudaMemsetAsync(P->h, 0, P->n * sizeof(float), s));
+  if (kind == FB_FISTA) {
+    CUDA_TRY(cudaMemcpyAsync(aux, P->x[0], P->n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    std::vector<float> bx(K > 0 ? K : 1, 0.f);
+    double t = 1.0;
+    for (int k = 0; k < K; ++k) {
+      const double tn = (1.0 + std::sqrt(1.0 + 4.0 * t * t)) / 2.0;
+      bx[k] = (float)((t - 1.0) / tn);
+      t = tn;
+    }
+    CUDA_TRY(cudaMemcpyAsync(P->beta_dev, bx.data(), sizeof(float) * bx.size(), cudaMemcpyHostToDevice, s));
+  }
+  const int na = step_parts_a(P), nb = step_parts_b(P);
+  const float fgamma = (float)gamma;
+  const float h_coef = (float)(p / gamma);
+
+  GraphSet G;
+  for (int c = 0; c < 2; ++c) {
+    if (c == 0 && kind != FB_PROXSKIP) continue;
+    for (int par = 0; par < 2; ++par) {
+      float* xc = P->x[par];
+      float* xn = P->x[par ^ 1];
+      TVS_TRY(capture(s, &G.exec[c][par], [&]() -> tvs_status {
+        if (kind == FB_PROXSKIP) {
+          if (c == 0) {
+            TVS_TRY(fb_step(P, xc, xn, P->h, fgamma, fgamma, s));
+          } else {
+            TVS_TRY(fb_step(P, xc, P->z, P->h, fgamma, (float)(gamma - gamma / p), s));
+          }
+        } else {
+          TVS_TRY(fb_step(P, kind == FB_FISTA ? aux : xc, P->z, nullptr, fgamma, 0.f, s));
+        }
+        if (kind != FB_FISTA)
+          CUDA_TRY(launch_reduce_record(P->part_a, na, P->part_b, nb, alpha, every, P->obj_dev,
+                                        P->ts_dev, prm->f_star, prm->target_rel_gap, P->flags,
+                                        P->done_host_dev, nullptr, s));
+        if (c == 1) {
+          int fin = 0;
+          CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 0, s));
+          if (use_prox) TVS_TRY(launch_fgp_sequence(d, P->z, P->dual, N, betas, lam, dtype, nonneg, s, &fin));
+          CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 1, s));
+          CUDA_TRY(launch_fgp_finalize(d, P->z, P->dual[fin], dtype, use_prox ? lam : 0.f, nonneg, xn,
+                                       kind == FB_PROXSKIP ? P->h : nullptr, h_coef,
+                                       fin != 0 ? P->dual[0] : nullptr, xc,
+                                       kind == FB_FISTA ? aux : nullptr, P->beta_dev, P->flags + 2, s));
+        }
+        if (kind == FB_FISTA) {
+          int a = 0, b = 0;
+          TVS_TRY(objective_parts(P, xn, P->part_a, P->part_b, &a, &b, s));
+          CUDA_TRY(launch_reduce_record(P->part_a, a, P->part_b, b, alpha, every, P->obj_dev,
+                                        P->ts_dev, prm->f_star, prm->target_rel_gap, P->flags,
+                                        P->done_host_dev, nullptr, s));
+        }
+        return TVS_OK;
+      }));
+    }
+  }
+  LoopState ls;
+  TVS_TRY(run_loop(P, K, coins, G, &ls));
+  float* xfin = P->x[ls.iters & 1];
+  if (kind != FB_FISTA && ls.iters > 0) {
+    int a = 0, b = 0;
+    TVS_TRY(objective_parts(P, xfin, P->part_a, P->part_b, &a, &b, s));
+    CUDA_TRY(launch_reduce_record(P->part_a, a, P->part_b, b, alpha, 1, P->obj_dev, P->ts_dev,
+                                  prm->f_star, prm->target_rel_gap, P->flags, P->done_host_dev,
+                                  nullptr, s));
+  }
+  TVS_TRY(copy_out(x_io, xfin, P->n, mem, s));
+  return finish_solve(P, K, ls, coins, use_prox ? N : 0, tr);
+}
+
+tvs_status pd_solve(tvs_problem* P, const tvs_pd_params* prm, float* x_io, float* y_io, tvs_mem mem,
+                    tvs_trace* tr, bool skip) {
+  if (!prm) return fail(TVS_EINVAL, "null params");
+  TVS_TRY(check_common(P, prm->max_iter, prm->n_inner, prm->dual, prm->f_star, prm->target_rel_gap,
+                       prm->objective_every, x_io));
+  if (!y_io) return fail(TVS_EINVAL, "null y_inout");
+  if (!(prm->sigma > 0) || !(prm->tau > 0) || !is_fin(prm->sigma) || !is_fin(prm->tau))
+    return fail(TVS_EINVAL, "sigma and tau must be > 0");
+  const double p = skip ? prm->p : 1.0;
+  if (!(p > 0.0 && p <= 1.0)) return fail(TVS_EINVAL, "p must lie in (0, 1]");
+  if (mem != TVS_MEM_DEVICE && mem != TVS_MEM_HOST) return fail(TVS_EINVAL, "invalid mem kind");
+  if (P->dims.ndim != 2) return fail(TVS_EUNSUPPORTED, "primal-dual solvers are 2D");
+  const int K = prm->max_iter, N = prm->n_inner, every = prm->objective_every < 1 ? 1 : prm->objective_every;
+  const int dtype = prm->dual;
+  const bool nonneg = P->desc.nonneg != 0;
+  const double sigma = prm->sigma, tau = prm->tau, alpha = P->desc.alpha;
+  const double lam_d = (skip ? sigma / p : sigma) * alpha;
+  const float lam = (float)lam_d;
+  const bool use_prox = lam_d > 0.0;
+  tvs_ctx* C = P->ctx;
+  cudaStream_t s = C->stream;
+  const Dims& d = P->dims;
+  const std::vector<float> betas = fgp_betas(N);
+  std::vector<unsigned char> coins(K, 1);
+  if (skip)
+    for (int k = 0; k < K; ++k) coins[k] = (unsigned char)tvs_coin(prm->seed, p, k);
+
+  TVS_TRY(begin_solve(P, K, -1));
+  TVS_TRY(copy_in(P->x[0], x_io, P->n, mem, s));
+  TVS_TRY(copy_in(P->y, y_io, P->m, mem, s));
+  TVS_TRY(zero_dual(P, dtype));
+  if (skip) CUDA_TRY(cudaMemsetAsync(P->h, 0, P->n * sizeof(float), s));
+  TVS_TRY(pd_forward(P, P->x[0], (float)tau, true, s));
+  const int na = pd_parts_a(P), nb = pd_parts_b(P);
+  const float fs = (float)sigma, ft = (float)tau;
+  GraphSet G;
+  for (int c = 0; c < 2; ++c) {
+    if (c == 0 && !skip) continue;
+    for (int par = 0; par < 2; ++par) {
+      float* xc = P->x[par];
+      float* xn = P->x[par ^ 1];
+      TVS_TRY(capture(s, &G.exec[c][par], [&]() -> tvs_status {
+        if (skip) {
+          if (c == 0) TVS_TRY(pd_backward(P, xc, xn, P->h, fs, fs, s));
+          else TVS_TRY(pd_backward(P, xc, P->z, P->h, fs, (float)(sigma - sigma / p), s));
+        } else {
+          TVS_TRY(pd_backward(P, xc, P->z, nullptr, fs, 0.f, s));
+        }
+        CUDA_TRY(launch_reduce_record(P->part_a, na, P->part_b, nb, alpha, every, P->obj_dev,
+                                      P->ts_dev, prm->f_star, prm->target_rel_gap, P->flags,
+                                      P->done_host_dev, nullptr, s));
+        if (c == 1) {
+          int fin = 0;
+          CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 0, s));
+          if (use_prox) TVS_TRY(launch_fgp_sequence(d, P->z, P->dual, N, betas, lam, dtype, nonneg, s, &fin));
+          CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 1, s));
+          CUDA_TRY(launch_fgp_finalize(d, P->z, P->dual[fin], dtype, use_prox ? lam : 0.f, nonneg, xn,
+                                       skip ? P->h : nullptr, (float)(p / sigma),
+                                       fin != 0 ? P->dual[0] : nullptr, nullptr, nullptr, nullptr,
+                                       nullptr, s));
+        }
+        TVS_TRY(pd_forward(P, xn, ft, false, s));
+        return TVS_OK;
+      }));
+    }
+  }
+  LoopState ls;
+  TVS_TRY(run_loop(P, K, coins, G, &ls));
+  float* xfin = P->x[ls.iters & 1];
+  if (ls.iters > 0) {
+    CUDA_TRY(launch_tv_partials(d, xfin, P->part_b, s));
+    CUDA_TRY(launch_reduce_record(P->part_a, na, P->part_b, pointwise_blocks(P->n), alpha, 1,
+                                  P->obj_dev, P->ts_dev, prm->f_star, prm->target_rel_gap, P->flags,
+                                  P->done_host_dev, nullptr, s));
+  }
+  TVS_TRY(copy_out(x_io, xfin, P->n, mem, s));
+  TVS_TRY(copy_out(y_io, P->y, P->m, mem, s));
+  return finish_solve(P, K, ls, coins, use_prox ? N : 0, tr);
+}
+
+}  // namespace
+
+// =====================================================================================
+extern "C" {
+
+const char* tvs_last_error(void) { return g_err.c_str(); }
+
+tvs_status tvs_create(tvs_ctx** out, int device, void* cuda_stream) {
+  if (!out) return fail(TVS_EINVAL, "null output pointer");
+  *out = nullptr;
+  int ndev = 0;
+  CUDA_TRY(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(TVS_EINVAL, "device %d out of range (%d devices)", device, ndev);
+  CUDA_TRY(cudaSetDevice(device));
+  tvs_ctx* C = new tvs_ctx();
+  C->device = device;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  if (s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread) {
+    cudaError_t e = cudaStreamCreateWithFlags(&C->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete C;
+      return fail(TVS_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+    }
+    C->own_stream = true;
+  } else {
+    C->stream = s;
+  }
+  cudaError_t e = cudaEventCreate(&C->ev_start);
+  if (e == cudaSuccess) e = cudaEventCreate(&C->ev_stop);
+  for (int i = 0; i < LAG && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&C->ring[i], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMalloc(&C->red_out, sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&C->flags, 4 * sizeof(int));
+  if (e != cudaSuccess) {
+    tvs_destroy(C);
+    return fail(TVS_ECUDA, "context setup: %s", cudaGetErrorString(e));
+  }
+  *out = C;
+  return TVS_OK;
+}
+
+tvs_status tvs_destroy(tvs_ctx* C) {
+  if (!C) return TVS_OK;
+  cudaSetDevice(C->device);
+  if (C->stream) cudaStreamSynchronize(C->stream);
+  dfree(C->prox_scratch);
+  dfree(C->red_out);
+  dfree(C->flags);
+  dfree(C->parts);
+  if (C->ev_start) cudaEventDestroy(C->ev_start);
+  if (C->ev_stop) cudaEventDestroy(C->ev_stop);
+  for (auto& ev : C->ring)
+    if (ev) cudaEventDestroy(ev);
+  if (C->own_stream && C->stream) cudaStreamDestroy(C->stream);
+  delete C;
+  return TVS_OK;
+}
+
+size_t tvs_device_bytes(const tvs_ctx* C) { return C ? C->bytes : 0; }
+
+tvs_status tvs_problem_create(tvs_ctx* C, const tvs_problem_desc* desc, const float* b,
+                              tvs_mem b_mem, tvs_problem** out) {
+  if (!C || !desc || !b || !out) return fail(TVS_EINVAL, "null argument");
+  *out = nullptr;
+  const tvs_problem_desc& D = *desc;
+  if (D.ndim != 2 && D.ndim != 3) return fail(TVS_EINVAL, "ndim must be 2 or 3");
+  if (D.nx < 1 || D.ny < 1 || D.nz < 1) return fail(TVS_EINVAL, "dims must be >= 1");
+  if (D.ndim == 2 && D.nz != 1) return fail(TVS_EINVAL, "2D problems need nz = 1");
+  if (!(D.alpha >= 0) || !is_fin(D.alpha)) return fail(TVS_EINVAL, "alpha must be finite and >= 0");
+  if (b_mem != TVS_MEM_DEVICE && b_mem != TVS_MEM_HOST) return fail(TVS_EINVAL, "invalid mem kind");
+  const tvs_op_desc& op = D.op;
+  if (op.kind != TVS_OP_IDENTITY && op.kind != TVS_OP_GAUSS_BLUR && op.kind != TVS_OP_PARALLEL_BEAM)
+    return fail(TVS_EINVAL, "invalid operator kind");
+  if (op.kind != TVS_OP_IDENTITY && D.ndim != 2) return fail(TVS_EUNSUPPORTED, "3D supports the identity operator only");
+  if (op.kind == TVS_OP_GAUSS_BLUR &&
+      (op.blur_radius < 1 || op.blur_radius > 8 || !(op.blur_sigma > 0) || !is_fin(op.blur_sigma)))
+    return fail(TVS_EINVAL, "blur needs 1 <= radius <= 8 and sigma > 0");
+  if (op.kind == TVS_OP_PARALLEL_BEAM &&
+      (D.nx != D.ny || op.n_angles < 1 || op.n_det < 1 || !(op.pixel_size > 0) || !(op.det_spacing > 0)))
+    return fail(TVS_EINVAL, "parallel beam needs a square image, n_angles, n_det >= 1 and positive spacings");
+  const size_t n = (size_t)D.nx * D.ny * D.nz;
+  if (n > ((size_t)1 << 34)) return fail(TVS_EINVAL, "image too large");
+  CUDA_TRY(cudaSetDevice(C->device));
+  tvs_problem* P = new tvs_problem();
+  P->ctx = C;
+  P->desc = D;
+  P->dims.nx = D.nx;
+  P->dims.ny = D.ny;
+  P->dims.nz = D.nz;
+  P->dims.ndim = D.ndim;
+  P->n = n;
+  P->m = op.kind == TVS_OP_PARALLEL_BEAM ? (size_t)op.n_angles * op.n_det : n;
+  auto bail = [&](tvs_status st) {
+    tvs_problem_destroy(P);
+    return st;
+  };
+  if (op.kind == TVS_OP_GAUSS_BLUR) {
+    const int R = op.blur_radius;
+    double w[17], sum = 0.0;
+    for (int i = -R; i <= R; ++i) sum += (w[i + R] = std::exp(-(double)(i * i) / (2.0 * op.blur_sigma * op.blur_sigma)));
+    P->bw.R = R;
+    for (int i = 0; i < 17; ++i) P->bw.w[i] = i <= 2 * R ? (float)(w[i] / sum) : 0.f;
+  }
+  tvs_status st;
+  const size_t n_img = n, m = P->m;
+  if ((st = palloc(P, &P->b, m)) || (st = palloc(P, &P->x[0], n_img)) || (st = palloc(P, &P->x[1], n_img)) ||
+      (st = palloc(P, &P->z, n_img)) || (st = palloc(P, &P->h, n_img)) || (st = palloc(P, &P->r, m)) ||
+      (st = palloc(P, &P->y, m)) || (st = palloc(P, &P->axp, m)))
+    return bail(st);
+  for (int i = 0; i < 3; ++i)
+    if ((st = dalloc(C, &P->bytes, &P->dual[i], 4 * (size_t)D.ndim * n_img))) return bail(st);
+  if (op.kind == TVS_OP_PARALLEL_BEAM) {
+    if ((st = palloc(P, &P->angle_tab, (size_t)op.n_angles)) || (st = palloc(P, &P->xt, n_img))) return bail(st);
+    P->geom.N = D.nx;
+    P->geom.n_angles = op.n_angles;
+    P->geom.n_det = op.n_det;
+    P->geom.pixel_size = (float)op.pixel_size;
+    P->geom.det_spacing = (float)op.det_spacing;
+    P->geom.angles = P->angle_tab;
+    P->geom.xt_scratch = P->xt;
+    cudaError_t e = ct_build_angle_table(P->geom, P->angle_tab, C->stream);
+    if (e != cudaSuccess) return bail(fail(TVS_ECUDA, "angle table: %s", cudaGetErrorString(e)));
+  }
+  int parts = tile_blocks_2d(D.ny * D.nz, D.nx);
+  parts = std::max(parts, pointwise_blocks(n_img));
+  parts = std::max(parts, pointwise_blocks(m));
+  if (op.kind == TVS_OP_PARALLEL_BEAM) {
+    parts = std::max(parts, ct_fwd_blocks(P->geom));
+    parts = std::max(parts, ct_bwd_blocks(P->geom));
+  }
+  P->max_parts = parts;
+  if ((st = palloc(P, &P->part_a, (size_t)parts)) || (st = palloc(P, &P->part_b, (size_t)parts)) ||
+      (st = palloc(P, &P->flags, 4)) || (st = palloc(P, &P->count, 1)))
+    return bail(st);
+  {
+    cudaError_t e = cudaHostAlloc((void**)&P->done_host, sizeof(int), cudaHostAllocMapped);
+    if (e != cudaSuccess) {
+      P->done_host = nullptr;
+      return bail(fail(TVS_ENOMEM, "cudaHostAlloc: %s", cudaGetErrorString(e)));
+    }
+    *P->done_host = 0;
+    e = cudaHostGetDevicePointer((void**)&P->done_host_dev, P->done_host, 0);
+    if (e != cudaSuccess) return bail(fail(TVS_ECUDA, "cudaHostGetDevicePointer: %s", cudaGetErrorString(e)));
+  }
+  if ((st = tvs_problem_set_data(P, b, b_mem))) return bail(st);
+  *out = P;
+  return TVS_OK;
+}
+
+tvs_status tvs_problem_set_data(tvs_problem* P, const float* b, tvs_mem b_mem) {
+  if (!P || !b) return fail(TVS_EINVAL, "null argument");
+  if (b_mem != TVS_MEM_DEVICE && b_mem != TVS_MEM_HOST) return fail(TVS_EINVAL, "invalid mem kind");
+  cudaStream_t s = P->ctx->stream;
+  TVS_TRY(copy_in(P->b, b, P->m, b_mem, s));
+  CUDA_TRY(cudaMemsetAsync(P->count, 0, sizeof(int), s));
+  CUDA_TRY(launch_count_nonfinite(P->b, P->m, P->count, s));
+  int cnt = 0;
+  CUDA_TRY(cudaMemcpyAsync(&cnt, P->count, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (cnt) return fail(TVS_ENUMERIC, "b holds %d non-finite values", cnt);
+  return TVS_OK;
+}
+
+tvs_status tvs_problem_destroy(tvs_problem* P) {
+  if (!P) return TVS_OK;
+  tvs_ctx* C = P->ctx;
+  cudaSetDevice(C->device);
+  cudaStreamSynchronize(C->stream);
+  void* bufs[] = {P->b, P->x[0], P->x[1], P->z, P->h, P->r, P->y, P->axp, P->dual[0], P->dual[1],
+                  P->dual[2], P->part_a, P->part_b, P->obj_dev, P->ts_dev, P->fgp_ts, P->beta_dev,
+                  P->flags, P->count, P->angle_tab, P->xt};
+  for (void* b : bufs) dfree(b);
+  if (P->done_host) cudaFreeHost(P->done_host);
+  C->bytes -= P->bytes;
+  delete P;
+  return TVS_OK;
+}
+
+tvs_status tvs_op_apply(tvs_problem* P, const float* x, float* y, int adjoint) {
+  if (!P || !x || !y) return fail(TVS_EINVAL, "null argument");
+  cudaStream_t s = P->ctx->stream;
+  const Dims& d = P->dims;
+  switch (P->desc.op.kind) {
+    case TVS_OP_GAUSS_BLUR:
+      CUDA_TRY(launch_blur(d.ny, d.nx, x, y, P->bw, s));
+      break;
+    case TVS_OP_PARALLEL_BEAM:
+      if (adjoint) CUDA_TRY(launch_ct_backward(P->geom, x, nullptr, nullptr, y, 0.f, 0.f, nullptr, s));
+      else CUDA_TRY(launch_ct_forward(P->geom, x, y, nullptr, nullptr, 0.f, nullptr, CT_FWD_PLAIN, s));
+      break;
+    default:
+      CUDA_TRY(cudaMemcpyAsync(y, x, P->n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  }
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return TVS_OK;
+}
+
+tvs_status tvs_objective(tvs_problem* P, const float* x, double* out) {
+  if (!P || !x || !out) return fail(TVS_EINVAL, "null argument");
+  cudaStream_t s = P->ctx->stream;
+  int na = 0, nb = 0;
+  TVS_TRY(objective_parts(P, x, P->part_a, P->part_b, &na, &nb, s));
+  CUDA_TRY(launch_reduce_record(P->part_a, na, P->part_b, nb, P->desc.alpha, 1, nullptr, nullptr, 0.0,
+                                0.0, nullptr, nullptr, P->ctx->red_out, s));
+  CUDA_TRY(cudaMemcpyAsync(out, P->ctx->red_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return TVS_OK;
+}
+
+tvs_status tv_prox(tvs_ctx* C, int ndim, const int dims[3], const float* z, float* u, double lambda,
+                   int n_iter, tvs_dual_dtype dual, void* dual_state, int nonneg) {
+  if (!C || !dims || !z || !u) return fail(TVS_EINVAL, "null argument");
+  if (ndim != 2 && ndim != 3) return fail(TVS_EINVAL, "ndim must be 2 or 3");
+  if (dims[0] < 1 || dims[1] < 1 || (ndim == 3 && dims[2] < 1)) return fail(TVS_EINVAL, "dims must be >= 1");
+  if (!(lambda >= 0) || !is_fin(lambda)) return fail(TVS_EINVAL, "lambda must be finite and >= 0");
+  if (n_iter < 0) return fail(TVS_EINVAL, "n_iter must be >= 0");
+  if (!valid_dual(dual)) return fail(TVS_EINVAL, "invalid dual dtype");
+  if (z == u) return fail(TVS_EINVAL, "z and u may not alias");
+  Dims d;
+  d.nx = dims[0];
+  d.ny = dims[1];
+  d.nz = ndim == 3 ? dims[2] : 1;
+  d.ndim = ndim;
+  const size_t n = d.n();
+  const size_t plane_bytes = dual_elem_bytes(dual) * ndim * n;
+  const size_t need = plane_bytes * (dual_state ? 2 : 3);
+  cudaStream_t s = C->stream;
+  if (need > C->prox_scratch_bytes) {
+    dfree(C->prox_scratch);
+    C->bytes -= C->prox_scratch_bytes;
+    C->prox_scratch = nullptr;
+    C->prox_scratch_bytes = 0;
+    TVS_TRY(dalloc(C, nullptr, &C->prox_scratch, need));
+    C->prox_scratch_bytes = need;
+  }
+  char* sc = (char*)C->prox_scratch;
+  void* buf[3];
+  if (dual_state) {
+    buf[0] = dual_state;
+    buf[1] = sc;
+    buf[2] = sc + plane_bytes;
+  } else {
+    buf[0] = sc;
+    buf[1] = sc + plane_bytes;
+    buf[2] = sc + 2 * plane_bytes;
+    CUDA_TRY(cudaMemsetAsync(buf[0], 0, plane_bytes, s));
+  }
+  const bool use = lambda > 0.0;
+  int fin = 0;
+  if (use) TVS_TRY(launch_fgp_sequence(d, z, buf, n_iter, fgp_betas(n_iter), (float)lambda, dual,
+                                       nonneg != 0, s, &fin));
+  CUDA_TRY(launch_fgp_finalize(d, z, buf[fin], dual, use ? (float)lambda : 0.f, nonneg != 0, u,
+                               nullptr, 0.f, (fin != 0 && dual_state) ? dual_state : nullptr,
+                               nullptr, nullptr, nullptr, nullptr, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return TVS_OK;
+}
+
+tvs_status pgd_solve(tvs_problem* P, const tvs_fb_params* prm, float* x, tvs_mem mem, tvs_trace* tr) {
+  return fb_solve(P, prm, x, mem, tr, FB_PGD);
+}
+tvs_status fista_solve(tvs_problem* P, const tvs_fb_params* prm, float* x, tvs_mem mem, tvs_trace* tr) {
+  return fb_solve(P, prm, x, mem, tr, FB_FISTA);
+}
+tvs_status proxskip_solve(tvs_problem* P, const tvs_fb_params* prm, float* x, tvs_mem mem, tvs_trace* tr) {
+  return fb_solve(P, prm, x, mem, tr, FB_PROXSKIP);
+}
+tvs_status pdhg_solve(tvs_problem* P, const tvs_pd_params* prm, float* x, float* y, tvs_mem mem,
+                      tvs_trace* tr) {
+  return pd_solve(P, prm, x, y, mem, tr, false);
+}
+tvs_status pdhgskip_solve(tvs_problem* P, const tvs_pd_params* prm, float* x, float* y, tvs_mem mem,
+                          tvs_trace* tr) {
+  return pd_solve(P, prm, x, y, mem, tr, true);
+}
+
+int tvs_coin(uint64_t seed, double p, int64_t k) {
+  if (!(p > 0.0 && p <= 1.0)) return -1;
+  return Philox4x64::coin(seed, p, (uint64_t)k);
+}
+
+tvs_status tvs_coin_schedule_device(tvs_ctx* C, uint64_t seed, double p, int64_t k0, int K,
+                                    unsigned char* out) {
+  if (!C || (!out && K > 0) || K < 0) return fail(TVS_EINVAL, "invalid argument");
+  if (!(p > 0.0 && p <= 1.0)) return fail(TVS_EINVAL, "p must lie in (0, 1]");
+  if (K == 0) return TVS_OK;
+  unsigned char* dev = nullptr;
+  TVS_TRY(dalloc(C, nullptr, (void**)&dev, (size_t)K));
+  cudaStream_t s = C->stream;
+  cudaError_t e = launch_coin_schedule(seed, p, k0, K, dev, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, dev, (size_t)K, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(dev);
+  C->bytes -= (size_t)K;
+  if (e != cudaSuccess) return fail(TVS_ECUDA, "coin schedule: %s", cudaGetErrorString(e));
+  return TVS_OK;
+}
+
+}  // extern "C"

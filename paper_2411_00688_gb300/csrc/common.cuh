@@ -1,0 +1,119 @@
+// Shared device helpers: dual-field storage types, Philox4x64-10, reductions.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tvs {
+
+// ---------------------------------------------------------------- storage
+// The TV dual field may be stored as float, bfloat16 or half; arithmetic is
+// always float32 and stores round to nearest even.
+template <typename T> struct Elem;
+template <> struct Elem<float> {
+  static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
+  static __device__ __forceinline__ float ldc(const float* p) { return *p; }
+  static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+};
+template <> struct Elem<__nv_bfloat16> {
+  static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+  static __device__ __forceinline__ float ldc(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+  static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+};
+template <> struct Elem<__half> {
+  static __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
+  static __device__ __forceinline__ float ldc(const __half* p) { return __half2float(*p); }
+  static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+};
+
+// ---------------------------------------------------------------- Philox4x64-10
+// Counter-based generator of Salmon et al. (SC'11): per round,
+// (hi0, lo0) = M0 * c0, (hi1, lo1) = M1 * c2, c <- (hi1^c1^k0, lo1, hi0^c3^k1, lo0),
+// with the key bumped by the Weyl constants between rounds.
+struct Philox4x64 {
+  static constexpr uint64_t M0 = 0xD2E7470EE14C6C93ull;
+  static constexpr uint64_t M1 = 0xCA5A826395121157ull;
+  static constexpr uint64_t W0 = 0x9E3779B97F4A7C15ull;
+  static constexpr uint64_t W1 = 0xBB67AE8584CAA73Bull;
+
+  static __host__ __device__ inline void mulhilo(uint64_t a, uint64_t b, uint64_t* hi, uint64_t* lo) {
+#if defined(__CUDA_ARCH__)
+    *lo = a * b;
+    *hi = __umul64hi(a, b);
+#else
+    unsigned __int128 pr = (unsigned __int128)a * (unsigned __int128)b;
+    *lo = (uint64_t)pr;
+    *hi = (uint64_t)(pr >> 64);
+#endif
+  }
+
+  static __host__ __device__ inline void block(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
+    uint64_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+      if (r > 0) { k0 += W0; k1 += W1; }
+      uint64_t hi0, lo0, hi1, lo1;
+      mulhilo(M0, c0, &hi0, &lo0);
+      mulhilo(M1, c2, &hi1, &lo1);
+      uint64_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+      c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+  }
+
+  // theta_k = [(w >> 11) < p 2^53], exact in double.
+  static __host__ __device__ inline int coin(uint64_t seed, double p, uint64_t k) {
+    uint64_t ctr[4] = {k, 0, 0, 0}, key[2] = {seed, 0}, out[4];
+    block(ctr, key, out);
+    return (double)(out[0] >> 11) < p * 9007199254740992.0 ? 1 : 0;
+  }
+};
+
+// ---------------------------------------------------------------- reductions
+// Sums two per-thread doubles over the block in a fixed order and writes the
+// block totals to part_a[blockLinear], part_b[blockLinear] (deterministic).
+template <int NT>
+__device__ __forceinline__ void block_sum2_store(double a, double b, double* part_a, double* part_b,
+                                                 int block_linear) {
+  __shared__ double sa[NT / 32], sb[NT / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  if (lane == 0) { sa[warp] = a; sb[warp] = b; }
+  __syncthreads();
+  if (warp == 0) {
+    a = lane < NT / 32 ? sa[lane] : 0.0;
+    b = lane < NT / 32 ? sb[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+      if (part_a) part_a[block_linear] = a;
+      if (part_b) part_b[block_linear] = b;
+    }
+  }
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Half-sample symmetric extension of index j into [0, n).
+__device__ __forceinline__ int reflect_index(int j, int n) {
+  if (j >= 0 && j < n) return j;
+  const int period = 2 * n;
+  j %= period;
+  if (j < 0) j += period;
+  return j >= n ? period - 1 - j : j;
+}
+
+}  // namespace tvs

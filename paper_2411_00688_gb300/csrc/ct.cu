@@ -1,0 +1,223 @@
+// Parallel-beam projector in Joseph's discretisation (the discrete Radon transform
+// of Section 3.3) and its exact transpose, with the PDHGSkip-2 epilogues fused.
+//
+// Geometry: an N x N image of pixel size s centred at the origin; angle a is
+// theta = a pi / n_angles; bin b is the line x cos + y sin = t_b with
+// t_b = (b - (n_det-1)/2) d.  A ray with |cos| >= |sin| is walked row by row,
+// otherwise column by column ("line" l); on line l it crosses the fractional
+// pixel coordinate
+//     fr(b, l) = (t_b - c_l m1) inv + (N-1)/2,   c_l = (l - (N-1)/2) s,
+// with m1 = sin, inv = 1/(cos s) for row walks and m1 = cos, inv = 1/(sin s) for
+// column walks.  The sample is (1-f) u[k0] + f u[k0+1], k0 = floor(fr), f = fr - k0,
+// pixels outside the image being zero, and every sample has weight
+// s / max(|cos|, |sin|).
+//
+// Both kernels evaluate fr with the same explicit FMA sequence (joseph_fr), so
+// the backprojector applies bit-identical weights: it is the exact transpose of
+// the projector up to the order of floating-point summation.  The projector
+// reads column-walked angles from a transposed copy of the image so that both
+// kinds of walk read image rows.
+#include "common.cuh"
+#include "kernels.hpp"
+
+namespace tvs {
+
+namespace {
+
+constexpr int CT_NT = 256;
+
+struct GeomConsts {
+  int N, n_angles, n_det;
+  float s, t0, d, c0, half;  // t_b = b d + t0; c_l = l s + c0; half = (N-1)/2
+};
+
+__device__ __forceinline__ float joseph_fr(const GeomConsts& g, float4 ang, int b, int l) {
+  const float tb = __fmaf_rn((float)b, g.d, g.t0);
+  const float cl = __fmaf_rn((float)l, g.s, g.c0);
+  return __fmaf_rn(__fmaf_rn(-cl, ang.x, tb), ang.y, g.half);
+}
+
+__global__ void transpose_kernel(const float* __restrict__ x, float* __restrict__ xt, int N) {
+  __shared__ float tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = by + r, j = bx + threadIdx.x;
+    if (i < N && j < N) tile[r][threadIdx.x] = x[(size_t)i * N + j];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = bx + r, j = by + threadIdx.x;
+    if (i < N && j < N) xt[(size_t)i * N + j] = tile[threadIdx.x][r];
+  }
+}
+
+// mode 0: sino = A x.  mode 1: PDHG dual epilogue (sino holds A x_prev on entry).
+// mode 2: sino = A x, partials of 1/2 (A x - b)^2.  mode 3: sino = A x - b, same partials.
+template <int MODE>
+__global__ void __launch_bounds__(CT_NT)
+joseph_fwd_kernel(GeomConsts g, const float4* __restrict__ angles, const float* __restrict__ x,
+                  const float* __restrict__ xt, float* __restrict__ sino, float* __restrict__ y,
+                  const float* __restrict__ b, float tau, double* __restrict__ part) {
+  const int ray = blockIdx.x * CT_NT + threadIdx.x;
+  const int n_rays = g.n_angles * g.n_det;
+  double acc_d = 0.0;
+  if (ray < n_rays) {
+    const int a = ray / g.n_det, bin = ray - a * g.n_det;
+    const float4 ang = __ldg(angles + a);
+    const float* img = ang.w != 0.f ? x : xt;  // row walk reads x[l][k], column walk xt[l][k]
+    const int N = g.N;
+    float acc = 0.f;
+    for (int l = 0; l < N; ++l) {
+      const float fr = joseph_fr(g, ang, bin, l);
+      const float k0f = floorf(fr);
+      if (k0f < -1.f || k0f > (float)(N - 1)) continue;
+      const int k0 = (int)k0f;
+      const float f = fr - k0f;
+      const float* row = img + (size_t)l * N;
+      const float v0 = k0 >= 0 ? __ldg(row + k0) : 0.f;
+      const float v1 = k0 + 1 <= N - 1 ? __ldg(row + k0 + 1) : 0.f;
+      acc += (1.f - f) * v0 + f * v1;
+    }
+    const float ax = ang.z * acc;
+    if (MODE == 0) {
+      sino[ray] = ax;
+    } else {
+      const float bb = __ldg(b + ray);
+      if (MODE == 1) {
+        const float prev = sino[ray];
+        y[ray] = (y[ray] + tau * (2.f * ax - prev) - tau * bb) / (1.f + tau);
+      }
+      const float r = ax - bb;
+      sino[ray] = MODE == 3 ? r : ax;
+      acc_d = 0.5 * (double)(r * r);
+    }
+  }
+  if (MODE != 0) block_sum2_store<CT_NT>(acc_d, 0.0, part, nullptr, blockIdx.x);
+}
+
+// g = A^T y at pixel (i, j); epilogue out = x - sigma g + ch h (when x given).
+__global__ void __launch_bounds__(CT_NT)
+joseph_bwd_kernel(GeomConsts g, const float4* __restrict__ angles, const float* __restrict__ ys,
+                  const float* __restrict__ x, const float* __restrict__ h, float* __restrict__ out,
+                  float sigma, float ch, double* __restrict__ part_tv) {
+  const int N = g.N;
+  const int pix = blockIdx.x * CT_NT + threadIdx.x;
+  double acc_tv = 0.0;
+  if (pix < N * N) {
+    const int i = pix / N, j = pix - i * N;
+    float total = 0.f;
+    for (int a = 0; a < g.n_angles; ++a) {
+      const float4 ang = __ldg(angles + a);
+      const bool rowwalk = ang.w != 0.f;
+      const int l = rowwalk ? i : j;   // line the ray walks
+      const int k = rowwalk ? j : i;   // this pixel's index along the line
+      // fr is affine in b with slope d * inv; find the b where fr = k, then scan
+      // the neighbourhood in which floor(fr) can be k - 1 or k.
+      const float slope = g.d * ang.y;
+      const float fr0 = joseph_fr(g, ang, 0, l);
+      const float bc = ((float)k - fr0) / slope;
+      const float span = 1.f / fabsf(slope) + 2.f;
+      int b_lo = (int)floorf(bc - span), b_hi = (int)ceilf(bc + span);
+      if (b_lo < 0) b_lo = 0;
+      if (b_hi > g.n_det - 1) b_hi = g.n_det - 1;
+      const float* yrow = ys + (size_t)a * g.n_det;
+      float acc = 0.f;
+      for (int b = b_lo; b <= b_hi; ++b) {
+        const float fr = joseph_fr(g, ang, b, l);
+        const float k0f = floorf(fr);
+        const float f = fr - k0f;
+        const int k0 = (int)k0f;
+        if (k0 == k) acc += (1.f - f) * __ldg(yrow + b);
+        else if (k0 + 1 == k) acc += f * __ldg(yrow + b);
+      }
+      total = fmaf(ang.z, acc, total);
+    }
+    if (x) {
+      const size_t o = (size_t)i * N + j;
+      const float xc = __ldg(x + o);
+      float v = xc - sigma * total;
+      if (h) v = fmaf(ch, __ldg(h + o), v);
+      out[o] = v;
+      if (part_tv) {
+        const float dy = i < N - 1 ? __ldg(x + o + N) - xc : 0.f;
+        const float dx = j < N - 1 ? __ldg(x + o + 1) - xc : 0.f;
+        acc_tv = (double)sqrtf(dy * dy + dx * dx);
+      }
+    } else {
+      out[(size_t)i * N + j] = total;
+    }
+  }
+  if (part_tv) block_sum2_store<CT_NT>(0.0, acc_tv, nullptr, part_tv, blockIdx.x);
+}
+
+GeomConsts consts(const CTGeom& g) {
+  GeomConsts c;
+  c.N = g.N;
+  c.n_angles = g.n_angles;
+  c.n_det = g.n_det;
+  c.s = g.pixel_size;
+  c.d = g.det_spacing;
+  c.t0 = (float)(-0.5 * (g.n_det - 1) * (double)g.det_spacing);
+  c.c0 = (float)(-0.5 * (g.N - 1) * (double)g.pixel_size);
+  c.half = (float)(0.5 * (g.N - 1));
+  return c;
+}
+
+}  // namespace
+
+cudaError_t ct_build_angle_table(const CTGeom& g, float4* dev_table, cudaStream_t s) {
+  float4* host = new float4[g.n_angles];
+  const double pi = 3.14159265358979323846;
+  for (int a = 0; a < g.n_angles; ++a) {
+    const double th = a * pi / g.n_angles;
+    const double c = cos(th), sn = sin(th);
+    const bool rowwalk = fabs(c) >= fabs(sn);
+    float4 v;
+    v.x = (float)(rowwalk ? sn : c);
+    v.y = (float)(1.0 / ((rowwalk ? c : sn) * (double)g.pixel_size));
+    v.z = (float)((double)g.pixel_size / (rowwalk ? fabs(c) : fabs(sn)));
+    v.w = rowwalk ? 1.f : 0.f;
+    host[a] = v;
+  }
+  cudaError_t e = cudaMemcpyAsync(dev_table, host, sizeof(float4) * g.n_angles,
+                                  cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  delete[] host;
+  return e;
+}
+
+int ct_fwd_blocks(const CTGeom& g) { return (g.n_angles * g.n_det + CT_NT - 1) / CT_NT; }
+int ct_bwd_blocks(const CTGeom& g) { return (g.N * g.N + CT_NT - 1) / CT_NT; }
+
+cudaError_t launch_ct_forward(const CTGeom& g, const float* x, float* sino, float* y,
+                              const float* b, float tau, double* part_data, int mode,
+                              cudaStream_t s) {
+  if (!g.xt_scratch) return cudaErrorInvalidValue;
+  dim3 tg((g.N + 31) / 32, (g.N + 31) / 32), tb(32, 8);
+  transpose_kernel<<<tg, tb, 0, s>>>(x, g.xt_scratch, g.N);
+  const GeomConsts c = consts(g);
+  const int blocks = ct_fwd_blocks(g);
+  switch (mode) {
+    case CT_FWD_PD:
+      joseph_fwd_kernel<1><<<blocks, CT_NT, 0, s>>>(c, g.angles, x, g.xt_scratch, sino, y, b, tau, part_data);
+      break;
+    case CT_FWD_STORE:
+      joseph_fwd_kernel<2><<<blocks, CT_NT, 0, s>>>(c, g.angles, x, g.xt_scratch, sino, nullptr, b, 0.f, part_data);
+      break;
+    case CT_FWD_RESID:
+      joseph_fwd_kernel<3><<<blocks, CT_NT, 0, s>>>(c, g.angles, x, g.xt_scratch, sino, nullptr, b, 0.f, part_data);
+      break;
+    default:
+      joseph_fwd_kernel<0><<<blocks, CT_NT, 0, s>>>(c, g.angles, x, g.xt_scratch, sino, nullptr, nullptr, 0.f, nullptr);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ct_backward(const CTGeom& g, const float* y, const float* x, const float* h,
+                               float* out, float sigma, float ch, double* part_tv, cudaStream_t s) {
+  const GeomConsts c = consts(g);
+  joseph_bwd_kernel<<<ct_bwd_blocks(g), CT_NT, 0, s>>>(c, g.angles, y, x, h, out, sigma, ch, part_tv);
+  return cudaGetLastError();
+}
+
+}  // namespace tvs

@@ -1,0 +1,270 @@
+// Inner TV-prox kernels: one fused accelerated dual projected-gradient (FGP)
+// iteration per launch, and the finalisation u = P_X(z + lam div p).
+//
+// Sign convention (Section 2.1): div = -D^T, so u = z + lam div p = z - lam D^T p.
+// One iteration, for the unit-ball dual p (the paper's q with |q_i| <= alpha is
+// lam p), with r the momentum point of the FISTA acceleration (Algorithm 3):
+//     r  = p_k + beta_k (p_k - p_{k-1})
+//     u  = P_X(z + lam div r)                 (P_X = max(., 0) when nonneg)
+//     p_{k+1} = P_B(r + D u / (4 ndim lam))   (P_B: pointwise unit-ball projection, Eq. 7)
+// Each CTA stages r over its tile plus a one-pixel halo in shared memory, forms
+// u over the tile plus the row/column after it, then writes p_{k+1}: the whole
+// iteration is one pass over z, p_k, p_{k-1} and one write of p_{k+1}.
+#include "common.cuh"
+#include "kernels.hpp"
+
+namespace tvs {
+
+namespace {
+
+constexpr int TX2 = 32, TY2 = 16, NT2 = 256;
+
+template <typename T, bool NONNEG>
+__global__ void __launch_bounds__(NT2)
+fgp2d_kernel(const float* __restrict__ z, const T* __restrict__ pc, const T* __restrict__ pp,
+             T* __restrict__ pn, int H, int W, float lam, float inv_step, float beta) {
+  __shared__ float sry[TY2 + 2][TX2 + 3];
+  __shared__ float srx[TY2 + 2][TX2 + 3];
+  __shared__ float su[TY2 + 1][TX2 + 2];
+  const int j0 = blockIdx.x * TX2, i0 = blockIdx.y * TY2;
+  const size_t n = (size_t)H * W;
+  // r over rows i0-1 .. i0+TY2, columns j0-1 .. j0+TX2
+  for (int e = threadIdx.x; e < (TY2 + 2) * (TX2 + 2); e += NT2) {
+    const int a = e / (TX2 + 2), b = e - a * (TX2 + 2);
+    const int gi = i0 - 1 + a, gj = j0 - 1 + b;
+    float ry = 0.f, rx = 0.f;
+    if (gi >= 0 && gi < H && gj >= 0 && gj < W) {
+      const size_t o = (size_t)gi * W + gj;
+      const float cy = Elem<T>::ld(pc + o), cx = Elem<T>::ld(pc + n + o);
+      if (beta != 0.f) {
+        const float qy = Elem<T>::ld(pp + o), qx = Elem<T>::ld(pp + n + o);
+        ry = cy + beta * (cy - qy);
+        rx = cx + beta * (cx - qx);
+      } else {
+        ry = cy;
+        rx = cx;
+      }
+    }
+    sry[a][b] = ry;
+    srx[a][b] = rx;
+  }
+  __syncthreads();
+  // u over rows i0 .. i0+TY2, columns j0 .. j0+TX2
+  for (int e = threadIdx.x; e < (TY2 + 1) * (TX2 + 1); e += NT2) {
+    const int a = e / (TX2 + 1), b = e - a * (TX2 + 1);
+    const int gi = i0 + a, gj = j0 + b;
+    float u = 0.f;
+    if (gi < H && gj < W) {
+      float dv = 0.f;
+      if (gi < H - 1) dv += sry[a + 1][b + 1];
+      if (gi > 0) dv -= sry[a][b + 1];
+      if (gj < W - 1) dv += srx[a + 1][b + 1];
+      if (gj > 0) dv -= srx[a + 1][b];
+      u = __ldg(z + (size_t)gi * W + gj) + lam * dv;
+      if (NONNEG) u = fmaxf(u, 0.f);
+    }
+    su[a][b] = u;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < TY2 * TX2; e += NT2) {
+    const int a = e / TX2, b = e - a * TX2;
+    const int gi = i0 + a, gj = j0 + b;
+    if (gi < H && gj < W) {
+      const float uc = su[a][b];
+      const float gy = gi < H - 1 ? su[a + 1][b] - uc : 0.f;
+      const float gx = gj < W - 1 ? su[a][b + 1] - uc : 0.f;
+      const float qy = sry[a + 1][b + 1] + inv_step * gy;
+      const float qx = srx[a + 1][b + 1] + inv_step * gx;
+      const float nrm2 = qy * qy + qx * qx;
+      const float sc = nrm2 > 1.f ? rsqrtf(nrm2) : 1.f;
+      const size_t o = (size_t)gi * W + gj;
+      Elem<T>::st(pn + o, qy * sc);
+      Elem<T>::st(pn + n + o, qx * sc);
+    }
+  }
+}
+
+constexpr int TX3 = 32, TY3 = 8, TZ3 = 4, NT3 = 256;
+
+template <typename T, bool NONNEG>
+__global__ void __launch_bounds__(NT3)
+fgp3d_kernel(const float* __restrict__ z, const T* __restrict__ pc, const T* __restrict__ pp,
+             T* __restrict__ pn, int D, int H, int W, float lam, float inv_step, float beta) {
+  __shared__ float sr[3][TZ3 + 2][TY3 + 2][TX3 + 2];
+  __shared__ float su[TZ3 + 1][TY3 + 1][TX3 + 1];
+  const int j0 = blockIdx.x * TX3, i0 = blockIdx.y * TY3, k0 = blockIdx.z * TZ3;
+  const size_t n = (size_t)D * H * W;
+  constexpr int RX = TX3 + 2, RY = TY3 + 2, RZ = TZ3 + 2;
+  for (int e = threadIdx.x; e < RZ * RY * RX; e += NT3) {
+    const int c = e / (RY * RX), rem = e - c * (RY * RX);
+    const int a = rem / RX, b = rem - a * RX;
+    const int gk = k0 - 1 + c, gi = i0 - 1 + a, gj = j0 - 1 + b;
+    float r0 = 0.f, r1 = 0.f, r2 = 0.f;
+    if (gk >= 0 && gk < D && gi >= 0 && gi < H && gj >= 0 && gj < W) {
+      const size_t o = ((size_t)gk * H + gi) * W + gj;
+      const float c0 = Elem<T>::ld(pc + o), c1 = Elem<T>::ld(pc + n + o), c2 = Elem<T>::ld(pc + 2 * n + o);
+      if (beta != 0.f) {
+        r0 = c0 + beta * (c0 - Elem<T>::ld(pp + o));
+        r1 = c1 + beta * (c1 - Elem<T>::ld(pp + n + o));
+        r2 = c2 + beta * (c2 - Elem<T>::ld(pp + 2 * n + o));
+      } else {
+        r0 = c0; r1 = c1; r2 = c2;
+      }
+    }
+    sr[0][c][a][b] = r0;
+    sr[1][c][a][b] = r1;
+    sr[2][c][a][b] = r2;
+  }
+  __syncthreads();
+  constexpr int UX = TX3 + 1, UY = TY3 + 1, UZ = TZ3 + 1;
+  for (int e = threadIdx.x; e < UZ * UY * UX; e += NT3) {
+    const int c = e / (UY * UX), rem = e - c * (UY * UX);
+    const int a = rem / UX, b = rem - a * UX;
+    const int gk = k0 + c, gi = i0 + a, gj = j0 + b;
+    float u = 0.f;
+    if (gk < D && gi < H && gj < W) {
+      float dv = 0.f;
+      if (gk < D - 1) dv += sr[0][c + 1][a + 1][b + 1];
+      if (gk > 0) dv -= sr[0][c][a + 1][b + 1];
+      if (gi < H - 1) dv += sr[1][c + 1][a + 1][b + 1];
+      if (gi > 0) dv -= sr[1][c + 1][a][b + 1];
+      if (gj < W - 1) dv += sr[2][c + 1][a + 1][b + 1];
+      if (gj > 0) dv -= sr[2][c + 1][a + 1][b];
+      u = __ldg(z + ((size_t)gk * H + gi) * W + gj) + lam * dv;
+      if (NONNEG) u = fmaxf(u, 0.f);
+    }
+    su[c][a][b] = u;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < TZ3 * TY3 * TX3; e += NT3) {
+    const int c = e / (TY3 * TX3), rem = e - c * (TY3 * TX3);
+    const int a = rem / TX3, b = rem - a * TX3;
+    const int gk = k0 + c, gi = i0 + a, gj = j0 + b;
+    if (gk < D && gi < H && gj < W) {
+      const float uc = su[c][a][b];
+      const float g0 = gk < D - 1 ? su[c + 1][a][b] - uc : 0.f;
+      const float g1 = gi < H - 1 ? su[c][a + 1][b] - uc : 0.f;
+      const float g2 = gj < W - 1 ? su[c][a][b + 1] - uc : 0.f;
+      const float q0 = sr[0][c + 1][a + 1][b + 1] + inv_step * g0;
+      const float q1 = sr[1][c + 1][a + 1][b + 1] + inv_step * g1;
+      const float q2 = sr[2][c + 1][a + 1][b + 1] + inv_step * g2;
+      const float nrm2 = q0 * q0 + q1 * q1 + q2 * q2;
+      const float sc = nrm2 > 1.f ? rsqrtf(nrm2) : 1.f;
+      const size_t o = ((size_t)gk * H + gi) * W + gj;
+      Elem<T>::st(pn + o, q0 * sc);
+      Elem<T>::st(pn + n + o, q1 * sc);
+      Elem<T>::st(pn + 2 * n + o, q2 * sc);
+    }
+  }
+}
+
+// Pointwise finalisation; div p at a pixel needs p at the pixel and at the
+// previous pixel along each axis.
+template <typename T, bool NONNEG>
+__global__ void fgp_finalize_kernel(const float* __restrict__ z, const T* __restrict__ p, int D,
+                                    int H, int W, int ndim, float lam, float* __restrict__ x_out,
+                                    float* __restrict__ h_out, float h_coef, T* __restrict__ p_home,
+                                    const float* __restrict__ x_prev, float* __restrict__ fista_y,
+                                    const float* __restrict__ beta_tab, const int* __restrict__ beta_idx) {
+  const float beta_x = fista_y ? beta_tab[*beta_idx] : 0.f;
+  const size_t n = (size_t)D * H * W;
+  const size_t HW = (size_t)H * W;
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n;
+       o += (size_t)gridDim.x * blockDim.x) {
+    const int gj = (int)(o % W);
+    const int gi = (int)((o / W) % H);
+    const int gk = (int)(o / HW);
+    float dv = 0.f;
+    int c = 0;
+    if (ndim == 3) {
+      if (gk < D - 1) dv += Elem<T>::ld(p + o);
+      if (gk > 0) dv -= Elem<T>::ld(p + o - HW);
+      c = 1;
+    }
+    const T* py = p + (size_t)c * n;
+    const T* px = p + (size_t)(c + 1) * n;
+    if (gi < H - 1) dv += Elem<T>::ld(py + o);
+    if (gi > 0) dv -= Elem<T>::ld(py + o - W);
+    if (gj < W - 1) dv += Elem<T>::ld(px + o);
+    if (gj > 0) dv -= Elem<T>::ld(px + o - 1);
+    const float zz = __ldg(z + o);
+    float u = zz + lam * dv;
+    if (NONNEG) u = fmaxf(u, 0.f);
+    if (fista_y) {
+      const float xp = __ldg(x_prev + o);
+      fista_y[o] = u + beta_x * (u - xp);
+    }
+    x_out[o] = u;
+    if (h_out) h_out[o] = h_coef * (u - zz);
+    if (p_home) {
+      for (int a = 0; a < ndim; ++a) p_home[(size_t)a * n + o] = p[(size_t)a * n + o];
+    }
+  }
+}
+
+template <typename T, bool NN>
+cudaError_t fgp_iter_t(const Dims& d, const float* z, const void* pc, const void* pp, void* pn,
+                       float lam, float inv_step, float beta, cudaStream_t s) {
+  if (d.ndim == 2) {
+    dim3 grid((d.nx + TX2 - 1) / TX2, (d.ny + TY2 - 1) / TY2);
+    fgp2d_kernel<T, NN><<<grid, NT2, 0, s>>>(z, (const T*)pc, (const T*)pp, (T*)pn, d.ny, d.nx, lam,
+                                             inv_step, beta);
+  } else {
+    dim3 grid((d.nx + TX3 - 1) / TX3, (d.ny + TY3 - 1) / TY3, (d.nz + TZ3 - 1) / TZ3);
+    fgp3d_kernel<T, NN><<<grid, NT3, 0, s>>>(z, (const T*)pc, (const T*)pp, (T*)pn, d.nz, d.ny,
+                                             d.nx, lam, inv_step, beta);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T, bool NN>
+cudaError_t fgp_finalize_t(const Dims& d, const float* z, const void* p, float lam, float* x_out,
+                           float* h_out, float h_coef, void* p_home, const float* x_prev,
+                           float* fista_y, const float* beta_tab, const int* beta_idx, cudaStream_t s) {
+  const size_t n = d.n();
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  fgp_finalize_kernel<T, NN><<<blocks, 256, 0, s>>>(z, (const T*)p, d.nz, d.ny, d.nx, d.ndim, lam,
+                                                    x_out, h_out, h_coef, (T*)p_home, x_prev,
+                                                    fista_y, beta_tab, beta_idx);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_fgp_iter(const Dims& d, const float* z, const void* pc, const void* pp, void* pn,
+                            float lam, float inv_step, float beta, int dtype, bool nonneg,
+                            cudaStream_t s) {
+  if (d.n() == 0) return cudaSuccess;
+  switch (dtype) {
+    case DUAL_F32:
+      return nonneg ? fgp_iter_t<float, true>(d, z, pc, pp, pn, lam, inv_step, beta, s)
+                    : fgp_iter_t<float, false>(d, z, pc, pp, pn, lam, inv_step, beta, s);
+    case DUAL_BF16:
+      return nonneg ? fgp_iter_t<__nv_bfloat16, true>(d, z, pc, pp, pn, lam, inv_step, beta, s)
+                    : fgp_iter_t<__nv_bfloat16, false>(d, z, pc, pp, pn, lam, inv_step, beta, s);
+    default:
+      return nonneg ? fgp_iter_t<__half, true>(d, z, pc, pp, pn, lam, inv_step, beta, s)
+                    : fgp_iter_t<__half, false>(d, z, pc, pp, pn, lam, inv_step, beta, s);
+  }
+}
+
+cudaError_t launch_fgp_finalize(const Dims& d, const float* z, const void* p, int dtype, float lam,
+                                bool nonneg, float* x_out, float* h_out, float h_coef,
+                                void* p_home, const float* x_prev, float* fista_y,
+                                const float* beta_tab, const int* beta_idx, cudaStream_t s) {
+  if (d.n() == 0) return cudaSuccess;
+  switch (dtype) {
+    case DUAL_F32:
+      return nonneg ? fgp_finalize_t<float, true>(d, z, p, lam, x_out, h_out, h_coef, p_home, x_prev, fista_y, beta_tab, beta_idx, s)
+                    : fgp_finalize_t<float, false>(d, z, p, lam, x_out, h_out, h_coef, p_home, x_prev, fista_y, beta_tab, beta_idx, s);
+    case DUAL_BF16:
+      return nonneg ? fgp_finalize_t<__nv_bfloat16, true>(d, z, p, lam, x_out, h_out, h_coef, p_home, x_prev, fista_y, beta_tab, beta_idx, s)
+                    : fgp_finalize_t<__nv_bfloat16, false>(d, z, p, lam, x_out, h_out, h_coef, p_home, x_prev, fista_y, beta_tab, beta_idx, s);
+    default:
+      return nonneg ? fgp_finalize_t<__half, true>(d, z, p, lam, x_out, h_out, h_coef, p_home, x_prev, fista_y, beta_tab, beta_idx, s)
+                    : fgp_finalize_t<__half, false>(d, z, p, lam, x_out, h_out, h_coef, p_home, x_prev, fista_y, beta_tab, beta_idx, s);
+  }
+}
+
+}  // namespace tvs

@@ -1,0 +1,103 @@
+// Host-side launchers of the device kernels (internal C++ interface).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace tvs {
+
+struct Dims {
+  int nx = 1, ny = 1, nz = 1, ndim = 2;
+  size_t n() const { return (size_t)nx * ny * nz; }
+};
+
+enum DualType { DUAL_F32 = 0, DUAL_BF16 = 1, DUAL_F16 = 2 };
+inline size_t dual_elem_bytes(int t) { return t == DUAL_F32 ? 4 : 2; }
+
+// ---- TV prox (fgp.cu) ----
+// One inner iteration: r = pc + beta (pc - pp); u = P_X(z + lam div r);
+// pn = P_B(r + inv_step * D u).  pp may equal pc when beta == 0.
+cudaError_t launch_fgp_iter(const Dims& d, const float* z, const void* pc, const void* pp, void* pn,
+                            float lam, float inv_step, float beta, int dtype, bool nonneg,
+                            cudaStream_t s);
+// x_out = P_X(z + lam div p); if h_out: h_out = h_coef (x_out - z);
+// if p_home: p_home = p.  When fista_y is set: fista_y = x_out + beta (x_out - x_prev) with
+// beta = beta_tab[*beta_idx] (FISTA extrapolation, read on the device).
+cudaError_t launch_fgp_finalize(const Dims& d, const float* z, const void* p, int dtype, float lam,
+                                bool nonneg, float* x_out, float* h_out, float h_coef,
+                                void* p_home, const float* x_prev, float* fista_y,
+                                const float* beta_tab, const int* beta_idx, cudaStream_t s);
+
+// ---- objective pieces and pointwise steps (ops.cu) ----
+struct BlurW {
+  float w[17];
+  int R;
+};
+int tile_blocks_2d(int H, int W);        // blocks of the 2D tile kernels
+int pointwise_blocks(size_t n);          // blocks of the grid-stride kernels
+
+// r_out = A x - b (r_out may be null); partials of 1/2 r^2 and of TV(x).
+cudaError_t launch_blur_residual(int H, int W, const float* x, const float* b, float* r_out,
+                                 const BlurW& w, double* part_data, double* part_tv, cudaStream_t s);
+// out = x - gamma A(in) + ch h   (h may be null); optional TV(x) partials.
+cudaError_t launch_blur_step(int H, int W, const float* in, const float* x, const float* h,
+                             float* out, const BlurW& w, float gamma, float ch, double* part_tv,
+                             cudaStream_t s);
+// y_out = (y + tau (2 A x - ax_prev) - tau b) / (1 + tau); ax_prev <- A x; partial 1/2 (A x - b)^2.
+cudaError_t launch_blur_pd_dual(int H, int W, const float* x, float* ax_prev, float* y,
+                                const float* b, const BlurW& w, float tau, double* part_data,
+                                cudaStream_t s);
+cudaError_t launch_blur(int H, int W, const float* x, float* y, const BlurW& w, cudaStream_t s);
+
+// Identity data term (2D or 3D): out = x - gamma (x - b) + ch h; partials of
+// 1/2 (x - b)^2 and TV(x).  out may be null (objective only).
+cudaError_t launch_identity_step(const Dims& d, const float* x, const float* b, const float* h,
+                                 float* out, float gamma, float ch, double* part_data,
+                                 double* part_tv, cudaStream_t s);
+// Generic pointwise step used by PDHG with identity/CT adjoint already formed:
+// out = x - sigma g + ch h; optional TV(x) partials.
+cudaError_t launch_axpy_step(const Dims& d, const float* g, const float* x, const float* h,
+                             float* out, float sigma, float ch, double* part_tv, cudaStream_t s);
+// y = (y + tau (2 ax - ax_prev) - tau b)/(1+tau); ax_prev <- ax; partial 1/2 (ax - b)^2.
+cudaError_t launch_pd_dual_pointwise(size_t m, const float* ax, float* ax_prev, float* y,
+                                     const float* b, float tau, double* part_data, cudaStream_t s);
+// Partials of TV(x) only (grid-stride, pointwise_blocks(n) blocks).
+cudaError_t launch_tv_partials(const Dims& d, const float* x, double* part_tv, cudaStream_t s);
+
+// Sum partials (fixed order), F = data + alpha tv.  k = flags[2] (then flags[2]++);
+// when k >= 0 and k % every == 0: obj[k] = F, ts[k] = now, and once
+// (F - f*) <= target f*: flags[0] = 1 (done), flags[1] = k, *done_host = 1.
+// obj == null: write F to *f_out only.
+cudaError_t launch_reduce_record(const double* part_data, int n_data, const double* part_tv,
+                                 int n_tv, double alpha, int every, double* obj,
+                                 unsigned long long* ts, double f_star, double target, int* flags,
+                                 int* done_host, double* f_out, cudaStream_t s);
+cudaError_t launch_timestamp(unsigned long long* ts, cudaStream_t s);
+// arr[2 * (*ctr) + which] = now; when which == 1 also (*ctr)++.
+cudaError_t launch_timestamp_pair(unsigned long long* arr, int* ctr, int which, cudaStream_t s);
+cudaError_t launch_count_nonfinite(const float* x, size_t n, int* count, cudaStream_t s);
+cudaError_t launch_coin_schedule(uint64_t seed, double p, int64_t k0, int K, unsigned char* out,
+                                 cudaStream_t s);
+
+// ---- parallel-beam projector (ct.cu) ----
+struct CTGeom {
+  int N, n_angles, n_det;
+  float pixel_size, det_spacing;
+  const float4* angles;  // device table: (m1, inv, weight, row_walk) per angle
+  float* xt_scratch;     // N*N floats: transposed image used by the projector
+};
+cudaError_t ct_build_angle_table(const CTGeom& g, float4* dev_table, cudaStream_t s);
+int ct_fwd_blocks(const CTGeom& g);
+int ct_bwd_blocks(const CTGeom& g);
+enum CTFwdMode { CT_FWD_PLAIN = 0, CT_FWD_PD = 1, CT_FWD_STORE = 2, CT_FWD_RESID = 3 };
+// PLAIN: sino = A x.  PD: y = (y + tau (2 Ax - sino) - tau b)/(1+tau), then sino = Ax.
+// STORE: sino = A x; RESID: sino = A x - b.  PD/STORE/RESID write partials of 1/2 (Ax-b)^2.
+cudaError_t launch_ct_forward(const CTGeom& g, const float* x, float* sino, float* y,
+                              const float* b, float tau, double* part_data, int mode,
+                              cudaStream_t s);
+// g = A^T y; when x != null: out = x - sigma g + ch h (+ TV(x) partials); else out = g.
+cudaError_t launch_ct_backward(const CTGeom& g, const float* y, const float* x, const float* h,
+                               float* out, float sigma, float ch, double* part_tv, cudaStream_t s);
+
+}  // namespace tvs

@@ -1,0 +1,343 @@
+// Data-term kernels: separable Gaussian blur with fused residual / gradient-step
+// / PDHG-dual epilogues, the pointwise identity-operator step, objective partial
+// sums, the deterministic objective reduction, and small utilities.
+//
+// ProxSkip step (Algorithm 4): x^ = x - gamma (grad f(x) - h) with
+// grad f = A^T (A x - b).  Every step kernel writes out = x - gamma g + ch h, so
+//   skip iteration:  ch = gamma            -> out = x^            (= x_{k+1})
+//   prox iteration:  ch = gamma - gamma/p  -> out = x^ - (gamma/p) h (prox input)
+//   PGD / FISTA:     ch = 0 (h unused)     -> out = x - gamma grad f(x)
+// The objective F(x) = 1/2 ||A x - b||^2 + alpha TV(x) (Eq. 5) is accumulated in
+// the same passes: per-pixel FP32 terms, FP64 per-thread and per-block sums,
+// block totals summed in a fixed order by one block (bitwise reproducible).
+#include "common.cuh"
+#include "kernels.hpp"
+
+namespace tvs {
+
+namespace {
+
+constexpr int BX = 32, BY = 16, BNT = 256, RMAX = 8;
+constexpr int PW_NT = 256;
+
+enum BlurMode { BM_RESID = 0, BM_STEP = 1, BM_PD = 2, BM_PLAIN = 3 };
+
+// TV term |(D x)_(gi,gj)| from global memory (Neumann: zero last differences).
+__device__ __forceinline__ float tv_at_2d(const float* __restrict__ x, int gi, int gj, int H, int W) {
+  const size_t o = (size_t)gi * W + gj;
+  const float c = __ldg(x + o);
+  const float dy = gi < H - 1 ? __ldg(x + o + W) - c : 0.f;
+  const float dx = gj < W - 1 ? __ldg(x + o + 1) - c : 0.f;
+  return sqrtf(dy * dy + dx * dx);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(BNT)
+blur_kernel(const float* __restrict__ src, int H, int W, BlurW w, const float* __restrict__ b,
+            float* __restrict__ out, const float* __restrict__ x, const float* __restrict__ h,
+            float gamma, float ch, float* __restrict__ axp, float* __restrict__ y, float tau,
+            double* __restrict__ part_a, double* __restrict__ part_b) {
+  __shared__ float s_in[BY + 2 * RMAX][BX + 2 * RMAX + 1];
+  __shared__ float s_tmp[BY + 2 * RMAX][BX + 1];
+  const int R = w.R;
+  const int j0 = blockIdx.x * BX, i0 = blockIdx.y * BY;
+  const int rows = BY + 2 * R, cols = BX + 2 * R;
+  for (int e = threadIdx.x; e < rows * cols; e += BNT) {
+    const int a = e / cols, c = e - a * cols;
+    const int gi = reflect_index(i0 - R + a, H), gj = reflect_index(j0 - R + c, W);
+    s_in[a][c] = __ldg(src + (size_t)gi * W + gj);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < rows * BX; e += BNT) {
+    const int a = e / BX, c = e - a * BX;
+    float acc = 0.f;
+    for (int k = 0; k <= 2 * R; ++k) acc = fmaf(w.w[k], s_in[a][c + k], acc);
+    s_tmp[a][c] = acc;
+  }
+  __syncthreads();
+  double acc_a = 0.0, acc_b = 0.0;
+  for (int e = threadIdx.x; e < BY * BX; e += BNT) {
+    const int a = e / BX, c = e - a * BX;
+    const int gi = i0 + a, gj = j0 + c;
+    if (gi >= H || gj >= W) continue;
+    float v = 0.f;
+    for (int k = 0; k <= 2 * R; ++k) v = fmaf(w.w[k], s_tmp[a + k][c], v);
+    const size_t o = (size_t)gi * W + gj;
+    if (MODE == BM_RESID) {
+      const float r = v - __ldg(b + o);
+      if (out) out[o] = r;
+      acc_a += 0.5 * (double)(r * r);
+      // TV of the blurred image's source x = src, from the staged tile
+      const float xc = s_in[a + R][c + R];
+      const float dy = gi < H - 1 ? s_in[a + R + 1][c + R] - xc : 0.f;
+      const float dx = gj < W - 1 ? s_in[a + R][c + R + 1] - xc : 0.f;
+      acc_b += (double)sqrtf(dy * dy + dx * dx);
+    } else if (MODE == BM_STEP) {
+      float o_v = __ldg(x + o) - gamma * v;
+      if (h) o_v = fmaf(ch, __ldg(h + o), o_v);
+      out[o] = o_v;
+      if (part_b) acc_b += (double)tv_at_2d(x, gi, gj, H, W);
+    } else if (MODE == BM_PD) {
+      const float bb = __ldg(b + o);
+      const float prev = axp[o];
+      const float yn = (y[o] + tau * (2.f * v - prev) - tau * bb) / (1.f + tau);
+      y[o] = yn;
+      axp[o] = v;
+      const float r = v - bb;
+      acc_a += 0.5 * (double)(r * r);
+    } else {
+      out[o] = v;
+    }
+  }
+  if (part_a || part_b)
+    block_sum2_store<BNT>(acc_a, acc_b, part_a, part_b, blockIdx.y * gridDim.x + blockIdx.x);
+}
+
+// Identity data term, 2D or 3D (nz slices of ny x nx).
+__global__ void __launch_bounds__(PW_NT)
+identity_step_kernel(const float* __restrict__ x, const float* __restrict__ b,
+                     const float* __restrict__ h, float* __restrict__ out, int D, int H, int W,
+                     int ndim, float gamma, float ch, double* __restrict__ part_a,
+                     double* __restrict__ part_b) {
+  const size_t n = (size_t)D * H * W, HW = (size_t)H * W;
+  double acc_a = 0.0, acc_b = 0.0;
+  for (size_t o = blockIdx.x * (size_t)PW_NT + threadIdx.x; o < n; o += (size_t)gridDim.x * PW_NT) {
+    const int gj = (int)(o % W), gi = (int)((o / W) % H), gk = (int)(o / HW);
+    const float xc = __ldg(x + o), bb = __ldg(b + o);
+    const float r = xc - bb;
+    if (out) {
+      float v = xc - gamma * r;
+      if (h) v = fmaf(ch, __ldg(h + o), v);
+      out[o] = v;
+    }
+    acc_a += 0.5 * (double)(r * r);
+    float s = 0.f;
+    if (ndim == 3 && gk < D - 1) { const float d0 = __ldg(x + o + HW) - xc; s += d0 * d0; }
+    if (gi < H - 1) { const float d1 = __ldg(x + o + W) - xc; s += d1 * d1; }
+    if (gj < W - 1) { const float d2 = __ldg(x + o + 1) - xc; s += d2 * d2; }
+    acc_b += (double)sqrtf(s);
+  }
+  block_sum2_store<PW_NT>(acc_a, acc_b, part_a, part_b, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(PW_NT)
+axpy_step_kernel(const float* __restrict__ g, const float* __restrict__ x,
+                 const float* __restrict__ h, float* __restrict__ out, int D, int H, int W,
+                 int ndim, float sigma, float ch, double* __restrict__ part_b) {
+  const size_t n = (size_t)D * H * W, HW = (size_t)H * W;
+  double acc_b = 0.0;
+  for (size_t o = blockIdx.x * (size_t)PW_NT + threadIdx.x; o < n; o += (size_t)gridDim.x * PW_NT) {
+    const float xc = __ldg(x + o);
+    float v = xc - sigma * __ldg(g + o);
+    if (h) v = fmaf(ch, __ldg(h + o), v);
+    out[o] = v;
+    if (part_b) {
+      const int gj = (int)(o % W), gi = (int)((o / W) % H), gk = (int)(o / HW);
+      float s = 0.f;
+      if (ndim == 3 && gk < D - 1) { const float d0 = __ldg(x + o + HW) - xc; s += d0 * d0; }
+      if (gi < H - 1) { const float d1 = __ldg(x + o + W) - xc; s += d1 * d1; }
+      if (gj < W - 1) { const float d2 = __ldg(x + o + 1) - xc; s += d2 * d2; }
+      acc_b += (double)sqrtf(s);
+    }
+  }
+  if (part_b) block_sum2_store<PW_NT>(0.0, acc_b, nullptr, part_b, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(PW_NT)
+tv_partials_kernel(const float* __restrict__ x, int D, int H, int W, int ndim,
+                   double* __restrict__ part_b) {
+  const size_t n = (size_t)D * H * W, HW = (size_t)H * W;
+  double acc_b = 0.0;
+  for (size_t o = blockIdx.x * (size_t)PW_NT + threadIdx.x; o < n; o += (size_t)gridDim.x * PW_NT) {
+    const int gj = (int)(o % W), gi = (int)((o / W) % H), gk = (int)(o / HW);
+    const float xc = __ldg(x + o);
+    float s = 0.f;
+    if (ndim == 3 && gk < D - 1) { const float d0 = __ldg(x + o + HW) - xc; s += d0 * d0; }
+    if (gi < H - 1) { const float d1 = __ldg(x + o + W) - xc; s += d1 * d1; }
+    if (gj < W - 1) { const float d2 = __ldg(x + o + 1) - xc; s += d2 * d2; }
+    acc_b += (double)sqrtf(s);
+  }
+  block_sum2_store<PW_NT>(0.0, acc_b, nullptr, part_b, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(PW_NT)
+pd_dual_pointwise_kernel(size_t m, const float* __restrict__ ax, float* __restrict__ axp,
+                         float* __restrict__ y, const float* __restrict__ b, float tau,
+                         double* __restrict__ part_a) {
+  double acc = 0.0;
+  for (size_t o = blockIdx.x * (size_t)PW_NT + threadIdx.x; o < m; o += (size_t)gridDim.x * PW_NT) {
+    const float v = __ldg(ax + o), bb = __ldg(b + o);
+    const float prev = axp[o];
+    y[o] = (y[o] + tau * (2.f * v - prev) - tau * bb) / (1.f + tau);
+    axp[o] = v;
+    const float r = v - bb;
+    acc += 0.5 * (double)(r * r);
+  }
+  block_sum2_store<PW_NT>(acc, 0.0, part_a, nullptr, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(512)
+reduce_record_kernel(const double* __restrict__ part_a, int n_a, const double* __restrict__ part_b,
+                     int n_b, double alpha, int every, double* obj, unsigned long long* ts,
+                     double f_star, double target, int* flags, int* done_host, double* f_out) {
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < n_a; i += 512) a += part_a[i];
+  for (int i = threadIdx.x; i < n_b; i += 512) b += part_b[i];
+  __shared__ double sa[512], sb[512];
+  sa[threadIdx.x] = a;
+  sb[threadIdx.x] = b;
+  __syncthreads();
+  for (int s = 256; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      sa[threadIdx.x] += sa[threadIdx.x + s];
+      sb[threadIdx.x] += sb[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double F = sa[0] + alpha * sb[0];
+    if (f_out) *f_out = F;
+    if (!flags) return;
+    const int k = flags[2];
+    flags[2] = k + 1;
+    if (k < 0 || !obj || (every > 1 && k % every != 0)) return;
+    obj[k] = F;
+    if (ts) ts[k] = globaltimer_ns();
+    if (f_star > 0.0 && flags[0] == 0 && (F - f_star) <= target * f_star) {
+      flags[0] = 1;
+      flags[1] = k;
+      if (done_host) {
+        *(volatile int*)done_host = 1;
+        __threadfence_system();
+      }
+    }
+  }
+}
+
+__global__ void timestamp_kernel(unsigned long long* ts) { *ts = globaltimer_ns(); }
+
+__global__ void timestamp_pair_kernel(unsigned long long* arr, int* ctr, int which) {
+  const int c = *ctr;
+  arr[2 * c + which] = globaltimer_ns();
+  if (which == 1) *ctr = c + 1;
+}
+
+__global__ void count_nonfinite_kernel(const float* __restrict__ x, size_t n, int* count) {
+  int c = 0;
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n;
+       o += (size_t)gridDim.x * blockDim.x)
+    c += isfinite(x[o]) ? 0 : 1;
+  if (c) atomicAdd(count, c);
+}
+
+__global__ void coin_kernel(uint64_t seed, double p, int64_t k0, int K, unsigned char* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < K) out[i] = (unsigned char)Philox4x64::coin(seed, p, (uint64_t)(k0 + i));
+}
+
+template <int MODE>
+cudaError_t blur_launch(int H, int W, const float* src, const BlurW& w, const float* b, float* out,
+                        const float* x, const float* h, float gamma, float ch, float* axp, float* y,
+                        float tau, double* pa, double* pb, cudaStream_t s) {
+  if (w.R < 1 || w.R > RMAX) return cudaErrorInvalidValue;
+  dim3 grid((W + BX - 1) / BX, (H + BY - 1) / BY);
+  blur_kernel<MODE><<<grid, BNT, 0, s>>>(src, H, W, w, b, out, x, h, gamma, ch, axp, y, tau, pa, pb);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int tile_blocks_2d(int H, int W) { return ((W + BX - 1) / BX) * ((H + BY - 1) / BY); }
+
+int pointwise_blocks(size_t n) {
+  size_t b = (n + PW_NT - 1) / PW_NT;
+  const size_t cap = 152 * 8;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+cudaError_t launch_blur_residual(int H, int W, const float* x, const float* b, float* r_out,
+                                 const BlurW& w, double* part_data, double* part_tv, cudaStream_t s) {
+  return blur_launch<BM_RESID>(H, W, x, w, b, r_out, nullptr, nullptr, 0.f, 0.f, nullptr, nullptr,
+                               0.f, part_data, part_tv, s);
+}
+
+cudaError_t launch_blur_step(int H, int W, const float* in, const float* x, const float* h,
+                             float* out, const BlurW& w, float gamma, float ch, double* part_tv,
+                             cudaStream_t s) {
+  return blur_launch<BM_STEP>(H, W, in, w, nullptr, out, x, h, gamma, ch, nullptr, nullptr, 0.f,
+                              nullptr, part_tv, s);
+}
+
+cudaError_t launch_blur_pd_dual(int H, int W, const float* x, float* ax_prev, float* y,
+                                const float* b, const BlurW& w, float tau, double* part_data,
+                                cudaStream_t s) {
+  return blur_launch<BM_PD>(H, W, x, w, b, nullptr, nullptr, nullptr, 0.f, 0.f, ax_prev, y, tau,
+                            part_data, nullptr, s);
+}
+
+cudaError_t launch_blur(int H, int W, const float* x, float* y, const BlurW& w, cudaStream_t s) {
+  return blur_launch<BM_PLAIN>(H, W, x, w, nullptr, y, nullptr, nullptr, 0.f, 0.f, nullptr, nullptr,
+                               0.f, nullptr, nullptr, s);
+}
+
+cudaError_t launch_identity_step(const Dims& d, const float* x, const float* b, const float* h,
+                                 float* out, float gamma, float ch, double* part_data,
+                                 double* part_tv, cudaStream_t s) {
+  identity_step_kernel<<<pointwise_blocks(d.n()), PW_NT, 0, s>>>(x, b, h, out, d.nz, d.ny, d.nx,
+                                                                  d.ndim, gamma, ch, part_data, part_tv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_step(const Dims& d, const float* g, const float* x, const float* h,
+                             float* out, float sigma, float ch, double* part_tv, cudaStream_t s) {
+  axpy_step_kernel<<<pointwise_blocks(d.n()), PW_NT, 0, s>>>(g, x, h, out, d.nz, d.ny, d.nx, d.ndim,
+                                                              sigma, ch, part_tv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tv_partials(const Dims& d, const float* x, double* part_tv, cudaStream_t s) {
+  tv_partials_kernel<<<pointwise_blocks(d.n()), PW_NT, 0, s>>>(x, d.nz, d.ny, d.nx, d.ndim, part_tv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pd_dual_pointwise(size_t m, const float* ax, float* ax_prev, float* y,
+                                     const float* b, float tau, double* part_data, cudaStream_t s) {
+  pd_dual_pointwise_kernel<<<pointwise_blocks(m), PW_NT, 0, s>>>(m, ax, ax_prev, y, b, tau, part_data);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_record(const double* part_data, int n_data, const double* part_tv,
+                                 int n_tv, double alpha, int every, double* obj,
+                                 unsigned long long* ts, double f_star, double target, int* flags,
+                                 int* done_host, double* f_out, cudaStream_t s) {
+  reduce_record_kernel<<<1, 512, 0, s>>>(part_data, n_data, part_tv, n_tv, alpha, every, obj, ts,
+                                         f_star, target, flags, done_host, f_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_timestamp(unsigned long long* ts, cudaStream_t s) {
+  timestamp_kernel<<<1, 1, 0, s>>>(ts);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_timestamp_pair(unsigned long long* arr, int* ctr, int which, cudaStream_t s) {
+  timestamp_pair_kernel<<<1, 1, 0, s>>>(arr, ctr, which);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_nonfinite(const float* x, size_t n, int* count, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  count_nonfinite_kernel<<<pointwise_blocks(n), PW_NT, 0, s>>>(x, n, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coin_schedule(uint64_t seed, double p, int64_t k0, int K, unsigned char* out,
+                                 cudaStream_t s) {
+  if (K <= 0) return cudaSuccess;
+  coin_kernel<<<(K + 255) / 256, 256, 0, s>>>(seed, p, k0, K, out);
+  return cudaGetLastError();
+}
+
+}  // namespace tvs

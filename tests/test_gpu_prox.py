@@ -1,0 +1,134 @@
+"""GPU parity of the TV prox (fused FGP kernels) against the FP64 oracle."""
+
+import numpy as np
+import pytest
+
+from oracle import tv
+from synth import phantoms
+from tests._util import TOL_X_F32, TOL_X_HALF, cuda, f32, host, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tvs():
+    import paper_2411_00688_gb300 as tvs
+    return tvs
+
+
+@pytest.fixture(scope="module")
+def ctx(tvs):
+    c = tvs.Context(0)
+    yield c
+    c.close()
+
+
+def _z(shape, seed):
+    g = np.random.default_rng(seed)
+    if len(shape) == 2 and min(shape) >= 8:
+        base = phantoms.shapes_phantom_2d(shape[0], shape[1], 5, seed)
+    else:
+        base = np.zeros(shape)
+    return base + 0.2 * g.standard_normal(shape)
+
+
+def _run(tvs, ctx, z32, lam, n_iter, dual="f32", state=None, nonneg=False):
+    import torch
+    zt = cuda(z32)
+    ut = torch.empty_like(zt)
+    tvs.tv_prox(ctx, zt, ut, lam, n_iter, dual=dual, dual_state=state, nonneg=nonneg)
+    return host(ut)
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 7), (7, 1), (2, 2), (33, 47), (100, 130), (256, 256)])
+@pytest.mark.parametrize("lam,n_iter", [(0.05, 1), (0.3, 2), (0.15, 37)])
+def test_prox_2d_cold(tvs, ctx, shape, lam, n_iter):
+    z32, z64 = f32(_z(shape, 1))
+    u_ref, _ = tv.fgp_prox(z64, lam, n_iter)
+    u = _run(tvs, ctx, z32, lam, n_iter)
+    assert rel_l2(u, u_ref) <= TOL_X_F32
+
+
+@pytest.mark.parametrize("n_iter", [0, 3])
+def test_prox_lambda_zero_and_no_iterations(tvs, ctx, n_iter):
+    z32, z64 = f32(_z((19, 23), 2))
+    np.testing.assert_array_equal(_run(tvs, ctx, z32, 0.0, n_iter), z64)
+    if n_iter == 0:
+        np.testing.assert_array_equal(_run(tvs, ctx, z32, 0.2, 0), z64)
+
+
+def test_prox_2d_warm_start_and_nonneg(tvs, ctx):
+    import torch
+    shape = (70, 61)
+    z32, z64 = f32(_z(shape, 3))
+    lam = 0.2
+    state = torch.zeros((2,) + shape, dtype=torch.float32, device="cuda")
+    p_ref = None
+    for call in range(3):
+        u_ref, p_ref = tv.fgp_prox(z64, lam, 10 + call, p_ref)
+        u = _run(tvs, ctx, z32, lam, 10 + call, state=state)
+        assert rel_l2(u, u_ref) <= TOL_X_F32
+        assert rel_l2(host(state), p_ref) <= TOL_X_F32
+    u_ref, _ = tv.fgp_prox(z64 - 0.3, lam, 25, nonneg=True)
+    z32b, _ = f32(z64 - 0.3)
+    u = _run(tvs, ctx, z32b, lam, 25, nonneg=True)
+    assert u.min() >= 0.0
+    assert rel_l2(u, u_ref) <= TOL_X_F32
+
+
+@pytest.mark.parametrize("dual", ["bf16", "f16"])
+def test_prox_half_dual(tvs, ctx, dual):
+    z32, z64 = f32(_z((128, 96), 4))
+    u_ref, _ = tv.fgp_prox(z64, 0.1, 50)
+    assert rel_l2(_run(tvs, ctx, z32, 0.1, 50, dual=dual), u_ref) <= TOL_X_HALF
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (3, 4, 5), (17, 33, 40), (40, 9, 70)])
+def test_prox_3d(tvs, ctx, shape):
+    g = np.random.default_rng(5)
+    z32, z64 = f32(g.standard_normal(shape))
+    u_ref, _ = tv.fgp_prox(z64, 0.1, 12)
+    assert rel_l2(_run(tvs, ctx, z32, 0.1, 12), u_ref) <= TOL_X_F32
+
+
+def test_prox_full_size_2d(tvs, ctx):
+    """1024 x 1024, 50 iterations (the deblurring workload's prox), whole image."""
+    z32, z64 = f32(phantoms.ellipses_phantom_2d(1024, 40, 2000) + phantoms.gaussian_noise((1024, 1024), 0.05, 3))
+    lam = 0.2
+    u_ref, p_ref = tv.fgp_prox(z64, lam, 50)
+    u = _run(tvs, ctx, z32, lam, 50)
+    assert rel_l2(u, u_ref) <= TOL_X_F32
+    assert abs(u.sum() - z64.sum()) <= 1e-5 * np.abs(z64).sum()
+
+
+def test_prox_3d_properties_large(tvs, ctx):
+    """256^3 volume: properties that hold at any size (mean preservation, and the
+    ROF duality gap of the returned dual is small and non-negative), plus a
+    128^3 sub-problem compared whole with the oracle."""
+    import torch
+    N = 256
+    vol = phantoms.ellipsoids_phantom_3d(N, 20, 4000) + phantoms.gaussian_noise((N,) * 3, 0.05, 4001,
+                                                                                  dtype=np.float32)
+    z32 = np.ascontiguousarray(vol.astype(np.float32))
+    zt = cuda(z32)
+    ut = torch.empty_like(zt)
+    state = torch.zeros((3,) + z32.shape, dtype=torch.float32, device="cuda")
+    tvs.tv_prox(ctx, zt, ut, 0.05, 30, dual_state=state)
+    u = ut.double()
+    assert abs(u.sum().item() - zt.double().sum().item()) <= 1e-5 * zt.double().abs().sum().item()
+    assert torch.sqrt((state.double() ** 2).sum(0)).max().item() <= 1.0 + 1e-6
+    sub32 = np.ascontiguousarray(z32[:128, 64:192, 32:160])
+    u_ref, _ = tv.fgp_prox(sub32.astype(np.float64), 0.05, 30)
+    assert rel_l2(_run(tvs, ctx, sub32, 0.05, 30), u_ref) <= TOL_X_F32
+
+
+def test_prox_invalid_arguments(tvs, ctx):
+    import torch
+    z = torch.zeros((8, 8), device="cuda")
+    u = torch.zeros((8, 8), device="cuda")
+    with pytest.raises(tvs.TVSError):
+        tvs.tv_prox(ctx, z, u, -1.0, 5)
+    with pytest.raises(tvs.TVSError):
+        tvs.tv_prox(ctx, z, u, float("nan"), 5)
+    with pytest.raises(tvs.TVSError):
+        tvs.tv_prox(ctx, z, z, 0.1, 5)

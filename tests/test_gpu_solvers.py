@@ -1,0 +1,225 @@
+"""GPU parity of the outer solvers (PGD, FISTA, ProxSkip, PDHG, PDHGSkip-2)
+against the FP64 oracle: same seeded inputs, same coin schedule, final iterate
+within 1e-4 relative l2 and every recorded objective within 1e-6 relative."""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import coin, operators, solvers
+from oracle.power import power_method
+from synth import configs, phantoms
+from tests._util import TOL_OBJ, TOL_X_F32, TOL_X_HALF, cuda, f32, host, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tvs():
+    import paper_2411_00688_gb300 as tvs
+    return tvs
+
+
+@pytest.fixture(scope="module")
+def ctx(tvs):
+    c = tvs.Context(0)
+    yield c
+    c.close()
+
+
+def _data(shape, op, seed, noise):
+    truth = phantoms.shapes_phantom_2d(shape[0], shape[1], 6, seed)
+    if op == "blur":
+        clean = operators.blur(truth, operators.gaussian_weights(2.0, 4))
+    else:
+        clean = truth
+    return f32(clean + phantoms.gaussian_noise(shape, noise, seed + 1))
+
+
+def _check(trace, ref, x_gpu, tol_x=TOL_X_F32):
+    assert list(trace.coins) == list(ref["coins"])
+    assert trace.prox_calls == ref["prox_calls"]
+    assert rel_l2(x_gpu, ref["x"]) <= tol_x
+    obj = np.asarray(ref["objective"])
+    rel = np.abs(trace.objective - obj) / np.abs(obj)
+    assert rel.max() <= TOL_OBJ, rel.max()
+
+
+@pytest.mark.parametrize("op,shape", [("identity", (64, 80)), ("blur", (61, 47)), ("blur", (128, 128))])
+@pytest.mark.parametrize("solver", ["pgd", "proxskip", "fista"])
+def test_fb_solvers_small(tvs, ctx, op, shape, solver):
+    b32, b64 = _data(shape, op, 11, 0.05)
+    alpha, gamma, p, seed, K, N = 0.04, 1.0, 0.3, 7, 30, 20
+    prob = tvs.Problem(ctx, cuda(b32), alpha, op=op, blur_sigma=2.0)
+    A = operators.identity_op() if op == "identity" else operators.blur_op(2.0)
+    oprob = solvers.Problem(A, b64, alpha, shape)
+    x = cuda(b32)
+    if solver == "pgd":
+        x, tr = tvs.pgd_solve(prob, x, gamma, K, N)
+        ref = solvers.pgd(oprob, b64, gamma, K, N)
+    elif solver == "fista":
+        x, tr = tvs.fista_solve(prob, x, gamma, K, N)
+        ref = solvers.fista(oprob, b64, gamma, K, N)
+    else:
+        x, tr = tvs.proxskip_solve(prob, x, gamma, p, seed, K, N)
+        ref = solvers.proxskip(oprob, b64, gamma, p, seed, K, N)
+    _check(tr, ref, host(x))
+
+
+def test_proxskip_3d_small(tvs, ctx):
+    g = np.random.default_rng(3)
+    shape = (12, 20, 33)
+    b32, b64 = f32((g.random(shape) > 0.5) * 1.0 + 0.1 * g.standard_normal(shape))
+    prob = tvs.Problem(ctx, cuda(b32), 0.08)
+    x, tr = tvs.proxskip_solve(prob, cuda(b32), 1.0, 0.4, 3, 15, 10)
+    ref = solvers.proxskip(solvers.Problem(operators.identity_op(), b64, 0.08, shape), b64, 1.0, 0.4, 3, 15, 10)
+    _check(tr, ref, host(x))
+
+
+def test_proxskip_nonneg_and_host_memory(tvs, ctx):
+    """Host (numpy) buffers go through the same path; the non-negativity constraint."""
+    b32, b64 = _data((40, 52), "blur", 21, 0.05)
+    b32 = b32 - np.float32(0.2)
+    b64 = b32.astype(np.float64)
+    prob = tvs.Problem(ctx, b32, 0.03, op="blur", blur_sigma=2.0, nonneg=True)
+    x = b32.copy()
+    x, tr = tvs.proxskip_solve(prob, x, 1.0, 0.5, 4, 20, 15)
+    ref = solvers.proxskip(solvers.Problem(operators.blur_op(2.0), b64, 0.03, (40, 52), nonneg=True),
+                           b64, 1.0, 0.5, 4, 20, 15)
+    _check(tr, ref, x.astype(np.float64))
+
+
+@pytest.mark.parametrize("dual", ["bf16", "f16"])
+def test_proxskip_half_dual(tvs, ctx, dual):
+    b32, b64 = _data((96, 96), "blur", 31, 0.02)
+    prob = tvs.Problem(ctx, cuda(b32), 0.03, op="blur", blur_sigma=2.0)
+    x, tr = tvs.proxskip_solve(prob, cuda(b32), 1.0, 0.3, 2, 25, 20, dual=dual)
+    ref = solvers.proxskip(solvers.Problem(operators.blur_op(2.0), b64, 0.03, (96, 96)), b64, 1.0, 0.3, 2, 25, 20)
+    assert rel_l2(host(x), ref["x"]) <= TOL_X_HALF
+
+
+def test_proxskip_p1_equals_pgd_on_gpu(tvs, ctx):
+    b32, _ = _data((50, 50), "blur", 41, 0.02)
+    prob = tvs.Problem(ctx, cuda(b32), 0.03, op="blur", blur_sigma=2.0)
+    x1, t1 = tvs.pgd_solve(prob, cuda(b32), 1.0, 12, 10)
+    x2, t2 = tvs.proxskip_solve(prob, cuda(b32), 1.0, 1.0, 9, 12, 10)
+    assert rel_l2(host(x2), host(x1)) <= 1e-5
+    assert t2.prox_calls == 12
+
+
+def _ct_setup(N, na, nd, seed, alpha, nonneg=False):
+    geom = operators.ParallelBeam.unit_square(N, na, nd)
+    truth = phantoms.ellipses_phantom_2d(N, 5, seed, intensity=(0.0, 0.5))
+    clean = operators.joseph_forward(truth, geom)
+    b32, b64 = f32(clean + phantoms.gaussian_noise(clean.shape, 0.002, seed + 1))
+    A = operators.ct_op(geom)
+    L = power_method(lambda x: A.adjoint(A.forward(x)), (N, N), 100)
+    return geom, b32, b64, solvers.Problem(A, b64, alpha, (N, N), nonneg), L
+
+
+@pytest.mark.parametrize("skip", [False, True])
+def test_pd_solvers_ct_small(tvs, ctx, skip):
+    N, na, nd = 48, 60, 69
+    geom, b32, b64, oprob, L = _ct_setup(N, na, nd, 51, 0.002)
+    st = 0.99 / math.sqrt(L)
+    prob = tvs.Problem(ctx, cuda(b32), 0.002, op="ct", shape=(N, N), n_angles=na, n_det=nd,
+                       pixel_size=1.0 / N, det_spacing=1.0 / N)
+    x0 = np.zeros((N, N), dtype=np.float32)
+    y0 = np.zeros((na, nd), dtype=np.float32)
+    K, NI, p, seed = 25, 15, 0.3, 6
+    if skip:
+        x, y, tr = tvs.pdhgskip_solve(prob, cuda(x0), cuda(y0), st, st, p, seed, K, NI)
+        ref = solvers.pdhgskip2(oprob, x0.astype(np.float64), y0.astype(np.float64), st, st, p, seed, K, NI)
+    else:
+        x, y, tr = tvs.pdhg_solve(prob, cuda(x0), cuda(y0), st, st, K, NI)
+        ref = solvers.pdhg(oprob, x0.astype(np.float64), y0.astype(np.float64), st, st, K, NI)
+    _check(tr, ref, host(x))
+    assert rel_l2(host(y), ref["y"]) <= TOL_X_F32
+
+
+@pytest.mark.parametrize("op", ["identity", "blur"])
+def test_pdhgskip_image_operators(tvs, ctx, op):
+    b32, b64 = _data((45, 58), op, 61, 0.05)
+    A = operators.identity_op() if op == "identity" else operators.blur_op(2.0)
+    oprob = solvers.Problem(A, b64, 0.04, (45, 58))
+    prob = tvs.Problem(ctx, cuda(b32), 0.04, op=op, blur_sigma=2.0)
+    y0 = np.zeros_like(b32)
+    x, y, tr = tvs.pdhgskip_solve(prob, cuda(b32), cuda(y0), 0.9, 0.9, 0.4, 8, 20, 12)
+    ref = solvers.pdhgskip2(oprob, b64, y0.astype(np.float64), 0.9, 0.9, 0.4, 8, 20, 12)
+    _check(tr, ref, host(x))
+
+
+def test_ct_nonneg_proxskip(tvs, ctx):
+    """ProxSkip on the CT operator with the non-negativity constraint."""
+    N, na, nd = 32, 40, 47
+    geom, b32, b64, oprob, L = _ct_setup(N, na, nd, 71, 0.002, nonneg=True)
+    gamma = 1.0 / L
+    prob = tvs.Problem(ctx, cuda(b32), 0.002, op="ct", shape=(N, N), n_angles=na, n_det=nd,
+                       pixel_size=1.0 / N, det_spacing=1.0 / N, nonneg=True)
+    x0 = np.zeros((N, N), dtype=np.float32)
+    x, tr = tvs.proxskip_solve(prob, cuda(x0), gamma, 0.3, 5, 20, 10)
+    ref = solvers.proxskip(oprob, x0.astype(np.float64), gamma, 0.3, 5, 20, 10)
+    _check(tr, ref, host(x))
+
+
+def test_deblur_full_size_prefix(tvs, ctx):
+    """1024 x 1024 deblurring workload (9x9 Gaussian sigma 2, alpha 0.02, 50 inner
+    iterations, p = 0.5) in the configuration the benchmark times: 4 outer iterations
+    compared with the oracle."""
+    cfg = configs.DeblurConfig()
+    truth = cfg.phantom()
+    w = operators.gaussian_weights(cfg.blur_sigma, cfg.blur_radius)
+    b32, b64 = f32(operators.blur(truth, w) + cfg.noise())
+    prob = tvs.Problem(ctx, cuda(b32), cfg.alpha, op="blur", blur_sigma=cfg.blur_sigma)
+    K = 4
+    x, tr = tvs.proxskip_solve(prob, cuda(b32), 1.0, 0.5, cfg.seed, K, cfg.n_inner)
+    ref = solvers.proxskip(solvers.Problem(operators.blur_op(cfg.blur_sigma), b64, cfg.alpha, b64.shape),
+                           b64, 1.0, 0.5, cfg.seed, K, cfg.n_inner)
+    _check(tr, ref, host(x))
+
+
+def test_denoise_full_size(tvs, ctx):
+    """256 x 256 denoising workload (alpha 0.1, p 0.1, 100 inner iterations), 40 iterations."""
+    cfg = configs.DenoiseConfig()
+    b32, b64 = f32(cfg.phantom() + cfg.noise())
+    prob = tvs.Problem(ctx, cuda(b32), cfg.alpha)
+    K = 40
+    x, tr = tvs.proxskip_solve(prob, cuda(b32), cfg.gamma, cfg.p, cfg.seed, K, cfg.n_inner)
+    ref = solvers.proxskip(solvers.Problem(operators.identity_op(), b64, cfg.alpha, b64.shape), b64,
+                           cfg.gamma, cfg.p, cfg.seed, K, cfg.n_inner)
+    _check(tr, ref, host(x))
+
+
+def test_solver_edge_cases(tvs, ctx):
+    b32, b64 = _data((20, 24), "blur", 81, 0.02)
+    prob = tvs.Problem(ctx, cuda(b32), 0.05, op="blur", blur_sigma=2.0)
+    x, tr = tvs.proxskip_solve(prob, cuda(b32), 1.0, 0.5, 1, 0, 10)      # no iterations
+    assert tr.iters_run == 0 and np.array_equal(host(x), b64)
+    x, tr = tvs.proxskip_solve(prob, cuda(b32), 1.0, 0.5, 1, 6, 0)      # no inner iterations
+    ref = solvers.proxskip(solvers.Problem(operators.blur_op(2.0), b64, 0.05, (20, 24)), b64, 1.0, 0.5, 1, 6, 0)
+    _check(tr, ref, host(x))
+    prob0 = tvs.Problem(ctx, cuda(b32), 0.0, op="blur", blur_sigma=2.0)  # alpha = 0: no prox
+    x, tr = tvs.pgd_solve(prob0, cuda(b32), 1.0, 5, 10)
+    ref = solvers.pgd(solvers.Problem(operators.blur_op(2.0), b64, 0.0, (20, 24)), b64, 1.0, 5, 10)
+    _check(tr, ref, host(x))
+    for bad in (0.0, 1.5, float("nan")):
+        with pytest.raises(tvs.TVSError):
+            tvs.proxskip_solve(prob, cuda(b32), 1.0, bad, 1, 5, 5)
+    with pytest.raises(tvs.TVSError):
+        tvs.pgd_solve(prob, cuda(b32), -1.0, 5, 5)
+
+
+def test_target_stops_early(tvs, ctx):
+    """With f* given, the solve stops within a few iterations after the gap target."""
+    b32, b64 = _data((64, 64), "identity", 91, 0.1)
+    prob = tvs.Problem(ctx, cuda(b32), 0.1)
+    _, full = tvs.pgd_solve(prob, cuda(b32), 1.0, 200, 30)
+    f_star = float(np.min(full.objective))
+    x, tr = tvs.pgd_solve(prob, cuda(b32), 1.0, 200, 30, f_star=f_star, target=1e-3)
+    assert tr.reached
+    k = tr.reached_iter
+    assert (tr.objective[k] - f_star) <= 1e-3 * f_star
+    assert np.all(tr.objective[:k] - f_star > 1e-3 * f_star)
+    assert tr.iters_run <= k + 1 + 10
+    assert tr.time_to_target_s > 0
