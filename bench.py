@@ -3,10 +3,12 @@ PGD with the same prox, and the fused FGP kernel's bandwidth against HBM peak.
 
 Workload: 2D TV deblurring, 1024 x 1024 phantom of 40 random ellipses, 9x9
 Gaussian blur (sigma 2, reflective boundary), noise sigma 0.01, alpha 0.02,
-gamma = 1/||A||^2 = 1, ProxSkip p = 0.1 (Philox seed 0), 50 FGP iterations per
-prox, at most 1000 outer iterations, FP32 iterates and dual.  One step = one
-ProxSkip solve from x_0 = b until (F(x_k) - F*)/F* <= 1e-4.  F* is the smallest
+gamma = 1/||A||^2 = 1, 50 FGP iterations per prox, at most 1000 outer
+iterations, FP32 iterates and dual.  One step = one ProxSkip solve (p = 0.5,
+Philox seed 0) from x_0 = b until (F(x_k) - F*)/F* <= 1e-4.  F* is the smallest
 objective of a long FISTA run (3000 iterations, 100 inner) made before timing.
+PGD with the same prox, and ProxSkip at p = 0.1 and 0.05, are run to the same
+target (at most 1000 iterations) outside the timed region and reported beside it.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -31,12 +33,13 @@ if ROOT not in sys.path:
 
 METRIC = "ProxSkip time-to-1e-4 gap vs PGD on one GB300; FGP TB/s vs HBM peak"
 TARGET = 1e-4
-P_SKIP = 0.1
+P_SKIP = 0.5
+P_OTHERS = (0.1, 0.05)
 F_STAR_ITERS, F_STAR_INNER = 3000, 100
 FGP_BYTES_PER_PX = 28        # read z (4) + p_k (8) + p_{k-1} (8), write p_{k+1} (8), FP32 dual
 # Iterations / prox calls this workload's ProxSkip solve needs to reach the target
 # (from the solver's trace); used only to scale the CPU oracle sample.
-REF_ITERS_DEFAULT, REF_PROX_DEFAULT = 300, 30
+REF_ITERS_DEFAULT, REF_PROX_DEFAULT = 260, 130
 
 
 def _env_rank():
@@ -154,9 +157,9 @@ def run_gpu(args):
     _, fista_tr = tvs.fista_solve(prob, b.clone(), gamma, F_STAR_ITERS, F_STAR_INNER)
     f_star = float(np.nanmin(fista_tr.objective))
 
-    def solve(kind, x):
+    def solve(kind, x, p=P_SKIP):
         if kind == "proxskip":
-            return tvs.proxskip_solve(prob, x, gamma, P_SKIP, cfg.seed, cfg.max_iter, cfg.n_inner,
+            return tvs.proxskip_solve(prob, x, gamma, p, cfg.seed, cfg.max_iter, cfg.n_inner,
                                       f_star=f_star, target=TARGET)
         return tvs.pgd_solve(prob, x, gamma, cfg.max_iter, cfg.n_inner, f_star=f_star, target=TARGET)
 
@@ -188,6 +191,21 @@ def run_gpu(args):
     with ClockSampler(local) as clk:
         ps_times, ps_tr = timed("proxskip", args.steps)
     clocks = clk.summary()
+
+    # the other probabilities of the workload, one solve each (outside the timed region)
+    per_p = {}
+    for pp in (P_SKIP,) + P_OTHERS:
+        x.copy_(b)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, tr = solve("proxskip", x, pp)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        gaps = (tr.objective - f_star) / f_star
+        per_p[str(pp)] = {"reached": tr.reached, "iterations": (tr.reached_iter + 1) if tr.reached else tr.iters_run,
+                          "prox_calls": tr.prox_calls, "time_s": e0.elapsed_time(e1) / 1e3,
+                          "final_rel_gap": float(gaps[-1]), "best_rel_gap": float(np.nanmin(gaps))}
 
     # FGP kernel duration with CUDA events on the launching stream: tv_prox with
     # N inner iterations minus tv_prox with none, divided by N.
@@ -257,7 +275,7 @@ def run_gpu(args):
         "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": "deblur2d_1024: 1024x1024, 40 ellipses, 9x9 Gaussian sigma 2, noise 0.01, "
-                               "alpha 0.02, gamma 1, ProxSkip p 0.1 seed 0, 50 FGP iterations per prox, "
+                               "alpha 0.02, gamma 1, ProxSkip p 0.5 seed 0, 50 FGP iterations per prox, "
                                "stop at relative objective gap 1e-4 (max 1000 iterations)",
                    "parallelism": f"replicas x{world}", "l2": "flushed between steps (256 MB write)",
                    "f_star": f_star},
@@ -269,6 +287,7 @@ def run_gpu(args):
         "pgd_iterations_to_target": pgd_tr[-1].reached_iter + 1 if pgd_tr[-1].reached else None,
         "speedup_vs_pgd": (statistics.mean(pgd_times) / statistics.mean(ps_times))
         if all(t.reached for t in pgd_tr) else None,
+        "proxskip_by_p": per_p,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": None,
                      "kernel": "fgp2d_kernel<float>", "bytes_per_launch": bytes_per_launch,

@@ -79,6 +79,7 @@ struct tvs_ctx {
   cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
   cudaEvent_t ring[LAG] = {};
   size_t bytes = 0;
+  FgpConfig fgp;
 };
 
 struct tvs_problem {
@@ -97,7 +98,7 @@ struct tvs_problem {
   float* r = nullptr;
   float* y = nullptr;
   float* axp = nullptr;
-  void* dual[3] = {nullptr, nullptr, nullptr};
+  void* dual[4] = {nullptr, nullptr, nullptr, nullptr};
   double* part_a = nullptr;
   double* part_b = nullptr;
   int max_parts = 0;
@@ -154,11 +155,27 @@ std::vector<float> fgp_betas(int n_iter) {
 }
 
 // N inner iterations on z starting from the dual in buf[0]; returns the index
-// of the buffer that holds p_N.
-tvs_status launch_fgp_sequence(const Dims& d, const float* z, void* const buf[3], int n_iter,
-                               const std::vector<float>& betas, float lam, int dtype, bool nonneg,
-                               cudaStream_t s, int* final_idx) {
+// of the buffer that holds p_N.  2D problems use the temporally blocked kernel
+// (pairs (buf[0], buf[1]) and (buf[2], buf[3]) alternate as input and output);
+// otherwise the one-iteration kernel rotates through buf[0..2].
+tvs_status launch_fgp_sequence(const FgpConfig& cfg, const Dims& d, const float* z,
+                               void* const buf[4], int n_iter, const std::vector<float>& betas,
+                               float lam, int dtype, bool nonneg, cudaStream_t s, int* final_idx) {
   const float inv_step = (float)(1.0 / (4.0 * d.ndim * (double)lam));
+  if (d.ndim == 2 && cfg.tb > 1) {
+    int q = 0;
+    for (int g = 1; g <= n_iter;) {
+      const int it = std::min(cfg.tb, n_iter - g + 1);
+      void* pc = buf[2 * q];
+      void* pp = g == 1 ? pc : buf[2 * q + 1];
+      CUDA_TRY(launch_fgp_block(cfg, d, z, pc, pp, buf[2 * (1 - q)], buf[2 * (1 - q) + 1], lam, inv_step,
+                                &betas[g - 1], it, dtype, nonneg, s));
+      q = 1 - q;
+      g += it;
+    }
+    *final_idx = 2 * q;
+    return TVS_OK;
+  }
   for (int i = 1; i <= n_iter; ++i) {
     void* cur = buf[(i - 1) % 3];
     void* prev = i >= 2 ? buf[(i - 2) % 3] : cur;
@@ -167,6 +184,20 @@ tvs_status launch_fgp_sequence(const Dims& d, const float* z, void* const buf[3]
   }
   *final_idx = n_iter % 3;
   return TVS_OK;
+}
+
+FgpConfig default_fgp_config() {
+  // 4 iterations per launch on 32 x 40 staged cells (24 x 32 outputs): the
+  // fastest variant measured on GB300 at 256^2 .. 8192^2.
+  FgpConfig c;
+  c.tb = 4;
+  c.cpl = 1;
+  c.rpw = 5;
+  if (const char* e = getenv("TVS_FGP_CONFIG")) {
+    FgpConfig t;
+    if (sscanf(e, "%d,%d,%d", &t.tb, &t.cpl, &t.rpw) >= 1 && fgp_config_valid(t)) c = t;
+  }
+  return c;
 }
 
 tvs_status copy_in(float* dst, const float* src, size_t n, tvs_mem mem, cudaStream_t s) {
@@ -527,7 +558,7 @@ tvs_status fb_solve(tvs_problem* P, const tvs_fb_params* prm, float* x_io, tvs_m
         if (c == 1) {
           int fin = 0;
           CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 0, s));
-          if (use_prox) TVS_TRY(launch_fgp_sequence(d, P->z, P->dual, N, betas, lam, dtype, nonneg, s, &fin));
+          if (use_prox) TVS_TRY(launch_fgp_sequence(C->fgp, d, P->z, P->dual, N, betas, lam, dtype, nonneg, s, &fin));
           CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 1, s));
           CUDA_TRY(launch_fgp_finalize(d, P->z, P->dual[fin], dtype, use_prox ? lam : 0.f, nonneg, xn,
                                        kind == FB_PROXSKIP ? P->h : nullptr, h_coef,
@@ -613,7 +644,7 @@ tvs_status pd_solve(tvs_problem* P, const tvs_pd_params* prm, float* x_io, float
         if (c == 1) {
           int fin = 0;
           CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 0, s));
-          if (use_prox) TVS_TRY(launch_fgp_sequence(d, P->z, P->dual, N, betas, lam, dtype, nonneg, s, &fin));
+          if (use_prox) TVS_TRY(launch_fgp_sequence(C->fgp, d, P->z, P->dual, N, betas, lam, dtype, nonneg, s, &fin));
           CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 1, s));
           CUDA_TRY(launch_fgp_finalize(d, P->z, P->dual[fin], dtype, use_prox ? lam : 0.f, nonneg, xn,
                                        skip ? P->h : nullptr, (float)(p / sigma),
@@ -655,6 +686,7 @@ tvs_status tvs_create(tvs_ctx** out, int device, void* cuda_stream) {
   CUDA_TRY(cudaSetDevice(device));
   tvs_ctx* C = new tvs_ctx();
   C->device = device;
+  C->fgp = default_fgp_config();
   cudaStream_t s = (cudaStream_t)cuda_stream;
   if (s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread) {
     cudaError_t e = cudaStreamCreateWithFlags(&C->stream, cudaStreamNonBlocking);
@@ -671,6 +703,7 @@ tvs_status tvs_create(tvs_ctx** out, int device, void* cuda_stream) {
   for (int i = 0; i < LAG && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&C->ring[i], cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMalloc(&C->red_out, sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&C->flags, 4 * sizeof(int));
+  if (e == cudaSuccess) e = fgp_prepare_device();
   if (e != cudaSuccess) {
     tvs_destroy(C);
     return fail(TVS_ECUDA, "context setup: %s", cudaGetErrorString(e));
@@ -747,7 +780,7 @@ tvs_status tvs_problem_create(tvs_ctx* C, const tvs_problem_desc* desc, const fl
       (st = palloc(P, &P->z, n_img)) || (st = palloc(P, &P->h, n_img)) || (st = palloc(P, &P->r, m)) ||
       (st = palloc(P, &P->y, m)) || (st = palloc(P, &P->axp, m)))
     return bail(st);
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < 4; ++i)
     if ((st = dalloc(C, &P->bytes, &P->dual[i], 4 * (size_t)D.ndim * n_img))) return bail(st);
   if (op.kind == TVS_OP_PARALLEL_BEAM) {
     if ((st = palloc(P, &P->angle_tab, (size_t)op.n_angles)) || (st = palloc(P, &P->xt, n_img))) return bail(st);
@@ -807,7 +840,7 @@ tvs_status tvs_problem_destroy(tvs_problem* P) {
   cudaSetDevice(C->device);
   cudaStreamSynchronize(C->stream);
   void* bufs[] = {P->b, P->x[0], P->x[1], P->z, P->h, P->r, P->y, P->axp, P->dual[0], P->dual[1],
-                  P->dual[2], P->part_a, P->part_b, P->obj_dev, P->ts_dev, P->fgp_ts, P->beta_dev,
+                  P->dual[2], P->dual[3], P->part_a, P->part_b, P->obj_dev, P->ts_dev, P->fgp_ts, P->beta_dev,
                   P->flags, P->count, P->angle_tab, P->xt};
   for (void* b : bufs) dfree(b);
   if (P->done_host) cudaFreeHost(P->done_host);
@@ -863,7 +896,7 @@ tvs_status tv_prox(tvs_ctx* C, int ndim, const int dims[3], const float* z, floa
   d.ndim = ndim;
   const size_t n = d.n();
   const size_t plane_bytes = dual_elem_bytes(dual) * ndim * n;
-  const size_t need = plane_bytes * (dual_state ? 2 : 3);
+  const size_t need = plane_bytes * (dual_state ? 3 : 4);
   cudaStream_t s = C->stream;
   if (need > C->prox_scratch_bytes) {
     dfree(C->prox_scratch);
@@ -874,21 +907,18 @@ tvs_status tv_prox(tvs_ctx* C, int ndim, const int dims[3], const float* z, floa
     C->prox_scratch_bytes = need;
   }
   char* sc = (char*)C->prox_scratch;
-  void* buf[3];
+  void* buf[4];
   if (dual_state) {
     buf[0] = dual_state;
-    buf[1] = sc;
-    buf[2] = sc + plane_bytes;
+    for (int i = 1; i < 4; ++i) buf[i] = sc + (i - 1) * plane_bytes;
   } else {
-    buf[0] = sc;
-    buf[1] = sc + plane_bytes;
-    buf[2] = sc + 2 * plane_bytes;
+    for (int i = 0; i < 4; ++i) buf[i] = sc + i * plane_bytes;
     CUDA_TRY(cudaMemsetAsync(buf[0], 0, plane_bytes, s));
   }
   const bool use = lambda > 0.0;
   int fin = 0;
-  if (use) TVS_TRY(launch_fgp_sequence(d, z, buf, n_iter, fgp_betas(n_iter), (float)lambda, dual,
-                                       nonneg != 0, s, &fin));
+  if (use) TVS_TRY(launch_fgp_sequence(C->fgp, d, z, buf, n_iter, fgp_betas(n_iter), (float)lambda,
+                                       dual, nonneg != 0, s, &fin));
   CUDA_TRY(launch_fgp_finalize(d, z, buf[fin], dual, use ? (float)lambda : 0.f, nonneg != 0, u,
                                nullptr, 0.f, (fin != 0 && dual_state) ? dual_state : nullptr,
                                nullptr, nullptr, nullptr, nullptr, s));

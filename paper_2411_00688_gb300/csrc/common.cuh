@@ -16,16 +16,19 @@ template <> struct Elem<float> {
   static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
   static __device__ __forceinline__ float ldc(const float* p) { return *p; }
   static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+  static __device__ __forceinline__ float round(float v) { return v; }
 };
 template <> struct Elem<__nv_bfloat16> {
   static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
   static __device__ __forceinline__ float ldc(const __nv_bfloat16* p) { return __bfloat162float(*p); }
   static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+  static __device__ __forceinline__ float round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 };
 template <> struct Elem<__half> {
   static __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
   static __device__ __forceinline__ float ldc(const __half* p) { return __half2float(*p); }
   static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+  static __device__ __forceinline__ float round(float v) { return __half2float(__float2half_rn(v)); }
 };
 
 // ---------------------------------------------------------------- Philox4x64-10

@@ -21,6 +21,21 @@ inline size_t dual_elem_bytes(int t) { return t == DUAL_F32 ? 4 : 2; }
 cudaError_t launch_fgp_iter(const Dims& d, const float* z, const void* pc, const void* pp, void* pn,
                             float lam, float inv_step, float beta, int dtype, bool nonneg,
                             cudaStream_t s);
+// Temporally blocked inner iterations (2D): tile-shape / depth configuration.
+// tb <= 1 selects the one-iteration kernel.  A launch of the blocked kernel runs
+// `iters` <= tb iterations from (pc = p_k, pp = p_{k-1}) and writes
+// pn = p_{k+iters}, pnp = p_{k+iters-1}; betas[i] is the momentum coefficient of
+// its i-th iteration.  pn/pnp may not alias pc/pp.
+struct FgpConfig {
+  int tb = 1, cpl = 2, rpw = 5;
+};
+bool fgp_config_valid(const FgpConfig& c);
+// Raises the dynamic shared-memory limit of every blocked-kernel variant on the
+// current device (called once per context, outside any stream capture).
+cudaError_t fgp_prepare_device();
+cudaError_t launch_fgp_block(const FgpConfig& c, const Dims& d, const float* z, const void* pc,
+                             const void* pp, void* pn, void* pnp, float lam, float inv_step,
+                             const float* betas, int iters, int dtype, bool nonneg, cudaStream_t s);
 // x_out = P_X(z + lam div p); if h_out: h_out = h_coef (x_out - z);
 // if p_home: p_home = p.  When fista_y is set: fista_y = x_out + beta (x_out - x_prev) with
 // beta = beta_tab[*beta_idx] (FISTA extrapolation, read on the device).
