@@ -1,0 +1,63 @@
+"""Small driver for profiling the inner TV-prox kernels with ncu.
+
+Runs ``tv_prox`` (the fused FGP iterations and the finalisation) on a seeded
+random image of the requested size, a few times, so that a profiler can capture
+single launches of the kernel of interest:
+
+    python -m paper_2411_00688_gb300.prof --shape 4096 4096 --iters 8 --reps 3
+    python -m paper_2411_00688_gb300.prof --shape 256 256 256 --iters 4 --dual bf16
+
+It prints the per-iteration time measured with CUDA events on the launching
+stream (not meaningful under a profiler).
+"""
+
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import statistics
+
+
+def main(argv=None):
+    import torch
+
+    import paper_2411_00688_gb300 as tvs
+    from paper_2411_00688_gb300 import _lib as L
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--shape", type=int, nargs="+", default=[4096, 4096])
+    ap.add_argument("--iters", type=int, default=8)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--lam", type=float, default=0.2)
+    ap.add_argument("--dual", default="f32", choices=["f32", "bf16", "f16"])
+    args = ap.parse_args(argv)
+
+    stream = torch.cuda.Stream()
+    ctx = tvs.Context.__new__(tvs.Context)
+    ctx._h = C.c_void_p()
+    L.check(L.lib().tvs_create(C.byref(ctx._h), torch.cuda.current_device(), C.c_void_p(stream.cuda_stream)))
+    ctx.device = torch.cuda.current_device()
+    shape = tuple(args.shape)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    z = (torch.rand(shape, device="cuda", generator=g) > 0.5).float() + 0.2 * torch.randn(
+        shape, device="cuda", generator=g)
+    u = torch.empty_like(z)
+    dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[args.dual]
+    state = torch.zeros((len(shape),) + shape, dtype=dt, device="cuda")
+    times = []
+    for _ in range(args.reps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tvs.tv_prox(ctx, z, u, args.lam, args.iters, dual=args.dual, dual_state=state)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / max(args.iters, 1))
+    print(f"shape {shape} dual {args.dual}: {statistics.median(times) * 1e3:.2f} us per inner iteration "
+          f"(incl. finalisation)")
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()
