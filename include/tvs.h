@@ -168,6 +168,32 @@ tvs_status tvs_objective(tvs_problem* prob, const float* x, double* out);
 tvs_status tv_prox(tvs_ctx* ctx, int ndim, const int dims[3], const float* z, float* u,
                    double lambda, int n_iter, tvs_dual_dtype dual, void* dual_state, int nonneg);
 
+/* ---- allocation-free TV prox -------------------------------------------------- */
+/* The paper has no counterpart to this entry point.  It serves callers that may
+ * not allocate device memory: applications that reserve all of the GPU's memory
+ * for their own pool, or that run beside a thread capturing a CUDA graph in
+ * global mode (where cudaMalloc is refused).  It computes exactly what tv_prox
+ * computes, without a context and without allocating or freeing anything: the
+ * working dual fields live in one array of TVS_NOALLOC_SCRATCH_BYTES that the
+ * library image places on every GPU that loads it (held until the process exits).
+ *
+ * Arguments are those of tv_prox, on the current device, plus the cudaStream_t
+ * to launch on (NULL = the default stream); the call synchronises that stream
+ * before returning.  The scratch needed is (dual_state ? 3 : 4) * ndim * n
+ * elements of the dual type (n = pixels): a 1024 x 1024 FP32 image fits, and a
+ * larger request returns TVS_EUNSUPPORTED without launching anything.  Invalid
+ * arguments give TVS_EINVAL, CUDA failures TVS_ECUDA; no message is recorded
+ * for tvs_last_error().  The first call on a device looks up the array's device
+ * address (and sets kernel attributes) with that device current; make it before
+ * any stream capture begins.  All calls on a device share the array, which keeps
+ * the last call's contents (the cold-start dual is cleared on every call): calls
+ * whose GPU work overlaps -- from several host threads or several streams --
+ * race on it and must be serialised by the caller. */
+#define TVS_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+tvs_status tv_prox_noalloc(int ndim, const int dims[3], const float* z, float* u, double lambda,
+                           int n_iter, tvs_dual_dtype dual, void* dual_state, int nonneg,
+                           void* cuda_stream);
+
 /* ---- outer solvers --------------------------------------------------------- */
 /* x_inout: initial iterate in, final iterate out (image size, TVS_MEM_* says
  * where it lives).  The control variate starts at h_0 = 0, the TV dual at 0. */

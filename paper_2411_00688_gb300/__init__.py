@@ -16,6 +16,7 @@ from .api import (  # noqa: F401
     pgd_solve,
     proxskip_solve,
     tv_prox,
+    tv_prox_noalloc,
     tvs_coin,
     tvs_coin_schedule_device,
     tvs_objective,

@@ -69,6 +69,8 @@ SIGNATURES = [
     ("tvs_objective", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     ("tv_prox", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_void_p, C.c_void_p,
                           C.c_double, C.c_int, C.c_int, C.c_void_p, C.c_int]),
+    ("tv_prox_noalloc", C.c_int, [C.c_int, C.POINTER(C.c_int), C.c_void_p, C.c_void_p, C.c_double,
+                                  C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p]),
     ("pgd_solve", C.c_int, [C.c_void_p, C.POINTER(FBParams), C.c_void_p, C.c_int, C.POINTER(Trace)]),
     ("fista_solve", C.c_int, [C.c_void_p, C.POINTER(FBParams), C.c_void_p, C.c_int, C.POINTER(Trace)]),
     ("proxskip_solve", C.c_int, [C.c_void_p, C.POINTER(FBParams), C.c_void_p, C.c_int,

@@ -208,6 +208,30 @@ def tv_prox(ctx: Context, z, u, lam: float, n_iter: int, dual: str = "f32", dual
     return u
 
 
+def tv_prox_noalloc(z, u, lam: float, n_iter: int, dual: str = "f32", dual_state=None,
+                    nonneg: bool = False) -> int:
+    """u = prox_{lam TV}(z) through the allocation-free entry point.
+
+    For callers that may not allocate device memory: no context is used and the
+    library allocates nothing (its working dual fields sit in a fixed device
+    array of TVS_NOALLOC_SCRATCH_BYTES).  Runs on torch's current stream and
+    returns the raw tvs_status (0 on success; 6 when the image needs more scratch
+    than the fixed array holds).
+    """
+    torch = _torch()
+    shape = tuple(z.shape)
+    if len(shape) == 2:
+        dims = (C.c_int * 3)(shape[1], shape[0], 1)
+    elif len(shape) == 3:
+        dims = (C.c_int * 3)(shape[2], shape[1], shape[0])
+    else:
+        raise ValueError("z must be 2D or 3D")
+    ds = C.c_void_p(dual_state.data_ptr()) if dual_state is not None else None
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return int(L.lib().tv_prox_noalloc(len(shape), dims, C.c_void_p(z.data_ptr()), C.c_void_p(u.data_ptr()),
+                                       float(lam), int(n_iter), L.DUAL[dual], ds, int(bool(nonneg)), stream))
+
+
 def _fb(fn_name, prob, x, gamma, max_iter, n_inner, p=1.0, seed=0, dual="f32", f_star=0.0,
         target=0.0, every=1):
     prm = L.FBParams(gamma=float(gamma), p=float(p), seed=int(seed) & ((1 << 64) - 1),
