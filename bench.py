@@ -233,13 +233,18 @@ def run_gpu(args):
             best.append(e0.elapsed_time(e1) * 1e-3)
         return statistics.median(best)
 
+    # one launch of the blocked 2D kernel runs fgp_cfg[0] inner iterations
+    fgp_cfg = tvs.tvs_fgp_config(ctx, (H, W))
     n_fgp = cfg.n_inner
-    fgp_s = (prox_time(n_fgp) - prox_time(0)) / n_fgp
+    iters_per_launch = fgp_cfg[0]
+    launches_per_prox = -(-n_fgp // iters_per_launch)
+    fgp_launch_s = (prox_time(n_fgp) - prox_time(0)) / launches_per_prox
     in_solve = [t.fgp_ms / t.fgp_launches for t in ps_tr if t.fgp_launches > 0]
     fgp_in_solve_s = statistics.median(in_solve) * 1e-3 if in_solve else None
     hbm_peak, peak_kind = _peaks()
-    bytes_per_launch = FGP_BYTES_PER_PX * H * W
-    achieved = bytes_per_launch / fgp_s / 1e9
+    # algorithmic bytes per launch: 28 B per pixel per inner iteration
+    bytes_per_launch = FGP_BYTES_PER_PX * H * W * n_fgp / launches_per_prox
+    achieved = bytes_per_launch / fgp_launch_s / 1e9
 
     # end to end through the C ABI with pinned host buffers: H2D of b and x_0,
     # D2H of the result, every step
@@ -266,7 +271,9 @@ def run_gpu(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms_per_step = float(t.item())
     last = ps_tr[-1]
-    launches = sum(tr.iters_run * 3 + tr.prox_calls * (cfg.n_inner + 3) + 3 for tr in ps_tr)
+    # kernels per iteration: 2 step kernels + 1 reduction; per prox: 2 timestamps,
+    # the blocked inner launches and the finalisation; per solve: start stamp + final objective (2)
+    launches = sum(tr.iters_run * 3 + tr.prox_calls * 3 + tr.fgp_launches + 3 for tr in ps_tr)
     result = {
         "metric": METRIC,
         "value": ms_per_step / 1e3,
@@ -296,8 +303,10 @@ def run_gpu(args):
         "proxskip_by_p": per_p,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": None,
-                     "kernel": "fgp2d_kernel<float>", "bytes_per_launch": bytes_per_launch,
-                     "launch_us": fgp_s * 1e6, "peak_kind": peak_kind,
+                     "kernel": ("fgp2d_rb_kernel" if fgp_cfg[2] >= 100 else "fgp2d_tb_kernel")
+                               + f"<float> ({fgp_cfg[0]} inner iterations per launch, config {list(fgp_cfg)})",
+                     "bytes_per_launch": bytes_per_launch,
+                     "launch_us": fgp_launch_s * 1e6, "peak_kind": peak_kind,
                      "launch_us_in_solve": fgp_in_solve_s * 1e6 if fgp_in_solve_s else None},
         "e2e": {"value": statistics.mean(e2e_times), "unit": "s",
                 "h2d_bytes_per_step": 2 * H * W * 4, "d2h_bytes_per_step": H * W * 4},

@@ -131,7 +131,8 @@ typedef struct {
   double time_to_target_s;/* t_s[reached_iter], or -1                           */
   double solve_ms;        /* device time of the whole solve (CUDA events)       */
   double fgp_ms;          /* device time inside inner-iteration launches        */
-  long long fgp_launches; /* number of inner-iteration kernel launches          */
+  long long fgp_launches; /* inner-iteration kernel launches (a 2D launch runs up
+                             to 4 inner iterations)                              */
   long long fgp_pixel_iters; /* pixels x inner iterations processed by them    */
 } tvs_trace;
 
@@ -167,6 +168,15 @@ tvs_status tvs_objective(tvs_problem* prob, const float* x, double* out);
  * u = P(z + lambda div p0).  z and u may not alias. */
 tvs_status tv_prox(tvs_ctx* ctx, int ndim, const int dims[3], const float* z, float* u,
                    double lambda, int n_iter, tvs_dual_dtype dual, void* dual_state, int nonneg);
+
+/* Kernel configuration the context uses for the inner iterations of an image of
+ * this shape and dual type: out = {iterations per launch, columns per lane,
+ * rows per warp (+100 for the register-blocked kernel)}; {1, ., .} means one
+ * iteration per launch (3D).  The first query (or the first prox / solve) of a
+ * 2D shape times the candidates on the device and caches the fastest;
+ * TVS_FGP_CONFIG="tb,cpl,rpw" in the environment forces one.  Not in the paper:
+ * a performance knob only (every configuration computes identical iterates). */
+tvs_status tvs_fgp_config(tvs_ctx* ctx, int ndim, const int dims[3], tvs_dual_dtype dual, int out[3]);
 
 /* ---- allocation-free TV prox -------------------------------------------------- */
 /* The paper has no counterpart to this entry point.  It serves callers that may

@@ -19,6 +19,7 @@ from .api import (  # noqa: F401
     tv_prox_noalloc,
     tvs_coin,
     tvs_coin_schedule_device,
+    tvs_fgp_config,
     tvs_objective,
     tvs_op_apply,
 )

@@ -208,6 +208,18 @@ def tv_prox(ctx: Context, z, u, lam: float, n_iter: int, dual: str = "f32", dual
     return u
 
 
+def tvs_fgp_config(ctx: Context, shape, dual: str = "f32"):
+    """(iterations per launch, columns per lane, rows per warp [+100 register-blocked])
+    of the inner kernel the context uses for this image shape (autotuned once)."""
+    if len(shape) == 2:
+        dims = (C.c_int * 3)(shape[1], shape[0], 1)
+    else:
+        dims = (C.c_int * 3)(shape[2], shape[1], shape[0])
+    out = (C.c_int * 3)()
+    L.check(L.lib().tvs_fgp_config(ctx.handle, len(shape), dims, L.DUAL[dual], out))
+    return tuple(out)
+
+
 def tv_prox_noalloc(z, u, lam: float, n_iter: int, dual: str = "f32", dual_state=None,
                     nonneg: bool = False) -> int:
     """u = prox_{lam TV}(z) through the allocation-free entry point.

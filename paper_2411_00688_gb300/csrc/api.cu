@@ -79,7 +79,12 @@ struct tvs_ctx {
   cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
   cudaEvent_t ring[LAG] = {};
   size_t bytes = 0;
-  FgpConfig fgp;
+  FgpConfig fgp;          // forced configuration (TVS_FGP_CONFIG), or tb == 0 to autotune
+  struct Tuned {
+    int nx, ny, dtype;
+    FgpConfig cfg;
+  };
+  std::vector<Tuned> tuned;  // autotuner cache, one entry per 2D shape and dual type
 };
 
 struct tvs_problem {
@@ -186,18 +191,77 @@ tvs_status launch_fgp_sequence(const FgpConfig& cfg, const Dims& d, const float*
   return TVS_OK;
 }
 
+// Configuration forced through TVS_FGP_CONFIG ("tb,cpl,rpw"), else tb = 0
+// (autotune per shape).
 FgpConfig default_fgp_config() {
-  // 4 iterations per launch on 32 x 40 staged cells (24 x 32 outputs): the
-  // fastest variant measured on GB300 at 256^2 .. 8192^2.
   FgpConfig c;
-  c.tb = 4;
-  c.cpl = 1;
-  c.rpw = 5;
+  c.tb = 0;
   if (const char* e = getenv("TVS_FGP_CONFIG")) {
     FgpConfig t;
     if (sscanf(e, "%d,%d,%d", &t.tb, &t.cpl, &t.rpw) >= 1 && fgp_config_valid(t)) c = t;
   }
   return c;
+}
+
+// Autotuner for the blocked 2D inner kernel: the first use of a (shape, dual
+// type) in a context times each candidate tile shape / depth on the caller's z
+// (two launches of 4 iterations after one warm-up, CUDA events on the context's
+// stream), reading the dual in `home` and writing only `scratch0/1`, and keeps
+// the fastest.  Candidates: register-blocked 32x40 and 64x40 regions, the
+// shared-memory 32x40 region, register-blocked 32x64.
+tvs_status fgp_config_for(tvs_ctx* C, const Dims& d, int dtype, const float* z, void* home,
+                          void* scratch0, void* scratch1, FgpConfig* out) {
+  if (d.ndim != 2) {
+    *out = FgpConfig();
+    out->tb = 1;
+    return TVS_OK;
+  }
+  if (C->fgp.tb != 0) {
+    *out = C->fgp;
+    return TVS_OK;
+  }
+  for (const auto& t : C->tuned)
+    if (t.nx == d.nx && t.ny == d.ny && t.dtype == dtype) {
+      *out = t.cfg;
+      return TVS_OK;
+    }
+  const int cands[][3] = {{4, 1, 105}, {4, 2, 105}, {4, 1, 5}, {4, 1, 108}};
+  const float betas[4] = {0.f, 0.f, 0.2f, 0.4f};
+  cudaStream_t s = C->stream;
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  FgpConfig best;
+  float best_ms = 1e30f;
+  for (const auto& k : cands) {
+    FgpConfig c;
+    c.tb = k[0];
+    c.cpl = k[1];
+    c.rpw = k[2];
+    float ms = 0.f;
+    cudaError_t e = launch_fgp_block(c, d, z, home, home, scratch0, scratch1, 0.1f, 1.25f, betas, 4, dtype,
+                                     false, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    for (int r = 0; r < 2 && e == cudaSuccess; ++r)
+      e = launch_fgp_block(c, d, z, home, home, scratch0, scratch1, 0.1f, 1.25f, betas, 4, dtype, false, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return fail(TVS_ECUDA, "fgp autotune: %s", cudaGetErrorString(e));
+    }
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  C->tuned.push_back({d.nx, d.ny, dtype, best});
+  *out = best;
+  return TVS_OK;
 }
 
 tvs_status copy_in(float* dst, const float* src, size_t n, tvs_mem mem, cudaStream_t s) {
@@ -421,7 +485,8 @@ tvs_status zero_dual(tvs_problem* P, int dtype) {
 }
 
 tvs_status finish_solve(tvs_problem* P, int K, const LoopState& ls,
-                        const std::vector<unsigned char>& coins, int n_inner, tvs_trace* tr) {
+                        const std::vector<unsigned char>& coins, int n_inner, const FgpConfig& fc,
+                        tvs_trace* tr) {
   tvs_ctx* C = P->ctx;
   cudaStream_t s = C->stream;
   CUDA_TRY(cudaEventRecord(C->ev_stop, s));
@@ -464,7 +529,8 @@ tvs_status finish_solve(tvs_problem* P, int K, const LoopState& ls,
       tr->time_to_target_s = (double)(ts[flags[1]] - t0) * 1e-9;
     tr->solve_ms = solve_ms;
     tr->fgp_ms = fgp_ms;
-    tr->fgp_launches = (long long)nprox * n_inner;
+    const long long per_prox = (P->dims.ndim == 2 && fc.tb > 1) ? (n_inner + fc.tb - 1) / fc.tb : n_inner;
+    tr->fgp_launches = (long long)nprox * per_prox;
     tr->fgp_pixel_iters = (long long)nprox * n_inner * (long long)P->n;
     const int lim = tr->cap < iters ? tr->cap : iters;
     for (int k = 0; k < lim; ++k) {
@@ -531,6 +597,8 @@ tvs_status fb_solve(tvs_problem* P, const tvs_fb_params* prm, float* x_io, tvs_m
     }
     CUDA_TRY(cudaMemcpyAsync(P->beta_dev, bx.data(), sizeof(float) * bx.size(), cudaMemcpyHostToDevice, s));
   }
+  FgpConfig fcfg;
+  TVS_TRY(fgp_config_for(C, d, dtype, P->x[0], P->dual[0], P->dual[2], P->dual[3], &fcfg));
   const int na = step_parts_a(P), nb = step_parts_b(P);
   const float fgamma = (float)gamma;
   const float h_coef = (float)(p / gamma);
@@ -558,7 +626,7 @@ tvs_status fb_solve(tvs_problem* P, const tvs_fb_params* prm, float* x_io, tvs_m
         if (c == 1) {
           int fin = 0;
           CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 0, s));
-          if (use_prox) TVS_TRY(launch_fgp_sequence(C->fgp, d, P->z, P->dual, N, betas, lam, dtype, nonneg, s, &fin));
+          if (use_prox) TVS_TRY(launch_fgp_sequence(fcfg, d, P->z, P->dual, N, betas, lam, dtype, nonneg, s, &fin));
           CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 1, s));
           CUDA_TRY(launch_fgp_finalize(d, P->z, P->dual[fin], dtype, use_prox ? lam : 0.f, nonneg, xn,
                                        kind == FB_PROXSKIP ? P->h : nullptr, h_coef,
@@ -587,7 +655,7 @@ tvs_status fb_solve(tvs_problem* P, const tvs_fb_params* prm, float* x_io, tvs_m
                                   nullptr, s));
   }
   TVS_TRY(copy_out(x_io, xfin, P->n, mem, s));
-  return finish_solve(P, K, ls, coins, use_prox ? N : 0, tr);
+  return finish_solve(P, K, ls, coins, use_prox ? N : 0, fcfg, tr);
 }
 
 tvs_status pd_solve(tvs_problem* P, const tvs_pd_params* prm, float* x_io, float* y_io, tvs_mem mem,
@@ -623,6 +691,8 @@ tvs_status pd_solve(tvs_problem* P, const tvs_pd_params* prm, float* x_io, float
   TVS_TRY(zero_dual(P, dtype));
   if (skip) CUDA_TRY(cudaMemsetAsync(P->h, 0, P->n * sizeof(float), s));
   TVS_TRY(pd_forward(P, P->x[0], (float)tau, true, s));
+  FgpConfig fcfg;
+  TVS_TRY(fgp_config_for(C, d, dtype, P->x[0], P->dual[0], P->dual[2], P->dual[3], &fcfg));
   const int na = pd_parts_a(P), nb = pd_parts_b(P);
   const float fs = (float)sigma, ft = (float)tau;
   GraphSet G;
@@ -644,7 +714,7 @@ tvs_status pd_solve(tvs_problem* P, const tvs_pd_params* prm, float* x_io, float
         if (c == 1) {
           int fin = 0;
           CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 0, s));
-          if (use_prox) TVS_TRY(launch_fgp_sequence(C->fgp, d, P->z, P->dual, N, betas, lam, dtype, nonneg, s, &fin));
+          if (use_prox) TVS_TRY(launch_fgp_sequence(fcfg, d, P->z, P->dual, N, betas, lam, dtype, nonneg, s, &fin));
           CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 1, s));
           CUDA_TRY(launch_fgp_finalize(d, P->z, P->dual[fin], dtype, use_prox ? lam : 0.f, nonneg, xn,
                                        skip ? P->h : nullptr, (float)(p / sigma),
@@ -667,7 +737,7 @@ tvs_status pd_solve(tvs_problem* P, const tvs_pd_params* prm, float* x_io, float
   }
   TVS_TRY(copy_out(x_io, xfin, P->n, mem, s));
   TVS_TRY(copy_out(y_io, P->y, P->m, mem, s));
-  return finish_solve(P, K, ls, coins, use_prox ? N : 0, tr);
+  return finish_solve(P, K, ls, coins, use_prox ? N : 0, fcfg, tr);
 }
 
 }  // namespace
@@ -917,12 +987,51 @@ tvs_status tv_prox(tvs_ctx* C, int ndim, const int dims[3], const float* z, floa
   }
   const bool use = lambda > 0.0;
   int fin = 0;
-  if (use) TVS_TRY(launch_fgp_sequence(C->fgp, d, z, buf, n_iter, fgp_betas(n_iter), (float)lambda,
+  FgpConfig fcfg;
+  if (use && n_iter > 0) TVS_TRY(fgp_config_for(C, d, dual, z, buf[0], buf[2], buf[3], &fcfg));
+  if (use) TVS_TRY(launch_fgp_sequence(fcfg, d, z, buf, n_iter, fgp_betas(n_iter), (float)lambda,
                                        dual, nonneg != 0, s, &fin));
   CUDA_TRY(launch_fgp_finalize(d, z, buf[fin], dual, use ? (float)lambda : 0.f, nonneg != 0, u,
                                nullptr, 0.f, (fin != 0 && dual_state) ? dual_state : nullptr,
                                nullptr, nullptr, nullptr, nullptr, s));
   CUDA_TRY(cudaStreamSynchronize(s));
+  return TVS_OK;
+}
+
+tvs_status tvs_fgp_config(tvs_ctx* C, int ndim, const int dims[3], tvs_dual_dtype dual, int out[3]) {
+  if (!C || !dims || !out) return fail(TVS_EINVAL, "null argument");
+  if (ndim != 2 && ndim != 3) return fail(TVS_EINVAL, "ndim must be 2 or 3");
+  if (dims[0] < 1 || dims[1] < 1 || (ndim == 3 && dims[2] < 1)) return fail(TVS_EINVAL, "dims must be >= 1");
+  if (!valid_dual(dual)) return fail(TVS_EINVAL, "invalid dual dtype");
+  Dims d;
+  d.nx = dims[0];
+  d.ny = dims[1];
+  d.nz = ndim == 3 ? dims[2] : 1;
+  d.ndim = ndim;
+  FgpConfig c;
+  if (ndim == 2) {
+    // tune on a scratch image and scratch dual fields of this shape
+    const size_t n = d.n(), plane_bytes = dual_elem_bytes(dual) * 2 * n;
+    const size_t need = plane_bytes * 4 + n * sizeof(float);
+    cudaStream_t s = C->stream;
+    if (need > C->prox_scratch_bytes) {
+      dfree(C->prox_scratch);
+      C->bytes -= C->prox_scratch_bytes;
+      C->prox_scratch = nullptr;
+      C->prox_scratch_bytes = 0;
+      TVS_TRY(dalloc(C, nullptr, &C->prox_scratch, need));
+      C->prox_scratch_bytes = need;
+    }
+    char* sc = (char*)C->prox_scratch;
+    CUDA_TRY(cudaMemsetAsync(sc, 0, need, s));
+    TVS_TRY(fgp_config_for(C, d, dual, (const float*)(sc + 4 * plane_bytes), sc, sc + plane_bytes,
+                           sc + 2 * plane_bytes, &c));
+  } else {
+    c.tb = 1;
+  }
+  out[0] = c.tb;
+  out[1] = c.cpl;
+  out[2] = c.rpw;
   return TVS_OK;
 }
 

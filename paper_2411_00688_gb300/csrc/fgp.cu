@@ -10,6 +10,8 @@
 // Each CTA stages r over its tile plus a one-pixel halo in shared memory, forms
 // u over the tile plus the row/column after it, then writes p_{k+1}: the whole
 // iteration is one pass over z, p_k, p_{k-1} and one write of p_{k+1}.
+#include <cstdlib>
+
 #include "common.cuh"
 #include "kernels.hpp"
 
@@ -312,6 +314,329 @@ fgp2d_tb_kernel(const float* __restrict__ z, const T* __restrict__ pc, const T* 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Register-blocked temporally blocked 2D variant.  Same staged region and the
+// same per-iteration arithmetic as fgp2d_tb_kernel, but every cell lives in the
+// registers of one thread for the whole launch: warp w owns RPW consecutive
+// region rows, lane l owns CPL adjacent columns.  Horizontal neighbours come
+// from warp shuffles, vertical neighbours from the thread's own registers; only
+// the row shared by two warps goes through shared memory (one row of r before
+// phase 1, one row of u before phase 2).  Cells are updated unconditionally:
+// values in the shrinking halo are stale but finite and never reach a cell of
+// the valid region (masks keep out-of-image cells out of in-image stencils).
+template <typename T, bool NONNEG, int TB, int CPL, int RPW>
+__global__ void __launch_bounds__(256, (RPW * CPL > 10) ? 1 : 2)
+fgp2d_rb_kernel(const float* __restrict__ z, const T* __restrict__ pc, const T* __restrict__ pp,
+                T* __restrict__ pn, T* __restrict__ pnp, int H, int W, float lam, float inv_step,
+                TBBetas betas, int iters) {
+  constexpr int NW = 8;
+  constexpr int RW = 32 * CPL, RH = NW * RPW;
+  constexpr int TW = RW - 2 * TB, TH = RH - 2 * TB;
+  __shared__ float edge_ry[NW][RW];  // bottom row of r_y of each warp's block
+  __shared__ float edge_u[NW][RW];   // top row of u of each warp's block
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gi0 = blockIdx.y * TH - TB + warp * RPW;   // global row of the thread's first cell
+  const int gj0 = blockIdx.x * TW - TB + lane * CPL;   // global column of its first cell
+  const size_t n = (size_t)H * W;
+
+  float Z[RPW][CPL], Ry[RPW][CPL], Rx[RPW][CPL], Py[RPW][CPL], Px[RPW][CPL], U[RPW][CPL];
+  // boundary masks: row masks per row, column masks per column (Neumann)
+  bool row_in[RPW], row_dn[RPW], row_up[RPW], col_in[CPL], col_rt[CPL], col_lf[CPL];
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) {
+    const int gi = gi0 + r;
+    row_in[r] = gi >= 0 && gi < H;
+    row_dn[r] = gi < H - 1;   // has a row below (D_y defined, div uses p_y here)
+    row_up[r] = gi > 0;       // has a row above (div uses p_y of the row above)
+  }
+#pragma unroll
+  for (int q = 0; q < CPL; ++q) {
+    const int gj = gj0 + q;
+    col_in[q] = gj >= 0 && gj < W;
+    col_rt[q] = gj < W - 1;
+    col_lf[q] = gj > 0;
+  }
+  const float b0 = betas.b[0];
+#pragma unroll
+  for (int r = 0; r < RPW; ++r)
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+      float zz = 0.f, cy = 0.f, cx = 0.f, ry = 0.f, rx = 0.f;
+      if (row_in[r] && col_in[q]) {
+        const size_t o = (size_t)(gi0 + r) * W + (gj0 + q);
+        zz = __ldg(z + o);
+        cy = Elem<T>::ld(pc + o);
+        cx = Elem<T>::ld(pc + n + o);
+        if (b0 != 0.f) {
+          ry = cy + b0 * (cy - Elem<T>::ld(pp + o));
+          rx = cx + b0 * (cx - Elem<T>::ld(pp + n + o));
+        } else {
+          ry = cy;
+          rx = cx;
+        }
+      }
+      Z[r][q] = zz;
+      Py[r][q] = cy;
+      Px[r][q] = cx;
+      Ry[r][q] = ry;
+      Rx[r][q] = rx;
+    }
+#pragma unroll
+  for (int q = 0; q < CPL; ++q) edge_ry[warp][lane * CPL + q] = Ry[RPW - 1][q];
+  __syncthreads();
+
+  for (int t = 1; t <= iters; ++t) {
+    // phase 1: U = P_X(Z + lam div R)
+    float ry_above[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) ry_above[q] = warp > 0 ? edge_ry[warp - 1][lane * CPL + q] : 0.f;
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+      const float rx_left = __shfl_up_sync(0xffffffffu, Rx[r][CPL - 1], 1);
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) {
+        const float up = r > 0 ? Ry[r - 1][q] : ry_above[q];
+        const float lf = q > 0 ? Rx[r][q - 1] : rx_left;
+        float dv = 0.f;
+        if (row_dn[r]) dv += Ry[r][q];
+        if (row_up[r]) dv -= up;
+        if (col_rt[q]) dv += Rx[r][q];
+        if (col_lf[q]) dv -= lf;
+        float u = Z[r][q] + lam * dv;
+        if (NONNEG) u = fmaxf(u, 0.f);
+        U[r][q] = (row_in[r] && col_in[q]) ? u : 0.f;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) edge_u[warp][lane * CPL + q] = U[0][q];
+    __syncthreads();
+    // phase 2: p_new = P_B(R + inv_step D U); R = next momentum point (or p_prev); P = p_new
+    const bool last = (t == iters);
+    const float bn = last ? 0.f : betas.b[t];
+    float u_below[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) u_below[q] = warp < NW - 1 ? edge_u[warp + 1][lane * CPL + q] : 0.f;
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+      const float u_right = __shfl_down_sync(0xffffffffu, U[r][0], 1);
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) {
+        const float uc = U[r][q];
+        const float dn = r < RPW - 1 ? U[r + 1][q] : u_below[q];
+        const float rt = q < CPL - 1 ? U[r][q + 1] : u_right;
+        const float gy = row_dn[r] ? dn - uc : 0.f;
+        const float gx = col_rt[q] ? rt - uc : 0.f;
+        const float qy = Ry[r][q] + inv_step * gy;
+        const float qx = Rx[r][q] + inv_step * gx;
+        const float nrm2 = qy * qy + qx * qx;
+        const float sc = nrm2 > 1.f ? rsqrtf(nrm2) : 1.f;
+        const float ny = Elem<T>::round(qy * sc), nx = Elem<T>::round(qx * sc);
+        const float oy = Py[r][q], ox = Px[r][q];
+        if (last) {
+          Ry[r][q] = oy;
+          Rx[r][q] = ox;
+        } else {
+          Ry[r][q] = ny + bn * (ny - oy);
+          Rx[r][q] = nx + bn * (nx - ox);
+        }
+        Py[r][q] = ny;
+        Px[r][q] = nx;
+      }
+    }
+    if (!last) {
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) edge_ry[warp][lane * CPL + q] = Ry[RPW - 1][q];
+    }
+    __syncthreads();
+  }
+  // tile interior: P = p_{k+iters}, R = p_{k+iters-1}
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) {
+    const int a = warp * RPW + r;
+    if (a < TB || a >= TB + TH || !row_in[r]) continue;
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+      const int c = lane * CPL + q;
+      if (c < TB || c >= TB + TW || !col_in[q]) continue;
+      const size_t o = (size_t)(gi0 + r) * W + (gj0 + q);
+      Elem<T>::st(pn + o, Py[r][q]);
+      Elem<T>::st(pn + n + o, Px[r][q]);
+      Elem<T>::st(pnp + o, Ry[r][q]);
+      Elem<T>::st(pnp + n + o, Rx[r][q]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 3D, one inner iteration per launch, marching through z ("2.5D").  A CTA owns an
+// x-y region of 32*CPL x 8*RPW cells (warp w: RPW consecutive rows, lane: CPL
+// adjacent columns) and a chunk of ZC planes.  Per plane k it loads r(k+1)
+// (from z, p_k, p_{k-1}), forms u(k+1), then writes p_{k+1} at plane k from
+// r(k), u(k), u(k+1): each voxel is read once (z, p_k, p_{k-1}) and written once,
+// plus one warm-up plane per chunk and a one-cell x-y halo.  x neighbours come
+// from warp shuffles, y neighbours from registers or, across warps, from a
+// double-buffered shared row (one barrier per plane).
+template <typename T, bool NONNEG, int CPL, int RPW, int ZC>
+__global__ void __launch_bounds__(256)
+fgp3d_zm_kernel(const float* __restrict__ z, const T* __restrict__ pc, const T* __restrict__ pp,
+                T* __restrict__ pn, int D, int H, int W, float lam, float inv_step, float beta) {
+  constexpr int NW = 8;
+  constexpr int RW = 32 * CPL, RH = NW * RPW;
+  constexpr int TW = RW - 2, TH = RH - 2;
+  __shared__ float sh_ry[2][NW][RW];   // bottom row of r_y(k+1) of each warp block
+  __shared__ float sh_u[2][NW][RW];    // top row of u(k+1) of each warp block
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gi0 = blockIdx.y * TH - 1 + warp * RPW;
+  const int gj0 = blockIdx.x * TW - 1 + lane * CPL;
+  const int k0 = blockIdx.z * ZC;
+  const int k1 = min(k0 + ZC, D);
+  const size_t HW = (size_t)H * W, n = (size_t)D * HW;
+  bool row_in[RPW], row_dn[RPW], row_up[RPW], col_in[CPL], col_rt[CPL], col_lf[CPL];
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) {
+    const int gi = gi0 + r;
+    row_in[r] = gi >= 0 && gi < H;
+    row_dn[r] = gi < H - 1;
+    row_up[r] = gi > 0;
+  }
+#pragma unroll
+  for (int q = 0; q < CPL; ++q) {
+    const int gj = gj0 + q;
+    col_in[q] = gj >= 0 && gj < W;
+    col_rt[q] = gj < W - 1;
+    col_lf[q] = gj > 0;
+  }
+  // r(k) (three components), r_z(k-1), u(k) of the thread's cells
+  float Rz[RPW][CPL], Ry[RPW][CPL], Rx[RPW][CPL], Rzm[RPW][CPL], Uk[RPW][CPL];
+
+  auto load_r = [&](int k, float (&rz)[RPW][CPL], float (&ry)[RPW][CPL], float (&rx)[RPW][CPL],
+                    float (&zz)[RPW][CPL], bool need_all) {
+#pragma unroll
+    for (int r = 0; r < RPW; ++r)
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, zv = 0.f;
+        if (k >= 0 && k < D && row_in[r] && col_in[q]) {
+          const size_t o = (size_t)k * HW + (size_t)(gi0 + r) * W + (gj0 + q);
+          const float c0 = Elem<T>::ld(pc + o);
+          a0 = beta != 0.f ? c0 + beta * (c0 - Elem<T>::ld(pp + o)) : c0;
+          if (need_all) {
+            const float c1 = Elem<T>::ld(pc + n + o), c2 = Elem<T>::ld(pc + 2 * n + o);
+            if (beta != 0.f) {
+              a1 = c1 + beta * (c1 - Elem<T>::ld(pp + n + o));
+              a2 = c2 + beta * (c2 - Elem<T>::ld(pp + 2 * n + o));
+            } else {
+              a1 = c1;
+              a2 = c2;
+            }
+            zv = __ldg(z + o);
+          }
+        }
+        rz[r][q] = a0;
+        ry[r][q] = a1;
+        rx[r][q] = a2;
+        zz[r][q] = zv;
+      }
+  };
+  // u at plane k from r(k) (Rz/Ry/Rx), r_z(k-1) and the staged r_y row above.
+  auto form_u = [&](int k, const float (&rz)[RPW][CPL], const float (&ry)[RPW][CPL],
+                    const float (&rx)[RPW][CPL], const float (&rzm)[RPW][CPL],
+                    const float (&zz)[RPW][CPL], const float* ry_above, float (&u)[RPW][CPL]) {
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+      const float rx_left = __shfl_up_sync(0xffffffffu, rx[r][CPL - 1], 1);
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) {
+        const float up = r > 0 ? ry[r - 1][q] : ry_above[q];
+        const float lf = q > 0 ? rx[r][q - 1] : rx_left;
+        float dv = 0.f;
+        if (k < D - 1) dv += rz[r][q];
+        if (k > 0) dv -= rzm[r][q];
+        if (row_dn[r]) dv += ry[r][q];
+        if (row_up[r]) dv -= up;
+        if (col_rt[q]) dv += rx[r][q];
+        if (col_lf[q]) dv -= lf;
+        float v = zz[r][q] + lam * dv;
+        if (NONNEG) v = fmaxf(v, 0.f);
+        u[r][q] = (k < D && row_in[r] && col_in[q]) ? v : 0.f;
+      }
+    }
+  };
+
+  float Zt[RPW][CPL], Dy[RPW][CPL], Dx[RPW][CPL];
+  // warm-up: r_z(k0-1) and r(k0), then u(k0)
+  load_r(k0 - 1, Rzm, Dy, Dx, Zt, false);
+  load_r(k0, Rz, Ry, Rx, Zt, true);
+  int buf = 0;
+#pragma unroll
+  for (int q = 0; q < CPL; ++q) sh_ry[buf][warp][lane * CPL + q] = Ry[RPW - 1][q];
+  __syncthreads();
+  {
+    float above[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) above[q] = warp > 0 ? sh_ry[buf][warp - 1][lane * CPL + q] : 0.f;
+    form_u(k0, Rz, Ry, Rx, Rzm, Zt, above, Uk);
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) sh_u[buf][warp][lane * CPL + q] = Uk[0][q];
+  }
+  for (int k = k0; k < k1; ++k) {
+    // next plane: r(k+1), u(k+1)
+    float Rz1[RPW][CPL], Ry1[RPW][CPL], Rx1[RPW][CPL], U1[RPW][CPL];
+    load_r(k + 1, Rz1, Ry1, Rx1, Zt, true);
+    const int nb = buf ^ 1;
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) sh_ry[nb][warp][lane * CPL + q] = Ry1[RPW - 1][q];
+    __syncthreads();
+    float above[CPL], below_u[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+      above[q] = warp > 0 ? sh_ry[nb][warp - 1][lane * CPL + q] : 0.f;
+      below_u[q] = warp < NW - 1 ? sh_u[buf][warp + 1][lane * CPL + q] : 0.f;
+    }
+    form_u(k + 1, Rz1, Ry1, Rx1, Rz, Zt, above, U1);
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) sh_u[nb][warp][lane * CPL + q] = U1[0][q];
+    // p_{k+1} at plane k
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+      const float u_right = __shfl_down_sync(0xffffffffu, Uk[r][0], 1);
+      const int a = warp * RPW + r;
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) {
+        const float uc = Uk[r][q];
+        const float dn = r < RPW - 1 ? Uk[r + 1][q] : below_u[q];
+        const float rt = q < CPL - 1 ? Uk[r][q + 1] : u_right;
+        const float g0 = k < D - 1 ? U1[r][q] - uc : 0.f;
+        const float g1 = row_dn[r] ? dn - uc : 0.f;
+        const float g2 = col_rt[q] ? rt - uc : 0.f;
+        const float q0 = Rz[r][q] + inv_step * g0;
+        const float q1 = Ry[r][q] + inv_step * g1;
+        const float q2 = Rx[r][q] + inv_step * g2;
+        const float nrm2 = q0 * q0 + q1 * q1 + q2 * q2;
+        const float sc = nrm2 > 1.f ? rsqrtf(nrm2) : 1.f;
+        const int c = lane * CPL + q;
+        if (a >= 1 && a <= TH && c >= 1 && c <= TW && row_in[r] && col_in[q]) {
+          const size_t o = (size_t)k * HW + (size_t)(gi0 + r) * W + (gj0 + q);
+          Elem<T>::st(pn + o, q0 * sc);
+          Elem<T>::st(pn + n + o, q1 * sc);
+          Elem<T>::st(pn + 2 * n + o, q2 * sc);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RPW; ++r)
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) {
+        Rzm[r][q] = Rz[r][q];
+        Rz[r][q] = Rz1[r][q];
+        Ry[r][q] = Ry1[r][q];
+        Rx[r][q] = Rx1[r][q];
+        Uk[r][q] = U1[r][q];
+      }
+    buf = nb;
+  }
+}
+
 // Pointwise finalisation; div p at a pixel needs p at the pixel and at the
 // previous pixel along each axis.
 template <typename T, bool NONNEG>
@@ -356,6 +681,15 @@ __global__ void fgp_finalize_kernel(const float* __restrict__ z, const T* __rest
   }
 }
 
+// The z-marching 3D kernel is the default; TVS_FGP3D=tile selects the tiled one.
+bool fgp3d_use_zmarch() {
+  static const bool zm = [] {
+    const char* e = getenv("TVS_FGP3D");
+    return !(e && e[0] == 't');
+  }();
+  return zm;
+}
+
 template <typename T, bool NN>
 cudaError_t fgp_iter_t(const Dims& d, const float* z, const void* pc, const void* pp, void* pn,
                        float lam, float inv_step, float beta, cudaStream_t s) {
@@ -363,6 +697,15 @@ cudaError_t fgp_iter_t(const Dims& d, const float* z, const void* pc, const void
     dim3 grid((d.nx + TX2 - 1) / TX2, (d.ny + TY2 - 1) / TY2);
     fgp2d_kernel<T, NN><<<grid, NT2, 0, s>>>(z, (const T*)pc, (const T*)pp, (T*)pn, d.ny, d.nx, lam,
                                              inv_step, beta);
+  } else if (fgp3d_use_zmarch() &&
+             (long long)((d.nx + 29) / 30) * ((d.ny + 29) / 30) * ((d.nz + 31) / 32) >= 4 * 152) {
+    // z-marching needs enough (x-y tile, z chunk) pairs to fill the GPU; small
+    // volumes use the tiled kernel
+    constexpr int CPL = 1, RPW = 4, ZC = 32;
+    constexpr int TW = 32 * CPL - 2, TH = 8 * RPW - 2;
+    dim3 grid((d.nx + TW - 1) / TW, (d.ny + TH - 1) / TH, (d.nz + ZC - 1) / ZC);
+    fgp3d_zm_kernel<T, NN, CPL, RPW, ZC><<<grid, 256, 0, s>>>(z, (const T*)pc, (const T*)pp, (T*)pn, d.nz,
+                                                               d.ny, d.nx, lam, inv_step, beta);
   } else {
     dim3 grid((d.nx + TX3 - 1) / TX3, (d.ny + TY3 - 1) / TY3, (d.nz + TZ3 - 1) / TZ3);
     fgp3d_kernel<T, NN><<<grid, NT3, 0, s>>>(z, (const T*)pc, (const T*)pp, (T*)pn, d.nz, d.ny,
@@ -388,6 +731,19 @@ cudaError_t fgp_tb_t(const Dims& d, const float* z, const void* pc, const void* 
   return cudaGetLastError();
 }
 
+template <typename T, bool NN, int TB, int CPL, int RPW>
+cudaError_t fgp_rb_t(const Dims& d, const float* z, const void* pc, const void* pp, void* pn, void* pnp,
+                     float lam, float inv_step, const float* betas, int iters, cudaStream_t s) {
+  constexpr int RW = 32 * CPL, RH = 8 * RPW, TW = RW - 2 * TB, TH = RH - 2 * TB;
+  if (iters < 0) return cudaSuccess;  // preparation call: static shared memory only
+  TBBetas b{};
+  for (int i = 0; i < iters && i < 8; ++i) b.b[i] = betas[i];
+  dim3 grid((d.nx + TW - 1) / TW, (d.ny + TH - 1) / TH);
+  fgp2d_rb_kernel<T, NN, TB, CPL, RPW><<<grid, 256, 0, s>>>(
+      z, (const T*)pc, (const T*)pp, (T*)pn, (T*)pnp, d.ny, d.nx, lam, inv_step, b, iters);
+  return cudaGetLastError();
+}
+
 template <typename T, bool NN>
 cudaError_t fgp_tb_dispatch(const FgpConfig& c, const Dims& d, const float* z, const void* pc,
                             const void* pp, void* pn, void* pnp, float lam, float inv_step,
@@ -403,6 +759,17 @@ cudaError_t fgp_tb_dispatch(const FgpConfig& c, const Dims& d, const float* z, c
   TVS_TB_CASE(6, 2, 6)
   TVS_TB_CASE(8, 2, 6)
 #undef TVS_TB_CASE
+#define TVS_RB_CASE(TB_, CPL_, RPW_)                                                          \
+  if (c.tb == TB_ && c.cpl == CPL_ && c.rpw == RPW_ + 100)                                   \
+    return fgp_rb_t<T, NN, TB_, CPL_, RPW_>(d, z, pc, pp, pn, pnp, lam, inv_step, betas, iters, s);
+  TVS_RB_CASE(2, 2, 4)
+  TVS_RB_CASE(4, 1, 5)
+  TVS_RB_CASE(4, 2, 5)
+  TVS_RB_CASE(4, 2, 8)
+  TVS_RB_CASE(4, 1, 8)
+  TVS_RB_CASE(6, 2, 8)
+  TVS_RB_CASE(3, 2, 6)
+#undef TVS_RB_CASE
   return cudaErrorInvalidValue;
 }
 
@@ -440,7 +807,9 @@ cudaError_t launch_fgp_iter(const Dims& d, const float* z, const void* pc, const
 
 bool fgp_config_valid(const FgpConfig& c) {
   if (c.tb <= 1) return true;
-  const int ok[][3] = {{2, 2, 4}, {3, 2, 4}, {4, 2, 4}, {4, 2, 5}, {4, 1, 5}, {6, 2, 6}, {8, 2, 6}};
+  const int ok[][3] = {{2, 2, 4},   {3, 2, 4},   {4, 2, 4},   {4, 2, 5},   {4, 1, 5},   {6, 2, 6},
+                       {8, 2, 6},   {2, 2, 104}, {4, 1, 105}, {4, 2, 105}, {4, 2, 108}, {4, 1, 108},
+                       {6, 2, 108}, {3, 2, 106}};
   for (const auto& k : ok)
     if (k[0] == c.tb && k[1] == c.cpl && k[2] == c.rpw) return true;
   return false;

@@ -26,6 +26,7 @@ cudaError_t launch_fgp_iter(const Dims& d, const float* z, const void* pc, const
 // `iters` <= tb iterations from (pc = p_k, pp = p_{k-1}) and writes
 // pn = p_{k+iters}, pnp = p_{k+iters-1}; betas[i] is the momentum coefficient of
 // its i-th iteration.  pn/pnp may not alias pc/pp.
+// rpw >= 100 selects the register-blocked variant with rpw - 100 rows per warp.
 struct FgpConfig {
   int tb = 1, cpl = 2, rpw = 5;
 };
