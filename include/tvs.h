@@ -219,6 +219,20 @@ tvs_status pdhg_solve(tvs_problem* prob, const tvs_pd_params* prm, float* x_inou
 tvs_status pdhgskip_solve(tvs_problem* prob, const tvs_pd_params* prm, float* x_inout,
                           float* y_inout, tvs_mem mem, tvs_trace* trace);
 
+/* ---- many independent problems at once -------------------------------------- */
+/* ProxSkip on n independent 2D problems (identity or blur operators; any sizes),
+ * each with its own alpha (from its problem), gamma, p, seed, f_star and target
+ * (prm[i]); max_iter, n_inner and the dual type must agree.  All problems advance
+ * in lockstep through shared launches (one CUDA graph per outer iteration covers
+ * every problem); problem i follows exactly the iteration proxskip_solve would
+ * run on it (same coins, same arithmetic) and stops at the first x_k whose
+ * objective meets its target, or after max_iter iterations.  x_inout[i] and
+ * traces[i] (may be NULL) as for proxskip_solve; problems must belong to ctx and
+ * be distinct.  Not in the paper: a batching mode for many small solves. */
+tvs_status proxskip_solve_batch(tvs_ctx* ctx, int n, tvs_problem* const* probs,
+                                const tvs_fb_params* prm, float* const* x_inout, tvs_mem mem,
+                                tvs_trace* traces);
+
 /* ---- the coin (Algorithms 4 and 6) ----------------------------------------- */
 /* theta_k = [(w >> 11) < p 2^53], w the first word of Philox4x64-10 with counter
  * (k, 0, 0, 0) and key (seed, 0).  Returns 0/1, or -1 if p is not in (0, 1]. */

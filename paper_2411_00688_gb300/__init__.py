@@ -15,6 +15,7 @@ from .api import (  # noqa: F401
     pdhgskip_solve,
     pgd_solve,
     proxskip_solve,
+    proxskip_solve_batch,
     tv_prox,
     tv_prox_noalloc,
     tvs_coin,

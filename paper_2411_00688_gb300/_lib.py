@@ -80,6 +80,8 @@ SIGNATURES = [
                              C.POINTER(Trace)]),
     ("pdhgskip_solve", C.c_int, [C.c_void_p, C.POINTER(PDParams), C.c_void_p, C.c_void_p, C.c_int,
                                  C.POINTER(Trace)]),
+    ("proxskip_solve_batch", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(FBParams),
+                                       C.POINTER(C.c_void_p), C.c_int, C.POINTER(Trace)]),
     ("tvs_coin", C.c_int, [C.c_uint64, C.c_double, C.c_int64]),
     ("tvs_coin_schedule_device", C.c_int, [C.c_void_p, C.c_uint64, C.c_double, C.c_int64, C.c_int,
                                            C.c_void_p]),

@@ -272,6 +272,46 @@ def proxskip_solve(prob, x, gamma, p, seed, max_iter, n_inner, **kw):
     return _fb("proxskip_solve", prob, x, gamma, max_iter, n_inner, p=p, seed=seed, **kw)
 
 
+def proxskip_solve_batch(ctx: Context, probs, xs, gammas, ps, seeds, max_iter, n_inner, dual="f32",
+                         f_stars=None, targets=None):
+    """ProxSkip on many independent problems in shared launches (proxskip_solve_batch).
+
+    probs: list of Problem; xs: matching list of CUDA tensors (x_0 in, result out);
+    gammas, ps, seeds (and optionally f_stars, targets): per-problem lists.
+    Returns (xs, [SolveTrace])."""
+    n = len(probs)
+    prm = (L.FBParams * n)()
+    for i in range(n):
+        prm[i] = L.FBParams(gamma=float(gammas[i]), p=float(ps[i]), seed=int(seeds[i]) & ((1 << 64) - 1),
+                            max_iter=int(max_iter), n_inner=int(n_inner), dual=L.DUAL[dual],
+                            f_star=float(f_stars[i]) if f_stars is not None else 0.0,
+                            target_rel_gap=float(targets[i]) if targets is not None else 0.0,
+                            objective_every=1)
+    mems = set()
+    ptrs = (C.c_void_p * n)()
+    keep = []
+    for i, x in enumerate(xs):
+        ptr, mem, k = _arr(x, f"x[{i}]")
+        ptrs[i] = ptr
+        mems.add(mem)
+        keep.append(k)
+    if len(mems) != 1:
+        raise ValueError("all x must live in the same memory")
+    mem = mems.pop()
+    if mem == L.MEM_DEVICE:
+        _sync_torch()
+    handles = (C.c_void_p * n)(*[p.handle.value for p in probs])
+    cap = max(int(max_iter), 1)
+    tr = (L.Trace * n)()
+    keep_tr = []
+    for i in range(n):
+        t, obj, coins, ts = _new_trace(cap)
+        tr[i] = t
+        keep_tr.append((obj, coins, ts))
+    L.check(L.lib().proxskip_solve_batch(ctx.handle, n, handles, prm, ptrs, mem, tr))
+    return xs, [_finish_trace(tr[i], *keep_tr[i]) for i in range(n)]
+
+
 def _pd(fn_name, prob, x, y, sigma, tau, max_iter, n_inner, p=1.0, seed=0, dual="f32", f_star=0.0,
         target=0.0, every=1):
     prm = L.PDParams(sigma=float(sigma), tau=float(tau), p=float(p), seed=int(seed) & ((1 << 64) - 1),

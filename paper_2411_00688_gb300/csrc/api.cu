@@ -742,6 +742,237 @@ tvs_status pd_solve(tvs_problem* P, const tvs_pd_params* prm, float* x_io, float
 
 }  // namespace
 
+
+// ---------------------------------------------------------------- batched ProxSkip
+namespace {
+
+struct BatchScratch {
+  std::vector<void*> bufs;
+  int* done_host = nullptr;
+  ~BatchScratch() {
+    for (void* b : bufs) cudaFree(b);
+    if (done_host) cudaFreeHost(done_host);
+  }
+  template <typename T>
+  tvs_status upload(const std::vector<T>& v, T** out, cudaStream_t s) {
+    *out = nullptr;
+    if (v.empty()) return TVS_OK;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, v.size() * sizeof(T));
+    if (e != cudaSuccess) return fail(TVS_ENOMEM, "batch scratch: %s", cudaGetErrorString(e));
+    bufs.push_back(p);
+    e = cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail(TVS_ECUDA, "batch upload: %s", cudaGetErrorString(e));
+    *out = (T*)p;
+    return TVS_OK;
+  }
+  template <typename T>
+  tvs_status zeros(size_t count, T** out, cudaStream_t s) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T) + 8);
+    if (e != cudaSuccess) return fail(TVS_ENOMEM, "batch scratch: %s", cudaGetErrorString(e));
+    bufs.push_back(p);
+    e = cudaMemsetAsync(p, 0, count * sizeof(T) + 8, s);
+    if (e != cudaSuccess) return fail(TVS_ECUDA, "batch memset: %s", cudaGetErrorString(e));
+    *out = (T*)p;
+    return TVS_OK;
+  }
+};
+
+}  // namespace
+
+extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const* probs,
+                                           const tvs_fb_params* prm, float* const* x_io, tvs_mem mem,
+                                           tvs_trace* traces) {
+  if (!C || n < 1 || !probs || !prm || !x_io) return fail(TVS_EINVAL, "null argument or n < 1");
+  if (mem != TVS_MEM_DEVICE && mem != TVS_MEM_HOST) return fail(TVS_EINVAL, "invalid mem kind");
+  const int K = prm[0].max_iter, N = prm[0].n_inner, dtype = prm[0].dual;
+  for (int i = 0; i < n; ++i) {
+    tvs_problem* P = probs[i];
+    if (!P || P->ctx != C) return fail(TVS_EINVAL, "problem %d is null or from another context", i);
+    if (!x_io[i]) return fail(TVS_EINVAL, "x_inout[%d] is null", i);
+    if (P->dims.ndim != 2 || P->desc.op.kind == TVS_OP_PARALLEL_BEAM)
+      return fail(TVS_EUNSUPPORTED, "batched solves take 2D identity or blur problems (problem %d)", i);
+    TVS_TRY(check_common(P, prm[i].max_iter, prm[i].n_inner, prm[i].dual, prm[i].f_star,
+                         prm[i].target_rel_gap, prm[i].objective_every, x_io[i]));
+    if (prm[i].max_iter != K || prm[i].n_inner != N || prm[i].dual != dtype)
+      return fail(TVS_EINVAL, "max_iter, n_inner and dual must agree across the batch");
+    if (!(prm[i].gamma > 0) || !is_fin(prm[i].gamma)) return fail(TVS_EINVAL, "gamma must be > 0");
+    if (!(prm[i].p > 0.0 && prm[i].p <= 1.0)) return fail(TVS_EINVAL, "p must lie in (0, 1]");
+    for (int j = 0; j < i; ++j)
+      if (probs[j] == P) return fail(TVS_EINVAL, "problem %d appears twice", i);
+  }
+  cudaStream_t s = C->stream;
+  BatchScratch S;
+  // per-problem state, descriptors and work lists
+  std::vector<BatchProb> desc(n);
+  std::vector<int4> blur_tiles, fgp_tiles;
+  std::vector<int2> ident_chunks, all_chunks;
+  const int chunk = batch_chunk(), ftw = batch_fgp_tile_w(), fth = batch_fgp_tile_h();
+  for (int i = 0; i < n; ++i) {
+    tvs_problem* P = probs[i];
+    TVS_TRY(ensure_trace(P, K));
+    TVS_TRY(copy_in(P->x[0], x_io[i], P->n, mem, s));
+    CUDA_TRY(cudaMemsetAsync(P->dual[0], 0, dual_elem_bytes(dtype) * 2 * P->n, s));
+    CUDA_TRY(cudaMemsetAsync(P->h, 0, P->n * sizeof(float), s));
+    CUDA_TRY(cudaMemsetAsync(P->obj_dev, 0xff, sizeof(double) * (K + 1), s));
+    const int H = P->dims.ny, W = P->dims.nx;
+    const double gamma = prm[i].gamma, p = prm[i].p, alpha = P->desc.alpha;
+    BatchProb& D = desc[i];
+    memset(&D, 0, sizeof(D));
+    D.H = H;
+    D.W = W;
+    D.nonneg = P->desc.nonneg != 0;
+    D.b = P->b;
+    D.x0 = P->x[0];
+    D.x1 = P->x[1];
+    D.z = P->z;
+    D.h = P->h;
+    D.r = P->r;
+    D.dual0 = P->dual[0];
+    D.dual1 = P->dual[1];
+    D.dual2 = P->dual[2];
+    D.dual3 = P->dual[3];
+    const double lam = gamma / p * alpha;
+    D.lam = (float)lam;
+    D.inv_step = lam > 0 ? (float)(1.0 / (8.0 * lam)) : 0.f;
+    D.gamma = (float)gamma;
+    D.ch_skip = (float)gamma;
+    D.ch_prox = (float)(gamma - gamma / p);
+    D.h_coef = (float)(p / gamma);
+    D.alpha = alpha;
+    D.f_star = prm[i].f_star;
+    D.target = prm[i].target_rel_gap;
+    D.bw = P->bw;
+    D.obj = P->obj_dev;
+    D.ts = P->ts_dev;
+    const size_t npx = P->n;
+    const int nchunks = (int)((npx + chunk - 1) / chunk);
+    if (P->desc.op.kind == TVS_OP_GAUSS_BLUR) {
+      D.part_off = (int)blur_tiles.size();
+      const int tx = (W + 31) / 32, ty = (H + 15) / 16;
+      for (int y = 0; y < ty; ++y)
+        for (int x = 0; x < tx; ++x) blur_tiles.push_back(make_int4(i, x, y, 0));
+      D.part_n = tx * ty;
+    } else {
+      D.part_off = -1 - (int)ident_chunks.size();  // fixed up below (after the blur tiles)
+      for (int c = 0; c < nchunks; ++c) ident_chunks.push_back(make_int2(i, c));
+      D.part_n = nchunks;
+    }
+    for (int c = 0; c < nchunks; ++c) all_chunks.push_back(make_int2(i, c));
+    const int fx = (W + ftw - 1) / ftw, fy = (H + fth - 1) / fth;
+    for (int y = 0; y < fy; ++y)
+      for (int x = 0; x < fx; ++x) fgp_tiles.push_back(make_int4(i, x, y, 0));
+  }
+  const int n_blur = (int)blur_tiles.size();
+  for (auto& D : desc)
+    if (D.part_off < 0) D.part_off = n_blur + (-1 - D.part_off);
+  std::vector<unsigned char> coins((size_t)K * n);
+  for (int k = 0; k < K; ++k)
+    for (int i = 0; i < n; ++i) coins[(size_t)k * n + i] = (unsigned char)tvs_coin(prm[i].seed, prm[i].p, k);
+  std::vector<BatchState> st0(n, BatchState{0, -1, 0, 0});
+
+  BatchLaunch L{};
+  L.n = n;
+  TVS_TRY(S.upload(desc, (BatchProb**)&L.probs, s));
+  TVS_TRY(S.upload(st0, &L.state, s));
+  TVS_TRY(S.upload(blur_tiles, (int4**)&L.blur_tiles, s));
+  TVS_TRY(S.upload(ident_chunks, (int2**)&L.ident_chunks, s));
+  TVS_TRY(S.upload(fgp_tiles, (int4**)&L.fgp_tiles, s));
+  TVS_TRY(S.upload(all_chunks, (int2**)&L.all_chunks, s));
+  TVS_TRY(S.upload(coins, (unsigned char**)&L.coins, s));
+  L.n_blur_tiles = n_blur;
+  L.n_ident_chunks = (int)ident_chunks.size();
+  L.n_fgp_tiles = (int)fgp_tiles.size();
+  L.n_all_chunks = (int)all_chunks.size();
+  TVS_TRY(S.zeros<int>(1, &L.kctr, s));
+  TVS_TRY(S.zeros<double>((size_t)n_blur + ident_chunks.size(), &L.part_a, s));
+  TVS_TRY(S.zeros<double>((size_t)n_blur + ident_chunks.size(), &L.part_b, s));
+  unsigned long long* t0_dev = nullptr;
+  TVS_TRY(S.zeros<unsigned long long>(1, &t0_dev, s));
+  {
+    cudaError_t e = cudaHostAlloc((void**)&S.done_host, sizeof(int) * n, cudaHostAllocMapped);
+    if (e != cudaSuccess) {
+      S.done_host = nullptr;
+      return fail(TVS_ENOMEM, "cudaHostAlloc: %s", cudaGetErrorString(e));
+    }
+    memset(S.done_host, 0, sizeof(int) * n);
+    CUDA_TRY(cudaHostGetDevicePointer((void**)&L.done_host, S.done_host, 0));
+  }
+  const std::vector<float> betas = fgp_betas(N);
+  L.betas = betas.data();
+  L.n_inner = N;
+  L.dtype = dtype;
+  L.use_prox = N > 0;
+  CUDA_TRY(cudaEventRecord(C->ev_start, s));
+  CUDA_TRY(launch_timestamp(t0_dev, s));
+  GraphSet G;
+  for (int par = 0; par < 2; ++par) {
+    TVS_TRY(capture(s, &G.exec[1][par], [&]() -> tvs_status {
+      CUDA_TRY(launch_batch_iteration(L, par, s));
+      return TVS_OK;
+    }));
+  }
+  int launched = 0;
+  for (int k = 0; k < K; ++k) {
+    if (k >= LAG) {
+      CUDA_TRY(cudaEventSynchronize(C->ring[k % LAG]));
+      int ndone = 0;
+      for (int i = 0; i < n; ++i) ndone += ((volatile int*)S.done_host)[i];
+      if (ndone == n) break;
+    }
+    CUDA_TRY(cudaGraphLaunch(G.exec[1][k & 1], s));
+    CUDA_TRY(cudaEventRecord(C->ring[k % LAG], s));
+    launched = k + 1;
+  }
+  CUDA_TRY(launch_batch_final_objective(L, launched & 1, s));
+  CUDA_TRY(cudaEventRecord(C->ev_stop, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<BatchState> st(n);
+  CUDA_TRY(cudaMemcpy(st.data(), L.state, sizeof(BatchState) * n, cudaMemcpyDeviceToHost));
+  unsigned long long t0 = 0;
+  CUDA_TRY(cudaMemcpy(&t0, t0_dev, sizeof(t0), cudaMemcpyDeviceToHost));
+  float solve_ms = 0.f;
+  CUDA_TRY(cudaEventElapsedTime(&solve_ms, C->ev_start, C->ev_stop));
+  bool bad = false;
+  for (int i = 0; i < n; ++i) {
+    tvs_problem* P = probs[i];
+    const int iters = st[i].iters;
+    TVS_TRY(copy_out(x_io[i], P->x[iters & 1], P->n, mem, s));
+    std::vector<double> obj(iters > 0 ? iters : 1);
+    std::vector<unsigned long long> ts(iters > 0 ? iters : 1);
+    if (iters > 0) {
+      CUDA_TRY(cudaMemcpy(obj.data(), P->obj_dev, sizeof(double) * iters, cudaMemcpyDeviceToHost));
+      CUDA_TRY(cudaMemcpy(ts.data(), P->ts_dev, sizeof(unsigned long long) * iters, cudaMemcpyDeviceToHost));
+      if (!is_fin(obj[iters - 1])) bad = true;
+    }
+    if (traces) {
+      tvs_trace* tr = &traces[i];
+      int prox = 0;
+      for (int k = 0; k < iters; ++k) prox += coins[(size_t)k * n + i];
+      tr->iters_run = iters;
+      tr->prox_calls = prox;
+      tr->reached = st[i].pad;
+      tr->reached_iter = st[i].reached;
+      tr->time_to_target_s = -1.0;
+      if (st[i].reached >= 0 && st[i].reached < iters) tr->time_to_target_s = (double)(ts[st[i].reached] - t0) * 1e-9;
+      tr->solve_ms = solve_ms;
+      tr->fgp_ms = 0.0;
+      tr->fgp_launches = (long long)prox * ((N + batch_fgp_iters_per_launch() - 1) / batch_fgp_iters_per_launch());
+      tr->fgp_pixel_iters = (long long)prox * N * (long long)P->n;
+      const int lim = tr->cap < iters ? tr->cap : iters;
+      for (int k = 0; k < lim; ++k) {
+        if (tr->objective) tr->objective[k] = obj[k];
+        if (tr->coins) tr->coins[k] = coins[(size_t)k * n + i];
+        if (tr->t_s) tr->t_s[k] = (double)(ts[k] - t0) * 1e-9;
+      }
+    }
+  }
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (bad) return fail(TVS_ENUMERIC, "non-finite objective in the batch");
+  return TVS_OK;
+}
+
 // =====================================================================================
 extern "C" {
 

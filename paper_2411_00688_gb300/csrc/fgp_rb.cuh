@@ -1,0 +1,169 @@
+// Register-blocked temporally blocked FGP body for 2D images, shared by the
+// single-problem kernel (fgp.cu) and the batched kernel (batch.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace tvs {
+
+// b[0]: momentum coefficient forming r for the first iteration of a launch;
+// b[t]: for iteration t+1.
+struct TBBetas {
+  float b[8];
+};
+
+// ---------------------------------------------------------------------------
+// Register-blocked temporally blocked 2D variant.  Same staged region and the
+// same per-iteration arithmetic as fgp2d_tb_kernel, but every cell lives in the
+// registers of one thread for the whole launch: warp w owns RPW consecutive
+// region rows, lane l owns CPL adjacent columns.  Horizontal neighbours come
+// from warp shuffles, vertical neighbours from the thread's own registers; only
+// the row shared by two warps goes through shared memory (one row of r before
+// phase 1, one row of u before phase 2).  Cells are updated unconditionally:
+// values in the shrinking halo are stale but finite and never reach a cell of
+// the valid region (masks keep out-of-image cells out of in-image stencils).
+template <typename T, bool NONNEG, int TB, int CPL, int RPW>
+__device__ __forceinline__ void fgp2d_rb_body(const float* __restrict__ z, const T* __restrict__ pc,
+                                              const T* __restrict__ pp, T* __restrict__ pn,
+                                              T* __restrict__ pnp, int H, int W, float lam,
+                                              float inv_step, const TBBetas& betas, int iters,
+                                              int tile_x, int tile_y) {
+  constexpr int NW = 8;
+  constexpr int RW = 32 * CPL, RH = NW * RPW;
+  constexpr int TW = RW - 2 * TB, TH = RH - 2 * TB;
+  __shared__ float edge_ry[NW][RW];  // bottom row of r_y of each warp's block
+  __shared__ float edge_u[NW][RW];   // top row of u of each warp's block
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gi0 = tile_y * TH - TB + warp * RPW;   // global row of the thread's first cell
+  const int gj0 = tile_x * TW - TB + lane * CPL;   // global column of its first cell
+  const size_t n = (size_t)H * W;
+
+  float Z[RPW][CPL], Ry[RPW][CPL], Rx[RPW][CPL], Py[RPW][CPL], Px[RPW][CPL], U[RPW][CPL];
+  // boundary masks: row masks per row, column masks per column (Neumann)
+  bool row_in[RPW], row_dn[RPW], row_up[RPW], col_in[CPL], col_rt[CPL], col_lf[CPL];
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) {
+    const int gi = gi0 + r;
+    row_in[r] = gi >= 0 && gi < H;
+    row_dn[r] = gi < H - 1;   // has a row below (D_y defined, div uses p_y here)
+    row_up[r] = gi > 0;       // has a row above (div uses p_y of the row above)
+  }
+#pragma unroll
+  for (int q = 0; q < CPL; ++q) {
+    const int gj = gj0 + q;
+    col_in[q] = gj >= 0 && gj < W;
+    col_rt[q] = gj < W - 1;
+    col_lf[q] = gj > 0;
+  }
+  const float b0 = betas.b[0];
+#pragma unroll
+  for (int r = 0; r < RPW; ++r)
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+      float zz = 0.f, cy = 0.f, cx = 0.f, ry = 0.f, rx = 0.f;
+      if (row_in[r] && col_in[q]) {
+        const size_t o = (size_t)(gi0 + r) * W + (gj0 + q);
+        zz = __ldg(z + o);
+        cy = Elem<T>::ld(pc + o);
+        cx = Elem<T>::ld(pc + n + o);
+        if (b0 != 0.f) {
+          ry = cy + b0 * (cy - Elem<T>::ld(pp + o));
+          rx = cx + b0 * (cx - Elem<T>::ld(pp + n + o));
+        } else {
+          ry = cy;
+          rx = cx;
+        }
+      }
+      Z[r][q] = zz;
+      Py[r][q] = cy;
+      Px[r][q] = cx;
+      Ry[r][q] = ry;
+      Rx[r][q] = rx;
+    }
+#pragma unroll
+  for (int q = 0; q < CPL; ++q) edge_ry[warp][lane * CPL + q] = Ry[RPW - 1][q];
+  __syncthreads();
+
+  for (int t = 1; t <= iters; ++t) {
+    // phase 1: U = P_X(Z + lam div R)
+    float ry_above[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) ry_above[q] = warp > 0 ? edge_ry[warp - 1][lane * CPL + q] : 0.f;
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+      const float rx_left = __shfl_up_sync(0xffffffffu, Rx[r][CPL - 1], 1);
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) {
+        const float up = r > 0 ? Ry[r - 1][q] : ry_above[q];
+        const float lf = q > 0 ? Rx[r][q - 1] : rx_left;
+        float dv = 0.f;
+        if (row_dn[r]) dv += Ry[r][q];
+        if (row_up[r]) dv -= up;
+        if (col_rt[q]) dv += Rx[r][q];
+        if (col_lf[q]) dv -= lf;
+        float u = Z[r][q] + lam * dv;
+        if (NONNEG) u = fmaxf(u, 0.f);
+        U[r][q] = (row_in[r] && col_in[q]) ? u : 0.f;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) edge_u[warp][lane * CPL + q] = U[0][q];
+    __syncthreads();
+    // phase 2: p_new = P_B(R + inv_step D U); R = next momentum point (or p_prev); P = p_new
+    const bool last = (t == iters);
+    const float bn = last ? 0.f : betas.b[t];
+    float u_below[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) u_below[q] = warp < NW - 1 ? edge_u[warp + 1][lane * CPL + q] : 0.f;
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+      const float u_right = __shfl_down_sync(0xffffffffu, U[r][0], 1);
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) {
+        const float uc = U[r][q];
+        const float dn = r < RPW - 1 ? U[r + 1][q] : u_below[q];
+        const float rt = q < CPL - 1 ? U[r][q + 1] : u_right;
+        const float gy = row_dn[r] ? dn - uc : 0.f;
+        const float gx = col_rt[q] ? rt - uc : 0.f;
+        const float qy = Ry[r][q] + inv_step * gy;
+        const float qx = Rx[r][q] + inv_step * gx;
+        const float nrm2 = qy * qy + qx * qx;
+        const float sc = nrm2 > 1.f ? rsqrtf(nrm2) : 1.f;
+        const float ny = Elem<T>::round(qy * sc), nx = Elem<T>::round(qx * sc);
+        const float oy = Py[r][q], ox = Px[r][q];
+        if (last) {
+          Ry[r][q] = oy;
+          Rx[r][q] = ox;
+        } else {
+          Ry[r][q] = ny + bn * (ny - oy);
+          Rx[r][q] = nx + bn * (nx - ox);
+        }
+        Py[r][q] = ny;
+        Px[r][q] = nx;
+      }
+    }
+    if (!last) {
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) edge_ry[warp][lane * CPL + q] = Ry[RPW - 1][q];
+    }
+    __syncthreads();
+  }
+  // tile interior: P = p_{k+iters}, R = p_{k+iters-1}
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) {
+    const int a = warp * RPW + r;
+    if (a < TB || a >= TB + TH || !row_in[r]) continue;
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+      const int c = lane * CPL + q;
+      if (c < TB || c >= TB + TW || !col_in[q]) continue;
+      const size_t o = (size_t)(gi0 + r) * W + (gj0 + q);
+      Elem<T>::st(pn + o, Py[r][q]);
+      Elem<T>::st(pn + n + o, Px[r][q]);
+      Elem<T>::st(pnp + o, Ry[r][q]);
+      Elem<T>::st(pnp + n + o, Rx[r][q]);
+    }
+  }
+}
+
+}  // namespace tvs

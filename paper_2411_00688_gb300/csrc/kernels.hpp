@@ -96,6 +96,53 @@ cudaError_t launch_count_nonfinite(const float* x, size_t n, int* count, cudaStr
 cudaError_t launch_coin_schedule(uint64_t seed, double p, int64_t k0, int K, unsigned char* out,
                                  cudaStream_t s);
 
+// ---- batched ProxSkip (batch.cu) ----
+// Descriptor of one problem of a batch (device memory).  Partials of its
+// objective occupy part_a/part_b[part_off, part_off + part_n).
+struct BatchProb {
+  int H, W, nonneg, pad;
+  const float* b;
+  float *x0, *x1, *z, *h, *r;
+  void *dual0, *dual1, *dual2, *dual3;
+  float lam, inv_step, gamma, ch_skip, ch_prox, h_coef;
+  double alpha, f_star, target;
+  BlurW bw;
+  int part_off, part_n;
+  double* obj;
+  unsigned long long* ts;
+};
+struct BatchState {
+  int done, reached, iters, pad;  // reached: trace index of the first iterate on target; pad: hit
+};
+struct BatchLaunch {
+  const BatchProb* probs;
+  BatchState* state;
+  int n;
+  const int4* blur_tiles;   // (problem, tile x, tile y) of the blur problems (32 x 16 tiles)
+  int n_blur_tiles;
+  const int2* ident_chunks; // (problem, chunk) of the identity problems
+  int n_ident_chunks;
+  const int4* fgp_tiles;    // (problem, tile x, tile y) of every problem (blocked inner tiles)
+  int n_fgp_tiles;
+  const int2* all_chunks;   // (problem, chunk) of every problem
+  int n_all_chunks;
+  const unsigned char* coins;  // [K][n]
+  int* kctr;                   // outer iteration counter (device)
+  double *part_a, *part_b;
+  int* done_host;              // n flags in mapped host memory
+  int n_inner, dtype;
+  bool use_prox;
+  const float* betas;          // host: momentum coefficient of each inner iteration
+};
+int batch_fgp_tile_w();
+int batch_fgp_tile_h();
+int batch_chunk();
+int batch_fgp_iters_per_launch();
+// One outer iteration of every problem (graph-capturable; reads k from kctr).
+cudaError_t launch_batch_iteration(const BatchLaunch& L, int par, cudaStream_t s);
+// F(x_k) of the problems still running, recorded as their final trace entry.
+cudaError_t launch_batch_final_objective(const BatchLaunch& L, int par, cudaStream_t s);
+
 // ---- parallel-beam projector (ct.cu) ----
 struct CTGeom {
   int N, n_angles, n_det;

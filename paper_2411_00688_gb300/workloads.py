@@ -1,0 +1,209 @@
+"""Time-to-target measurements of the synthetic workloads other than the
+benchmark's headline one (python -m paper_2411_00688_gb300.workloads NAME ...).
+
+  denoise2d_256  ProxSkip p = 0.1 vs PGD, 100 inner iterations, <= 500 iterations
+  ct2d_512       PDHGSkip-2 p in {0.2, 0.05} vs PDHG, 50 inner, <= 2000 iterations
+  denoise3d_512  ProxSkip p = 0.1 vs PGD, 30 inner, <= 200 iterations (FP32 / BF16 / FP16 dual)
+  batch2d_256    256 uneven problems: one batched solve vs a loop of single solves
+
+Each prints one JSON line per solver: iterations and prox calls to a 1e-4
+relative objective gap, device time to the target and wall time of the solve.
+F* is the smallest objective of a long reference run on the same GPU
+(FISTA for forward-backward problems, PDHG for CT), made first.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+
+TARGET = 1e-4
+
+
+def _ctx():
+    import paper_2411_00688_gb300 as tvs
+    return tvs, tvs.Context(0)
+
+
+def _solve_record(name, tr, wall_s, f_star, **extra):
+    gaps = (tr.objective - f_star) / f_star if len(tr.objective) else np.array([np.nan])
+    rec = {"solver": name, "reached": tr.reached, "iterations": (tr.reached_iter + 1) if tr.reached else tr.iters_run,
+           "prox_calls": tr.prox_calls, "time_to_target_s": tr.time_to_target_s if tr.reached else None,
+           "wall_s": wall_s, "final_rel_gap": float(gaps[-1]), "best_rel_gap": float(np.nanmin(gaps))}
+    rec.update(extra)
+    return rec
+
+
+def _timed(fn):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return out, time.perf_counter() - t0
+
+
+def denoise2d_256():
+    import torch
+    from synth.configs import DenoiseConfig
+    tvs, ctx = _ctx()
+    cfg = DenoiseConfig()
+    b = torch.from_numpy((cfg.phantom() + cfg.noise()).astype(np.float32)).cuda()
+    prob = tvs.Problem(ctx, b, cfg.alpha)
+    _, ref = tvs.fista_solve(prob, b.clone(), cfg.gamma, 3000, 200)
+    f_star = float(np.nanmin(ref.objective))
+    out = []
+    for name, fn in [
+        ("pgd", lambda: tvs.pgd_solve(prob, b.clone(), cfg.gamma, cfg.max_iter, cfg.n_inner, f_star=f_star, target=TARGET)),
+        ("proxskip_p0.1", lambda: tvs.proxskip_solve(prob, b.clone(), cfg.gamma, cfg.p, cfg.seed, cfg.max_iter,
+                                                     cfg.n_inner, f_star=f_star, target=TARGET)),
+    ]:
+        fn()  # warm-up (graph capture paths, autotuner)
+        (_, tr), wall = _timed(fn)
+        out.append(_solve_record(name, tr, wall, f_star, workload=cfg.name))
+    return out
+
+
+def _power_norm_sq(tvs, prob, shape, meas_shape, iters=100):
+    import torch
+    x = torch.randn(shape, device="cuda")
+    x /= x.norm()
+    y = torch.empty(meas_shape, device="cuda")
+    z = torch.empty(shape, device="cuda")
+    lam = 0.0
+    for _ in range(iters):
+        tvs.tvs_op_apply(prob, x, y)
+        tvs.tvs_op_apply(prob, y, z, adjoint=True)
+        lam = float((x * z).sum())
+        x = z / z.norm()
+    return lam
+
+
+def ct2d_512():
+    import torch
+    from synth.configs import CTConfig
+    tvs, ctx = _ctx()
+    cfg = CTConfig()
+    N = cfg.N
+    truth = torch.from_numpy(cfg.phantom().astype(np.float32)).cuda()
+    mk = dict(op="ct", shape=(N, N), n_angles=cfg.n_angles, n_det=cfg.n_det, pixel_size=1.0 / N,
+              det_spacing=1.0 / N)
+    zeros_sino = torch.zeros((cfg.n_angles, cfg.n_det), device="cuda")
+    op = tvs.Problem(ctx, zeros_sino, cfg.alpha, **mk)
+    clean = torch.empty_like(zeros_sino)
+    tvs.tvs_op_apply(op, truth, clean)
+    counts = cfg.counts(clean.cpu().numpy().astype(np.float64))
+    b = torch.from_numpy((-np.log(np.maximum(counts, 1.0) / cfg.photons)).astype(np.float32)).cuda()
+    prob = tvs.Problem(ctx, b, cfg.alpha, **mk)
+    L = _power_norm_sq(tvs, prob, (N, N), (cfg.n_angles, cfg.n_det))
+    st = 0.99 / math.sqrt(L)
+    x0 = torch.zeros((N, N), device="cuda")
+    _, _, ref = tvs.pdhg_solve(prob, x0.clone(), zeros_sino.clone(), st, st, 6000, 100)
+    f_star = float(np.nanmin(ref.objective))
+    out = []
+    runs = [("pdhg", lambda: tvs.pdhg_solve(prob, x0.clone(), zeros_sino.clone(), st, st, cfg.max_iter, cfg.n_inner,
+                                            f_star=f_star, target=TARGET))]
+    for p in cfg.ps:
+        runs.append((f"pdhgskip_p{p}", lambda p=p: tvs.pdhgskip_solve(prob, x0.clone(), zeros_sino.clone(), st, st, p,
+                                                                       cfg.seed, cfg.max_iter, cfg.n_inner,
+                                                                       f_star=f_star, target=TARGET)))
+    for name, fn in runs:
+        fn()
+        (_, _, tr), wall = _timed(fn)
+        out.append(_solve_record(name, tr, wall, f_star, workload=cfg.name, norm_A_sq=L, sigma=st, tau=st))
+    return out
+
+
+def denoise3d_512(duals=("f32", "bf16", "f16")):
+    import torch
+    from synth.configs import Denoise3DConfig
+    tvs, ctx = _ctx()
+    cfg = Denoise3DConfig()
+    vol = cfg.phantom()
+    vol += cfg.noise()
+    b = torch.from_numpy(vol).cuda()
+    del vol
+    prob = tvs.Problem(ctx, b, cfg.alpha)
+    _, ref = tvs.fista_solve(prob, b.clone(), cfg.gamma, 400, 60)
+    f_star = float(np.nanmin(ref.objective))
+    out = []
+    for dual in duals:
+        for name, fn in [
+            ("pgd", lambda: tvs.pgd_solve(prob, b.clone(), cfg.gamma, cfg.max_iter, cfg.n_inner, dual=dual,
+                                          f_star=f_star, target=TARGET)),
+            ("proxskip_p0.1", lambda: tvs.proxskip_solve(prob, b.clone(), cfg.gamma, cfg.p, cfg.seed, cfg.max_iter,
+                                                         cfg.n_inner, dual=dual, f_star=f_star, target=TARGET)),
+        ]:
+            (_, tr), wall = _timed(fn)
+            per_it = tr.fgp_ms / max(tr.fgp_launches, 1) * 1e-3
+            bpv = 40 if dual == "f32" else 22
+            out.append(_solve_record(name, tr, wall, f_star, workload=cfg.name, dual=dual,
+                                     fgp_launch_us=per_it * 1e6,
+                                     fgp_gbs=bpv * cfg.N ** 3 / per_it / 1e9 if per_it > 0 else None))
+    return out
+
+
+def _batch(n_problems=None, K=None):
+    import torch
+    from synth.configs import BatchConfig
+    tvs, ctx = _ctx()
+    cfg = BatchConfig()
+    specs = cfg.specs()[: n_problems or cfg.n_problems]
+    K = K or cfg.max_iter
+    probs, bs = [], []
+    for sp in specs:
+        truth = torch.from_numpy(cfg.phantom(sp).astype(np.float32)).cuda()
+        noise = torch.from_numpy(cfg.noise(sp).astype(np.float32)).cuda()
+        if sp["kind"] == "deblur":
+            opp = tvs.Problem(ctx, truth, sp["alpha"], op="blur", blur_sigma=sp["blur_sigma"])
+            clean = torch.empty_like(truth)
+            tvs.tvs_op_apply(opp, truth, clean)
+            opp.close()
+            b = (clean + noise).contiguous()
+            probs.append(tvs.Problem(ctx, b, sp["alpha"], op="blur", blur_sigma=sp["blur_sigma"]))
+        else:
+            b = (truth + noise).contiguous()
+            probs.append(tvs.Problem(ctx, b, sp["alpha"]))
+        bs.append(b)
+    ps = [sp["p"] for sp in specs]
+    seeds = [sp["seed"] for sp in specs]
+    npx = sum(sp["H"] * sp["W"] for sp in specs)
+
+    def batched():
+        xs = [b.clone() for b in bs]
+        return tvs.proxskip_solve_batch(ctx, probs, xs, [1.0] * len(probs), ps, seeds, K, cfg.n_inner)
+
+    def loop():
+        trs = []
+        for pr, b, p, s in zip(probs, bs, ps, seeds):
+            trs.append(tvs.proxskip_solve(pr, b.clone(), 1.0, p, s, K, cfg.n_inner)[1])
+        return trs
+
+    batched()
+    _, t_batch = _timed(batched)
+    loop()
+    _, t_loop = _timed(loop)
+    return [{"workload": cfg.name, "problems": len(specs), "pixels": npx, "iterations": K,
+             "n_inner": cfg.n_inner, "batched_s": t_batch, "loop_s": t_loop, "speedup": t_loop / t_batch}]
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("workload", choices=["denoise2d_256", "ct2d_512", "denoise3d_512", "batch2d_256"])
+    ap.add_argument("--problems", type=int, default=None)
+    ap.add_argument("--iters", type=int, default=None)
+    args = ap.parse_args(argv)
+    if args.workload == "batch2d_256":
+        recs = _batch(args.problems, args.iters)
+    else:
+        recs = {"denoise2d_256": denoise2d_256, "ct2d_512": ct2d_512, "denoise3d_512": denoise3d_512}[args.workload]()
+    for r in recs:
+        print(json.dumps(r), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,122 @@
+"""GPU parity of the batched ProxSkip solve (many problems of uneven sizes, each
+with its own alpha, p and seed, in shared launches) against the FP64 oracle and
+against one-at-a-time solves."""
+
+import numpy as np
+import pytest
+
+from oracle import operators, solvers
+from synth import phantoms
+from tests._util import TOL_OBJ, TOL_X_F32, cuda, f32, host, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+SPECS = [  # (H, W, op, alpha, p, seed, blur sigma)
+    (64, 64, "identity", 0.10, 0.30, 0, 2.0),
+    (61, 47, "blur", 0.03, 0.50, 1, 2.0),
+    (100, 130, "identity", 0.05, 0.10, 2, 2.0),
+    (96, 200, "blur", 0.02, 0.25, 3, 1.3),
+    (33, 257, "identity", 0.15, 0.45, 4, 2.0),
+    (128, 128, "blur", 0.04, 0.05, 5, 2.9),
+    (9, 11, "blur", 0.05, 0.9, 6, 1.0),
+]
+
+
+@pytest.fixture(scope="module")
+def tvs():
+    import paper_2411_00688_gb300 as tvs
+    return tvs
+
+
+@pytest.fixture(scope="module")
+def ctx(tvs):
+    c = tvs.Context(0)
+    yield c
+    c.close()
+
+
+def _problem(spec, k):
+    H, W, op, alpha, p, seed, sig = spec
+    truth = phantoms.shapes_phantom_2d(H, W, 4, 100 + k)
+    clean = operators.blur(truth, operators.gaussian_weights(sig, 4)) if op == "blur" else truth
+    b32, b64 = f32(clean + phantoms.gaussian_noise((H, W), 0.05, 200 + k))
+    A = operators.blur_op(sig) if op == "blur" else operators.identity_op()
+    return b32, b64, solvers.Problem(A, b64, alpha, (H, W))
+
+
+def _build(tvs, ctx):
+    probs, xs, data = [], [], []
+    for k, spec in enumerate(SPECS):
+        b32, b64, oprob = _problem(spec, k)
+        H, W, op, alpha, p, seed, sig = spec
+        probs.append(tvs.Problem(ctx, cuda(b32), alpha, op=op, blur_sigma=sig))
+        xs.append(cuda(b32))
+        data.append((b32, b64, oprob))
+    return probs, xs, data
+
+
+def test_batch_matches_oracle_and_single_solves(tvs, ctx):
+    K, N = 20, 12
+    probs, xs, data = _build(tvs, ctx)
+    gam = [1.0] * len(SPECS)
+    ps = [s[4] for s in SPECS]
+    seeds = [s[5] for s in SPECS]
+    xs, traces = tvs.proxskip_solve_batch(ctx, probs, xs, gam, ps, seeds, K, N)
+    for k, spec in enumerate(SPECS):
+        b32, b64, oprob = data[k]
+        tr = traces[k]
+        ref = solvers.proxskip(oprob, b64, 1.0, spec[4], spec[5], K, N)
+        assert tr.iters_run == K
+        assert list(tr.coins) == ref["coins"] and tr.prox_calls == ref["prox_calls"]
+        assert rel_l2(host(xs[k]), ref["x"]) <= TOL_X_F32, spec
+        rel = np.abs(tr.objective - np.asarray(ref["objective"])) / np.abs(np.asarray(ref["objective"]))
+        assert rel.max() <= TOL_OBJ, spec
+        x1, t1 = tvs.proxskip_solve(probs[k], cuda(b32), 1.0, spec[4], spec[5], K, N)
+        assert rel_l2(host(xs[k]), host(x1)) <= 1e-5
+
+
+def test_batch_stops_each_problem_at_its_target(tvs, ctx):
+    K, N = 30, 10
+    probs, xs, data = _build(tvs, ctx)
+    ps = [s[4] for s in SPECS]
+    seeds = [s[5] for s in SPECS]
+    # per-problem reference optimum: the lowest objective a plain run reaches in K
+    # iterations; the target 1e-3 then stops each problem at a different iteration
+    f_stars, expect = [], []
+    tol = 1e-3
+    for k, spec in enumerate(SPECS):
+        b32, b64, oprob = data[k]
+        _, t = tvs.proxskip_solve(probs[k], cuda(b32), 1.0, spec[4], spec[5], K, N)
+        fs = float(np.nanmin(t.objective))
+        f_stars.append(fs)
+        expect.append(int(np.argmax(t.objective - fs <= tol * fs)))
+    xs, traces = tvs.proxskip_solve_batch(ctx, probs, xs, [1.0] * len(SPECS), ps, seeds, K, N,
+                                          f_stars=f_stars, targets=[tol] * len(SPECS))
+    for k, spec in enumerate(SPECS):
+        tr = traces[k]
+        fs = f_stars[k]
+        b32, b64, oprob = data[k]
+        assert tr.reached and tr.iters_run == tr.reached_iter + 1
+        if tr.iters_run == 0:  # x_0 itself met the target
+            np.testing.assert_array_equal(host(xs[k]), b64)
+            continue
+        # stopped at the first recorded iterate within the target, by its own trace
+        assert tr.objective[-1] - fs <= tol * fs
+        assert np.all(tr.objective[:-1] - fs > tol * fs)
+        assert tr.reached_iter == expect[k]
+        ref = solvers.proxskip(oprob, b64, 1.0, spec[4], spec[5], tr.iters_run, N)
+        assert rel_l2(host(xs[k]), ref["x"]) <= TOL_X_F32
+
+
+def test_batch_rejects_mismatched_parameters(tvs, ctx):
+    import ctypes as C
+    from paper_2411_00688_gb300 import _lib as L
+    probs, xs, _ = _build(tvs, ctx)
+    prm = (L.FBParams * 2)(L.FBParams(gamma=1.0, p=0.5, max_iter=5, n_inner=4),
+                           L.FBParams(gamma=1.0, p=0.5, max_iter=5, n_inner=5))
+    handles = (C.c_void_p * 2)(probs[0].handle.value, probs[1].handle.value)
+    ptrs = (C.c_void_p * 2)(xs[0].data_ptr(), xs[1].data_ptr())
+    assert L.lib().proxskip_solve_batch(ctx.handle, 2, handles, prm, ptrs, 0, None) == 1
+    handles2 = (C.c_void_p * 2)(probs[0].handle.value, probs[0].handle.value)
+    prm[1].n_inner = 4
+    assert L.lib().proxskip_solve_batch(ctx.handle, 2, handles2, prm, ptrs, 0, None) == 1
