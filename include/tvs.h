@@ -228,7 +228,8 @@ tvs_status pdhgskip_solve(tvs_problem* prob, const tvs_pd_params* prm, float* x_
  * run on it (same coins, same arithmetic) and stops at the first x_k whose
  * objective meets its target, or after max_iter iterations.  x_inout[i] and
  * traces[i] (may be NULL) as for proxskip_solve; problems must belong to ctx and
- * be distinct.  Not in the paper: a batching mode for many small solves. */
+ * be distinct, and blur problems must share one blur radius.  Not in the paper:
+ * a batching mode for many small solves. */
 tvs_status proxskip_solve_batch(tvs_ctx* ctx, int n, tvs_problem* const* probs,
                                 const tvs_fb_params* prm, float* const* x_inout, tvs_mem mem,
                                 tvs_trace* traces);

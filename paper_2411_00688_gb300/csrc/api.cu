@@ -802,6 +802,13 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
     for (int j = 0; j < i; ++j)
       if (probs[j] == P) return fail(TVS_EINVAL, "problem %d appears twice", i);
   }
+  int blur_radius = 0;
+  for (int i = 0; i < n; ++i)
+    if (probs[i]->desc.op.kind == TVS_OP_GAUSS_BLUR) {
+      if (blur_radius && probs[i]->bw.R != blur_radius)
+        return fail(TVS_EUNSUPPORTED, "blur problems of a batch must share the blur radius");
+      blur_radius = probs[i]->bw.R;
+    }
   cudaStream_t s = C->stream;
   BatchScratch S;
   // per-problem state, descriptors and work lists
@@ -903,6 +910,7 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
   L.betas = betas.data();
   L.n_inner = N;
   L.dtype = dtype;
+  L.blur_radius = blur_radius;
   L.use_prox = N > 0;
   CUDA_TRY(cudaEventRecord(C->ev_start, s));
   CUDA_TRY(launch_timestamp(t0_dev, s));

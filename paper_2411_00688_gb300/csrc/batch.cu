@@ -22,16 +22,18 @@ constexpr int CHUNK = 1024;                        // pixels per pointwise work 
 
 __device__ __forceinline__ bool active(const BatchState& st) { return st.done == 0; }
 
+template <int R>
 __global__ void __launch_bounds__(BNT)
 batch_blur_resid_kernel(const BatchProb* __restrict__ probs, BatchState* __restrict__ state,
                         const int4* __restrict__ tiles, int par, double* part_a, double* part_b) {
   const int4 e = tiles[blockIdx.x];
   const BatchProb& P = probs[e.x];
   if (!active(state[e.x])) return;
-  blur_tile_body<BM_RESID>(par ? P.x1 : P.x0, P.H, P.W, P.bw, P.b, P.r, nullptr, nullptr, 0.f, 0.f,
+  blur_tile_body<BM_RESID, R>(par ? P.x1 : P.x0, P.H, P.W, P.bw, P.b, P.r, nullptr, nullptr, 0.f, 0.f,
                            nullptr, nullptr, 0.f, part_a, part_b, e.y, e.z, blockIdx.x);
 }
 
+template <int R>
 __global__ void __launch_bounds__(BNT)
 batch_blur_step_kernel(const BatchProb* __restrict__ probs, BatchState* __restrict__ state,
                        const int4* __restrict__ tiles, const unsigned char* __restrict__ coins, int n,
@@ -43,7 +45,7 @@ batch_blur_step_kernel(const BatchProb* __restrict__ probs, BatchState* __restri
   const bool coin = coins[(size_t)k * n + e.x] != 0;
   const float* xc = par ? P.x1 : P.x0;
   float* out = coin ? P.z : (par ? P.x0 : P.x1);
-  blur_tile_body<BM_STEP>(P.r, P.H, P.W, P.bw, nullptr, out, xc, P.h, P.gamma,
+  blur_tile_body<BM_STEP, R>(P.r, P.H, P.W, P.bw, nullptr, out, xc, P.h, P.gamma,
                           coin ? P.ch_prox : P.ch_skip, nullptr, nullptr, 0.f, nullptr, nullptr, e.y,
                           e.z, 0);
 }
@@ -194,12 +196,30 @@ int batch_fgp_tile_h() { return BT_TH; }
 int batch_chunk() { return CHUNK; }
 int batch_fgp_iters_per_launch() { return BT_TB; }
 
+namespace {
+cudaError_t batch_blur(const BatchLaunch& L, int par, bool step, cudaStream_t s) {
+  switch (L.blur_radius) {
+#define TVS_BB_R(R_)                                                                                   \
+  case R_:                                                                                             \
+    batch_blur_resid_kernel<R_><<<L.n_blur_tiles, BNT, 0, s>>>(L.probs, L.state, L.blur_tiles, par,   \
+                                                              L.part_a, L.part_b);                     \
+    if (step)                                                                                          \
+      batch_blur_step_kernel<R_><<<L.n_blur_tiles, BNT, 0, s>>>(L.probs, L.state, L.blur_tiles,        \
+                                                                L.coins, L.n, L.kctr, par);            \
+    break;
+    TVS_BB_R(1) TVS_BB_R(2) TVS_BB_R(3) TVS_BB_R(4) TVS_BB_R(5) TVS_BB_R(6) TVS_BB_R(7) TVS_BB_R(8)
+#undef TVS_BB_R
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+}  // namespace
+
 cudaError_t launch_batch_iteration(const BatchLaunch& L, int par, cudaStream_t s) {
   if (L.n_blur_tiles > 0) {
-    batch_blur_resid_kernel<<<L.n_blur_tiles, BNT, 0, s>>>(L.probs, L.state, L.blur_tiles, par, L.part_a,
-                                                           L.part_b);
-    batch_blur_step_kernel<<<L.n_blur_tiles, BNT, 0, s>>>(L.probs, L.state, L.blur_tiles, L.coins, L.n,
-                                                          L.kctr, par);
+    cudaError_t e = batch_blur(L, par, true, s);
+    if (e != cudaSuccess) return e;
   }
   if (L.n_ident_chunks > 0)
     batch_ident_step_kernel<<<L.n_ident_chunks, 256, 0, s>>>(L.probs, L.state, L.ident_chunks, L.coins, L.n,
@@ -264,9 +284,10 @@ cudaError_t launch_batch_iteration(const BatchLaunch& L, int par, cudaStream_t s
 }
 
 cudaError_t launch_batch_final_objective(const BatchLaunch& L, int par, cudaStream_t s) {
-  if (L.n_blur_tiles > 0)
-    batch_blur_resid_kernel<<<L.n_blur_tiles, BNT, 0, s>>>(L.probs, L.state, L.blur_tiles, par, L.part_a,
-                                                           L.part_b);
+  if (L.n_blur_tiles > 0) {
+    cudaError_t e = batch_blur(L, par, false, s);
+    if (e != cudaSuccess) return e;
+  }
   if (L.n_ident_chunks > 0)
     batch_ident_step_kernel<<<L.n_ident_chunks, 256, 0, s>>>(L.probs, L.state, L.ident_chunks, L.coins, L.n,
                                                              L.kctr, par, 0, L.part_a, L.part_b,

@@ -20,7 +20,9 @@ __device__ __forceinline__ float tv_at_2d(const float* __restrict__ x, int gi, i
   return sqrtf(dy * dy + dx * dx);
 }
 
-template <int MODE>
+// R: blur radius (compile time, so the tap loops unroll and the weights stay in
+// registers).
+template <int MODE, int R>
 __device__ __forceinline__ void blur_tile_body(const float* __restrict__ src, int H, int W, const BlurW& w,
                                                const float* __restrict__ b, float* __restrict__ out,
                                                const float* __restrict__ x, const float* __restrict__ h,
@@ -30,7 +32,9 @@ __device__ __forceinline__ void blur_tile_body(const float* __restrict__ src, in
                                                int part_index) {
   __shared__ float s_in[BY + 2 * RMAX][BX + 2 * RMAX + 1];
   __shared__ float s_tmp[BY + 2 * RMAX][BX + 1];
-  const int R = w.R;
+  float wk[2 * R + 1];
+#pragma unroll
+  for (int k = 0; k <= 2 * R; ++k) wk[k] = w.w[k];
   const int j0 = tile_x * BX, i0 = tile_y * BY;
   const int rows = BY + 2 * R, cols = BX + 2 * R;
   for (int e = threadIdx.x; e < rows * cols; e += BNT) {
@@ -42,7 +46,8 @@ __device__ __forceinline__ void blur_tile_body(const float* __restrict__ src, in
   for (int e = threadIdx.x; e < rows * BX; e += BNT) {
     const int a = e / BX, c = e - a * BX;
     float acc = 0.f;
-    for (int k = 0; k <= 2 * R; ++k) acc = fmaf(w.w[k], s_in[a][c + k], acc);
+#pragma unroll
+    for (int k = 0; k <= 2 * R; ++k) acc = fmaf(wk[k], s_in[a][c + k], acc);
     s_tmp[a][c] = acc;
   }
   __syncthreads();
@@ -52,7 +57,8 @@ __device__ __forceinline__ void blur_tile_body(const float* __restrict__ src, in
     const int gi = i0 + a, gj = j0 + c;
     if (gi >= H || gj >= W) continue;
     float v = 0.f;
-    for (int k = 0; k <= 2 * R; ++k) v = fmaf(w.w[k], s_tmp[a + k][c], v);
+#pragma unroll
+    for (int k = 0; k <= 2 * R; ++k) v = fmaf(wk[k], s_tmp[a + k][c], v);
     const size_t o = (size_t)gi * W + gj;
     if (MODE == BM_RESID) {
       const float r = v - __ldg(b + o);

@@ -22,12 +22,14 @@ struct TBBetas {
 // phase 1, one row of u before phase 2).  Cells are updated unconditionally:
 // values in the shrinking halo are stale but finite and never reach a cell of
 // the valid region (masks keep out-of-image cells out of in-image stencils).
-template <typename T, bool NONNEG, int TB, int CPL, int RPW>
-__device__ __forceinline__ void fgp2d_rb_body(const float* __restrict__ z, const T* __restrict__ pc,
-                                              const T* __restrict__ pp, T* __restrict__ pn,
-                                              T* __restrict__ pnp, int H, int W, float lam,
-                                              float inv_step, const TBBetas& betas, int iters,
-                                              int tile_x, int tile_y) {
+// INTERIOR: the whole staged region lies in rows/columns 1 .. n-2, so every
+// Neumann mask is true and the masked terms are dropped (same arithmetic).
+template <typename T, bool NONNEG, int TB, int CPL, int RPW, bool INTERIOR>
+__device__ __forceinline__ void fgp2d_rb_body_impl(const float* __restrict__ z, const T* __restrict__ pc,
+                                                   const T* __restrict__ pp, T* __restrict__ pn,
+                                                   T* __restrict__ pnp, int H, int W, float lam,
+                                                   float inv_step, const TBBetas& betas, int iters,
+                                                   int tile_x, int tile_y) {
   constexpr int NW = 8;
   constexpr int RW = 32 * CPL, RH = NW * RPW;
   constexpr int TW = RW - 2 * TB, TH = RH - 2 * TB;
@@ -44,16 +46,16 @@ __device__ __forceinline__ void fgp2d_rb_body(const float* __restrict__ z, const
 #pragma unroll
   for (int r = 0; r < RPW; ++r) {
     const int gi = gi0 + r;
-    row_in[r] = gi >= 0 && gi < H;
-    row_dn[r] = gi < H - 1;   // has a row below (D_y defined, div uses p_y here)
-    row_up[r] = gi > 0;       // has a row above (div uses p_y of the row above)
+    row_in[r] = INTERIOR || (gi >= 0 && gi < H);
+    row_dn[r] = INTERIOR || gi < H - 1;   // has a row below (D_y defined, div uses p_y here)
+    row_up[r] = INTERIOR || gi > 0;       // has a row above (div uses p_y of the row above)
   }
 #pragma unroll
   for (int q = 0; q < CPL; ++q) {
     const int gj = gj0 + q;
-    col_in[q] = gj >= 0 && gj < W;
-    col_rt[q] = gj < W - 1;
-    col_lf[q] = gj > 0;
+    col_in[q] = INTERIOR || (gj >= 0 && gj < W);
+    col_rt[q] = INTERIOR || gj < W - 1;
+    col_lf[q] = INTERIOR || gj > 0;
   }
   const float b0 = betas.b[0];
 #pragma unroll
@@ -128,7 +130,7 @@ __device__ __forceinline__ void fgp2d_rb_body(const float* __restrict__ z, const
         const float qy = Ry[r][q] + inv_step * gy;
         const float qx = Rx[r][q] + inv_step * gx;
         const float nrm2 = qy * qy + qx * qx;
-        const float sc = nrm2 > 1.f ? rsqrtf(nrm2) : 1.f;
+        const float sc = fminf(1.f, rsqrtf(nrm2));  // 1 / max(1, |q|): rsqrt(n2) < 1 iff n2 > 1
         const float ny = Elem<T>::round(qy * sc), nx = Elem<T>::round(qx * sc);
         const float oy = Py[r][q], ox = Px[r][q];
         if (last) {
@@ -164,6 +166,23 @@ __device__ __forceinline__ void fgp2d_rb_body(const float* __restrict__ z, const
       Elem<T>::st(pnp + n + o, Rx[r][q]);
     }
   }
+}
+
+template <typename T, bool NONNEG, int TB, int CPL, int RPW>
+__device__ __forceinline__ void fgp2d_rb_body(const float* __restrict__ z, const T* __restrict__ pc,
+                                              const T* __restrict__ pp, T* __restrict__ pn,
+                                              T* __restrict__ pnp, int H, int W, float lam,
+                                              float inv_step, const TBBetas& betas, int iters,
+                                              int tile_x, int tile_y) {
+  constexpr int RW = 32 * CPL, RH = 8 * RPW, TW = RW - 2 * TB, TH = RH - 2 * TB;
+  const int r0 = tile_y * TH - TB, c0 = tile_x * TW - TB;
+  const bool interior = r0 >= 1 && r0 + RH <= H - 1 && c0 >= 1 && c0 + RW <= W - 1;
+  if (interior)
+    fgp2d_rb_body_impl<T, NONNEG, TB, CPL, RPW, true>(z, pc, pp, pn, pnp, H, W, lam, inv_step, betas, iters,
+                                                      tile_x, tile_y);
+  else
+    fgp2d_rb_body_impl<T, NONNEG, TB, CPL, RPW, false>(z, pc, pp, pn, pnp, H, W, lam, inv_step, betas, iters,
+                                                       tile_x, tile_y);
 }
 
 }  // namespace tvs

@@ -131,6 +131,7 @@ struct BatchLaunch {
   double *part_a, *part_b;
   int* done_host;              // n flags in mapped host memory
   int n_inner, dtype;
+  int blur_radius;             // shared by every blur problem of the batch
   bool use_prox;
   const float* betas;          // host: momentum coefficient of each inner iteration
 };

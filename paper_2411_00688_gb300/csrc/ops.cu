@@ -20,14 +20,14 @@ namespace {
 
 constexpr int PW_NT = 256;
 
-template <int MODE>
+template <int MODE, int R>
 __global__ void __launch_bounds__(BNT)
 blur_kernel(const float* __restrict__ src, int H, int W, BlurW w, const float* __restrict__ b,
             float* __restrict__ out, const float* __restrict__ x, const float* __restrict__ h,
             float gamma, float ch, float* __restrict__ axp, float* __restrict__ y, float tau,
             double* __restrict__ part_a, double* __restrict__ part_b) {
-  blur_tile_body<MODE>(src, H, W, w, b, out, x, h, gamma, ch, axp, y, tau, part_a, part_b, blockIdx.x,
-                       blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x);
+  blur_tile_body<MODE, R>(src, H, W, w, b, out, x, h, gamma, ch, axp, y, tau, part_a, part_b, blockIdx.x,
+                          blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // Identity data term, 2D or 3D (nz slices of ny x nx).
@@ -176,9 +176,15 @@ template <int MODE>
 cudaError_t blur_launch(int H, int W, const float* src, const BlurW& w, const float* b, float* out,
                         const float* x, const float* h, float gamma, float ch, float* axp, float* y,
                         float tau, double* pa, double* pb, cudaStream_t s) {
-  if (w.R < 1 || w.R > RMAX) return cudaErrorInvalidValue;
   dim3 grid((W + BX - 1) / BX, (H + BY - 1) / BY);
-  blur_kernel<MODE><<<grid, BNT, 0, s>>>(src, H, W, w, b, out, x, h, gamma, ch, axp, y, tau, pa, pb);
+  switch (w.R) {
+#define TVS_BLUR_R(R_) \
+  case R_: blur_kernel<MODE, R_><<<grid, BNT, 0, s>>>(src, H, W, w, b, out, x, h, gamma, ch, axp, y, tau, pa, pb); break;
+    TVS_BLUR_R(1) TVS_BLUR_R(2) TVS_BLUR_R(3) TVS_BLUR_R(4) TVS_BLUR_R(5) TVS_BLUR_R(6) TVS_BLUR_R(7) TVS_BLUR_R(8)
+#undef TVS_BLUR_R
+    default:
+      return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
