@@ -213,6 +213,18 @@ def run_gpu(args):
                           "prox_calls": tr.prox_calls, "time_s": e0.elapsed_time(e1) / 1e3,
                           "final_rel_gap": float(gaps[-1]), "best_rel_gap": float(np.nanmin(gaps))}
 
+    # FISTA with the same warm-started prox (the paper's main comparator), one solve
+    x.copy_(b)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    _, ftr = tvs.fista_solve(prob, x, gamma, cfg.max_iter, cfg.n_inner, f_star=f_star, target=TARGET)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fista = {"reached": ftr.reached, "iterations": (ftr.reached_iter + 1) if ftr.reached else ftr.iters_run,
+             "prox_calls": ftr.prox_calls, "time_s": e0.elapsed_time(e1) / 1e3,
+             "best_rel_gap": float(np.nanmin((ftr.objective - f_star) / f_star))}
+
     # FGP kernel duration with CUDA events on the launching stream: tv_prox with
     # N inner iterations minus tv_prox with none, divided by N.
     z = b.clone()
@@ -301,6 +313,7 @@ def run_gpu(args):
         "speedup_vs_pgd": (statistics.mean(pgd_times) / statistics.mean(ps_times))
         if all(t.reached for t in pgd_tr) else None,
         "proxskip_by_p": per_p,
+        "fista": fista,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": None,
                      "kernel": ("fgp2d_rb_kernel" if fgp_cfg[2] >= 100 else "fgp2d_tb_kernel")

@@ -87,7 +87,15 @@ typedef struct {
  * iterations per prox, warm-started from the dual of the previous prox call;
  * max_iter >= 0 outer iterations.  When f_star > 0 the solve stops (within a
  * few iterations) once (F(x_k) - f_star) / f_star <= target_rel_gap.
- * objective_every >= 1: F is evaluated every that many iterations (NaN between). */
+ * objective_every >= 1: F is evaluated every that many iterations (NaN between).
+ * Checkpoint / resume: with resume = 1 the solve continues the previous solve of
+ * the same problem instead of starting afresh -- the control variate h and the
+ * warm-start TV dual kept in the problem are not reset, x_inout (and y_inout)
+ * hold the iterate it returned, and iteration numbering (hence the coins)
+ * starts at k0, the number of iterations already done.  A run of K iterations
+ * followed by a resumed run of K' iterations with k0 = K computes the same
+ * iterates as one run of K + K' iterations.  Not available for FISTA (its
+ * extrapolation state is not kept). */
 typedef struct {
   double gamma;
   double p;
@@ -98,10 +106,15 @@ typedef struct {
   double f_star;
   double target_rel_gap;
   int objective_every;
+  int resume;
+  long long k0;
+  double target_rel_dist;  /* > 0: also stop once ||x_k - u*|| / ||u*|| <= this
+                              (needs a reference set with tvs_problem_set_reference) */
 } tvs_fb_params;
 
 /* Primal-dual solvers (PDHG, PDHGSkip-2 = Algorithm 6) with the naming of
- * Algorithm 6: sigma is the primal and tau the dual step, sigma tau ||A||^2 <= 1. */
+ * Algorithm 6: sigma is the primal and tau the dual step, sigma tau ||A||^2 <= 1.
+ * resume / k0 as for tvs_fb_params. */
 typedef struct {
   double sigma;
   double tau;
@@ -113,6 +126,9 @@ typedef struct {
   double f_star;
   double target_rel_gap;
   int objective_every;
+  int resume;
+  long long k0;
+  double target_rel_dist;  /* as in tvs_fb_params */
 } tvs_pd_params;
 
 /* Solve record.  The caller owns the three host arrays (any may be NULL) and
@@ -134,12 +150,15 @@ typedef struct {
   long long fgp_launches; /* inner-iteration kernel launches (a 2D launch runs up
                              to 4 inner iterations)                              */
   long long fgp_pixel_iters; /* pixels x inner iterations processed by them    */
+  double* rel_dist;       /* host, may be NULL: ||x_{k+1} - u*|| / ||u*|| per iteration
+                             when the problem has a reference (NaN otherwise)   */
 } tvs_trace;
 
 /* ---- context ----------------------------------------------------------- */
 /* Creates a context on `device`.  `cuda_stream` is a cudaStream_t to launch on;
  * NULL creates a private non-blocking stream owned by the context. */
 tvs_status tvs_create(tvs_ctx** ctx, int device, void* cuda_stream);
+/* Destroys the context and every problem still attached to it. */
 tvs_status tvs_destroy(tvs_ctx* ctx);
 const char* tvs_last_error(void);
 /* Bytes of device memory currently held by the context and its problems. */
@@ -151,6 +170,11 @@ size_t tvs_device_bytes(const tvs_ctx* ctx);
  * holds a non-finite value. */
 tvs_status tvs_problem_create(tvs_ctx* ctx, const tvs_problem_desc* desc, const float* b,
                               tvs_mem b_mem, tvs_problem** out);
+/* Reference solution u* (image size; NULL removes it).  While set, every solve
+ * of the problem records the relative distance ||x_k - u*|| / ||u*|| -- the
+ * error measure of Sections 2 and 3 -- next to the objective, and can stop on it
+ * (target_rel_dist). */
+tvs_status tvs_problem_set_reference(tvs_problem* prob, const float* u_ref, tvs_mem mem);
 /* Replaces the problem's copy of b (same size). */
 tvs_status tvs_problem_set_data(tvs_problem* prob, const float* b, tvs_mem b_mem);
 tvs_status tvs_problem_destroy(tvs_problem* prob);
@@ -174,7 +198,8 @@ tvs_status tv_prox(tvs_ctx* ctx, int ndim, const int dims[3], const float* z, fl
  * rows per warp (+100 for the register-blocked kernel)}; {1, ., .} means one
  * iteration per launch (3D).  The first query (or the first prox / solve) of a
  * 2D shape times the candidates on the device and caches the fastest;
- * TVS_FGP_CONFIG="tb,cpl,rpw" in the environment forces one.  Not in the paper:
+ * TVS_FGP_CONFIG="tb,cpl,rpw" in the environment forces one, and
+ * TVS_TUNE_CACHE=path keeps the choices in a text file across processes.  Not in the paper:
  * a performance knob only (every configuration computes identical iterates). */
 tvs_status tvs_fgp_config(tvs_ctx* ctx, int ndim, const int dims[3], tvs_dual_dtype dual, int out[3]);
 
@@ -219,6 +244,13 @@ tvs_status pdhg_solve(tvs_problem* prob, const tvs_pd_params* prm, float* x_inou
 tvs_status pdhgskip_solve(tvs_problem* prob, const tvs_pd_params* prm, float* x_inout,
                           float* y_inout, tvs_mem mem, tvs_trace* trace);
 
+/* PDHGSkip-1 (Algorithm 5, Condat's skipping PDHG) with omega + 1 = 1/p: when
+ * theta_k = 0 the iteration skips the prox and both applications of A (only
+ * y <- prox_{tau f*}(y + tau A x_k) runs, from the stored A x_k).  Same arguments
+ * and trace as pdhgskip_solve. */
+tvs_status pdhgskip1_solve(tvs_problem* prob, const tvs_pd_params* prm, float* x_inout,
+                           float* y_inout, tvs_mem mem, tvs_trace* trace);
+
 /* ---- many independent problems at once -------------------------------------- */
 /* ProxSkip on n independent 2D problems (identity or blur operators; any sizes),
  * each with its own alpha (from its problem), gamma, p, seed, f_star and target
@@ -233,6 +265,28 @@ tvs_status pdhgskip_solve(tvs_problem* prob, const tvs_pd_params* prm, float* x_
 tvs_status proxskip_solve_batch(tvs_ctx* ctx, int n, tvs_problem* const* probs,
                                 const tvs_fb_params* prm, float* const* x_inout, tvs_mem mem,
                                 tvs_trace* traces);
+
+/* ---- the light-prox case: Dual-ROF (Section 2.1, Eq. 6) and Dual-Huber-ROF
+ * (Section 2.2, Eq. 8) -------------------------------------------------------- */
+/* min over |q_i| <= alpha of F(q) = 1/2 ||div q + b||^2 + (eps/(2 alpha)) ||q||^2
+ * (eps = 0: Dual-ROF), by projected gradient (p = 1) or ProxSkip with the
+ * pointwise alpha-ball projection (Eq. 7) as the prox (p < 1), step gamma
+ * (Section 2.1 uses 1/8).  dims = {nx, ny}; b is a 2D image; q_inout holds the
+ * two dual planes (vertical, horizontal), initial value in, final out; u_out
+ * (may be NULL) receives u = b + div q.  The trace's objective[k] = F(q_{k+1});
+ * f_star > 0 stops at the relative-gap target as for the other solvers. */
+typedef struct {
+  double alpha;
+  double eps;
+  double gamma;
+  double p;
+  uint64_t seed;
+  int max_iter;
+  double f_star;
+  double target_rel_gap;
+} tvs_rof_params;
+tvs_status dual_rof_solve(tvs_ctx* ctx, const int dims[2], const float* b, const tvs_rof_params* prm,
+                          float* q_inout, float* u_out, tvs_mem mem, tvs_trace* trace);
 
 /* ---- the coin (Algorithms 4 and 6) ----------------------------------------- */
 /* theta_k = [(w >> 11) < p 2^53], w the first word of Philox4x64-10 with counter

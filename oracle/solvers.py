@@ -176,3 +176,91 @@ def pdhgskip2(prob: Problem, x0, y0, sigma, tau, p, seed, K, n_inner, h0=None,
         if record:
             obj.append(prob.objective(x))
     return dict(x=x, y=y, h=h, dual=dual, objective=obj, coins=coins, prox_calls=n_prox)
+
+
+def pdhgskip1(prob: Problem, x0, y0, sigma, tau, p, seed, K, n_inner, record=True):
+    """Algorithm 5 (PDHGSkip-1, Condat's skipping PDHG) with omega + 1 = 1/p (Section 3.2).
+
+    x^_k = B_p(prox_{sigma g}(x_k - sigma K^T y_k) - x_k), where B_p(v) = v / p when
+    theta_k = 1 and 0 otherwise (the prox is evaluated only when theta_k = 1);
+    x_{k+1} = x_k + x^_k / (1 + omega);
+    y_{k+1} = prox_{tau f*}(y_k + tau K (x_{k+1} + x^_k)).
+    """
+    x = np.array(x0, dtype=np.float64)
+    y = np.array(y0, dtype=np.float64)
+    omega = 1.0 / p - 1.0
+    dual = None
+    obj, coins = [], []
+    n_prox = 0
+    for k in range(K):
+        theta = coin_mod.coin(seed, p, k)
+        coins.append(theta)
+        if theta:
+            u, dual = _prox_g(prob, x - sigma * prob.A.adjoint(y), sigma, n_inner, dual)
+            x_hat = (u - x) / p
+            n_prox += 1
+        else:
+            x_hat = np.zeros_like(x)
+        x_new = x + x_hat / (1.0 + omega)
+        y = prox_fconj(y + tau * prob.A.forward(x_new + x_hat), tau, prob.b)
+        x = x_new
+        if record:
+            obj.append(prob.objective(x))
+    return dict(x=x, y=y, dual=dual, objective=obj, coins=coins, prox_calls=n_prox)
+
+
+# ---------------------------------------------------------------- light-prox case
+def dual_rof_objective(q, b, alpha, eps=0.0):
+    """F(q) = 1/2 ||div q + b||^2 + (eps / (2 alpha)) ||q||^2 (Eq. 6 / Eq. 8 without
+    their constant term)."""
+    w = tv.div(q) + b
+    val = 0.5 * float(np.sum(w * w))
+    if eps > 0.0:
+        val += eps / (2.0 * alpha) * float(np.sum(q * q))
+    return val
+
+
+def _dual_rof_grad(q, b, alpha, eps):
+    """Gradient of F: -D(div q + b) + (eps / alpha) q  (div = -D^T)."""
+    g = -tv.grad(tv.div(q) + b)
+    if eps > 0.0:
+        g = g + (eps / alpha) * q
+    return g
+
+
+def dual_rof_projgd(b, alpha, gamma, K, eps=0.0, q0=None, record=True):
+    """Projected gradient on Dual-ROF (Section 2.1) or Dual-Huber-ROF (Section 2.2):
+    q_{k+1} = P_C(q_k - gamma grad F(q_k)), P_C the pointwise projection onto the
+    alpha-ball (Eq. 7).  The primal iterate is u_k = b + div q_k."""
+    b = np.asarray(b, dtype=np.float64)
+    q = np.zeros((b.ndim,) + b.shape) if q0 is None else np.array(q0, dtype=np.float64)
+    obj = []
+    for _ in range(K):
+        q = tv.project_ball(q - gamma * _dual_rof_grad(q, b, alpha, eps), alpha)
+        if record:
+            obj.append(dual_rof_objective(q, b, alpha, eps))
+    return dict(q=q, u=b + tv.div(q), objective=obj, coins=[1] * K, prox_calls=K)
+
+
+def dual_rof_proxskip(b, alpha, gamma, p, seed, K, eps=0.0, record=True):
+    """Algorithm 4 on Dual-ROF / Dual-Huber-ROF: f = F, g = indicator of C, so the
+    prox is P_C (prox of an indicator does not depend on the step)."""
+    b = np.asarray(b, dtype=np.float64)
+    q = np.zeros((b.ndim,) + b.shape)
+    h = np.zeros_like(q)
+    obj, coins = [], []
+    n_prox = 0
+    for k in range(K):
+        q_hat = q - gamma * (_dual_rof_grad(q, b, alpha, eps) - h)
+        theta = coin_mod.coin(seed, p, k)
+        coins.append(theta)
+        if theta:
+            q_new = tv.project_ball(q_hat - (gamma / p) * h, alpha)
+            n_prox += 1
+        else:
+            q_new = q_hat
+        h = h + (p / gamma) * (q_new - q_hat)
+        q = q_new
+        if record:
+            obj.append(dual_rof_objective(q, b, alpha, eps))
+    return dict(q=q, h=h, u=b + tv.div(q), objective=obj, coins=coins, prox_calls=n_prox)

@@ -8,10 +8,12 @@ loads the library and fails if it has not been built.
 from .api import (  # noqa: F401
     Context,
     Problem,
+    dual_rof_solve,
     SolveTrace,
     fista_solve,
     pd_steps,
     pdhg_solve,
+    pdhgskip1_solve,
     pdhgskip_solve,
     pgd_solve,
     proxskip_solve,

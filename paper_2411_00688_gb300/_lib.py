@@ -36,14 +36,22 @@ class FBParams(C.Structure):
     _fields_ = [("gamma", C.c_double), ("p", C.c_double), ("seed", C.c_uint64),
                 ("max_iter", C.c_int), ("n_inner", C.c_int), ("dual", C.c_int),
                 ("f_star", C.c_double), ("target_rel_gap", C.c_double),
-                ("objective_every", C.c_int)]
+                ("objective_every", C.c_int), ("resume", C.c_int), ("k0", C.c_longlong),
+                ("target_rel_dist", C.c_double)]
 
 
 class PDParams(C.Structure):
     _fields_ = [("sigma", C.c_double), ("tau", C.c_double), ("p", C.c_double),
                 ("seed", C.c_uint64), ("max_iter", C.c_int), ("n_inner", C.c_int),
                 ("dual", C.c_int), ("f_star", C.c_double), ("target_rel_gap", C.c_double),
-                ("objective_every", C.c_int)]
+                ("objective_every", C.c_int), ("resume", C.c_int), ("k0", C.c_longlong),
+                ("target_rel_dist", C.c_double)]
+
+
+class RofParams(C.Structure):
+    _fields_ = [("alpha", C.c_double), ("eps", C.c_double), ("gamma", C.c_double), ("p", C.c_double),
+                ("seed", C.c_uint64), ("max_iter", C.c_int), ("f_star", C.c_double),
+                ("target_rel_gap", C.c_double)]
 
 
 class Trace(C.Structure):
@@ -52,7 +60,8 @@ class Trace(C.Structure):
                 ("iters_run", C.c_int), ("prox_calls", C.c_int), ("reached", C.c_int),
                 ("reached_iter", C.c_int), ("time_to_target_s", C.c_double),
                 ("solve_ms", C.c_double), ("fgp_ms", C.c_double),
-                ("fgp_launches", C.c_longlong), ("fgp_pixel_iters", C.c_longlong)]
+                ("fgp_launches", C.c_longlong), ("fgp_pixel_iters", C.c_longlong),
+                ("rel_dist", C.POINTER(C.c_double))]
 
 
 # (name, restype, argtypes) of every entry point declared in include/tvs.h
@@ -63,6 +72,7 @@ SIGNATURES = [
     ("tvs_device_bytes", C.c_size_t, [C.c_void_p]),
     ("tvs_problem_create", C.c_int, [C.c_void_p, C.POINTER(ProblemDesc), C.c_void_p, C.c_int,
                                      C.POINTER(C.c_void_p)]),
+    ("tvs_problem_set_reference", C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     ("tvs_problem_set_data", C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     ("tvs_problem_destroy", C.c_int, [C.c_void_p]),
     ("tvs_op_apply", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
@@ -80,8 +90,12 @@ SIGNATURES = [
                              C.POINTER(Trace)]),
     ("pdhgskip_solve", C.c_int, [C.c_void_p, C.POINTER(PDParams), C.c_void_p, C.c_void_p, C.c_int,
                                  C.POINTER(Trace)]),
+    ("pdhgskip1_solve", C.c_int, [C.c_void_p, C.POINTER(PDParams), C.c_void_p, C.c_void_p, C.c_int,
+                                  C.POINTER(Trace)]),
     ("proxskip_solve_batch", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(FBParams),
                                        C.POINTER(C.c_void_p), C.c_int, C.POINTER(Trace)]),
+    ("dual_rof_solve", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_void_p, C.POINTER(RofParams), C.c_void_p,
+                                 C.c_void_p, C.c_int, C.POINTER(Trace)]),
     ("tvs_coin", C.c_int, [C.c_uint64, C.c_double, C.c_int64]),
     ("tvs_coin_schedule_device", C.c_int, [C.c_void_p, C.c_uint64, C.c_double, C.c_int64, C.c_int,
                                            C.c_void_p]),

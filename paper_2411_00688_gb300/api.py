@@ -90,25 +90,33 @@ class SolveTrace:
     fgp_ms: float
     fgp_launches: int
     fgp_pixel_iters: int
+    rel_dist: np.ndarray
+
+
+class _TraceBuffers:
+    def __init__(self, cap):
+        self.obj = np.full(cap, np.nan)
+        self.coins = np.zeros(cap, dtype=np.uint8)
+        self.ts = np.full(cap, np.nan)
+        self.dist = np.full(cap, np.nan)
 
 
 def _new_trace(cap):
-    obj = np.full(cap, np.nan)
-    coins = np.zeros(cap, dtype=np.uint8)
-    ts = np.full(cap, np.nan)
+    buf = _TraceBuffers(cap)
     tr = L.Trace()
     tr.cap = cap
-    tr.objective = obj.ctypes.data_as(C.POINTER(C.c_double))
-    tr.coins = coins.ctypes.data_as(C.POINTER(C.c_ubyte))
-    tr.t_s = ts.ctypes.data_as(C.POINTER(C.c_double))
-    return tr, obj, coins, ts
+    tr.objective = buf.obj.ctypes.data_as(C.POINTER(C.c_double))
+    tr.coins = buf.coins.ctypes.data_as(C.POINTER(C.c_ubyte))
+    tr.t_s = buf.ts.ctypes.data_as(C.POINTER(C.c_double))
+    tr.rel_dist = buf.dist.ctypes.data_as(C.POINTER(C.c_double))
+    return tr, buf
 
 
-def _finish_trace(tr, obj, coins, ts):
+def _finish_trace(tr, buf):
     n = tr.iters_run
-    return SolveTrace(obj[:n].copy(), coins[:n].copy(), ts[:n].copy(), tr.iters_run, tr.prox_calls,
+    return SolveTrace(buf.obj[:n].copy(), buf.coins[:n].copy(), buf.ts[:n].copy(), tr.iters_run, tr.prox_calls,
                       bool(tr.reached), tr.reached_iter, tr.time_to_target_s, tr.solve_ms, tr.fgp_ms,
-                      tr.fgp_launches, tr.fgp_pixel_iters)
+                      tr.fgp_launches, tr.fgp_pixel_iters, buf.dist[:n].copy())
 
 
 class Problem:
@@ -157,6 +165,16 @@ class Problem:
     def handle(self):
         return self._h
 
+    def set_reference(self, u_ref):
+        """Reference solution u*: solves then record ||x_k - u*|| / ||u*|| (None removes it)."""
+        if u_ref is None:
+            L.check(L.lib().tvs_problem_set_reference(self._h, None, L.MEM_DEVICE))
+            return
+        ptr, mem, keep = _arr(u_ref, "u_ref")
+        if mem == L.MEM_DEVICE:
+            _sync_torch()
+        L.check(L.lib().tvs_problem_set_reference(self._h, C.c_void_p(ptr), mem))
+
     def set_data(self, b):
         ptr, mem, keep = _arr(b, "b")
         if mem == L.MEM_DEVICE:
@@ -164,9 +182,10 @@ class Problem:
         L.check(L.lib().tvs_problem_set_data(self._h, C.c_void_p(ptr), mem))
 
     def close(self):
-        if self._h:
+        # a closed context has already destroyed its problems
+        if self._h and self.ctx.handle:
             L.lib().tvs_problem_destroy(self._h)
-            self._h = C.c_void_p()
+        self._h = C.c_void_p()
 
     def __del__(self):
         try:
@@ -245,16 +264,17 @@ def tv_prox_noalloc(z, u, lam: float, n_iter: int, dual: str = "f32", dual_state
 
 
 def _fb(fn_name, prob, x, gamma, max_iter, n_inner, p=1.0, seed=0, dual="f32", f_star=0.0,
-        target=0.0, every=1):
+        target=0.0, every=1, resume=False, k0=0, target_dist=0.0):
     prm = L.FBParams(gamma=float(gamma), p=float(p), seed=int(seed) & ((1 << 64) - 1),
                      max_iter=int(max_iter), n_inner=int(n_inner), dual=L.DUAL[dual],
-                     f_star=float(f_star), target_rel_gap=float(target), objective_every=int(every))
+                     f_star=float(f_star), target_rel_gap=float(target), objective_every=int(every),
+                     resume=int(bool(resume)), k0=int(k0), target_rel_dist=float(target_dist))
     ptr, mem, keep = _arr(x, "x")
     if mem == L.MEM_DEVICE:
         _sync_torch()
-    tr, obj, coins, ts = _new_trace(max(int(max_iter), 1))
+    tr, buf = _new_trace(max(int(max_iter), 1))
     L.check(getattr(L.lib(), fn_name)(prob.handle, C.byref(prm), C.c_void_p(ptr), mem, C.byref(tr)))
-    return x, _finish_trace(tr, obj, coins, ts)
+    return x, _finish_trace(tr, buf)
 
 
 def pgd_solve(prob, x, gamma, max_iter, n_inner, **kw):
@@ -305,28 +325,29 @@ def proxskip_solve_batch(ctx: Context, probs, xs, gammas, ps, seeds, max_iter, n
     tr = (L.Trace * n)()
     keep_tr = []
     for i in range(n):
-        t, obj, coins, ts = _new_trace(cap)
+        t, buf = _new_trace(cap)
         tr[i] = t
-        keep_tr.append((obj, coins, ts))
+        keep_tr.append(buf)
     L.check(L.lib().proxskip_solve_batch(ctx.handle, n, handles, prm, ptrs, mem, tr))
-    return xs, [_finish_trace(tr[i], *keep_tr[i]) for i in range(n)]
+    return xs, [_finish_trace(tr[i], keep_tr[i]) for i in range(n)]
 
 
 def _pd(fn_name, prob, x, y, sigma, tau, max_iter, n_inner, p=1.0, seed=0, dual="f32", f_star=0.0,
-        target=0.0, every=1):
+        target=0.0, every=1, resume=False, k0=0, target_dist=0.0):
     prm = L.PDParams(sigma=float(sigma), tau=float(tau), p=float(p), seed=int(seed) & ((1 << 64) - 1),
                      max_iter=int(max_iter), n_inner=int(n_inner), dual=L.DUAL[dual],
-                     f_star=float(f_star), target_rel_gap=float(target), objective_every=int(every))
+                     f_star=float(f_star), target_rel_gap=float(target), objective_every=int(every),
+                     resume=int(bool(resume)), k0=int(k0), target_rel_dist=float(target_dist))
     px, mem, kx = _arr(x, "x")
     py, mem_y, ky = _arr(y, "y")
     if mem != mem_y:
         raise ValueError("x and y must live in the same memory")
     if mem == L.MEM_DEVICE:
         _sync_torch()
-    tr, obj, coins, ts = _new_trace(max(int(max_iter), 1))
+    tr, buf = _new_trace(max(int(max_iter), 1))
     L.check(getattr(L.lib(), fn_name)(prob.handle, C.byref(prm), C.c_void_p(px), C.c_void_p(py), mem,
                                       C.byref(tr)))
-    return x, y, _finish_trace(tr, obj, coins, ts)
+    return x, y, _finish_trace(tr, buf)
 
 
 def pdhg_solve(prob, x, y, sigma, tau, max_iter, n_inner, **kw):
@@ -337,6 +358,37 @@ def pdhg_solve(prob, x, y, sigma, tau, max_iter, n_inner, **kw):
 def pdhgskip_solve(prob, x, y, sigma, tau, p, seed, max_iter, n_inner, **kw):
     """PDHGSkip-2 (Algorithm 6)."""
     return _pd("pdhgskip_solve", prob, x, y, sigma, tau, max_iter, n_inner, p=p, seed=seed, **kw)
+
+
+def pdhgskip1_solve(prob, x, y, sigma, tau, p, seed, max_iter, n_inner, **kw):
+    """PDHGSkip-1 (Algorithm 5, omega + 1 = 1/p)."""
+    return _pd("pdhgskip1_solve", prob, x, y, sigma, tau, max_iter, n_inner, p=p, seed=seed, **kw)
+
+
+def dual_rof_solve(ctx: Context, b, q, alpha, gamma, max_iter, p=1.0, seed=0, eps=0.0, u=None,
+                   f_star=0.0, target=0.0):
+    """Projected gradient (p = 1) or ProxSkip on Dual-ROF / Dual-Huber-ROF.
+
+    b: image (H, W); q: dual field (2, H, W), initial value in, final out; u: optional
+    output for b + div q.  All CUDA tensors or all numpy float32 arrays."""
+    prm = L.RofParams(alpha=float(alpha), eps=float(eps), gamma=float(gamma), p=float(p),
+                      seed=int(seed) & ((1 << 64) - 1), max_iter=int(max_iter), f_star=float(f_star),
+                      target_rel_gap=float(target))
+    pb, mem, kb = _arr(b, "b")
+    pq, mem_q, kq = _arr(q, "q")
+    pu, mem_u = (None, mem)
+    if u is not None:
+        pu, mem_u, ku = _arr(u, "u")
+    if len({mem, mem_q, mem_u}) != 1:
+        raise ValueError("b, q and u must live in the same memory")
+    if mem == L.MEM_DEVICE:
+        _sync_torch()
+    H, W = b.shape
+    dims = (C.c_int * 2)(W, H)
+    tr, buf = _new_trace(max(int(max_iter), 1))
+    L.check(L.lib().dual_rof_solve(ctx.handle, dims, C.c_void_p(pb), C.byref(prm), C.c_void_p(pq),
+                                   C.c_void_p(pu) if pu is not None else None, mem, C.byref(tr)))
+    return q, u, _finish_trace(tr, buf)
 
 
 def tvs_coin(seed: int, p: float, k: int) -> int:

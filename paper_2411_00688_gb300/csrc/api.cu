@@ -85,6 +85,7 @@ struct tvs_ctx {
     FgpConfig cfg;
   };
   std::vector<Tuned> tuned;  // autotuner cache, one entry per 2D shape and dual type
+  std::vector<tvs_problem*> problems;  // live problems, destroyed with the context
 };
 
 struct tvs_problem {
@@ -95,6 +96,7 @@ struct tvs_problem {
   BlurW bw{};
   CTGeom geom{};
   float4* angle_tab = nullptr;
+  float4* angle_tab2 = nullptr;
   float* xt = nullptr;
   float* b = nullptr;
   float* x[2] = {nullptr, nullptr};
@@ -116,6 +118,10 @@ struct tvs_problem {
   int* done_host = nullptr;               // pinned, mapped
   int* done_host_dev = nullptr;
   int* count = nullptr;
+  float* uref = nullptr;        // reference solution (tvs_problem_set_reference)
+  double uref_norm2 = 0.0;
+  double* part_c = nullptr;     // partials of ||x - uref||^2
+  double* dist_dev = nullptr;   // relative distance per trace entry
   size_t bytes = 0;
 };
 
@@ -225,6 +231,29 @@ tvs_status fgp_config_for(tvs_ctx* C, const Dims& d, int dtype, const float* z, 
       *out = t.cfg;
       return TVS_OK;
     }
+  // optional on-disk cache (TVS_TUNE_CACHE=path): lines "nx ny dtype tb cpl rpw"
+  const char* cache = getenv("TVS_TUNE_CACHE");
+  if (cache && cache[0]) {
+    if (FILE* f = fopen(cache, "r")) {
+      int a, b, c, t0, t1, t2;
+      bool found = false;
+      while (fscanf(f, "%d %d %d %d %d %d", &a, &b, &c, &t0, &t1, &t2) == 6) {
+        FgpConfig k;
+        k.tb = t0;
+        k.cpl = t1;
+        k.rpw = t2;
+        if (a == d.nx && b == d.ny && c == dtype && fgp_config_valid(k)) {
+          *out = k;
+          found = true;
+        }
+      }
+      fclose(f);
+      if (found) {
+        C->tuned.push_back({d.nx, d.ny, dtype, *out});
+        return TVS_OK;
+      }
+    }
+  }
   const int cands[][3] = {{4, 1, 105}, {4, 2, 105}, {4, 1, 5}, {4, 1, 108}};
   const float betas[4] = {0.f, 0.f, 0.2f, 0.4f};
   cudaStream_t s = C->stream;
@@ -233,33 +262,49 @@ tvs_status fgp_config_for(tvs_ctx* C, const Dims& d, int dtype, const float* z, 
   CUDA_TRY(cudaEventCreate(&e1));
   FgpConfig best;
   float best_ms = 1e30f;
-  for (const auto& k : cands) {
-    FgpConfig c;
-    c.tb = k[0];
-    c.cpl = k[1];
-    c.rpw = k[2];
-    float ms = 0.f;
-    cudaError_t e = launch_fgp_block(c, d, z, home, home, scratch0, scratch1, 0.1f, 1.25f, betas, 4, dtype,
-                                     false, s);
-    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-    for (int r = 0; r < 2 && e == cudaSuccess; ++r)
-      e = launch_fgp_block(c, d, z, home, home, scratch0, scratch1, 0.1f, 1.25f, betas, 4, dtype, false, s);
-    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
-    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-    if (e != cudaSuccess) {
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      return fail(TVS_ECUDA, "fgp autotune: %s", cudaGetErrorString(e));
-    }
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = c;
+  // three rounds over the candidates, each timing 6 launches after a warm-up;
+  // a candidate's score is its best round (robust against clock ramps and noise)
+  const int ncand = (int)(sizeof(cands) / sizeof(cands[0]));
+  std::vector<float> score(ncand, 1e30f);
+  for (int round = 0; round < 3; ++round) {
+    for (int ci = 0; ci < ncand; ++ci) {
+      FgpConfig c;
+      c.tb = cands[ci][0];
+      c.cpl = cands[ci][1];
+      c.rpw = cands[ci][2];
+      float ms = 0.f;
+      cudaError_t e = launch_fgp_block(c, d, z, home, home, scratch0, scratch1, 0.1f, 1.25f, betas, 4, dtype,
+                                       false, s);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+      for (int r = 0; r < 6 && e == cudaSuccess; ++r)
+        e = launch_fgp_block(c, d, z, home, home, scratch0, scratch1, 0.1f, 1.25f, betas, 4, dtype, false, s);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return fail(TVS_ECUDA, "fgp autotune: %s", cudaGetErrorString(e));
+      }
+      score[ci] = std::min(score[ci], ms);
     }
   }
+  for (int ci = 0; ci < ncand; ++ci)
+    if (score[ci] < best_ms) {
+      best_ms = score[ci];
+      best.tb = cands[ci][0];
+      best.cpl = cands[ci][1];
+      best.rpw = cands[ci][2];
+    }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   C->tuned.push_back({d.nx, d.ny, dtype, best});
+  if (cache && cache[0]) {
+    if (FILE* f = fopen(cache, "a")) {
+      fprintf(f, "%d %d %d %d %d %d\n", d.nx, d.ny, dtype, best.tb, best.cpl, best.rpw);
+      fclose(f);
+    }
+  }
   *out = best;
   return TVS_OK;
 }
@@ -279,7 +324,7 @@ tvs_status copy_out(float* dst, const float* src, size_t n, tvs_mem mem, cudaStr
 tvs_status ensure_trace(tvs_problem* P, int K) {
   if (K + 1 <= P->trace_cap) return TVS_OK;
   if (P->trace_cap > 0) {
-    const size_t old = (size_t)P->trace_cap * (sizeof(double) + 2 * sizeof(unsigned long long) + sizeof(float)) +
+    const size_t old = (size_t)P->trace_cap * (2 * sizeof(double) + 2 * sizeof(unsigned long long) + sizeof(float)) +
                        sizeof(unsigned long long);
     P->bytes -= old;
     P->ctx->bytes -= old;
@@ -288,6 +333,8 @@ tvs_status ensure_trace(tvs_problem* P, int K) {
   dfree(P->ts_dev);
   dfree(P->fgp_ts);
   dfree(P->beta_dev);
+  dfree(P->dist_dev);
+  P->dist_dev = nullptr;
   P->obj_dev = nullptr;
   P->ts_dev = nullptr;
   P->fgp_ts = nullptr;
@@ -297,6 +344,7 @@ tvs_status ensure_trace(tvs_problem* P, int K) {
   TVS_TRY(palloc(P, &P->ts_dev, cap + 1));
   TVS_TRY(palloc(P, &P->fgp_ts, 2 * (size_t)cap));
   TVS_TRY(palloc(P, &P->beta_dev, cap));
+  TVS_TRY(palloc(P, &P->dist_dev, cap));
   P->trace_cap = cap;
   return TVS_OK;
 }
@@ -361,17 +409,35 @@ tvs_status objective_parts(tvs_problem* P, const float* x, double* pa, double* p
 
 // PDHG pieces.  Backward step: out = x - sigma A^T y + ch h, TV(x) partials -> part_b.
 tvs_status pd_backward(tvs_problem* P, const float* x, float* out, const float* h, float sigma,
-                       float ch, cudaStream_t s) {
+                       float ch, cudaStream_t s, bool tv_partials = true) {
+  const Dims& d = P->dims;
+  double* pb = tv_partials ? P->part_b : nullptr;
+  switch (P->desc.op.kind) {
+    case TVS_OP_GAUSS_BLUR:
+      CUDA_TRY(launch_blur_step(d.ny, d.nx, P->y, x, h, out, P->bw, sigma, ch, pb, s));
+      break;
+    case TVS_OP_PARALLEL_BEAM:
+      CUDA_TRY(launch_ct_backward(P->geom, P->y, x, h, out, sigma, ch, pb, s));
+      break;
+    default:
+      CUDA_TRY(launch_axpy_step(d, P->y, x, h, out, sigma, ch, pb, s));
+  }
+  return TVS_OK;
+}
+
+// PDHGSkip-1 dual step from x^ (xh): A x_{k+1} = A x_k + p A x^ kept in axp,
+// y <- prox(y + tau A(x_{k+1} + x^)), data partials of F(x_{k+1}).
+tvs_status pd1_forward(tvs_problem* P, const float* xh, float prob_p, float tau, cudaStream_t s) {
   const Dims& d = P->dims;
   switch (P->desc.op.kind) {
     case TVS_OP_GAUSS_BLUR:
-      CUDA_TRY(launch_blur_step(d.ny, d.nx, P->y, x, h, out, P->bw, sigma, ch, P->part_b, s));
+      CUDA_TRY(launch_blur_pd1_dual(d.ny, d.nx, xh, P->axp, P->y, P->b, P->bw, prob_p, tau, P->part_a, s));
       break;
     case TVS_OP_PARALLEL_BEAM:
-      CUDA_TRY(launch_ct_backward(P->geom, P->y, x, h, out, sigma, ch, P->part_b, s));
+      CUDA_TRY(launch_ct_forward(P->geom, xh, P->axp, P->y, P->b, tau, P->part_a, CT_FWD_PD1, s, prob_p));
       break;
     default:
-      CUDA_TRY(launch_axpy_step(d, P->y, x, h, out, sigma, ch, P->part_b, s));
+      CUDA_TRY(launch_pd1_dual_pointwise(P->m, xh, P->axp, P->y, P->b, prob_p, tau, P->part_a, s));
   }
   return TVS_OK;
 }
@@ -474,8 +540,19 @@ tvs_status begin_solve(tvs_problem* P, int K, int flags_counter_start) {
   int f[4] = {0, -1, flags_counter_start, 0};
   CUDA_TRY(cudaMemcpyAsync(P->flags, f, sizeof(f), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemsetAsync(P->obj_dev, 0xff, sizeof(double) * (K + 1), s));  // NaN pattern
+  CUDA_TRY(cudaMemsetAsync(P->dist_dev, 0xff, sizeof(double) * (K + 1), s));
   CUDA_TRY(cudaEventRecord(P->ctx->ev_start, s));
   CUDA_TRY(launch_timestamp(P->ts_dev + P->trace_cap, s));
+  return TVS_OK;
+}
+
+// Distance of x to the problem's reference, recorded at the trace index the
+// preceding objective reduction used (no-op without a reference).
+tvs_status track_distance(tvs_problem* P, const float* x, double target, cudaStream_t s) {
+  if (!P->uref) return TVS_OK;
+  CUDA_TRY(launch_dist_partials(P->n, x, P->uref, P->part_c, s));
+  CUDA_TRY(launch_dist_record(P->part_c, pointwise_blocks(P->n), P->uref_norm2, P->dist_dev, target, P->flags,
+                              P->done_host_dev, s));
   return TVS_OK;
 }
 
@@ -512,6 +589,11 @@ tvs_status finish_solve(tvs_problem* P, int K, const LoopState& ls,
     CUDA_TRY(cudaMemcpy(f.data(), P->fgp_ts, sizeof(unsigned long long) * f.size(), cudaMemcpyDeviceToHost));
     for (int i = 0; i < nprox; ++i) fgp_ms += (double)(f[2 * i + 1] - f[2 * i]) * 1e-6;
   }
+  std::vector<double> dist;
+  if (P->uref && iters > 0 && tr && tr->rel_dist) {
+    dist.resize(iters);
+    CUDA_TRY(cudaMemcpy(dist.data(), P->dist_dev, sizeof(double) * iters, cudaMemcpyDeviceToHost));
+  }
   bool bad = false;
   for (int k = 0; k < iters; ++k) {
     // NaN entries between evaluations carry the 0xff pattern; non-finite
@@ -537,6 +619,7 @@ tvs_status finish_solve(tvs_problem* P, int K, const LoopState& ls,
       if (tr->objective) tr->objective[k] = obj[k];
       if (tr->coins) tr->coins[k] = coins[k];
       if (tr->t_s) tr->t_s[k] = std::isnan(obj[k]) ? NAN : (double)(ts[k] - t0) * 1e-9;
+      if (tr->rel_dist) tr->rel_dist[k] = dist.empty() ? NAN : dist[k];
     }
   }
   if (bad) return fail(TVS_ENUMERIC, "non-finite objective during the solve");
@@ -562,6 +645,7 @@ tvs_status fb_solve(tvs_problem* P, const tvs_fb_params* prm, float* x_io, tvs_m
   TVS_TRY(check_common(P, prm->max_iter, prm->n_inner, prm->dual, prm->f_star, prm->target_rel_gap,
                        prm->objective_every, x_io));
   if (!(prm->gamma > 0) || !is_fin(prm->gamma)) return fail(TVS_EINVAL, "gamma must be > 0");
+  if (!(prm->target_rel_dist >= 0) || !is_fin(prm->target_rel_dist)) return fail(TVS_EINVAL, "invalid target_rel_dist");
   const double p = kind == FB_PROXSKIP ? prm->p : 1.0;
   if (!(p > 0.0 && p <= 1.0)) return fail(TVS_EINVAL, "p must lie in (0, 1]");
   if (mem != TVS_MEM_DEVICE && mem != TVS_MEM_HOST) return fail(TVS_EINVAL, "invalid mem kind");
@@ -577,15 +661,18 @@ tvs_status fb_solve(tvs_problem* P, const tvs_fb_params* prm, float* x_io, tvs_m
   const Dims& d = P->dims;
   const std::vector<float> betas = fgp_betas(N);
 
+  if (prm->resume && kind == FB_FISTA) return fail(TVS_EUNSUPPORTED, "FISTA cannot resume");
+  if (prm->resume && prm->k0 < 0) return fail(TVS_EINVAL, "k0 must be >= 0");
+  const long long k0 = prm->resume ? prm->k0 : 0;
   std::vector<unsigned char> coins(K, 1);
   if (kind == FB_PROXSKIP)
-    for (int k = 0; k < K; ++k) coins[k] = (unsigned char)tvs_coin(prm->seed, p, k);
+    for (int k = 0; k < K; ++k) coins[k] = (unsigned char)tvs_coin(prm->seed, p, k0 + k);
 
   TVS_TRY(begin_solve(P, K, kind == FB_FISTA ? 0 : -1));
   TVS_TRY(copy_in(P->x[0], x_io, P->n, mem, s));
-  TVS_TRY(zero_dual(P, dtype));
+  if (!prm->resume) TVS_TRY(zero_dual(P, dtype));
   float* aux = P->h;  // control variate h (ProxSkip) or extrapolated point y (FISTA)
-  if (kind == FB_PROXSKIP) CUDA_TRY(cudaMemsetAsync(P->h, 0, P->n * sizeof(float), s));
+  if (kind == FB_PROXSKIP && !prm->resume) CUDA_TRY(cudaMemsetAsync(P->h, 0, P->n * sizeof(float), s));
   if (kind == FB_FISTA) {
     CUDA_TRY(cudaMemcpyAsync(aux, P->x[0], P->n * sizeof(float), cudaMemcpyDeviceToDevice, s));
     std::vector<float> bx(K > 0 ? K : 1, 0.f);
@@ -619,10 +706,12 @@ tvs_status fb_solve(tvs_problem* P, const tvs_fb_params* prm, float* x_io, tvs_m
         } else {
           TVS_TRY(fb_step(P, kind == FB_FISTA ? aux : xc, P->z, nullptr, fgamma, 0.f, s));
         }
-        if (kind != FB_FISTA)
+        if (kind != FB_FISTA) {
           CUDA_TRY(launch_reduce_record(P->part_a, na, P->part_b, nb, alpha, every, P->obj_dev,
                                         P->ts_dev, prm->f_star, prm->target_rel_gap, P->flags,
                                         P->done_host_dev, nullptr, s));
+          TVS_TRY(track_distance(P, xc, prm->target_rel_dist, s));
+        }
         if (c == 1) {
           int fin = 0;
           CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 0, s));
@@ -639,6 +728,7 @@ tvs_status fb_solve(tvs_problem* P, const tvs_fb_params* prm, float* x_io, tvs_m
           CUDA_TRY(launch_reduce_record(P->part_a, a, P->part_b, b, alpha, every, P->obj_dev,
                                         P->ts_dev, prm->f_star, prm->target_rel_gap, P->flags,
                                         P->done_host_dev, nullptr, s));
+          TVS_TRY(track_distance(P, xn, prm->target_rel_dist, s));
         }
         return TVS_OK;
       }));
@@ -653,6 +743,7 @@ tvs_status fb_solve(tvs_problem* P, const tvs_fb_params* prm, float* x_io, tvs_m
     CUDA_TRY(launch_reduce_record(P->part_a, a, P->part_b, b, alpha, 1, P->obj_dev, P->ts_dev,
                                   prm->f_star, prm->target_rel_gap, P->flags, P->done_host_dev,
                                   nullptr, s));
+    TVS_TRY(track_distance(P, xfin, prm->target_rel_dist, s));
   }
   TVS_TRY(copy_out(x_io, xfin, P->n, mem, s));
   return finish_solve(P, K, ls, coins, use_prox ? N : 0, fcfg, tr);
@@ -666,6 +757,7 @@ tvs_status pd_solve(tvs_problem* P, const tvs_pd_params* prm, float* x_io, float
   if (!y_io) return fail(TVS_EINVAL, "null y_inout");
   if (!(prm->sigma > 0) || !(prm->tau > 0) || !is_fin(prm->sigma) || !is_fin(prm->tau))
     return fail(TVS_EINVAL, "sigma and tau must be > 0");
+  if (!(prm->target_rel_dist >= 0) || !is_fin(prm->target_rel_dist)) return fail(TVS_EINVAL, "invalid target_rel_dist");
   const double p = skip ? prm->p : 1.0;
   if (!(p > 0.0 && p <= 1.0)) return fail(TVS_EINVAL, "p must lie in (0, 1]");
   if (mem != TVS_MEM_DEVICE && mem != TVS_MEM_HOST) return fail(TVS_EINVAL, "invalid mem kind");
@@ -681,15 +773,17 @@ tvs_status pd_solve(tvs_problem* P, const tvs_pd_params* prm, float* x_io, float
   cudaStream_t s = C->stream;
   const Dims& d = P->dims;
   const std::vector<float> betas = fgp_betas(N);
+  if (prm->resume && prm->k0 < 0) return fail(TVS_EINVAL, "k0 must be >= 0");
+  const long long k0 = prm->resume ? prm->k0 : 0;
   std::vector<unsigned char> coins(K, 1);
   if (skip)
-    for (int k = 0; k < K; ++k) coins[k] = (unsigned char)tvs_coin(prm->seed, p, k);
+    for (int k = 0; k < K; ++k) coins[k] = (unsigned char)tvs_coin(prm->seed, p, k0 + k);
 
   TVS_TRY(begin_solve(P, K, -1));
   TVS_TRY(copy_in(P->x[0], x_io, P->n, mem, s));
   TVS_TRY(copy_in(P->y, y_io, P->m, mem, s));
-  TVS_TRY(zero_dual(P, dtype));
-  if (skip) CUDA_TRY(cudaMemsetAsync(P->h, 0, P->n * sizeof(float), s));
+  if (!prm->resume) TVS_TRY(zero_dual(P, dtype));
+  if (skip && !prm->resume) CUDA_TRY(cudaMemsetAsync(P->h, 0, P->n * sizeof(float), s));
   TVS_TRY(pd_forward(P, P->x[0], (float)tau, true, s));
   FgpConfig fcfg;
   TVS_TRY(fgp_config_for(C, d, dtype, P->x[0], P->dual[0], P->dual[2], P->dual[3], &fcfg));
@@ -711,6 +805,7 @@ tvs_status pd_solve(tvs_problem* P, const tvs_pd_params* prm, float* x_io, float
         CUDA_TRY(launch_reduce_record(P->part_a, na, P->part_b, nb, alpha, every, P->obj_dev,
                                       P->ts_dev, prm->f_star, prm->target_rel_gap, P->flags,
                                       P->done_host_dev, nullptr, s));
+        TVS_TRY(track_distance(P, xc, prm->target_rel_dist, s));
         if (c == 1) {
           int fin = 0;
           CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 0, s));
@@ -734,8 +829,101 @@ tvs_status pd_solve(tvs_problem* P, const tvs_pd_params* prm, float* x_io, float
     CUDA_TRY(launch_reduce_record(P->part_a, na, P->part_b, pointwise_blocks(P->n), alpha, 1,
                                   P->obj_dev, P->ts_dev, prm->f_star, prm->target_rel_gap, P->flags,
                                   P->done_host_dev, nullptr, s));
+    TVS_TRY(track_distance(P, xfin, prm->target_rel_dist, s));
   }
   TVS_TRY(copy_out(x_io, xfin, P->n, mem, s));
+  TVS_TRY(copy_out(y_io, P->y, P->m, mem, s));
+  return finish_solve(P, K, ls, coins, use_prox ? N : 0, fcfg, tr);
+}
+
+// PDHGSkip-1 (Algorithm 5, omega + 1 = 1/p).  Iteration k with theta_k = 1:
+//   z = x - sigma A^T y; u = prox_{sigma g}(z) (N FGP iterations, warm dual);
+//   x^ = (u - x)/p; x <- x + p x^ (in place); A x <- A x + p A x^;
+//   y <- prox_{tau f*}(y + tau A(x + x^)); TV partials of the new x.
+// With theta_k = 0, x^ = 0: x and A x are unchanged and y <- prox(y + tau A x) is a
+// pointwise update from the stored A x (no prox, no projector application).
+tvs_status pd1_solve(tvs_problem* P, const tvs_pd_params* prm, float* x_io, float* y_io, tvs_mem mem,
+                     tvs_trace* tr) {
+  if (!prm) return fail(TVS_EINVAL, "null params");
+  TVS_TRY(check_common(P, prm->max_iter, prm->n_inner, prm->dual, prm->f_star, prm->target_rel_gap,
+                       prm->objective_every, x_io));
+  if (!y_io) return fail(TVS_EINVAL, "null y_inout");
+  if (!(prm->sigma > 0) || !(prm->tau > 0) || !is_fin(prm->sigma) || !is_fin(prm->tau))
+    return fail(TVS_EINVAL, "sigma and tau must be > 0");
+  const double p = prm->p;
+  if (!(p > 0.0 && p <= 1.0)) return fail(TVS_EINVAL, "p must lie in (0, 1]");
+  if (mem != TVS_MEM_DEVICE && mem != TVS_MEM_HOST) return fail(TVS_EINVAL, "invalid mem kind");
+  if (P->dims.ndim != 2) return fail(TVS_EUNSUPPORTED, "primal-dual solvers are 2D");
+  const int K = prm->max_iter, N = prm->n_inner, every = prm->objective_every < 1 ? 1 : prm->objective_every;
+  const int dtype = prm->dual;
+  const bool nonneg = P->desc.nonneg != 0;
+  const double sigma = prm->sigma, tau = prm->tau, alpha = P->desc.alpha;
+  const double lam_d = sigma * alpha;
+  const float lam = (float)lam_d;
+  const bool use_prox = lam_d > 0.0;
+  tvs_ctx* C = P->ctx;
+  cudaStream_t s = C->stream;
+  const Dims& d = P->dims;
+  const std::vector<float> betas = fgp_betas(N);
+  if (prm->resume && prm->k0 < 0) return fail(TVS_EINVAL, "k0 must be >= 0");
+  const long long k0 = prm->resume ? prm->k0 : 0;
+  std::vector<unsigned char> coins(K);
+  for (int k = 0; k < K; ++k) coins[k] = (unsigned char)tvs_coin(prm->seed, p, k0 + k);
+
+  TVS_TRY(begin_solve(P, K, -1));
+  TVS_TRY(copy_in(P->x[0], x_io, P->n, mem, s));
+  TVS_TRY(copy_in(P->y, y_io, P->m, mem, s));
+  if (!prm->resume) {
+    TVS_TRY(zero_dual(P, dtype));
+    TVS_TRY(pd_forward(P, P->x[0], (float)tau, true, s));
+    CUDA_TRY(launch_tv_partials(d, P->x[0], P->part_b, s));
+  }
+  // on resume, A x_k (kept up to date incrementally, A x += p A x^) and the
+  // objective partials of x_k are the ones the previous solve left in the problem
+  FgpConfig fcfg;
+  TVS_TRY(fgp_config_for(C, d, dtype, P->x[0], P->dual[0], P->dual[2], P->dual[3], &fcfg));
+  const int na = pd_parts_a(P), nb = pointwise_blocks(P->n);
+  float* x = P->x[0];
+  GraphSet G;
+  for (int c = 0; c < 2; ++c) {
+    TVS_TRY(capture(s, &G.exec[c][0], [&]() -> tvs_status {
+      CUDA_TRY(launch_reduce_record(P->part_a, na, P->part_b, nb, alpha, every, P->obj_dev, P->ts_dev,
+                                    prm->f_star, prm->target_rel_gap, P->flags, P->done_host_dev, nullptr, s));
+      TVS_TRY(track_distance(P, x, prm->target_rel_dist, s));
+      if (c == 0) {
+        CUDA_TRY(launch_pd1_dual_pointwise(P->m, nullptr, P->axp, P->y, P->b, (float)p, (float)tau, nullptr, s));
+        return TVS_OK;
+      }
+      TVS_TRY(pd_backward(P, x, P->z, nullptr, (float)sigma, 0.f, s, false));
+      int fin = 0;
+      CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 0, s));
+      if (use_prox) TVS_TRY(launch_fgp_sequence(fcfg, d, P->z, P->dual, N, betas, lam, dtype, nonneg, s, &fin));
+      CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 1, s));
+      CUDA_TRY(launch_fgp_finalize_pd1(d, P->z, P->dual[fin], dtype, use_prox ? lam : 0.f, nonneg, (float)p, x,
+                                       P->h, fin != 0 ? P->dual[0] : nullptr, s));
+      TVS_TRY(pd1_forward(P, P->h, (float)p, (float)tau, s));
+      CUDA_TRY(launch_tv_partials(d, x, P->part_b, s));
+      return TVS_OK;
+    }));
+  }
+  LoopState ls;
+  for (int k = 0; k < K; ++k) {
+    if (k >= LAG) {
+      CUDA_TRY(cudaEventSynchronize(C->ring[k % LAG]));
+      if (*(volatile int*)P->done_host) break;
+    }
+    const int cc = coins[k] ? 1 : 0;
+    CUDA_TRY(cudaGraphLaunch(G.exec[cc][0], s));
+    CUDA_TRY(cudaEventRecord(C->ring[k % LAG], s));
+    ls.iters = k + 1;
+    ls.prox += cc;
+  }
+  if (ls.iters > 0) {
+    CUDA_TRY(launch_reduce_record(P->part_a, na, P->part_b, nb, alpha, 1, P->obj_dev, P->ts_dev, prm->f_star,
+                                  prm->target_rel_gap, P->flags, P->done_host_dev, nullptr, s));
+    TVS_TRY(track_distance(P, x, prm->target_rel_dist, s));
+  }
+  TVS_TRY(copy_out(x_io, x, P->n, mem, s));
   TVS_TRY(copy_out(y_io, P->y, P->m, mem, s));
   return finish_solve(P, K, ls, coins, use_prox ? N : 0, fcfg, tr);
 }
@@ -799,6 +987,7 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
       return fail(TVS_EINVAL, "max_iter, n_inner and dual must agree across the batch");
     if (!(prm[i].gamma > 0) || !is_fin(prm[i].gamma)) return fail(TVS_EINVAL, "gamma must be > 0");
     if (!(prm[i].p > 0.0 && prm[i].p <= 1.0)) return fail(TVS_EINVAL, "p must lie in (0, 1]");
+    if (prm[i].resume) return fail(TVS_EUNSUPPORTED, "batched solves do not resume");
     for (int j = 0; j < i; ++j)
       if (probs[j] == P) return fail(TVS_EINVAL, "problem %d appears twice", i);
   }
@@ -981,6 +1170,131 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
   return TVS_OK;
 }
 
+// ---------------------------------------------------------------- Dual-ROF (light prox)
+extern "C" tvs_status dual_rof_solve(tvs_ctx* C, const int dims[2], const float* b,
+                                     const tvs_rof_params* prm, float* q_io, float* u_out, tvs_mem mem,
+                                     tvs_trace* tr) {
+  if (!C || !dims || !b || !prm || !q_io) return fail(TVS_EINVAL, "null argument");
+  if (mem != TVS_MEM_DEVICE && mem != TVS_MEM_HOST) return fail(TVS_EINVAL, "invalid mem kind");
+  const int W = dims[0], H = dims[1];
+  if (W < 1 || H < 1) return fail(TVS_EINVAL, "dims must be >= 1");
+  if (!(prm->alpha > 0) || !is_fin(prm->alpha)) return fail(TVS_EINVAL, "alpha must be > 0");
+  if (!(prm->eps >= 0) || !is_fin(prm->eps)) return fail(TVS_EINVAL, "eps must be >= 0");
+  if (!(prm->gamma > 0) || !is_fin(prm->gamma)) return fail(TVS_EINVAL, "gamma must be > 0");
+  if (!(prm->p > 0.0 && prm->p <= 1.0)) return fail(TVS_EINVAL, "p must lie in (0, 1]");
+  if (prm->max_iter < 0) return fail(TVS_EINVAL, "max_iter must be >= 0");
+  if (!is_fin(prm->f_star) || !(prm->target_rel_gap >= 0)) return fail(TVS_EINVAL, "invalid f_star/target");
+  const int K = prm->max_iter;
+  const size_t n = (size_t)H * W;
+  const bool skip = prm->p < 1.0;
+  cudaStream_t s = C->stream;
+  BatchScratch S;
+  float *q0, *q1, *h = nullptr, *bd;
+  double *pa, *pb, *obj;
+  unsigned long long* ts;
+  int* flags;
+  const int nparts = std::max(dual_rof_blocks(H, W), pointwise_blocks(n));
+  TVS_TRY(S.zeros<float>(2 * n, &q0, s));
+  TVS_TRY(S.zeros<float>(2 * n, &q1, s));
+  if (skip) TVS_TRY(S.zeros<float>(2 * n, &h, s));
+  TVS_TRY(S.zeros<float>(n, &bd, s));
+  TVS_TRY(S.zeros<double>(nparts, &pa, s));
+  TVS_TRY(S.zeros<double>(nparts, &pb, s));
+  TVS_TRY(S.zeros<double>((size_t)K + 1, &obj, s));
+  TVS_TRY(S.zeros<unsigned long long>((size_t)K + 2, &ts, s));
+  TVS_TRY(S.zeros<int>(4, &flags, s));
+  int* done_host = nullptr;
+  int* done_dev = nullptr;
+  {
+    cudaError_t e = cudaHostAlloc((void**)&S.done_host, sizeof(int), cudaHostAllocMapped);
+    if (e != cudaSuccess) {
+      S.done_host = nullptr;
+      return fail(TVS_ENOMEM, "cudaHostAlloc: %s", cudaGetErrorString(e));
+    }
+    done_host = S.done_host;
+    *done_host = 0;
+    CUDA_TRY(cudaHostGetDevicePointer((void**)&done_dev, done_host, 0));
+  }
+  TVS_TRY(copy_in(bd, b, n, mem, s));
+  TVS_TRY(copy_in(q0, q_io, 2 * n, mem, s));
+  int f0[4] = {0, -1, -1, 0};
+  CUDA_TRY(cudaMemcpyAsync(flags, f0, sizeof(f0), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemsetAsync(obj, 0xff, sizeof(double) * (K + 1), s));
+  std::vector<unsigned char> coins(K, 1);
+  if (skip)
+    for (int k = 0; k < K; ++k) coins[k] = (unsigned char)tvs_coin(prm->seed, prm->p, k);
+  const float alpha = (float)prm->alpha, eps = (float)prm->eps, gamma = (float)prm->gamma, p = (float)prm->p;
+  const double ea = prm->eps / prm->alpha;
+  const int nb = dual_rof_blocks(H, W);
+  float* q[2] = {q0, q1};
+  CUDA_TRY(cudaEventRecord(C->ev_start, s));
+  CUDA_TRY(launch_timestamp(ts + K + 1, s));
+  GraphSet G;
+  for (int c = 0; c < 2; ++c) {
+    if (c == 0 && !skip) continue;
+    for (int par = 0; par < 2; ++par) {
+      TVS_TRY(capture(s, &G.exec[c][par], [&]() -> tvs_status {
+        CUDA_TRY(launch_dual_rof_step(H, W, q[par], q[par ^ 1], h, bd, alpha, eps, gamma, p, c == 1, pa, pb, s));
+        CUDA_TRY(launch_reduce_record(pa, nb, pb, nb, ea, 1, obj, ts, prm->f_star, prm->target_rel_gap, flags,
+                                      done_dev, nullptr, s));
+        return TVS_OK;
+      }));
+    }
+  }
+  int iters = 0, prox = 0;
+  for (int k = 0; k < K; ++k) {
+    if (k >= LAG) {
+      CUDA_TRY(cudaEventSynchronize(C->ring[k % LAG]));
+      if (*(volatile int*)done_host) break;
+    }
+    const int c = coins[k] ? 1 : 0;
+    CUDA_TRY(cudaGraphLaunch(G.exec[c][k & 1], s));
+    CUDA_TRY(cudaEventRecord(C->ring[k % LAG], s));
+    iters = k + 1;
+    prox += c;
+  }
+  float* qf = q[iters & 1];
+  float* u_dev = nullptr;
+  if (u_out) TVS_TRY(S.zeros<float>(n, &u_dev, s));
+  CUDA_TRY(launch_dual_rof_primal(H, W, qf, bd, u_dev, pa, pb, s));
+  if (iters > 0)
+    CUDA_TRY(launch_reduce_record(pa, pointwise_blocks(n), pb, pointwise_blocks(n), ea, 1, obj, ts, prm->f_star,
+                                  prm->target_rel_gap, flags, done_dev, nullptr, s));
+  TVS_TRY(copy_out(q_io, qf, 2 * n, mem, s));
+  if (u_out) TVS_TRY(copy_out(u_out, u_dev, n, mem, s));
+  CUDA_TRY(cudaEventRecord(C->ev_stop, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (tr) {
+    std::vector<double> o(iters > 0 ? iters : 1);
+    std::vector<unsigned long long> t(iters + 1);
+    int fl[4];
+    if (iters > 0) {
+      CUDA_TRY(cudaMemcpy(o.data(), obj, sizeof(double) * iters, cudaMemcpyDeviceToHost));
+      CUDA_TRY(cudaMemcpy(t.data(), ts, sizeof(unsigned long long) * iters, cudaMemcpyDeviceToHost));
+    }
+    CUDA_TRY(cudaMemcpy(&t[iters], ts + K + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(fl, flags, sizeof(fl), cudaMemcpyDeviceToHost));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, C->ev_start, C->ev_stop));
+    tr->iters_run = iters;
+    tr->prox_calls = prox;
+    tr->reached = fl[0];
+    tr->reached_iter = fl[0] ? fl[1] : -1;
+    tr->time_to_target_s = (fl[0] && fl[1] >= 0 && fl[1] < iters) ? (double)(t[fl[1]] - t[iters]) * 1e-9 : -1.0;
+    tr->solve_ms = ms;
+    tr->fgp_ms = 0.0;
+    tr->fgp_launches = 0;
+    tr->fgp_pixel_iters = 0;
+    const int lim = tr->cap < iters ? tr->cap : iters;
+    for (int k = 0; k < lim; ++k) {
+      if (tr->objective) tr->objective[k] = o[k];
+      if (tr->coins) tr->coins[k] = coins[k];
+      if (tr->t_s) tr->t_s[k] = (double)(t[k] - t[iters]) * 1e-9;
+    }
+  }
+  return TVS_OK;
+}
+
 // =====================================================================================
 extern "C" {
 
@@ -1025,6 +1339,7 @@ tvs_status tvs_destroy(tvs_ctx* C) {
   if (!C) return TVS_OK;
   cudaSetDevice(C->device);
   if (C->stream) cudaStreamSynchronize(C->stream);
+  while (!C->problems.empty()) tvs_problem_destroy(C->problems.back());
   dfree(C->prox_scratch);
   dfree(C->red_out);
   dfree(C->flags);
@@ -1092,13 +1407,16 @@ tvs_status tvs_problem_create(tvs_ctx* C, const tvs_problem_desc* desc, const fl
   for (int i = 0; i < 4; ++i)
     if ((st = dalloc(C, &P->bytes, &P->dual[i], 4 * (size_t)D.ndim * n_img))) return bail(st);
   if (op.kind == TVS_OP_PARALLEL_BEAM) {
-    if ((st = palloc(P, &P->angle_tab, (size_t)op.n_angles)) || (st = palloc(P, &P->xt, n_img))) return bail(st);
+    if ((st = palloc(P, &P->angle_tab, (size_t)op.n_angles)) || (st = palloc(P, &P->angle_tab2, (size_t)op.n_angles)) ||
+        (st = palloc(P, &P->xt, n_img)))
+      return bail(st);
     P->geom.N = D.nx;
     P->geom.n_angles = op.n_angles;
     P->geom.n_det = op.n_det;
     P->geom.pixel_size = (float)op.pixel_size;
     P->geom.det_spacing = (float)op.det_spacing;
     P->geom.angles = P->angle_tab;
+    P->geom.angles2 = P->angle_tab2;
     P->geom.xt_scratch = P->xt;
     cudaError_t e = ct_build_angle_table(P->geom, P->angle_tab, C->stream);
     if (e != cudaSuccess) return bail(fail(TVS_ECUDA, "angle table: %s", cudaGetErrorString(e)));
@@ -1125,7 +1443,41 @@ tvs_status tvs_problem_create(tvs_ctx* C, const tvs_problem_desc* desc, const fl
     if (e != cudaSuccess) return bail(fail(TVS_ECUDA, "cudaHostGetDevicePointer: %s", cudaGetErrorString(e)));
   }
   if ((st = tvs_problem_set_data(P, b, b_mem))) return bail(st);
+  C->problems.push_back(P);
   *out = P;
+  return TVS_OK;
+}
+
+tvs_status tvs_problem_set_reference(tvs_problem* P, const float* u_ref, tvs_mem mem) {
+  if (!P) return fail(TVS_EINVAL, "null problem");
+  if (mem != TVS_MEM_DEVICE && mem != TVS_MEM_HOST) return fail(TVS_EINVAL, "invalid mem kind");
+  cudaStream_t s = P->ctx->stream;
+  if (!u_ref) {
+    dfree(P->uref);
+    dfree(P->part_c);
+    P->uref = nullptr;
+    P->part_c = nullptr;
+    return TVS_OK;
+  }
+  std::vector<float> host(P->n);
+  if (mem == TVS_MEM_HOST) {
+    memcpy(host.data(), u_ref, P->n * sizeof(float));
+  } else {
+    CUDA_TRY(cudaMemcpy(host.data(), u_ref, P->n * sizeof(float), cudaMemcpyDeviceToHost));
+  }
+  double nrm = 0.0;
+  for (float v : host) {
+    if (!std::isfinite(v)) return fail(TVS_ENUMERIC, "reference holds a non-finite value");
+    nrm += (double)v * (double)v;
+  }
+  if (!(nrm > 0.0)) return fail(TVS_EINVAL, "reference must be nonzero");
+  if (!P->uref) {
+    TVS_TRY(palloc(P, &P->uref, P->n));
+    TVS_TRY(palloc(P, &P->part_c, (size_t)pointwise_blocks(P->n)));
+  }
+  CUDA_TRY(cudaMemcpyAsync(P->uref, host.data(), P->n * sizeof(float), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  P->uref_norm2 = nrm;
   return TVS_OK;
 }
 
@@ -1150,10 +1502,12 @@ tvs_status tvs_problem_destroy(tvs_problem* P) {
   cudaStreamSynchronize(C->stream);
   void* bufs[] = {P->b, P->x[0], P->x[1], P->z, P->h, P->r, P->y, P->axp, P->dual[0], P->dual[1],
                   P->dual[2], P->dual[3], P->part_a, P->part_b, P->obj_dev, P->ts_dev, P->fgp_ts, P->beta_dev,
-                  P->flags, P->count, P->angle_tab, P->xt};
+                  P->flags, P->count, P->angle_tab, P->angle_tab2, P->xt, P->uref, P->part_c, P->dist_dev};
   for (void* b : bufs) dfree(b);
   if (P->done_host) cudaFreeHost(P->done_host);
   C->bytes -= P->bytes;
+  auto& v = C->problems;
+  v.erase(std::remove(v.begin(), v.end(), P), v.end());
   delete P;
   return TVS_OK;
 }
@@ -1290,6 +1644,11 @@ tvs_status pdhg_solve(tvs_problem* P, const tvs_pd_params* prm, float* x, float*
 tvs_status pdhgskip_solve(tvs_problem* P, const tvs_pd_params* prm, float* x, float* y, tvs_mem mem,
                           tvs_trace* tr) {
   return pd_solve(P, prm, x, y, mem, tr, true);
+}
+
+tvs_status pdhgskip1_solve(tvs_problem* P, const tvs_pd_params* prm, float* x, float* y, tvs_mem mem,
+                           tvs_trace* tr) {
+  return pd1_solve(P, prm, x, y, mem, tr);
 }
 
 int tvs_coin(uint64_t seed, double p, int64_t k) {

@@ -76,7 +76,7 @@ batch_ident_step_kernel(const BatchProb* __restrict__ probs, BatchState* __restr
     acc_a += 0.5 * (double)(r * r);
     const float dy = gi < P.H - 1 ? __ldg(x + o + P.W) - xc : 0.f;
     const float dx = gj < P.W - 1 ? __ldg(x + o + 1) - xc : 0.f;
-    acc_b += (double)sqrtf(dy * dy + dx * dx);
+    acc_b += (double)tv_term(0.f, dy, dx);
   }
   block_sum2_store<256>(acc_a, acc_b, part_a, part_b, part_base + blockIdx.x);
 }

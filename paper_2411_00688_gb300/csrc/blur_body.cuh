@@ -9,7 +9,7 @@ namespace tvs {
 
 constexpr int BX = 32, BY = 16, BNT = 256, RMAX = 8;
 
-enum BlurMode { BM_RESID = 0, BM_STEP = 1, BM_PD = 2, BM_PLAIN = 3 };
+enum BlurMode { BM_RESID = 0, BM_STEP = 1, BM_PD = 2, BM_PLAIN = 3, BM_PD1 = 4 };
 
 // TV term |(D x)_(gi,gj)| from global memory (Neumann: zero last differences).
 __device__ __forceinline__ float tv_at_2d(const float* __restrict__ x, int gi, int gj, int H, int W) {
@@ -17,7 +17,7 @@ __device__ __forceinline__ float tv_at_2d(const float* __restrict__ x, int gi, i
   const float c = __ldg(x + o);
   const float dy = gi < H - 1 ? __ldg(x + o + W) - c : 0.f;
   const float dx = gj < W - 1 ? __ldg(x + o + 1) - c : 0.f;
-  return sqrtf(dy * dy + dx * dx);
+  return tv_term(0.f, dy, dx);
 }
 
 // R: blur radius (compile time, so the tap loops unroll and the weights stay in
@@ -68,7 +68,7 @@ __device__ __forceinline__ void blur_tile_body(const float* __restrict__ src, in
       const float xc = s_in[a + R][c + R];
       const float dy = gi < H - 1 ? s_in[a + R + 1][c + R] - xc : 0.f;
       const float dx = gj < W - 1 ? s_in[a + R][c + R + 1] - xc : 0.f;
-      acc_b += (double)sqrtf(dy * dy + dx * dx);
+      acc_b += (double)tv_term(0.f, dy, dx);
     } else if (MODE == BM_STEP) {
       float o_v = __ldg(x + o) - gamma * v;
       if (h) o_v = fmaf(ch, __ldg(h + o), o_v);
@@ -81,6 +81,14 @@ __device__ __forceinline__ void blur_tile_body(const float* __restrict__ src, in
       y[o] = yn;
       axp[o] = v;
       const float r = v - bb;
+      acc_a += 0.5 * (double)(r * r);
+    } else if (MODE == BM_PD1) {
+      // v = A x^; A x_{k+1} = A x_k + p A x^ (A x_k in axp); y <- prox(y + tau A(x_{k+1} + x^))
+      const float bb = __ldg(b + o);
+      const float axn = axp[o] + gamma * v;  // gamma carries p here
+      y[o] = (y[o] + tau * (axn + v) - tau * bb) / (1.f + tau);
+      axp[o] = axn;
+      const float r = axn - bb;
       acc_a += 0.5 * (double)(r * r);
     } else {
       out[o] = v;

@@ -110,6 +110,13 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   return t;
 }
 
+// Isotropic TV term of one pixel, |(D x)_i| = sqrt(dz^2 + dy^2 + dx^2), with one
+// fixed rounding sequence so that every kernel produces identical per-pixel terms
+// (dz = 0 for images: fma(0, 0, t) = t exactly).
+__device__ __forceinline__ float tv_term(float dz, float dy, float dx) {
+  return sqrtf(__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))));
+}
+
 // Half-sample symmetric extension of index j into [0, n).
 __device__ __forceinline__ int reflect_index(int j, int n) {
   if (j >= 0 && j < n) return j;

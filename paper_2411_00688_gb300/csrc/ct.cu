@@ -57,7 +57,7 @@ template <int MODE>
 __global__ void __launch_bounds__(CT_NT)
 joseph_fwd_kernel(GeomConsts g, const float4* __restrict__ angles, const float* __restrict__ x,
                   const float* __restrict__ xt, float* __restrict__ sino, float* __restrict__ y,
-                  const float* __restrict__ b, float tau, double* __restrict__ part) {
+                  const float* __restrict__ b, float tau, double* __restrict__ part, float tau2 = 0.f) {
   const int ray = blockIdx.x * CT_NT + threadIdx.x;
   const int n_rays = g.n_angles * g.n_det;
   double acc_d = 0.0;
@@ -66,8 +66,21 @@ joseph_fwd_kernel(GeomConsts g, const float4* __restrict__ angles, const float* 
     const float4 ang = __ldg(angles + a);
     const float* img = ang.w != 0.f ? x : xt;  // row walk reads x[l][k], column walk xt[l][k]
     const int N = g.N;
+    // fr is affine in l, fr(l) = fr(0) - l * rate; only lines with -1 <= fr < N can
+    // contribute, so walk a superset of them (one line of margin each side)
+    int l_lo = 0, l_hi = N - 1;
+    {
+      const float fr0 = joseph_fr(g, ang, bin, 0);
+      const float rate = fr0 - joseph_fr(g, ang, bin, 1);
+      if (fabsf(rate) > 1e-6f) {
+        const float la = (fr0 + 1.f) / rate, lb = (fr0 - (float)N) / rate;
+        const float lmin = fminf(la, lb), lmax = fmaxf(la, lb);
+        l_lo = max(0, (int)floorf(lmin) - 1);
+        l_hi = min(N - 1, (int)ceilf(lmax) + 1);
+      }
+    }
     float acc = 0.f;
-    for (int l = 0; l < N; ++l) {
+    for (int l = l_lo; l <= l_hi; ++l) {
       const float fr = joseph_fr(g, ang, bin, l);
       const float k0f = floorf(fr);
       if (k0f < -1.f || k0f > (float)(N - 1)) continue;
@@ -83,13 +96,21 @@ joseph_fwd_kernel(GeomConsts g, const float4* __restrict__ angles, const float* 
       sino[ray] = ax;
     } else {
       const float bb = __ldg(b + ray);
-      if (MODE == 1) {
-        const float prev = sino[ray];
-        y[ray] = (y[ray] + tau * (2.f * ax - prev) - tau * bb) / (1.f + tau);
+      if (MODE == 4) {  // PDHGSkip-1: ax = A x^, sino holds A x_k on entry, tau2 = p
+        const float axn = sino[ray] + tau2 * ax;
+        y[ray] = (y[ray] + tau * (axn + ax) - tau * bb) / (1.f + tau);
+        sino[ray] = axn;
+        const float r = axn - bb;
+        acc_d = 0.5 * (double)(r * r);
+      } else {
+        if (MODE == 1) {
+          const float prev = sino[ray];
+          y[ray] = (y[ray] + tau * (2.f * ax - prev) - tau * bb) / (1.f + tau);
+        }
+        const float r = ax - bb;
+        sino[ray] = MODE == 3 ? r : ax;
+        acc_d = 0.5 * (double)(r * r);
       }
-      const float r = ax - bb;
-      sino[ray] = MODE == 3 ? r : ax;
-      acc_d = 0.5 * (double)(r * r);
     }
   }
   if (MODE != 0) block_sum2_store<CT_NT>(acc_d, 0.0, part, nullptr, blockIdx.x);
@@ -97,7 +118,8 @@ joseph_fwd_kernel(GeomConsts g, const float4* __restrict__ angles, const float* 
 
 // g = A^T y at pixel (i, j); epilogue out = x - sigma g + ch h (when x given).
 __global__ void __launch_bounds__(CT_NT)
-joseph_bwd_kernel(GeomConsts g, const float4* __restrict__ angles, const float* __restrict__ ys,
+joseph_bwd_kernel(GeomConsts g, const float4* __restrict__ angles, const float4* __restrict__ angles2,
+                  const float* __restrict__ ys,
                   const float* __restrict__ x, const float* __restrict__ h, float* __restrict__ out,
                   float sigma, float ch, double* __restrict__ part_tv) {
   const int N = g.N;
@@ -111,18 +133,22 @@ joseph_bwd_kernel(GeomConsts g, const float4* __restrict__ angles, const float* 
       const bool rowwalk = ang.w != 0.f;
       const int l = rowwalk ? i : j;   // line the ray walks
       const int k = rowwalk ? j : i;   // this pixel's index along the line
-      // fr is affine in b with slope d * inv; find the b where fr = k, then scan
-      // the neighbourhood in which floor(fr) can be k - 1 or k.
-      const float slope = g.d * ang.y;
+      // fr is affine in b with slope d * inv, so the bins whose floor(fr) is
+      // k - 1 or k lie in an interval of length 2 / |slope| around the b where
+      // fr = k; the ncand integers from ceil(bc - 1/|slope| - margin) cover it
+      // (3 when bins have the pixel width), and each candidate is decided with
+      // the projector's own fr.
+      const float4 a2 = __ldg(angles2 + a);  // (1 / slope, 1 / |slope| + margin, ncand, -)
       const float fr0 = joseph_fr(g, ang, 0, l);
-      const float bc = ((float)k - fr0) / slope;
-      const float span = 1.f / fabsf(slope) + 2.f;
-      int b_lo = (int)floorf(bc - span), b_hi = (int)ceilf(bc + span);
-      if (b_lo < 0) b_lo = 0;
-      if (b_hi > g.n_det - 1) b_hi = g.n_det - 1;
+      const float bc = ((float)k - fr0) * a2.x;
+      const int b_first = (int)ceilf(bc - a2.y);
+      const int ncand = (int)a2.z;
       const float* yrow = ys + (size_t)a * g.n_det;
       float acc = 0.f;
-      for (int b = b_lo; b <= b_hi; ++b) {
+#pragma unroll 3
+      for (int j = 0; j < ncand; ++j) {
+        const int b = b_first + j;
+        if (b < 0 || b >= g.n_det) continue;
         const float fr = joseph_fr(g, ang, b, l);
         const float k0f = floorf(fr);
         const float f = fr - k0f;
@@ -141,7 +167,7 @@ joseph_bwd_kernel(GeomConsts g, const float4* __restrict__ angles, const float* 
       if (part_tv) {
         const float dy = i < N - 1 ? __ldg(x + o + N) - xc : 0.f;
         const float dx = j < N - 1 ? __ldg(x + o + 1) - xc : 0.f;
-        acc_tv = (double)sqrtf(dy * dy + dx * dx);
+        acc_tv = (double)tv_term(0.f, dy, dx);
       }
     } else {
       out[(size_t)i * N + j] = total;
@@ -167,6 +193,7 @@ GeomConsts consts(const CTGeom& g) {
 
 cudaError_t ct_build_angle_table(const CTGeom& g, float4* dev_table, cudaStream_t s) {
   float4* host = new float4[g.n_angles];
+  float4* host2 = new float4[g.n_angles];
   const double pi = 3.14159265358979323846;
   for (int a = 0; a < g.n_angles; ++a) {
     const double th = a * pi / g.n_angles;
@@ -178,11 +205,18 @@ cudaError_t ct_build_angle_table(const CTGeom& g, float4* dev_table, cudaStream_
     v.z = (float)((double)g.pixel_size / (rowwalk ? fabs(c) : fabs(sn)));
     v.w = rowwalk ? 1.f : 0.f;
     host[a] = v;
+    // backprojector helpers: slope of fr in b is d * inv (inv as stored, in float)
+    const double slope = (double)g.det_spacing * (double)v.y;
+    const double half = 1.0 / fabs(slope) + 0.02;
+    host2[a] = make_float4((float)(1.0 / slope), (float)half, (float)(floor(2.0 * half) + 1.0), 0.f);
   }
   cudaError_t e = cudaMemcpyAsync(dev_table, host, sizeof(float4) * g.n_angles,
                                   cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(g.angles2, host2, sizeof(float4) * g.n_angles, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   delete[] host;
+  delete[] host2;
   return e;
 }
 
@@ -191,7 +225,7 @@ int ct_bwd_blocks(const CTGeom& g) { return (g.N * g.N + CT_NT - 1) / CT_NT; }
 
 cudaError_t launch_ct_forward(const CTGeom& g, const float* x, float* sino, float* y,
                               const float* b, float tau, double* part_data, int mode,
-                              cudaStream_t s) {
+                              cudaStream_t s, float p) {
   if (!g.xt_scratch) return cudaErrorInvalidValue;
   dim3 tg((g.N + 31) / 32, (g.N + 31) / 32), tb(32, 8);
   transpose_kernel<<<tg, tb, 0, s>>>(x, g.xt_scratch, g.N);
@@ -207,6 +241,9 @@ cudaError_t launch_ct_forward(const CTGeom& g, const float* x, float* sino, floa
     case CT_FWD_RESID:
       joseph_fwd_kernel<3><<<blocks, CT_NT, 0, s>>>(c, g.angles, x, g.xt_scratch, sino, nullptr, b, 0.f, part_data);
       break;
+    case CT_FWD_PD1:
+      joseph_fwd_kernel<4><<<blocks, CT_NT, 0, s>>>(c, g.angles, x, g.xt_scratch, sino, y, b, tau, part_data, p);
+      break;
     default:
       joseph_fwd_kernel<0><<<blocks, CT_NT, 0, s>>>(c, g.angles, x, g.xt_scratch, sino, nullptr, nullptr, 0.f, nullptr);
   }
@@ -216,7 +253,8 @@ cudaError_t launch_ct_forward(const CTGeom& g, const float* x, float* sino, floa
 cudaError_t launch_ct_backward(const CTGeom& g, const float* y, const float* x, const float* h,
                                float* out, float sigma, float ch, double* part_tv, cudaStream_t s) {
   const GeomConsts c = consts(g);
-  joseph_bwd_kernel<<<ct_bwd_blocks(g), CT_NT, 0, s>>>(c, g.angles, y, x, h, out, sigma, ch, part_tv);
+  joseph_bwd_kernel<<<ct_bwd_blocks(g), CT_NT, 0, s>>>(c, g.angles, g.angles2, y, x, h, out, sigma, ch,
+                                                       part_tv);
   return cudaGetLastError();
 }
 

@@ -10,6 +10,7 @@
 // Each CTA stages r over its tile plus a one-pixel halo in shared memory, forms
 // u over the tile plus the row/column after it, then writes p_{k+1}: the whole
 // iteration is one pass over z, p_k, p_{k-1} and one write of p_{k+1}.
+#include <cstdio>
 #include <cstdlib>
 
 #include "common.cuh"
@@ -535,6 +536,53 @@ __global__ void fgp_finalize_kernel(const float* __restrict__ z, const T* __rest
   }
 }
 
+// z-marching variants: (columns per lane, rows per warp, planes per chunk);
+// TVS_FGP3D_CFG="cpl,rpw,zc" selects one (default 1,2,64).
+template <typename T, bool NN, int CPL, int RPW, int ZC>
+cudaError_t fgp3d_zm_launch(const Dims& d, const float* z, const void* pc, const void* pp, void* pn, float lam,
+                            float inv_step, float beta, cudaStream_t s) {
+  constexpr int TW = 32 * CPL - 2, TH = 8 * RPW - 2;
+  dim3 grid((d.nx + TW - 1) / TW, (d.ny + TH - 1) / TH, (d.nz + ZC - 1) / ZC);
+  fgp3d_zm_kernel<T, NN, CPL, RPW, ZC><<<grid, 256, 0, s>>>(z, (const T*)pc, (const T*)pp, (T*)pn, d.nz, d.ny,
+                                                             d.nx, lam, inv_step, beta);
+  return cudaGetLastError();
+}
+
+struct ZmCfg {
+  int cpl = 1, rpw = 2, zc = 64;  // fastest measured at 512^3 (FP32 and BF16 duals)
+};
+ZmCfg fgp3d_zm_cfg() {
+  static const ZmCfg c = [] {
+    ZmCfg r;
+    if (const char* e = getenv("TVS_FGP3D_CFG")) {
+      ZmCfg t;
+      if (sscanf(e, "%d,%d,%d", &t.cpl, &t.rpw, &t.zc) == 3) r = t;
+    }
+    return r;
+  }();
+  return c;
+}
+
+template <typename T, bool NN>
+cudaError_t fgp3d_zm_dispatch(const Dims& d, const float* z, const void* pc, const void* pp, void* pn, float lam,
+                              float inv_step, float beta, cudaStream_t s) {
+  const ZmCfg c = fgp3d_zm_cfg();
+#define TVS_ZM(C_, R_, Z_) \
+  if (c.cpl == C_ && c.rpw == R_ && c.zc == Z_) return fgp3d_zm_launch<T, NN, C_, R_, Z_>(d, z, pc, pp, pn, lam, inv_step, beta, s);
+  TVS_ZM(1, 4, 64)
+  TVS_ZM(1, 2, 64)
+  TVS_ZM(2, 2, 64)
+  TVS_ZM(2, 4, 64)
+  TVS_ZM(1, 8, 64)
+  TVS_ZM(1, 4, 128)
+  TVS_ZM(1, 4, 32)
+  TVS_ZM(1, 2, 32)
+  TVS_ZM(1, 2, 16)
+  TVS_ZM(2, 2, 32)
+#undef TVS_ZM
+  return fgp3d_zm_launch<T, NN, 1, 2, 64>(d, z, pc, pp, pn, lam, inv_step, beta, s);
+}
+
 // The z-marching 3D kernel is the default; TVS_FGP3D=tile selects the tiled one.
 bool fgp3d_use_zmarch() {
   static const bool zm = [] {
@@ -542,6 +590,33 @@ bool fgp3d_use_zmarch() {
     return !(e && e[0] == 't');
   }();
   return zm;
+}
+
+// PDHGSkip-1 finalisation (Algorithm 5 with omega + 1 = 1/p):
+// u = P_X(z + lam div p_N); x^ = (u - x) / p; x <- x + p x^ (in place).
+template <typename T, bool NONNEG>
+__global__ void fgp_finalize_pd1_kernel(const float* __restrict__ z, const T* __restrict__ p, int H, int W,
+                                        float lam, float prob_p, float* __restrict__ x,
+                                        float* __restrict__ xh, T* __restrict__ p_home) {
+  const size_t n = (size_t)H * W;
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+    const int gj = (int)(o % W), gi = (int)(o / W);
+    float dv = 0.f;
+    if (gi < H - 1) dv += Elem<T>::ld(p + o);
+    if (gi > 0) dv -= Elem<T>::ld(p + o - W);
+    if (gj < W - 1) dv += Elem<T>::ld(p + n + o);
+    if (gj > 0) dv -= Elem<T>::ld(p + n + o - 1);
+    float u = __ldg(z + o) + lam * dv;
+    if (NONNEG) u = fmaxf(u, 0.f);
+    const float xc = x[o];
+    const float h = (u - xc) / prob_p;
+    xh[o] = h;
+    x[o] = xc + prob_p * h;
+    if (p_home) {
+      p_home[o] = p[o];
+      p_home[n + o] = p[n + o];
+    }
+  }
 }
 
 template <typename T, bool NN>
@@ -552,14 +627,11 @@ cudaError_t fgp_iter_t(const Dims& d, const float* z, const void* pc, const void
     fgp2d_kernel<T, NN><<<grid, NT2, 0, s>>>(z, (const T*)pc, (const T*)pp, (T*)pn, d.ny, d.nx, lam,
                                              inv_step, beta);
   } else if (fgp3d_use_zmarch() &&
-             (long long)((d.nx + 29) / 30) * ((d.ny + 29) / 30) * ((d.nz + 31) / 32) >= 4 * 152) {
+             (long long)((d.nx + 29) / 30) * ((d.ny + 13) / 14) * ((d.nz + 63) / 64) >= 4 * 152) {
     // z-marching needs enough (x-y tile, z chunk) pairs to fill the GPU; small
     // volumes use the tiled kernel
-    constexpr int CPL = 1, RPW = 4, ZC = 32;
-    constexpr int TW = 32 * CPL - 2, TH = 8 * RPW - 2;
-    dim3 grid((d.nx + TW - 1) / TW, (d.ny + TH - 1) / TH, (d.nz + ZC - 1) / ZC);
-    fgp3d_zm_kernel<T, NN, CPL, RPW, ZC><<<grid, 256, 0, s>>>(z, (const T*)pc, (const T*)pp, (T*)pn, d.nz,
-                                                               d.ny, d.nx, lam, inv_step, beta);
+    const cudaError_t e = fgp3d_zm_dispatch<T, NN>(d, z, pc, pp, pn, lam, inv_step, beta, s);
+    if (e != cudaSuccess) return e;
   } else {
     dim3 grid((d.nx + TX3 - 1) / TX3, (d.ny + TY3 - 1) / TY3, (d.nz + TZ3 - 1) / TZ3);
     fgp3d_kernel<T, NN><<<grid, NT3, 0, s>>>(z, (const T*)pc, (const T*)pp, (T*)pn, d.nz, d.ny,
@@ -657,6 +729,31 @@ cudaError_t launch_fgp_iter(const Dims& d, const float* z, const void* pc, const
       return nonneg ? fgp_iter_t<__half, true>(d, z, pc, pp, pn, lam, inv_step, beta, s)
                     : fgp_iter_t<__half, false>(d, z, pc, pp, pn, lam, inv_step, beta, s);
   }
+}
+
+cudaError_t launch_fgp_finalize_pd1(const Dims& d, const float* z, const void* p, int dtype, float lam,
+                                    bool nonneg, float prob_p, float* x, float* xh, void* p_home,
+                                    cudaStream_t s) {
+  const size_t n = d.n();
+  if (n == 0) return cudaSuccess;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+#define TVS_PD1(T_)                                                                                   \
+  if (nonneg)                                                                                         \
+    fgp_finalize_pd1_kernel<T_, true><<<blocks, 256, 0, s>>>(z, (const T_*)p, d.ny, d.nx, lam, prob_p, x, xh, \
+                                                             (T_*)p_home);                            \
+  else                                                                                                \
+    fgp_finalize_pd1_kernel<T_, false><<<blocks, 256, 0, s>>>(z, (const T_*)p, d.ny, d.nx, lam, prob_p, x, xh, \
+                                                              (T_*)p_home);
+  if (dtype == DUAL_F32) {
+    TVS_PD1(float)
+  } else if (dtype == DUAL_BF16) {
+    TVS_PD1(__nv_bfloat16)
+  } else {
+    TVS_PD1(__half)
+  }
+#undef TVS_PD1
+  return cudaGetLastError();
 }
 
 bool fgp_config_valid(const FgpConfig& c) {

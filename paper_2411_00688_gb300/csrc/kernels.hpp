@@ -21,6 +21,10 @@ inline size_t dual_elem_bytes(int t) { return t == DUAL_F32 ? 4 : 2; }
 cudaError_t launch_fgp_iter(const Dims& d, const float* z, const void* pc, const void* pp, void* pn,
                             float lam, float inv_step, float beta, int dtype, bool nonneg,
                             cudaStream_t s);
+// PDHGSkip-1 finalisation: u = P_X(z + lam div p); xh = (u - x)/prob_p; x += prob_p xh.
+cudaError_t launch_fgp_finalize_pd1(const Dims& d, const float* z, const void* p, int dtype, float lam,
+                                    bool nonneg, float prob_p, float* x, float* xh, void* p_home,
+                                    cudaStream_t s);
 // Temporally blocked inner iterations (2D): tile-shape / depth configuration.
 // tb <= 1 selects the one-iteration kernel.  A launch of the blocked kernel runs
 // `iters` <= tb iterations from (pc = p_k, pp = p_{k-1}) and writes
@@ -65,6 +69,14 @@ cudaError_t launch_blur_pd_dual(int H, int W, const float* x, float* ax_prev, fl
                                 const float* b, const BlurW& w, float tau, double* part_data,
                                 cudaStream_t s);
 cudaError_t launch_blur(int H, int W, const float* x, float* y, const BlurW& w, cudaStream_t s);
+// PDHGSkip-1 dual step: v = A x^; A x_new = ax_prev + p v (stored back);
+// y = (y + tau (A x_new + v) - tau b)/(1+tau); partial 1/2 (A x_new - b)^2.
+cudaError_t launch_blur_pd1_dual(int H, int W, const float* xh, float* ax_prev, float* y, const float* b,
+                                 const BlurW& w, float p, float tau, double* part_data, cudaStream_t s);
+// Identity-operator form of the same (axh = x^), or with axh == null the skipped
+// iteration y = (y + tau ax_prev - tau b)/(1+tau) (part_data unused then).
+cudaError_t launch_pd1_dual_pointwise(size_t m, const float* axh, float* ax_prev, float* y, const float* b,
+                                      float p, float tau, double* part_data, cudaStream_t s);
 
 // Identity data term (2D or 3D): out = x - gamma (x - b) + ch h; partials of
 // 1/2 (x - b)^2 and TV(x).  out may be null (objective only).
@@ -89,12 +101,31 @@ cudaError_t launch_reduce_record(const double* part_data, int n_data, const doub
                                  int n_tv, double alpha, int every, double* obj,
                                  unsigned long long* ts, double f_star, double target, int* flags,
                                  int* done_host, double* f_out, cudaStream_t s);
+// Distance to a reference: partials of (x - u_ref)^2 (pointwise_blocks(n) blocks),
+// then one block records dist[k] = sqrt(sum / ref_norm2) at k = flags[2] - 1 (the
+// index the preceding reduce_record used) and, when target > 0 and dist <= target,
+// raises the same done flags.
+cudaError_t launch_dist_partials(size_t n, const float* x, const float* u_ref, double* part, cudaStream_t s);
+cudaError_t launch_dist_record(const double* part, int n_part, double ref_norm2, double* dist, double target,
+                               int* flags, int* done_host, cudaStream_t s);
 cudaError_t launch_timestamp(unsigned long long* ts, cudaStream_t s);
 // arr[2 * (*ctr) + which] = now; when which == 1 also (*ctr)++.
 cudaError_t launch_timestamp_pair(unsigned long long* arr, int* ctr, int which, cudaStream_t s);
 cudaError_t launch_count_nonfinite(const float* x, size_t n, int* count, cudaStream_t s);
 cudaError_t launch_coin_schedule(uint64_t seed, double p, int64_t k0, int K, unsigned char* out,
                                  cudaStream_t s);
+
+// ---- Dual-ROF / Dual-Huber-ROF (rof.cu) ----
+int dual_rof_blocks(int H, int W);
+// One ProxSkip / projected-gradient step on q (2 planes) -> qn; h updated in place
+// on prox iterations (h == null: projected gradient).  Partials: 1/2 (div q + b)^2
+// and 1/2 |q|^2 of the current q.
+cudaError_t launch_dual_rof_step(int H, int W, const float* q, float* qn, float* h, const float* b,
+                                 float alpha, float eps, float gamma, float p, bool prox,
+                                 double* part_a, double* part_b, cudaStream_t s);
+// u = b + div q (u may be null) and the same partials (pointwise_blocks(H W) blocks).
+cudaError_t launch_dual_rof_primal(int H, int W, const float* q, const float* b, float* u, double* part_a,
+                                   double* part_b, cudaStream_t s);
 
 // ---- batched ProxSkip (batch.cu) ----
 // Descriptor of one problem of a batch (device memory).  Partials of its
@@ -149,17 +180,20 @@ struct CTGeom {
   int N, n_angles, n_det;
   float pixel_size, det_spacing;
   const float4* angles;  // device table: (m1, inv, weight, row_walk) per angle
+  float4* angles2;       // device table: (1 / slope of fr in b, 1 / |slope| + margin, candidates, -)
   float* xt_scratch;     // N*N floats: transposed image used by the projector
 };
 cudaError_t ct_build_angle_table(const CTGeom& g, float4* dev_table, cudaStream_t s);
 int ct_fwd_blocks(const CTGeom& g);
 int ct_bwd_blocks(const CTGeom& g);
-enum CTFwdMode { CT_FWD_PLAIN = 0, CT_FWD_PD = 1, CT_FWD_STORE = 2, CT_FWD_RESID = 3 };
+enum CTFwdMode { CT_FWD_PLAIN = 0, CT_FWD_PD = 1, CT_FWD_STORE = 2, CT_FWD_RESID = 3, CT_FWD_PD1 = 4 };
 // PLAIN: sino = A x.  PD: y = (y + tau (2 Ax - sino) - tau b)/(1+tau), then sino = Ax.
-// STORE: sino = A x; RESID: sino = A x - b.  PD/STORE/RESID write partials of 1/2 (Ax-b)^2.
+// STORE: sino = A x; RESID: sino = A x - b.  PD1 (x = x^ of PDHGSkip-1): sino <- sino + p A x^,
+// y = (y + tau (sino + A x^) - tau b)/(1+tau).  PD/STORE/RESID/PD1 write partials of
+// 1/2 (A x_new - b)^2.
 cudaError_t launch_ct_forward(const CTGeom& g, const float* x, float* sino, float* y,
                               const float* b, float tau, double* part_data, int mode,
-                              cudaStream_t s);
+                              cudaStream_t s, float p = 0.f);
 // g = A^T y; when x != null: out = x - sigma g + ch h (+ TV(x) partials); else out = g.
 cudaError_t launch_ct_backward(const CTGeom& g, const float* y, const float* x, const float* h,
                                float* out, float sigma, float ch, double* part_tv, cudaStream_t s);

@@ -48,11 +48,10 @@ identity_step_kernel(const float* __restrict__ x, const float* __restrict__ b,
       out[o] = v;
     }
     acc_a += 0.5 * (double)(r * r);
-    float s = 0.f;
-    if (ndim == 3 && gk < D - 1) { const float d0 = __ldg(x + o + HW) - xc; s += d0 * d0; }
-    if (gi < H - 1) { const float d1 = __ldg(x + o + W) - xc; s += d1 * d1; }
-    if (gj < W - 1) { const float d2 = __ldg(x + o + 1) - xc; s += d2 * d2; }
-    acc_b += (double)sqrtf(s);
+    const float d0 = (ndim == 3 && gk < D - 1) ? __ldg(x + o + HW) - xc : 0.f;
+    const float d1 = gi < H - 1 ? __ldg(x + o + W) - xc : 0.f;
+    const float d2 = gj < W - 1 ? __ldg(x + o + 1) - xc : 0.f;
+    acc_b += (double)tv_term(d0, d1, d2);
   }
   block_sum2_store<PW_NT>(acc_a, acc_b, part_a, part_b, blockIdx.x);
 }
@@ -70,11 +69,10 @@ axpy_step_kernel(const float* __restrict__ g, const float* __restrict__ x,
     out[o] = v;
     if (part_b) {
       const int gj = (int)(o % W), gi = (int)((o / W) % H), gk = (int)(o / HW);
-      float s = 0.f;
-      if (ndim == 3 && gk < D - 1) { const float d0 = __ldg(x + o + HW) - xc; s += d0 * d0; }
-      if (gi < H - 1) { const float d1 = __ldg(x + o + W) - xc; s += d1 * d1; }
-      if (gj < W - 1) { const float d2 = __ldg(x + o + 1) - xc; s += d2 * d2; }
-      acc_b += (double)sqrtf(s);
+      const float d0 = (ndim == 3 && gk < D - 1) ? __ldg(x + o + HW) - xc : 0.f;
+      const float d1 = gi < H - 1 ? __ldg(x + o + W) - xc : 0.f;
+      const float d2 = gj < W - 1 ? __ldg(x + o + 1) - xc : 0.f;
+      acc_b += (double)tv_term(d0, d1, d2);
     }
   }
   if (part_b) block_sum2_store<PW_NT>(0.0, acc_b, nullptr, part_b, blockIdx.x);
@@ -88,13 +86,35 @@ tv_partials_kernel(const float* __restrict__ x, int D, int H, int W, int ndim,
   for (size_t o = blockIdx.x * (size_t)PW_NT + threadIdx.x; o < n; o += (size_t)gridDim.x * PW_NT) {
     const int gj = (int)(o % W), gi = (int)((o / W) % H), gk = (int)(o / HW);
     const float xc = __ldg(x + o);
-    float s = 0.f;
-    if (ndim == 3 && gk < D - 1) { const float d0 = __ldg(x + o + HW) - xc; s += d0 * d0; }
-    if (gi < H - 1) { const float d1 = __ldg(x + o + W) - xc; s += d1 * d1; }
-    if (gj < W - 1) { const float d2 = __ldg(x + o + 1) - xc; s += d2 * d2; }
-    acc_b += (double)sqrtf(s);
+    const float d0 = (ndim == 3 && gk < D - 1) ? __ldg(x + o + HW) - xc : 0.f;
+    const float d1 = gi < H - 1 ? __ldg(x + o + W) - xc : 0.f;
+    const float d2 = gj < W - 1 ? __ldg(x + o + 1) - xc : 0.f;
+    acc_b += (double)tv_term(d0, d1, d2);
   }
   block_sum2_store<PW_NT>(0.0, acc_b, nullptr, part_b, blockIdx.x);
+}
+
+// PDHGSkip-1 dual step for the identity operator (ax = x^), or, with ax == null,
+// the skipped iteration y <- prox(y + tau A x_k) from the stored A x_k.
+__global__ void __launch_bounds__(PW_NT)
+pd1_dual_pointwise_kernel(size_t m, const float* __restrict__ axh, float* __restrict__ axp,
+                          float* __restrict__ y, const float* __restrict__ b, float p, float tau,
+                          double* __restrict__ part_a) {
+  double acc = 0.0;
+  for (size_t o = blockIdx.x * (size_t)PW_NT + threadIdx.x; o < m; o += (size_t)gridDim.x * PW_NT) {
+    const float bb = __ldg(b + o);
+    if (axh) {
+      const float v = __ldg(axh + o);
+      const float axn = axp[o] + p * v;
+      y[o] = (y[o] + tau * (axn + v) - tau * bb) / (1.f + tau);
+      axp[o] = axn;
+      const float r = axn - bb;
+      acc += 0.5 * (double)(r * r);
+    } else {
+      y[o] = (y[o] + tau * axp[o] - tau * bb) / (1.f + tau);
+    }
+  }
+  if (part_a) block_sum2_store<PW_NT>(acc, 0.0, part_a, nullptr, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(PW_NT)
@@ -147,6 +167,43 @@ reduce_record_kernel(const double* __restrict__ part_a, int n_a, const double* _
         *(volatile int*)done_host = 1;
         __threadfence_system();
       }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(PW_NT)
+dist_partials_kernel(size_t n, const float* __restrict__ x, const float* __restrict__ u, double* __restrict__ part) {
+  double acc = 0.0;
+  for (size_t o = blockIdx.x * (size_t)PW_NT + threadIdx.x; o < n; o += (size_t)gridDim.x * PW_NT) {
+    const float d = __ldg(x + o) - __ldg(u + o);
+    acc += (double)d * (double)d;
+  }
+  block_sum2_store<PW_NT>(acc, 0.0, part, nullptr, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(512)
+dist_record_kernel(const double* __restrict__ part, int n_part, double ref_norm2, double* dist, double target,
+                   int* flags, int* done_host) {
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n_part; i += 512) a += part[i];
+  __shared__ double sa[512];
+  sa[threadIdx.x] = a;
+  __syncthreads();
+  for (int s = 256; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sa[threadIdx.x] += sa[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  const int k = flags[2] - 1;
+  if (k < 0) return;
+  const double d = sqrt(sa[0] / ref_norm2);
+  dist[k] = d;
+  if (target > 0.0 && flags[0] == 0 && d <= target) {
+    flags[0] = 1;
+    flags[1] = k;
+    if (done_host) {
+      *(volatile int*)done_host = 1;
+      __threadfence_system();
     }
   }
 }
@@ -220,6 +277,12 @@ cudaError_t launch_blur_pd_dual(int H, int W, const float* x, float* ax_prev, fl
                             part_data, nullptr, s);
 }
 
+cudaError_t launch_blur_pd1_dual(int H, int W, const float* xh, float* ax_prev, float* y, const float* b,
+                                 const BlurW& w, float p, float tau, double* part_data, cudaStream_t s) {
+  return blur_launch<BM_PD1>(H, W, xh, w, b, nullptr, nullptr, nullptr, p, 0.f, ax_prev, y, tau, part_data,
+                             nullptr, s);
+}
+
 cudaError_t launch_blur(int H, int W, const float* x, float* y, const BlurW& w, cudaStream_t s) {
   return blur_launch<BM_PLAIN>(H, W, x, w, nullptr, y, nullptr, nullptr, 0.f, 0.f, nullptr, nullptr,
                                0.f, nullptr, nullptr, s);
@@ -240,6 +303,12 @@ cudaError_t launch_axpy_step(const Dims& d, const float* g, const float* x, cons
   return cudaGetLastError();
 }
 
+cudaError_t launch_pd1_dual_pointwise(size_t m, const float* axh, float* ax_prev, float* y, const float* b,
+                                      float p, float tau, double* part_data, cudaStream_t s) {
+  pd1_dual_pointwise_kernel<<<pointwise_blocks(m), PW_NT, 0, s>>>(m, axh, ax_prev, y, b, p, tau, part_data);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_tv_partials(const Dims& d, const float* x, double* part_tv, cudaStream_t s) {
   tv_partials_kernel<<<pointwise_blocks(d.n()), PW_NT, 0, s>>>(x, d.nz, d.ny, d.nx, d.ndim, part_tv);
   return cudaGetLastError();
@@ -257,6 +326,17 @@ cudaError_t launch_reduce_record(const double* part_data, int n_data, const doub
                                  int* done_host, double* f_out, cudaStream_t s) {
   reduce_record_kernel<<<1, 512, 0, s>>>(part_data, n_data, part_tv, n_tv, alpha, every, obj, ts,
                                          f_star, target, flags, done_host, f_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dist_partials(size_t n, const float* x, const float* u_ref, double* part, cudaStream_t s) {
+  dist_partials_kernel<<<pointwise_blocks(n), PW_NT, 0, s>>>(n, x, u_ref, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dist_record(const double* part, int n_part, double ref_norm2, double* dist, double target,
+                               int* flags, int* done_host, cudaStream_t s) {
+  dist_record_kernel<<<1, 512, 0, s>>>(part, n_part, ref_norm2, dist, target, flags, done_host);
   return cudaGetLastError();
 }
 

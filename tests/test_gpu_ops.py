@@ -129,3 +129,23 @@ def test_nonfinite_measurement_rejected(tvs, ctx):
     with pytest.raises(tvs.TVSError) as e:
         tvs.Problem(ctx, b, 0.1)
     assert e.value.status == 4
+
+
+@pytest.mark.parametrize("det_ratio", [0.6, 1.7])
+def test_projector_other_detector_spacing(tvs, ctx, det_ratio):
+    """Bins narrower / wider than a pixel: the backprojector's candidate window widens."""
+    import torch
+    N, na, nd = 24, 30, 41
+    geom = operators.ParallelBeam(N, na, nd, 1.0 / N, det_ratio / N)
+    g = np.random.default_rng(5)
+    x32, x64 = f32(g.standard_normal((N, N)))
+    y32, y64 = f32(g.standard_normal((na, nd)))
+    prob = tvs.Problem(ctx, y32, 0.0, op="ct", shape=(N, N), n_angles=na, n_det=nd,
+                       pixel_size=1.0 / N, det_spacing=det_ratio / N)
+    xt, yt = cuda(x32), cuda(y32)
+    ax = torch.empty_like(yt)
+    aty = torch.empty_like(xt)
+    tvs.tvs_op_apply(prob, xt, ax)
+    tvs.tvs_op_apply(prob, yt, aty, adjoint=True)
+    assert rel_l2(host(ax), operators.joseph_forward(x64, geom)) <= 1e-5
+    assert rel_l2(host(aty), operators.joseph_adjoint(y64, geom)) <= 1e-5

@@ -138,6 +138,33 @@ def test_pd_solvers_ct_small(tvs, ctx, skip):
     assert rel_l2(host(y), ref["y"]) <= TOL_X_F32
 
 
+@pytest.mark.parametrize("p", [1.0, 0.3])
+def test_pdhgskip1_ct_small(tvs, ctx, p):
+    N, na, nd = 48, 60, 69
+    geom, b32, b64, oprob, L = _ct_setup(N, na, nd, 52, 0.002)
+    st = 0.99 / math.sqrt(L)
+    prob = tvs.Problem(ctx, cuda(b32), 0.002, op="ct", shape=(N, N), n_angles=na, n_det=nd,
+                       pixel_size=1.0 / N, det_spacing=1.0 / N)
+    x0 = np.zeros((N, N), dtype=np.float32)
+    y0 = np.zeros((na, nd), dtype=np.float32)
+    x, y, tr = tvs.pdhgskip1_solve(prob, cuda(x0), cuda(y0), st, st, p, 7, 25, 15)
+    ref = solvers.pdhgskip1(oprob, x0.astype(np.float64), y0.astype(np.float64), st, st, p, 7, 25, 15)
+    _check(tr, ref, host(x))
+    assert rel_l2(host(y), ref["y"]) <= TOL_X_F32
+
+
+@pytest.mark.parametrize("op", ["identity", "blur"])
+def test_pdhgskip1_image_operators(tvs, ctx, op):
+    b32, b64 = _data((45, 58), op, 62, 0.05)
+    A = operators.identity_op() if op == "identity" else operators.blur_op(2.0)
+    oprob = solvers.Problem(A, b64, 0.04, (45, 58))
+    prob = tvs.Problem(ctx, cuda(b32), 0.04, op=op, blur_sigma=2.0)
+    y0 = np.zeros_like(b32)
+    x, y, tr = tvs.pdhgskip1_solve(prob, cuda(b32), cuda(y0), 0.9, 0.9, 0.4, 8, 20, 12)
+    ref = solvers.pdhgskip1(oprob, b64, y0.astype(np.float64), 0.9, 0.9, 0.4, 8, 20, 12)
+    _check(tr, ref, host(x))
+
+
 @pytest.mark.parametrize("op", ["identity", "blur"])
 def test_pdhgskip_image_operators(tvs, ctx, op):
     b32, b64 = _data((45, 58), op, 61, 0.05)
@@ -223,3 +250,77 @@ def test_target_stops_early(tvs, ctx):
     assert np.all(tr.objective[:k] - f_star > 1e-3 * f_star)
     assert tr.iters_run <= k + 1 + 10
     assert tr.time_to_target_s > 0
+
+
+def test_resume_equals_uninterrupted_proxskip(tvs, ctx):
+    """K iterations + a resumed run of K more (k0 = K) equals one run of 2K iterations."""
+    b32, _ = _data((64, 80), "blur", 101, 0.02)
+    prob = tvs.Problem(ctx, cuda(b32), 0.03, op="blur", blur_sigma=2.0)
+    K = 12
+    xa, ta = tvs.proxskip_solve(prob, cuda(b32), 1.0, 0.4, 17, 2 * K, 10)
+    xb, tb = tvs.proxskip_solve(prob, cuda(b32), 1.0, 0.4, 17, K, 10)
+    xc, tc = tvs.proxskip_solve(prob, xb, 1.0, 0.4, 17, K, 10, resume=True, k0=K)
+    np.testing.assert_array_equal(host(xc), host(xa))
+    assert list(tb.coins) + list(tc.coins) == list(ta.coins)
+    np.testing.assert_allclose(np.concatenate([tb.objective, tc.objective]), ta.objective, rtol=1e-12)
+
+
+def test_resume_equals_uninterrupted_pdhgskip(tvs, ctx):
+    N, na, nd = 40, 48, 57
+    geom, b32, b64, oprob, L = _ct_setup(N, na, nd, 55, 0.002)
+    st = 0.99 / math.sqrt(L)
+    prob = tvs.Problem(ctx, cuda(b32), 0.002, op="ct", shape=(N, N), n_angles=na, n_det=nd,
+                       pixel_size=1.0 / N, det_spacing=1.0 / N)
+    z = np.zeros((N, N), dtype=np.float32)
+    y0 = np.zeros((na, nd), dtype=np.float32)
+    K = 10
+    for fn in (tvs.pdhgskip_solve, tvs.pdhgskip1_solve):
+        xa, ya, ta = fn(prob, cuda(z), cuda(y0), st, st, 0.3, 9, 2 * K, 8)
+        xb, yb, tb = fn(prob, cuda(z), cuda(y0), st, st, 0.3, 9, K, 8)
+        xc, yc, tc = fn(prob, xb, yb, st, st, 0.3, 9, K, 8, resume=True, k0=K)
+        np.testing.assert_array_equal(host(xc), host(xa))
+        np.testing.assert_array_equal(host(yc), host(ya))
+        np.testing.assert_allclose(np.concatenate([tb.objective, tc.objective]), ta.objective, rtol=1e-12)
+
+
+def test_resume_rejected_for_fista(tvs, ctx):
+    b32, _ = _data((20, 20), "identity", 5, 0.05)
+    prob = tvs.Problem(ctx, cuda(b32), 0.05)
+    with pytest.raises(tvs.TVSError) as e:
+        tvs.fista_solve(prob, cuda(b32), 1.0, 5, 5, resume=True, k0=5)
+    assert e.value.status == 6
+
+
+@pytest.mark.parametrize("solver", ["proxskip", "fista", "pdhgskip", "pdhgskip1"])
+def test_reference_distance_trace_and_stop(tvs, ctx, solver):
+    """With a reference u*, the trace records ||x_{k+1} - u*|| / ||u*|| (checked on
+    the returned iterate) and target_rel_dist stops the solve at the first
+    iterate within it."""
+    b32, b64 = _data((48, 56), "blur", 111, 0.02)
+    prob = tvs.Problem(ctx, cuda(b32), 0.03, op="blur", blur_sigma=2.0)
+    ref = solvers.fista(solvers.Problem(operators.blur_op(2.0), b64, 0.03, (48, 56)), b64, 1.0, 150, 30,
+                        record=False)["x"]
+    u32, _ = f32(ref)
+    prob.set_reference(cuda(u32))
+    y0 = cuda(np.zeros_like(b32))
+
+    def run(**kw):
+        if solver == "proxskip":
+            x, tr = tvs.proxskip_solve(prob, cuda(b32), 1.0, 0.5, 3, 40, 20, **kw)
+        elif solver == "fista":
+            x, tr = tvs.fista_solve(prob, cuda(b32), 1.0, 40, 20, **kw)
+        elif solver == "pdhgskip":
+            x, _, tr = tvs.pdhgskip_solve(prob, cuda(b32), y0.clone(), 0.9, 0.9, 0.5, 3, 40, 20, **kw)
+        else:
+            x, _, tr = tvs.pdhgskip1_solve(prob, cuda(b32), y0.clone(), 0.9, 0.9, 0.5, 3, 40, 20, **kw)
+        return host(x), tr
+
+    x, tr = run()
+    assert np.all(np.isfinite(tr.rel_dist))
+    d_last = np.linalg.norm(x - u32.astype(np.float64)) / np.linalg.norm(u32.astype(np.float64))
+    assert abs(tr.rel_dist[-1] - d_last) <= 1e-5 * d_last
+    target = float(np.quantile(tr.rel_dist, 0.5))
+    x2, tr2 = run(target_dist=target)
+    assert tr2.reached and tr2.rel_dist[tr2.reached_iter] <= target
+    assert np.all(tr2.rel_dist[:tr2.reached_iter] > target)
+    prob.set_reference(None)

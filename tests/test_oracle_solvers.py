@@ -70,6 +70,32 @@ def test_pdhgskip_p1_equals_pdhg():
     np.testing.assert_allclose(b["y"], a["y"], rtol=0, atol=1e-12)
 
 
+def test_pdhgskip1_p1_equals_pdhg():
+    """Algorithm 5 with p = 1 (omega = 0, every coin 1) is PDHG: x_{k+1} = prox(...) and
+    K(x_{k+1} + x^_k) = K(2 x_{k+1} - x_k)."""
+    prob, geom = _ct_problem()
+    from oracle.power import power_method
+    L = power_method(lambda x: prob.A.adjoint(prob.A.forward(x)), prob.shape, 300)
+    st = 0.99 / math.sqrt(L)
+    y0 = np.zeros_like(prob.b)
+    a = solvers.pdhg(prob, np.zeros(prob.shape), y0, st, st, 20, 6)
+    b = solvers.pdhgskip1(prob, np.zeros(prob.shape), y0, st, st, 1.0, 5, 20, 6)
+    np.testing.assert_allclose(b["x"], a["x"], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(b["y"], a["y"], rtol=0, atol=1e-12)
+
+
+def test_pdhgskip1_skipped_iterations_keep_x():
+    """With theta_k = 0 the primal iterate does not move (x^ = 0), only y does."""
+    prob, _ = _ct_problem()
+    p, seed = 0.3, 8
+    sched = coin.schedule(seed, p, 12)
+    xs = [solvers.pdhgskip1(prob, np.zeros(prob.shape), np.zeros_like(prob.b), 0.3, 0.3, p, seed, k, 5,
+                            record=False)["x"] for k in range(1, 13)]
+    for k in range(1, 12):
+        if not sched[k]:
+            np.testing.assert_array_equal(xs[k], xs[k - 1])
+
+
 @pytest.mark.parametrize("p", [0.5, 0.2])
 def test_proxskip_control_variate_identity(p):
     prob = _deblur_problem(seed=3)
@@ -130,6 +156,7 @@ def test_solvers_reach_two_pixel_minimiser(b1, b2, alpha):
         solvers.proxskip(prob, x0, 0.5, 0.5, 1, 400, 60)["x"],
         solvers.pdhg(prob, x0, np.zeros_like(b), 0.5, 0.5, 600, 60)["x"],
         solvers.pdhgskip2(prob, x0, np.zeros_like(b), 0.5, 0.5, 0.5, 2, 1500, 60)["x"],
+        solvers.pdhgskip1(prob, x0, np.zeros_like(b), 0.5, 0.5, 0.5, 3, 3000, 60)["x"],
     ]
     for x in outs:
         np.testing.assert_allclose(x, expect, atol=1e-7)
@@ -169,3 +196,41 @@ def test_objective_closed_form():
     x[:, 3:] = 2.0
     prob = solvers.Problem(operators.identity_op(), np.zeros_like(x), 0.1, x.shape)
     assert prob.objective(x) == pytest.approx(0.5 * 4.0 * 25 + 0.1 * 2.0 * 5, rel=1e-15)
+
+
+# ---------------------------------------------------------------- Dual-ROF (light prox)
+def test_dual_rof_projgd_reaches_rof_solution():
+    """Chambolle's projected gradient on Dual-ROF: u = b + div q converges to the TV
+    prox of b, pinned by the 1D exact solver on a single row (isotropic = 1D there)."""
+    from tests.test_oracle_tv import _exact_1d_tv_prox
+    z = np.random.default_rng(31).standard_normal(9)
+    out = solvers.dual_rof_projgd(z[None, :], 0.3, 1.0 / 8.0, 20000)
+    np.testing.assert_allclose(out["u"].ravel(), _exact_1d_tv_prox(z, 0.3), atol=1e-8)
+
+
+def test_dual_rof_proxskip_p1_equals_projgd():
+    b = np.random.default_rng(32).standard_normal((9, 12))
+    a = solvers.dual_rof_projgd(b, 0.2, 1.0 / 8.0, 40)
+    c = solvers.dual_rof_proxskip(b, 0.2, 1.0 / 8.0, 1.0, 4, 40)
+    np.testing.assert_allclose(c["q"], a["q"], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("eps", [0.0, 0.1])
+def test_dual_rof_proxskip_converges(eps):
+    """ProxSkip on (Huber-)Dual-ROF reaches the projected-gradient fixed point."""
+    b = np.random.default_rng(33).standard_normal((8, 10))
+    ref = solvers.dual_rof_projgd(b, 0.25, 1.0 / 8.0, 20000, eps=eps, record=False)
+    out = solvers.dual_rof_proxskip(b, 0.25, 1.0 / 8.0, 0.3, 5, 20000, eps=eps, record=False)
+    np.testing.assert_allclose(out["u"], ref["u"], atol=1e-6)
+    assert np.sqrt((out["q"] ** 2).sum(axis=0)).max() <= 0.25 * (1 + 1e-12)
+
+
+def test_huber_dual_rof_closed_form_two_pixel():
+    """Dual-Huber-ROF on two pixels: F(q) = 1/2 (q + b1)^2 + 1/2 (b2 - q)^2 + eps/(2a) q^2
+    with |q| <= a (the single horizontal difference) has the closed-form minimiser
+    q* = clip((b2 - b1) / (2 + eps/a), -a, a)."""
+    b1, b2, a, eps = 0.1, 0.9, 0.3, 0.1
+    b = np.array([[b1, b2]])
+    out = solvers.dual_rof_projgd(b, a, 1.0 / 8.0, 5000, eps=eps, record=False)
+    q_star = np.clip((b2 - b1) / (2 + eps / a), -a, a)
+    assert abs(out["q"][1, 0, 0] - q_star) < 1e-10
