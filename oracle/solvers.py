@@ -209,6 +209,71 @@ def pdhgskip1(prob: Problem, x0, y0, sigma, tau, p, seed, K, n_inner, record=Tru
     return dict(x=x, y=y, dual=dual, objective=obj, coins=coins, prox_calls=n_prox)
 
 
+# ---------------------------------------------------------------- explicit PDHG
+def difference_column_counts(shape):
+    """Entries of D in each pixel's column, sum_i |D_ij|: per axis a, pixel j enters
+    the difference at j (when j_a < n_a - 1) and the one at j - e_a (when j_a > 0)."""
+    cnt = np.zeros(shape, dtype=np.float64)
+    for a, n_a in enumerate(shape):
+        idx = np.arange(n_a).reshape([-1 if b == a else 1 for b in range(len(shape))])
+        cnt += (idx < n_a - 1).astype(np.float64) + (idx > 0).astype(np.float64)
+    return cnt
+
+
+def pdhg_explicit_preconditioners(prob: Problem):
+    """Diagonal step sizes of Pock and Chambolle (ICCV 2011), Lemma 2 with exponent 1,
+    for the block operator K = [A; D] of the explicit formulation (Section 3.2):
+    T_j = 1 / sum_i |K_ij| per pixel and Sigma_i = 1 / sum_j |K_ij| per dual entry.
+
+    Every operator here has non-negative entries (blur weights, Joseph weights, the
+    identity), so |A| 1 = A 1 and |A|^T 1 = A^T 1.  A row of D holds -1 and +1, or
+    nothing on the last slice of its axis: all D rows take Sigma = 1/2 (a smaller
+    step than 1/0 on the empty rows, which keeps the bound of the lemma).  An empty
+    row of A or an empty column of K takes 1: the matching entries of K are zero,
+    so the bound does not involve them.
+    Returns (T, Sigma_A, Sigma_D)."""
+    col = prob.A.adjoint(np.ones(prob.b.shape)) + difference_column_counts(prob.shape)
+    row = prob.A.forward(np.ones(prob.shape))
+    T = np.where(col > 0, 1.0 / np.where(col > 0, col, 1.0), 1.0)
+    S_A = np.where(row > 0, 1.0 / np.where(row > 0, row, 1.0), 1.0)
+    return T, S_A, 0.5
+
+
+def pdhg_explicit(prob: Problem, x0, y0=None, q0=None, K=100, sigma=1.0, tau=1.0, record=True):
+    """Explicit PDHG with diagonal preconditioning, the solver behind the paper's
+    reference solutions u* (Section 4.1) in the explicit form of Section 3.2:
+    K = [A; D], f(v, w) = 1/2 ||v - b||^2 + alpha sum_i |w_i|_2 (separable), g = 0 or
+    the indicator of x >= 0; every prox is closed-form.  With T, Sigma from
+    ``pdhg_explicit_preconditioners`` scaled by sigma (primal) and tau (dual),
+    sigma * tau <= 1, and the step naming of Algorithm 6:
+
+        x_{k+1} = P_X(x_k - sigma T (A^T y_k - div q_k))        (K^T (y, q) = A^T y - div q)
+        x-bar   = 2 x_{k+1} - x_k
+        y_{k+1} = (y_k + tau S_A (A x-bar - b)) / (1 + tau S_A)  (prox of the conjugate of 1/2||. - b||^2)
+        q_{k+1} = P_alpha(q_k + tau S_D D x-bar)                  (prox of the conjugate of alpha |.|_{2,1})
+    """
+    x = np.array(x0, dtype=np.float64)
+    y = np.zeros(prob.b.shape) if y0 is None else np.array(y0, dtype=np.float64)
+    q = np.zeros((x.ndim,) + x.shape) if q0 is None else np.array(q0, dtype=np.float64)
+    T, S_A, S_D = pdhg_explicit_preconditioners(prob)
+    obj = []
+    for _ in range(K):
+        x_new = x - sigma * T * (prob.A.adjoint(y) - tv.div(q))
+        if prob.nonneg:
+            x_new = np.maximum(x_new, 0.0)
+        x_bar = 2.0 * x_new - x
+        s_a = tau * S_A
+        y = (y + s_a * (prob.A.forward(x_bar) - prob.b)) / (1.0 + s_a)
+        if prob.alpha > 0:
+            q = tv.project_ball(q + (tau * S_D) * tv.grad(x_bar), prob.alpha)
+        else:  # the ball of radius 0
+            q = np.zeros_like(q)
+        x = x_new
+        if record:
+            obj.append(prob.objective(x))
+    return dict(x=x, y=y, q=q, objective=obj, coins=[1] * K, prox_calls=K)
+
+
 # ---------------------------------------------------------------- light-prox case
 def dual_rof_objective(q, b, alpha, eps=0.0):
     """F(q) = 1/2 ||div q + b||^2 + (eps / (2 alpha)) ||q||^2 (Eq. 6 / Eq. 8 without

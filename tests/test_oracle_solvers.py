@@ -1,4 +1,5 @@
-"""Pins of the oracle's outer solvers (Algorithms 2, 3, 4, 6 and implicit PDHG).
+"""Pins of the oracle's outer solvers (Algorithms 2, 3, 4, 5, 6, implicit PDHG and
+explicit, diagonally preconditioned PDHG).
 
 * ProxSkip with p = 1 is PGD and PDHGSkip-2 with p = 1 is PDHG (the prox argument
   x^ - gamma h equals x - gamma grad f(x)): compared iterate for iterate against the
@@ -8,6 +9,10 @@
 * Between prox events h does not change.
 * All solvers reach the closed-form two-pixel minimiser, and on a small deblurring
   problem PGD, FISTA and PDHG agree on the minimum.
+* Explicit PDHG: its step sizes are the reciprocal row and column sums of the dense
+  block matrix [A; D] and satisfy the norm bound of Pock and Chambolle's Lemma 2; it
+  reaches the two-pixel minimiser, the optimality (KKT) conditions of Eq. 5, and the
+  minimisers of the implicit solvers.
 """
 
 import math
@@ -234,3 +239,94 @@ def test_huber_dual_rof_closed_form_two_pixel():
     out = solvers.dual_rof_projgd(b, a, 1.0 / 8.0, 5000, eps=eps, record=False)
     q_star = np.clip((b2 - b1) / (2 + eps / a), -a, a)
     assert abs(out["q"][1, 0, 0] - q_star) < 1e-10
+
+
+# ---------------------------------------------------------------- explicit PDHG
+def _dense(fn, in_shape):
+    """Matrix of a linear map, one unit vector at a time."""
+    n = int(np.prod(in_shape))
+    cols = []
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        cols.append(np.asarray(fn(e.reshape(in_shape))).ravel())
+    return np.stack(cols, axis=1)
+
+
+def _explicit_cases():
+    ct, _ = _ct_problem(N=6)  # 16 angles x 17 bins on a 6 x 6 image: some rays miss it
+    return [_denoise_problem(n=5), _deblur_problem(n=6), ct]
+
+
+@pytest.mark.parametrize("case", range(3))
+def test_explicit_preconditioners_satisfy_lemma(case):
+    """T and Sigma are the reciprocal column and row sums of |K|, K = [A; D], taken
+    from the dense matrix, and ||Sigma^1/2 K T^1/2||_2 <= 1 (Pock and Chambolle 2011,
+    Lemma 2), which is what makes sigma = tau = 1 a convergent step."""
+    prob = _explicit_cases()[case]
+    A = _dense(prob.A.forward, prob.shape)
+    Dm = _dense(tv.grad, prob.shape)
+    assert A.min() >= 0.0  # |A| = A for every operator here
+    Kd = np.vstack([A, Dm])
+    T, S_A, S_D = solvers.pdhg_explicit_preconditioners(prob)
+    col = np.abs(Kd).sum(axis=0)
+    np.testing.assert_allclose(T.ravel(), 1.0 / col, rtol=1e-13)
+    row = np.abs(A).sum(axis=1)
+    live = row > 0
+    np.testing.assert_allclose(S_A.ravel()[live], 1.0 / row[live], rtol=1e-13)
+    assert np.all(S_A.ravel()[~live] == 1.0)
+    drow = np.abs(Dm).sum(axis=1)
+    assert set(np.unique(drow)) <= {0.0, 2.0} and S_D == 0.5
+    sig = np.concatenate([np.broadcast_to(S_A, prob.b.shape).ravel(), np.full(Dm.shape[0], S_D)])
+    M = np.sqrt(sig)[:, None] * Kd * np.sqrt(T.ravel())[None, :]
+    assert np.linalg.norm(M, 2) <= 1.0 + 1e-12
+
+
+@pytest.mark.parametrize("b1,b2,alpha", [(0.0, 1.0, 0.2), (0.4, 0.5, 0.1)])
+def test_explicit_pdhg_reaches_two_pixel_minimiser(b1, b2, alpha):
+    b = np.array([[b1, b2]])
+    prob = solvers.Problem(operators.identity_op(), b, alpha, (1, 2))
+    out = solvers.pdhg_explicit(prob, np.zeros_like(b), K=400, record=False)
+    np.testing.assert_allclose(out["x"], _two_pixel(b1, b2, alpha), atol=1e-9)
+
+
+def _kkt(prob, x, q):
+    """Optimality of Eq. 5 at (x, q) with no constraint: A^T(Ax - b) - div q = 0,
+    |q_i| <= alpha, and q_i = alpha (Dx)_i / |(Dx)_i| wherever (Dx)_i != 0."""
+    stat = prob.A.adjoint(prob.A.forward(x) - prob.b) - tv.div(q)
+    g = tv.grad(x)
+    nrm = np.sqrt((g * g).sum(axis=0))
+    qn = np.sqrt((q * q).sum(axis=0))
+    big = nrm > 1e-6
+    align = np.abs(q[:, big] - prob.alpha * g[:, big] / nrm[big]).max() if big.any() else 0.0
+    return np.abs(stat).max(), qn.max() - prob.alpha, align
+
+
+@pytest.mark.parametrize("make,K", [(_denoise_problem, 20000), (_deblur_problem, 4000)])
+def test_explicit_pdhg_satisfies_optimality(make, K):
+    prob = make()
+    out = solvers.pdhg_explicit(prob, prob.b.copy(), K=K, record=False)
+    stat, excess, align = _kkt(prob, out["x"], out["q"])
+    assert stat <= 1e-7 and excess <= 1e-12 and align <= 1e-5
+
+
+def test_explicit_pdhg_agrees_with_implicit_solvers():
+    """Same minimum value as FISTA with the FGP prox on a small deblurring problem,
+    and, with the non-negativity constraint on a small tomography problem, the
+    minimiser of implicit PDHG (explicit PDHG converges at the slower O(1/k) rate
+    there, hence the looser bound)."""
+    prob = _deblur_problem(n=10, alpha=0.03)
+    f_fista = solvers.fista(prob, prob.b.copy(), 1.0, 300, 30)["objective"][-1]
+    f_exp = solvers.pdhg_explicit(prob, prob.b.copy(), K=4000)["objective"][-1]
+    assert abs(f_exp - f_fista) <= 1e-7 * f_fista
+    ct, _ = _ct_problem(N=8, alpha=0.01)
+    ct.nonneg = True
+    from oracle.power import power_method
+    L = power_method(lambda x: ct.A.adjoint(ct.A.forward(x)), ct.shape, 300)
+    st = 0.99 / math.sqrt(L)
+    imp = solvers.pdhg(ct, np.zeros(ct.shape), np.zeros_like(ct.b), st, st, 800, 40)
+    out = solvers.pdhg_explicit(ct, np.zeros(ct.shape), K=1500)
+    assert out["x"].min() >= 0.0
+    assert np.linalg.norm(out["x"] - imp["x"]) <= 2e-5 * np.linalg.norm(imp["x"])
+    f_imp = imp["objective"][-1]
+    assert -1e-9 <= (out["objective"][-1] - f_imp) / f_imp <= 2e-6
