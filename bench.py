@@ -37,6 +37,15 @@ P_SKIP = 0.5
 P_OTHERS = (0.1, 0.05)
 F_STAR_ITERS, F_STAR_INNER = 3000, 100
 FGP_BYTES_PER_PX = 28        # read z (4) + p_k (8) + p_{k-1} (8), write p_{k+1} (8), FP32 dual
+# DRAM bytes (read + write) per launch of the 2D FGP kernel inside this workload's
+# ProxSkip solve, averaged over the 26 launches of two proxes (the first launch of
+# a prox reads no previous dual), from one ncu capture of
+# `dram__bytes_read.sum + dram__bytes_write.sum`.  It describes only the kernel
+# sources and launch configuration it was taken on: the bench line carries it only
+# while the hash of those sources and the autotuned configuration still match.
+FGP_TRAFFIC = {"config": [4, 1, 105], "bytes": 20359906,
+               "sources": ["common.cuh", "fgp_rb.cuh", "fgp.cu"],
+               "sha256": "8a330bf64bc3ba8e16d0280689fe4535f74d6e6b6085dc2c3f6001aa52760492"}
 # Iterations / prox calls this workload's ProxSkip solve needs to reach the target
 # (from the solver's trace); used only to scale the CPU oracle sample.
 REF_ITERS_DEFAULT, REF_PROX_DEFAULT = 260, 130
@@ -53,6 +62,19 @@ def _peaks():
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def _fgp_traffic(fgp_cfg):
+    """The recorded DRAM traffic per launch, or None when the kernel or its
+    configuration differs from the one it was measured on."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in FGP_TRAFFIC["sources"]:
+        with open(os.path.join(ROOT, "paper_2411_00688_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    if h.hexdigest() != FGP_TRAFFIC["sha256"] or list(fgp_cfg) != FGP_TRAFFIC["config"]:
+        return None
+    return FGP_TRAFFIC["bytes"]
 
 
 def _workload_inputs():
@@ -315,7 +337,7 @@ def run_gpu(args):
         "proxskip_by_p": per_p,
         "fista": fista,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": None,
+                     "frac": achieved / hbm_peak, "traffic": _fgp_traffic(fgp_cfg),
                      "kernel": ("fgp2d_rb_kernel" if fgp_cfg[2] >= 100 else "fgp2d_tb_kernel")
                                + f"<float> ({fgp_cfg[0]} inner iterations per launch, config {list(fgp_cfg)})",
                      "bytes_per_launch": bytes_per_launch,

@@ -251,6 +251,36 @@ tvs_status pdhgskip_solve(tvs_problem* prob, const tvs_pd_params* prm, float* x_
 tvs_status pdhgskip1_solve(tvs_problem* prob, const tvs_pd_params* prm, float* x_inout,
                            float* y_inout, tvs_mem mem, tvs_trace* trace);
 
+/* Explicit PDHG with diagonal preconditioning: the explicit formulation of
+ * Section 3.2 (K = [A; D], f = 1/2 ||. - b||^2 + alpha ||.||_{2,1}, g = 0 or the
+ * non-negativity indicator when the problem has nonneg set, every prox closed
+ * form), the solver the paper uses for its reference solutions (Section 4.1),
+ * with the step sizes of Pock and Chambolle (ICCV 2011, Lemma 2, exponent 1):
+ * pixel j steps T_j = sigma / sum_i |K_ij| = sigma / ((A^T 1)_j + n_j), where n_j
+ * counts the differences touching pixel j; row i of A steps S_i = tau / (A 1)_i;
+ * the rows of D step tau / 2.  An empty row or column steps by the bare scale.
+ * Per iteration:
+ *   x+ = P_X(x - T (A^T y - div q));  x- = 2 x+ - x;
+ *   y+ = (y + S (A x- - b)) / (1 + S);  q+ = P_alpha(q + (tau/2) D x-).
+ * sigma, tau > 0 with sigma * tau <= 1 (1, 1 is the lemma's choice).  2D only. */
+typedef struct {
+  double sigma;            /* primal step scale                                  */
+  double tau;              /* dual step scale                                    */
+  int max_iter;
+  double f_star;           /* > 0: stop at the relative-gap target               */
+  double target_rel_gap;
+  int objective_every;     /* record F(x_{k+1}) every this many iterations (>= 1) */
+  double target_rel_dist;  /* as in tvs_fb_params                                */
+} tvs_pdx_params;
+/* x_inout (image), y_inout (measurement size) and q_inout (two planes of the
+ * image size, vertical then horizontal differences; may be NULL for q_0 = 0 and
+ * no output) carry the iterates in and out, so a long solve can run in pieces.
+ * The trace as for the other solvers (every iteration counts as a prox call; the
+ * inner-iteration fields are 0).  The first call on a problem allocates one
+ * measurement-sized work buffer that the problem keeps. */
+tvs_status pdhg_explicit_solve(tvs_problem* prob, const tvs_pdx_params* prm, float* x_inout,
+                               float* y_inout, float* q_inout, tvs_mem mem, tvs_trace* trace);
+
 /* ---- many independent problems at once -------------------------------------- */
 /* ProxSkip on n independent 2D problems (identity or blur operators; any sizes),
  * each with its own alpha (from its problem), gamma, p, seed, f_star and target

@@ -14,6 +14,7 @@ from .api import (  # noqa: F401
     pd_steps,
     pdhg_solve,
     pdhgskip1_solve,
+    pdhg_explicit_solve,
     pdhgskip_solve,
     pgd_solve,
     proxskip_solve,

@@ -48,6 +48,12 @@ class PDParams(C.Structure):
                 ("target_rel_dist", C.c_double)]
 
 
+class PDXParams(C.Structure):
+    _fields_ = [("sigma", C.c_double), ("tau", C.c_double), ("max_iter", C.c_int),
+                ("f_star", C.c_double), ("target_rel_gap", C.c_double),
+                ("objective_every", C.c_int), ("target_rel_dist", C.c_double)]
+
+
 class RofParams(C.Structure):
     _fields_ = [("alpha", C.c_double), ("eps", C.c_double), ("gamma", C.c_double), ("p", C.c_double),
                 ("seed", C.c_uint64), ("max_iter", C.c_int), ("f_star", C.c_double),
@@ -92,6 +98,8 @@ SIGNATURES = [
                                  C.POINTER(Trace)]),
     ("pdhgskip1_solve", C.c_int, [C.c_void_p, C.POINTER(PDParams), C.c_void_p, C.c_void_p, C.c_int,
                                   C.POINTER(Trace)]),
+    ("pdhg_explicit_solve", C.c_int, [C.c_void_p, C.POINTER(PDXParams), C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_int, C.POINTER(Trace)]),
     ("proxskip_solve_batch", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(FBParams),
                                        C.POINTER(C.c_void_p), C.c_int, C.POINTER(Trace)]),
     ("dual_rof_solve", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_void_p, C.POINTER(RofParams), C.c_void_p,

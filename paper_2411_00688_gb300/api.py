@@ -365,6 +365,29 @@ def pdhgskip1_solve(prob, x, y, sigma, tau, p, seed, max_iter, n_inner, **kw):
     return _pd("pdhgskip1_solve", prob, x, y, sigma, tau, max_iter, n_inner, p=p, seed=seed, **kw)
 
 
+def pdhg_explicit_solve(prob, x, y, q=None, max_iter=100, sigma=1.0, tau=1.0, f_star=0.0, target=0.0,
+                        every=1, target_dist=0.0):
+    """Explicit PDHG with diagonal preconditioning (the explicit formulation of
+    Section 3.2; the paper's solver for reference solutions).  x (image), y
+    (measurement size) and the optional q (2, H, W) carry the iterates in and out."""
+    prm = L.PDXParams(sigma=float(sigma), tau=float(tau), max_iter=int(max_iter), f_star=float(f_star),
+                      target_rel_gap=float(target), objective_every=int(every),
+                      target_rel_dist=float(target_dist))
+    px, mem, kx = _arr(x, "x")
+    py, mem_y, ky = _arr(y, "y")
+    pq, mem_q = None, mem
+    if q is not None:
+        pq, mem_q, kq = _arr(q, "q")
+    if len({mem, mem_y, mem_q}) != 1:
+        raise ValueError("x, y and q must live in the same memory")
+    if mem == L.MEM_DEVICE:
+        _sync_torch()
+    tr, buf = _new_trace(max(int(max_iter), 1))
+    L.check(L.lib().pdhg_explicit_solve(prob.handle, C.byref(prm), C.c_void_p(px), C.c_void_p(py),
+                                        C.c_void_p(pq) if pq is not None else None, mem, C.byref(tr)))
+    return x, y, q, _finish_trace(tr, buf)
+
+
 def dual_rof_solve(ctx: Context, b, q, alpha, gamma, max_iter, p=1.0, seed=0, eps=0.0, u=None,
                    f_star=0.0, target=0.0):
     """Projected gradient (p = 1) or ProxSkip on Dual-ROF / Dual-Huber-ROF.

@@ -122,6 +122,7 @@ struct tvs_problem {
   double uref_norm2 = 0.0;
   double* part_c = nullptr;     // partials of ||x - uref||^2
   double* dist_dev = nullptr;   // relative distance per trace entry
+  float* aux = nullptr;         // m floats, allocated by the first explicit PDHG solve
   size_t bytes = 0;
 };
 
@@ -928,6 +929,123 @@ tvs_status pd1_solve(tvs_problem* P, const tvs_pd_params* prm, float* x_io, floa
   return finish_solve(P, K, ls, coins, use_prox ? N : 0, fcfg, tr);
 }
 
+// Explicit PDHG with diagonal preconditioning (kernels and formulas in pdx.cu).
+// Buffers: x[2] primal parity, dual[0..1] q parity (FP32, 2 n), z = A^T y,
+// h = T (pixel steps), r = S (row steps), aux = A x+, axp = A x.
+tvs_status apply_A(tvs_problem* P, const float* x, float* out, cudaStream_t s) {
+  const Dims& d = P->dims;
+  switch (P->desc.op.kind) {
+    case TVS_OP_GAUSS_BLUR: CUDA_TRY(launch_blur(d.ny, d.nx, x, out, P->bw, s)); break;
+    case TVS_OP_PARALLEL_BEAM:
+      CUDA_TRY(launch_ct_forward(P->geom, x, out, nullptr, nullptr, 0.f, nullptr, CT_FWD_PLAIN, s));
+      break;
+    default: CUDA_TRY(cudaMemcpyAsync(out, x, P->n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  }
+  return TVS_OK;
+}
+tvs_status apply_At(tvs_problem* P, const float* y, float* out, cudaStream_t s) {
+  const Dims& d = P->dims;
+  switch (P->desc.op.kind) {
+    case TVS_OP_GAUSS_BLUR: CUDA_TRY(launch_blur(d.ny, d.nx, y, out, P->bw, s)); break;  // A = A^T
+    case TVS_OP_PARALLEL_BEAM:
+      CUDA_TRY(launch_ct_backward(P->geom, y, nullptr, nullptr, out, 0.f, 0.f, nullptr, s));
+      break;
+    default: CUDA_TRY(cudaMemcpyAsync(out, y, P->n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  }
+  return TVS_OK;
+}
+
+tvs_status pdx_solve(tvs_problem* P, const tvs_pdx_params* prm, float* x_io, float* y_io, float* q_io,
+                     tvs_mem mem, tvs_trace* tr) {
+  if (!prm) return fail(TVS_EINVAL, "null params");
+  TVS_TRY(check_common(P, prm->max_iter, 0, TVS_DUAL_F32, prm->f_star, prm->target_rel_gap,
+                       prm->objective_every, x_io));
+  if (!y_io) return fail(TVS_EINVAL, "null y_inout");
+  if (!(prm->sigma > 0) || !(prm->tau > 0) || !is_fin(prm->sigma) || !is_fin(prm->tau))
+    return fail(TVS_EINVAL, "sigma and tau must be > 0");
+  if (prm->sigma * prm->tau > 1.0 + 1e-12) return fail(TVS_EINVAL, "sigma * tau must be <= 1");
+  if (!(prm->target_rel_dist >= 0) || !is_fin(prm->target_rel_dist)) return fail(TVS_EINVAL, "invalid target_rel_dist");
+  if (mem != TVS_MEM_DEVICE && mem != TVS_MEM_HOST) return fail(TVS_EINVAL, "invalid mem kind");
+  if (P->dims.ndim != 2) return fail(TVS_EUNSUPPORTED, "primal-dual solvers are 2D");
+  const int K = prm->max_iter, every = prm->objective_every < 1 ? 1 : prm->objective_every;
+  const bool nonneg = P->desc.nonneg != 0;
+  const double alpha = P->desc.alpha;
+  const bool ident = P->desc.op.kind == TVS_OP_IDENTITY;
+  tvs_ctx* C = P->ctx;
+  cudaStream_t s = C->stream;
+  const Dims& d = P->dims;
+  if (!P->aux) TVS_TRY(palloc(P, &P->aux, P->m));
+  float* T = P->h;
+  float* S = P->r;
+
+  TVS_TRY(begin_solve(P, K, -1));
+  // step sizes from the row sums A 1 (into aux) and column sums A^T 1 (into z)
+  if (ident) {
+    CUDA_TRY(launch_pdx_precond(nullptr, nullptr, d.ny, d.nx, P->m, (float)prm->sigma, (float)prm->tau, T, S, s));
+  } else {
+    CUDA_TRY(launch_fill(P->x[1], P->n, 1.f, s));
+    TVS_TRY(apply_A(P, P->x[1], P->aux, s));
+    CUDA_TRY(launch_fill(P->axp, P->m, 1.f, s));
+    TVS_TRY(apply_At(P, P->axp, P->z, s));
+    CUDA_TRY(launch_pdx_precond(P->z, P->aux, d.ny, d.nx, P->m, (float)prm->sigma, (float)prm->tau, T, S, s));
+  }
+  TVS_TRY(copy_in(P->x[0], x_io, P->n, mem, s));
+  TVS_TRY(copy_in(P->y, y_io, P->m, mem, s));
+  float* q0 = (float*)P->dual[0];
+  if (q_io) TVS_TRY(copy_in(q0, q_io, 2 * P->n, mem, s));
+  else CUDA_TRY(cudaMemsetAsync(q0, 0, 2 * P->n * sizeof(float), s));
+  // A x_0 and the data partials of x_0
+  const float* ax0 = P->x[0];
+  if (!ident) {
+    TVS_TRY(apply_A(P, P->x[0], P->aux, s));
+    ax0 = P->aux;
+  }
+  CUDA_TRY(launch_pdx_dual(P->m, ax0, P->axp, P->y, P->b, S, true, P->part_a, s));
+  const int na = pointwise_blocks(P->m), nb = pdx_tv_blocks(d.ny, d.nx);
+  const float s_d = (float)(0.5 * prm->tau);
+  GraphSet G;
+  for (int par = 0; par < 2; ++par) {
+    float* xc = P->x[par];
+    float* xn = P->x[par ^ 1];
+    const float* qc = (const float*)P->dual[par];
+    float* qn = (float*)P->dual[par ^ 1];
+    TVS_TRY(capture(s, &G.exec[1][par], [&]() -> tvs_status {
+      const float* g = P->y;
+      if (!ident) {
+        TVS_TRY(apply_At(P, P->y, P->z, s));
+        g = P->z;
+      }
+      CUDA_TRY(launch_pdx_tv_step(d.ny, d.nx, xc, g, T, qc, xn, qn, (float)alpha, s_d, nonneg, P->part_b, s));
+      CUDA_TRY(launch_reduce_record(P->part_a, na, P->part_b, nb, alpha, every, P->obj_dev, P->ts_dev,
+                                    prm->f_star, prm->target_rel_gap, P->flags, P->done_host_dev, nullptr, s));
+      TVS_TRY(track_distance(P, xc, prm->target_rel_dist, s));
+      const float* ax = xn;
+      if (!ident) {
+        TVS_TRY(apply_A(P, xn, P->aux, s));
+        ax = P->aux;
+      }
+      CUDA_TRY(launch_pdx_dual(P->m, ax, P->axp, P->y, P->b, S, false, P->part_a, s));
+      return TVS_OK;
+    }));
+  }
+  std::vector<unsigned char> coins(K, 1);
+  LoopState ls;
+  TVS_TRY(run_loop(P, K, coins, G, &ls));
+  float* xfin = P->x[ls.iters & 1];
+  const float* qfin = (const float*)P->dual[ls.iters & 1];
+  if (ls.iters > 0) {
+    CUDA_TRY(launch_tv_partials(d, xfin, P->part_b, s));
+    CUDA_TRY(launch_reduce_record(P->part_a, na, P->part_b, pointwise_blocks(P->n), alpha, 1, P->obj_dev,
+                                  P->ts_dev, prm->f_star, prm->target_rel_gap, P->flags, P->done_host_dev,
+                                  nullptr, s));
+    TVS_TRY(track_distance(P, xfin, prm->target_rel_dist, s));
+  }
+  TVS_TRY(copy_out(x_io, xfin, P->n, mem, s));
+  TVS_TRY(copy_out(y_io, P->y, P->m, mem, s));
+  if (q_io) TVS_TRY(copy_out(q_io, qfin, 2 * P->n, mem, s));
+  return finish_solve(P, K, ls, coins, 0, FgpConfig{}, tr);
+}
+
 }  // namespace
 
 
@@ -1502,7 +1620,8 @@ tvs_status tvs_problem_destroy(tvs_problem* P) {
   cudaStreamSynchronize(C->stream);
   void* bufs[] = {P->b, P->x[0], P->x[1], P->z, P->h, P->r, P->y, P->axp, P->dual[0], P->dual[1],
                   P->dual[2], P->dual[3], P->part_a, P->part_b, P->obj_dev, P->ts_dev, P->fgp_ts, P->beta_dev,
-                  P->flags, P->count, P->angle_tab, P->angle_tab2, P->xt, P->uref, P->part_c, P->dist_dev};
+                  P->flags, P->count, P->angle_tab, P->angle_tab2, P->xt, P->uref, P->part_c, P->dist_dev,
+                  P->aux};
   for (void* b : bufs) dfree(b);
   if (P->done_host) cudaFreeHost(P->done_host);
   C->bytes -= P->bytes;
@@ -1646,6 +1765,10 @@ tvs_status pdhgskip_solve(tvs_problem* P, const tvs_pd_params* prm, float* x, fl
   return pd_solve(P, prm, x, y, mem, tr, true);
 }
 
+tvs_status pdhg_explicit_solve(tvs_problem* P, const tvs_pdx_params* prm, float* x, float* y, float* q,
+                               tvs_mem mem, tvs_trace* tr) {
+  return pdx_solve(P, prm, x, y, q, mem, tr);
+}
 tvs_status pdhgskip1_solve(tvs_problem* P, const tvs_pd_params* prm, float* x, float* y, tvs_mem mem,
                            tvs_trace* tr) {
   return pd1_solve(P, prm, x, y, mem, tr);

@@ -537,7 +537,7 @@ __global__ void fgp_finalize_kernel(const float* __restrict__ z, const T* __rest
 }
 
 // z-marching variants: (columns per lane, rows per warp, planes per chunk);
-// TVS_FGP3D_CFG="cpl,rpw,zc" selects one (default 1,2,64).
+// TVS_FGP3D_CFG="cpl,rpw,zc" selects one.
 template <typename T, bool NN, int CPL, int RPW, int ZC>
 cudaError_t fgp3d_zm_launch(const Dims& d, const float* z, const void* pc, const void* pp, void* pn, float lam,
                             float inv_step, float beta, cudaStream_t s) {
@@ -549,10 +549,12 @@ cudaError_t fgp3d_zm_launch(const Dims& d, const float* z, const void* pc, const
 }
 
 struct ZmCfg {
-  int cpl = 1, rpw = 2, zc = 64;  // fastest measured at 512^3 (FP32 and BF16 duals)
+  int cpl = 0, rpw = 0, zc = 0;
 };
-ZmCfg fgp3d_zm_cfg() {
-  static const ZmCfg c = [] {
+// Defaults: the fastest variant measured at 512^3 for each dual width (FP32:
+// 1,2,64; BF16 and FP16: 2,2,32); TVS_FGP3D_CFG overrides both.
+ZmCfg fgp3d_zm_cfg(bool half_dual) {
+  static const ZmCfg env = [] {
     ZmCfg r;
     if (const char* e = getenv("TVS_FGP3D_CFG")) {
       ZmCfg t;
@@ -560,13 +562,18 @@ ZmCfg fgp3d_zm_cfg() {
     }
     return r;
   }();
+  if (env.cpl > 0) return env;
+  ZmCfg c;
+  c.cpl = half_dual ? 2 : 1;
+  c.rpw = 2;
+  c.zc = half_dual ? 32 : 64;
   return c;
 }
 
 template <typename T, bool NN>
 cudaError_t fgp3d_zm_dispatch(const Dims& d, const float* z, const void* pc, const void* pp, void* pn, float lam,
                               float inv_step, float beta, cudaStream_t s) {
-  const ZmCfg c = fgp3d_zm_cfg();
+  const ZmCfg c = fgp3d_zm_cfg(sizeof(T) == 2);
 #define TVS_ZM(C_, R_, Z_) \
   if (c.cpl == C_ && c.rpw == R_ && c.zc == Z_) return fgp3d_zm_launch<T, NN, C_, R_, Z_>(d, z, pc, pp, pn, lam, inv_step, beta, s);
   TVS_ZM(1, 4, 64)

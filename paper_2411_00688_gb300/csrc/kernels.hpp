@@ -116,6 +116,17 @@ cudaError_t launch_coin_schedule(uint64_t seed, double p, int64_t k0, int K, uns
                                  cudaStream_t s);
 
 // ---- Dual-ROF / Dual-Huber-ROF (rof.cu) ----
+// Explicit, diagonally preconditioned PDHG (pdx.cu).
+int pdx_tv_blocks(int H, int W);
+cudaError_t launch_pdx_precond(const float* colA, const float* rowA, int H, int W, size_t m, float sigma,
+                               float tau, float* T, float* S, cudaStream_t s);
+cudaError_t launch_fill(float* a, size_t n, float v, cudaStream_t s);
+cudaError_t launch_pdx_tv_step(int H, int W, const float* x, const float* g, const float* T, const float* q,
+                               float* xn, float* qn, float alpha, float s_d, bool nonneg, double* part_tv,
+                               cudaStream_t s);
+cudaError_t launch_pdx_dual(size_t m, const float* ax, float* axp, float* y, const float* b, const float* S,
+                            bool init, double* part_a, cudaStream_t s);
+
 int dual_rof_blocks(int H, int W);
 // One ProxSkip / projected-gradient step on q (2 planes) -> qn; h updated in place
 // on prox iterations (h == null: projected gradient).  Partials: 1/2 (div q + b)^2

@@ -6,9 +6,11 @@ single launches of the kernel of interest:
 
     python -m paper_2411_00688_gb300.prof --shape 4096 4096 --iters 8 --reps 3
     python -m paper_2411_00688_gb300.prof --shape 256 256 256 --iters 4 --dual bf16
+    python -m paper_2411_00688_gb300.prof --ct 512 720 725 --reps 3
 
 It prints the per-iteration time measured with CUDA events on the launching
-stream (not meaningful under a profiler).
+stream (not meaningful under a profiler).  --ct N ANGLES BINS instead applies the
+parallel-beam projector and backprojector of an N x N unit-square geometry.
 """
 
 from __future__ import annotations
@@ -30,7 +32,10 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--lam", type=float, default=0.2)
     ap.add_argument("--dual", default="f32", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--ct", type=int, nargs=3, default=None, metavar=("N", "ANGLES", "BINS"))
     args = ap.parse_args(argv)
+    if args.ct:
+        return _ct(args, tvs, L)
 
     stream = torch.cuda.Stream()
     ctx = tvs.Context.__new__(tvs.Context)
@@ -56,6 +61,37 @@ def main(argv=None):
         times.append(e0.elapsed_time(e1) / max(args.iters, 1))
     print(f"shape {shape} dual {args.dual}: {statistics.median(times) * 1e3:.2f} us per inner iteration "
           f"(incl. finalisation)")
+    ctx.close()
+
+
+def _ct(args, tvs, L):
+    import torch
+    N, na, nd = args.ct
+    stream = torch.cuda.Stream()
+    ctx = tvs.Context.__new__(tvs.Context)
+    ctx._h = C.c_void_p()
+    L.check(L.lib().tvs_create(C.byref(ctx._h), torch.cuda.current_device(), C.c_void_p(stream.cuda_stream)))
+    ctx.device = torch.cuda.current_device()
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    x = torch.rand((N, N), device="cuda", generator=g)
+    y = torch.rand((na, nd), device="cuda", generator=g)
+    prob = tvs.Problem(ctx, y, 0.0, op="ct", shape=(N, N), n_angles=na, n_det=nd, pixel_size=1.0 / N,
+                       det_spacing=1.0 / N)
+    ax = torch.empty_like(y)
+    aty = torch.empty_like(x)
+    for name, src, dst, adj in (("projector", x, ax, False), ("backprojector", y, aty, True)):
+        times = []
+        for _ in range(args.reps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tvs.tvs_op_apply(prob, src, dst, adjoint=adj)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        print(f"{name} {N}^2, {na} angles, {nd} bins: {statistics.median(times) * 1e3:.1f} us")
+    prob.close()
     ctx.close()
 
 

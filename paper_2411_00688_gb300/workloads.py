@@ -2,7 +2,10 @@
 benchmark's headline one (python -m paper_2411_00688_gb300.workloads NAME ...).
 
   denoise2d_256  ProxSkip p = 0.1 vs PGD, 100 inner iterations, <= 500 iterations
-  ct2d_512       PDHGSkip-2 p in {0.2, 0.05} vs PDHG, 50 inner, <= 2000 iterations
+  ct2d_512       PDHGSkip-2 p in {0.2, 0.05} vs PDHG, 50 inner, <= 2000 iterations; explicit
+                 preconditioned PDHG (closed-form proxes) <= 20000 iterations
+  deblur2d_1024  explicit preconditioned PDHG, <= 20000 iterations (the ProxSkip / PGD /
+                 FISTA numbers of this workload come from the benchmark)
   denoise3d_512  ProxSkip p = 0.1 vs PGD, 30 inner, <= 200 iterations (FP32 / BF16 / FP16 dual)
   batch2d_256    256 uneven problems: one batched solve vs a loop of single solves
 
@@ -115,7 +118,34 @@ def ct2d_512():
         fn()
         (_, _, tr), wall = _timed(fn)
         out.append(_solve_record(name, tr, wall, f_star, workload=cfg.name, norm_A_sq=L, sigma=st, tau=st))
+    out.append(_explicit(tvs, prob, x0, zeros_sino, f_star, cfg.name))
     return out
+
+
+def _explicit(tvs, prob, x0, y0, f_star, name, K=20000):
+    def run():
+        return tvs.pdhg_explicit_solve(prob, x0.clone(), y0.clone(), None, K, f_star=f_star, target=TARGET)
+    run()
+    (_, _, _, tr), wall = _timed(run)
+    return _solve_record("pdhg_explicit", tr, wall, f_star, workload=name,
+                         ms_per_iteration=tr.solve_ms / max(tr.iters_run, 1))
+
+
+def deblur2d_1024():
+    import torch
+    from synth.configs import DeblurConfig
+    tvs, ctx = _ctx()
+    cfg = DeblurConfig()
+    truth = torch.from_numpy(cfg.phantom().astype(np.float32)).cuda()
+    noise = torch.from_numpy(cfg.noise().astype(np.float32)).cuda()
+    prob = tvs.Problem(ctx, truth, cfg.alpha, op="blur", blur_sigma=cfg.blur_sigma)
+    b = torch.empty_like(truth)
+    tvs.tvs_op_apply(prob, truth, b)
+    b = (b + noise).contiguous()
+    prob.set_data(b)
+    _, ref = tvs.fista_solve(prob, b.clone(), 1.0, 3000, 100)  # gamma = 1/||A||^2 = 1
+    f_star = float(np.nanmin(ref.objective))
+    return [_explicit(tvs, prob, b, torch.zeros_like(b), f_star, cfg.name)]
 
 
 def denoise3d_512(duals=("f32", "bf16", "f16")):
@@ -193,14 +223,16 @@ def _batch(n_problems=None, K=None):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("workload", choices=["denoise2d_256", "ct2d_512", "denoise3d_512", "batch2d_256"])
+    ap.add_argument("workload", choices=["denoise2d_256", "ct2d_512", "denoise3d_512", "batch2d_256",
+                                         "deblur2d_1024"])
     ap.add_argument("--problems", type=int, default=None)
     ap.add_argument("--iters", type=int, default=None)
     args = ap.parse_args(argv)
     if args.workload == "batch2d_256":
         recs = _batch(args.problems, args.iters)
     else:
-        recs = {"denoise2d_256": denoise2d_256, "ct2d_512": ct2d_512, "denoise3d_512": denoise3d_512}[args.workload]()
+        recs = {"denoise2d_256": denoise2d_256, "ct2d_512": ct2d_512, "denoise3d_512": denoise3d_512,
+                "deblur2d_1024": deblur2d_1024}[args.workload]()
     for r in recs:
         print(json.dumps(r), flush=True)
 

@@ -55,7 +55,7 @@ def test_struct_layout_matches_c(tmp_path, built_lib):
         pytest.skip("no C compiler")
     structs = {"tvs_op_desc": L.OpDesc, "tvs_problem_desc": L.ProblemDesc,
                "tvs_fb_params": L.FBParams, "tvs_pd_params": L.PDParams, "tvs_trace": L.Trace,
-               "tvs_rof_params": L.RofParams}
+               "tvs_rof_params": L.RofParams, "tvs_pdx_params": L.PDXParams}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tvs.h"', "int main(void){"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
