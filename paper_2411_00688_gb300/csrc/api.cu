@@ -74,7 +74,7 @@ struct tvs_ctx {
   size_t prox_scratch_bytes = 0;
   double* red_out = nullptr;  // one double for tvs_objective
   int* flags = nullptr;       // scratch flags for tvs_objective
-  double* parts = nullptr;    // partials for tvs_objective
+  Partial* parts = nullptr;    // partials for tvs_objective
   size_t parts_cap = 0;
   cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
   cudaEvent_t ring[LAG] = {};
@@ -106,8 +106,8 @@ struct tvs_problem {
   float* y = nullptr;
   float* axp = nullptr;
   void* dual[4] = {nullptr, nullptr, nullptr, nullptr};
-  double* part_a = nullptr;
-  double* part_b = nullptr;
+  Partial* part_a = nullptr;
+  Partial* part_b = nullptr;
   int max_parts = 0;
   double* obj_dev = nullptr;
   unsigned long long* ts_dev = nullptr;   // [cap] objective timestamps, [cap] = solve start
@@ -120,7 +120,7 @@ struct tvs_problem {
   int* count = nullptr;
   float* uref = nullptr;        // reference solution (tvs_problem_set_reference)
   double uref_norm2 = 0.0;
-  double* part_c = nullptr;     // partials of ||x - uref||^2
+  Partial* part_c = nullptr;     // partials of ||x - uref||^2
   double* dist_dev = nullptr;   // relative distance per trace entry
   float* aux = nullptr;         // m floats, allocated by the first explicit PDHG solve
   size_t bytes = 0;
@@ -354,14 +354,14 @@ tvs_status ensure_trace(tvs_problem* P, int K) {
 // Partials of the data term / TV term written by the step kernels.
 int step_parts_a(const tvs_problem* P) {
   switch (P->desc.op.kind) {
-    case TVS_OP_GAUSS_BLUR: return tile_blocks_2d(P->dims.ny, P->dims.nx);
+    case TVS_OP_GAUSS_BLUR: return fb_step_blocks_2d(P->dims.ny, P->dims.nx);
     case TVS_OP_PARALLEL_BEAM: return ct_fwd_blocks(P->geom);
     default: return pointwise_blocks(P->n);
   }
 }
 int step_parts_b(const tvs_problem* P) {
   switch (P->desc.op.kind) {
-    case TVS_OP_GAUSS_BLUR: return tile_blocks_2d(P->dims.ny, P->dims.nx);
+    case TVS_OP_GAUSS_BLUR: return fb_step_blocks_2d(P->dims.ny, P->dims.nx);
     case TVS_OP_PARALLEL_BEAM: return ct_bwd_blocks(P->geom);
     default: return pointwise_blocks(P->n);
   }
@@ -373,8 +373,7 @@ tvs_status fb_step(tvs_problem* P, const float* src, float* out, const float* h,
   const Dims& d = P->dims;
   switch (P->desc.op.kind) {
     case TVS_OP_GAUSS_BLUR:
-      CUDA_TRY(launch_blur_residual(d.ny, d.nx, src, P->b, P->r, P->bw, P->part_a, P->part_b, s));
-      CUDA_TRY(launch_blur_step(d.ny, d.nx, P->r, src, h, out, P->bw, gamma, ch, nullptr, s));
+      CUDA_TRY(launch_blur_fb_step(d.ny, d.nx, src, P->b, h, out, P->bw, gamma, ch, P->part_a, P->part_b, s));
       break;
     case TVS_OP_PARALLEL_BEAM:
       CUDA_TRY(launch_ct_forward(P->geom, src, P->r, nullptr, P->b, 0.f, P->part_a, CT_FWD_RESID, s));
@@ -387,7 +386,7 @@ tvs_status fb_step(tvs_problem* P, const float* src, float* out, const float* h,
 }
 
 // Partials of F(x) only; returns their counts.
-tvs_status objective_parts(tvs_problem* P, const float* x, double* pa, double* pb, int* na, int* nb,
+tvs_status objective_parts(tvs_problem* P, const float* x, Partial* pa, Partial* pb, int* na, int* nb,
                            cudaStream_t s) {
   const Dims& d = P->dims;
   switch (P->desc.op.kind) {
@@ -412,7 +411,7 @@ tvs_status objective_parts(tvs_problem* P, const float* x, double* pa, double* p
 tvs_status pd_backward(tvs_problem* P, const float* x, float* out, const float* h, float sigma,
                        float ch, cudaStream_t s, bool tv_partials = true) {
   const Dims& d = P->dims;
-  double* pb = tv_partials ? P->part_b : nullptr;
+  Partial* pb = tv_partials ? P->part_b : nullptr;
   switch (P->desc.op.kind) {
     case TVS_OP_GAUSS_BLUR:
       CUDA_TRY(launch_blur_step(d.ny, d.nx, P->y, x, h, out, P->bw, sigma, ch, pb, s));
@@ -1200,8 +1199,8 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
   L.n_fgp_tiles = (int)fgp_tiles.size();
   L.n_all_chunks = (int)all_chunks.size();
   TVS_TRY(S.zeros<int>(1, &L.kctr, s));
-  TVS_TRY(S.zeros<double>((size_t)n_blur + ident_chunks.size(), &L.part_a, s));
-  TVS_TRY(S.zeros<double>((size_t)n_blur + ident_chunks.size(), &L.part_b, s));
+  TVS_TRY(S.zeros<Partial>((size_t)n_blur + ident_chunks.size(), &L.part_a, s));
+  TVS_TRY(S.zeros<Partial>((size_t)n_blur + ident_chunks.size(), &L.part_b, s));
   unsigned long long* t0_dev = nullptr;
   TVS_TRY(S.zeros<unsigned long long>(1, &t0_dev, s));
   {
@@ -1308,7 +1307,8 @@ extern "C" tvs_status dual_rof_solve(tvs_ctx* C, const int dims[2], const float*
   cudaStream_t s = C->stream;
   BatchScratch S;
   float *q0, *q1, *h = nullptr, *bd;
-  double *pa, *pb, *obj;
+  Partial *pa, *pb;
+  double* obj;
   unsigned long long* ts;
   int* flags;
   const int nparts = std::max(dual_rof_blocks(H, W), pointwise_blocks(n));
@@ -1316,8 +1316,8 @@ extern "C" tvs_status dual_rof_solve(tvs_ctx* C, const int dims[2], const float*
   TVS_TRY(S.zeros<float>(2 * n, &q1, s));
   if (skip) TVS_TRY(S.zeros<float>(2 * n, &h, s));
   TVS_TRY(S.zeros<float>(n, &bd, s));
-  TVS_TRY(S.zeros<double>(nparts, &pa, s));
-  TVS_TRY(S.zeros<double>(nparts, &pb, s));
+  TVS_TRY(S.zeros<Partial>(nparts, &pa, s));
+  TVS_TRY(S.zeros<Partial>(nparts, &pb, s));
   TVS_TRY(S.zeros<double>((size_t)K + 1, &obj, s));
   TVS_TRY(S.zeros<unsigned long long>((size_t)K + 2, &ts, s));
   TVS_TRY(S.zeros<int>(4, &flags, s));

@@ -25,7 +25,7 @@ __device__ __forceinline__ bool active(const BatchState& st) { return st.done ==
 template <int R>
 __global__ void __launch_bounds__(BNT)
 batch_blur_resid_kernel(const BatchProb* __restrict__ probs, BatchState* __restrict__ state,
-                        const int4* __restrict__ tiles, int par, double* part_a, double* part_b) {
+                        const int4* __restrict__ tiles, int par, Partial* part_a, Partial* part_b) {
   const int4 e = tiles[blockIdx.x];
   const BatchProb& P = probs[e.x];
   if (!active(state[e.x])) return;
@@ -54,8 +54,8 @@ batch_blur_step_kernel(const BatchProb* __restrict__ probs, BatchState* __restri
 __global__ void __launch_bounds__(256)
 batch_ident_step_kernel(const BatchProb* __restrict__ probs, BatchState* __restrict__ state,
                         const int2* __restrict__ chunks, const unsigned char* __restrict__ coins, int n,
-                        const int* __restrict__ kctr, int par, int write_out, double* part_a,
-                        double* part_b, int part_base) {
+                        const int* __restrict__ kctr, int par, int write_out, Partial* part_a,
+                        Partial* part_b, int part_base) {
   const int2 e = chunks[blockIdx.x];
   const BatchProb& P = probs[e.x];
   if (!active(state[e.x])) return;
@@ -65,7 +65,7 @@ batch_ident_step_kernel(const BatchProb* __restrict__ probs, BatchState* __restr
   float* out = coin ? P.z : (par ? P.x0 : P.x1);
   const float ch = coin ? P.ch_prox : P.ch_skip;
   const size_t npx = (size_t)P.H * P.W;
-  double acc_a = 0.0, acc_b = 0.0;
+  FAcc acc_a, acc_b;
   for (int t = threadIdx.x; t < CHUNK; t += 256) {
     const size_t o = (size_t)e.y * CHUNK + t;
     if (o >= npx) break;
@@ -73,10 +73,10 @@ batch_ident_step_kernel(const BatchProb* __restrict__ probs, BatchState* __restr
     const float xc = __ldg(x + o), bb = __ldg(P.b + o);
     const float r = xc - bb;
     if (write_out) out[o] = fmaf(ch, __ldg(P.h + o), xc - P.gamma * r);
-    acc_a += 0.5 * (double)(r * r);
+    acc_a.add(0.5f * (r * r));
     const float dy = gi < P.H - 1 ? __ldg(x + o + P.W) - xc : 0.f;
     const float dx = gj < P.W - 1 ? __ldg(x + o + 1) - xc : 0.f;
-    acc_b += (double)tv_term(0.f, dy, dx);
+    acc_b.add(tv_term(0.f, dy, dx));
   }
   block_sum2_store<256>(acc_a, acc_b, part_a, part_b, part_base + blockIdx.x);
 }
@@ -85,30 +85,16 @@ batch_ident_step_kernel(const BatchProb* __restrict__ probs, BatchState* __restr
 // sets done once (F - f*) <= target f*.  final_pass: records F(x_K) at K - 1.
 __global__ void __launch_bounds__(256)
 batch_reduce_kernel(const BatchProb* __restrict__ probs, BatchState* __restrict__ state,
-                    const int* __restrict__ kctr, const double* __restrict__ part_a,
-                    const double* __restrict__ part_b, int final_pass, int* done_host) {
+                    const int* __restrict__ kctr, const Partial* __restrict__ part_a,
+                    const Partial* __restrict__ part_b, int final_pass, int* done_host) {
   const BatchProb& P = probs[blockIdx.x];
   BatchState& S = state[blockIdx.x];
   if (!active(S)) return;
-  double a = 0.0, b = 0.0;
-  for (int i = threadIdx.x; i < P.part_n; i += 256) {
-    a += part_a[P.part_off + i];
-    b += part_b[P.part_off + i];
-  }
-  __shared__ double sa[256], sb[256];
-  sa[threadIdx.x] = a;
-  sb[threadIdx.x] = b;
-  __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
-    if (threadIdx.x < s) {
-      sa[threadIdx.x] += sa[threadIdx.x + s];
-      sb[threadIdx.x] += sb[threadIdx.x + s];
-    }
-    __syncthreads();
-  }
+  const double sum_a = block_sum_partials<256>(part_a + P.part_off, P.part_n);
+  const double sum_b = block_sum_partials<256>(part_b + P.part_off, P.part_n);
   if (threadIdx.x != 0) return;
   const int k = *kctr;  // F of x_k
-  const double F = sa[0] + P.alpha * sb[0];
+  const double F = sum_a + P.alpha * sum_b;
   if (k >= 1) {
     P.obj[k - 1] = F;
     P.ts[k - 1] = globaltimer_ns();

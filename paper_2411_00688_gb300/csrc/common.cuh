@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "kernels.hpp"
+
 namespace tvs {
 
 // ---------------------------------------------------------------- storage
@@ -75,33 +77,88 @@ struct Philox4x64 {
 };
 
 // ---------------------------------------------------------------- reductions
-// Sums two per-thread doubles over the block in a fixed order and writes the
-// block totals to part_a[blockLinear], part_b[blockLinear] (deterministic).
-template <int NT>
-__device__ __forceinline__ void block_sum2_store(double a, double b, double* part_a, double* part_b,
-                                                 int block_linear) {
-  __shared__ double sa[NT / 32], sb[NT / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_down_sync(0xffffffffu, a, o);
-    b += __shfl_down_sync(0xffffffffu, b, o);
+// Compensated FP32 accumulator: s + c carries the running sum to about twice single
+// precision (Knuth's TwoSum gives the exact rounding error of every addition, which
+// c collects).  The objective and distance sums use it in place of FP64 arithmetic,
+// whose throughput on this GPU is a small fraction of FP32's; its accuracy for
+// sums of up to millions of FP32 terms is at the level of FP64 accumulation.  The
+// intrinsics keep the compiler from fusing or reassociating the additions.
+struct FAcc {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float t = __fadd_rn(s, v);
+    const float bp = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
+    s = t;
+    c = __fadd_rn(c, e);
   }
-  if (lane == 0) { sa[warp] = a; sb[warp] = b; }
+  __device__ __forceinline__ void add(float os, float oc) {
+    add(os);
+    c = __fadd_rn(c, oc);
+  }
+  __device__ __forceinline__ void add(const Partial& p) { add(p.s, p.c); }
+};
+
+template <int W>
+__device__ __forceinline__ void warp_sum(FAcc& a) {
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1) {
+    const float os = __shfl_down_sync(0xffffffffu, a.s, o);
+    const float oc = __shfl_down_sync(0xffffffffu, a.c, o);
+    a.add(os, oc);
+  }
+}
+
+// Sums two per-thread accumulators over the block in a fixed order and writes the
+// block totals to part_a[block_linear], part_b[block_linear] (deterministic).
+template <int NT>
+__device__ __forceinline__ void block_sum2_store(FAcc a, FAcc b, Partial* part_a, Partial* part_b,
+                                                 int block_linear) {
+  __shared__ Partial sa[NT / 32], sb[NT / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  warp_sum<32>(a);
+  warp_sum<32>(b);
+  if (lane == 0) {
+    sa[warp] = Partial{a.s, a.c};
+    sb[warp] = Partial{b.s, b.c};
+  }
   __syncthreads();
   if (warp == 0) {
-    a = lane < NT / 32 ? sa[lane] : 0.0;
-    b = lane < NT / 32 ? sb[lane] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_down_sync(0xffffffffu, a, o);
-      b += __shfl_down_sync(0xffffffffu, b, o);
+    a = FAcc();
+    b = FAcc();
+    if (lane < NT / 32) {
+      a.s = sa[lane].s; a.c = sa[lane].c;
+      b.s = sb[lane].s; b.c = sb[lane].c;
     }
+    warp_sum<32>(a);
+    warp_sum<32>(b);
     if (lane == 0) {
-      if (part_a) part_a[block_linear] = a;
-      if (part_b) part_b[block_linear] = b;
+      if (part_a) part_a[block_linear] = Partial{a.s, a.c};
+      if (part_b) part_b[block_linear] = Partial{b.s, b.c};
     }
   }
+}
+
+// Sum of n partials by one block of NT threads (fixed order); every thread gets
+// the total as a double.
+template <int NT>
+__device__ __forceinline__ double block_sum_partials(const Partial* __restrict__ p, int n) {
+  __shared__ Partial sp[NT / 32];
+  __shared__ double total;
+  FAcc a;
+  for (int i = threadIdx.x; i < n; i += NT) a.add(p[i]);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  warp_sum<32>(a);
+  if (lane == 0) sp[warp] = Partial{a.s, a.c};
+  __syncthreads();
+  if (warp == 0) {
+    a = FAcc();
+    if (lane < NT / 32) { a.s = sp[lane].s; a.c = sp[lane].c; }
+    warp_sum<32>(a);
+    if (lane == 0) total = (double)a.s + (double)a.c;
+  }
+  __syncthreads();
+  return total;
 }
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {

@@ -57,10 +57,10 @@ template <int MODE>
 __global__ void __launch_bounds__(CT_NT)
 joseph_fwd_kernel(GeomConsts g, const float4* __restrict__ angles, const float* __restrict__ x,
                   const float* __restrict__ xt, float* __restrict__ sino, float* __restrict__ y,
-                  const float* __restrict__ b, float tau, double* __restrict__ part, float tau2 = 0.f) {
+                  const float* __restrict__ b, float tau, Partial* __restrict__ part, float tau2 = 0.f) {
   const int ray = blockIdx.x * CT_NT + threadIdx.x;
   const int n_rays = g.n_angles * g.n_det;
-  double acc_d = 0.0;
+  FAcc acc_d;
   if (ray < n_rays) {
     const int a = ray / g.n_det, bin = ray - a * g.n_det;
     const float4 ang = __ldg(angles + a);
@@ -101,7 +101,7 @@ joseph_fwd_kernel(GeomConsts g, const float4* __restrict__ angles, const float* 
         y[ray] = (y[ray] + tau * (axn + ax) - tau * bb) / (1.f + tau);
         sino[ray] = axn;
         const float r = axn - bb;
-        acc_d = 0.5 * (double)(r * r);
+        acc_d.add(0.5f * (r * r));
       } else {
         if (MODE == 1) {
           const float prev = sino[ray];
@@ -109,11 +109,11 @@ joseph_fwd_kernel(GeomConsts g, const float4* __restrict__ angles, const float* 
         }
         const float r = ax - bb;
         sino[ray] = MODE == 3 ? r : ax;
-        acc_d = 0.5 * (double)(r * r);
+        acc_d.add(0.5f * (r * r));
       }
     }
   }
-  if (MODE != 0) block_sum2_store<CT_NT>(acc_d, 0.0, part, nullptr, blockIdx.x);
+  if (MODE != 0) block_sum2_store<CT_NT>(acc_d, FAcc(), part, nullptr, blockIdx.x);
 }
 
 // g = A^T y at pixel (i, j); epilogue out = x - sigma g + ch h (when x given).
@@ -121,10 +121,10 @@ __global__ void __launch_bounds__(CT_NT)
 joseph_bwd_kernel(GeomConsts g, const float4* __restrict__ angles, const float4* __restrict__ angles2,
                   const float* __restrict__ ys,
                   const float* __restrict__ x, const float* __restrict__ h, float* __restrict__ out,
-                  float sigma, float ch, double* __restrict__ part_tv) {
+                  float sigma, float ch, Partial* __restrict__ part_tv) {
   const int N = g.N;
   const int pix = blockIdx.x * CT_NT + threadIdx.x;
-  double acc_tv = 0.0;
+  FAcc acc_tv;
   if (pix < N * N) {
     const int i = pix / N, j = pix - i * N;
     float total = 0.f;
@@ -167,13 +167,13 @@ joseph_bwd_kernel(GeomConsts g, const float4* __restrict__ angles, const float4*
       if (part_tv) {
         const float dy = i < N - 1 ? __ldg(x + o + N) - xc : 0.f;
         const float dx = j < N - 1 ? __ldg(x + o + 1) - xc : 0.f;
-        acc_tv = (double)tv_term(0.f, dy, dx);
+        acc_tv.add(tv_term(0.f, dy, dx));
       }
     } else {
       out[(size_t)i * N + j] = total;
     }
   }
-  if (part_tv) block_sum2_store<CT_NT>(0.0, acc_tv, nullptr, part_tv, blockIdx.x);
+  if (part_tv) block_sum2_store<CT_NT>(FAcc(), acc_tv, nullptr, part_tv, blockIdx.x);
 }
 
 GeomConsts consts(const CTGeom& g) {
@@ -224,7 +224,7 @@ int ct_fwd_blocks(const CTGeom& g) { return (g.n_angles * g.n_det + CT_NT - 1) /
 int ct_bwd_blocks(const CTGeom& g) { return (g.N * g.N + CT_NT - 1) / CT_NT; }
 
 cudaError_t launch_ct_forward(const CTGeom& g, const float* x, float* sino, float* y,
-                              const float* b, float tau, double* part_data, int mode,
+                              const float* b, float tau, Partial* part_data, int mode,
                               cudaStream_t s, float p) {
   if (!g.xt_scratch) return cudaErrorInvalidValue;
   dim3 tg((g.N + 31) / 32, (g.N + 31) / 32), tb(32, 8);
@@ -251,7 +251,7 @@ cudaError_t launch_ct_forward(const CTGeom& g, const float* x, float* sino, floa
 }
 
 cudaError_t launch_ct_backward(const CTGeom& g, const float* y, const float* x, const float* h,
-                               float* out, float sigma, float ch, double* part_tv, cudaStream_t s) {
+                               float* out, float sigma, float ch, Partial* part_tv, cudaStream_t s) {
   const GeomConsts c = consts(g);
   joseph_bwd_kernel<<<ct_bwd_blocks(g), CT_NT, 0, s>>>(c, g.angles, g.angles2, y, x, h, out, sigma, ch,
                                                        part_tv);

@@ -13,6 +13,12 @@ struct Dims {
 };
 
 enum DualType { DUAL_F32 = 0, DUAL_BF16 = 1, DUAL_F16 = 2 };
+
+// One block's partial sum of an objective term: a compensated FP32 pair whose
+// value is s + c (see FAcc in common.cuh).
+struct Partial {
+  float s, c;
+};
 inline size_t dual_elem_bytes(int t) { return t == DUAL_F32 ? 4 : 2; }
 
 // ---- TV prox (fgp.cu) ----
@@ -55,49 +61,55 @@ struct BlurW {
   int R;
 };
 int tile_blocks_2d(int H, int W);        // blocks of the 2D tile kernels
+int fb_step_blocks_2d(int H, int W);     // blocks of launch_blur_fb_step
+// Fused forward-backward step: out = x - gamma A (A x - b) + ch h (h may be null),
+// partials of 1/2 ||A x - b||^2 and TV(x) (fb_step_blocks_2d of each).
+cudaError_t launch_blur_fb_step(int H, int W, const float* x, const float* b, const float* h, float* out,
+                                const BlurW& w, float gamma, float ch, Partial* part_data, Partial* part_tv,
+                                cudaStream_t s);
 int pointwise_blocks(size_t n);          // blocks of the grid-stride kernels
 
 // r_out = A x - b (r_out may be null); partials of 1/2 r^2 and of TV(x).
 cudaError_t launch_blur_residual(int H, int W, const float* x, const float* b, float* r_out,
-                                 const BlurW& w, double* part_data, double* part_tv, cudaStream_t s);
+                                 const BlurW& w, Partial* part_data, Partial* part_tv, cudaStream_t s);
 // out = x - gamma A(in) + ch h   (h may be null); optional TV(x) partials.
 cudaError_t launch_blur_step(int H, int W, const float* in, const float* x, const float* h,
-                             float* out, const BlurW& w, float gamma, float ch, double* part_tv,
+                             float* out, const BlurW& w, float gamma, float ch, Partial* part_tv,
                              cudaStream_t s);
 // y_out = (y + tau (2 A x - ax_prev) - tau b) / (1 + tau); ax_prev <- A x; partial 1/2 (A x - b)^2.
 cudaError_t launch_blur_pd_dual(int H, int W, const float* x, float* ax_prev, float* y,
-                                const float* b, const BlurW& w, float tau, double* part_data,
+                                const float* b, const BlurW& w, float tau, Partial* part_data,
                                 cudaStream_t s);
 cudaError_t launch_blur(int H, int W, const float* x, float* y, const BlurW& w, cudaStream_t s);
 // PDHGSkip-1 dual step: v = A x^; A x_new = ax_prev + p v (stored back);
 // y = (y + tau (A x_new + v) - tau b)/(1+tau); partial 1/2 (A x_new - b)^2.
 cudaError_t launch_blur_pd1_dual(int H, int W, const float* xh, float* ax_prev, float* y, const float* b,
-                                 const BlurW& w, float p, float tau, double* part_data, cudaStream_t s);
+                                 const BlurW& w, float p, float tau, Partial* part_data, cudaStream_t s);
 // Identity-operator form of the same (axh = x^), or with axh == null the skipped
 // iteration y = (y + tau ax_prev - tau b)/(1+tau) (part_data unused then).
 cudaError_t launch_pd1_dual_pointwise(size_t m, const float* axh, float* ax_prev, float* y, const float* b,
-                                      float p, float tau, double* part_data, cudaStream_t s);
+                                      float p, float tau, Partial* part_data, cudaStream_t s);
 
 // Identity data term (2D or 3D): out = x - gamma (x - b) + ch h; partials of
 // 1/2 (x - b)^2 and TV(x).  out may be null (objective only).
 cudaError_t launch_identity_step(const Dims& d, const float* x, const float* b, const float* h,
-                                 float* out, float gamma, float ch, double* part_data,
-                                 double* part_tv, cudaStream_t s);
+                                 float* out, float gamma, float ch, Partial* part_data,
+                                 Partial* part_tv, cudaStream_t s);
 // Generic pointwise step used by PDHG with identity/CT adjoint already formed:
 // out = x - sigma g + ch h; optional TV(x) partials.
 cudaError_t launch_axpy_step(const Dims& d, const float* g, const float* x, const float* h,
-                             float* out, float sigma, float ch, double* part_tv, cudaStream_t s);
+                             float* out, float sigma, float ch, Partial* part_tv, cudaStream_t s);
 // y = (y + tau (2 ax - ax_prev) - tau b)/(1+tau); ax_prev <- ax; partial 1/2 (ax - b)^2.
 cudaError_t launch_pd_dual_pointwise(size_t m, const float* ax, float* ax_prev, float* y,
-                                     const float* b, float tau, double* part_data, cudaStream_t s);
+                                     const float* b, float tau, Partial* part_data, cudaStream_t s);
 // Partials of TV(x) only (grid-stride, pointwise_blocks(n) blocks).
-cudaError_t launch_tv_partials(const Dims& d, const float* x, double* part_tv, cudaStream_t s);
+cudaError_t launch_tv_partials(const Dims& d, const float* x, Partial* part_tv, cudaStream_t s);
 
 // Sum partials (fixed order), F = data + alpha tv.  k = flags[2] (then flags[2]++);
 // when k >= 0 and k % every == 0: obj[k] = F, ts[k] = now, and once
 // (F - f*) <= target f*: flags[0] = 1 (done), flags[1] = k, *done_host = 1.
 // obj == null: write F to *f_out only.
-cudaError_t launch_reduce_record(const double* part_data, int n_data, const double* part_tv,
+cudaError_t launch_reduce_record(const Partial* part_data, int n_data, const Partial* part_tv,
                                  int n_tv, double alpha, int every, double* obj,
                                  unsigned long long* ts, double f_star, double target, int* flags,
                                  int* done_host, double* f_out, cudaStream_t s);
@@ -105,8 +117,8 @@ cudaError_t launch_reduce_record(const double* part_data, int n_data, const doub
 // then one block records dist[k] = sqrt(sum / ref_norm2) at k = flags[2] - 1 (the
 // index the preceding reduce_record used) and, when target > 0 and dist <= target,
 // raises the same done flags.
-cudaError_t launch_dist_partials(size_t n, const float* x, const float* u_ref, double* part, cudaStream_t s);
-cudaError_t launch_dist_record(const double* part, int n_part, double ref_norm2, double* dist, double target,
+cudaError_t launch_dist_partials(size_t n, const float* x, const float* u_ref, Partial* part, cudaStream_t s);
+cudaError_t launch_dist_record(const Partial* part, int n_part, double ref_norm2, double* dist, double target,
                                int* flags, int* done_host, cudaStream_t s);
 cudaError_t launch_timestamp(unsigned long long* ts, cudaStream_t s);
 // arr[2 * (*ctr) + which] = now; when which == 1 also (*ctr)++.
@@ -122,10 +134,10 @@ cudaError_t launch_pdx_precond(const float* colA, const float* rowA, int H, int 
                                float tau, float* T, float* S, cudaStream_t s);
 cudaError_t launch_fill(float* a, size_t n, float v, cudaStream_t s);
 cudaError_t launch_pdx_tv_step(int H, int W, const float* x, const float* g, const float* T, const float* q,
-                               float* xn, float* qn, float alpha, float s_d, bool nonneg, double* part_tv,
+                               float* xn, float* qn, float alpha, float s_d, bool nonneg, Partial* part_tv,
                                cudaStream_t s);
 cudaError_t launch_pdx_dual(size_t m, const float* ax, float* axp, float* y, const float* b, const float* S,
-                            bool init, double* part_a, cudaStream_t s);
+                            bool init, Partial* part_a, cudaStream_t s);
 
 int dual_rof_blocks(int H, int W);
 // One ProxSkip / projected-gradient step on q (2 planes) -> qn; h updated in place
@@ -133,10 +145,10 @@ int dual_rof_blocks(int H, int W);
 // and 1/2 |q|^2 of the current q.
 cudaError_t launch_dual_rof_step(int H, int W, const float* q, float* qn, float* h, const float* b,
                                  float alpha, float eps, float gamma, float p, bool prox,
-                                 double* part_a, double* part_b, cudaStream_t s);
+                                 Partial* part_a, Partial* part_b, cudaStream_t s);
 // u = b + div q (u may be null) and the same partials (pointwise_blocks(H W) blocks).
-cudaError_t launch_dual_rof_primal(int H, int W, const float* q, const float* b, float* u, double* part_a,
-                                   double* part_b, cudaStream_t s);
+cudaError_t launch_dual_rof_primal(int H, int W, const float* q, const float* b, float* u, Partial* part_a,
+                                   Partial* part_b, cudaStream_t s);
 
 // ---- batched ProxSkip (batch.cu) ----
 // Descriptor of one problem of a batch (device memory).  Partials of its
@@ -170,7 +182,7 @@ struct BatchLaunch {
   int n_all_chunks;
   const unsigned char* coins;  // [K][n]
   int* kctr;                   // outer iteration counter (device)
-  double *part_a, *part_b;
+  Partial *part_a, *part_b;
   int* done_host;              // n flags in mapped host memory
   int n_inner, dtype;
   int blur_radius;             // shared by every blur problem of the batch
@@ -203,10 +215,10 @@ enum CTFwdMode { CT_FWD_PLAIN = 0, CT_FWD_PD = 1, CT_FWD_STORE = 2, CT_FWD_RESID
 // y = (y + tau (sino + A x^) - tau b)/(1+tau).  PD/STORE/RESID/PD1 write partials of
 // 1/2 (A x_new - b)^2.
 cudaError_t launch_ct_forward(const CTGeom& g, const float* x, float* sino, float* y,
-                              const float* b, float tau, double* part_data, int mode,
+                              const float* b, float tau, Partial* part_data, int mode,
                               cudaStream_t s, float p = 0.f);
 // g = A^T y; when x != null: out = x - sigma g + ch h (+ TV(x) partials); else out = g.
 cudaError_t launch_ct_backward(const CTGeom& g, const float* y, const float* x, const float* h,
-                               float* out, float sigma, float ch, double* part_tv, cudaStream_t s);
+                               float* out, float sigma, float ch, Partial* part_tv, cudaStream_t s);
 
 }  // namespace tvs

@@ -25,19 +25,28 @@ __global__ void __launch_bounds__(BNT)
 blur_kernel(const float* __restrict__ src, int H, int W, BlurW w, const float* __restrict__ b,
             float* __restrict__ out, const float* __restrict__ x, const float* __restrict__ h,
             float gamma, float ch, float* __restrict__ axp, float* __restrict__ y, float tau,
-            double* __restrict__ part_a, double* __restrict__ part_b) {
+            Partial* __restrict__ part_a, Partial* __restrict__ part_b) {
   blur_tile_body<MODE, R>(src, H, W, w, b, out, x, h, gamma, ch, axp, y, tau, part_a, part_b, blockIdx.x,
                           blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x);
+}
+
+template <int R>
+__global__ void __launch_bounds__(FNT)
+blur_fb_step_kernel(const float* __restrict__ x, const float* __restrict__ b, const float* __restrict__ h,
+                    float* __restrict__ out, int H, int W, BlurW w, float gamma, float ch,
+                    Partial* __restrict__ part_a, Partial* __restrict__ part_b) {
+  blur_fb_step_body<R>(x, b, h, out, H, W, w, gamma, ch, part_a, part_b, blockIdx.x, blockIdx.y,
+                       blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // Identity data term, 2D or 3D (nz slices of ny x nx).
 __global__ void __launch_bounds__(PW_NT)
 identity_step_kernel(const float* __restrict__ x, const float* __restrict__ b,
                      const float* __restrict__ h, float* __restrict__ out, int D, int H, int W,
-                     int ndim, float gamma, float ch, double* __restrict__ part_a,
-                     double* __restrict__ part_b) {
+                     int ndim, float gamma, float ch, Partial* __restrict__ part_a,
+                     Partial* __restrict__ part_b) {
   const size_t n = (size_t)D * H * W, HW = (size_t)H * W;
-  double acc_a = 0.0, acc_b = 0.0;
+  FAcc acc_a, acc_b;
   for (size_t o = blockIdx.x * (size_t)PW_NT + threadIdx.x; o < n; o += (size_t)gridDim.x * PW_NT) {
     const int gj = (int)(o % W), gi = (int)((o / W) % H), gk = (int)(o / HW);
     const float xc = __ldg(x + o), bb = __ldg(b + o);
@@ -47,11 +56,11 @@ identity_step_kernel(const float* __restrict__ x, const float* __restrict__ b,
       if (h) v = fmaf(ch, __ldg(h + o), v);
       out[o] = v;
     }
-    acc_a += 0.5 * (double)(r * r);
+    acc_a.add(0.5f * (r * r));
     const float d0 = (ndim == 3 && gk < D - 1) ? __ldg(x + o + HW) - xc : 0.f;
     const float d1 = gi < H - 1 ? __ldg(x + o + W) - xc : 0.f;
     const float d2 = gj < W - 1 ? __ldg(x + o + 1) - xc : 0.f;
-    acc_b += (double)tv_term(d0, d1, d2);
+    acc_b.add(tv_term(d0, d1, d2));
   }
   block_sum2_store<PW_NT>(acc_a, acc_b, part_a, part_b, blockIdx.x);
 }
@@ -59,9 +68,9 @@ identity_step_kernel(const float* __restrict__ x, const float* __restrict__ b,
 __global__ void __launch_bounds__(PW_NT)
 axpy_step_kernel(const float* __restrict__ g, const float* __restrict__ x,
                  const float* __restrict__ h, float* __restrict__ out, int D, int H, int W,
-                 int ndim, float sigma, float ch, double* __restrict__ part_b) {
+                 int ndim, float sigma, float ch, Partial* __restrict__ part_b) {
   const size_t n = (size_t)D * H * W, HW = (size_t)H * W;
-  double acc_b = 0.0;
+  FAcc acc_b;
   for (size_t o = blockIdx.x * (size_t)PW_NT + threadIdx.x; o < n; o += (size_t)gridDim.x * PW_NT) {
     const float xc = __ldg(x + o);
     float v = xc - sigma * __ldg(g + o);
@@ -72,26 +81,26 @@ axpy_step_kernel(const float* __restrict__ g, const float* __restrict__ x,
       const float d0 = (ndim == 3 && gk < D - 1) ? __ldg(x + o + HW) - xc : 0.f;
       const float d1 = gi < H - 1 ? __ldg(x + o + W) - xc : 0.f;
       const float d2 = gj < W - 1 ? __ldg(x + o + 1) - xc : 0.f;
-      acc_b += (double)tv_term(d0, d1, d2);
+      acc_b.add(tv_term(d0, d1, d2));
     }
   }
-  if (part_b) block_sum2_store<PW_NT>(0.0, acc_b, nullptr, part_b, blockIdx.x);
+  if (part_b) block_sum2_store<PW_NT>(FAcc(), acc_b, nullptr, part_b, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(PW_NT)
 tv_partials_kernel(const float* __restrict__ x, int D, int H, int W, int ndim,
-                   double* __restrict__ part_b) {
+                   Partial* __restrict__ part_b) {
   const size_t n = (size_t)D * H * W, HW = (size_t)H * W;
-  double acc_b = 0.0;
+  FAcc acc_b;
   for (size_t o = blockIdx.x * (size_t)PW_NT + threadIdx.x; o < n; o += (size_t)gridDim.x * PW_NT) {
     const int gj = (int)(o % W), gi = (int)((o / W) % H), gk = (int)(o / HW);
     const float xc = __ldg(x + o);
     const float d0 = (ndim == 3 && gk < D - 1) ? __ldg(x + o + HW) - xc : 0.f;
     const float d1 = gi < H - 1 ? __ldg(x + o + W) - xc : 0.f;
     const float d2 = gj < W - 1 ? __ldg(x + o + 1) - xc : 0.f;
-    acc_b += (double)tv_term(d0, d1, d2);
+    acc_b.add(tv_term(d0, d1, d2));
   }
-  block_sum2_store<PW_NT>(0.0, acc_b, nullptr, part_b, blockIdx.x);
+  block_sum2_store<PW_NT>(FAcc(), acc_b, nullptr, part_b, blockIdx.x);
 }
 
 // PDHGSkip-1 dual step for the identity operator (ax = x^), or, with ax == null,
@@ -99,8 +108,8 @@ tv_partials_kernel(const float* __restrict__ x, int D, int H, int W, int ndim,
 __global__ void __launch_bounds__(PW_NT)
 pd1_dual_pointwise_kernel(size_t m, const float* __restrict__ axh, float* __restrict__ axp,
                           float* __restrict__ y, const float* __restrict__ b, float p, float tau,
-                          double* __restrict__ part_a) {
-  double acc = 0.0;
+                          Partial* __restrict__ part_a) {
+  FAcc acc;
   for (size_t o = blockIdx.x * (size_t)PW_NT + threadIdx.x; o < m; o += (size_t)gridDim.x * PW_NT) {
     const float bb = __ldg(b + o);
     if (axh) {
@@ -109,50 +118,38 @@ pd1_dual_pointwise_kernel(size_t m, const float* __restrict__ axh, float* __rest
       y[o] = (y[o] + tau * (axn + v) - tau * bb) / (1.f + tau);
       axp[o] = axn;
       const float r = axn - bb;
-      acc += 0.5 * (double)(r * r);
+      acc.add(0.5f * (r * r));
     } else {
       y[o] = (y[o] + tau * axp[o] - tau * bb) / (1.f + tau);
     }
   }
-  if (part_a) block_sum2_store<PW_NT>(acc, 0.0, part_a, nullptr, blockIdx.x);
+  if (part_a) block_sum2_store<PW_NT>(acc, FAcc(), part_a, nullptr, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(PW_NT)
 pd_dual_pointwise_kernel(size_t m, const float* __restrict__ ax, float* __restrict__ axp,
                          float* __restrict__ y, const float* __restrict__ b, float tau,
-                         double* __restrict__ part_a) {
-  double acc = 0.0;
+                         Partial* __restrict__ part_a) {
+  FAcc acc;
   for (size_t o = blockIdx.x * (size_t)PW_NT + threadIdx.x; o < m; o += (size_t)gridDim.x * PW_NT) {
     const float v = __ldg(ax + o), bb = __ldg(b + o);
     const float prev = axp[o];
     y[o] = (y[o] + tau * (2.f * v - prev) - tau * bb) / (1.f + tau);
     axp[o] = v;
     const float r = v - bb;
-    acc += 0.5 * (double)(r * r);
+    acc.add(0.5f * (r * r));
   }
-  block_sum2_store<PW_NT>(acc, 0.0, part_a, nullptr, blockIdx.x);
+  block_sum2_store<PW_NT>(acc, FAcc(), part_a, nullptr, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(512)
-reduce_record_kernel(const double* __restrict__ part_a, int n_a, const double* __restrict__ part_b,
+reduce_record_kernel(const Partial* __restrict__ part_a, int n_a, const Partial* __restrict__ part_b,
                      int n_b, double alpha, int every, double* obj, unsigned long long* ts,
                      double f_star, double target, int* flags, int* done_host, double* f_out) {
-  double a = 0.0, b = 0.0;
-  for (int i = threadIdx.x; i < n_a; i += 512) a += part_a[i];
-  for (int i = threadIdx.x; i < n_b; i += 512) b += part_b[i];
-  __shared__ double sa[512], sb[512];
-  sa[threadIdx.x] = a;
-  sb[threadIdx.x] = b;
-  __syncthreads();
-  for (int s = 256; s > 0; s >>= 1) {
-    if (threadIdx.x < s) {
-      sa[threadIdx.x] += sa[threadIdx.x + s];
-      sb[threadIdx.x] += sb[threadIdx.x + s];
-    }
-    __syncthreads();
-  }
+  const double sum_a = block_sum_partials<512>(part_a, n_a);
+  const double sum_b = block_sum_partials<512>(part_b, n_b);
   if (threadIdx.x == 0) {
-    const double F = sa[0] + alpha * sb[0];
+    const double F = sum_a + alpha * sum_b;
     if (f_out) *f_out = F;
     if (!flags) return;
     const int k = flags[2];
@@ -172,31 +169,23 @@ reduce_record_kernel(const double* __restrict__ part_a, int n_a, const double* _
 }
 
 __global__ void __launch_bounds__(PW_NT)
-dist_partials_kernel(size_t n, const float* __restrict__ x, const float* __restrict__ u, double* __restrict__ part) {
-  double acc = 0.0;
+dist_partials_kernel(size_t n, const float* __restrict__ x, const float* __restrict__ u, Partial* __restrict__ part) {
+  FAcc acc;
   for (size_t o = blockIdx.x * (size_t)PW_NT + threadIdx.x; o < n; o += (size_t)gridDim.x * PW_NT) {
     const float d = __ldg(x + o) - __ldg(u + o);
-    acc += (double)d * (double)d;
+    acc.add(d * d);
   }
-  block_sum2_store<PW_NT>(acc, 0.0, part, nullptr, blockIdx.x);
+  block_sum2_store<PW_NT>(acc, FAcc(), part, nullptr, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(512)
-dist_record_kernel(const double* __restrict__ part, int n_part, double ref_norm2, double* dist, double target,
+dist_record_kernel(const Partial* __restrict__ part, int n_part, double ref_norm2, double* dist, double target,
                    int* flags, int* done_host) {
-  double a = 0.0;
-  for (int i = threadIdx.x; i < n_part; i += 512) a += part[i];
-  __shared__ double sa[512];
-  sa[threadIdx.x] = a;
-  __syncthreads();
-  for (int s = 256; s > 0; s >>= 1) {
-    if (threadIdx.x < s) sa[threadIdx.x] += sa[threadIdx.x + s];
-    __syncthreads();
-  }
+  const double sum = block_sum_partials<512>(part, n_part);
   if (threadIdx.x != 0) return;
   const int k = flags[2] - 1;
   if (k < 0) return;
-  const double d = sqrt(sa[0] / ref_norm2);
+  const double d = sqrt(sum / ref_norm2);
   dist[k] = d;
   if (target > 0.0 && flags[0] == 0 && d <= target) {
     flags[0] = 1;
@@ -232,7 +221,7 @@ __global__ void coin_kernel(uint64_t seed, double p, int64_t k0, int K, unsigned
 template <int MODE>
 cudaError_t blur_launch(int H, int W, const float* src, const BlurW& w, const float* b, float* out,
                         const float* x, const float* h, float gamma, float ch, float* axp, float* y,
-                        float tau, double* pa, double* pb, cudaStream_t s) {
+                        float tau, Partial* pa, Partial* pb, cudaStream_t s) {
   dim3 grid((W + BX - 1) / BX, (H + BY - 1) / BY);
   switch (w.R) {
 #define TVS_BLUR_R(R_) \
@@ -248,6 +237,22 @@ cudaError_t blur_launch(int H, int W, const float* src, const BlurW& w, const fl
 }  // namespace
 
 int tile_blocks_2d(int H, int W) { return ((W + BX - 1) / BX) * ((H + BY - 1) / BY); }
+int fb_step_blocks_2d(int H, int W) { return ((W + FX - 1) / FX) * ((H + FY - 1) / FY); }
+
+cudaError_t launch_blur_fb_step(int H, int W, const float* x, const float* b, const float* h, float* out,
+                                const BlurW& w, float gamma, float ch, Partial* part_data, Partial* part_tv,
+                                cudaStream_t s) {
+  dim3 grid((W + FX - 1) / FX, (H + FY - 1) / FY);
+  switch (w.R) {
+#define TVS_FB_R(R_) \
+  case R_: blur_fb_step_kernel<R_><<<grid, FNT, 0, s>>>(x, b, h, out, H, W, w, gamma, ch, part_data, part_tv); break;
+    TVS_FB_R(1) TVS_FB_R(2) TVS_FB_R(3) TVS_FB_R(4) TVS_FB_R(5) TVS_FB_R(6) TVS_FB_R(7) TVS_FB_R(8)
+#undef TVS_FB_R
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
 
 int pointwise_blocks(size_t n) {
   size_t b = (n + PW_NT - 1) / PW_NT;
@@ -258,27 +263,27 @@ int pointwise_blocks(size_t n) {
 }
 
 cudaError_t launch_blur_residual(int H, int W, const float* x, const float* b, float* r_out,
-                                 const BlurW& w, double* part_data, double* part_tv, cudaStream_t s) {
+                                 const BlurW& w, Partial* part_data, Partial* part_tv, cudaStream_t s) {
   return blur_launch<BM_RESID>(H, W, x, w, b, r_out, nullptr, nullptr, 0.f, 0.f, nullptr, nullptr,
                                0.f, part_data, part_tv, s);
 }
 
 cudaError_t launch_blur_step(int H, int W, const float* in, const float* x, const float* h,
-                             float* out, const BlurW& w, float gamma, float ch, double* part_tv,
+                             float* out, const BlurW& w, float gamma, float ch, Partial* part_tv,
                              cudaStream_t s) {
   return blur_launch<BM_STEP>(H, W, in, w, nullptr, out, x, h, gamma, ch, nullptr, nullptr, 0.f,
                               nullptr, part_tv, s);
 }
 
 cudaError_t launch_blur_pd_dual(int H, int W, const float* x, float* ax_prev, float* y,
-                                const float* b, const BlurW& w, float tau, double* part_data,
+                                const float* b, const BlurW& w, float tau, Partial* part_data,
                                 cudaStream_t s) {
   return blur_launch<BM_PD>(H, W, x, w, b, nullptr, nullptr, nullptr, 0.f, 0.f, ax_prev, y, tau,
                             part_data, nullptr, s);
 }
 
 cudaError_t launch_blur_pd1_dual(int H, int W, const float* xh, float* ax_prev, float* y, const float* b,
-                                 const BlurW& w, float p, float tau, double* part_data, cudaStream_t s) {
+                                 const BlurW& w, float p, float tau, Partial* part_data, cudaStream_t s) {
   return blur_launch<BM_PD1>(H, W, xh, w, b, nullptr, nullptr, nullptr, p, 0.f, ax_prev, y, tau, part_data,
                              nullptr, s);
 }
@@ -289,38 +294,38 @@ cudaError_t launch_blur(int H, int W, const float* x, float* y, const BlurW& w, 
 }
 
 cudaError_t launch_identity_step(const Dims& d, const float* x, const float* b, const float* h,
-                                 float* out, float gamma, float ch, double* part_data,
-                                 double* part_tv, cudaStream_t s) {
+                                 float* out, float gamma, float ch, Partial* part_data,
+                                 Partial* part_tv, cudaStream_t s) {
   identity_step_kernel<<<pointwise_blocks(d.n()), PW_NT, 0, s>>>(x, b, h, out, d.nz, d.ny, d.nx,
                                                                   d.ndim, gamma, ch, part_data, part_tv);
   return cudaGetLastError();
 }
 
 cudaError_t launch_axpy_step(const Dims& d, const float* g, const float* x, const float* h,
-                             float* out, float sigma, float ch, double* part_tv, cudaStream_t s) {
+                             float* out, float sigma, float ch, Partial* part_tv, cudaStream_t s) {
   axpy_step_kernel<<<pointwise_blocks(d.n()), PW_NT, 0, s>>>(g, x, h, out, d.nz, d.ny, d.nx, d.ndim,
                                                               sigma, ch, part_tv);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pd1_dual_pointwise(size_t m, const float* axh, float* ax_prev, float* y, const float* b,
-                                      float p, float tau, double* part_data, cudaStream_t s) {
+                                      float p, float tau, Partial* part_data, cudaStream_t s) {
   pd1_dual_pointwise_kernel<<<pointwise_blocks(m), PW_NT, 0, s>>>(m, axh, ax_prev, y, b, p, tau, part_data);
   return cudaGetLastError();
 }
 
-cudaError_t launch_tv_partials(const Dims& d, const float* x, double* part_tv, cudaStream_t s) {
+cudaError_t launch_tv_partials(const Dims& d, const float* x, Partial* part_tv, cudaStream_t s) {
   tv_partials_kernel<<<pointwise_blocks(d.n()), PW_NT, 0, s>>>(x, d.nz, d.ny, d.nx, d.ndim, part_tv);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pd_dual_pointwise(size_t m, const float* ax, float* ax_prev, float* y,
-                                     const float* b, float tau, double* part_data, cudaStream_t s) {
+                                     const float* b, float tau, Partial* part_data, cudaStream_t s) {
   pd_dual_pointwise_kernel<<<pointwise_blocks(m), PW_NT, 0, s>>>(m, ax, ax_prev, y, b, tau, part_data);
   return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_record(const double* part_data, int n_data, const double* part_tv,
+cudaError_t launch_reduce_record(const Partial* part_data, int n_data, const Partial* part_tv,
                                  int n_tv, double alpha, int every, double* obj,
                                  unsigned long long* ts, double f_star, double target, int* flags,
                                  int* done_host, double* f_out, cudaStream_t s) {
@@ -329,12 +334,12 @@ cudaError_t launch_reduce_record(const double* part_data, int n_data, const doub
   return cudaGetLastError();
 }
 
-cudaError_t launch_dist_partials(size_t n, const float* x, const float* u_ref, double* part, cudaStream_t s) {
+cudaError_t launch_dist_partials(size_t n, const float* x, const float* u_ref, Partial* part, cudaStream_t s) {
   dist_partials_kernel<<<pointwise_blocks(n), PW_NT, 0, s>>>(n, x, u_ref, part);
   return cudaGetLastError();
 }
 
-cudaError_t launch_dist_record(const double* part, int n_part, double ref_norm2, double* dist, double target,
+cudaError_t launch_dist_record(const Partial* part, int n_part, double ref_norm2, double* dist, double target,
                                int* flags, int* done_host, cudaStream_t s) {
   dist_record_kernel<<<1, 512, 0, s>>>(part, n_part, ref_norm2, dist, target, flags, done_host);
   return cudaGetLastError();

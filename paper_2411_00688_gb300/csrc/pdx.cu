@@ -54,7 +54,7 @@ template <bool NONNEG>
 __global__ void __launch_bounds__(QNT)
 pdx_tv_step_kernel(const float* __restrict__ x, const float* __restrict__ g, const float* __restrict__ T,
                    const float* __restrict__ q, float* __restrict__ xn, float* __restrict__ qn, int H, int W,
-                   float alpha, float s_d, double* __restrict__ part_tv) {
+                   float alpha, float s_d, Partial* __restrict__ part_tv) {
   __shared__ float sqy[QY + 2][QX + 3];
   __shared__ float sqx[QY + 2][QX + 3];
   __shared__ float sxb[QY + 1][QX + 2];  // x- = 2 x+ - x
@@ -96,7 +96,7 @@ pdx_tv_step_kernel(const float* __restrict__ x, const float* __restrict__ g, con
     sxc[a][c] = xc;
   }
   __syncthreads();
-  double acc = 0.0;
+  FAcc acc;
   for (int e = threadIdx.x; e < QY * QX; e += QNT) {
     const int a = e / QX, c = e - a * QX;
     const int gi = i0 + a, gj = j0 + c;
@@ -111,9 +111,9 @@ pdx_tv_step_kernel(const float* __restrict__ x, const float* __restrict__ g, con
     qn[n + o] = vx * sc;
     const float ty = gi < H - 1 ? sxc[a + 1][c] - sxc[a][c] : 0.f;
     const float tx = gj < W - 1 ? sxc[a][c + 1] - sxc[a][c] : 0.f;
-    acc += (double)tv_term(0.f, ty, tx);
+    acc.add(tv_term(0.f, ty, tx));
   }
-  block_sum2_store<QNT>(0.0, acc, nullptr, part_tv, blockIdx.y * gridDim.x + blockIdx.x);
+  block_sum2_store<QNT>(FAcc(), acc, nullptr, part_tv, blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // y+ = (y + S (2 A x+ - A x - b)) / (1 + S); A x <- A x+; data partials of x+.
@@ -121,8 +121,8 @@ pdx_tv_step_kernel(const float* __restrict__ x, const float* __restrict__ g, con
 template <bool INIT>
 __global__ void __launch_bounds__(PW)
 pdx_dual_kernel(size_t m, const float* __restrict__ ax, float* __restrict__ axp, float* __restrict__ y,
-                const float* __restrict__ b, const float* __restrict__ S, double* __restrict__ part_a) {
-  double acc = 0.0;
+                const float* __restrict__ b, const float* __restrict__ S, Partial* __restrict__ part_a) {
+  FAcc acc;
   for (size_t o = blockIdx.x * (size_t)PW + threadIdx.x; o < m; o += (size_t)gridDim.x * PW) {
     const float v = __ldg(ax + o), bb = __ldg(b + o);
     if (!INIT) {
@@ -132,9 +132,9 @@ pdx_dual_kernel(size_t m, const float* __restrict__ ax, float* __restrict__ axp,
     }
     axp[o] = v;
     const float r = v - bb;
-    acc += 0.5 * (double)(r * r);
+    acc.add(0.5f * (r * r));
   }
-  block_sum2_store<PW>(acc, 0.0, part_a, nullptr, blockIdx.x);
+  block_sum2_store<PW>(acc, FAcc(), part_a, nullptr, blockIdx.x);
 }
 
 }  // namespace
@@ -154,7 +154,7 @@ cudaError_t launch_fill(float* a, size_t n, float v, cudaStream_t s) {
 }
 
 cudaError_t launch_pdx_tv_step(int H, int W, const float* x, const float* g, const float* T, const float* q,
-                               float* xn, float* qn, float alpha, float s_d, bool nonneg, double* part_tv,
+                               float* xn, float* qn, float alpha, float s_d, bool nonneg, Partial* part_tv,
                                cudaStream_t s) {
   dim3 grid((W + QX - 1) / QX, (H + QY - 1) / QY);
   if (nonneg) pdx_tv_step_kernel<true><<<grid, QNT, 0, s>>>(x, g, T, q, xn, qn, H, W, alpha, s_d, part_tv);
@@ -163,7 +163,7 @@ cudaError_t launch_pdx_tv_step(int H, int W, const float* x, const float* g, con
 }
 
 cudaError_t launch_pdx_dual(size_t m, const float* ax, float* axp, float* y, const float* b, const float* S,
-                            bool init, double* part_a, cudaStream_t s) {
+                            bool init, Partial* part_a, cudaStream_t s) {
   if (init) pdx_dual_kernel<true><<<pointwise_blocks(m), PW, 0, s>>>(m, ax, axp, y, b, S, part_a);
   else pdx_dual_kernel<false><<<pointwise_blocks(m), PW, 0, s>>>(m, ax, axp, y, b, S, part_a);
   return cudaGetLastError();

@@ -22,7 +22,7 @@ template <bool PROX, bool HAS_H>
 __global__ void __launch_bounds__(RNT)
 dual_rof_step_kernel(const float* __restrict__ q, float* __restrict__ qn, float* __restrict__ h,
                      const float* __restrict__ b, int H, int W, float alpha, float eps_over_alpha,
-                     float gamma, float p, double* __restrict__ part_a, double* __restrict__ part_b) {
+                     float gamma, float p, Partial* __restrict__ part_a, Partial* __restrict__ part_b) {
   __shared__ float sqy[RY + 2][RX + 3];
   __shared__ float sqx[RY + 2][RX + 3];
   __shared__ float sw[RY + 1][RX + 2];
@@ -58,7 +58,7 @@ dual_rof_step_kernel(const float* __restrict__ q, float* __restrict__ qn, float*
     sw[a][c] = w;
   }
   __syncthreads();
-  double acc_a = 0.0, acc_b = 0.0;
+  FAcc acc_a, acc_b;
   const float step_h = gamma / p, inv_step_h = p / gamma;
   for (int e = threadIdx.x; e < RY * RX; e += RNT) {
     const int a = e / RX, c = e - a * RX;
@@ -90,8 +90,8 @@ dual_rof_step_kernel(const float* __restrict__ q, float* __restrict__ qn, float*
     }
     qn[o] = ny;
     qn[n + o] = nx;
-    acc_a += 0.5 * (double)(wc * wc);
-    acc_b += 0.5 * (double)(qy * qy + qx * qx);
+    acc_a.add(0.5f * (wc * wc));
+    acc_b.add(0.5f * (qy * qy + qx * qx));
   }
   block_sum2_store<RNT>(acc_a, acc_b, part_a, part_b, blockIdx.y * gridDim.x + blockIdx.x);
 }
@@ -99,9 +99,9 @@ dual_rof_step_kernel(const float* __restrict__ q, float* __restrict__ qn, float*
 // u = b + div q and the objective partials of the final iterate.
 __global__ void __launch_bounds__(RNT)
 dual_rof_primal_kernel(const float* __restrict__ q, const float* __restrict__ b, float* __restrict__ u,
-                       int H, int W, double* __restrict__ part_a, double* __restrict__ part_b) {
+                       int H, int W, Partial* __restrict__ part_a, Partial* __restrict__ part_b) {
   const size_t n = (size_t)H * W;
-  double acc_a = 0.0, acc_b = 0.0;
+  FAcc acc_a, acc_b;
   for (size_t o = blockIdx.x * (size_t)RNT + threadIdx.x; o < n; o += (size_t)gridDim.x * RNT) {
     const int gj = (int)(o % W), gi = (int)(o / W);
     float dv = 0.f;
@@ -112,8 +112,8 @@ dual_rof_primal_kernel(const float* __restrict__ q, const float* __restrict__ b,
     const float w = dv + __ldg(b + o);
     if (u) u[o] = w;
     const float qy = __ldg(q + o), qx = __ldg(q + n + o);
-    acc_a += 0.5 * (double)(w * w);
-    acc_b += 0.5 * (double)(qy * qy + qx * qx);
+    acc_a.add(0.5f * (w * w));
+    acc_b.add(0.5f * (qy * qy + qx * qx));
   }
   block_sum2_store<RNT>(acc_a, acc_b, part_a, part_b, blockIdx.x);
 }
@@ -124,7 +124,7 @@ int dual_rof_blocks(int H, int W) { return ((W + RX - 1) / RX) * ((H + RY - 1) /
 
 cudaError_t launch_dual_rof_step(int H, int W, const float* q, float* qn, float* h, const float* b,
                                  float alpha, float eps, float gamma, float p, bool prox,
-                                 double* part_a, double* part_b, cudaStream_t s) {
+                                 Partial* part_a, Partial* part_b, cudaStream_t s) {
   dim3 grid((W + RX - 1) / RX, (H + RY - 1) / RY);
   const float ea = alpha > 0.f ? eps / alpha : 0.f;
   if (prox) {
@@ -137,8 +137,8 @@ cudaError_t launch_dual_rof_step(int H, int W, const float* q, float* qn, float*
   return cudaGetLastError();
 }
 
-cudaError_t launch_dual_rof_primal(int H, int W, const float* q, const float* b, float* u, double* part_a,
-                                   double* part_b, cudaStream_t s) {
+cudaError_t launch_dual_rof_primal(int H, int W, const float* q, const float* b, float* u, Partial* part_a,
+                                   Partial* part_b, cudaStream_t s) {
   dual_rof_primal_kernel<<<pointwise_blocks((size_t)H * W), RNT, 0, s>>>(q, b, u, H, W, part_a, part_b);
   return cudaGetLastError();
 }
