@@ -26,6 +26,7 @@ template <int R>
 __global__ void __launch_bounds__(BNT)
 batch_blur_resid_kernel(const BatchProb* __restrict__ probs, BatchState* __restrict__ state,
                         const int4* __restrict__ tiles, int par, Partial* part_a, Partial* part_b) {
+  pdl_enter();
   const int4 e = tiles[blockIdx.x];
   const BatchProb& P = probs[e.x];
   if (!active(state[e.x])) return;
@@ -38,6 +39,7 @@ __global__ void __launch_bounds__(BNT)
 batch_blur_step_kernel(const BatchProb* __restrict__ probs, BatchState* __restrict__ state,
                        const int4* __restrict__ tiles, const unsigned char* __restrict__ coins, int n,
                        const int* __restrict__ kctr, int par) {
+  pdl_enter();
   const int4 e = tiles[blockIdx.x];
   const BatchProb& P = probs[e.x];
   if (!active(state[e.x])) return;
@@ -56,6 +58,7 @@ batch_ident_step_kernel(const BatchProb* __restrict__ probs, BatchState* __restr
                         const int2* __restrict__ chunks, const unsigned char* __restrict__ coins, int n,
                         const int* __restrict__ kctr, int par, int write_out, Partial* part_a,
                         Partial* part_b, int part_base) {
+  pdl_enter();
   const int2 e = chunks[blockIdx.x];
   const BatchProb& P = probs[e.x];
   if (!active(state[e.x])) return;
@@ -87,6 +90,7 @@ __global__ void __launch_bounds__(256)
 batch_reduce_kernel(const BatchProb* __restrict__ probs, BatchState* __restrict__ state,
                     const int* __restrict__ kctr, const Partial* __restrict__ part_a,
                     const Partial* __restrict__ part_b, int final_pass, int* done_host) {
+  pdl_enter();
   const BatchProb& P = probs[blockIdx.x];
   BatchState& S = state[blockIdx.x];
   if (!active(S)) return;
@@ -119,6 +123,7 @@ __global__ void __launch_bounds__(256, 2)
 batch_fgp_kernel(const BatchProb* __restrict__ probs, BatchState* __restrict__ state,
                  const int4* __restrict__ tiles, const unsigned char* __restrict__ coins, int n,
                  const int* __restrict__ kctr, int q_in, TBBetas betas, int iters) {
+  pdl_enter();
   const int4 e = tiles[blockIdx.x];
   const BatchProb& P = probs[e.x];
   if (!active(state[e.x])) return;
@@ -143,6 +148,7 @@ __global__ void __launch_bounds__(256)
 batch_finalize_kernel(const BatchProb* __restrict__ probs, BatchState* __restrict__ state,
                       const int2* __restrict__ chunks, const unsigned char* __restrict__ coins, int n,
                       const int* __restrict__ kctr, int par, int fin_pair) {
+  pdl_enter();
   const int2 e = chunks[blockIdx.x];
   const BatchProb& P = probs[e.x];
   if (!active(state[e.x])) return;
@@ -173,7 +179,8 @@ batch_finalize_kernel(const BatchProb* __restrict__ probs, BatchState* __restric
   }
 }
 
-__global__ void batch_tick_kernel(int* kctr) { *kctr += 1; }
+__global__ void batch_tick_kernel(int* kctr) {
+  pdl_enter(); *kctr += 1; }
 
 }  // namespace
 
@@ -187,10 +194,10 @@ cudaError_t batch_blur(const BatchLaunch& L, int par, bool step, cudaStream_t s)
   switch (L.blur_radius) {
 #define TVS_BB_R(R_)                                                                                   \
   case R_:                                                                                             \
-    batch_blur_resid_kernel<R_><<<L.n_blur_tiles, BNT, 0, s>>>(L.probs, L.state, L.blur_tiles, par,   \
+    launch_kernel(batch_blur_resid_kernel<R_>, dim3(L.n_blur_tiles), dim3(BNT), 0, s, L.probs, L.state, L.blur_tiles, par,   \
                                                               L.part_a, L.part_b);                     \
     if (step)                                                                                          \
-      batch_blur_step_kernel<R_><<<L.n_blur_tiles, BNT, 0, s>>>(L.probs, L.state, L.blur_tiles,        \
+      launch_kernel(batch_blur_step_kernel<R_>, dim3(L.n_blur_tiles), dim3(BNT), 0, s, L.probs, L.state, L.blur_tiles,        \
                                                                 L.coins, L.n, L.kctr, par);            \
     break;
     TVS_BB_R(1) TVS_BB_R(2) TVS_BB_R(3) TVS_BB_R(4) TVS_BB_R(5) TVS_BB_R(6) TVS_BB_R(7) TVS_BB_R(8)
@@ -208,10 +215,10 @@ cudaError_t launch_batch_iteration(const BatchLaunch& L, int par, cudaStream_t s
     if (e != cudaSuccess) return e;
   }
   if (L.n_ident_chunks > 0)
-    batch_ident_step_kernel<<<L.n_ident_chunks, 256, 0, s>>>(L.probs, L.state, L.ident_chunks, L.coins, L.n,
+    launch_kernel(batch_ident_step_kernel, dim3(L.n_ident_chunks), dim3(256), 0, s, L.probs, L.state, L.ident_chunks, L.coins, L.n,
                                                              L.kctr, par, 1, L.part_a, L.part_b,
                                                              L.n_blur_tiles);
-  batch_reduce_kernel<<<L.n, 256, 0, s>>>(L.probs, L.state, L.kctr, L.part_a, L.part_b, 0, L.done_host);
+  launch_kernel(batch_reduce_kernel, dim3(L.n), dim3(256), 0, s, L.probs, L.state, L.kctr, L.part_a, L.part_b, 0, L.done_host);
   if (L.n_inner > 0 && L.use_prox) {
     int q = 0;
     for (int g = 1; g <= L.n_inner;) {
@@ -220,15 +227,15 @@ cudaError_t launch_batch_iteration(const BatchLaunch& L, int par, cudaStream_t s
       for (int j = 0; j < it; ++j) b.b[j] = L.betas[g - 1 + j];
       switch (L.dtype) {
         case DUAL_F32:
-          batch_fgp_kernel<float><<<L.n_fgp_tiles, 256, 0, s>>>(L.probs, L.state, L.fgp_tiles, L.coins, L.n,
+          launch_kernel(batch_fgp_kernel<float>, dim3(L.n_fgp_tiles), dim3(256), 0, s, L.probs, L.state, L.fgp_tiles, L.coins, L.n,
                                                                 L.kctr, q, b, it);
           break;
         case DUAL_BF16:
-          batch_fgp_kernel<__nv_bfloat16><<<L.n_fgp_tiles, 256, 0, s>>>(L.probs, L.state, L.fgp_tiles, L.coins,
+          launch_kernel(batch_fgp_kernel<__nv_bfloat16>, dim3(L.n_fgp_tiles), dim3(256), 0, s, L.probs, L.state, L.fgp_tiles, L.coins,
                                                                         L.n, L.kctr, q, b, it);
           break;
         default:
-          batch_fgp_kernel<__half><<<L.n_fgp_tiles, 256, 0, s>>>(L.probs, L.state, L.fgp_tiles, L.coins, L.n,
+          launch_kernel(batch_fgp_kernel<__half>, dim3(L.n_fgp_tiles), dim3(256), 0, s, L.probs, L.state, L.fgp_tiles, L.coins, L.n,
                                                                  L.kctr, q, b, it);
       }
       q = 1 - q;
@@ -237,15 +244,15 @@ cudaError_t launch_batch_iteration(const BatchLaunch& L, int par, cudaStream_t s
     const int fin_pair = q;  // pair holding p_N
     switch (L.dtype) {
       case DUAL_F32:
-        batch_finalize_kernel<float><<<L.n_all_chunks, 256, 0, s>>>(L.probs, L.state, L.all_chunks, L.coins,
+        launch_kernel(batch_finalize_kernel<float>, dim3(L.n_all_chunks), dim3(256), 0, s, L.probs, L.state, L.all_chunks, L.coins,
                                                                     L.n, L.kctr, par, fin_pair);
         break;
       case DUAL_BF16:
-        batch_finalize_kernel<__nv_bfloat16><<<L.n_all_chunks, 256, 0, s>>>(L.probs, L.state, L.all_chunks,
+        launch_kernel(batch_finalize_kernel<__nv_bfloat16>, dim3(L.n_all_chunks), dim3(256), 0, s, L.probs, L.state, L.all_chunks,
                                                                             L.coins, L.n, L.kctr, par, fin_pair);
         break;
       default:
-        batch_finalize_kernel<__half><<<L.n_all_chunks, 256, 0, s>>>(L.probs, L.state, L.all_chunks, L.coins,
+        launch_kernel(batch_finalize_kernel<__half>, dim3(L.n_all_chunks), dim3(256), 0, s, L.probs, L.state, L.all_chunks, L.coins,
                                                                      L.n, L.kctr, par, fin_pair);
     }
   } else {
@@ -253,19 +260,19 @@ cudaError_t launch_batch_iteration(const BatchLaunch& L, int par, cudaStream_t s
     // when alpha = 0; handled by the same kernel with lam = 0 through the descriptors
     switch (L.dtype) {
       case DUAL_F32:
-        batch_finalize_kernel<float><<<L.n_all_chunks, 256, 0, s>>>(L.probs, L.state, L.all_chunks, L.coins,
+        launch_kernel(batch_finalize_kernel<float>, dim3(L.n_all_chunks), dim3(256), 0, s, L.probs, L.state, L.all_chunks, L.coins,
                                                                     L.n, L.kctr, par, 0);
         break;
       case DUAL_BF16:
-        batch_finalize_kernel<__nv_bfloat16><<<L.n_all_chunks, 256, 0, s>>>(L.probs, L.state, L.all_chunks,
+        launch_kernel(batch_finalize_kernel<__nv_bfloat16>, dim3(L.n_all_chunks), dim3(256), 0, s, L.probs, L.state, L.all_chunks,
                                                                             L.coins, L.n, L.kctr, par, 0);
         break;
       default:
-        batch_finalize_kernel<__half><<<L.n_all_chunks, 256, 0, s>>>(L.probs, L.state, L.all_chunks, L.coins,
+        launch_kernel(batch_finalize_kernel<__half>, dim3(L.n_all_chunks), dim3(256), 0, s, L.probs, L.state, L.all_chunks, L.coins,
                                                                      L.n, L.kctr, par, 0);
     }
   }
-  batch_tick_kernel<<<1, 1, 0, s>>>(L.kctr);
+  launch_kernel(batch_tick_kernel, dim3(1), dim3(1), 0, s, L.kctr);
   return cudaGetLastError();
 }
 
@@ -275,10 +282,10 @@ cudaError_t launch_batch_final_objective(const BatchLaunch& L, int par, cudaStre
     if (e != cudaSuccess) return e;
   }
   if (L.n_ident_chunks > 0)
-    batch_ident_step_kernel<<<L.n_ident_chunks, 256, 0, s>>>(L.probs, L.state, L.ident_chunks, L.coins, L.n,
+    launch_kernel(batch_ident_step_kernel, dim3(L.n_ident_chunks), dim3(256), 0, s, L.probs, L.state, L.ident_chunks, L.coins, L.n,
                                                              L.kctr, par, 0, L.part_a, L.part_b,
                                                              L.n_blur_tiles);
-  batch_reduce_kernel<<<L.n, 256, 0, s>>>(L.probs, L.state, L.kctr, L.part_a, L.part_b, 1, L.done_host);
+  launch_kernel(batch_reduce_kernel, dim3(L.n), dim3(256), 0, s, L.probs, L.state, L.kctr, L.part_a, L.part_b, 1, L.done_host);
   return cudaGetLastError();
 }
 

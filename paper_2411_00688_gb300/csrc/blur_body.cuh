@@ -115,70 +115,125 @@ __device__ __forceinline__ void blur_fb_step_body(const float* __restrict__ x, c
                                                   int tile_x, int tile_y, int part_index) {
   constexpr int XR = FY + 4 * R, XC = FX + 4 * R;  // staged x: rows/cols i0-2R .. i0+FY+2R
   constexpr int RR = FY + 2 * R, RC = FX + 2 * R;  // residual region: i0-R .. i0+FY+R
+  constexpr int NW = FNT / 32;                     // warps; lane = column, warp = row phase
+  constexpr int VR = (RR + NW - 1) / NW;           // residual rows per warp (vertical pass)
+  constexpr int VO = FY / NW;                      // output rows per warp (final pass)
+  static_assert(FX == 32 && FY % NW == 0, "tile layout");
   __shared__ float sx[XR][XC + 1];
   __shared__ float sh[XR][RC + 1];  // horizontal pass of x, later of r
   __shared__ float sr[RR][RC + 1];
   float wk[2 * R + 1];
 #pragma unroll
   for (int k = 0; k <= 2 * R; ++k) wk[k] = w.w[k];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int j0 = tile_x * FX, i0 = tile_y * FY;
-  for (int e = threadIdx.x; e < XR * XC; e += FNT) {
-    const int a = e / XC, c = e - a * XC;
-    const int gi = reflect_index(i0 - 2 * R + a, H), gj = reflect_index(j0 - 2 * R + c, W);
-    sx[a][c] = __ldg(x + (size_t)gi * W + gj);
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < XR * RC; e += FNT) {
-    const int a = e / RC, c = e - a * RC;
-    float acc = 0.f;
+  const bool c1x = lane + 32 < XC, c1r = lane + 32 < RC;  // second column of a lane
+  {
+    const int gj0 = reflect_index(j0 - 2 * R + lane, W);
+    const int gj1 = c1x ? reflect_index(j0 - 2 * R + lane + 32, W) : 0;
 #pragma unroll
-    for (int k = 0; k <= 2 * R; ++k) acc = fmaf(wk[k], sx[a][c + k], acc);
-    sh[a][c] = acc;
+    for (int t = 0; t < (XR + NW - 1) / NW; ++t) {
+      const int a = wp + NW * t;
+      if (a < XR) {
+        const float* row = x + (size_t)reflect_index(i0 - 2 * R + a, H) * W;
+        sx[a][lane] = __ldg(row + gj0);
+        if (c1x) sx[a][lane + 32] = __ldg(row + gj1);
+      }
+    }
   }
   __syncthreads();
+#pragma unroll
+  for (int t = 0; t < (XR + NW - 1) / NW; ++t) {
+    const int a = wp + NW * t;
+    if (a < XR) {
+      float acc = 0.f;
+#pragma unroll
+      for (int k = 0; k <= 2 * R; ++k) acc = fmaf(wk[k], sx[a][lane + k], acc);
+      sh[a][lane] = acc;
+      if (c1r) {
+        float acc1 = 0.f;
+#pragma unroll
+        for (int k = 0; k <= 2 * R; ++k) acc1 = fmaf(wk[k], sx[a][lane + 32 + k], acc1);
+        sh[a][lane + 32] = acc1;
+      }
+    }
+  }
+  __syncthreads();
+  // vertical pass -> r = A x - b on the in-image cells of the residual region; each
+  // warp owns VR consecutive rows and slides a register window down its columns
   FAcc acc_a, acc_b;
-  for (int e = threadIdx.x; e < RR * RC; e += FNT) {
-    const int a = e / RC, c = e - a * RC;
-    const int gi = i0 - R + a, gj = j0 - R + c;
-    if (gi < 0 || gi >= H || gj < 0 || gj >= W) continue;
-    float v = 0.f;
 #pragma unroll
-    for (int k = 0; k <= 2 * R; ++k) v = fmaf(wk[k], sh[a + k][c], v);
-    const float r = v - __ldg(b + (size_t)gi * W + gj);
-    sr[a][c] = r;
-    if (a >= R && a < R + FY && c >= R && c < R + FX) acc_a.add(0.5f * (r * r));
+  for (int half = 0; half < 2; ++half) {
+    const int c = lane + 32 * half;
+    if (half == 1 && !c1r) break;
+    const int a0 = wp * VR;
+    float win[VR + 2 * R];
+#pragma unroll
+    for (int t = 0; t < VR + 2 * R; ++t) win[t] = a0 + t < XR ? sh[a0 + t][c] : 0.f;
+    const int gj = j0 - R + c;
+#pragma unroll
+    for (int t = 0; t < VR; ++t) {
+      const int a = a0 + t;
+      const int gi = i0 - R + a;
+      if (a >= RR || gi < 0 || gi >= H || gj < 0 || gj >= W) continue;
+      float v = 0.f;
+#pragma unroll
+      for (int k = 0; k <= 2 * R; ++k) v = fmaf(wk[k], win[t + k], v);
+      const float r = v - __ldg(b + (size_t)gi * W + gj);
+      sr[a][c] = r;
+      if (a >= R && a < R + FY && c >= R && c < R + FX) acc_a.add(0.5f * (r * r));
+    }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < RR * RC; e += FNT) {
-    const int a = e / RC, c = e - a * RC;
-    const int gi = i0 - R + a, gj = j0 - R + c;
-    if (gi >= 0 && gi < H && gj >= 0 && gj < W) continue;
-    sr[a][c] = sr[reflect_index(gi, H) - (i0 - R)][reflect_index(gj, W) - (j0 - R)];
+  // ring cells outside the image take their mirror cell's residual
+  if (i0 < R || j0 < R || i0 + FY + R > H || j0 + FX + R > W) {
+    for (int a = wp; a < RR; a += NW) {
+      const int gi = i0 - R + a;
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const int c = lane + 32 * half;
+        if (c >= RC) continue;
+        const int gj = j0 - R + c;
+        if (gi >= 0 && gi < H && gj >= 0 && gj < W) continue;
+        sr[a][c] = sr[reflect_index(gi, H) - (i0 - R)][reflect_index(gj, W) - (j0 - R)];
+      }
+    }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < RR * FX; e += FNT) {
-    const int a = e / FX, c = e - a * FX;
-    float acc = 0.f;
 #pragma unroll
-    for (int k = 0; k <= 2 * R; ++k) acc = fmaf(wk[k], sr[a][c + k], acc);
-    sh[a][c] = acc;
+  for (int t = 0; t < (RR + NW - 1) / NW; ++t) {
+    const int a = wp + NW * t;
+    if (a < RR) {
+      float acc = 0.f;
+#pragma unroll
+      for (int k = 0; k <= 2 * R; ++k) acc = fmaf(wk[k], sr[a][lane + k], acc);
+      sh[a][lane] = acc;
+    }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < FY * FX; e += FNT) {
-    const int a = e / FX, c = e - a * FX;
-    const int gi = i0 + a, gj = j0 + c;
-    if (gi >= H || gj >= W) continue;
-    float v = 0.f;
+  {
+    const int a0 = wp * VO;
+    float win[VO + 2 * R];
 #pragma unroll
-    for (int k = 0; k <= 2 * R; ++k) v = fmaf(wk[k], sh[a + k][c], v);
-    const size_t o = (size_t)gi * W + gj;
-    const float xc = sx[a + 2 * R][c + 2 * R];
-    float o_v = xc - gamma * v;
-    if (h) o_v = fmaf(ch, __ldg(h + o), o_v);
-    out[o] = o_v;
-    const float dy = gi < H - 1 ? sx[a + 2 * R + 1][c + 2 * R] - xc : 0.f;
-    const float dx = gj < W - 1 ? sx[a + 2 * R][c + 2 * R + 1] - xc : 0.f;
-    acc_b.add(tv_term(0.f, dy, dx));
+    for (int t = 0; t < VO + 2 * R; ++t) win[t] = sh[a0 + t][lane];
+    const int gj = j0 + lane;
+#pragma unroll
+    for (int t = 0; t < VO; ++t) {
+      const int a = a0 + t;
+      const int gi = i0 + a;
+      if (gi >= H || gj >= W) continue;
+      float v = 0.f;
+#pragma unroll
+      for (int k = 0; k <= 2 * R; ++k) v = fmaf(wk[k], win[t + k], v);
+      const size_t o = (size_t)gi * W + gj;
+      const float xc = sx[a + 2 * R][lane + 2 * R];
+      float o_v = xc - gamma * v;
+      if (h) o_v = fmaf(ch, __ldg(h + o), o_v);
+      out[o] = o_v;
+      const float dy = gi < H - 1 ? sx[a + 2 * R + 1][lane + 2 * R] - xc : 0.f;
+      const float dx = gj < W - 1 ? sx[a + 2 * R][lane + 2 * R + 1] - xc : 0.f;
+      acc_b.add(tv_term(0.f, dy, dx));
+    }
   }
   block_sum2_store<FNT>(acc_a, acc_b, part_a, part_b, part_index);
 }

@@ -6,9 +6,45 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "kernels.hpp"
 
 namespace tvs {
+
+// ---------------------------------------------------------------- launches
+// Every kernel is launched with programmatic dependent launch allowed (unless
+// TVS_PDL=0): the next kernel in the stream may be scheduled while the previous
+// one drains, and each kernel's first action, pdl_enter(), waits until the
+// previous grid has completed and its memory is visible before touching any
+// memory, then lets its own successor be scheduled.  The overlap hides the launch
+// latency and ramp of the long chains of short, dependent kernels (thousands per
+// solve); kernels not launched this way pass through pdl_enter() at no cost.
+bool pdl_enabled();
+
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" :::);
+}
+
+template <typename... P, typename... A>
+inline void launch_kernel(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                          A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  if (pdl_enabled()) {
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  // errors surface through cudaGetLastError() at the launcher's return
+  (void)cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
 
 // ---------------------------------------------------------------- storage
 // The TV dual field may be stored as float, bfloat16 or half; arithmetic is

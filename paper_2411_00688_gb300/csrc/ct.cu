@@ -38,6 +38,7 @@ __device__ __forceinline__ float joseph_fr(const GeomConsts& g, float4 ang, int 
 }
 
 __global__ void transpose_kernel(const float* __restrict__ x, float* __restrict__ xt, int N) {
+  pdl_enter();
   __shared__ float tile[32][33];
   const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
@@ -58,6 +59,7 @@ __global__ void __launch_bounds__(CT_NT)
 joseph_fwd_kernel(GeomConsts g, const float4* __restrict__ angles, const float* __restrict__ x,
                   const float* __restrict__ xt, float* __restrict__ sino, float* __restrict__ y,
                   const float* __restrict__ b, float tau, Partial* __restrict__ part, float tau2 = 0.f) {
+  pdl_enter();
   const int ray = blockIdx.x * CT_NT + threadIdx.x;
   const int n_rays = g.n_angles * g.n_det;
   FAcc acc_d;
@@ -122,6 +124,7 @@ joseph_bwd_kernel(GeomConsts g, const float4* __restrict__ angles, const float4*
                   const float* __restrict__ ys,
                   const float* __restrict__ x, const float* __restrict__ h, float* __restrict__ out,
                   float sigma, float ch, Partial* __restrict__ part_tv) {
+  pdl_enter();
   const int N = g.N;
   const int pix = blockIdx.x * CT_NT + threadIdx.x;
   FAcc acc_tv;
@@ -228,24 +231,24 @@ cudaError_t launch_ct_forward(const CTGeom& g, const float* x, float* sino, floa
                               cudaStream_t s, float p) {
   if (!g.xt_scratch) return cudaErrorInvalidValue;
   dim3 tg((g.N + 31) / 32, (g.N + 31) / 32), tb(32, 8);
-  transpose_kernel<<<tg, tb, 0, s>>>(x, g.xt_scratch, g.N);
+  launch_kernel(transpose_kernel, dim3(tg), dim3(tb), 0, s, x, g.xt_scratch, g.N);
   const GeomConsts c = consts(g);
   const int blocks = ct_fwd_blocks(g);
   switch (mode) {
     case CT_FWD_PD:
-      joseph_fwd_kernel<1><<<blocks, CT_NT, 0, s>>>(c, g.angles, x, g.xt_scratch, sino, y, b, tau, part_data);
+      launch_kernel(joseph_fwd_kernel<1>, dim3(blocks), dim3(CT_NT), 0, s, c, g.angles, x, g.xt_scratch, sino, y, b, tau, part_data, 0.f);
       break;
     case CT_FWD_STORE:
-      joseph_fwd_kernel<2><<<blocks, CT_NT, 0, s>>>(c, g.angles, x, g.xt_scratch, sino, nullptr, b, 0.f, part_data);
+      launch_kernel(joseph_fwd_kernel<2>, dim3(blocks), dim3(CT_NT), 0, s, c, g.angles, x, g.xt_scratch, sino, nullptr, b, 0.f, part_data, 0.f);
       break;
     case CT_FWD_RESID:
-      joseph_fwd_kernel<3><<<blocks, CT_NT, 0, s>>>(c, g.angles, x, g.xt_scratch, sino, nullptr, b, 0.f, part_data);
+      launch_kernel(joseph_fwd_kernel<3>, dim3(blocks), dim3(CT_NT), 0, s, c, g.angles, x, g.xt_scratch, sino, nullptr, b, 0.f, part_data, 0.f);
       break;
     case CT_FWD_PD1:
-      joseph_fwd_kernel<4><<<blocks, CT_NT, 0, s>>>(c, g.angles, x, g.xt_scratch, sino, y, b, tau, part_data, p);
+      launch_kernel(joseph_fwd_kernel<4>, dim3(blocks), dim3(CT_NT), 0, s, c, g.angles, x, g.xt_scratch, sino, y, b, tau, part_data, p);
       break;
     default:
-      joseph_fwd_kernel<0><<<blocks, CT_NT, 0, s>>>(c, g.angles, x, g.xt_scratch, sino, nullptr, nullptr, 0.f, nullptr);
+      launch_kernel(joseph_fwd_kernel<0>, dim3(blocks), dim3(CT_NT), 0, s, c, g.angles, x, g.xt_scratch, sino, nullptr, nullptr, 0.f, nullptr, 0.f);
   }
   return cudaGetLastError();
 }
@@ -253,7 +256,7 @@ cudaError_t launch_ct_forward(const CTGeom& g, const float* x, float* sino, floa
 cudaError_t launch_ct_backward(const CTGeom& g, const float* y, const float* x, const float* h,
                                float* out, float sigma, float ch, Partial* part_tv, cudaStream_t s) {
   const GeomConsts c = consts(g);
-  joseph_bwd_kernel<<<ct_bwd_blocks(g), CT_NT, 0, s>>>(c, g.angles, g.angles2, y, x, h, out, sigma, ch,
+  launch_kernel(joseph_bwd_kernel, dim3(ct_bwd_blocks(g)), dim3(CT_NT), 0, s, c, g.angles, g.angles2, y, x, h, out, sigma, ch,
                                                        part_tv);
   return cudaGetLastError();
 }

@@ -27,6 +27,7 @@ template <typename T, bool NONNEG>
 __global__ void __launch_bounds__(NT2)
 fgp2d_kernel(const float* __restrict__ z, const T* __restrict__ pc, const T* __restrict__ pp,
              T* __restrict__ pn, int H, int W, float lam, float inv_step, float beta) {
+  pdl_enter();
   __shared__ float sry[TY2 + 2][TX2 + 3];
   __shared__ float srx[TY2 + 2][TX2 + 3];
   __shared__ float su[TY2 + 1][TX2 + 2];
@@ -94,6 +95,7 @@ template <typename T, bool NONNEG>
 __global__ void __launch_bounds__(NT3)
 fgp3d_kernel(const float* __restrict__ z, const T* __restrict__ pc, const T* __restrict__ pp,
              T* __restrict__ pn, int D, int H, int W, float lam, float inv_step, float beta) {
+  pdl_enter();
   __shared__ float sr[3][TZ3 + 2][TY3 + 2][TX3 + 2];
   __shared__ float su[TZ3 + 1][TY3 + 1][TX3 + 1];
   const int j0 = blockIdx.x * TX3, i0 = blockIdx.y * TY3, k0 = blockIdx.z * TZ3;
@@ -181,6 +183,7 @@ __global__ void __launch_bounds__(256)
 fgp2d_tb_kernel(const float* __restrict__ z, const T* __restrict__ pc, const T* __restrict__ pp,
                 T* __restrict__ pn, T* __restrict__ pnp, int H, int W, float lam, float inv_step,
                 TBBetas betas, int iters) {
+  pdl_enter();
   constexpr int NW = 8;
   constexpr int RW = 32 * CPL, RH = NW * RPW;
   constexpr int TW = RW - 2 * TB, TH = RH - 2 * TB;
@@ -318,6 +321,7 @@ __global__ void __launch_bounds__(256, (RPW * CPL > 10) ? 1 : 2)
 fgp2d_rb_kernel(const float* __restrict__ z, const T* __restrict__ pc, const T* __restrict__ pp,
                 T* __restrict__ pn, T* __restrict__ pnp, int H, int W, float lam, float inv_step,
                 TBBetas betas, int iters) {
+  pdl_enter();
   fgp2d_rb_body<T, NONNEG, TB, CPL, RPW>(z, pc, pp, pn, pnp, H, W, lam, inv_step, betas, iters,
                                           blockIdx.x, blockIdx.y);
 }
@@ -335,6 +339,7 @@ template <typename T, bool NONNEG, int CPL, int RPW, int ZC>
 __global__ void __launch_bounds__(256)
 fgp3d_zm_kernel(const float* __restrict__ z, const T* __restrict__ pc, const T* __restrict__ pp,
                 T* __restrict__ pn, int D, int H, int W, float lam, float inv_step, float beta) {
+  pdl_enter();
   constexpr int NW = 8;
   constexpr int RW = 32 * CPL, RH = NW * RPW;
   constexpr int TW = RW - 2, TH = RH - 2;
@@ -499,15 +504,16 @@ __global__ void fgp_finalize_kernel(const float* __restrict__ z, const T* __rest
                                     int H, int W, int ndim, float lam, float* __restrict__ x_out,
                                     float* __restrict__ h_out, float h_coef, T* __restrict__ p_home,
                                     const float* __restrict__ x_prev, float* __restrict__ fista_y,
-                                    const float* __restrict__ beta_tab, const int* __restrict__ beta_idx) {
+                                    const float* __restrict__ beta_tab, const int* __restrict__ beta_idx,
+                                    IndexMap im) {
+  pdl_enter();
   const float beta_x = fista_y ? beta_tab[*beta_idx] : 0.f;
   const size_t n = (size_t)D * H * W;
   const size_t HW = (size_t)H * W;
   for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n;
        o += (size_t)gridDim.x * blockDim.x) {
-    const int gj = (int)(o % W);
-    const int gi = (int)((o / W) % H);
-    const int gk = (int)(o / HW);
+    int gk, gi, gj;
+    im.coords(o, gk, gi, gj);
     float dv = 0.f;
     int c = 0;
     if (ndim == 3) {
@@ -543,7 +549,7 @@ cudaError_t fgp3d_zm_launch(const Dims& d, const float* z, const void* pc, const
                             float inv_step, float beta, cudaStream_t s) {
   constexpr int TW = 32 * CPL - 2, TH = 8 * RPW - 2;
   dim3 grid((d.nx + TW - 1) / TW, (d.ny + TH - 1) / TH, (d.nz + ZC - 1) / ZC);
-  fgp3d_zm_kernel<T, NN, CPL, RPW, ZC><<<grid, 256, 0, s>>>(z, (const T*)pc, (const T*)pp, (T*)pn, d.nz, d.ny,
+  launch_kernel(fgp3d_zm_kernel<T, NN, CPL, RPW, ZC>, dim3(grid), dim3(256), 0, s, z, (const T*)pc, (const T*)pp, (T*)pn, d.nz, d.ny,
                                                              d.nx, lam, inv_step, beta);
   return cudaGetLastError();
 }
@@ -604,10 +610,12 @@ bool fgp3d_use_zmarch() {
 template <typename T, bool NONNEG>
 __global__ void fgp_finalize_pd1_kernel(const float* __restrict__ z, const T* __restrict__ p, int H, int W,
                                         float lam, float prob_p, float* __restrict__ x,
-                                        float* __restrict__ xh, T* __restrict__ p_home) {
+                                        float* __restrict__ xh, T* __restrict__ p_home, IndexMap im) {
+  pdl_enter();
   const size_t n = (size_t)H * W;
   for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
-    const int gj = (int)(o % W), gi = (int)(o / W);
+    int gk, gi, gj;
+    im.coords(o, gk, gi, gj);
     float dv = 0.f;
     if (gi < H - 1) dv += Elem<T>::ld(p + o);
     if (gi > 0) dv -= Elem<T>::ld(p + o - W);
@@ -631,7 +639,7 @@ cudaError_t fgp_iter_t(const Dims& d, const float* z, const void* pc, const void
                        float lam, float inv_step, float beta, cudaStream_t s) {
   if (d.ndim == 2) {
     dim3 grid((d.nx + TX2 - 1) / TX2, (d.ny + TY2 - 1) / TY2);
-    fgp2d_kernel<T, NN><<<grid, NT2, 0, s>>>(z, (const T*)pc, (const T*)pp, (T*)pn, d.ny, d.nx, lam,
+    launch_kernel(fgp2d_kernel<T, NN>, dim3(grid), dim3(NT2), 0, s, z, (const T*)pc, (const T*)pp, (T*)pn, d.ny, d.nx, lam,
                                              inv_step, beta);
   } else if (fgp3d_use_zmarch() &&
              (long long)((d.nx + 29) / 30) * ((d.ny + 13) / 14) * ((d.nz + 63) / 64) >= 4 * 152) {
@@ -641,7 +649,7 @@ cudaError_t fgp_iter_t(const Dims& d, const float* z, const void* pc, const void
     if (e != cudaSuccess) return e;
   } else {
     dim3 grid((d.nx + TX3 - 1) / TX3, (d.ny + TY3 - 1) / TY3, (d.nz + TZ3 - 1) / TZ3);
-    fgp3d_kernel<T, NN><<<grid, NT3, 0, s>>>(z, (const T*)pc, (const T*)pp, (T*)pn, d.nz, d.ny,
+    launch_kernel(fgp3d_kernel<T, NN>, dim3(grid), dim3(NT3), 0, s, z, (const T*)pc, (const T*)pp, (T*)pn, d.nz, d.ny,
                                              d.nx, lam, inv_step, beta);
   }
   return cudaGetLastError();
@@ -659,7 +667,7 @@ cudaError_t fgp_tb_t(const Dims& d, const float* z, const void* pc, const void* 
   TBBetas b{};
   for (int i = 0; i < iters && i < 8; ++i) b.b[i] = betas[i];
   dim3 grid((d.nx + TW - 1) / TW, (d.ny + TH - 1) / TH);
-  fgp2d_tb_kernel<T, NN, TB, CPL, RPW><<<grid, 256, smem, s>>>(
+  launch_kernel(fgp2d_tb_kernel<T, NN, TB, CPL, RPW>, dim3(grid), dim3(256), smem, s, 
       z, (const T*)pc, (const T*)pp, (T*)pn, (T*)pnp, d.ny, d.nx, lam, inv_step, b, iters);
   return cudaGetLastError();
 }
@@ -672,7 +680,7 @@ cudaError_t fgp_rb_t(const Dims& d, const float* z, const void* pc, const void* 
   TBBetas b{};
   for (int i = 0; i < iters && i < 8; ++i) b.b[i] = betas[i];
   dim3 grid((d.nx + TW - 1) / TW, (d.ny + TH - 1) / TH);
-  fgp2d_rb_kernel<T, NN, TB, CPL, RPW><<<grid, 256, 0, s>>>(
+  launch_kernel(fgp2d_rb_kernel<T, NN, TB, CPL, RPW>, dim3(grid), dim3(256), 0, s, 
       z, (const T*)pc, (const T*)pp, (T*)pn, (T*)pnp, d.ny, d.nx, lam, inv_step, b, iters);
   return cudaGetLastError();
 }
@@ -713,9 +721,9 @@ cudaError_t fgp_finalize_t(const Dims& d, const float* z, const void* p, float l
   const size_t n = d.n();
   int blocks = (int)((n + 255) / 256);
   if (blocks > 152 * 16) blocks = 152 * 16;
-  fgp_finalize_kernel<T, NN><<<blocks, 256, 0, s>>>(z, (const T*)p, d.nz, d.ny, d.nx, d.ndim, lam,
+  launch_kernel(fgp_finalize_kernel<T, NN>, dim3(blocks), dim3(256), 0, s, z, (const T*)p, d.nz, d.ny, d.nx, d.ndim, lam,
                                                     x_out, h_out, h_coef, (T*)p_home, x_prev,
-                                                    fista_y, beta_tab, beta_idx);
+                                                    fista_y, beta_tab, beta_idx, IndexMap(d.nz, d.ny, d.nx));
   return cudaGetLastError();
 }
 
@@ -747,11 +755,11 @@ cudaError_t launch_fgp_finalize_pd1(const Dims& d, const float* z, const void* p
   if (blocks > 152 * 16) blocks = 152 * 16;
 #define TVS_PD1(T_)                                                                                   \
   if (nonneg)                                                                                         \
-    fgp_finalize_pd1_kernel<T_, true><<<blocks, 256, 0, s>>>(z, (const T_*)p, d.ny, d.nx, lam, prob_p, x, xh, \
-                                                             (T_*)p_home);                            \
+    launch_kernel(fgp_finalize_pd1_kernel<T_, true>, dim3(blocks), dim3(256), 0, s, z, (const T_*)p, d.ny, d.nx, lam, prob_p, x, xh, \
+                                                             (T_*)p_home, IndexMap(1, d.ny, d.nx));   \
   else                                                                                                \
-    fgp_finalize_pd1_kernel<T_, false><<<blocks, 256, 0, s>>>(z, (const T_*)p, d.ny, d.nx, lam, prob_p, x, xh, \
-                                                              (T_*)p_home);
+    launch_kernel(fgp_finalize_pd1_kernel<T_, false>, dim3(blocks), dim3(256), 0, s, z, (const T_*)p, d.ny, d.nx, lam, prob_p, x, xh, \
+                                                              (T_*)p_home, IndexMap(1, d.ny, d.nx));
   if (dtype == DUAL_F32) {
     TVS_PD1(float)
   } else if (dtype == DUAL_BF16) {

@@ -14,6 +14,48 @@ struct Dims {
 
 enum DualType { DUAL_F32 = 0, DUAL_BF16 = 1, DUAL_F16 = 2 };
 
+// floor(n / d) for 0 <= n < 2^31 by one multiply and shift (division by an
+// invariant integer, Granlund and Montgomery, PLDI 1994, Theorem 4.2 with N = 31):
+// L = 31 + ceil(log2 d) and m = ceil(2^L / d), which is below 2^32.
+struct FastDiv {
+  uint32_t m = 1u << 31, L = 31;
+  FastDiv() = default;
+  explicit FastDiv(uint32_t d) {
+    uint32_t s = 0;
+    while ((1ull << s) < d) ++s;
+    L = 31 + s;
+    m = (uint32_t)(((1ull << L) + d - 1) / d);
+  }
+#ifdef __CUDACC__
+  __device__ __forceinline__ uint32_t div(uint32_t n) const { return (uint32_t)(((uint64_t)n * m) >> L); }
+#endif
+};
+
+// Row-major coordinates (k, i, j) of a linear index over a D x H x W grid, by
+// FastDiv when the grid has fewer than 2^31 cells, else by 64-bit division.
+struct IndexMap {
+  FastDiv fW, fH;
+  int W = 1, H = 1, small = 1;
+  IndexMap() = default;
+  IndexMap(int D, int H_, int W_)
+      : fW((uint32_t)W_), fH((uint32_t)H_), W(W_), H(H_), small((size_t)D * H_ * W_ < ((size_t)1 << 31)) {}
+#ifdef __CUDACC__
+  __device__ __forceinline__ void coords(size_t o, int& k, int& i, int& j) const {
+    if (small) {
+      const uint32_t u = (uint32_t)o, r = fW.div(u), kk = fH.div(r);
+      j = (int)(u - r * (uint32_t)W);
+      i = (int)(r - kk * (uint32_t)H);
+      k = (int)kk;
+    } else {
+      const size_t r = o / (size_t)W;
+      j = (int)(o - r * W);
+      k = (int)(r / (size_t)H);
+      i = (int)(r - (size_t)k * H);
+    }
+  }
+#endif
+};
+
 // One block's partial sum of an objective term: a compensated FP32 pair whose
 // value is s + c (see FAcc in common.cuh).
 struct Partial {

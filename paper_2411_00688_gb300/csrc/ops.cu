@@ -10,6 +10,8 @@
 // The objective F(x) = 1/2 ||A x - b||^2 + alpha TV(x) (Eq. 5) is accumulated in
 // the same passes: per-pixel FP32 terms, FP64 per-thread and per-block sums,
 // block totals summed in a fixed order by one block (bitwise reproducible).
+#include <cstdlib>
+
 #include "blur_body.cuh"
 #include "common.cuh"
 #include "kernels.hpp"
@@ -26,6 +28,7 @@ blur_kernel(const float* __restrict__ src, int H, int W, BlurW w, const float* _
             float* __restrict__ out, const float* __restrict__ x, const float* __restrict__ h,
             float gamma, float ch, float* __restrict__ axp, float* __restrict__ y, float tau,
             Partial* __restrict__ part_a, Partial* __restrict__ part_b) {
+  pdl_enter();
   blur_tile_body<MODE, R>(src, H, W, w, b, out, x, h, gamma, ch, axp, y, tau, part_a, part_b, blockIdx.x,
                           blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x);
 }
@@ -35,6 +38,7 @@ __global__ void __launch_bounds__(FNT)
 blur_fb_step_kernel(const float* __restrict__ x, const float* __restrict__ b, const float* __restrict__ h,
                     float* __restrict__ out, int H, int W, BlurW w, float gamma, float ch,
                     Partial* __restrict__ part_a, Partial* __restrict__ part_b) {
+  pdl_enter();
   blur_fb_step_body<R>(x, b, h, out, H, W, w, gamma, ch, part_a, part_b, blockIdx.x, blockIdx.y,
                        blockIdx.y * gridDim.x + blockIdx.x);
 }
@@ -44,11 +48,13 @@ __global__ void __launch_bounds__(PW_NT)
 identity_step_kernel(const float* __restrict__ x, const float* __restrict__ b,
                      const float* __restrict__ h, float* __restrict__ out, int D, int H, int W,
                      int ndim, float gamma, float ch, Partial* __restrict__ part_a,
-                     Partial* __restrict__ part_b) {
+                     Partial* __restrict__ part_b, IndexMap im) {
+  pdl_enter();
   const size_t n = (size_t)D * H * W, HW = (size_t)H * W;
   FAcc acc_a, acc_b;
   for (size_t o = blockIdx.x * (size_t)PW_NT + threadIdx.x; o < n; o += (size_t)gridDim.x * PW_NT) {
-    const int gj = (int)(o % W), gi = (int)((o / W) % H), gk = (int)(o / HW);
+    int gk, gi, gj;
+    im.coords(o, gk, gi, gj);
     const float xc = __ldg(x + o), bb = __ldg(b + o);
     const float r = xc - bb;
     if (out) {
@@ -68,7 +74,8 @@ identity_step_kernel(const float* __restrict__ x, const float* __restrict__ b,
 __global__ void __launch_bounds__(PW_NT)
 axpy_step_kernel(const float* __restrict__ g, const float* __restrict__ x,
                  const float* __restrict__ h, float* __restrict__ out, int D, int H, int W,
-                 int ndim, float sigma, float ch, Partial* __restrict__ part_b) {
+                 int ndim, float sigma, float ch, Partial* __restrict__ part_b, IndexMap im) {
+  pdl_enter();
   const size_t n = (size_t)D * H * W, HW = (size_t)H * W;
   FAcc acc_b;
   for (size_t o = blockIdx.x * (size_t)PW_NT + threadIdx.x; o < n; o += (size_t)gridDim.x * PW_NT) {
@@ -77,7 +84,8 @@ axpy_step_kernel(const float* __restrict__ g, const float* __restrict__ x,
     if (h) v = fmaf(ch, __ldg(h + o), v);
     out[o] = v;
     if (part_b) {
-      const int gj = (int)(o % W), gi = (int)((o / W) % H), gk = (int)(o / HW);
+      int gk, gi, gj;
+    im.coords(o, gk, gi, gj);
       const float d0 = (ndim == 3 && gk < D - 1) ? __ldg(x + o + HW) - xc : 0.f;
       const float d1 = gi < H - 1 ? __ldg(x + o + W) - xc : 0.f;
       const float d2 = gj < W - 1 ? __ldg(x + o + 1) - xc : 0.f;
@@ -89,11 +97,13 @@ axpy_step_kernel(const float* __restrict__ g, const float* __restrict__ x,
 
 __global__ void __launch_bounds__(PW_NT)
 tv_partials_kernel(const float* __restrict__ x, int D, int H, int W, int ndim,
-                   Partial* __restrict__ part_b) {
+                   Partial* __restrict__ part_b, IndexMap im) {
+  pdl_enter();
   const size_t n = (size_t)D * H * W, HW = (size_t)H * W;
   FAcc acc_b;
   for (size_t o = blockIdx.x * (size_t)PW_NT + threadIdx.x; o < n; o += (size_t)gridDim.x * PW_NT) {
-    const int gj = (int)(o % W), gi = (int)((o / W) % H), gk = (int)(o / HW);
+    int gk, gi, gj;
+    im.coords(o, gk, gi, gj);
     const float xc = __ldg(x + o);
     const float d0 = (ndim == 3 && gk < D - 1) ? __ldg(x + o + HW) - xc : 0.f;
     const float d1 = gi < H - 1 ? __ldg(x + o + W) - xc : 0.f;
@@ -109,6 +119,7 @@ __global__ void __launch_bounds__(PW_NT)
 pd1_dual_pointwise_kernel(size_t m, const float* __restrict__ axh, float* __restrict__ axp,
                           float* __restrict__ y, const float* __restrict__ b, float p, float tau,
                           Partial* __restrict__ part_a) {
+  pdl_enter();
   FAcc acc;
   for (size_t o = blockIdx.x * (size_t)PW_NT + threadIdx.x; o < m; o += (size_t)gridDim.x * PW_NT) {
     const float bb = __ldg(b + o);
@@ -130,6 +141,7 @@ __global__ void __launch_bounds__(PW_NT)
 pd_dual_pointwise_kernel(size_t m, const float* __restrict__ ax, float* __restrict__ axp,
                          float* __restrict__ y, const float* __restrict__ b, float tau,
                          Partial* __restrict__ part_a) {
+  pdl_enter();
   FAcc acc;
   for (size_t o = blockIdx.x * (size_t)PW_NT + threadIdx.x; o < m; o += (size_t)gridDim.x * PW_NT) {
     const float v = __ldg(ax + o), bb = __ldg(b + o);
@@ -146,6 +158,7 @@ __global__ void __launch_bounds__(512)
 reduce_record_kernel(const Partial* __restrict__ part_a, int n_a, const Partial* __restrict__ part_b,
                      int n_b, double alpha, int every, double* obj, unsigned long long* ts,
                      double f_star, double target, int* flags, int* done_host, double* f_out) {
+  pdl_enter();
   const double sum_a = block_sum_partials<512>(part_a, n_a);
   const double sum_b = block_sum_partials<512>(part_b, n_b);
   if (threadIdx.x == 0) {
@@ -170,6 +183,7 @@ reduce_record_kernel(const Partial* __restrict__ part_a, int n_a, const Partial*
 
 __global__ void __launch_bounds__(PW_NT)
 dist_partials_kernel(size_t n, const float* __restrict__ x, const float* __restrict__ u, Partial* __restrict__ part) {
+  pdl_enter();
   FAcc acc;
   for (size_t o = blockIdx.x * (size_t)PW_NT + threadIdx.x; o < n; o += (size_t)gridDim.x * PW_NT) {
     const float d = __ldg(x + o) - __ldg(u + o);
@@ -181,6 +195,7 @@ dist_partials_kernel(size_t n, const float* __restrict__ x, const float* __restr
 __global__ void __launch_bounds__(512)
 dist_record_kernel(const Partial* __restrict__ part, int n_part, double ref_norm2, double* dist, double target,
                    int* flags, int* done_host) {
+  pdl_enter();
   const double sum = block_sum_partials<512>(part, n_part);
   if (threadIdx.x != 0) return;
   const int k = flags[2] - 1;
@@ -197,15 +212,18 @@ dist_record_kernel(const Partial* __restrict__ part, int n_part, double ref_norm
   }
 }
 
-__global__ void timestamp_kernel(unsigned long long* ts) { *ts = globaltimer_ns(); }
+__global__ void timestamp_kernel(unsigned long long* ts) {
+  pdl_enter(); *ts = globaltimer_ns(); }
 
 __global__ void timestamp_pair_kernel(unsigned long long* arr, int* ctr, int which) {
+  pdl_enter();
   const int c = *ctr;
   arr[2 * c + which] = globaltimer_ns();
   if (which == 1) *ctr = c + 1;
 }
 
 __global__ void count_nonfinite_kernel(const float* __restrict__ x, size_t n, int* count) {
+  pdl_enter();
   int c = 0;
   for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n;
        o += (size_t)gridDim.x * blockDim.x)
@@ -214,6 +232,7 @@ __global__ void count_nonfinite_kernel(const float* __restrict__ x, size_t n, in
 }
 
 __global__ void coin_kernel(uint64_t seed, double p, int64_t k0, int K, unsigned char* out) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < K) out[i] = (unsigned char)Philox4x64::coin(seed, p, (uint64_t)(k0 + i));
 }
@@ -225,7 +244,7 @@ cudaError_t blur_launch(int H, int W, const float* src, const BlurW& w, const fl
   dim3 grid((W + BX - 1) / BX, (H + BY - 1) / BY);
   switch (w.R) {
 #define TVS_BLUR_R(R_) \
-  case R_: blur_kernel<MODE, R_><<<grid, BNT, 0, s>>>(src, H, W, w, b, out, x, h, gamma, ch, axp, y, tau, pa, pb); break;
+  case R_: launch_kernel(blur_kernel<MODE, R_>, dim3(grid), dim3(BNT), 0, s, src, H, W, w, b, out, x, h, gamma, ch, axp, y, tau, pa, pb); break;
     TVS_BLUR_R(1) TVS_BLUR_R(2) TVS_BLUR_R(3) TVS_BLUR_R(4) TVS_BLUR_R(5) TVS_BLUR_R(6) TVS_BLUR_R(7) TVS_BLUR_R(8)
 #undef TVS_BLUR_R
     default:
@@ -236,6 +255,14 @@ cudaError_t blur_launch(int H, int W, const float* src, const BlurW& w, const fl
 
 }  // namespace
 
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("TVS_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
 int tile_blocks_2d(int H, int W) { return ((W + BX - 1) / BX) * ((H + BY - 1) / BY); }
 int fb_step_blocks_2d(int H, int W) { return ((W + FX - 1) / FX) * ((H + FY - 1) / FY); }
 
@@ -245,7 +272,7 @@ cudaError_t launch_blur_fb_step(int H, int W, const float* x, const float* b, co
   dim3 grid((W + FX - 1) / FX, (H + FY - 1) / FY);
   switch (w.R) {
 #define TVS_FB_R(R_) \
-  case R_: blur_fb_step_kernel<R_><<<grid, FNT, 0, s>>>(x, b, h, out, H, W, w, gamma, ch, part_data, part_tv); break;
+  case R_: launch_kernel(blur_fb_step_kernel<R_>, dim3(grid), dim3(FNT), 0, s, x, b, h, out, H, W, w, gamma, ch, part_data, part_tv); break;
     TVS_FB_R(1) TVS_FB_R(2) TVS_FB_R(3) TVS_FB_R(4) TVS_FB_R(5) TVS_FB_R(6) TVS_FB_R(7) TVS_FB_R(8)
 #undef TVS_FB_R
     default:
@@ -296,32 +323,33 @@ cudaError_t launch_blur(int H, int W, const float* x, float* y, const BlurW& w, 
 cudaError_t launch_identity_step(const Dims& d, const float* x, const float* b, const float* h,
                                  float* out, float gamma, float ch, Partial* part_data,
                                  Partial* part_tv, cudaStream_t s) {
-  identity_step_kernel<<<pointwise_blocks(d.n()), PW_NT, 0, s>>>(x, b, h, out, d.nz, d.ny, d.nx,
-                                                                  d.ndim, gamma, ch, part_data, part_tv);
+  launch_kernel(identity_step_kernel, dim3(pointwise_blocks(d.n())), dim3(PW_NT), 0, s, x, b, h, out, d.nz, d.ny, d.nx,
+                                                                  d.ndim, gamma, ch, part_data, part_tv, IndexMap(d.nz, d.ny, d.nx));
   return cudaGetLastError();
 }
 
 cudaError_t launch_axpy_step(const Dims& d, const float* g, const float* x, const float* h,
                              float* out, float sigma, float ch, Partial* part_tv, cudaStream_t s) {
-  axpy_step_kernel<<<pointwise_blocks(d.n()), PW_NT, 0, s>>>(g, x, h, out, d.nz, d.ny, d.nx, d.ndim,
-                                                              sigma, ch, part_tv);
+  launch_kernel(axpy_step_kernel, dim3(pointwise_blocks(d.n())), dim3(PW_NT), 0, s, g, x, h, out, d.nz, d.ny, d.nx, d.ndim,
+                                                              sigma, ch, part_tv, IndexMap(d.nz, d.ny, d.nx));
   return cudaGetLastError();
 }
 
 cudaError_t launch_pd1_dual_pointwise(size_t m, const float* axh, float* ax_prev, float* y, const float* b,
                                       float p, float tau, Partial* part_data, cudaStream_t s) {
-  pd1_dual_pointwise_kernel<<<pointwise_blocks(m), PW_NT, 0, s>>>(m, axh, ax_prev, y, b, p, tau, part_data);
+  launch_kernel(pd1_dual_pointwise_kernel, dim3(pointwise_blocks(m)), dim3(PW_NT), 0, s, m, axh, ax_prev, y, b, p, tau, part_data);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tv_partials(const Dims& d, const float* x, Partial* part_tv, cudaStream_t s) {
-  tv_partials_kernel<<<pointwise_blocks(d.n()), PW_NT, 0, s>>>(x, d.nz, d.ny, d.nx, d.ndim, part_tv);
+  launch_kernel(tv_partials_kernel, dim3(pointwise_blocks(d.n())), dim3(PW_NT), 0, s, x, d.nz, d.ny, d.nx, d.ndim, part_tv,
+                IndexMap(d.nz, d.ny, d.nx));
   return cudaGetLastError();
 }
 
 cudaError_t launch_pd_dual_pointwise(size_t m, const float* ax, float* ax_prev, float* y,
                                      const float* b, float tau, Partial* part_data, cudaStream_t s) {
-  pd_dual_pointwise_kernel<<<pointwise_blocks(m), PW_NT, 0, s>>>(m, ax, ax_prev, y, b, tau, part_data);
+  launch_kernel(pd_dual_pointwise_kernel, dim3(pointwise_blocks(m)), dim3(PW_NT), 0, s, m, ax, ax_prev, y, b, tau, part_data);
   return cudaGetLastError();
 }
 
@@ -329,42 +357,42 @@ cudaError_t launch_reduce_record(const Partial* part_data, int n_data, const Par
                                  int n_tv, double alpha, int every, double* obj,
                                  unsigned long long* ts, double f_star, double target, int* flags,
                                  int* done_host, double* f_out, cudaStream_t s) {
-  reduce_record_kernel<<<1, 512, 0, s>>>(part_data, n_data, part_tv, n_tv, alpha, every, obj, ts,
+  launch_kernel(reduce_record_kernel, dim3(1), dim3(512), 0, s, part_data, n_data, part_tv, n_tv, alpha, every, obj, ts,
                                          f_star, target, flags, done_host, f_out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dist_partials(size_t n, const float* x, const float* u_ref, Partial* part, cudaStream_t s) {
-  dist_partials_kernel<<<pointwise_blocks(n), PW_NT, 0, s>>>(n, x, u_ref, part);
+  launch_kernel(dist_partials_kernel, dim3(pointwise_blocks(n)), dim3(PW_NT), 0, s, n, x, u_ref, part);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dist_record(const Partial* part, int n_part, double ref_norm2, double* dist, double target,
                                int* flags, int* done_host, cudaStream_t s) {
-  dist_record_kernel<<<1, 512, 0, s>>>(part, n_part, ref_norm2, dist, target, flags, done_host);
+  launch_kernel(dist_record_kernel, dim3(1), dim3(512), 0, s, part, n_part, ref_norm2, dist, target, flags, done_host);
   return cudaGetLastError();
 }
 
 cudaError_t launch_timestamp(unsigned long long* ts, cudaStream_t s) {
-  timestamp_kernel<<<1, 1, 0, s>>>(ts);
+  launch_kernel(timestamp_kernel, dim3(1), dim3(1), 0, s, ts);
   return cudaGetLastError();
 }
 
 cudaError_t launch_timestamp_pair(unsigned long long* arr, int* ctr, int which, cudaStream_t s) {
-  timestamp_pair_kernel<<<1, 1, 0, s>>>(arr, ctr, which);
+  launch_kernel(timestamp_pair_kernel, dim3(1), dim3(1), 0, s, arr, ctr, which);
   return cudaGetLastError();
 }
 
 cudaError_t launch_count_nonfinite(const float* x, size_t n, int* count, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  count_nonfinite_kernel<<<pointwise_blocks(n), PW_NT, 0, s>>>(x, n, count);
+  launch_kernel(count_nonfinite_kernel, dim3(pointwise_blocks(n)), dim3(PW_NT), 0, s, x, n, count);
   return cudaGetLastError();
 }
 
 cudaError_t launch_coin_schedule(uint64_t seed, double p, int64_t k0, int K, unsigned char* out,
                                  cudaStream_t s) {
   if (K <= 0) return cudaSuccess;
-  coin_kernel<<<(K + 255) / 256, 256, 0, s>>>(seed, p, k0, K, out);
+  launch_kernel(coin_kernel, dim3((K + 255) / 256), dim3(256), 0, s, seed, p, k0, K, out);
   return cudaGetLastError();
 }
 

@@ -28,6 +28,7 @@ constexpr int PW = 256;
 __global__ void __launch_bounds__(PW)
 pdx_precond_kernel(const float* __restrict__ colA, const float* __restrict__ rowA, int H, int W, size_t m,
                    float sigma, float tau, float* __restrict__ T, float* __restrict__ S) {
+  pdl_enter();
   const size_t n = (size_t)H * W, total = n > m ? n : m;
   for (size_t o = blockIdx.x * (size_t)PW + threadIdx.x; o < total; o += (size_t)gridDim.x * PW) {
     if (o < n) {
@@ -44,6 +45,7 @@ pdx_precond_kernel(const float* __restrict__ colA, const float* __restrict__ row
 }
 
 __global__ void __launch_bounds__(PW) fill_kernel(float* __restrict__ a, size_t n, float v) {
+  pdl_enter();
   for (size_t o = blockIdx.x * (size_t)PW + threadIdx.x; o < n; o += (size_t)gridDim.x * PW) a[o] = v;
 }
 
@@ -55,6 +57,7 @@ __global__ void __launch_bounds__(QNT)
 pdx_tv_step_kernel(const float* __restrict__ x, const float* __restrict__ g, const float* __restrict__ T,
                    const float* __restrict__ q, float* __restrict__ xn, float* __restrict__ qn, int H, int W,
                    float alpha, float s_d, Partial* __restrict__ part_tv) {
+  pdl_enter();
   __shared__ float sqy[QY + 2][QX + 3];
   __shared__ float sqx[QY + 2][QX + 3];
   __shared__ float sxb[QY + 1][QX + 2];  // x- = 2 x+ - x
@@ -122,6 +125,7 @@ template <bool INIT>
 __global__ void __launch_bounds__(PW)
 pdx_dual_kernel(size_t m, const float* __restrict__ ax, float* __restrict__ axp, float* __restrict__ y,
                 const float* __restrict__ b, const float* __restrict__ S, Partial* __restrict__ part_a) {
+  pdl_enter();
   FAcc acc;
   for (size_t o = blockIdx.x * (size_t)PW + threadIdx.x; o < m; o += (size_t)gridDim.x * PW) {
     const float v = __ldg(ax + o), bb = __ldg(b + o);
@@ -144,12 +148,12 @@ int pdx_tv_blocks(int H, int W) { return ((W + QX - 1) / QX) * ((H + QY - 1) / Q
 cudaError_t launch_pdx_precond(const float* colA, const float* rowA, int H, int W, size_t m, float sigma,
                                float tau, float* T, float* S, cudaStream_t s) {
   const size_t n = (size_t)H * W;
-  pdx_precond_kernel<<<pointwise_blocks(n > m ? n : m), PW, 0, s>>>(colA, rowA, H, W, m, sigma, tau, T, S);
+  launch_kernel(pdx_precond_kernel, dim3(pointwise_blocks(n > m ? n : m)), dim3(PW), 0, s, colA, rowA, H, W, m, sigma, tau, T, S);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fill(float* a, size_t n, float v, cudaStream_t s) {
-  fill_kernel<<<pointwise_blocks(n), PW, 0, s>>>(a, n, v);
+  launch_kernel(fill_kernel, dim3(pointwise_blocks(n)), dim3(PW), 0, s, a, n, v);
   return cudaGetLastError();
 }
 
@@ -157,15 +161,15 @@ cudaError_t launch_pdx_tv_step(int H, int W, const float* x, const float* g, con
                                float* xn, float* qn, float alpha, float s_d, bool nonneg, Partial* part_tv,
                                cudaStream_t s) {
   dim3 grid((W + QX - 1) / QX, (H + QY - 1) / QY);
-  if (nonneg) pdx_tv_step_kernel<true><<<grid, QNT, 0, s>>>(x, g, T, q, xn, qn, H, W, alpha, s_d, part_tv);
-  else pdx_tv_step_kernel<false><<<grid, QNT, 0, s>>>(x, g, T, q, xn, qn, H, W, alpha, s_d, part_tv);
+  if (nonneg) launch_kernel(pdx_tv_step_kernel<true>, dim3(grid), dim3(QNT), 0, s, x, g, T, q, xn, qn, H, W, alpha, s_d, part_tv);
+  else launch_kernel(pdx_tv_step_kernel<false>, dim3(grid), dim3(QNT), 0, s, x, g, T, q, xn, qn, H, W, alpha, s_d, part_tv);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pdx_dual(size_t m, const float* ax, float* axp, float* y, const float* b, const float* S,
                             bool init, Partial* part_a, cudaStream_t s) {
-  if (init) pdx_dual_kernel<true><<<pointwise_blocks(m), PW, 0, s>>>(m, ax, axp, y, b, S, part_a);
-  else pdx_dual_kernel<false><<<pointwise_blocks(m), PW, 0, s>>>(m, ax, axp, y, b, S, part_a);
+  if (init) launch_kernel(pdx_dual_kernel<true>, dim3(pointwise_blocks(m)), dim3(PW), 0, s, m, ax, axp, y, b, S, part_a);
+  else launch_kernel(pdx_dual_kernel<false>, dim3(pointwise_blocks(m)), dim3(PW), 0, s, m, ax, axp, y, b, S, part_a);
   return cudaGetLastError();
 }
 

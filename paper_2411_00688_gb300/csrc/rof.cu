@@ -23,6 +23,7 @@ __global__ void __launch_bounds__(RNT)
 dual_rof_step_kernel(const float* __restrict__ q, float* __restrict__ qn, float* __restrict__ h,
                      const float* __restrict__ b, int H, int W, float alpha, float eps_over_alpha,
                      float gamma, float p, Partial* __restrict__ part_a, Partial* __restrict__ part_b) {
+  pdl_enter();
   __shared__ float sqy[RY + 2][RX + 3];
   __shared__ float sqx[RY + 2][RX + 3];
   __shared__ float sw[RY + 1][RX + 2];
@@ -100,6 +101,7 @@ dual_rof_step_kernel(const float* __restrict__ q, float* __restrict__ qn, float*
 __global__ void __launch_bounds__(RNT)
 dual_rof_primal_kernel(const float* __restrict__ q, const float* __restrict__ b, float* __restrict__ u,
                        int H, int W, Partial* __restrict__ part_a, Partial* __restrict__ part_b) {
+  pdl_enter();
   const size_t n = (size_t)H * W;
   FAcc acc_a, acc_b;
   for (size_t o = blockIdx.x * (size_t)RNT + threadIdx.x; o < n; o += (size_t)gridDim.x * RNT) {
@@ -128,18 +130,18 @@ cudaError_t launch_dual_rof_step(int H, int W, const float* q, float* qn, float*
   dim3 grid((W + RX - 1) / RX, (H + RY - 1) / RY);
   const float ea = alpha > 0.f ? eps / alpha : 0.f;
   if (prox) {
-    if (h) dual_rof_step_kernel<true, true><<<grid, RNT, 0, s>>>(q, qn, h, b, H, W, alpha, ea, gamma, p, part_a, part_b);
-    else dual_rof_step_kernel<true, false><<<grid, RNT, 0, s>>>(q, qn, h, b, H, W, alpha, ea, gamma, p, part_a, part_b);
+    if (h) launch_kernel(dual_rof_step_kernel<true, true>, dim3(grid), dim3(RNT), 0, s, q, qn, h, b, H, W, alpha, ea, gamma, p, part_a, part_b);
+    else launch_kernel(dual_rof_step_kernel<true, false>, dim3(grid), dim3(RNT), 0, s, q, qn, h, b, H, W, alpha, ea, gamma, p, part_a, part_b);
   } else {
-    if (h) dual_rof_step_kernel<false, true><<<grid, RNT, 0, s>>>(q, qn, h, b, H, W, alpha, ea, gamma, p, part_a, part_b);
-    else dual_rof_step_kernel<false, false><<<grid, RNT, 0, s>>>(q, qn, h, b, H, W, alpha, ea, gamma, p, part_a, part_b);
+    if (h) launch_kernel(dual_rof_step_kernel<false, true>, dim3(grid), dim3(RNT), 0, s, q, qn, h, b, H, W, alpha, ea, gamma, p, part_a, part_b);
+    else launch_kernel(dual_rof_step_kernel<false, false>, dim3(grid), dim3(RNT), 0, s, q, qn, h, b, H, W, alpha, ea, gamma, p, part_a, part_b);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_dual_rof_primal(int H, int W, const float* q, const float* b, float* u, Partial* part_a,
                                    Partial* part_b, cudaStream_t s) {
-  dual_rof_primal_kernel<<<pointwise_blocks((size_t)H * W), RNT, 0, s>>>(q, b, u, H, W, part_a, part_b);
+  launch_kernel(dual_rof_primal_kernel, dim3(pointwise_blocks((size_t)H * W)), dim3(RNT), 0, s, q, b, u, H, W, part_a, part_b);
   return cudaGetLastError();
 }
 
