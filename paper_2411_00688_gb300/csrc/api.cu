@@ -214,8 +214,8 @@ FgpConfig default_fgp_config() {
 // type) in a context times each candidate tile shape / depth on the caller's z
 // (two launches of 4 iterations after one warm-up, CUDA events on the context's
 // stream), reading the dual in `home` and writing only `scratch0/1`, and keeps
-// the fastest.  Candidates: register-blocked 32x40 and 64x40 regions, the
-// shared-memory 32x40 region, register-blocked 32x64.
+// the fastest.  Candidates: register-blocked 32x40, 64x32 and 64x40 regions, the
+// shared-memory 32x40 region.
 tvs_status fgp_config_for(tvs_ctx* C, const Dims& d, int dtype, const float* z, void* home,
                           void* scratch0, void* scratch1, FgpConfig* out) {
   if (d.ndim != 2) {
@@ -255,7 +255,7 @@ tvs_status fgp_config_for(tvs_ctx* C, const Dims& d, int dtype, const float* z, 
       }
     }
   }
-  const int cands[][3] = {{4, 1, 105}, {4, 2, 105}, {4, 1, 5}, {4, 1, 108}};
+  const int cands[][3] = {{4, 1, 105}, {4, 2, 104}, {4, 2, 105}, {4, 1, 5}};
   const float betas[4] = {0.f, 0.f, 0.2f, 0.4f};
   cudaStream_t s = C->stream;
   cudaEvent_t e0, e1;
@@ -1098,6 +1098,7 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
     if (!x_io[i]) return fail(TVS_EINVAL, "x_inout[%d] is null", i);
     if (P->dims.ndim != 2 || P->desc.op.kind == TVS_OP_PARALLEL_BEAM)
       return fail(TVS_EUNSUPPORTED, "batched solves take 2D identity or blur problems (problem %d)", i);
+    if (P->n >= ((size_t)1 << 31)) return fail(TVS_EUNSUPPORTED, "batched problems have fewer than 2^31 pixels");
     TVS_TRY(check_common(P, prm[i].max_iter, prm[i].n_inner, prm[i].dual, prm[i].f_star,
                          prm[i].target_rel_gap, prm[i].objective_every, x_io[i]));
     if (prm[i].max_iter != K || prm[i].n_inner != N || prm[i].dual != dtype)
@@ -1120,7 +1121,7 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
   // per-problem state, descriptors and work lists
   std::vector<BatchProb> desc(n);
   std::vector<int4> blur_tiles, fgp_tiles;
-  std::vector<int2> ident_chunks, all_chunks;
+  std::vector<int2> ident_chunks, all_chunks, tile_range(n), chunk_range(n);
   const int chunk = batch_chunk(), ftw = batch_fgp_tile_w(), fth = batch_fgp_tile_h();
   for (int i = 0; i < n; ++i) {
     tvs_problem* P = probs[i];
@@ -1135,6 +1136,7 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
     memset(&D, 0, sizeof(D));
     D.H = H;
     D.W = W;
+    D.fw = FastDiv((uint32_t)W);
     D.nonneg = P->desc.nonneg != 0;
     D.b = P->b;
     D.x0 = P->x[0];
@@ -1163,7 +1165,7 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
     const int nchunks = (int)((npx + chunk - 1) / chunk);
     if (P->desc.op.kind == TVS_OP_GAUSS_BLUR) {
       D.part_off = (int)blur_tiles.size();
-      const int tx = (W + 31) / 32, ty = (H + 15) / 16;
+      const int tx = (W + 31) / 32, ty = (H + 31) / 32;  // tiles of the fused blur step
       for (int y = 0; y < ty; ++y)
         for (int x = 0; x < tx; ++x) blur_tiles.push_back(make_int4(i, x, y, 0));
       D.part_n = tx * ty;
@@ -1172,8 +1174,10 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
       for (int c = 0; c < nchunks; ++c) ident_chunks.push_back(make_int2(i, c));
       D.part_n = nchunks;
     }
+    chunk_range[i] = make_int2((int)all_chunks.size(), nchunks);
     for (int c = 0; c < nchunks; ++c) all_chunks.push_back(make_int2(i, c));
     const int fx = (W + ftw - 1) / ftw, fy = (H + fth - 1) / fth;
+    tile_range[i] = make_int2((int)fgp_tiles.size(), fx * fy);
     for (int y = 0; y < fy; ++y)
       for (int x = 0; x < fx; ++x) fgp_tiles.push_back(make_int4(i, x, y, 0));
   }
@@ -1194,10 +1198,22 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
   TVS_TRY(S.upload(fgp_tiles, (int4**)&L.fgp_tiles, s));
   TVS_TRY(S.upload(all_chunks, (int2**)&L.all_chunks, s));
   TVS_TRY(S.upload(coins, (unsigned char**)&L.coins, s));
+  TVS_TRY(S.upload(tile_range, (int2**)&L.tile_range, s));
+  TVS_TRY(S.upload(chunk_range, (int2**)&L.chunk_range, s));
+  TVS_TRY(S.zeros<int>((size_t)n + 1, &L.scan_tiles, s));
+  TVS_TRY(S.zeros<int>((size_t)n + 1, &L.scan_chunks, s));
   L.n_blur_tiles = n_blur;
   L.n_ident_chunks = (int)ident_chunks.size();
   L.n_fgp_tiles = (int)fgp_tiles.size();
   L.n_all_chunks = (int)all_chunks.size();
+  {
+    // persistent grids: every resident CTA slot of the inner kernel, and eight
+    // 256-thread CTAs per SM for the finalisation (never more than the work)
+    const int resident = batch_fgp_resident_ctas();
+    if (resident <= 0) return fail(TVS_ECUDA, "cannot size the batched inner kernel");
+    L.fgp_grid = std::max(1, std::min(resident, L.n_fgp_tiles));
+    L.fin_grid = std::max(1, std::min(pointwise_blocks((size_t)L.n_all_chunks * 256), L.n_all_chunks));
+  }
   TVS_TRY(S.zeros<int>(1, &L.kctr, s));
   TVS_TRY(S.zeros<Partial>((size_t)n_blur + ident_chunks.size(), &L.part_a, s));
   TVS_TRY(S.zeros<Partial>((size_t)n_blur + ident_chunks.size(), &L.part_b, s));

@@ -16,40 +16,34 @@ namespace tvs {
 
 namespace {
 
-constexpr int BT_TB = 4, BT_CPL = 1, BT_RPW = 5;  // blocked inner kernel of the batch
+constexpr int BT_TB = 4, BT_CPL = 2, BT_RPW = 4;  // blocked inner kernel of the batch
 constexpr int BT_TW = 32 * BT_CPL - 2 * BT_TB, BT_TH = 8 * BT_RPW - 2 * BT_TB;
 constexpr int CHUNK = 1024;                        // pixels per pointwise work item
 
 __device__ __forceinline__ bool active(const BatchState& st) { return st.done == 0; }
 
+// Blur data term, one fused forward-backward step per FX x FY tile:
+// out = x - gamma A(A x - b) + ch h (out = z on a prox iteration, the next x on a
+// skip), partials of 1/2 ||A x - b||^2 and TV(x).  write_out = 0: partials only
+// (the final objective; the coin is not read).
 template <int R>
-__global__ void __launch_bounds__(BNT)
-batch_blur_resid_kernel(const BatchProb* __restrict__ probs, BatchState* __restrict__ state,
-                        const int4* __restrict__ tiles, int par, Partial* part_a, Partial* part_b) {
+__global__ void __launch_bounds__(FNT)
+batch_blur_fb_kernel(const BatchProb* __restrict__ probs, BatchState* __restrict__ state,
+                     const int4* __restrict__ tiles, const unsigned char* __restrict__ coins, int n,
+                     const int* __restrict__ kctr, int par, int write_out, Partial* part_a, Partial* part_b) {
   pdl_enter();
   const int4 e = tiles[blockIdx.x];
   const BatchProb& P = probs[e.x];
   if (!active(state[e.x])) return;
-  blur_tile_body<BM_RESID, R>(par ? P.x1 : P.x0, P.H, P.W, P.bw, P.b, P.r, nullptr, nullptr, 0.f, 0.f,
-                           nullptr, nullptr, 0.f, part_a, part_b, e.y, e.z, blockIdx.x);
-}
-
-template <int R>
-__global__ void __launch_bounds__(BNT)
-batch_blur_step_kernel(const BatchProb* __restrict__ probs, BatchState* __restrict__ state,
-                       const int4* __restrict__ tiles, const unsigned char* __restrict__ coins, int n,
-                       const int* __restrict__ kctr, int par) {
-  pdl_enter();
-  const int4 e = tiles[blockIdx.x];
-  const BatchProb& P = probs[e.x];
-  if (!active(state[e.x])) return;
-  const int k = *kctr;
-  const bool coin = coins[(size_t)k * n + e.x] != 0;
   const float* xc = par ? P.x1 : P.x0;
-  float* out = coin ? P.z : (par ? P.x0 : P.x1);
-  blur_tile_body<BM_STEP, R>(P.r, P.H, P.W, P.bw, nullptr, out, xc, P.h, P.gamma,
-                          coin ? P.ch_prox : P.ch_skip, nullptr, nullptr, 0.f, nullptr, nullptr, e.y,
-                          e.z, 0);
+  float* out = nullptr;
+  float ch = 0.f;
+  if (write_out) {
+    const bool coin = coins[(size_t)(*kctr) * n + e.x] != 0;
+    out = coin ? P.z : (par ? P.x0 : P.x1);
+    ch = coin ? P.ch_prox : P.ch_skip;
+  }
+  blur_fb_step_body<R>(xc, P.b, P.h, out, P.H, P.W, P.bw, P.gamma, ch, part_a, part_b, e.y, e.z, blockIdx.x);
 }
 
 // Identity data term: out = x - gamma (x - b) + ch h; partials of 1/2 (x-b)^2, TV(x).
@@ -72,7 +66,7 @@ batch_ident_step_kernel(const BatchProb* __restrict__ probs, BatchState* __restr
   for (int t = threadIdx.x; t < CHUNK; t += 256) {
     const size_t o = (size_t)e.y * CHUNK + t;
     if (o >= npx) break;
-    const int gi = (int)(o / P.W), gj = (int)(o - (size_t)gi * P.W);
+    const int gi = (int)P.fw.div((uint32_t)o), gj = (int)o - gi * P.W;
     const float xc = __ldg(x + o), bb = __ldg(P.b + o);
     const float r = xc - bb;
     if (write_out) out[o] = fmaf(ch, __ldg(P.h + o), xc - P.gamma * r);
@@ -118,63 +112,158 @@ batch_reduce_kernel(const BatchProb* __restrict__ probs, BatchState* __restrict_
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256, 2)
-batch_fgp_kernel(const BatchProb* __restrict__ probs, BatchState* __restrict__ state,
-                 const int4* __restrict__ tiles, const unsigned char* __restrict__ coins, int n,
-                 const int* __restrict__ kctr, int q_in, TBBetas betas, int iters) {
+// Problem owning entry w of this iteration's compacted work list: the largest i
+// with scan[i] <= w (problems without work have scan[i] == scan[i + 1]).  The
+// persistent kernels search a shared-memory copy of the scan when it fits.
+constexpr int SCAN_SMEM = 2048;
+__device__ __forceinline__ const int* stage_scan(const int* __restrict__ scan, int n, int* s_scan) {
+  if (n + 1 > SCAN_SMEM) return scan;
+  for (int i = threadIdx.x; i <= n; i += blockDim.x) s_scan[i] = scan[i];
+  __syncthreads();
+  return s_scan;
+}
+__device__ __forceinline__ int owner_of(const int* scan, int n, int w) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (scan[mid] <= w) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Compacts the work of outer iteration k (one block): a problem takes part in the
+// prox of iteration k when it is still running and its coin is 1; its inner tiles
+// count only when lam > 0.  Writes exclusive scans of the tile and chunk counts.
+__global__ void __launch_bounds__(1024)
+batch_active_kernel(const BatchProb* __restrict__ probs, const BatchState* __restrict__ state,
+                    const unsigned char* __restrict__ coins, int n, const int* __restrict__ kctr,
+                    const int2* __restrict__ tile_range, const int2* __restrict__ chunk_range,
+                    int* __restrict__ scan_tiles, int* __restrict__ scan_chunks) {
   pdl_enter();
-  const int4 e = tiles[blockIdx.x];
-  const BatchProb& P = probs[e.x];
-  if (!active(state[e.x])) return;
-  if (coins[(size_t)(*kctr) * n + e.x] == 0 || P.lam == 0.f) return;
-  const T* pc = (const T*)(q_in ? P.dual2 : P.dual0);
-  const T* pp = (const T*)(q_in ? P.dual3 : P.dual1);
-  if (betas.b[0] == 0.f) pp = pc;  // first iteration of a prox call: p_{k-1} unused
-  T* pn = (T*)(q_in ? P.dual0 : P.dual2);
-  T* pnp = (T*)(q_in ? P.dual1 : P.dual3);
-  if (P.nonneg)
-    fgp2d_rb_body<T, true, BT_TB, BT_CPL, BT_RPW>(P.z, pc, pp, pn, pnp, P.H, P.W, P.lam, P.inv_step, betas,
-                                                  iters, e.y, e.z);
-  else
-    fgp2d_rb_body<T, false, BT_TB, BT_CPL, BT_RPW>(P.z, pc, pp, pn, pnp, P.H, P.W, P.lam, P.inv_step, betas,
-                                                   iters, e.y, e.z);
+  __shared__ int wt[32], wc[32];
+  const int k = *kctr, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int carry_t = 0, carry_c = 0;
+  for (int base = 0; base < n; base += 1024) {
+    const int i = base + threadIdx.x;
+    int ct = 0, cc = 0;
+    if (i < n && state[i].done == 0 && coins[(size_t)k * n + i] != 0) {
+      cc = chunk_range[i].y;
+      if (probs[i].lam != 0.f) ct = tile_range[i].y;
+    }
+    // inclusive warp scans, then the warp totals
+    int st = ct, sc = cc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int vt = __shfl_up_sync(0xffffffffu, st, o), vc = __shfl_up_sync(0xffffffffu, sc, o);
+      if (lane >= o) {
+        st += vt;
+        sc += vc;
+      }
+    }
+    if (lane == 31) {
+      wt[warp] = st;
+      wc[warp] = sc;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      int a = wt[lane], b = wc[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int va = __shfl_up_sync(0xffffffffu, a, o), vb = __shfl_up_sync(0xffffffffu, b, o);
+        if (lane >= o) {
+          a += va;
+          b += vb;
+        }
+      }
+      wt[lane] = a;  // inclusive over warps
+      wc[lane] = b;
+    }
+    __syncthreads();
+    const int off_t = carry_t + (warp > 0 ? wt[warp - 1] : 0) + st - ct;
+    const int off_c = carry_c + (warp > 0 ? wc[warp - 1] : 0) + sc - cc;
+    if (i < n) {
+      scan_tiles[i] = off_t;
+      scan_chunks[i] = off_c;
+    }
+    carry_t += wt[31];
+    carry_c += wc[31];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    scan_tiles[n] = carry_t;
+    scan_chunks[n] = carry_c;
+  }
+}
+
+// Persistent inner kernel: the grid strides over the compacted tiles of the
+// problems whose coin is 1 (no CTA is spent on skipping problems).
+template <typename T>
+__global__ void __launch_bounds__(256, 3)
+batch_fgp_kernel(const BatchProb* __restrict__ probs, const int4* __restrict__ tiles,
+                 const int2* __restrict__ tile_range, const int* __restrict__ scan, int n, int q_in,
+                 TBBetas betas, int iters) {
+  pdl_enter();
+  __shared__ int s_scan[SCAN_SMEM];
+  const int* sc = stage_scan(scan, n, s_scan);
+  const int total = sc[n];
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    const int i = owner_of(sc, n, w);
+    const BatchProb& P = probs[i];
+    const int t = w - sc[i], fx = (P.W + BT_TW - 1) / BT_TW;
+    const int ty = t / fx, tx = t - ty * fx;
+    const T* pc = (const T*)(q_in ? P.dual2 : P.dual0);
+    const T* pp = (const T*)(q_in ? P.dual3 : P.dual1);
+    if (betas.b[0] == 0.f) pp = pc;  // first iteration of a prox call: p_{k-1} unused
+    T* pn = (T*)(q_in ? P.dual0 : P.dual2);
+    T* pnp = (T*)(q_in ? P.dual1 : P.dual3);
+    if (P.nonneg)
+      fgp2d_rb_body<T, true, BT_TB, BT_CPL, BT_RPW>(P.z, pc, pp, pn, pnp, P.H, P.W, P.lam, P.inv_step, betas,
+                                                    iters, tx, ty);
+    else
+      fgp2d_rb_body<T, false, BT_TB, BT_CPL, BT_RPW>(P.z, pc, pp, pn, pnp, P.H, P.W, P.lam, P.inv_step, betas,
+                                                     iters, tx, ty);
+  }
 }
 
 // x_{k+1} = P_X(z + lam div p_N); h = (p/gamma)(x_{k+1} - z); p_N copied home if
 // it sits in the second pair.
 template <typename T>
 __global__ void __launch_bounds__(256)
-batch_finalize_kernel(const BatchProb* __restrict__ probs, BatchState* __restrict__ state,
-                      const int2* __restrict__ chunks, const unsigned char* __restrict__ coins, int n,
-                      const int* __restrict__ kctr, int par, int fin_pair) {
+batch_finalize_kernel(const BatchProb* __restrict__ probs, const int2* __restrict__ chunks,
+                      const int2* __restrict__ chunk_range, const int* __restrict__ scan, int n, int par,
+                      int fin_pair) {
   pdl_enter();
-  const int2 e = chunks[blockIdx.x];
-  const BatchProb& P = probs[e.x];
-  if (!active(state[e.x])) return;
-  if (coins[(size_t)(*kctr) * n + e.x] == 0) return;
-  const T* p = (const T*)(fin_pair ? P.dual2 : P.dual0);
-  T* home = (fin_pair && P.lam != 0.f) ? (T*)P.dual0 : nullptr;
-  float* xo = par ? P.x0 : P.x1;
-  const int H = P.H, W = P.W;
-  const size_t npx = (size_t)H * W;
-  for (int t = threadIdx.x; t < CHUNK; t += 256) {
-    const size_t o = (size_t)e.y * CHUNK + t;
-    if (o >= npx) break;
-    const int gi = (int)(o / W), gj = (int)(o - (size_t)gi * W);
-    float dv = 0.f;
-    if (gi < H - 1) dv += Elem<T>::ld(p + o);
-    if (gi > 0) dv -= Elem<T>::ld(p + o - W);
-    if (gj < W - 1) dv += Elem<T>::ld(p + npx + o);
-    if (gj > 0) dv -= Elem<T>::ld(p + npx + o - 1);
-    const float zz = __ldg(P.z + o);
-    float u = P.lam != 0.f ? zz + P.lam * dv : zz;
-    if (P.nonneg) u = fmaxf(u, 0.f);
-    xo[o] = u;
-    P.h[o] = P.h_coef * (u - zz);
-    if (home) {
-      home[o] = p[o];
-      home[npx + o] = p[npx + o];
+  __shared__ int s_scan[SCAN_SMEM];
+  const int* sc = stage_scan(scan, n, s_scan);
+  const int total = sc[n];
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    const int i = owner_of(sc, n, w);
+    const int2 e = make_int2(i, w - sc[i]);
+    const BatchProb& P = probs[i];
+    const T* p = (const T*)(fin_pair ? P.dual2 : P.dual0);
+    T* home = (fin_pair && P.lam != 0.f) ? (T*)P.dual0 : nullptr;
+    float* xo = par ? P.x0 : P.x1;
+    const int H = P.H, W = P.W;
+    const size_t npx = (size_t)H * W;
+    for (int t = threadIdx.x; t < CHUNK; t += 256) {
+      const size_t o = (size_t)e.y * CHUNK + t;
+      if (o >= npx) break;
+      const int gi = (int)P.fw.div((uint32_t)o), gj = (int)o - gi * W;
+      float dv = 0.f;
+      if (gi < H - 1) dv += Elem<T>::ld(p + o);
+      if (gi > 0) dv -= Elem<T>::ld(p + o - W);
+      if (gj < W - 1) dv += Elem<T>::ld(p + npx + o);
+      if (gj > 0) dv -= Elem<T>::ld(p + npx + o - 1);
+      const float zz = __ldg(P.z + o);
+      float u = P.lam != 0.f ? zz + P.lam * dv : zz;
+      if (P.nonneg) u = fmaxf(u, 0.f);
+      xo[o] = u;
+      P.h[o] = P.h_coef * (u - zz);
+      if (home) {
+        home[o] = p[o];
+        home[npx + o] = p[npx + o];
+      }
     }
   }
 }
@@ -188,17 +277,22 @@ int batch_fgp_tile_w() { return BT_TW; }
 int batch_fgp_tile_h() { return BT_TH; }
 int batch_chunk() { return CHUNK; }
 int batch_fgp_iters_per_launch() { return BT_TB; }
+int batch_fgp_resident_ctas() {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_fgp_kernel<float>, 256, 0) != cudaSuccess)
+    return 0;
+  return sms * (per_sm > 0 ? per_sm : 1);
+}
 
 namespace {
 cudaError_t batch_blur(const BatchLaunch& L, int par, bool step, cudaStream_t s) {
   switch (L.blur_radius) {
 #define TVS_BB_R(R_)                                                                                   \
   case R_:                                                                                             \
-    launch_kernel(batch_blur_resid_kernel<R_>, dim3(L.n_blur_tiles), dim3(BNT), 0, s, L.probs, L.state, L.blur_tiles, par,   \
-                                                              L.part_a, L.part_b);                     \
-    if (step)                                                                                          \
-      launch_kernel(batch_blur_step_kernel<R_>, dim3(L.n_blur_tiles), dim3(BNT), 0, s, L.probs, L.state, L.blur_tiles,        \
-                                                                L.coins, L.n, L.kctr, par);            \
+    launch_kernel(batch_blur_fb_kernel<R_>, dim3(L.n_blur_tiles), dim3(FNT), 0, s, L.probs, L.state,   \
+                  L.blur_tiles, L.coins, L.n, (const int*)L.kctr, par, step ? 1 : 0, L.part_a, L.part_b); \
     break;
     TVS_BB_R(1) TVS_BB_R(2) TVS_BB_R(3) TVS_BB_R(4) TVS_BB_R(5) TVS_BB_R(6) TVS_BB_R(7) TVS_BB_R(8)
 #undef TVS_BB_R
@@ -219,6 +313,9 @@ cudaError_t launch_batch_iteration(const BatchLaunch& L, int par, cudaStream_t s
                                                              L.kctr, par, 1, L.part_a, L.part_b,
                                                              L.n_blur_tiles);
   launch_kernel(batch_reduce_kernel, dim3(L.n), dim3(256), 0, s, L.probs, L.state, L.kctr, L.part_a, L.part_b, 0, L.done_host);
+  launch_kernel(batch_active_kernel, dim3(1), dim3(1024), 0, s, L.probs, (const BatchState*)L.state, L.coins, L.n,
+                (const int*)L.kctr, L.tile_range, L.chunk_range, L.scan_tiles, L.scan_chunks);
+  int fin_pair = 0;  // pair holding p_N
   if (L.n_inner > 0 && L.use_prox) {
     int q = 0;
     for (int g = 1; g <= L.n_inner;) {
@@ -227,50 +324,36 @@ cudaError_t launch_batch_iteration(const BatchLaunch& L, int par, cudaStream_t s
       for (int j = 0; j < it; ++j) b.b[j] = L.betas[g - 1 + j];
       switch (L.dtype) {
         case DUAL_F32:
-          launch_kernel(batch_fgp_kernel<float>, dim3(L.n_fgp_tiles), dim3(256), 0, s, L.probs, L.state, L.fgp_tiles, L.coins, L.n,
-                                                                L.kctr, q, b, it);
+          launch_kernel(batch_fgp_kernel<float>, dim3(L.fgp_grid), dim3(256), 0, s, L.probs, L.fgp_tiles,
+                        L.tile_range, (const int*)L.scan_tiles, L.n, q, b, it);
           break;
         case DUAL_BF16:
-          launch_kernel(batch_fgp_kernel<__nv_bfloat16>, dim3(L.n_fgp_tiles), dim3(256), 0, s, L.probs, L.state, L.fgp_tiles, L.coins,
-                                                                        L.n, L.kctr, q, b, it);
+          launch_kernel(batch_fgp_kernel<__nv_bfloat16>, dim3(L.fgp_grid), dim3(256), 0, s, L.probs, L.fgp_tiles,
+                        L.tile_range, (const int*)L.scan_tiles, L.n, q, b, it);
           break;
         default:
-          launch_kernel(batch_fgp_kernel<__half>, dim3(L.n_fgp_tiles), dim3(256), 0, s, L.probs, L.state, L.fgp_tiles, L.coins, L.n,
-                                                                 L.kctr, q, b, it);
+          launch_kernel(batch_fgp_kernel<__half>, dim3(L.fgp_grid), dim3(256), 0, s, L.probs, L.fgp_tiles,
+                        L.tile_range, (const int*)L.scan_tiles, L.n, q, b, it);
       }
       q = 1 - q;
       g += it;
     }
-    const int fin_pair = q;  // pair holding p_N
-    switch (L.dtype) {
-      case DUAL_F32:
-        launch_kernel(batch_finalize_kernel<float>, dim3(L.n_all_chunks), dim3(256), 0, s, L.probs, L.state, L.all_chunks, L.coins,
-                                                                    L.n, L.kctr, par, fin_pair);
-        break;
-      case DUAL_BF16:
-        launch_kernel(batch_finalize_kernel<__nv_bfloat16>, dim3(L.n_all_chunks), dim3(256), 0, s, L.probs, L.state, L.all_chunks,
-                                                                            L.coins, L.n, L.kctr, par, fin_pair);
-        break;
-      default:
-        launch_kernel(batch_finalize_kernel<__half>, dim3(L.n_all_chunks), dim3(256), 0, s, L.probs, L.state, L.all_chunks, L.coins,
-                                                                     L.n, L.kctr, par, fin_pair);
-    }
-  } else {
-    // no prox work: finalisation reduces to x_{k+1} = z and h = (p/gamma)(z - z) = 0
-    // when alpha = 0; handled by the same kernel with lam = 0 through the descriptors
-    switch (L.dtype) {
-      case DUAL_F32:
-        launch_kernel(batch_finalize_kernel<float>, dim3(L.n_all_chunks), dim3(256), 0, s, L.probs, L.state, L.all_chunks, L.coins,
-                                                                    L.n, L.kctr, par, 0);
-        break;
-      case DUAL_BF16:
-        launch_kernel(batch_finalize_kernel<__nv_bfloat16>, dim3(L.n_all_chunks), dim3(256), 0, s, L.probs, L.state, L.all_chunks,
-                                                                            L.coins, L.n, L.kctr, par, 0);
-        break;
-      default:
-        launch_kernel(batch_finalize_kernel<__half>, dim3(L.n_all_chunks), dim3(256), 0, s, L.probs, L.state, L.all_chunks, L.coins,
-                                                                     L.n, L.kctr, par, 0);
-    }
+    fin_pair = q;
+  }
+  // with no inner iterations the finalisation gives x_{k+1} = z and h = 0 (lam = 0
+  // in every descriptor)
+  switch (L.dtype) {
+    case DUAL_F32:
+      launch_kernel(batch_finalize_kernel<float>, dim3(L.fin_grid), dim3(256), 0, s, L.probs, L.all_chunks,
+                    L.chunk_range, (const int*)L.scan_chunks, L.n, par, fin_pair);
+      break;
+    case DUAL_BF16:
+      launch_kernel(batch_finalize_kernel<__nv_bfloat16>, dim3(L.fin_grid), dim3(256), 0, s, L.probs,
+                    L.all_chunks, L.chunk_range, (const int*)L.scan_chunks, L.n, par, fin_pair);
+      break;
+    default:
+      launch_kernel(batch_finalize_kernel<__half>, dim3(L.fin_grid), dim3(256), 0, s, L.probs, L.all_chunks,
+                    L.chunk_range, (const int*)L.scan_chunks, L.n, par, fin_pair);
   }
   launch_kernel(batch_tick_kernel, dim3(1), dim3(1), 0, s, L.kctr);
   return cudaGetLastError();

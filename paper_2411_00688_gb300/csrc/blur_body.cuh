@@ -98,7 +98,8 @@ __device__ __forceinline__ void blur_tile_body(const float* __restrict__ src, in
     block_sum2_store<BNT>(acc_a, acc_b, part_a, part_b, part_index);
 }
 
-// Fused forward-backward step for the blur operator (A = A^T):
+// Fused forward-backward step for the blur operator (A = A^T) (out may be null:
+// partials only):
 //   r = A x - b on the FX x FY tile plus an R-cell ring, the ring cells outside the
 //   image copied from their mirror cells (the reflective A reads r there), then
 //   out = x - gamma A r + ch h on the tile, with the partials of 1/2 ||r||^2 and
@@ -227,9 +228,11 @@ __device__ __forceinline__ void blur_fb_step_body(const float* __restrict__ x, c
       for (int k = 0; k <= 2 * R; ++k) v = fmaf(wk[k], win[t + k], v);
       const size_t o = (size_t)gi * W + gj;
       const float xc = sx[a + 2 * R][lane + 2 * R];
-      float o_v = xc - gamma * v;
-      if (h) o_v = fmaf(ch, __ldg(h + o), o_v);
-      out[o] = o_v;
+      if (out) {
+        float o_v = xc - gamma * v;
+        if (h) o_v = fmaf(ch, __ldg(h + o), o_v);
+        out[o] = o_v;
+      }
       const float dy = gi < H - 1 ? sx[a + 2 * R + 1][lane + 2 * R] - xc : 0.f;
       const float dx = gj < W - 1 ? sx[a + 2 * R][lane + 2 * R + 1] - xc : 0.f;
       acc_b.add(tv_term(0.f, dy, dx));

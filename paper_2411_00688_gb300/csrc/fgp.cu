@@ -317,7 +317,7 @@ fgp2d_tb_kernel(const float* __restrict__ z, const T* __restrict__ pc, const T* 
 }
 
 template <typename T, bool NONNEG, int TB, int CPL, int RPW>
-__global__ void __launch_bounds__(256, (RPW * CPL > 10) ? 1 : 2)
+__global__ void __launch_bounds__(256, (RPW * CPL > 10) ? 1 : (CPL == 2 ? 3 : 2))
 fgp2d_rb_kernel(const float* __restrict__ z, const T* __restrict__ pc, const T* __restrict__ pp,
                 T* __restrict__ pn, T* __restrict__ pnp, int H, int W, float lam, float inv_step,
                 TBBetas betas, int iters) {
@@ -710,6 +710,8 @@ cudaError_t fgp_tb_dispatch(const FgpConfig& c, const Dims& d, const float* z, c
   TVS_RB_CASE(4, 1, 8)
   TVS_RB_CASE(6, 2, 8)
   TVS_RB_CASE(3, 2, 6)
+  TVS_RB_CASE(4, 2, 4)
+  TVS_RB_CASE(4, 1, 6)
 #undef TVS_RB_CASE
   return cudaErrorInvalidValue;
 }
@@ -775,7 +777,7 @@ bool fgp_config_valid(const FgpConfig& c) {
   if (c.tb <= 1) return true;
   const int ok[][3] = {{2, 2, 4},   {3, 2, 4},   {4, 2, 4},   {4, 2, 5},   {4, 1, 5},   {6, 2, 6},
                        {8, 2, 6},   {2, 2, 104}, {4, 1, 105}, {4, 2, 105}, {4, 2, 108}, {4, 1, 108},
-                       {6, 2, 108}, {3, 2, 106}};
+                       {6, 2, 108}, {3, 2, 106}, {4, 2, 104}, {4, 1, 106}};
   for (const auto& k : ok)
     if (k[0] == c.tb && k[1] == c.cpl && k[2] == c.rpw) return true;
   return false;

@@ -129,7 +129,7 @@ __device__ __forceinline__ void fgp2d_rb_body_impl(const float* __restrict__ z, 
         const float gx = col_rt[q] ? rt - uc : 0.f;
         const float qy = Ry[r][q] + inv_step * gy;
         const float qx = Rx[r][q] + inv_step * gx;
-        const float nrm2 = qy * qy + qx * qx;
+        const float nrm2 = __fmaf_rn(qy, qy, __fmul_rn(qx, qx));
         const float sc = fminf(1.f, rsqrtf(nrm2));  // 1 / max(1, |q|): rsqrt(n2) < 1 iff n2 > 1
         const float ny = Elem<T>::round(qy * sc), nx = Elem<T>::round(qx * sc);
         const float oy = Py[r][q], ox = Px[r][q];
@@ -168,6 +168,164 @@ __device__ __forceinline__ void fgp2d_rb_body_impl(const float* __restrict__ z, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// The two-columns-per-lane layout with packed FP32x2 arithmetic (Blackwell's
+// paired FMA/ADD/MUL): a lane's two cells of a row form one float2 (left column
+// in .x), so each step of the iteration above is one paired instruction instead
+// of two.  The per-value arithmetic is unchanged (a - b is formed as
+// fma(b, -1, a), which rounds exactly like the subtraction; a masked-out term is
+// added as zero instead of skipped, which changes no value), so it agrees bitwise
+// with the scalar body.  INTERIOR drops the Neumann masks as above.
+__device__ __forceinline__ float2 p2_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 p2_mask(float2 v, bool mx, bool my) {
+  return make_float2(mx ? v.x : 0.f, my ? v.y : 0.f);
+}
+
+template <typename T, bool NONNEG, int TB, int RPW, bool INTERIOR>
+__device__ __forceinline__ void fgp2d_rb_body_packed(const float* __restrict__ z, const T* __restrict__ pc,
+                                                     const T* __restrict__ pp, T* __restrict__ pn,
+                                                     T* __restrict__ pnp, int H, int W, float lam,
+                                                     float inv_step, const TBBetas& betas, int iters,
+                                                     int tile_x, int tile_y) {
+  constexpr int NW = 8, CPL = 2;
+  constexpr int RW = 32 * CPL, RH = NW * RPW;
+  constexpr int TW = RW - 2 * TB, TH = RH - 2 * TB;
+  __shared__ float2 edge_ry2[NW][32];
+  __shared__ float2 edge_u2[NW][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gi0 = tile_y * TH - TB + warp * RPW;
+  const int gj0 = tile_x * TW - TB + lane * CPL;
+  const size_t n = (size_t)H * W;
+  float2 Z[RPW], Ry[RPW], Rx[RPW], Py[RPW], Px[RPW], U[RPW];
+  bool row_in[RPW], row_dn[RPW], row_up[RPW];
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) {
+    const int gi = gi0 + r;
+    row_in[r] = INTERIOR || (gi >= 0 && gi < H);
+    row_dn[r] = INTERIOR || gi < H - 1;
+    row_up[r] = INTERIOR || gi > 0;
+  }
+  // column masks of the lane's left (.x) and right (.y) cell
+  const bool in0 = INTERIOR || (gj0 >= 0 && gj0 < W), in1 = INTERIOR || (gj0 + 1 >= 0 && gj0 + 1 < W);
+  const bool rt0 = INTERIOR || gj0 < W - 1, rt1 = INTERIOR || gj0 + 1 < W - 1;
+  const bool lf0 = INTERIOR || gj0 > 0, lf1 = INTERIOR || gj0 + 1 > 0;
+  const float b0 = betas.b[0];
+  const float2 bb = make_float2(b0, b0);
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) {
+    float2 zz = make_float2(0.f, 0.f), cy = zz, cx = zz, qy = zz, qx = zz;
+    const size_t o = (size_t)(gi0 + r) * W + gj0;
+    if (row_in[r]) {
+      if (in0) {
+        zz.x = __ldg(z + o);
+        cy.x = Elem<T>::ld(pc + o);
+        cx.x = Elem<T>::ld(pc + n + o);
+        if (b0 != 0.f) {
+          qy.x = Elem<T>::ld(pp + o);
+          qx.x = Elem<T>::ld(pp + n + o);
+        }
+      }
+      if (in1) {
+        zz.y = __ldg(z + o + 1);
+        cy.y = Elem<T>::ld(pc + o + 1);
+        cx.y = Elem<T>::ld(pc + n + o + 1);
+        if (b0 != 0.f) {
+          qy.y = Elem<T>::ld(pp + o + 1);
+          qx.y = Elem<T>::ld(pp + n + o + 1);
+        }
+      }
+    }
+    Z[r] = zz;
+    Py[r] = cy;
+    Px[r] = cx;
+    if (b0 != 0.f) {
+      Ry[r] = __ffma2_rn(bb, p2_sub(cy, qy), cy);
+      Rx[r] = __ffma2_rn(bb, p2_sub(cx, qx), cx);
+    } else {
+      Ry[r] = cy;
+      Rx[r] = cx;
+    }
+  }
+  edge_ry2[warp][lane] = Ry[RPW - 1];
+  __syncthreads();
+  const float2 lam2 = make_float2(lam, lam), inv2 = make_float2(inv_step, inv_step);
+  for (int t = 1; t <= iters; ++t) {
+    // phase 1: U = P_X(Z + lam div R), div R = Ry - Ry(above) + Rx - Rx(left)
+    const float2 ry_above = warp > 0 ? edge_ry2[warp - 1][lane] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+      const float rx_left = __shfl_up_sync(0xffffffffu, Rx[r].y, 1);
+      const float2 up = r > 0 ? Ry[r - 1] : ry_above;
+      const float2 lf = make_float2(rx_left, Rx[r].x);
+      float2 dv;
+      if (INTERIOR) {
+        dv = p2_sub(Ry[r], up);
+        dv = __fadd2_rn(dv, Rx[r]);
+        dv = p2_sub(dv, lf);
+      } else {
+        dv = p2_sub(p2_mask(Ry[r], row_dn[r], row_dn[r]), p2_mask(up, row_up[r], row_up[r]));
+        dv = __fadd2_rn(dv, p2_mask(Rx[r], rt0, rt1));
+        dv = p2_sub(dv, p2_mask(lf, lf0, lf1));
+      }
+      float2 u = __ffma2_rn(lam2, dv, Z[r]);
+      if (NONNEG) u = make_float2(fmaxf(u.x, 0.f), fmaxf(u.y, 0.f));
+      U[r] = INTERIOR ? u : p2_mask(u, row_in[r] && in0, row_in[r] && in1);
+    }
+    edge_u2[warp][lane] = U[0];
+    __syncthreads();
+    // phase 2: p_new = P_B(R + inv_step D U); R = next momentum point (or p_prev); P = p_new
+    const bool last = (t == iters);
+    const float bn = last ? 0.f : betas.b[t];
+    const float2 bn2 = make_float2(bn, bn);
+    const float2 u_below = warp < NW - 1 ? edge_u2[warp + 1][lane] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+      const float u_right = __shfl_down_sync(0xffffffffu, U[r].x, 1);
+      const float2 uc = U[r];
+      const float2 dn = r < RPW - 1 ? U[r + 1] : u_below;
+      const float2 rt = make_float2(uc.y, u_right);
+      float2 gy = p2_sub(dn, uc), gx = p2_sub(rt, uc);
+      if (!INTERIOR) {
+        gy = p2_mask(gy, row_dn[r], row_dn[r]);
+        gx = p2_mask(gx, rt0, rt1);
+      }
+      const float2 qy = __ffma2_rn(inv2, gy, Ry[r]);
+      const float2 qx = __ffma2_rn(inv2, gx, Rx[r]);
+      const float2 nrm2 = __ffma2_rn(qy, qy, __fmul2_rn(qx, qx));
+      const float2 sc = make_float2(fminf(1.f, rsqrtf(nrm2.x)), fminf(1.f, rsqrtf(nrm2.y)));
+      float2 ny = __fmul2_rn(qy, sc), nx = __fmul2_rn(qx, sc);
+      ny = make_float2(Elem<T>::round(ny.x), Elem<T>::round(ny.y));
+      nx = make_float2(Elem<T>::round(nx.x), Elem<T>::round(nx.y));
+      if (last) {
+        Ry[r] = Py[r];
+        Rx[r] = Px[r];
+      } else {
+        Ry[r] = __ffma2_rn(bn2, p2_sub(ny, Py[r]), ny);
+        Rx[r] = __ffma2_rn(bn2, p2_sub(nx, Px[r]), nx);
+      }
+      Py[r] = ny;
+      Px[r] = nx;
+    }
+    if (!last) edge_ry2[warp][lane] = Ry[RPW - 1];
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) {
+    const int a = warp * RPW + r;
+    if (a < TB || a >= TB + TH || !row_in[r]) continue;
+    const size_t o = (size_t)(gi0 + r) * W + gj0;
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+      const int c = lane * CPL + q;
+      if (c < TB || c >= TB + TW || !(q ? in1 : in0)) continue;
+      Elem<T>::st(pn + o + q, q ? Py[r].y : Py[r].x);
+      Elem<T>::st(pn + n + o + q, q ? Px[r].y : Px[r].x);
+      Elem<T>::st(pnp + o + q, q ? Ry[r].y : Ry[r].x);
+      Elem<T>::st(pnp + n + o + q, q ? Rx[r].y : Rx[r].x);
+    }
+  }
+}
+
 template <typename T, bool NONNEG, int TB, int CPL, int RPW>
 __device__ __forceinline__ void fgp2d_rb_body(const float* __restrict__ z, const T* __restrict__ pc,
                                               const T* __restrict__ pp, T* __restrict__ pn,
@@ -177,12 +335,21 @@ __device__ __forceinline__ void fgp2d_rb_body(const float* __restrict__ z, const
   constexpr int RW = 32 * CPL, RH = 8 * RPW, TW = RW - 2 * TB, TH = RH - 2 * TB;
   const int r0 = tile_y * TH - TB, c0 = tile_x * TW - TB;
   const bool interior = r0 >= 1 && r0 + RH <= H - 1 && c0 >= 1 && c0 + RW <= W - 1;
-  if (interior)
-    fgp2d_rb_body_impl<T, NONNEG, TB, CPL, RPW, true>(z, pc, pp, pn, pnp, H, W, lam, inv_step, betas, iters,
+  if constexpr (CPL == 2) {
+    if (interior)
+      fgp2d_rb_body_packed<T, NONNEG, TB, RPW, true>(z, pc, pp, pn, pnp, H, W, lam, inv_step, betas, iters,
+                                                     tile_x, tile_y);
+    else
+      fgp2d_rb_body_packed<T, NONNEG, TB, RPW, false>(z, pc, pp, pn, pnp, H, W, lam, inv_step, betas, iters,
                                                       tile_x, tile_y);
-  else
-    fgp2d_rb_body_impl<T, NONNEG, TB, CPL, RPW, false>(z, pc, pp, pn, pnp, H, W, lam, inv_step, betas, iters,
-                                                       tile_x, tile_y);
+  } else {
+    if (interior)
+      fgp2d_rb_body_impl<T, NONNEG, TB, CPL, RPW, true>(z, pc, pp, pn, pnp, H, W, lam, inv_step, betas, iters,
+                                                        tile_x, tile_y);
+    else
+      fgp2d_rb_body_impl<T, NONNEG, TB, CPL, RPW, false>(z, pc, pp, pn, pnp, H, W, lam, inv_step, betas, iters,
+                                                         tile_x, tile_y);
+  }
 }
 
 }  // namespace tvs

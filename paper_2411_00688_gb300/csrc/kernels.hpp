@@ -197,6 +197,7 @@ cudaError_t launch_dual_rof_primal(int H, int W, const float* q, const float* b,
 // objective occupy part_a/part_b[part_off, part_off + part_n).
 struct BatchProb {
   int H, W, nonneg, pad;
+  FastDiv fw;  // division by W (every batched problem has fewer than 2^31 pixels)
   const float* b;
   float *x0, *x1, *z, *h, *r;
   void *dual0, *dual1, *dual2, *dual3;
@@ -214,7 +215,7 @@ struct BatchLaunch {
   const BatchProb* probs;
   BatchState* state;
   int n;
-  const int4* blur_tiles;   // (problem, tile x, tile y) of the blur problems (32 x 16 tiles)
+  const int4* blur_tiles;   // (problem, tile x, tile y) of the blur problems (32 x 32 tiles)
   int n_blur_tiles;
   const int2* ident_chunks; // (problem, chunk) of the identity problems
   int n_ident_chunks;
@@ -230,11 +231,18 @@ struct BatchLaunch {
   int blur_radius;             // shared by every blur problem of the batch
   bool use_prox;
   const float* betas;          // host: momentum coefficient of each inner iteration
+  // per-problem ranges of fgp_tiles / all_chunks (each problem's entries are contiguous)
+  const int2* tile_range;      // (first, count)
+  const int2* chunk_range;     // (first, count)
+  int* scan_tiles;             // [n + 1]: exclusive scan of the tiles of this iteration's active problems
+  int* scan_chunks;            // [n + 1]: the same for their chunks
+  int fgp_grid, fin_grid;      // persistent grid sizes of the inner and finalisation kernels
 };
 int batch_fgp_tile_w();
 int batch_fgp_tile_h();
 int batch_chunk();
 int batch_fgp_iters_per_launch();
+int batch_fgp_resident_ctas();  // SMs x resident CTAs of the batched inner kernel (0 on error)
 // One outer iteration of every problem (graph-capturable; reads k from kctr).
 cudaError_t launch_batch_iteration(const BatchLaunch& L, int par, cudaStream_t s);
 // F(x_k) of the problems still running, recorded as their final trace entry.

@@ -177,7 +177,7 @@ def denoise3d_512(duals=("f32", "bf16", "f16")):
     return out
 
 
-def _batch(n_problems=None, K=None):
+def _batch(n_problems=None, K=None, batch_only=False):
     import torch
     from synth.configs import BatchConfig
     tvs, ctx = _ctx()
@@ -215,6 +215,9 @@ def _batch(n_problems=None, K=None):
 
     batched()
     _, t_batch = _timed(batched)
+    if batch_only:
+        return [{"workload": cfg.name, "problems": len(specs), "pixels": npx, "iterations": K,
+                 "n_inner": cfg.n_inner, "batched_s": t_batch}]
     loop()
     _, t_loop = _timed(loop)
     return [{"workload": cfg.name, "problems": len(specs), "pixels": npx, "iterations": K,
@@ -227,9 +230,10 @@ def main(argv=None):
                                          "deblur2d_1024"])
     ap.add_argument("--problems", type=int, default=None)
     ap.add_argument("--iters", type=int, default=None)
+    ap.add_argument("--batch-only", action="store_true", help="batch2d_256: time the batched solve only")
     args = ap.parse_args(argv)
     if args.workload == "batch2d_256":
-        recs = _batch(args.problems, args.iters)
+        recs = _batch(args.problems, args.iters, args.batch_only)
     else:
         recs = {"denoise2d_256": denoise2d_256, "ct2d_512": ct2d_512, "denoise3d_512": denoise3d_512,
                 "deblur2d_1024": deblur2d_1024}[args.workload]()

@@ -90,13 +90,22 @@ def test_proxskip_nonneg_and_host_memory(tvs, ctx):
     _check(tr, ref, x.astype(np.float64))
 
 
+def _psnr(u, truth):
+    """10 log10(max(u_true)^2 / MSE) against the ground-truth phantom."""
+    return 10.0 * math.log10(float(truth.max()) ** 2 / float(np.mean((u - truth) ** 2)))
+
+
 @pytest.mark.parametrize("dual", ["bf16", "f16"])
 def test_proxskip_half_dual(tvs, ctx, dual):
+    """BF16/FP16 dual storage: final iterate within 2e-3 relative l2 of the FP64
+    oracle and its PSNR against the phantom within 0.05 dB of the oracle's."""
     b32, b64 = _data((96, 96), "blur", 31, 0.02)
+    truth = phantoms.shapes_phantom_2d(96, 96, 6, 31)
     prob = tvs.Problem(ctx, cuda(b32), 0.03, op="blur", blur_sigma=2.0)
     x, tr = tvs.proxskip_solve(prob, cuda(b32), 1.0, 0.3, 2, 25, 20, dual=dual)
     ref = solvers.proxskip(solvers.Problem(operators.blur_op(2.0), b64, 0.03, (96, 96)), b64, 1.0, 0.3, 2, 25, 20)
     assert rel_l2(host(x), ref["x"]) <= TOL_X_HALF
+    assert abs(_psnr(host(x), truth) - _psnr(ref["x"], truth)) <= 0.05
 
 
 def test_proxskip_p1_equals_pgd_on_gpu(tvs, ctx):
