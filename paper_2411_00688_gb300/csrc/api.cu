@@ -1207,6 +1207,11 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
   L.n_fgp_tiles = (int)fgp_tiles.size();
   L.n_all_chunks = (int)all_chunks.size();
   {
+    int nn = 0;
+    for (int i = 0; i < n; ++i) nn += probs[i]->desc.nonneg != 0;
+    L.nonneg_mode = nn == 0 ? 0 : (nn == n ? 1 : 2);
+  }
+  {
     // persistent grids: every resident CTA slot of the inner kernel, and eight
     // 256-thread CTAs per SM for the finalisation (never more than the work)
     const int resident = batch_fgp_resident_ctas();

@@ -197,9 +197,14 @@ batch_active_kernel(const BatchProb* __restrict__ probs, const BatchState* __res
 }
 
 // Persistent inner kernel: the grid strides over the compacted tiles of the
-// problems whose coin is 1 (no CTA is spent on skipping problems).
-template <typename T>
-__global__ void __launch_bounds__(256, 3)
+// problems whose coin is 1 (no CTA is spent on skipping problems).  NN: 0 when
+// no problem of the batch has the non-negativity constraint, 1 when all have it,
+// 2 for a mix (both bodies compiled in).
+#ifndef TVS_BATCH_FGP_MIN_CTAS
+#define TVS_BATCH_FGP_MIN_CTAS 3
+#endif
+template <typename T, int NN>
+__global__ void __launch_bounds__(256, TVS_BATCH_FGP_MIN_CTAS)
 batch_fgp_kernel(const BatchProb* __restrict__ probs, const int4* __restrict__ tiles,
                  const int2* __restrict__ tile_range, const int* __restrict__ scan, int n, int q_in,
                  TBBetas betas, int iters) {
@@ -217,7 +222,7 @@ batch_fgp_kernel(const BatchProb* __restrict__ probs, const int4* __restrict__ t
     if (betas.b[0] == 0.f) pp = pc;  // first iteration of a prox call: p_{k-1} unused
     T* pn = (T*)(q_in ? P.dual0 : P.dual2);
     T* pnp = (T*)(q_in ? P.dual1 : P.dual3);
-    if (P.nonneg)
+    if (NN == 1 || (NN == 2 && P.nonneg))
       fgp2d_rb_body<T, true, BT_TB, BT_CPL, BT_RPW>(P.z, pc, pp, pn, pnp, P.H, P.W, P.lam, P.inv_step, betas,
                                                     iters, tx, ty);
     else
@@ -281,7 +286,7 @@ int batch_fgp_resident_ctas() {
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_fgp_kernel<float>, 256, 0) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_fgp_kernel<float, 2>, 256, 0) != cudaSuccess)
     return 0;
   return sms * (per_sm > 0 ? per_sm : 1);
 }
@@ -322,18 +327,16 @@ cudaError_t launch_batch_iteration(const BatchLaunch& L, int par, cudaStream_t s
       const int it = L.n_inner - g + 1 < BT_TB ? L.n_inner - g + 1 : BT_TB;
       TBBetas b{};
       for (int j = 0; j < it; ++j) b.b[j] = L.betas[g - 1 + j];
-      switch (L.dtype) {
-        case DUAL_F32:
-          launch_kernel(batch_fgp_kernel<float>, dim3(L.fgp_grid), dim3(256), 0, s, L.probs, L.fgp_tiles,
-                        L.tile_range, (const int*)L.scan_tiles, L.n, q, b, it);
-          break;
-        case DUAL_BF16:
-          launch_kernel(batch_fgp_kernel<__nv_bfloat16>, dim3(L.fgp_grid), dim3(256), 0, s, L.probs, L.fgp_tiles,
-                        L.tile_range, (const int*)L.scan_tiles, L.n, q, b, it);
-          break;
-        default:
-          launch_kernel(batch_fgp_kernel<__half>, dim3(L.fgp_grid), dim3(256), 0, s, L.probs, L.fgp_tiles,
-                        L.tile_range, (const int*)L.scan_tiles, L.n, q, b, it);
+      switch (L.dtype * 3 + L.nonneg_mode) {
+#define TVS_BF(IDX, T_, NN_)                                                                              \
+  case IDX:                                                                                           \
+    launch_kernel(batch_fgp_kernel<T_, NN_>, dim3(L.fgp_grid), dim3(256), 0, s, L.probs, L.fgp_tiles,  \
+                  L.tile_range, (const int*)L.scan_tiles, L.n, q, b, it);                            \
+    break;
+        TVS_BF(0, float, 0) TVS_BF(1, float, 1) TVS_BF(2, float, 2)
+        TVS_BF(3, __nv_bfloat16, 0) TVS_BF(4, __nv_bfloat16, 1) TVS_BF(5, __nv_bfloat16, 2)
+        TVS_BF(6, __half, 0) TVS_BF(7, __half, 1) default: TVS_BF(8, __half, 2)
+#undef TVS_BF
       }
       q = 1 - q;
       g += it;

@@ -237,6 +237,7 @@ struct BatchLaunch {
   int* scan_tiles;             // [n + 1]: exclusive scan of the tiles of this iteration's active problems
   int* scan_chunks;            // [n + 1]: the same for their chunks
   int fgp_grid, fin_grid;      // persistent grid sizes of the inner and finalisation kernels
+  int nonneg_mode;             // 0: no problem constrained, 1: all, 2: mixed
 };
 int batch_fgp_tile_w();
 int batch_fgp_tile_h();
