@@ -229,6 +229,18 @@ tvs_status tv_prox_noalloc(int ndim, const int dims[3], const float* z, float* u
                            int n_iter, tvs_dual_dtype dual, void* dual_state, int nonneg,
                            void* cuda_stream);
 
+/* ROF duality gap of a TV-prox dual, the certificate of the prox's accuracy
+ * (Section 2.1: prox_{lambda TV}(z) and its dual, the Dual-ROF problem Eq. 6,
+ * written for the unit-ball dual p = q / lambda).  With u = z + lambda div p,
+ *   G = P(u) - D(p) = lambda * sum_i ( |(D u)_i|_2 - <(D u)_i, p_i> ),
+ * which is >= 0 whenever every |p_i| <= 1 and 0 exactly at the optimum.
+ * dual_state: p as tv_prox leaves it (ndim planes of the dual dtype, device
+ * memory); z as passed to tv_prox (device).  For the unconstrained prox
+ * (nonneg = 0).  Synchronous: *gap (host) receives G, accumulated in compensated
+ * FP32 and combined in FP64. */
+tvs_status tv_prox_gap(tvs_ctx* ctx, int ndim, const int dims[3], const float* z, double lambda,
+                       tvs_dual_dtype dual, const void* dual_state, double* gap);
+
 /* ---- outer solvers --------------------------------------------------------- */
 /* x_inout: initial iterate in, final iterate out (image size, TVS_MEM_* says
  * where it lives).  The control variate starts at h_0 = 0, the TV dual at 0. */

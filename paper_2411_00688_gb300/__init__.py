@@ -20,6 +20,7 @@ from .api import (  # noqa: F401
     proxskip_solve,
     proxskip_solve_batch,
     tv_prox,
+    tv_prox_gap,
     tv_prox_noalloc,
     tvs_coin,
     tvs_coin_schedule_device,

@@ -85,6 +85,8 @@ SIGNATURES = [
     ("tvs_objective", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     ("tv_prox", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_void_p, C.c_void_p,
                           C.c_double, C.c_int, C.c_int, C.c_void_p, C.c_int]),
+    ("tv_prox_gap", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_void_p, C.c_double, C.c_int,
+                              C.c_void_p, C.POINTER(C.c_double)]),
     ("tvs_fgp_config", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int)]),
     ("tv_prox_noalloc", C.c_int, [C.c_int, C.POINTER(C.c_int), C.c_void_p, C.c_void_p, C.c_double,
                                   C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p]),

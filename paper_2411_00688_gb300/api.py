@@ -227,6 +227,20 @@ def tv_prox(ctx: Context, z, u, lam: float, n_iter: int, dual: str = "f32", dual
     return u
 
 
+def tv_prox_gap(ctx: Context, z, lam: float, dual_state, dual: str = "f32") -> float:
+    """ROF duality gap G = P(u) - D(p) of the dual p = dual_state (as tv_prox leaves
+    it) for prox_{lam TV}(z), u = z + lam div p.  z and dual_state: CUDA tensors."""
+    shape = tuple(z.shape)
+    if len(shape) not in (2, 3):
+        raise ValueError("z must be 2D or 3D")
+    dims = (C.c_int * 3)(*(list(reversed(shape)) + [1] * (3 - len(shape))))
+    _sync_torch()
+    out = C.c_double()
+    L.check(L.lib().tv_prox_gap(ctx.handle, len(shape), dims, C.c_void_p(z.data_ptr()), float(lam), L.DUAL[dual],
+                                C.c_void_p(dual_state.data_ptr()), C.byref(out)))
+    return out.value
+
+
 def tvs_fgp_config(ctx: Context, shape, dual: str = "f32"):
     """(iterations per launch, columns per lane, rows per warp [+100 register-blocked])
     of the inner kernel the context uses for this image shape (autotuned once)."""

@@ -1731,6 +1731,38 @@ tvs_status tv_prox(tvs_ctx* C, int ndim, const int dims[3], const float* z, floa
   return TVS_OK;
 }
 
+tvs_status tv_prox_gap(tvs_ctx* C, int ndim, const int dims[3], const float* z, double lambda,
+                       tvs_dual_dtype dual, const void* dual_state, double* gap) {
+  if (!C || !dims || !z || !dual_state || !gap) return fail(TVS_EINVAL, "null argument");
+  if (ndim != 2 && ndim != 3) return fail(TVS_EINVAL, "ndim must be 2 or 3");
+  if (dims[0] < 1 || dims[1] < 1 || (ndim == 3 && dims[2] < 1)) return fail(TVS_EINVAL, "dims must be >= 1");
+  if (!(lambda >= 0) || !is_fin(lambda)) return fail(TVS_EINVAL, "lambda must be finite and >= 0");
+  if (!valid_dual(dual)) return fail(TVS_EINVAL, "invalid dual dtype");
+  Dims d;
+  d.nx = dims[0];
+  d.ny = dims[1];
+  d.nz = ndim == 3 ? dims[2] : 1;
+  d.ndim = ndim;
+  cudaStream_t s = C->stream;
+  const size_t nb = (size_t)rof_gap_blocks(d.n());
+  if (nb > C->parts_cap) {
+    dfree(C->parts);
+    C->bytes -= C->parts_cap * sizeof(Partial);
+    C->parts = nullptr;
+    C->parts_cap = 0;
+    TVS_TRY(dalloc(C, nullptr, (void**)&C->parts, nb * sizeof(Partial)));
+    C->parts_cap = nb;
+  }
+  CUDA_TRY(launch_rof_gap_partials(d, z, dual_state, dual, (float)lambda, C->parts, s));
+  CUDA_TRY(launch_reduce_record(C->parts, (int)nb, nullptr, 0, 0.0, 1, nullptr, nullptr, 0.0, 0.0, nullptr,
+                                nullptr, C->red_out, s));
+  double sum = 0.0;
+  CUDA_TRY(cudaMemcpyAsync(&sum, C->red_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  *gap = lambda * sum;
+  return TVS_OK;
+}
+
 tvs_status tvs_fgp_config(tvs_ctx* C, int ndim, const int dims[3], tvs_dual_dtype dual, int out[3]) {
   if (!C || !dims || !out) return fail(TVS_EINVAL, "null argument");
   if (ndim != 2 && ndim != 3) return fail(TVS_EINVAL, "ndim must be 2 or 3");

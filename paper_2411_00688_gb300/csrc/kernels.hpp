@@ -92,6 +92,11 @@ cudaError_t launch_fgp_block(const FgpConfig& c, const Dims& d, const float* z, 
 // x_out = P_X(z + lam div p); if h_out: h_out = h_coef (x_out - z);
 // if p_home: p_home = p.  When fista_y is set: fista_y = x_out + beta (x_out - x_prev) with
 // beta = beta_tab[*beta_idx] (FISTA extrapolation, read on the device).
+// ROF duality-gap partials of a unit-ball dual p (rof_gap_blocks(n) of them):
+// lam * their sum = P(u) - D(p) at u = z + lam div p.
+int rof_gap_blocks(size_t n);
+cudaError_t launch_rof_gap_partials(const Dims& d, const float* z, const void* p, int dtype, float lam,
+                                    Partial* part, cudaStream_t s);
 cudaError_t launch_fgp_finalize(const Dims& d, const float* z, const void* p, int dtype, float lam,
                                 bool nonneg, float* x_out, float* h_out, float h_coef,
                                 void* p_home, const float* x_prev, float* fista_y,

@@ -177,7 +177,7 @@ def denoise3d_512(duals=("f32", "bf16", "f16")):
     return out
 
 
-def _batch(n_problems=None, K=None, batch_only=False):
+def _batch(n_problems=None, K=None, batch_only=False, dual="f32"):
     import torch
     from synth.configs import BatchConfig
     tvs, ctx = _ctx()
@@ -205,12 +205,12 @@ def _batch(n_problems=None, K=None, batch_only=False):
 
     def batched():
         xs = [b.clone() for b in bs]
-        return tvs.proxskip_solve_batch(ctx, probs, xs, [1.0] * len(probs), ps, seeds, K, cfg.n_inner)
+        return tvs.proxskip_solve_batch(ctx, probs, xs, [1.0] * len(probs), ps, seeds, K, cfg.n_inner, dual=dual)
 
     def loop():
         trs = []
         for pr, b, p, s in zip(probs, bs, ps, seeds):
-            trs.append(tvs.proxskip_solve(pr, b.clone(), 1.0, p, s, K, cfg.n_inner)[1])
+            trs.append(tvs.proxskip_solve(pr, b.clone(), 1.0, p, s, K, cfg.n_inner, dual=dual)[1])
         return trs
 
     batched()
@@ -220,7 +220,7 @@ def _batch(n_problems=None, K=None, batch_only=False):
                  "n_inner": cfg.n_inner, "batched_s": t_batch}]
     loop()
     _, t_loop = _timed(loop)
-    return [{"workload": cfg.name, "problems": len(specs), "pixels": npx, "iterations": K,
+    return [{"workload": cfg.name, "dual": dual, "problems": len(specs), "pixels": npx, "iterations": K,
              "n_inner": cfg.n_inner, "batched_s": t_batch, "loop_s": t_loop, "speedup": t_loop / t_batch}]
 
 
@@ -231,9 +231,10 @@ def main(argv=None):
     ap.add_argument("--problems", type=int, default=None)
     ap.add_argument("--iters", type=int, default=None)
     ap.add_argument("--batch-only", action="store_true", help="batch2d_256: time the batched solve only")
+    ap.add_argument("--dual", default="f32", choices=["f32", "bf16", "f16"], help="batch2d_256: dual storage")
     args = ap.parse_args(argv)
     if args.workload == "batch2d_256":
-        recs = _batch(args.problems, args.iters, args.batch_only)
+        recs = _batch(args.problems, args.iters, args.batch_only, args.dual)
     else:
         recs = {"denoise2d_256": denoise2d_256, "ct2d_512": ct2d_512, "denoise3d_512": denoise3d_512,
                 "deblur2d_1024": deblur2d_1024}[args.workload]()

@@ -132,3 +132,33 @@ def test_prox_invalid_arguments(tvs, ctx):
         tvs.tv_prox(ctx, z, u, float("nan"), 5)
     with pytest.raises(tvs.TVSError):
         tvs.tv_prox(ctx, z, z, 0.1, 5)
+
+
+@pytest.mark.parametrize("shape,dual", [((130, 97), "f32"), ((20, 33, 17), "f32"), ((130, 97), "bf16")])
+def test_prox_gap_matches_oracle(tvs, ctx, shape, dual):
+    """The ROF duality gap of the dual tv_prox leaves equals the oracle's P(u) - D(p)
+    on the same dual, is non-negative and shrinks as the prox converges (with a
+    BF16 dual the rounded |p_i| may exceed 1 by an ulp, so only the first two
+    checks apply there, and the gap levels off at the storage precision)."""
+    import torch
+    z32, z64 = f32(_z(shape, 7))
+    lam = 0.2
+    zt = cuda(z32)
+    ut = torch.empty_like(zt)
+    dt = {"f32": torch.float32, "bf16": torch.bfloat16}[dual]
+    state = torch.zeros((len(shape),) + shape, dtype=dt, device="cuda")
+    gaps = []
+    for n_iter in (3, 30, 300):
+        state.zero_()
+        tvs.tv_prox(ctx, zt, ut, lam, n_iter, dual=dual, dual_state=state)
+        g = tvs.tv_prox_gap(ctx, zt, lam, state, dual=dual)
+        p64 = state.float().cpu().numpy().astype(np.float64)
+        ref = tv.rof_gap(z64, lam, p64)
+        if dual == "f32":
+            assert g >= 0.0
+        # FP32 evaluation of u = z + lam div p: absolute error ~ n * lam * 1e-7 * |D u|
+        assert abs(g - ref) <= 1e-4 * ref + 1e-6 * z64.size * lam, (n_iter, g, ref)
+        gaps.append(g)
+    assert gaps[1] < gaps[0]
+    if dual == "f32":
+        assert gaps[2] < gaps[1]
