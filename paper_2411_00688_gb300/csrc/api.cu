@@ -1120,8 +1120,9 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
   BatchScratch S;
   // per-problem state, descriptors and work lists
   std::vector<BatchProb> desc(n);
-  std::vector<int4> blur_tiles, fgp_tiles;
-  std::vector<int2> ident_chunks, all_chunks, tile_range(n), chunk_range(n);
+  std::vector<int4> blur_tiles;
+  std::vector<int2> ident_chunks, tile_range(n), chunk_range(n);
+  int n_fgp_tiles = 0, n_all_chunks = 0;  // inner tiles / pixel chunks of all problems
   const int chunk = batch_chunk(), ftw = batch_fgp_tile_w(), fth = batch_fgp_tile_h();
   for (int i = 0; i < n; ++i) {
     tvs_problem* P = probs[i];
@@ -1174,12 +1175,11 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
       for (int c = 0; c < nchunks; ++c) ident_chunks.push_back(make_int2(i, c));
       D.part_n = nchunks;
     }
-    chunk_range[i] = make_int2((int)all_chunks.size(), nchunks);
-    for (int c = 0; c < nchunks; ++c) all_chunks.push_back(make_int2(i, c));
+    chunk_range[i] = make_int2(n_all_chunks, nchunks);
+    n_all_chunks += nchunks;
     const int fx = (W + ftw - 1) / ftw, fy = (H + fth - 1) / fth;
-    tile_range[i] = make_int2((int)fgp_tiles.size(), fx * fy);
-    for (int y = 0; y < fy; ++y)
-      for (int x = 0; x < fx; ++x) fgp_tiles.push_back(make_int4(i, x, y, 0));
+    tile_range[i] = make_int2(n_fgp_tiles, fx * fy);  // row-major tiles, decoded in the kernel
+    n_fgp_tiles += fx * fy;
   }
   const int n_blur = (int)blur_tiles.size();
   for (auto& D : desc)
@@ -1195,8 +1195,6 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
   TVS_TRY(S.upload(st0, &L.state, s));
   TVS_TRY(S.upload(blur_tiles, (int4**)&L.blur_tiles, s));
   TVS_TRY(S.upload(ident_chunks, (int2**)&L.ident_chunks, s));
-  TVS_TRY(S.upload(fgp_tiles, (int4**)&L.fgp_tiles, s));
-  TVS_TRY(S.upload(all_chunks, (int2**)&L.all_chunks, s));
   TVS_TRY(S.upload(coins, (unsigned char**)&L.coins, s));
   TVS_TRY(S.upload(tile_range, (int2**)&L.tile_range, s));
   TVS_TRY(S.upload(chunk_range, (int2**)&L.chunk_range, s));
@@ -1204,8 +1202,8 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
   TVS_TRY(S.zeros<int>((size_t)n + 1, &L.scan_chunks, s));
   L.n_blur_tiles = n_blur;
   L.n_ident_chunks = (int)ident_chunks.size();
-  L.n_fgp_tiles = (int)fgp_tiles.size();
-  L.n_all_chunks = (int)all_chunks.size();
+  L.n_fgp_tiles = n_fgp_tiles;
+  L.n_all_chunks = n_all_chunks;
   {
     int nn = 0;
     for (int i = 0; i < n; ++i) nn += probs[i]->desc.nonneg != 0;

@@ -205,8 +205,7 @@ batch_active_kernel(const BatchProb* __restrict__ probs, const BatchState* __res
 #endif
 template <typename T, int NN>
 __global__ void __launch_bounds__(256, TVS_BATCH_FGP_MIN_CTAS)
-batch_fgp_kernel(const BatchProb* __restrict__ probs, const int4* __restrict__ tiles,
-                 const int2* __restrict__ tile_range, const int* __restrict__ scan, int n, int q_in,
+batch_fgp_kernel(const BatchProb* __restrict__ probs, const int2* __restrict__ tile_range, const int* __restrict__ scan, int n, int q_in,
                  TBBetas betas, int iters) {
   pdl_enter();
   __shared__ int s_scan[SCAN_SMEM];
@@ -235,8 +234,7 @@ batch_fgp_kernel(const BatchProb* __restrict__ probs, const int4* __restrict__ t
 // it sits in the second pair.
 template <typename T>
 __global__ void __launch_bounds__(256)
-batch_finalize_kernel(const BatchProb* __restrict__ probs, const int2* __restrict__ chunks,
-                      const int2* __restrict__ chunk_range, const int* __restrict__ scan, int n, int par,
+batch_finalize_kernel(const BatchProb* __restrict__ probs, const int2* __restrict__ chunk_range, const int* __restrict__ scan, int n, int par,
                       int fin_pair) {
   pdl_enter();
   __shared__ int s_scan[SCAN_SMEM];
@@ -330,7 +328,7 @@ cudaError_t launch_batch_iteration(const BatchLaunch& L, int par, cudaStream_t s
       switch (L.dtype * 3 + L.nonneg_mode) {
 #define TVS_BF(IDX, T_, NN_)                                                                              \
   case IDX:                                                                                           \
-    launch_kernel(batch_fgp_kernel<T_, NN_>, dim3(L.fgp_grid), dim3(256), 0, s, L.probs, L.fgp_tiles,  \
+    launch_kernel(batch_fgp_kernel<T_, NN_>, dim3(L.fgp_grid), dim3(256), 0, s, L.probs,                \
                   L.tile_range, (const int*)L.scan_tiles, L.n, q, b, it);                            \
     break;
         TVS_BF(0, float, 0) TVS_BF(1, float, 1) TVS_BF(2, float, 2)
@@ -347,15 +345,15 @@ cudaError_t launch_batch_iteration(const BatchLaunch& L, int par, cudaStream_t s
   // in every descriptor)
   switch (L.dtype) {
     case DUAL_F32:
-      launch_kernel(batch_finalize_kernel<float>, dim3(L.fin_grid), dim3(256), 0, s, L.probs, L.all_chunks,
+      launch_kernel(batch_finalize_kernel<float>, dim3(L.fin_grid), dim3(256), 0, s, L.probs,
                     L.chunk_range, (const int*)L.scan_chunks, L.n, par, fin_pair);
       break;
     case DUAL_BF16:
       launch_kernel(batch_finalize_kernel<__nv_bfloat16>, dim3(L.fin_grid), dim3(256), 0, s, L.probs,
-                    L.all_chunks, L.chunk_range, (const int*)L.scan_chunks, L.n, par, fin_pair);
+                    L.chunk_range, (const int*)L.scan_chunks, L.n, par, fin_pair);
       break;
     default:
-      launch_kernel(batch_finalize_kernel<__half>, dim3(L.fin_grid), dim3(256), 0, s, L.probs, L.all_chunks,
+      launch_kernel(batch_finalize_kernel<__half>, dim3(L.fin_grid), dim3(256), 0, s, L.probs,
                     L.chunk_range, (const int*)L.scan_chunks, L.n, par, fin_pair);
   }
   launch_kernel(batch_tick_kernel, dim3(1), dim3(1), 0, s, L.kctr);

@@ -224,10 +224,8 @@ struct BatchLaunch {
   int n_blur_tiles;
   const int2* ident_chunks; // (problem, chunk) of the identity problems
   int n_ident_chunks;
-  const int4* fgp_tiles;    // (problem, tile x, tile y) of every problem (blocked inner tiles)
-  int n_fgp_tiles;
-  const int2* all_chunks;   // (problem, chunk) of every problem
-  int n_all_chunks;
+  int n_fgp_tiles;          // blocked inner tiles of all problems
+  int n_all_chunks;         // pixel chunks of all problems
   const unsigned char* coins;  // [K][n]
   int* kctr;                   // outer iteration counter (device)
   Partial *part_a, *part_b;

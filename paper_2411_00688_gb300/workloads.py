@@ -2,8 +2,9 @@
 benchmark's headline one (python -m paper_2411_00688_gb300.workloads NAME ...).
 
   denoise2d_256  ProxSkip p = 0.1 vs PGD, 100 inner iterations, <= 500 iterations
-  ct2d_512       PDHGSkip-2 p in {0.2, 0.05} vs PDHG, 50 inner, <= 2000 iterations; explicit
-                 preconditioned PDHG (closed-form proxes) <= 20000 iterations
+  ct2d_512       PDHGSkip-2 p in {0.2, 0.05} vs PDHG, <= 2000 iterations, at sigma = tau with 50
+                 inner iterations and at sigma = tau / 4 with 200; explicit preconditioned PDHG
+                 (closed-form proxes) <= 20000 iterations
   deblur2d_1024  explicit preconditioned PDHG, <= 20000 iterations (the ProxSkip / PGD /
                  FISTA numbers of this workload come from the benchmark)
   denoise3d_512  ProxSkip p = 0.1 vs PGD, 30 inner, <= 200 iterations (FP32 / BF16 / FP16 dual)
@@ -108,16 +109,23 @@ def ct2d_512():
     _, _, ref = tvs.pdhg_solve(prob, x0.clone(), zeros_sino.clone(), st, st, 6000, 100)
     f_star = float(np.nanmin(ref.objective))
     out = []
-    runs = [("pdhg", lambda: tvs.pdhg_solve(prob, x0.clone(), zeros_sino.clone(), st, st, cfg.max_iter, cfg.n_inner,
-                                            f_star=f_star, target=TARGET))]
-    for p in cfg.ps:
-        runs.append((f"pdhgskip_p{p}", lambda p=p: tvs.pdhgskip_solve(prob, x0.clone(), zeros_sino.clone(), st, st, p,
-                                                                       cfg.seed, cfg.max_iter, cfg.n_inner,
-                                                                       f_star=f_star, target=TARGET)))
-    for name, fn in runs:
-        fn()
-        (_, _, tr), wall = _timed(fn)
-        out.append(_solve_record(name, tr, wall, f_star, workload=cfg.name, norm_A_sq=L, sigma=st, tau=st))
+    # the configuration's setting (sigma = tau, 50 inner iterations) and a second
+    # one with a smaller primal step (sigma = tau / 4, sigma tau ||A||^2 = 0.98) and
+    # 200 inner iterations, where the larger prox steps lambda = sigma alpha / p of
+    # PDHGSkip-2 are solved accurately enough to reach the target
+    for ratio, n_inner in ((1.0, cfg.n_inner), (0.25, 200)):
+        sg, ta = st * math.sqrt(ratio), st / math.sqrt(ratio)
+        runs = [("pdhg", lambda sg=sg, ta=ta, ni=n_inner: tvs.pdhg_solve(
+            prob, x0.clone(), zeros_sino.clone(), sg, ta, cfg.max_iter, ni, f_star=f_star, target=TARGET))]
+        for p in cfg.ps:
+            runs.append((f"pdhgskip_p{p}", lambda p=p, sg=sg, ta=ta, ni=n_inner: tvs.pdhgskip_solve(
+                prob, x0.clone(), zeros_sino.clone(), sg, ta, p, cfg.seed, cfg.max_iter, ni, f_star=f_star,
+                target=TARGET)))
+        for name, fn in runs:
+            fn()
+            (_, _, tr), wall = _timed(fn)
+            out.append(_solve_record(name, tr, wall, f_star, workload=cfg.name, norm_A_sq=L, sigma=sg, tau=ta,
+                                     n_inner=n_inner))
     out.append(_explicit(tvs, prob, x0, zeros_sino, f_star, cfg.name))
     return out
 
