@@ -329,6 +329,8 @@ def run_gpu(args):
                    "f_star": f_star},
         "time_to_target_device_s": statistics.mean(t.time_to_target_s for t in ps_tr),
         "iterations_to_target": last.reached_iter + 1 if last.reached else None,
+        "outer_iterations_per_s": (last.reached_iter + 1) / last.time_to_target_s
+        if last.reached and last.time_to_target_s > 0 else None,
         "prox_calls": last.prox_calls,
         "reached": all(t.reached for t in ps_tr),
         "pgd_time_to_target_s": statistics.mean(pgd_times) if all(t.reached for t in pgd_tr) else None,

@@ -354,14 +354,14 @@ tvs_status ensure_trace(tvs_problem* P, int K) {
 // Partials of the data term / TV term written by the step kernels.
 int step_parts_a(const tvs_problem* P) {
   switch (P->desc.op.kind) {
-    case TVS_OP_GAUSS_BLUR: return fb_step_blocks_2d(P->dims.ny, P->dims.nx);
+    case TVS_OP_GAUSS_BLUR: return fb_step_blocks_2d(P->dims.ny, P->dims.nx, P->bw.R);
     case TVS_OP_PARALLEL_BEAM: return ct_fwd_blocks(P->geom);
     default: return pointwise_blocks(P->n);
   }
 }
 int step_parts_b(const tvs_problem* P) {
   switch (P->desc.op.kind) {
-    case TVS_OP_GAUSS_BLUR: return fb_step_blocks_2d(P->dims.ny, P->dims.nx);
+    case TVS_OP_GAUSS_BLUR: return fb_step_blocks_2d(P->dims.ny, P->dims.nx, P->bw.R);
     case TVS_OP_PARALLEL_BEAM: return ct_bwd_blocks(P->geom);
     default: return pointwise_blocks(P->n);
   }
@@ -1166,7 +1166,8 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
     const int nchunks = (int)((npx + chunk - 1) / chunk);
     if (P->desc.op.kind == TVS_OP_GAUSS_BLUR) {
       D.part_off = (int)blur_tiles.size();
-      const int tx = (W + 31) / 32, ty = (H + 31) / 32;  // tiles of the fused blur step
+      const int fx = fb_step_tile_w(P->bw.R);  // tiles of the fused blur step
+      const int tx = (W + fx - 1) / fx, ty = (H + fb_step_tile_h() - 1) / fb_step_tile_h();
       for (int y = 0; y < ty; ++y)
         for (int x = 0; x < tx; ++x) blur_tiles.push_back(make_int4(i, x, y, 0));
       D.part_n = tx * ty;

@@ -100,13 +100,34 @@ __device__ __forceinline__ void blur_tile_body(const float* __restrict__ src, in
 
 // Fused forward-backward step for the blur operator (A = A^T) (out may be null:
 // partials only):
-//   r = A x - b on the FX x FY tile plus an R-cell ring, the ring cells outside the
-//   image copied from their mirror cells (the reflective A reads r there), then
+//   r = A x - b on the tile plus an R-cell ring, the ring cells outside the image
+//   copied from their mirror cells (the reflective A reads r there), then
 //   out = x - gamma A r + ch h on the tile, with the partials of 1/2 ||r||^2 and
 //   TV(x) over the tile.  The arithmetic of every output value is the residual
 //   kernel's followed by the step kernel's (same taps, same order); only the
 //   residual never leaves shared memory.
-constexpr int FX = 32, FY = 32, FNT = 256;
+// Layout: every lane owns two adjacent columns (one float2) in every pass, so a
+// tap is one packed FP32x2 FMA and a horizontal pass reads R + 1 float2 per two
+// outputs; the staged region is 64 columns wide, the tile fb_tile_w(R) =
+// 64 - 4R columns by FY rows.
+constexpr int FY = 32, FNT = 256;
+__host__ __device__ constexpr int fb_tile_w(int R) { return 64 - 4 * R; }
+
+// Two adjacent taps positions: (v[c], v[c + 1]) for even c is one float2; for odd
+// c it straddles two.
+template <int K>
+__device__ __forceinline__ float2 fb_pair(const float2* v) {
+  return (K & 1) ? make_float2(v[K / 2].y, v[K / 2 + 1].x) : v[K / 2];
+}
+template <int R, int K = 0>
+__device__ __forceinline__ float2 fb_taps(const float2* v, const float* wk, float2 acc) {
+  if constexpr (K > 2 * R) {
+    return acc;
+  } else {
+    acc = __ffma2_rn(make_float2(wk[K], wk[K]), fb_pair<K>(v), acc);
+    return fb_taps<R, K + 1>(v, wk, acc);
+  }
+}
 
 template <int R>
 __device__ __forceinline__ void blur_fb_step_body(const float* __restrict__ x, const float* __restrict__ b,
@@ -114,128 +135,157 @@ __device__ __forceinline__ void blur_fb_step_body(const float* __restrict__ x, c
                                                   int W, const BlurW& w, float gamma, float ch,
                                                   Partial* __restrict__ part_a, Partial* __restrict__ part_b,
                                                   int tile_x, int tile_y, int part_index) {
-  constexpr int XR = FY + 4 * R, XC = FX + 4 * R;  // staged x: rows/cols i0-2R .. i0+FY+2R
-  constexpr int RR = FY + 2 * R, RC = FX + 2 * R;  // residual region: i0-R .. i0+FY+R
-  constexpr int NW = FNT / 32;                     // warps; lane = column, warp = row phase
+  constexpr int FX = fb_tile_w(R);
+  constexpr int XR = FY + 4 * R;                   // staged x: rows i0-2R .., columns j0-2R .. j0-2R+63
+  constexpr int RR = FY + 2 * R;                   // residual region rows i0-R .., columns j0-R .. j0+FX+R
+  constexpr int NW = FNT / 32;                     // warps; lane = column pair, warp = row phase
+  constexpr int RP = 32 - R, OP = 32 - 2 * R;      // column pairs of the residual region / of the tile
   constexpr int VR = (RR + NW - 1) / NW;           // residual rows per warp (vertical pass)
   constexpr int VO = FY / NW;                      // output rows per warp (final pass)
-  static_assert(FX == 32 && FY % NW == 0, "tile layout");
-  __shared__ float sx[XR][XC + 1];
-  __shared__ float sh[XR][RC + 1];  // horizontal pass of x, later of r
-  __shared__ float sr[RR][RC + 1];
+  static_assert(FY % NW == 0 && R >= 1 && R <= 8, "tile layout");
+  __shared__ float2 sx[XR][32];
+  __shared__ float2 sh[XR][32];  // horizontal pass of x, later of r
+  __shared__ float2 sr[RR][32];
   float wk[2 * R + 1];
 #pragma unroll
   for (int k = 0; k <= 2 * R; ++k) wk[k] = w.w[k];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int j0 = tile_x * FX, i0 = tile_y * FY;
-  const bool c1x = lane + 32 < XC, c1r = lane + 32 < RC;  // second column of a lane
   {
-    const int gj0 = reflect_index(j0 - 2 * R + lane, W);
-    const int gj1 = c1x ? reflect_index(j0 - 2 * R + lane + 32, W) : 0;
+    const int gj0 = reflect_index(j0 - 2 * R + 2 * lane, W), gj1 = reflect_index(j0 - 2 * R + 2 * lane + 1, W);
 #pragma unroll
     for (int t = 0; t < (XR + NW - 1) / NW; ++t) {
       const int a = wp + NW * t;
       if (a < XR) {
         const float* row = x + (size_t)reflect_index(i0 - 2 * R + a, H) * W;
-        sx[a][lane] = __ldg(row + gj0);
-        if (c1x) sx[a][lane + 32] = __ldg(row + gj1);
+        sx[a][lane] = make_float2(__ldg(row + gj0), __ldg(row + gj1));
       }
     }
   }
+  // the b values the vertical pass needs, issued now so that they arrive during
+  // the horizontal pass
+  float2 bv[VR];
+  {
+    const int a0 = wp * VR, gj = j0 - R + 2 * lane;
+    const bool cin0 = gj >= 0 && gj < W, cin1 = gj + 1 >= 0 && gj + 1 < W;
+#pragma unroll
+    for (int t = 0; t < VR; ++t) {
+      const int gi = i0 - R + a0 + t;
+      const bool rin = lane < RP && a0 + t < RR && gi >= 0 && gi < H;
+      const float* brow = b + (size_t)(rin ? gi : 0) * W;
+      bv[t] = make_float2(rin && cin0 ? __ldg(brow + gj) : 0.f, rin && cin1 ? __ldg(brow + gj + 1) : 0.f);
+    }
+  }
   __syncthreads();
+  // horizontal pass of x over all staged rows, output columns 2m, 2m+1 < 64 - 2R
 #pragma unroll
   for (int t = 0; t < (XR + NW - 1) / NW; ++t) {
     const int a = wp + NW * t;
-    if (a < XR) {
-      float acc = 0.f;
+    if (a < XR && lane < RP) {
+      float2 v[R + 1];
 #pragma unroll
-      for (int k = 0; k <= 2 * R; ++k) acc = fmaf(wk[k], sx[a][lane + k], acc);
-      sh[a][lane] = acc;
-      if (c1r) {
-        float acc1 = 0.f;
-#pragma unroll
-        for (int k = 0; k <= 2 * R; ++k) acc1 = fmaf(wk[k], sx[a][lane + 32 + k], acc1);
-        sh[a][lane + 32] = acc1;
-      }
+      for (int j = 0; j <= R; ++j) v[j] = sx[a][lane + j];
+      sh[a][lane] = fb_taps<R>(v, wk, make_float2(0.f, 0.f));
     }
   }
   __syncthreads();
-  // vertical pass -> r = A x - b on the in-image cells of the residual region; each
-  // warp owns VR consecutive rows and slides a register window down its columns
+  // vertical pass -> r = A x - b on the in-image cells of the residual region;
+  // each warp owns VR consecutive rows and slides a register window down them
   FAcc acc_a, acc_b;
-#pragma unroll
-  for (int half = 0; half < 2; ++half) {
-    const int c = lane + 32 * half;
-    if (half == 1 && !c1r) break;
+  if (lane < RP) {
     const int a0 = wp * VR;
-    float win[VR + 2 * R];
+    float2 win[VR + 2 * R];
 #pragma unroll
-    for (int t = 0; t < VR + 2 * R; ++t) win[t] = a0 + t < XR ? sh[a0 + t][c] : 0.f;
-    const int gj = j0 - R + c;
+    for (int t = 0; t < VR + 2 * R; ++t) win[t] = a0 + t < XR ? sh[a0 + t][lane] : make_float2(0.f, 0.f);
+    const int gj = j0 - R + 2 * lane;  // global column of the pair's left cell
+    const bool cin0 = gj >= 0 && gj < W, cin1 = gj + 1 >= 0 && gj + 1 < W;
+    const bool own0 = 2 * lane >= R && 2 * lane < R + FX, own1 = 2 * lane + 1 >= R && 2 * lane + 1 < R + FX;
 #pragma unroll
     for (int t = 0; t < VR; ++t) {
       const int a = a0 + t;
       const int gi = i0 - R + a;
-      if (a >= RR || gi < 0 || gi >= H || gj < 0 || gj >= W) continue;
-      float v = 0.f;
+      if (a >= RR || gi < 0 || gi >= H) continue;
+      float2 v = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int k = 0; k <= 2 * R; ++k) v = fmaf(wk[k], win[t + k], v);
-      const float r = v - __ldg(b + (size_t)gi * W + gj);
-      sr[a][c] = r;
-      if (a >= R && a < R + FY && c >= R && c < R + FX) acc_a.add(0.5f * (r * r));
+      for (int k = 0; k <= 2 * R; ++k) v = __ffma2_rn(make_float2(wk[k], wk[k]), win[t + k], v);
+      float2 r = make_float2(0.f, 0.f);
+      if (cin0) r.x = v.x - bv[t].x;
+      if (cin1) r.y = v.y - bv[t].y;
+      sr[a][lane] = r;
+      if (a >= R && a < R + FY) {
+        if (cin0 && own0) acc_a.add(0.5f * (r.x * r.x));
+        if (cin1 && own1) acc_a.add(0.5f * (r.y * r.y));
+      }
     }
   }
   __syncthreads();
   // ring cells outside the image take their mirror cell's residual
   if (i0 < R || j0 < R || i0 + FY + R > H || j0 + FX + R > W) {
+    float* srf = &sr[0][0].x;  // row stride 64 floats
     for (int a = wp; a < RR; a += NW) {
       const int gi = i0 - R + a;
 #pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        const int c = lane + 32 * half;
-        if (c >= RC) continue;
+      for (int q = 0; q < 2; ++q) {
+        const int c = 2 * lane + q;
+        if (c >= 2 * RP) continue;
         const int gj = j0 - R + c;
         if (gi >= 0 && gi < H && gj >= 0 && gj < W) continue;
-        sr[a][c] = sr[reflect_index(gi, H) - (i0 - R)][reflect_index(gj, W) - (j0 - R)];
+        srf[a * 64 + c] = srf[(reflect_index(gi, H) - (i0 - R)) * 64 + (reflect_index(gj, W) - (j0 - R))];
       }
     }
   }
   __syncthreads();
+  // horizontal pass of r, output columns 2m, 2m+1 < FX
 #pragma unroll
   for (int t = 0; t < (RR + NW - 1) / NW; ++t) {
     const int a = wp + NW * t;
-    if (a < RR) {
-      float acc = 0.f;
+    if (a < RR && lane < OP) {
+      float2 v[R + 1];
 #pragma unroll
-      for (int k = 0; k <= 2 * R; ++k) acc = fmaf(wk[k], sr[a][lane + k], acc);
-      sh[a][lane] = acc;
+      for (int j = 0; j <= R; ++j) v[j] = sr[a][lane + j];
+      sh[a][lane] = fb_taps<R>(v, wk, make_float2(0.f, 0.f));
     }
   }
   __syncthreads();
-  {
+  if (lane < OP) {
     const int a0 = wp * VO;
-    float win[VO + 2 * R];
+    float2 win[VO + 2 * R];
 #pragma unroll
     for (int t = 0; t < VO + 2 * R; ++t) win[t] = sh[a0 + t][lane];
-    const int gj = j0 + lane;
+    const int gj = j0 + 2 * lane;
+    float2 hv[VO];  // the control variate of the pair's cells, loaded up front
+#pragma unroll
+    for (int t = 0; t < VO; ++t) {
+      const int gi = i0 + a0 + t;
+      const size_t o = (size_t)(gi < H ? gi : 0) * W + gj;
+      hv[t] = make_float2(h && out && gi < H && gj < W ? __ldg(h + o) : 0.f,
+                          h && out && gi < H && gj + 1 < W ? __ldg(h + o + 1) : 0.f);
+    }
 #pragma unroll
     for (int t = 0; t < VO; ++t) {
       const int a = a0 + t;
       const int gi = i0 + a;
-      if (gi >= H || gj >= W) continue;
-      float v = 0.f;
+      if (gi >= H) continue;
+      float2 v = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int k = 0; k <= 2 * R; ++k) v = fmaf(wk[k], win[t + k], v);
+      for (int k = 0; k <= 2 * R; ++k) v = __ffma2_rn(make_float2(wk[k], wk[k]), win[t + k], v);
+      const float2 xc = sx[a + 2 * R][lane + R];
+      const float2 xd = sx[a + 2 * R + 1][lane + R];
+      const float xr = sx[a + 2 * R][lane + R + 1].x;  // right neighbour of the pair's right cell
       const size_t o = (size_t)gi * W + gj;
-      const float xc = sx[a + 2 * R][lane + 2 * R];
-      if (out) {
-        float o_v = xc - gamma * v;
-        if (h) o_v = fmaf(ch, __ldg(h + o), o_v);
-        out[o] = o_v;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (gj + q >= W) continue;
+        const float xq = q ? xc.y : xc.x, vq = q ? v.y : v.x;
+        if (out) {
+          float o_v = xq - gamma * vq;
+          if (h) o_v = fmaf(ch, q ? hv[t].y : hv[t].x, o_v);
+          out[o + q] = o_v;
+        }
+        const float dy = gi < H - 1 ? (q ? xd.y : xd.x) - xq : 0.f;
+        const float dx = gj + q < W - 1 ? (q ? xr : xc.y) - xq : 0.f;
+        acc_b.add(tv_term(0.f, dy, dx));
       }
-      const float dy = gi < H - 1 ? sx[a + 2 * R + 1][lane + 2 * R] - xc : 0.f;
-      const float dx = gj < W - 1 ? sx[a + 2 * R][lane + 2 * R + 1] - xc : 0.f;
-      acc_b.add(tv_term(0.f, dy, dx));
     }
   }
   block_sum2_store<FNT>(acc_a, acc_b, part_a, part_b, part_index);

@@ -108,7 +108,9 @@ struct BlurW {
   int R;
 };
 int tile_blocks_2d(int H, int W);        // blocks of the 2D tile kernels
-int fb_step_blocks_2d(int H, int W);     // blocks of launch_blur_fb_step
+int fb_step_blocks_2d(int H, int W, int R);  // blocks of launch_blur_fb_step (blur radius R)
+int fb_step_tile_w(int R);                   // its tile: fb_step_tile_w(R) x fb_step_tile_h()
+int fb_step_tile_h();
 // Fused forward-backward step: out = x - gamma A (A x - b) + ch h (h may be null),
 // partials of 1/2 ||A x - b||^2 and TV(x) (fb_step_blocks_2d of each).
 cudaError_t launch_blur_fb_step(int H, int W, const float* x, const float* b, const float* h, float* out,
@@ -220,7 +222,7 @@ struct BatchLaunch {
   const BatchProb* probs;
   BatchState* state;
   int n;
-  const int4* blur_tiles;   // (problem, tile x, tile y) of the blur problems (32 x 32 tiles)
+  const int4* blur_tiles;   // (problem, tile x, tile y) of the blur problems (fused-step tiles)
   int n_blur_tiles;
   const int2* ident_chunks; // (problem, chunk) of the identity problems
   int n_ident_chunks;

@@ -35,7 +35,10 @@ def _ctx():
 
 def _solve_record(name, tr, wall_s, f_star, **extra):
     gaps = (tr.objective - f_star) / f_star if len(tr.objective) else np.array([np.nan])
-    rec = {"solver": name, "reached": tr.reached, "iterations": (tr.reached_iter + 1) if tr.reached else tr.iters_run,
+    its = (tr.reached_iter + 1) if tr.reached else tr.iters_run
+    rec = {"solver": name, "reached": tr.reached, "iterations": its,
+           "iterations_per_s": its / (tr.time_to_target_s if tr.reached and tr.time_to_target_s > 0
+                                      else max(tr.solve_ms * 1e-3, 1e-12)),
            "prox_calls": tr.prox_calls, "time_to_target_s": tr.time_to_target_s if tr.reached else None,
            "wall_s": wall_s, "final_rel_gap": float(gaps[-1]), "best_rel_gap": float(np.nanmin(gaps))}
     rec.update(extra)
