@@ -55,6 +55,18 @@ def _env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(value, device=None):
+    """The largest value over the ranks of the default process group (the value
+    itself without one): replicas are timed by their slowest rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -299,11 +311,7 @@ def run_gpu(args):
         if i >= args.warmup:
             e2e_times.append(t1 - t0)
 
-    ms_per_step = 1e3 * statistics.mean(ps_times)
-    if world > 1:
-        t = torch.tensor([ms_per_step], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_per_step = float(t.item())
+    ms_per_step = max_over_ranks(1e3 * statistics.mean(ps_times), device="cuda")
     last = ps_tr[-1]
     # kernels per iteration: the fused step kernel + 1 reduction; per prox: 2
     # timestamps, the blocked inner launches and the finalisation; per solve: start
