@@ -114,7 +114,7 @@ struct tvs_problem {
   unsigned long long* fgp_ts = nullptr;   // 2 per prox call
   float* beta_dev = nullptr;              // FISTA outer extrapolation table
   int trace_cap = 0;
-  int* flags = nullptr;                   // [0] done [1] reached k [2] trace counter [3] prox counter
+  int* flags = nullptr;  // [0] done [1] reached k [2] trace counter [3] prox counter [4] non-finite F seen
   int* done_host = nullptr;               // pinned, mapped
   int* done_host_dev = nullptr;
   int* count = nullptr;
@@ -537,7 +537,7 @@ tvs_status begin_solve(tvs_problem* P, int K, int flags_counter_start) {
   cudaStream_t s = P->ctx->stream;
   TVS_TRY(ensure_trace(P, K));
   *(volatile int*)P->done_host = 0;
-  int f[4] = {0, -1, flags_counter_start, 0};
+  int f[5] = {0, -1, flags_counter_start, 0, 0};
   CUDA_TRY(cudaMemcpyAsync(P->flags, f, sizeof(f), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemsetAsync(P->obj_dev, 0xff, sizeof(double) * (K + 1), s));  // NaN pattern
   CUDA_TRY(cudaMemsetAsync(P->dist_dev, 0xff, sizeof(double) * (K + 1), s));
@@ -571,7 +571,7 @@ tvs_status finish_solve(tvs_problem* P, int K, const LoopState& ls,
   const int iters = ls.iters;
   std::vector<double> obj(iters > 0 ? iters : 1);
   std::vector<unsigned long long> ts(iters + 1);
-  int flags[4];
+  int flags[5];
   if (iters > 0) {
     CUDA_TRY(cudaMemcpy(obj.data(), P->obj_dev, sizeof(double) * iters, cudaMemcpyDeviceToHost));
     CUDA_TRY(cudaMemcpy(ts.data(), P->ts_dev, sizeof(unsigned long long) * iters, cudaMemcpyDeviceToHost));
@@ -594,13 +594,9 @@ tvs_status finish_solve(tvs_problem* P, int K, const LoopState& ls,
     dist.resize(iters);
     CUDA_TRY(cudaMemcpy(dist.data(), P->dist_dev, sizeof(double) * iters, cudaMemcpyDeviceToHost));
   }
-  bool bad = false;
-  for (int k = 0; k < iters; ++k) {
-    // NaN entries between evaluations carry the 0xff pattern; non-finite
-    // evaluated objectives signal divergence or bad input.
-    if (std::isinf(obj[k])) bad = true;
-  }
-  if (iters > 0 && !std::isnan(obj[iters - 1]) && !is_fin(obj[iters - 1])) bad = true;
+  // the reduction raises flags[4] (and stops the solve) when an evaluated
+  // objective is not finite: divergence or non-finite data
+  const bool bad = flags[4] != 0;
   if (tr) {
     tr->iters_run = iters;
     tr->prox_calls = ls.prox;
@@ -1340,7 +1336,7 @@ extern "C" tvs_status dual_rof_solve(tvs_ctx* C, const int dims[2], const float*
   TVS_TRY(S.zeros<Partial>(nparts, &pb, s));
   TVS_TRY(S.zeros<double>((size_t)K + 1, &obj, s));
   TVS_TRY(S.zeros<unsigned long long>((size_t)K + 2, &ts, s));
-  TVS_TRY(S.zeros<int>(4, &flags, s));
+  TVS_TRY(S.zeros<int>(5, &flags, s));
   int* done_host = nullptr;
   int* done_dev = nullptr;
   {
@@ -1402,16 +1398,16 @@ extern "C" tvs_status dual_rof_solve(tvs_ctx* C, const int dims[2], const float*
   if (u_out) TVS_TRY(copy_out(u_out, u_dev, n, mem, s));
   CUDA_TRY(cudaEventRecord(C->ev_stop, s));
   CUDA_TRY(cudaStreamSynchronize(s));
+  int fl[5];
+  CUDA_TRY(cudaMemcpy(fl, flags, sizeof(fl), cudaMemcpyDeviceToHost));
   if (tr) {
     std::vector<double> o(iters > 0 ? iters : 1);
     std::vector<unsigned long long> t(iters + 1);
-    int fl[4];
     if (iters > 0) {
       CUDA_TRY(cudaMemcpy(o.data(), obj, sizeof(double) * iters, cudaMemcpyDeviceToHost));
       CUDA_TRY(cudaMemcpy(t.data(), ts, sizeof(unsigned long long) * iters, cudaMemcpyDeviceToHost));
     }
     CUDA_TRY(cudaMemcpy(&t[iters], ts + K + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost));
-    CUDA_TRY(cudaMemcpy(fl, flags, sizeof(fl), cudaMemcpyDeviceToHost));
     float ms = 0.f;
     CUDA_TRY(cudaEventElapsedTime(&ms, C->ev_start, C->ev_stop));
     tr->iters_run = iters;
@@ -1430,6 +1426,7 @@ extern "C" tvs_status dual_rof_solve(tvs_ctx* C, const int dims[2], const float*
       if (tr->t_s) tr->t_s[k] = (double)(t[k] - t[iters]) * 1e-9;
     }
   }
+  if (fl[4]) return fail(TVS_ENUMERIC, "non-finite objective during the solve");
   return TVS_OK;
 }
 
@@ -1463,7 +1460,7 @@ tvs_status tvs_create(tvs_ctx** out, int device, void* cuda_stream) {
   if (e == cudaSuccess) e = cudaEventCreate(&C->ev_stop);
   for (int i = 0; i < LAG && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&C->ring[i], cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMalloc(&C->red_out, sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&C->flags, 4 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&C->flags, 5 * sizeof(int));
   if (e == cudaSuccess) e = fgp_prepare_device();
   if (e != cudaSuccess) {
     tvs_destroy(C);
@@ -1568,7 +1565,7 @@ tvs_status tvs_problem_create(tvs_ctx* C, const tvs_problem_desc* desc, const fl
   }
   P->max_parts = parts;
   if ((st = palloc(P, &P->part_a, (size_t)parts)) || (st = palloc(P, &P->part_b, (size_t)parts)) ||
-      (st = palloc(P, &P->flags, 4)) || (st = palloc(P, &P->count, 1)))
+      (st = palloc(P, &P->flags, 5)) || (st = palloc(P, &P->count, 1)))
     return bail(st);
   {
     cudaError_t e = cudaHostAlloc((void**)&P->done_host, sizeof(int), cudaHostAllocMapped);

@@ -165,6 +165,13 @@ reduce_record_kernel(const Partial* __restrict__ part_a, int n_a, const Partial*
     const double F = sum_a + alpha * sum_b;
     if (f_out) *f_out = F;
     if (!flags) return;
+    if (!isfinite(F)) {  // divergence or non-finite data: stop the solve, the host reports it
+      flags[4] = 1;
+      if (done_host) {
+        *(volatile int*)done_host = 1;
+        __threadfence_system();
+      }
+    }
     const int k = flags[2];
     flags[2] = k + 1;
     if (k < 0 || !obj || (every > 1 && k % every != 0)) return;

@@ -162,3 +162,29 @@ def test_prox_gap_matches_oracle(tvs, ctx, shape, dual):
     assert gaps[1] < gaps[0]
     if dual == "f32":
         assert gaps[2] < gaps[1]
+
+
+def test_prox_3d_full_size_sampled(tvs, ctx):
+    """512^3, the 3D denoising workload's size, in the launch configuration of its
+    solves (z-marching kernel): 4 inner iterations, sampled voxels compared with
+    the oracle run on a 15^3 crop around each (after N iterations u at a voxel
+    depends on z within N + 2 voxels, so a crop of radius N + 3, clipped at the
+    volume's own faces, reproduces it)."""
+    import torch
+    N, n_iter, lam, rad = 512, 4, 0.05, 7
+    g = np.random.default_rng(11)
+    z32 = g.standard_normal((N, N, N), dtype=np.float32)
+    z32[100:300, 50:400, 200:500] += 1.0
+    zt = cuda(z32)
+    ut = torch.empty_like(zt)
+    tvs.tv_prox(ctx, zt, ut, lam, n_iter)
+    samples = [(0, 0, 0), (511, 511, 511), (0, 255, 300), (137, 13, 0), (255, 255, 255), (400, 511, 29),
+               (63, 64, 65), (99, 301, 199), (300, 49, 500), (511, 0, 256)]
+    for (k, i, j) in samples:
+        lo = [max(0, c - rad) for c in (k, i, j)]
+        hi = [min(N, c + rad + 1) for c in (k, i, j)]
+        crop = z32[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]].astype(np.float64)
+        u_ref, _ = tv.fgp_prox(crop, lam, n_iter)
+        ref = u_ref[k - lo[0], i - lo[1], j - lo[2]]
+        got = float(ut[k, i, j].item())
+        assert abs(got - ref) <= 1e-5 * (1.0 + abs(ref)), ((k, i, j), got, ref)

@@ -333,3 +333,19 @@ def test_reference_distance_trace_and_stop(tvs, ctx, solver):
     assert tr2.reached and tr2.rel_dist[tr2.reached_iter] <= target
     assert np.all(tr2.rel_dist[:tr2.reached_iter] > target)
     prob.set_reference(None)
+
+
+@pytest.mark.parametrize("solver", ["pgd", "proxskip", "pdhg"])
+def test_divergence_reported(tvs, ctx, solver):
+    """A step far above 2/L makes the iteration diverge; the device reduction sees
+    the non-finite objective, stops the solve and the call returns TVS_ENUMERIC."""
+    b32, _ = _data((40, 40), "blur", 3, 0.05)
+    prob = tvs.Problem(ctx, cuda(b32), 0.02, op="blur", blur_sigma=2.0)
+    with pytest.raises(tvs.TVSError) as e:
+        if solver == "pgd":
+            tvs.pgd_solve(prob, cuda(b32), 200.0, 500, 5)
+        elif solver == "proxskip":
+            tvs.proxskip_solve(prob, cuda(b32), 200.0, 0.5, 1, 500, 5)
+        else:
+            tvs.pdhg_solve(prob, cuda(b32), cuda(np.zeros_like(b32)), 50.0, 50.0, 500, 5)
+    assert e.value.status == 4
