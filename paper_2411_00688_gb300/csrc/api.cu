@@ -78,6 +78,8 @@ struct tvs_ctx {
   size_t parts_cap = 0;
   cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
   cudaEvent_t ring[LAG] = {};
+  cudaStream_t side = nullptr;                       // captured side branch (objective records)
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;  // fork / join of that branch
   size_t bytes = 0;
   FgpConfig fgp;          // forced configuration (TVS_FGP_CONFIG), or tb == 0 to autotune
   struct Tuned {
@@ -702,11 +704,19 @@ tvs_status fb_solve(tvs_problem* P, const tvs_fb_params* prm, float* x_io, tvs_m
         } else {
           TVS_TRY(fb_step(P, kind == FB_FISTA ? aux : xc, P->z, nullptr, fgamma, 0.f, s));
         }
+        const bool branch = kind != FB_FISTA && c == 1;  // overlap the record with the prox
         if (kind != FB_FISTA) {
+          cudaStream_t rs = s;
+          if (branch) {
+            CUDA_TRY(cudaEventRecord(C->fork_ev, s));
+            CUDA_TRY(cudaStreamWaitEvent(C->side, C->fork_ev, 0));
+            rs = C->side;
+          }
           CUDA_TRY(launch_reduce_record(P->part_a, na, P->part_b, nb, alpha, every, P->obj_dev,
                                         P->ts_dev, prm->f_star, prm->target_rel_gap, P->flags,
-                                        P->done_host_dev, nullptr, s));
-          TVS_TRY(track_distance(P, xc, prm->target_rel_dist, s));
+                                        P->done_host_dev, nullptr, rs));
+          TVS_TRY(track_distance(P, xc, prm->target_rel_dist, rs));
+          if (branch) CUDA_TRY(cudaEventRecord(C->join_ev, C->side));
         }
         if (c == 1) {
           int fin = 0;
@@ -718,6 +728,7 @@ tvs_status fb_solve(tvs_problem* P, const tvs_fb_params* prm, float* x_io, tvs_m
                                        fin != 0 ? P->dual[0] : nullptr, xc,
                                        kind == FB_FISTA ? aux : nullptr, P->beta_dev, P->flags + 2, s));
         }
+        if (branch) CUDA_TRY(cudaStreamWaitEvent(s, C->join_ev, 0));
         if (kind == FB_FISTA) {
           int a = 0, b = 0;
           TVS_TRY(objective_parts(P, xn, P->part_a, P->part_b, &a, &b, s));
@@ -1459,6 +1470,9 @@ tvs_status tvs_create(tvs_ctx** out, int device, void* cuda_stream) {
   cudaError_t e = cudaEventCreate(&C->ev_start);
   if (e == cudaSuccess) e = cudaEventCreate(&C->ev_stop);
   for (int i = 0; i < LAG && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&C->ring[i], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&C->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&C->fork_ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&C->join_ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMalloc(&C->red_out, sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&C->flags, 5 * sizeof(int));
   if (e == cudaSuccess) e = fgp_prepare_device();
@@ -1483,6 +1497,9 @@ tvs_status tvs_destroy(tvs_ctx* C) {
   if (C->ev_stop) cudaEventDestroy(C->ev_stop);
   for (auto& ev : C->ring)
     if (ev) cudaEventDestroy(ev);
+  if (C->fork_ev) cudaEventDestroy(C->fork_ev);
+  if (C->join_ev) cudaEventDestroy(C->join_ev);
+  if (C->side) cudaStreamDestroy(C->side);
   if (C->own_stream && C->stream) cudaStreamDestroy(C->stream);
   delete C;
   return TVS_OK;
