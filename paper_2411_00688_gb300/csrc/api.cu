@@ -809,10 +809,18 @@ tvs_status pd_solve(tvs_problem* P, const tvs_pd_params* prm, float* x_io, float
         } else {
           TVS_TRY(pd_backward(P, xc, P->z, nullptr, fs, 0.f, s));
         }
+        // on prox iterations the objective record runs beside the inner iterations
+        cudaStream_t rs = s;
+        if (c == 1) {
+          CUDA_TRY(cudaEventRecord(C->fork_ev, s));
+          CUDA_TRY(cudaStreamWaitEvent(C->side, C->fork_ev, 0));
+          rs = C->side;
+        }
         CUDA_TRY(launch_reduce_record(P->part_a, na, P->part_b, nb, alpha, every, P->obj_dev,
                                       P->ts_dev, prm->f_star, prm->target_rel_gap, P->flags,
-                                      P->done_host_dev, nullptr, s));
-        TVS_TRY(track_distance(P, xc, prm->target_rel_dist, s));
+                                      P->done_host_dev, nullptr, rs));
+        TVS_TRY(track_distance(P, xc, prm->target_rel_dist, rs));
+        if (c == 1) CUDA_TRY(cudaEventRecord(C->join_ev, C->side));
         if (c == 1) {
           int fin = 0;
           CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 0, s));
@@ -822,6 +830,7 @@ tvs_status pd_solve(tvs_problem* P, const tvs_pd_params* prm, float* x_io, float
                                        skip ? P->h : nullptr, (float)(p / sigma),
                                        fin != 0 ? P->dual[0] : nullptr, nullptr, nullptr, nullptr,
                                        nullptr, s));
+          CUDA_TRY(cudaStreamWaitEvent(s, C->join_ev, 0));  // the record read part_a
         }
         TVS_TRY(pd_forward(P, xn, ft, false, s));
         return TVS_OK;

@@ -156,8 +156,10 @@ joseph_bwd_kernel(GeomConsts g, const float4* __restrict__ angles, const float4*
         const float k0f = floorf(fr);
         const float f = fr - k0f;
         const int k0 = (int)k0f;
-        if (k0 == k) acc += (1.f - f) * __ldg(yrow + b);
-        else if (k0 + 1 == k) acc += f * __ldg(yrow + b);
+        // the projector's weight of this pixel on ray b (0 when the ray's two
+        // interpolation cells miss it), applied without a divergent branch
+        const float wgt = k0 == k ? 1.f - f : (k0 + 1 == k ? f : 0.f);
+        acc = fmaf(wgt, __ldg(yrow + b), acc);
       }
       total = fmaf(ang.z, acc, total);
     }

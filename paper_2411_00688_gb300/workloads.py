@@ -5,8 +5,8 @@ benchmark's headline one (python -m paper_2411_00688_gb300.workloads NAME ...).
   ct2d_512       PDHGSkip-2 p in {0.2, 0.05} vs PDHG, <= 2000 iterations, at sigma = tau with 50
                  inner iterations and at sigma = tau / 4 with 200; explicit preconditioned PDHG
                  (closed-form proxes) <= 20000 iterations
-  deblur2d_1024  explicit preconditioned PDHG, <= 20000 iterations (the ProxSkip / PGD /
-                 FISTA numbers of this workload come from the benchmark)
+  deblur2d_1024  PGD, FISTA and ProxSkip p in {0.5, 0.1, 0.05} at 50, 100 and 200 inner
+                 iterations (<= 1000 iterations); explicit preconditioned PDHG <= 20000
   denoise3d_512  ProxSkip p = 0.1 vs PGD, 30 inner, <= 200 iterations (FP32 / BF16 / FP16 dual)
   batch2d_256    256 uneven problems: one batched solve vs a loop of single solves
 
@@ -156,7 +156,24 @@ def deblur2d_1024():
     prob.set_data(b)
     _, ref = tvs.fista_solve(prob, b.clone(), 1.0, 3000, 100)  # gamma = 1/||A||^2 = 1
     f_star = float(np.nanmin(ref.objective))
-    return [_explicit(tvs, prob, b, torch.zeros_like(b), f_star, cfg.name)]
+    out = []
+    # ProxSkip at every probability of the configuration and PGD / FISTA with the
+    # same prox, at the configuration's 50 inner iterations and at 100 and 200 (a
+    # more accurate prox is what the small-p runs need at lambda = gamma alpha / p)
+    for n_inner in (cfg.n_inner, 100, 200):
+        runs = [("pgd", lambda ni=n_inner: tvs.pgd_solve(prob, b.clone(), 1.0, cfg.max_iter, ni, f_star=f_star,
+                                                           target=TARGET)),
+                ("fista", lambda ni=n_inner: tvs.fista_solve(prob, b.clone(), 1.0, cfg.max_iter, ni, f_star=f_star,
+                                                               target=TARGET))]
+        for p in cfg.ps:
+            runs.append((f"proxskip_p{p}", lambda p=p, ni=n_inner: tvs.proxskip_solve(
+                prob, b.clone(), 1.0, p, cfg.seed, cfg.max_iter, ni, f_star=f_star, target=TARGET)))
+        for name, fn in runs:
+            fn()
+            (_, tr), wall = _timed(fn)
+            out.append(_solve_record(name, tr, wall, f_star, workload=cfg.name, n_inner=n_inner))
+    out.append(_explicit(tvs, prob, b, torch.zeros_like(b), f_star, cfg.name))
+    return out
 
 
 def denoise3d_512(duals=("f32", "bf16", "f16")):
