@@ -2,7 +2,7 @@
 benchmark's headline one (python -m paper_2411_00688_gb300.workloads NAME ...).
 
   denoise2d_256  ProxSkip p = 0.1 vs PGD, 100 inner iterations, <= 500 iterations
-  ct2d_512       PDHGSkip-2 p in {0.2, 0.05} vs PDHG, <= 2000 iterations, at sigma = tau with 50
+  ct2d_512       PDHGSkip-2 and PDHGSkip-1 p in {0.2, 0.05} vs PDHG, <= 2000 iterations, at sigma = tau with 50
                  inner iterations and at sigma = tau / 4 with 200; explicit preconditioned PDHG
                  (closed-form proxes) <= 20000 iterations
   deblur2d_1024  PGD, FISTA and ProxSkip p in {0.5, 0.1, 0.05} at 50, 100 and 200 inner
@@ -122,6 +122,10 @@ def ct2d_512():
             prob, x0.clone(), zeros_sino.clone(), sg, ta, cfg.max_iter, ni, f_star=f_star, target=TARGET))]
         for p in cfg.ps:
             runs.append((f"pdhgskip_p{p}", lambda p=p, sg=sg, ta=ta, ni=n_inner: tvs.pdhgskip_solve(
+                prob, x0.clone(), zeros_sino.clone(), sg, ta, p, cfg.seed, cfg.max_iter, ni, f_star=f_star,
+                target=TARGET)))
+            # PDHGSkip-1 also skips both projector applications when theta_k = 0
+            runs.append((f"pdhgskip1_p{p}", lambda p=p, sg=sg, ta=ta, ni=n_inner: tvs.pdhgskip1_solve(
                 prob, x0.clone(), zeros_sino.clone(), sg, ta, p, cfg.seed, cfg.max_iter, ni, f_star=f_star,
                 target=TARGET)))
         for name, fn in runs:
