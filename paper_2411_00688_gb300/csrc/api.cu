@@ -1143,10 +1143,8 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
   for (int i = 0; i < n; ++i) {
     tvs_problem* P = probs[i];
     TVS_TRY(ensure_trace(P, K));
-    TVS_TRY(copy_in(P->x[0], x_io[i], P->n, mem, s));
-    CUDA_TRY(cudaMemsetAsync(P->dual[0], 0, dual_elem_bytes(dtype) * 2 * P->n, s));
-    CUDA_TRY(cudaMemsetAsync(P->h, 0, P->n * sizeof(float), s));
-    CUDA_TRY(cudaMemsetAsync(P->obj_dev, 0xff, sizeof(double) * (K + 1), s));
+    // host iterates are copied in here; device iterates by the set-up kernel below
+    if (mem == TVS_MEM_HOST) TVS_TRY(copy_in(P->x[0], x_io[i], P->n, mem, s));
     const int H = P->dims.ny, W = P->dims.nx;
     const double gamma = prm[i].gamma, p = prm[i].p, alpha = P->desc.alpha;
     BatchProb& D = desc[i];
@@ -1201,10 +1199,13 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
   const int n_blur = (int)blur_tiles.size();
   for (auto& D : desc)
     if (D.part_off < 0) D.part_off = n_blur + (-1 - D.part_off);
-  std::vector<unsigned char> coins((size_t)K * n);
-  for (int k = 0; k < K; ++k)
-    for (int i = 0; i < n; ++i) coins[(size_t)k * n + i] = (unsigned char)tvs_coin(prm[i].seed, prm[i].p, k);
   std::vector<BatchState> st0(n, BatchState{0, -1, 0, 0});
+  std::vector<unsigned long long> seeds(n);
+  std::vector<double> pvals(n);
+  for (int i = 0; i < n; ++i) {
+    seeds[i] = prm[i].seed;
+    pvals[i] = prm[i].p;
+  }
 
   BatchLaunch L{};
   L.n = n;
@@ -1212,7 +1213,17 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
   TVS_TRY(S.upload(st0, &L.state, s));
   TVS_TRY(S.upload(blur_tiles, (int4**)&L.blur_tiles, s));
   TVS_TRY(S.upload(ident_chunks, (int2**)&L.ident_chunks, s));
-  TVS_TRY(S.upload(coins, (unsigned char**)&L.coins, s));
+  {
+    // the coins of every problem and outer iteration, drawn on the device
+    unsigned long long* seeds_dev = nullptr;
+    double* p_dev = nullptr;
+    unsigned char* coins_dev = nullptr;
+    TVS_TRY(S.upload(seeds, &seeds_dev, s));
+    TVS_TRY(S.upload(pvals, &p_dev, s));
+    TVS_TRY(S.zeros<unsigned char>((size_t)K * n, &coins_dev, s));
+    CUDA_TRY(launch_batch_coins(seeds_dev, p_dev, n, K, coins_dev, s));
+    L.coins = coins_dev;
+  }
   TVS_TRY(S.upload(tile_range, (int2**)&L.tile_range, s));
   TVS_TRY(S.upload(chunk_range, (int2**)&L.chunk_range, s));
   TVS_TRY(S.zeros<int>((size_t)n + 1, &L.scan_tiles, s));
@@ -1235,6 +1246,8 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
     L.fin_grid = std::max(1, std::min(pointwise_blocks((size_t)L.n_all_chunks * 256), L.n_all_chunks));
   }
   TVS_TRY(S.zeros<int>(1, &L.kctr, s));
+  L.n_work = std::max(1, (N + batch_fgp_iters_per_launch() - 1) / batch_fgp_iters_per_launch());
+  TVS_TRY(S.zeros<int>((size_t)L.n_work, &L.work, s));
   TVS_TRY(S.zeros<Partial>((size_t)n_blur + ident_chunks.size(), &L.part_a, s));
   TVS_TRY(S.zeros<Partial>((size_t)n_blur + ident_chunks.size(), &L.part_b, s));
   unsigned long long* t0_dev = nullptr;
@@ -1254,6 +1267,12 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
   L.dtype = dtype;
   L.blur_radius = blur_radius;
   L.use_prox = N > 0;
+  float** x_dev_list = nullptr;  // the caller's device iterates, for the set-up and trace kernels
+  if (mem == TVS_MEM_DEVICE) {
+    std::vector<float*> xs(x_io, x_io + n);
+    TVS_TRY(S.upload(xs, &x_dev_list, s));
+  }
+  CUDA_TRY(launch_batch_init(L, (const float* const*)x_dev_list, K, s));
   CUDA_TRY(cudaEventRecord(C->ev_start, s));
   CUDA_TRY(launch_timestamp(t0_dev, s));
   GraphSet G;
@@ -1277,25 +1296,36 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
   }
   CUDA_TRY(launch_batch_final_objective(L, launched & 1, s));
   CUDA_TRY(cudaEventRecord(C->ev_stop, s));
-  CUDA_TRY(cudaStreamSynchronize(s));
+  // records of every problem packed on the device (and device results copied
+  // out), then brought back in four copies
+  double* obj_pack = nullptr;
+  unsigned long long* ts_pack = nullptr;
+  const size_t rows = (size_t)n * (K > 0 ? K : 1);
+  TVS_TRY(S.zeros<double>(rows, &obj_pack, s));
+  TVS_TRY(S.zeros<unsigned long long>(rows, &ts_pack, s));
+  CUDA_TRY(launch_batch_trace(L, K, obj_pack, ts_pack, mem == TVS_MEM_DEVICE ? x_dev_list : nullptr, s));
   std::vector<BatchState> st(n);
-  CUDA_TRY(cudaMemcpy(st.data(), L.state, sizeof(BatchState) * n, cudaMemcpyDeviceToHost));
+  std::vector<double> obj_all(rows);
+  std::vector<unsigned long long> ts_all(rows);
+  std::vector<unsigned char> coins((size_t)K * n);
   unsigned long long t0 = 0;
-  CUDA_TRY(cudaMemcpy(&t0, t0_dev, sizeof(t0), cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemcpyAsync(st.data(), L.state, sizeof(BatchState) * n, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(obj_all.data(), obj_pack, sizeof(double) * rows, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(ts_all.data(), ts_pack, sizeof(unsigned long long) * rows, cudaMemcpyDeviceToHost, s));
+  if (!coins.empty())
+    CUDA_TRY(cudaMemcpyAsync(coins.data(), L.coins, coins.size(), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(&t0, t0_dev, sizeof(t0), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
   float solve_ms = 0.f;
   CUDA_TRY(cudaEventElapsedTime(&solve_ms, C->ev_start, C->ev_stop));
   bool bad = false;
   for (int i = 0; i < n; ++i) {
     tvs_problem* P = probs[i];
     const int iters = st[i].iters;
-    TVS_TRY(copy_out(x_io[i], P->x[iters & 1], P->n, mem, s));
-    std::vector<double> obj(iters > 0 ? iters : 1);
-    std::vector<unsigned long long> ts(iters > 0 ? iters : 1);
-    if (iters > 0) {
-      CUDA_TRY(cudaMemcpy(obj.data(), P->obj_dev, sizeof(double) * iters, cudaMemcpyDeviceToHost));
-      CUDA_TRY(cudaMemcpy(ts.data(), P->ts_dev, sizeof(unsigned long long) * iters, cudaMemcpyDeviceToHost));
-      if (!is_fin(obj[iters - 1])) bad = true;
-    }
+    if (mem == TVS_MEM_HOST) TVS_TRY(copy_out(x_io[i], P->x[iters & 1], P->n, mem, s));
+    const double* obj = obj_all.data() + (size_t)i * K;
+    const unsigned long long* ts = ts_all.data() + (size_t)i * K;
+    if (iters > 0 && !is_fin(obj[iters - 1])) bad = true;
     if (traces) {
       tvs_trace* tr = &traces[i];
       int prox = 0;

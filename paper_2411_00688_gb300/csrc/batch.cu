@@ -61,19 +61,22 @@ batch_ident_step_kernel(const BatchProb* __restrict__ probs, BatchState* __restr
   const float* x = par ? P.x1 : P.x0;
   float* out = coin ? P.z : (par ? P.x0 : P.x1);
   const float ch = coin ? P.ch_prox : P.ch_skip;
-  const size_t npx = (size_t)P.H * P.W;
+  const size_t npx = (size_t)P.H * P.W, base = (size_t)e.y * CHUNK;
   FAcc acc_a, acc_b;
-  for (int t = threadIdx.x; t < CHUNK; t += 256) {
-    const size_t o = (size_t)e.y * CHUNK + t;
-    if (o >= npx) break;
-    const int gi = (int)P.fw.div((uint32_t)o), gj = (int)o - gi * P.W;
-    const float xc = __ldg(x + o), bb = __ldg(P.b + o);
-    const float r = xc - bb;
-    if (write_out) out[o] = fmaf(ch, __ldg(P.h + o), xc - P.gamma * r);
-    acc_a.add(0.5f * (r * r));
-    const float dy = gi < P.H - 1 ? __ldg(x + o + P.W) - xc : 0.f;
-    const float dx = gj < P.W - 1 ? __ldg(x + o + 1) - xc : 0.f;
-    acc_b.add(tv_term(0.f, dy, dx));
+  // predicated, fully unrolled: the loads of every pixel of the chunk are issued together
+#pragma unroll
+  for (int u = 0; u < CHUNK / 256; ++u) {
+    const size_t o = base + u * 256 + threadIdx.x;
+    if (o < npx) {
+      const int gi = (int)P.fw.div((uint32_t)o), gj = (int)o - gi * P.W;
+      const float xc = __ldg(x + o), bb = __ldg(P.b + o);
+      const float r = xc - bb;
+      if (write_out) out[o] = fmaf(ch, __ldg(P.h + o), xc - P.gamma * r);
+      acc_a.add(0.5f * (r * r));
+      const float dy = gi < P.H - 1 ? __ldg(x + o + P.W) - xc : 0.f;
+      const float dx = gj < P.W - 1 ? __ldg(x + o + 1) - xc : 0.f;
+      acc_b.add(tv_term(0.f, dy, dx));
+    }
   }
   block_sum2_store<256>(acc_a, acc_b, part_a, part_b, part_base + blockIdx.x);
 }
@@ -134,14 +137,18 @@ __device__ __forceinline__ int owner_of(const int* scan, int n, int w) {
 
 // Compacts the work of outer iteration k (one block): a problem takes part in the
 // prox of iteration k when it is still running and its coin is 1; its inner tiles
-// count only when lam > 0.  Writes exclusive scans of the tile and chunk counts.
+// count only when lam > 0.  Writes exclusive scans of the tile and chunk counts,
+// zeroes the work counters of the iteration's inner launches and advances the
+// outer iteration counter.
 __global__ void __launch_bounds__(1024)
 batch_active_kernel(const BatchProb* __restrict__ probs, const BatchState* __restrict__ state,
-                    const unsigned char* __restrict__ coins, int n, const int* __restrict__ kctr,
+                    const unsigned char* __restrict__ coins, int n, int* __restrict__ kctr,
                     const int2* __restrict__ tile_range, const int2* __restrict__ chunk_range,
-                    int* __restrict__ scan_tiles, int* __restrict__ scan_chunks) {
+                    int* __restrict__ scan_tiles, int* __restrict__ scan_chunks, int* __restrict__ work,
+                    int n_work) {
   pdl_enter();
   __shared__ int wt[32], wc[32];
+  for (int j = threadIdx.x; j < n_work; j += blockDim.x) work[j] = 0;
   const int k = *kctr, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int carry_t = 0, carry_c = 0;
   for (int base = 0; base < n; base += 1024) {
@@ -193,25 +200,33 @@ batch_active_kernel(const BatchProb* __restrict__ probs, const BatchState* __res
   if (threadIdx.x == 0) {
     scan_tiles[n] = carry_t;
     scan_chunks[n] = carry_c;
+    *kctr = k + 1;  // nothing later in the iteration reads k; every thread read it above
   }
 }
 
-// Persistent inner kernel: the grid strides over the compacted tiles of the
-// problems whose coin is 1 (no CTA is spent on skipping problems).  NN: 0 when
-// no problem of the batch has the non-negativity constraint, 1 when all have it,
-// 2 for a mix (both bodies compiled in).
+// Persistent inner kernel over the compacted tiles of the problems whose coin is 1
+// (no CTA is spent on skipping problems).  Each CTA starts on tile blockIdx.x and
+// then takes the next unclaimed tile from the launch's work counter (zeroed by
+// batch_active_kernel), so tiles of uneven cost (image borders, partial tiles)
+// balance over the grid instead of piling up on CTAs that a fixed stride keeps
+// handing the same tile column (the other resident CTAs of the SM cover the
+// counter's round trip after each tile).  NN: 0 when no problem of the batch has
+// the non-negativity constraint, 1 when all have it, 2 for a mix (both bodies
+// compiled in).
 #ifndef TVS_BATCH_FGP_MIN_CTAS
 #define TVS_BATCH_FGP_MIN_CTAS 3
 #endif
 template <typename T, int NN>
 __global__ void __launch_bounds__(256, TVS_BATCH_FGP_MIN_CTAS)
 batch_fgp_kernel(const BatchProb* __restrict__ probs, const int2* __restrict__ tile_range, const int* __restrict__ scan, int n, int q_in,
-                 TBBetas betas, int iters) {
+                 TBBetas betas, int iters, int* __restrict__ work) {
   pdl_enter();
   __shared__ int s_scan[SCAN_SMEM];
+  __shared__ int s_next[2];
   const int* sc = stage_scan(scan, n, s_scan);
   const int total = sc[n];
-  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+  int w = blockIdx.x, buf = 0;
+  while (w < total) {
     const int i = owner_of(sc, n, w);
     const BatchProb& P = probs[i];
     const int t = w - sc[i], fx = (P.W + BT_TW - 1) / BT_TW;
@@ -227,6 +242,12 @@ batch_fgp_kernel(const BatchProb* __restrict__ probs, const int2* __restrict__ t
     else
       fgp2d_rb_body<T, false, BT_TB, BT_CPL, BT_RPW>(P.z, pc, pp, pn, pnp, P.H, P.W, P.lam, P.inv_step, betas,
                                                      iters, tx, ty);
+    // two slots: slot buf is written again only after the next barrier, which every
+    // thread reaches after reading it
+    if (threadIdx.x == 0) s_next[buf] = (int)gridDim.x + atomicAdd(work, 1);
+    __syncthreads();
+    w = s_next[buf];
+    buf ^= 1;
   }
 }
 
@@ -248,31 +269,119 @@ batch_finalize_kernel(const BatchProb* __restrict__ probs, const int2* __restric
     T* home = (fin_pair && P.lam != 0.f) ? (T*)P.dual0 : nullptr;
     float* xo = par ? P.x0 : P.x1;
     const int H = P.H, W = P.W;
-    const size_t npx = (size_t)H * W;
-    for (int t = threadIdx.x; t < CHUNK; t += 256) {
-      const size_t o = (size_t)e.y * CHUNK + t;
-      if (o >= npx) break;
-      const int gi = (int)P.fw.div((uint32_t)o), gj = (int)o - gi * W;
-      float dv = 0.f;
-      if (gi < H - 1) dv += Elem<T>::ld(p + o);
-      if (gi > 0) dv -= Elem<T>::ld(p + o - W);
-      if (gj < W - 1) dv += Elem<T>::ld(p + npx + o);
-      if (gj > 0) dv -= Elem<T>::ld(p + npx + o - 1);
-      const float zz = __ldg(P.z + o);
-      float u = P.lam != 0.f ? zz + P.lam * dv : zz;
-      if (P.nonneg) u = fmaxf(u, 0.f);
-      xo[o] = u;
-      P.h[o] = P.h_coef * (u - zz);
-      if (home) {
-        home[o] = p[o];
-        home[npx + o] = p[npx + o];
+    const size_t npx = (size_t)H * W, base = (size_t)e.y * CHUNK;
+    // all loads of the chunk first (predicated, unrolled), then the stores, so the
+    // loads are not held behind stores the compiler cannot prove disjoint
+    constexpr int U = CHUNK / 256;
+    float dv[U], zz[U];
+    T c0[U], c1[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const size_t o = base + u * 256 + threadIdx.x;
+      dv[u] = 0.f;
+      zz[u] = 0.f;
+      if (o < npx) {
+        const int gi = (int)P.fw.div((uint32_t)o), gj = (int)o - gi * W;
+        float d = 0.f;
+        if (gi < H - 1) d += Elem<T>::ld(p + o);
+        if (gi > 0) d -= Elem<T>::ld(p + o - W);
+        if (gj < W - 1) d += Elem<T>::ld(p + npx + o);
+        if (gj > 0) d -= Elem<T>::ld(p + npx + o - 1);
+        dv[u] = d;
+        zz[u] = __ldg(P.z + o);
+        if (home) {
+          c0[u] = p[o];
+          c1[u] = p[npx + o];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const size_t o = base + u * 256 + threadIdx.x;
+      if (o < npx) {
+        float v = P.lam != 0.f ? zz[u] + P.lam * dv[u] : zz[u];
+        if (P.nonneg) v = fmaxf(v, 0.f);
+        xo[o] = v;
+        P.h[o] = P.h_coef * (v - zz[u]);
+        if (home) {
+          home[o] = c0[u];
+          home[npx + o] = c1[u];
+        }
       }
     }
   }
 }
 
-__global__ void batch_tick_kernel(int* kctr) {
-  pdl_enter(); *kctr += 1; }
+// Per-solve set-up of every problem, one block per pixel chunk: x_0 copied in (when
+// the caller's iterates live in device memory; x_src[i] is problem i's), the first
+// dual pair and h zeroed, the objective record (K + 1 entries) set to NaN.
+__global__ void __launch_bounds__(256)
+batch_init_kernel(const BatchProb* __restrict__ probs, const int2* __restrict__ chunk_range, int n,
+                  const float* const* __restrict__ x_src, int dual_bytes, int K) {
+  pdl_enter();
+  int lo = 0, hi = n;  // problem owning chunk blockIdx.x: largest i with first(i) <= blockIdx.x
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (chunk_range[mid].x <= (int)blockIdx.x) lo = mid;
+    else hi = mid;
+  }
+  const BatchProb& P = probs[lo];
+  const int c = (int)blockIdx.x - chunk_range[lo].x;
+  const size_t npx = (size_t)P.H * P.W, base = (size_t)c * CHUNK;
+  const float* src = x_src ? x_src[lo] : nullptr;
+#pragma unroll
+  for (int u = 0; u < CHUNK / 256; ++u) {
+    const size_t o = base + u * 256 + threadIdx.x;
+    if (o < npx) {
+      if (src) P.x0[o] = src[o];
+      P.h[o] = 0.f;
+      if (dual_bytes == 4) {
+        ((float*)P.dual0)[o] = 0.f;
+        ((float*)P.dual0)[npx + o] = 0.f;
+      } else {
+        ((unsigned short*)P.dual0)[o] = 0;
+        ((unsigned short*)P.dual0)[npx + o] = 0;
+      }
+    }
+  }
+  if (c == 0)
+    for (int k = threadIdx.x; k <= K; k += 256) P.obj[k] = __longlong_as_double(-1ll);
+}
+
+// theta_k of every problem for k = 0 .. K-1, as coins[k][i] (Algorithm 4's coin,
+// from problem i's seed and p).
+__global__ void __launch_bounds__(256)
+batch_coins_kernel(const unsigned long long* __restrict__ seeds, const double* __restrict__ ps, int n, int K,
+                   unsigned char* __restrict__ coins) {
+  pdl_enter();
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)K * n) return;
+  const int i = (int)(t % n);
+  coins[t] = (unsigned char)Philox4x64::coin(seeds[i], ps[i], (uint64_t)(t / n));
+}
+
+// After the solve, one block per problem: its objective and timestamp records
+// packed as rows of K entries, and (for device-memory iterates) its result copied
+// to x_dst[i].
+__global__ void __launch_bounds__(256)
+batch_trace_kernel(const BatchProb* __restrict__ probs, const BatchState* __restrict__ state, int K,
+                   double* __restrict__ obj_out, unsigned long long* __restrict__ ts_out,
+                   float* const* __restrict__ x_dst) {
+  pdl_enter();
+  const BatchProb& P = probs[blockIdx.x];
+  const int iters = state[blockIdx.x].iters;
+  const size_t row = (size_t)blockIdx.x * K;
+  for (int k = threadIdx.x; k < iters; k += blockDim.x) {
+    obj_out[row + k] = P.obj[k];
+    ts_out[row + k] = P.ts[k];
+  }
+  if (x_dst) {
+    const float* x = (iters & 1) ? P.x1 : P.x0;
+    float* dst = x_dst[blockIdx.x];
+    const size_t npx = (size_t)P.H * P.W;
+    for (size_t o = threadIdx.x; o < npx; o += blockDim.x) dst[o] = x[o];
+  }
+}
 
 }  // namespace
 
@@ -317,19 +426,20 @@ cudaError_t launch_batch_iteration(const BatchLaunch& L, int par, cudaStream_t s
                                                              L.n_blur_tiles);
   launch_kernel(batch_reduce_kernel, dim3(L.n), dim3(256), 0, s, L.probs, L.state, L.kctr, L.part_a, L.part_b, 0, L.done_host);
   launch_kernel(batch_active_kernel, dim3(1), dim3(1024), 0, s, L.probs, (const BatchState*)L.state, L.coins, L.n,
-                (const int*)L.kctr, L.tile_range, L.chunk_range, L.scan_tiles, L.scan_chunks);
+                L.kctr, L.tile_range, L.chunk_range, L.scan_tiles, L.scan_chunks, L.work,
+                L.n_work);
   int fin_pair = 0;  // pair holding p_N
   if (L.n_inner > 0 && L.use_prox) {
-    int q = 0;
-    for (int g = 1; g <= L.n_inner;) {
+    int q = 0, j = 0;
+    for (int g = 1; g <= L.n_inner; ++j) {
       const int it = L.n_inner - g + 1 < BT_TB ? L.n_inner - g + 1 : BT_TB;
       TBBetas b{};
-      for (int j = 0; j < it; ++j) b.b[j] = L.betas[g - 1 + j];
+      for (int m = 0; m < it; ++m) b.b[m] = L.betas[g - 1 + m];
       switch (L.dtype * 3 + L.nonneg_mode) {
 #define TVS_BF(IDX, T_, NN_)                                                                              \
   case IDX:                                                                                           \
     launch_kernel(batch_fgp_kernel<T_, NN_>, dim3(L.fgp_grid), dim3(256), 0, s, L.probs,                \
-                  L.tile_range, (const int*)L.scan_tiles, L.n, q, b, it);                            \
+                  L.tile_range, (const int*)L.scan_tiles, L.n, q, b, it, L.work + j);                \
     break;
         TVS_BF(0, float, 0) TVS_BF(1, float, 1) TVS_BF(2, float, 2)
         TVS_BF(3, __nv_bfloat16, 0) TVS_BF(4, __nv_bfloat16, 1) TVS_BF(5, __nv_bfloat16, 2)
@@ -356,7 +466,27 @@ cudaError_t launch_batch_iteration(const BatchLaunch& L, int par, cudaStream_t s
       launch_kernel(batch_finalize_kernel<__half>, dim3(L.fin_grid), dim3(256), 0, s, L.probs,
                     L.chunk_range, (const int*)L.scan_chunks, L.n, par, fin_pair);
   }
-  launch_kernel(batch_tick_kernel, dim3(1), dim3(1), 0, s, L.kctr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_init(const BatchLaunch& L, const float* const* x_src, int K, cudaStream_t s) {
+  launch_kernel(batch_init_kernel, dim3(L.n_all_chunks), dim3(256), 0, s, L.probs, L.chunk_range, L.n, x_src,
+                L.dtype == DUAL_F32 ? 4 : 2, K);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_coins(const unsigned long long* seeds, const double* ps, int n, int K,
+                               unsigned char* coins, cudaStream_t s) {
+  const long long total = (long long)K * n;
+  if (total == 0) return cudaSuccess;
+  launch_kernel(batch_coins_kernel, dim3((unsigned)((total + 255) / 256)), dim3(256), 0, s, seeds, ps, n, K, coins);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_trace(const BatchLaunch& L, int K, double* obj_out, unsigned long long* ts_out,
+                               float* const* x_dst, cudaStream_t s) {
+  launch_kernel(batch_trace_kernel, dim3(L.n), dim3(256), 0, s, L.probs, (const BatchState*)L.state, K, obj_out,
+                ts_out, x_dst);
   return cudaGetLastError();
 }
 

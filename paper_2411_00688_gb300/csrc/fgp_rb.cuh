@@ -175,13 +175,19 @@ __device__ __forceinline__ void fgp2d_rb_body_impl(const float* __restrict__ z, 
 // of two.  The per-value arithmetic is unchanged (a - b is formed as
 // fma(b, -1, a), which rounds exactly like the subtraction; a masked-out term is
 // added as zero instead of skipped, which changes no value), so it agrees bitwise
-// with the scalar body.  INTERIOR drops the Neumann masks as above.
+// with the scalar body.  The Neumann masks are split by direction: ROWM keeps the
+// row masks (the region meets the first or last image row), COLM the column masks
+// (first or last column); a region meeting neither is the interior case.  u is not
+// masked outside the image: an in-image cell reads u only of in-image cells (the
+// differences toward the last row / column are masked), and outside values never
+// reach an in-image cell (the div terms from row -1 / column -1 are masked), so
+// they stay finite and unused.
 __device__ __forceinline__ float2 p2_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 __device__ __forceinline__ float2 p2_mask(float2 v, bool mx, bool my) {
   return make_float2(mx ? v.x : 0.f, my ? v.y : 0.f);
 }
 
-template <typename T, bool NONNEG, int TB, int RPW, bool INTERIOR>
+template <typename T, bool NONNEG, int TB, int RPW, bool ROWM, bool COLM>
 __device__ __forceinline__ void fgp2d_rb_body_packed(const float* __restrict__ z, const T* __restrict__ pc,
                                                      const T* __restrict__ pp, T* __restrict__ pn,
                                                      T* __restrict__ pnp, int H, int W, float lam,
@@ -201,14 +207,14 @@ __device__ __forceinline__ void fgp2d_rb_body_packed(const float* __restrict__ z
 #pragma unroll
   for (int r = 0; r < RPW; ++r) {
     const int gi = gi0 + r;
-    row_in[r] = INTERIOR || (gi >= 0 && gi < H);
-    row_dn[r] = INTERIOR || gi < H - 1;
-    row_up[r] = INTERIOR || gi > 0;
+    row_in[r] = !ROWM || (gi >= 0 && gi < H);
+    row_dn[r] = !ROWM || gi < H - 1;
+    row_up[r] = !ROWM || gi > 0;
   }
   // column masks of the lane's left (.x) and right (.y) cell
-  const bool in0 = INTERIOR || (gj0 >= 0 && gj0 < W), in1 = INTERIOR || (gj0 + 1 >= 0 && gj0 + 1 < W);
-  const bool rt0 = INTERIOR || gj0 < W - 1, rt1 = INTERIOR || gj0 + 1 < W - 1;
-  const bool lf0 = INTERIOR || gj0 > 0, lf1 = INTERIOR || gj0 + 1 > 0;
+  const bool in0 = !COLM || (gj0 >= 0 && gj0 < W), in1 = !COLM || (gj0 + 1 >= 0 && gj0 + 1 < W);
+  const bool rt0 = !COLM || gj0 < W - 1, rt1 = !COLM || gj0 + 1 < W - 1;
+  const bool lf0 = !COLM || gj0 > 0, lf1 = !COLM || gj0 + 1 > 0;
   const float b0 = betas.b[0];
   const float2 bb = make_float2(b0, b0);
 #pragma unroll
@@ -257,19 +263,21 @@ __device__ __forceinline__ void fgp2d_rb_body_packed(const float* __restrict__ z
       const float rx_left = __shfl_up_sync(0xffffffffu, Rx[r].y, 1);
       const float2 up = r > 0 ? Ry[r - 1] : ry_above;
       const float2 lf = make_float2(rx_left, Rx[r].x);
-      float2 dv;
-      if (INTERIOR) {
-        dv = p2_sub(Ry[r], up);
-        dv = __fadd2_rn(dv, Rx[r]);
-        dv = p2_sub(dv, lf);
-      } else {
-        dv = p2_sub(p2_mask(Ry[r], row_dn[r], row_dn[r]), p2_mask(up, row_up[r], row_up[r]));
-        dv = __fadd2_rn(dv, p2_mask(Rx[r], rt0, rt1));
-        dv = p2_sub(dv, p2_mask(lf, lf0, lf1));
+      float2 ry = Ry[r], upv = up, rx = Rx[r], lfv = lf;
+      if (ROWM) {
+        ry = p2_mask(ry, row_dn[r], row_dn[r]);
+        upv = p2_mask(upv, row_up[r], row_up[r]);
       }
+      if (COLM) {
+        rx = p2_mask(rx, rt0, rt1);
+        lfv = p2_mask(lfv, lf0, lf1);
+      }
+      float2 dv = p2_sub(ry, upv);
+      dv = __fadd2_rn(dv, rx);
+      dv = p2_sub(dv, lfv);
       float2 u = __ffma2_rn(lam2, dv, Z[r]);
       if (NONNEG) u = make_float2(fmaxf(u.x, 0.f), fmaxf(u.y, 0.f));
-      U[r] = INTERIOR ? u : p2_mask(u, row_in[r] && in0, row_in[r] && in1);
+      U[r] = u;
     }
     edge_u2[warp][lane] = U[0];
     __syncthreads();
@@ -285,10 +293,8 @@ __device__ __forceinline__ void fgp2d_rb_body_packed(const float* __restrict__ z
       const float2 dn = r < RPW - 1 ? U[r + 1] : u_below;
       const float2 rt = make_float2(uc.y, u_right);
       float2 gy = p2_sub(dn, uc), gx = p2_sub(rt, uc);
-      if (!INTERIOR) {
-        gy = p2_mask(gy, row_dn[r], row_dn[r]);
-        gx = p2_mask(gx, rt0, rt1);
-      }
+      if (ROWM) gy = p2_mask(gy, row_dn[r], row_dn[r]);
+      if (COLM) gx = p2_mask(gx, rt0, rt1);
       const float2 qy = __ffma2_rn(inv2, gy, Ry[r]);
       const float2 qx = __ffma2_rn(inv2, gx, Rx[r]);
       const float2 nrm2 = __ffma2_rn(qy, qy, __fmul2_rn(qx, qx));
@@ -334,14 +340,21 @@ __device__ __forceinline__ void fgp2d_rb_body(const float* __restrict__ z, const
                                               int tile_x, int tile_y) {
   constexpr int RW = 32 * CPL, RH = 8 * RPW, TW = RW - 2 * TB, TH = RH - 2 * TB;
   const int r0 = tile_y * TH - TB, c0 = tile_x * TW - TB;
-  const bool interior = r0 >= 1 && r0 + RH <= H - 1 && c0 >= 1 && c0 + RW <= W - 1;
+  const bool rows_in = r0 >= 1 && r0 + RH <= H - 1, cols_in = c0 >= 1 && c0 + RW <= W - 1;
+  const bool interior = rows_in && cols_in;
   if constexpr (CPL == 2) {
     if (interior)
-      fgp2d_rb_body_packed<T, NONNEG, TB, RPW, true>(z, pc, pp, pn, pnp, H, W, lam, inv_step, betas, iters,
-                                                     tile_x, tile_y);
+      fgp2d_rb_body_packed<T, NONNEG, TB, RPW, false, false>(z, pc, pp, pn, pnp, H, W, lam, inv_step, betas,
+                                                             iters, tile_x, tile_y);
+    else if (cols_in)
+      fgp2d_rb_body_packed<T, NONNEG, TB, RPW, true, false>(z, pc, pp, pn, pnp, H, W, lam, inv_step, betas,
+                                                            iters, tile_x, tile_y);
+    else if (rows_in)
+      fgp2d_rb_body_packed<T, NONNEG, TB, RPW, false, true>(z, pc, pp, pn, pnp, H, W, lam, inv_step, betas,
+                                                            iters, tile_x, tile_y);
     else
-      fgp2d_rb_body_packed<T, NONNEG, TB, RPW, false>(z, pc, pp, pn, pnp, H, W, lam, inv_step, betas, iters,
-                                                      tile_x, tile_y);
+      fgp2d_rb_body_packed<T, NONNEG, TB, RPW, true, true>(z, pc, pp, pn, pnp, H, W, lam, inv_step, betas,
+                                                           iters, tile_x, tile_y);
   } else {
     if (interior)
       fgp2d_rb_body_impl<T, NONNEG, TB, CPL, RPW, true>(z, pc, pp, pn, pnp, H, W, lam, inv_step, betas, iters,

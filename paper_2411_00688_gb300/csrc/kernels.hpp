@@ -229,7 +229,7 @@ struct BatchLaunch {
   int n_fgp_tiles;          // blocked inner tiles of all problems
   int n_all_chunks;         // pixel chunks of all problems
   const unsigned char* coins;  // [K][n]
-  int* kctr;                   // outer iteration counter (device)
+  int* kctr;                   // outer iteration counter (device; advanced by the compaction kernel)
   Partial *part_a, *part_b;
   int* done_host;              // n flags in mapped host memory
   int n_inner, dtype;
@@ -243,6 +243,8 @@ struct BatchLaunch {
   int* scan_chunks;            // [n + 1]: the same for their chunks
   int fgp_grid, fin_grid;      // persistent grid sizes of the inner and finalisation kernels
   int nonneg_mode;             // 0: no problem constrained, 1: all, 2: mixed
+  int* work;                   // [n_work]: tile counter of each inner launch of an iteration
+  int n_work;
 };
 int batch_fgp_tile_w();
 int batch_fgp_tile_h();
@@ -253,6 +255,16 @@ int batch_fgp_resident_ctas();  // SMs x resident CTAs of the batched inner kern
 cudaError_t launch_batch_iteration(const BatchLaunch& L, int par, cudaStream_t s);
 // F(x_k) of the problems still running, recorded as their final trace entry.
 cudaError_t launch_batch_final_objective(const BatchLaunch& L, int par, cudaStream_t s);
+// Per-solve set-up of every problem (x_0 from x_src[i] when x_src is not null,
+// first dual pair and h zeroed, objective record set to NaN).
+cudaError_t launch_batch_init(const BatchLaunch& L, const float* const* x_src, int K, cudaStream_t s);
+// coins[k * n + i] = theta_k of problem i for k < K.
+cudaError_t launch_batch_coins(const unsigned long long* seeds, const double* ps, int n, int K,
+                               unsigned char* coins, cudaStream_t s);
+// Objective / timestamp records packed as [n][K] rows; results copied to x_dst[i]
+// when x_dst is not null.
+cudaError_t launch_batch_trace(const BatchLaunch& L, int K, double* obj_out, unsigned long long* ts_out,
+                               float* const* x_dst, cudaStream_t s);
 
 // ---- parallel-beam projector (ct.cu) ----
 struct CTGeom {

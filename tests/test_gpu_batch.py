@@ -179,3 +179,21 @@ def test_batch_full_size_sampled(tvs, ctx):
         x1, t1 = tvs.proxskip_solve(probs[k], cuda(bs[k]), 1.0, ps[k], seeds[k], K, N)
         assert rel_l2(host(xs[k]), host(x1)) <= 1e-5
         np.testing.assert_allclose(traces[k].objective, t1.objective, rtol=1e-6)
+
+
+def test_batch_host_memory_matches_device_memory(tvs, ctx):
+    """Iterates in host memory (copied in and out around the solve) give the same
+    results and traces as iterates in device memory."""
+    K, N = 12, 8
+    probs, xs_dev, data = _build(tvs, ctx)
+    xs_host = [d[0].copy() for d in data]
+    ps = [s[4] for s in SPECS]
+    seeds = [s[5] for s in SPECS]
+    gam = [1.0] * len(SPECS)
+    xs_dev, tr_dev = tvs.proxskip_solve_batch(ctx, probs, xs_dev, gam, ps, seeds, K, N)
+    xs_host, tr_host = tvs.proxskip_solve_batch(ctx, probs, xs_host, gam, ps, seeds, K, N)
+    for k in range(len(SPECS)):
+        np.testing.assert_array_equal(xs_host[k], host(xs_dev[k]))
+        np.testing.assert_array_equal(tr_host[k].objective, tr_dev[k].objective)
+        np.testing.assert_array_equal(tr_host[k].coins, tr_dev[k].coins)
+        assert tr_host[k].iters_run == tr_dev[k].iters_run == K
