@@ -45,9 +45,9 @@ FGP_BYTES_PER_PX = 28        # read z (4) + p_k (8) + p_{k-1} (8), write p_{k+1}
 # `dram__bytes_read.sum + dram__bytes_write.sum`.  It describes only the kernel
 # sources and launch configuration it was taken on: the bench line carries it only
 # while the hash of those sources and the autotuned configuration still match.
-FGP_TRAFFIC = {"config": [4, 2, 104], "bytes": 20360793,
+FGP_TRAFFIC = {"config": [4, 2, 104], "bytes": 20388923,
                "sources": ["common.cuh", "fgp_rb.cuh", "fgp.cu"],
-               "sha256": "26cb04fea115b338494962523d32b8e48e8eaadb016a252cfcd6206cb5919262"}
+               "sha256": "f85ca1745d3605c853a0aa5dea49ed6e9cdea435ef0ff130694d79ce466959b7"}
 # Iterations / prox calls this workload's ProxSkip solve needs to reach the target
 # (from the solver's trace); used only to scale the CPU oracle sample.
 REF_ITERS_DEFAULT, REF_PROX_DEFAULT = 260, 130
