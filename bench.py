@@ -47,7 +47,7 @@ FGP_BYTES_PER_PX = 28        # read z (4) + p_k (8) + p_{k-1} (8), write p_{k+1}
 # while the hash of those sources and the autotuned configuration still match.
 FGP_TRAFFIC = {"config": [4, 2, 104], "bytes": 20388923,
                "sources": ["common.cuh", "fgp_rb.cuh", "fgp.cu"],
-               "sha256": "f85ca1745d3605c853a0aa5dea49ed6e9cdea435ef0ff130694d79ce466959b7"}
+               "sha256": "9400c3397cae3c57988378ed31992c99ddbed0ba82af16c2e3bad042fc8cb953"}
 # Iterations / prox calls this workload's ProxSkip solve needs to reach the target
 # (from the solver's trace); used only to scale the CPU oracle sample.
 REF_ITERS_DEFAULT, REF_PROX_DEFAULT = 260, 130

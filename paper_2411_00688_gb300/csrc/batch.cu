@@ -216,38 +216,62 @@ batch_active_kernel(const BatchProb* __restrict__ probs, const BatchState* __res
 #ifndef TVS_BATCH_FGP_MIN_CTAS
 #define TVS_BATCH_FGP_MIN_CTAS 3
 #endif
+// The tile being processed, as thread 0 prepared it (problem lookup and
+// descriptor loads done once per tile): the body reads it at the start and again
+// in its store phase, so its pointers and sizes need no registers in between.
+template <typename T>
+struct TileRec {
+  const float* z;
+  const T *pc, *pp;
+  T *pn, *pnp;
+  int H, W, tx, ty, nonneg, valid;
+  float lam, inv_step;
+};
+
 template <typename T, int NN>
 __global__ void __launch_bounds__(256, TVS_BATCH_FGP_MIN_CTAS)
 batch_fgp_kernel(const BatchProb* __restrict__ probs, const int2* __restrict__ tile_range, const int* __restrict__ scan, int n, int q_in,
                  TBBetas betas, int iters, int* __restrict__ work) {
   pdl_enter();
   __shared__ int s_scan[SCAN_SMEM];
-  __shared__ int s_next[2];
+  __shared__ int s_w;
+  __shared__ TileRec<T> rec;
+  if (threadIdx.x == 0) s_w = blockIdx.x;
   const int* sc = stage_scan(scan, n, s_scan);
-  const int total = sc[n];
-  int w = blockIdx.x, buf = 0;
-  while (w < total) {
-    const int i = owner_of(sc, n, w);
-    const BatchProb& P = probs[i];
-    const int t = w - sc[i], fx = (P.W + BT_TW - 1) / BT_TW;
-    const int ty = t / fx, tx = t - ty * fx;
-    const T* pc = (const T*)(q_in ? P.dual2 : P.dual0);
-    const T* pp = (const T*)(q_in ? P.dual3 : P.dual1);
-    if (betas.b[0] == 0.f) pp = pc;  // first iteration of a prox call: p_{k-1} unused
-    T* pn = (T*)(q_in ? P.dual0 : P.dual2);
-    T* pnp = (T*)(q_in ? P.dual1 : P.dual3);
-    if (NN == 1 || (NN == 2 && P.nonneg))
-      fgp2d_rb_body<T, true, BT_TB, BT_CPL, BT_RPW>(P.z, pc, pp, pn, pnp, P.H, P.W, P.lam, P.inv_step, betas,
-                                                    iters, tx, ty);
-    else
-      fgp2d_rb_body<T, false, BT_TB, BT_CPL, BT_RPW>(P.z, pc, pp, pn, pnp, P.H, P.W, P.lam, P.inv_step, betas,
-                                                     iters, tx, ty);
-    // two slots: slot buf is written again only after the next barrier, which every
-    // thread reaches after reading it
-    if (threadIdx.x == 0) s_next[buf] = (int)gridDim.x + atomicAdd(work, 1);
+  __syncthreads();
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int w = s_w, total = sc[n];
+      rec.valid = w < total;
+      if (w < total) {
+        const int i = owner_of(sc, n, w);
+        const BatchProb& P = probs[i];
+        const int t = w - sc[i], fx = (P.W + BT_TW - 1) / BT_TW;
+        rec.ty = t / fx;
+        rec.tx = t - rec.ty * fx;
+        rec.z = P.z;
+        rec.pc = (const T*)(q_in ? P.dual2 : P.dual0);
+        // first iteration of a prox call: p_{k-1} unused
+        rec.pp = betas.b[0] == 0.f ? rec.pc : (const T*)(q_in ? P.dual3 : P.dual1);
+        rec.pn = (T*)(q_in ? P.dual0 : P.dual2);
+        rec.pnp = (T*)(q_in ? P.dual1 : P.dual3);
+        rec.H = P.H;
+        rec.W = P.W;
+        rec.nonneg = P.nonneg;
+        rec.lam = P.lam;
+        rec.inv_step = P.inv_step;
+      }
+    }
     __syncthreads();
-    w = s_next[buf];
-    buf ^= 1;
+    if (!rec.valid) break;
+    if (NN == 1 || (NN == 2 && rec.nonneg))
+      fgp2d_rb_body<T, true, BT_TB, BT_CPL, BT_RPW>(rec.z, rec.pc, rec.pp, rec.pn, rec.pnp, rec.H, rec.W, rec.lam,
+                                                    rec.inv_step, betas, iters, rec.tx, rec.ty);
+    else
+      fgp2d_rb_body<T, false, BT_TB, BT_CPL, BT_RPW>(rec.z, rec.pc, rec.pp, rec.pn, rec.pnp, rec.H, rec.W, rec.lam,
+                                                     rec.inv_step, betas, iters, rec.tx, rec.ty);
+    if (threadIdx.x == 0) s_w = (int)gridDim.x + atomicAdd(work, 1);
+    __syncthreads();  // every thread is done with rec before thread 0 rewrites it
   }
 }
 

@@ -322,8 +322,10 @@ fgp2d_rb_kernel(const float* __restrict__ z, const T* __restrict__ pc, const T* 
                 T* __restrict__ pn, T* __restrict__ pnp, int H, int W, float lam, float inv_step,
                 TBBetas betas, int iters) {
   pdl_enter();
-  fgp2d_rb_body<T, NONNEG, TB, CPL, RPW>(z, pc, pp, pn, pnp, H, W, lam, inv_step, betas, iters,
-                                          blockIdx.x, blockIdx.y);
+  T* const dst_p = pn;
+  T* const dst_r = pnp;
+  const int tx = blockIdx.x, ty = blockIdx.y;
+  fgp2d_rb_body<T, NONNEG, TB, CPL, RPW>(z, pc, pp, dst_p, dst_r, H, W, lam, inv_step, betas, iters, tx, ty);
 }
 
 // ---------------------------------------------------------------------------

@@ -189,10 +189,10 @@ __device__ __forceinline__ float2 p2_mask(float2 v, bool mx, bool my) {
 
 template <typename T, bool NONNEG, int TB, int RPW, bool ROWM, bool COLM>
 __device__ __forceinline__ void fgp2d_rb_body_packed(const float* __restrict__ z, const T* __restrict__ pc,
-                                                     const T* __restrict__ pp, T* __restrict__ pn,
-                                                     T* __restrict__ pnp, int H, int W, float lam,
-                                                     float inv_step, const TBBetas& betas, int iters,
-                                                     int tile_x, int tile_y) {
+                                                     const T* __restrict__ pp, T* const& pn, T* const& pnp,
+                                                     const int& H, const int& W, float lam, float inv_step,
+                                                     const TBBetas& betas, int iters, const int& tile_x,
+                                                     const int& tile_y) {
   constexpr int NW = 8, CPL = 2;
   constexpr int RW = 32 * CPL, RH = NW * RPW;
   constexpr int TW = RW - 2 * TB, TH = RH - 2 * TB;
@@ -315,29 +315,39 @@ __device__ __forceinline__ void fgp2d_rb_body_packed(const float* __restrict__ z
     if (!last) edge_ry2[warp][lane] = Ry[RPW - 1];
     __syncthreads();
   }
+  // The store phase takes the tile's geometry and destinations afresh through the
+  // references (kernel parameters, or a shared-memory tile record read after the
+  // last barrier), so none of them stays live in registers across the iterations.
+  const int Hs = H, Ws = W;
+  const size_t ns = (size_t)Hs * Ws;
+  const int gi0s = tile_y * TH - TB + warp * RPW, gj0s = tile_x * TW - TB + lane * CPL;
+  T* const dst_p = pn;
+  T* const dst_r = pnp;
 #pragma unroll
   for (int r = 0; r < RPW; ++r) {
-    const int a = warp * RPW + r;
-    if (a < TB || a >= TB + TH || !row_in[r]) continue;
-    const size_t o = (size_t)(gi0 + r) * W + gj0;
+    const int a = warp * RPW + r, gi = gi0s + r;
+    if (a < TB || a >= TB + TH || (ROWM && (gi < 0 || gi >= Hs))) continue;
+    const size_t o = (size_t)gi * Ws + gj0s;
 #pragma unroll
     for (int q = 0; q < CPL; ++q) {
-      const int c = lane * CPL + q;
-      if (c < TB || c >= TB + TW || !(q ? in1 : in0)) continue;
-      Elem<T>::st(pn + o + q, q ? Py[r].y : Py[r].x);
-      Elem<T>::st(pn + n + o + q, q ? Px[r].y : Px[r].x);
-      Elem<T>::st(pnp + o + q, q ? Ry[r].y : Ry[r].x);
-      Elem<T>::st(pnp + n + o + q, q ? Rx[r].y : Rx[r].x);
+      const int c = lane * CPL + q, gj = gj0s + q;
+      if (c < TB || c >= TB + TW || (COLM && (gj < 0 || gj >= Ws))) continue;
+      Elem<T>::st(dst_p + o + q, q ? Py[r].y : Py[r].x);
+      Elem<T>::st(dst_p + ns + o + q, q ? Px[r].y : Px[r].x);
+      Elem<T>::st(dst_r + o + q, q ? Ry[r].y : Ry[r].x);
+      Elem<T>::st(dst_r + ns + o + q, q ? Rx[r].y : Rx[r].x);
     }
   }
 }
 
+// pn, pnp, H, W and the tile coordinates are taken by reference: the two-column
+// body reads them again for its store phase (see there).
 template <typename T, bool NONNEG, int TB, int CPL, int RPW>
 __device__ __forceinline__ void fgp2d_rb_body(const float* __restrict__ z, const T* __restrict__ pc,
-                                              const T* __restrict__ pp, T* __restrict__ pn,
-                                              T* __restrict__ pnp, int H, int W, float lam,
-                                              float inv_step, const TBBetas& betas, int iters,
-                                              int tile_x, int tile_y) {
+                                              const T* __restrict__ pp, T* const& pn, T* const& pnp,
+                                              const int& H, const int& W, float lam, float inv_step,
+                                              const TBBetas& betas, int iters, const int& tile_x,
+                                              const int& tile_y) {
   constexpr int RW = 32 * CPL, RH = 8 * RPW, TW = RW - 2 * TB, TH = RH - 2 * TB;
   const int r0 = tile_y * TH - TB, c0 = tile_x * TW - TB;
   const bool rows_in = r0 >= 1 && r0 + RH <= H - 1, cols_in = c0 >= 1 && c0 + RW <= W - 1;
