@@ -204,18 +204,6 @@ batch_active_kernel(const BatchProb* __restrict__ probs, const BatchState* __res
   }
 }
 
-// Persistent inner kernel over the compacted tiles of the problems whose coin is 1
-// (no CTA is spent on skipping problems).  Each CTA starts on tile blockIdx.x and
-// then takes the next unclaimed tile from the launch's work counter (zeroed by
-// batch_active_kernel), so tiles of uneven cost (image borders, partial tiles)
-// balance over the grid instead of piling up on CTAs that a fixed stride keeps
-// handing the same tile column (the other resident CTAs of the SM cover the
-// counter's round trip after each tile).  NN: 0 when no problem of the batch has
-// the non-negativity constraint, 1 when all have it, 2 for a mix (both bodies
-// compiled in).
-#ifndef TVS_BATCH_FGP_MIN_CTAS
-#define TVS_BATCH_FGP_MIN_CTAS 3
-#endif
 // The tile being processed, as thread 0 prepared it (problem lookup and
 // descriptor loads done once per tile): the body reads it at the start and again
 // in its store phase, so its pointers and sizes need no registers in between.
@@ -228,10 +216,22 @@ struct TileRec {
   float lam, inv_step;
 };
 
+// Persistent inner kernel over the compacted tiles of the problems whose coin is 1
+// (no CTA is spent on skipping problems).  Each CTA starts on tile blockIdx.x and
+// then takes the next unclaimed tile from the launch's work counter (zeroed by
+// batch_active_kernel), so tiles of uneven cost (image borders, partial tiles)
+// balance over the grid instead of piling up on CTAs that a fixed stride keeps
+// handing the same tile column (the other resident CTAs of the SM cover the
+// counter's round trip after each tile).  NN: 0 when no problem of the batch has
+// the non-negativity constraint, 1 when all have it, 2 for a mix (both bodies
+// compiled in).
+#ifndef TVS_BATCH_FGP_MIN_CTAS
+#define TVS_BATCH_FGP_MIN_CTAS 3
+#endif
 template <typename T, int NN>
 __global__ void __launch_bounds__(256, TVS_BATCH_FGP_MIN_CTAS)
-batch_fgp_kernel(const BatchProb* __restrict__ probs, const int2* __restrict__ tile_range, const int* __restrict__ scan, int n, int q_in,
-                 TBBetas betas, int iters, int* __restrict__ work) {
+batch_fgp_kernel(const BatchProb* __restrict__ probs, const int* __restrict__ scan, int n, int q_in, TBBetas betas,
+                 int iters, int* __restrict__ work) {
   pdl_enter();
   __shared__ int s_scan[SCAN_SMEM];
   __shared__ int s_w;
@@ -463,7 +463,7 @@ cudaError_t launch_batch_iteration(const BatchLaunch& L, int par, cudaStream_t s
 #define TVS_BF(IDX, T_, NN_)                                                                              \
   case IDX:                                                                                           \
     launch_kernel(batch_fgp_kernel<T_, NN_>, dim3(L.fgp_grid), dim3(256), 0, s, L.probs,                \
-                  L.tile_range, (const int*)L.scan_tiles, L.n, q, b, it, L.work + j);                \
+                  (const int*)L.scan_tiles, L.n, q, b, it, L.work + j);                              \
     break;
         TVS_BF(0, float, 0) TVS_BF(1, float, 1) TVS_BF(2, float, 2)
         TVS_BF(3, __nv_bfloat16, 0) TVS_BF(4, __nv_bfloat16, 1) TVS_BF(5, __nv_bfloat16, 2)
