@@ -18,7 +18,7 @@ namespace {
 
 constexpr int BT_TB = 4, BT_CPL = 2, BT_RPW = 4;  // blocked inner kernel of the batch
 constexpr int BT_TW = 32 * BT_CPL - 2 * BT_TB, BT_TH = 8 * BT_RPW - 2 * BT_TB;
-constexpr int CHUNK = 1024;                        // pixels per pointwise work item
+constexpr int CHUNK = 2048;                        // pixels per pointwise work item
 
 __device__ __forceinline__ bool active(const BatchState& st) { return st.done == 0; }
 
