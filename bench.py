@@ -45,6 +45,9 @@ FGP_BYTES_PER_PX = 28        # read z (4) + p_k (8) + p_{k-1} (8), write p_{k+1}
 # `dram__bytes_read.sum + dram__bytes_write.sum`.  It describes only the kernel
 # sources and launch configuration it was taken on: the bench line carries it only
 # while the hash of those sources and the autotuned configuration still match.
+WORKLOAD = ("deblur2d_1024: 1024x1024, 40 ellipses, 9x9 Gaussian sigma 2, noise 0.01, alpha 0.02, gamma 1, "
+            "ProxSkip p 0.5 seed 0, 50 FGP iterations per prox, stop at relative objective gap 1e-4 "
+            "(max 1000 iterations)")
 FGP_TRAFFIC = {"config": [4, 2, 104], "bytes": 20388923,
                "sources": ["common.cuh", "fgp_rb.cuh", "fgp.cu"],
                "sha256": "9400c3397cae3c57988378ed31992c99ddbed0ba82af16c2e3bad042fc8cb953"}
@@ -353,9 +356,7 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "deblur2d_1024: 1024x1024, 40 ellipses, 9x9 Gaussian sigma 2, noise 0.01, "
-                               "alpha 0.02, gamma 1, ProxSkip p 0.5 seed 0, 50 FGP iterations per prox, "
-                               "stop at relative objective gap 1e-4 (max 1000 iterations)",
+        "config": {"workload": WORKLOAD,
                    "parallelism": f"replicas x{world}", "l2": "flushed between steps (256 MB write)",
                    "f_star": f_star},
         "time_to_target_device_s": statistics.mean(t.time_to_target_s for t in ps_tr),
@@ -440,7 +441,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "deblur2d_1024 (see the GPU arm)", "parallelism": "cpu"},
+        "config": {"workload": WORKLOAD, "parallelism": "cpu"},
         "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
