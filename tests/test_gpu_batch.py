@@ -197,3 +197,28 @@ def test_batch_host_memory_matches_device_memory(tvs, ctx):
         np.testing.assert_array_equal(tr_host[k].objective, tr_dev[k].objective)
         np.testing.assert_array_equal(tr_host[k].coins, tr_dev[k].coins)
         assert tr_host[k].iters_run == tr_dev[k].iters_run == K
+
+
+def test_batch_many_problems_uses_global_scan(tvs, ctx):
+    """More problems than the inner kernel's shared-memory copy of the work scan
+    holds (2047): the kernels search the scan in device memory.  Every problem
+    must still follow its own single solve."""
+    import torch
+    n, K, N = 2100, 3, 4
+    g = np.random.default_rng(21)
+    probs, xs, bs = [], [], []
+    for i in range(n):
+        H, W = int(g.integers(3, 9)), int(g.integers(3, 9))
+        b = cuda(g.random((H, W)).astype(np.float32))
+        probs.append(tvs.Problem(ctx, b, 0.05 + 0.001 * (i % 7)))
+        bs.append(b)
+        xs.append(b.clone())
+    ps = [0.5 + 0.2 * (i % 3) for i in range(n)]
+    xs, traces = tvs.proxskip_solve_batch(ctx, probs, xs, [1.0] * n, ps, list(range(n)), K, N)
+    for i in list(range(0, n, 97)) + [n - 1]:
+        x1, t1 = tvs.proxskip_solve(probs[i], bs[i].clone(), 1.0, ps[i], i, K, N)
+        assert list(traces[i].coins) == list(t1.coins)
+        assert rel_l2(host(xs[i]), host(x1)) <= 1e-5
+    for p in probs:
+        p.close()
+    torch.cuda.synchronize()
