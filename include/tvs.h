@@ -209,8 +209,10 @@ tvs_status tvs_fgp_config(tvs_ctx* ctx, int ndim, const int dims[3], tvs_dual_dt
  * for their own pool, or that run beside a thread capturing a CUDA graph in
  * global mode (where cudaMalloc is refused).  It computes exactly what tv_prox
  * computes, without a context and without allocating or freeing anything: the
- * working dual fields live in one array of TVS_NOALLOC_SCRATCH_BYTES that the
- * library image places on every GPU that loads it (held until the process exits).
+ * working dual fields live in one array of TVS_NOALLOC_SCRATCH_BYTES inside the
+ * library's device image.  CUDA loads that image onto a device lazily (by
+ * default), so the array takes its device memory when the first call on that
+ * device looks up its address, and keeps it until the process exits.
  *
  * Arguments are those of tv_prox, on the current device, plus the cudaStream_t
  * to launch on (NULL = the default stream); the call synchronises that stream
@@ -219,8 +221,10 @@ tvs_status tvs_fgp_config(tvs_ctx* ctx, int ndim, const int dims[3], tvs_dual_dt
  * larger request returns TVS_EUNSUPPORTED without launching anything.  Invalid
  * arguments give TVS_EINVAL, CUDA failures TVS_ECUDA; no message is recorded
  * for tvs_last_error().  The first call on a device looks up the array's device
- * address (and sets kernel attributes) with that device current; make it before
- * any stream capture begins.  All calls on a device share the array, which keeps
+ * address (and sets kernel attributes) with that device current; make it -- a
+ * call with n_iter = 0 on a 1 x 1 image will do -- before the application
+ * reserves the device's memory for its own pool and before any stream capture
+ * begins.  All calls on a device share the array, which keeps
  * the last call's contents (the cold-start dual is cleared on every call): calls
  * whose GPU work overlaps -- from several host threads or several streams --
  * race on it and must be serialised by the caller. */

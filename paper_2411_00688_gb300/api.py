@@ -209,19 +209,47 @@ def tvs_objective(prob: Problem, x) -> float:
     return out.value
 
 
+_DUAL_TORCH = {"f32": "float32", "bf16": "bfloat16", "f16": "float16"}
+
+
+def _prox_args(z, u, dual, dual_state):
+    """Checked C arguments of the TV-prox entry points: (dims, ndim, dual pointer).
+
+    z and u: contiguous float32 CUDA tensors of one 2D (H, W) or 3D (D, H, W) shape
+    on the current device; dual_state (optional): a contiguous tensor of the dual
+    type with shape (ndim,) + z.shape on the same device."""
+    torch = _torch()
+    if dual not in L.DUAL:
+        raise ValueError(f"dual must be one of {sorted(L.DUAL)}")
+    for name, t in (("z", z), ("u", u)):
+        if not _is_cuda_tensor(t) or t.dtype != torch.float32 or not t.is_contiguous():
+            raise ValueError(f"{name}: expected a contiguous float32 CUDA tensor")
+    shape = tuple(z.shape)
+    if len(shape) not in (2, 3):
+        raise ValueError("z must be 2D or 3D")
+    if tuple(u.shape) != shape:
+        raise ValueError("u must have z's shape")
+    dev = torch.cuda.current_device()
+    if z.device.index != dev or u.device.index != dev:
+        raise ValueError("z and u must be on the current CUDA device")
+    ds = None
+    if dual_state is not None:
+        want = getattr(torch, _DUAL_TORCH[dual])
+        if (not _is_cuda_tensor(dual_state) or dual_state.dtype != want or not dual_state.is_contiguous()
+                or tuple(dual_state.shape) != (len(shape),) + shape or dual_state.device.index != dev):
+            raise ValueError(f"dual_state: expected a contiguous {want} CUDA tensor of shape "
+                             f"{(len(shape),) + shape} on the current device")
+        ds = C.c_void_p(dual_state.data_ptr())
+    dims = (C.c_int * 3)(*(list(reversed(shape)) + [1] * (3 - len(shape))))
+    return dims, len(shape), ds
+
+
 def tv_prox(ctx: Context, z, u, lam: float, n_iter: int, dual: str = "f32", dual_state=None,
             nonneg: bool = False):
     """u = prox_{lam TV}(z) on device tensors (2D (H, W) or 3D (D, H, W))."""
+    dims, ndim, ds = _prox_args(z, u, dual, dual_state)
     _sync_torch()
-    shape = tuple(z.shape)
-    if len(shape) == 2:
-        dims = (C.c_int * 3)(shape[1], shape[0], 1)
-    elif len(shape) == 3:
-        dims = (C.c_int * 3)(shape[2], shape[1], shape[0])
-    else:
-        raise ValueError("z must be 2D or 3D")
-    ds = C.c_void_p(dual_state.data_ptr()) if dual_state is not None else None
-    L.check(L.lib().tv_prox(ctx.handle, len(shape), dims, C.c_void_p(z.data_ptr()),
+    L.check(L.lib().tv_prox(ctx.handle, ndim, dims, C.c_void_p(z.data_ptr()),
                             C.c_void_p(u.data_ptr()), float(lam), int(n_iter), L.DUAL[dual], ds,
                             int(bool(nonneg))))
     return u
@@ -264,16 +292,11 @@ def tv_prox_noalloc(z, u, lam: float, n_iter: int, dual: str = "f32", dual_state
     than the fixed array holds).
     """
     torch = _torch()
-    shape = tuple(z.shape)
-    if len(shape) == 2:
-        dims = (C.c_int * 3)(shape[1], shape[0], 1)
-    elif len(shape) == 3:
-        dims = (C.c_int * 3)(shape[2], shape[1], shape[0])
-    else:
-        raise ValueError("z must be 2D or 3D")
-    ds = C.c_void_p(dual_state.data_ptr()) if dual_state is not None else None
+    if z.data_ptr() == u.data_ptr():
+        return L.TVS_EINVAL
+    dims, ndim, ds = _prox_args(z, u, dual, dual_state)
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
-    return int(L.lib().tv_prox_noalloc(len(shape), dims, C.c_void_p(z.data_ptr()), C.c_void_p(u.data_ptr()),
+    return int(L.lib().tv_prox_noalloc(ndim, dims, C.c_void_p(z.data_ptr()), C.c_void_p(u.data_ptr()),
                                        float(lam), int(n_iter), L.DUAL[dual], ds, int(bool(nonneg)), stream))
 
 

@@ -1566,8 +1566,8 @@ tvs_status tvs_problem_create(tvs_ctx* C, const tvs_problem_desc* desc, const fl
   if (op.kind == TVS_OP_PARALLEL_BEAM &&
       (D.nx != D.ny || op.n_angles < 1 || op.n_det < 1 || !(op.pixel_size > 0) || !(op.det_spacing > 0)))
     return fail(TVS_EINVAL, "parallel beam needs a square image, n_angles, n_det >= 1 and positive spacings");
-  const size_t n = (size_t)D.nx * D.ny * D.nz;
-  if (n > ((size_t)1 << 34)) return fail(TVS_EINVAL, "image too large");
+  size_t n = 0;
+  if (!pixels_within(D.nx, D.ny, D.nz, kMaxPixels, &n)) return fail(TVS_EINVAL, "image too large");
   CUDA_TRY(cudaSetDevice(C->device));
   tvs_problem* P = new tvs_problem();
   P->ctx = C;
@@ -1749,7 +1749,8 @@ tvs_status tv_prox(tvs_ctx* C, int ndim, const int dims[3], const float* z, floa
   d.ny = dims[1];
   d.nz = ndim == 3 ? dims[2] : 1;
   d.ndim = ndim;
-  const size_t n = d.n();
+  size_t n = 0;
+  if (!pixels_within(d.nx, d.ny, d.nz, kMaxPixels, &n)) return fail(TVS_EINVAL, "image too large");
   const size_t plane_bytes = dual_elem_bytes(dual) * ndim * n;
   const size_t need = plane_bytes * (dual_state ? 3 : 4);
   cudaStream_t s = C->stream;
@@ -1795,8 +1796,10 @@ tvs_status tv_prox_gap(tvs_ctx* C, int ndim, const int dims[3], const float* z, 
   d.ny = dims[1];
   d.nz = ndim == 3 ? dims[2] : 1;
   d.ndim = ndim;
+  size_t n = 0;
+  if (!pixels_within(d.nx, d.ny, d.nz, kMaxPixels, &n)) return fail(TVS_EINVAL, "image too large");
   cudaStream_t s = C->stream;
-  const size_t nb = (size_t)rof_gap_blocks(d.n());
+  const size_t nb = (size_t)rof_gap_blocks(n);
   if (nb > C->parts_cap) {
     dfree(C->parts);
     C->bytes -= C->parts_cap * sizeof(Partial);
@@ -1825,10 +1828,12 @@ tvs_status tvs_fgp_config(tvs_ctx* C, int ndim, const int dims[3], tvs_dual_dtyp
   d.ny = dims[1];
   d.nz = ndim == 3 ? dims[2] : 1;
   d.ndim = ndim;
+  size_t n = 0;
+  if (!pixels_within(d.nx, d.ny, d.nz, kMaxPixels, &n)) return fail(TVS_EINVAL, "image too large");
   FgpConfig c;
   if (ndim == 2) {
     // tune on a scratch image and scratch dual fields of this shape
-    const size_t n = d.n(), plane_bytes = dual_elem_bytes(dual) * 2 * n;
+    const size_t plane_bytes = dual_elem_bytes(dual) * 2 * n;
     const size_t need = plane_bytes * 4 + n * sizeof(float);
     cudaStream_t s = C->stream;
     if (need > C->prox_scratch_bytes) {

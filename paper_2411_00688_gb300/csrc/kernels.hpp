@@ -12,6 +12,19 @@ struct Dims {
   size_t n() const { return (size_t)nx * ny * nz; }
 };
 
+// Largest pixel count any entry point accepts.
+constexpr size_t kMaxPixels = (size_t)1 << 34;
+
+// nx * ny * nz without wrap-around: false when the product of the (positive)
+// sides exceeds cap, true with *n set otherwise.
+inline bool pixels_within(int nx, int ny, int nz, size_t cap, size_t* n) {
+  if (nx < 1 || ny < 1 || nz < 1) return false;
+  const size_t a = (size_t)nx * (size_t)ny;  // < 2^62
+  if (a > cap || (size_t)nz > cap / a) return false;
+  *n = a * (size_t)nz;
+  return true;
+}
+
 enum DualType { DUAL_F32 = 0, DUAL_BF16 = 1, DUAL_F16 = 2 };
 
 // floor(n / d) for 0 <= n < 2^31 by one multiply and shift (division by an

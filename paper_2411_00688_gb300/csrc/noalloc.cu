@@ -9,11 +9,13 @@
 // context is needed and nothing is allocated or freed, on the device or on the
 // host.
 //
-// The array is a file-scope __device__ variable, so every GPU that loads the
-// library holds TVS_NOALLOC_SCRATCH_BYTES of it until the process exits.  Host
-// code cannot use the variable's name as a device address; the first call on a
-// device (with that device current) asks the runtime for the address once and
-// keeps it.  All calls on a device share the array and it keeps the previous
+// The array is a file-scope __device__ variable of TVS_NOALLOC_SCRATCH_BYTES.  A
+// device holds it from the moment CUDA loads this file's device image there --
+// with the default lazy module loading, at the first call's address lookup on
+// that device -- until the process exits.  Host code cannot use the variable's
+// name as a device address; the first call on a device (with that device
+// current) asks the runtime for the address once and keeps it, so that call
+// belongs before the application reserves the device's memory for itself.  All calls on a device share the array and it keeps the previous
 // call's contents: the part that must start at zero (the cold-start dual) is
 // cleared on every call, and calls whose work overlaps on the GPU race on it.
 #include <mutex>
@@ -81,9 +83,13 @@ extern "C" tvs_status tv_prox_noalloc(int ndim, const int dims[3], const float* 
   d.ny = dims[1];
   d.nz = ndim == 3 ? dims[2] : 1;
   d.ndim = ndim;
-  const size_t plane_bytes = dual_elem_bytes(dual) * (size_t)ndim * d.n();
-  const size_t need = plane_bytes * (dual_state ? 3 : 4);
-  if (need > kScratchBytes) return TVS_EUNSUPPORTED;  // larger than the static scratch
+  // Pixels that fit in the static scratch, bounded before any product is formed
+  // so that no size wraps around.
+  const size_t planes = (size_t)ndim * (dual_state ? 3 : 4);
+  const size_t max_px = kScratchBytes / (dual_elem_bytes(dual) * planes);
+  size_t n = 0;
+  if (!pixels_within(d.nx, d.ny, d.nz, max_px, &n)) return TVS_EUNSUPPORTED;
+  const size_t plane_bytes = dual_elem_bytes(dual) * (size_t)ndim * n;
 
   void* base = nullptr;
   tvs_status st = scratch_for_current_device(&base);

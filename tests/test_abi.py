@@ -76,3 +76,28 @@ def test_struct_layout_matches_c(tmp_path, built_lib):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+@pytest.mark.parametrize("dims,ndim,warm_too", [((1 << 30, 1 << 30, 1), 2, True),
+                                                ((1 << 30, 1 << 30, 1 << 30), 3, True),
+                                                ((1 << 16, 1 << 16, 1 << 16), 3, True),
+                                                ((1024, 1366, 1), 2, True),
+                                                ((1025, 1024, 1), 2, False)])
+def test_noalloc_rejects_oversized_requests_before_any_cuda_call(built_lib, dims, ndim, warm_too):
+    """Sizes whose scratch would exceed the static array -- including products of
+    the sides that wrap around 64 bits -- are refused with TVS_EUNSUPPORTED by
+    arithmetic alone: the call returns before touching CUDA (this machine has no
+    GPU), so nothing can have been launched.  The pointers are never dereferenced.
+    A cold start needs four FP32 dual planes per axis (1025 x 1024 is over the
+    32 MiB limit), a caller-owned dual three (1024 x 1366 is over it)."""
+    lib = ctypes.CDLL(built_lib)
+    fn = lib.tv_prox_noalloc
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_void_p, ctypes.c_void_p,
+                   ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                   ctypes.c_void_p]
+    d = (ctypes.c_int * 3)(*dims)
+    assert fn(ndim, d, ctypes.c_void_p(256), ctypes.c_void_p(512), 0.1, 5, 0, None, 0, None) == 6
+    if warm_too:
+        assert fn(ndim, d, ctypes.c_void_p(256), ctypes.c_void_p(512), 0.1, 5, 0, ctypes.c_void_p(1024), 0,
+                  None) == 6

@@ -84,3 +84,34 @@ def test_noalloc_rejects_sizes_beyond_the_scratch(tvs):
     torch.cuda.synchronize()
     assert bool((u == 7.0).all())                           # nothing was launched
     assert tvs.tv_prox_noalloc(z, z, 0.1, 5) == 1           # aliasing: TVS_EINVAL
+
+
+def test_noalloc_leaves_device_memory_unchanged(tvs):
+    """The property the entry point exists for: after its first call on a device
+    (which places the static array there), further calls of several sizes, cold
+    and warm-started, change the device's free memory by nothing.  A context-based
+    tv_prox on a fresh context, the control, does allocate."""
+    import torch
+    shapes = [(512, 700), (1024, 1024), (9, 33, 40), (1, 1)]
+    zs = [_image(s, 40 + i) for i, s in enumerate(shapes)]
+    us = [torch.empty_like(z) for z in zs]
+    state = torch.zeros((2,) + shapes[0], device="cuda")
+    assert tvs.tv_prox_noalloc(zs[0], us[0], 0.1, 0) == 0           # first call: set-up
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for rep in range(2):
+        for z, u in zip(zs, us):
+            assert tvs.tv_prox_noalloc(z, u, 0.2, 11) == 0
+        assert tvs.tv_prox_noalloc(zs[0], us[0], 0.2, 7, dual_state=state) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    ctx = tvs.Context(0)
+    try:
+        u = torch.empty_like(zs[1])
+        tvs.tv_prox(ctx, zs[1], u, 0.2, 11)
+        torch.cuda.synchronize()
+        free2, _ = torch.cuda.mem_get_info()
+        assert free2 < free1 - 16 * 2 ** 20
+    finally:
+        ctx.close()
