@@ -1,0 +1,405 @@
+/*
+ * tvo.c -- the oracle's 2D/3D TV prox, Gaussian blur, objective and
+ * forward-backward solvers (PGD, FISTA, ProxSkip) written out in plain FP64 C.
+ *
+ * Test and measurement infrastructure only: it restates, loop for loop, what
+ * oracle/tv.py, oracle/operators.py and oracle/solvers.py compute (and is
+ * checked against them to 1e-12 by tests/test_oracle_c.py), so that full-size
+ * oracle runs -- the reference optimum of a 1024 x 1024 deblurring problem, the
+ * CPU baseline timed on every host core -- finish in minutes instead of hours.
+ * OpenMP spreads each pass over image rows; the arithmetic per pixel is that of
+ * the numpy code (sums over the image are reduced in a different order).  It
+ * shares nothing with the CUDA library.
+ *
+ * Conventions (Eq. 5, Section 2.1): component a of D u differentiates along
+ * array axis a (slowest first) with a zero last difference (Neumann); div = -D^T;
+ * TV(u) = sum_i |(D u)_i|_2.  The TV prox prox_{lam TV}(z) runs the accelerated
+ * dual projected gradient (AProjGD of Section 2.2 with the momentum of
+ * Algorithm 3) on the unit-ball dual: t_1 = 1, r_1 = p_0 (the warm start),
+ *   u = P_X(z + lam div r_k),  p_k = P_B(r_k + D u / (4 ndim lam)),
+ *   t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2,
+ *   r_{k+1} = p_k + ((t_k - 1) / t_{k+1}) (p_k - p_{k-1}),
+ * and returns u = P_X(z + lam div p_N) with p_N as the next warm start.
+ * The blur is the separable, unit-sum sampled Gaussian with half-sample
+ * symmetric extension (Section 3.1); its adjoint is formed by scattering.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct {
+  int ndim;
+  long n0, n1, n2; /* slowest .. fastest; n0 = 1 for 2D */
+} tvo_shape;
+
+static tvo_shape mk_shape(int ndim, const long* s) {
+  tvo_shape sh;
+  sh.ndim = ndim;
+  if (ndim == 2) {
+    sh.n0 = 1;
+    sh.n1 = s[0];
+    sh.n2 = s[1];
+  } else {
+    sh.n0 = s[0];
+    sh.n1 = s[1];
+    sh.n2 = s[2];
+  }
+  return sh;
+}
+
+/* D u: ndim planes, plane a differentiating along the a-th slowest axis. */
+static void grad_sh(tvo_shape sh, const double* u, double* g) {
+  const long n = sh.n0 * sh.n1 * sh.n2, HW = sh.n1 * sh.n2, W = sh.n2;
+  double* gz = sh.ndim == 3 ? g : NULL;
+  double* gy = sh.ndim == 3 ? g + n : g;
+  double* gx = gy + n;
+#pragma omp parallel for schedule(static)
+  for (long r = 0; r < sh.n0 * sh.n1; ++r) {
+    const long k = r / sh.n1, i = r % sh.n1;
+    for (long j = 0; j < W; ++j) {
+      const long o = r * W + j;
+      if (gz) gz[o] = k < sh.n0 - 1 ? u[o + HW] - u[o] : 0.0;
+      gy[o] = i < sh.n1 - 1 ? u[o + W] - u[o] : 0.0;
+      gx[o] = j < W - 1 ? u[o + 1] - u[o] : 0.0;
+    }
+  }
+}
+
+/* div p = -D^T p: sum_a ( p_a[i] [i_a < n_a - 1] - p_a[i - e_a] [i_a > 0] ). */
+static void div_sh(tvo_shape sh, const double* p, double* out) {
+  const long n = sh.n0 * sh.n1 * sh.n2, HW = sh.n1 * sh.n2, W = sh.n2;
+  const double* pz = sh.ndim == 3 ? p : NULL;
+  const double* py = sh.ndim == 3 ? p + n : p;
+  const double* px = py + n;
+#pragma omp parallel for schedule(static)
+  for (long r = 0; r < sh.n0 * sh.n1; ++r) {
+    const long k = r / sh.n1, i = r % sh.n1;
+    for (long j = 0; j < W; ++j) {
+      const long o = r * W + j;
+      double d = 0.0;
+      if (pz) {
+        if (k < sh.n0 - 1) d += pz[o];
+        if (k > 0) d -= pz[o - HW];
+      }
+      if (i < sh.n1 - 1) d += py[o];
+      if (i > 0) d -= py[o - W];
+      if (j < W - 1) d += px[o];
+      if (j > 0) d -= px[o - 1];
+      out[o] = d;
+    }
+  }
+}
+
+void tvo_grad(int ndim, const long* shape, const double* u, double* g) {
+  grad_sh(mk_shape(ndim, shape), u, g);
+}
+
+void tvo_div(int ndim, const long* shape, const double* p, double* out) {
+  div_sh(mk_shape(ndim, shape), p, out);
+}
+
+static double tv_sh(tvo_shape sh, const double* u, double* g) {
+  const long n = sh.n0 * sh.n1 * sh.n2;
+  grad_sh(sh, u, g);
+  double s = 0.0;
+#pragma omp parallel for reduction(+ : s) schedule(static)
+  for (long o = 0; o < n; ++o) {
+    double q = 0.0;
+    for (int a = 0; a < sh.ndim; ++a) q += g[a * n + o] * g[a * n + o];
+    s += sqrt(q);
+  }
+  return s;
+}
+
+/* Isotropic TV(u); g is scratch of ndim * n doubles. */
+double tvo_tv(int ndim, const long* shape, const double* u, double* g) {
+  return tv_sh(mk_shape(ndim, shape), u, g);
+}
+
+/* prox_{lam TV}(z) by n_iter AProjGD iterations; p: warm start in (zeros for a
+ * cold start), p_N out; u: the result.  Returns 0, or -1 if memory ran out. */
+int tvo_fgp_prox(int ndim, const long* shape, const double* z, double lam, int n_iter, double* p,
+                 int nonneg, double* u) {
+  const tvo_shape sh = mk_shape(ndim, shape);
+  const long n = sh.n0 * sh.n1 * sh.n2, nd = (long)ndim * n;
+  if (lam == 0.0) {
+    for (long o = 0; o < n; ++o) u[o] = nonneg ? fmax(z[o], 0.0) : z[o];
+    return 0;
+  }
+  double* r = (double*)malloc(sizeof(double) * nd);
+  double* p_prev = (double*)malloc(sizeof(double) * nd);
+  double* g = (double*)malloc(sizeof(double) * nd);
+  double* dv = (double*)malloc(sizeof(double) * n);
+  if (!r || !p_prev || !g || !dv) {
+    free(r);
+    free(p_prev);
+    free(g);
+    free(dv);
+    return -1;
+  }
+  const double L = 4.0 * ndim;
+  memcpy(r, p, sizeof(double) * nd);       /* r_1 = p_0 */
+  memcpy(p_prev, p, sizeof(double) * nd);  /* p_0 */
+  double t = 1.0;                          /* t_1 */
+  for (int it = 0; it < n_iter; ++it) {
+    div_sh(sh, r, dv);
+#pragma omp parallel for schedule(static)
+    for (long o = 0; o < n; ++o) {
+      const double v = z[o] + lam * dv[o];
+      u[o] = nonneg ? fmax(v, 0.0) : v;
+    }
+    grad_sh(sh, u, g);
+    const double t_new = (1.0 + sqrt(1.0 + 4.0 * t * t)) / 2.0;
+    const double beta = (t - 1.0) / t_new;
+#pragma omp parallel for schedule(static)
+    for (long o = 0; o < n; ++o) {
+      double q[3], nrm2 = 0.0;
+      for (int a = 0; a < ndim; ++a) {
+        q[a] = r[a * n + o] + g[a * n + o] / (L * lam);
+        nrm2 += q[a] * q[a];
+      }
+      const double den = fmax(1.0, sqrt(nrm2));
+      for (int a = 0; a < ndim; ++a) {
+        const double pn = q[a] / den;
+        r[a * n + o] = pn + beta * (pn - p_prev[a * n + o]);
+        p_prev[a * n + o] = pn;
+      }
+    }
+    t = t_new;
+  }
+  memcpy(p, p_prev, sizeof(double) * nd);
+  div_sh(sh, p, dv);
+  for (long o = 0; o < n; ++o) {
+    const double v = z[o] + lam * dv[o];
+    u[o] = nonneg ? fmax(v, 0.0) : v;
+  }
+  free(r);
+  free(p_prev);
+  free(g);
+  free(dv);
+  return 0;
+}
+
+/* ------------------------------------------------------------------ blur */
+static long reflect(long j, long n) {
+  j %= 2 * n;
+  if (j < 0) j += 2 * n;
+  return j >= n ? 2 * n - 1 - j : j;
+}
+
+/* out = A u: taps w[0..2R] along x (axis 1), then along y (axis 0). */
+static void blur_fwd(long H, long W, const double* w, int R, const double* u, double* tmp, double* out) {
+#pragma omp parallel for schedule(static)
+  for (long i = 0; i < H; ++i)
+    for (long j = 0; j < W; ++j) {
+      double s = 0.0;
+      for (int k = 0; k <= 2 * R; ++k) s += w[k] * u[i * W + reflect(j + k - R, W)];
+      tmp[i * W + j] = s;
+    }
+#pragma omp parallel for schedule(static)
+  for (long i = 0; i < H; ++i)
+    for (long j = 0; j < W; ++j) {
+      double s = 0.0;
+      for (int k = 0; k <= 2 * R; ++k) s += w[k] * tmp[reflect(i + k - R, H) * W + j];
+      out[i * W + j] = s;
+    }
+}
+
+/* out = A^T y by scattering: every tap of every output sample is added back to
+ * the input it came from, first along y (axis 0), then along x (axis 1). */
+static void blur_adj(long H, long W, const double* w, int R, const double* y, double* tmp, double* out) {
+  memset(tmp, 0, sizeof(double) * H * W);
+  /* columns are independent: blocks of 64 of them per thread, each element still
+   * receiving its contributions in the order (tap k, then source row i) */
+#pragma omp parallel for schedule(static)
+  for (long j0 = 0; j0 < W; j0 += 64) {
+    const long j1 = j0 + 64 < W ? j0 + 64 : W;
+    for (int k = 0; k <= 2 * R; ++k)
+      for (long i = 0; i < H; ++i) {
+        double* dst = tmp + reflect(i + k - R, H) * W;
+        for (long j = j0; j < j1; ++j) dst[j] += w[k] * y[i * W + j];
+      }
+  }
+  memset(out, 0, sizeof(double) * H * W);
+#pragma omp parallel for schedule(static)
+  for (long i = 0; i < H; ++i)
+    for (int k = 0; k <= 2 * R; ++k)
+      for (long j = 0; j < W; ++j) out[i * W + reflect(j + k - R, W)] += w[k] * tmp[i * W + j];
+}
+
+void tvo_blur(long H, long W, const double* w, int R, const double* u, double* out, int adjoint) {
+  double* tmp = (double*)malloc(sizeof(double) * H * W);
+  if (!tmp) return;
+  if (adjoint)
+    blur_adj(H, W, w, R, u, tmp, out);
+  else
+    blur_fwd(H, W, w, R, u, tmp, out);
+  free(tmp);
+}
+
+/* ------------------------------------------------------------------ solvers */
+/* min_x 1/2 ||A x - b||^2 + alpha TV(x) with A the identity (R = 0) or the blur
+ * with taps w[0..2R] (2D only); 3D problems take the identity. */
+typedef struct {
+  tvo_shape sh;
+  long n;
+  const double* w;
+  int R;
+  const double* b;
+  double alpha;
+  int nonneg;
+  double *t1, *t2, *t3, *g; /* scratch: 3 images, ndim planes */
+} prob_t;
+
+static void op_fwd(prob_t* P, const double* x, double* y) {
+  if (P->R == 0)
+    memcpy(y, x, sizeof(double) * P->n);
+  else
+    blur_fwd(P->sh.n1, P->sh.n2, P->w, P->R, x, P->t3, y);
+}
+
+static void op_adj(prob_t* P, const double* x, double* y) {
+  if (P->R == 0)
+    memcpy(y, x, sizeof(double) * P->n);
+  else
+    blur_adj(P->sh.n1, P->sh.n2, P->w, P->R, x, P->t3, y);
+}
+
+/* grad f(x) = A^T (A x - b) into out. */
+static void grad_f(prob_t* P, const double* x, double* out) {
+  op_fwd(P, x, P->t1);
+  for (long o = 0; o < P->n; ++o) P->t1[o] -= P->b[o];
+  op_adj(P, P->t1, out);
+}
+
+static double objective(prob_t* P, const double* x) {
+  op_fwd(P, x, P->t1);
+  double s = 0.0;
+#pragma omp parallel for reduction(+ : s) schedule(static)
+  for (long o = 0; o < P->n; ++o) {
+    const double r = P->t1[o] - P->b[o];
+    s += r * r;
+  }
+  return 0.5 * s + P->alpha * tv_sh(P->sh, x, P->g);
+}
+
+double tvo_objective(int ndim, const long* shape, const double* w, int R, const double* b, double alpha,
+                     const double* x) {
+  prob_t P;
+  P.sh = mk_shape(ndim, shape);
+  P.n = P.sh.n0 * P.sh.n1 * P.sh.n2;
+  P.w = w;
+  P.R = ndim == 2 ? R : 0;
+  P.b = b;
+  P.alpha = alpha;
+  P.nonneg = 0;
+  P.t1 = (double*)malloc(sizeof(double) * P.n);
+  P.t3 = (double*)malloc(sizeof(double) * P.n);
+  P.g = (double*)malloc(sizeof(double) * P.n * ndim);
+  double v = NAN;
+  if (P.t1 && P.t3 && P.g) v = objective(&P, x);
+  free(P.t1);
+  free(P.t3);
+  free(P.g);
+  return v;
+}
+
+/* kind 0: PGD (Algorithm 2); 1: FISTA (Algorithm 3, Beck-Teboulle form);
+ * 2: ProxSkip (Algorithm 4) with the coin of iteration k in coins[k].
+ * x: x_0 in, last iterate out.  dual: the warm-start TV dual (ndim planes, zeros
+ * for a fresh solve), kept across prox calls and returned.  obj (may be NULL):
+ * F(x_{k+1}) per iteration.  With f_star > 0 the solve stops after the first
+ * iteration whose (F - f_star)/f_star <= target.  Returns the number of
+ * iterations run (>= 0), or -1 if memory ran out; *prox_calls receives the prox
+ * evaluations among them. */
+int tvo_fb_solve(int kind, int ndim, const long* shape, const double* w, int R, const double* b,
+                 double alpha, int nonneg, double gamma, double p, const unsigned char* coins, int K,
+                 int n_inner, double* x, double* dual, double* obj, double f_star, double target,
+                 int* prox_calls) {
+  prob_t P;
+  P.sh = mk_shape(ndim, shape);
+  P.n = P.sh.n0 * P.sh.n1 * P.sh.n2;
+  P.w = w;
+  P.R = ndim == 2 ? R : 0;
+  P.b = b;
+  P.alpha = alpha;
+  P.nonneg = nonneg;
+  const long n = P.n;
+  P.t1 = (double*)malloc(sizeof(double) * n);
+  P.t2 = (double*)malloc(sizeof(double) * n);
+  P.t3 = (double*)malloc(sizeof(double) * n);
+  P.g = (double*)malloc(sizeof(double) * n * ndim);
+  double* gf = (double*)malloc(sizeof(double) * n);
+  double* v = (double*)malloc(sizeof(double) * n);
+  double* xn = (double*)malloc(sizeof(double) * n);
+  double* aux = (double*)malloc(sizeof(double) * n); /* FISTA: y;  ProxSkip: h */
+  int ran = -1, n_prox = 0;
+  if (!P.t1 || !P.t2 || !P.t3 || !P.g || !gf || !v || !xn || !aux) goto done;
+  double t = 1.0;
+  if (kind == 1) memcpy(aux, x, sizeof(double) * n); /* y_0 = x_0 */
+  if (kind == 2) memset(aux, 0, sizeof(double) * n); /* h_0 = 0 */
+  ran = 0;
+  for (int k = 0; k < K; ++k) {
+    if (kind == 0) {
+      grad_f(&P, x, gf);
+      for (long o = 0; o < n; ++o) v[o] = x[o] - gamma * gf[o];
+      if (tvo_fgp_prox(ndim, shape, v, gamma * alpha, n_inner, dual, nonneg, xn)) { ran = -1; goto done; }
+      ++n_prox;
+    } else if (kind == 1) {
+      grad_f(&P, aux, gf);
+      for (long o = 0; o < n; ++o) v[o] = aux[o] - gamma * gf[o];
+      if (tvo_fgp_prox(ndim, shape, v, gamma * alpha, n_inner, dual, nonneg, xn)) { ran = -1; goto done; }
+      ++n_prox;
+      const double t_new = (1.0 + sqrt(1.0 + 4.0 * t * t)) / 2.0;
+      const double beta = (t - 1.0) / t_new;
+      for (long o = 0; o < n; ++o) aux[o] = xn[o] + beta * (xn[o] - x[o]);
+      t = t_new;
+    } else {
+      /* x^ = x - gamma (grad f(x) - h) */
+      grad_f(&P, x, gf);
+      for (long o = 0; o < n; ++o) P.t2[o] = x[o] - gamma * (gf[o] - aux[o]);
+      if (coins[k]) {
+        for (long o = 0; o < n; ++o) v[o] = P.t2[o] - (gamma / p) * aux[o];
+        if (tvo_fgp_prox(ndim, shape, v, (gamma / p) * alpha, n_inner, dual, nonneg, xn)) {
+          ran = -1;
+          goto done;
+        }
+        ++n_prox;
+      } else {
+        memcpy(xn, P.t2, sizeof(double) * n);
+      }
+      for (long o = 0; o < n; ++o) aux[o] = aux[o] + (p / gamma) * (xn[o] - P.t2[o]);
+    }
+    memcpy(x, xn, sizeof(double) * n);
+    ran = k + 1;
+    if (obj || f_star > 0.0) {
+      const double F = objective(&P, x);
+      if (obj) obj[k] = F;
+      if (f_star > 0.0 && (F - f_star) / f_star <= target) break;
+    }
+  }
+done:
+  if (prox_calls) *prox_calls = n_prox;
+  free(P.t1);
+  free(P.t2);
+  free(P.t3);
+  free(P.g);
+  free(gf);
+  free(v);
+  free(xn);
+  free(aux);
+  return ran;
+}
+
+/* Threads the OpenMP passes use (1 without OpenMP). */
+int tvo_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
