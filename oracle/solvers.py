@@ -307,6 +307,30 @@ def dual_rof_projgd(b, alpha, gamma, K, eps=0.0, q0=None, record=True):
     return dict(q=q, u=b + tv.div(q), objective=obj, coins=[1] * K, prox_calls=K)
 
 
+def dual_rof_aprojgd(b, alpha, gamma, K, eps=0.0, q0=None, record=True):
+    """AProjGD on Dual-ROF / Dual-Huber-ROF (Section 2.2): the projected gradient
+    step of Algorithm 2 taken from the extrapolated point of Algorithm 3 (FISTA,
+    Beck and Teboulle's form):
+
+        q_{k+1} = P_C(y_k - gamma grad F(y_k));  t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2;
+        y_{k+1} = q_{k+1} + ((t_k - 1) / t_{k+1}) (q_{k+1} - q_k);  y_0 = q_0, t_0 = 1.
+
+    The objective is recorded at q_{k+1}; the primal iterate is u_k = b + div q_k."""
+    b = np.asarray(b, dtype=np.float64)
+    q = np.zeros((b.ndim,) + b.shape) if q0 is None else np.array(q0, dtype=np.float64)
+    y = q.copy()
+    t = 1.0
+    obj = []
+    for _ in range(K):
+        q_new = tv.project_ball(y - gamma * _dual_rof_grad(y, b, alpha, eps), alpha)
+        t_new = (1.0 + math.sqrt(1.0 + 4.0 * t * t)) / 2.0
+        y = q_new + ((t - 1.0) / t_new) * (q_new - q)
+        q, t = q_new, t_new
+        if record:
+            obj.append(dual_rof_objective(q, b, alpha, eps))
+    return dict(q=q, u=b + tv.div(q), objective=obj, coins=[1] * K, prox_calls=K)
+
+
 def dual_rof_proxskip(b, alpha, gamma, p, seed, K, eps=0.0, record=True):
     """Algorithm 4 on Dual-ROF / Dual-Huber-ROF: f = F, g = indicator of C, so the
     prox is P_C (prox of an indicator does not depend on the step)."""

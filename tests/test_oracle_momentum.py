@@ -286,3 +286,88 @@ def test_fista_mutants_fail_a_pin(name):
         except AssertionError:
             failed.append(pin.__name__)
     assert failed, f"planted mistake {name} passes every FISTA pin"
+
+
+# ----------------------------------------------------------------- pins (AProjGD on Dual-ROF)
+def _pin_aprojgd_first_two_are_projgd(aprojgd):
+    """y_0 = q_0 and the first extrapolation coefficient is zero: one and two
+    AProjGD steps are ProjGD steps, bit for bit."""
+    g = np.random.default_rng(14)
+    b = g.standard_normal((7, 9))
+    for eps in (0.0, 0.1):
+        for K in (1, 2):
+            a = solvers.dual_rof_projgd(b, 0.2, 1.0 / 8.0, K, eps=eps)
+            c = aprojgd(b, 0.2, 1.0 / 8.0, K, eps=eps)
+            np.testing.assert_array_equal(c["q"], a["q"])
+            np.testing.assert_array_equal(c["objective"], a["objective"])
+
+
+def _pin_aprojgd_two_pixel_unrolled(aprojgd):
+    """Dual-Huber-ROF on two pixels b = (0.1, 0.3), alpha = 0.3, eps = 0.1, gamma = 1/8:
+    the single dual entry q has grad F(q) = (2 + eps/alpha) q - (b_2 - b_1), so while
+    |q| < alpha a step is y -> m y + c with m = 1 - (2 + eps/alpha)/8 and c = 0.2/8:
+      q_1 = c, y_1 = q_1;  q_2 = m y_1 + c, y_2 = q_2 + beta_2 (q_2 - q_1);
+      q_3 = m y_2 + c, y_3 = q_3 + beta_3 (q_3 - q_2);  q_4 = m y_3 + c."""
+    b = np.array([[0.1, 0.3]])
+    a, eps = 0.3, 0.1
+    m, c = 1.0 - (2.0 + eps / a) / 8.0, 0.2 / 8.0
+    q1 = c
+    q2 = m * q1 + c
+    y2 = q2 + BETA2 * (q2 - q1)
+    q3 = m * y2 + c
+    y3 = q3 + BETA3 * (q3 - q2)
+    q4 = m * y3 + c
+    for K, q in [(1, q1), (2, q2), (3, q3), (4, q4)]:
+        assert abs(q) < a
+        out = aprojgd(b, a, 1.0 / 8.0, K, eps=eps)
+        np.testing.assert_allclose(out["q"][1, 0, 0], q, rtol=0, atol=1e-15)
+        np.testing.assert_allclose(out["u"].ravel(), [0.1 + q, 0.3 - q], rtol=0, atol=1e-15)
+
+
+def _pin_aprojgd_beck_teboulle(aprojgd):
+    """F(q_K) - F* <= 2 L ||q_0 - q*||^2 / (K + 1)^2 with L = 8 (the step 1/8) on a
+    64-pixel ramp, alpha = 0.5: ||q*||^2 <= 63 alpha^2, and F* >= 1/2 ||b||^2 - P(u)
+    for any u (weak duality with the ROF primal P), here u from a long run."""
+    z = np.linspace(0.0, 1.0, 64)[None, :]
+    alpha = 0.5
+    u_long, _ = tv.fgp_prox(z, alpha, 20000)
+    F_lo = 0.5 * float(np.sum(z * z)) - tv.rof_primal(u_long, z, alpha)
+    R2 = 63 * alpha * alpha
+    for K in RATE_N:
+        F = aprojgd(z, alpha, 1.0 / 8.0, K)["objective"][-1]
+        assert F - F_lo <= 2.0 * 8.0 * R2 / (K + 1) ** 2
+
+
+PINS_APROJGD = [_pin_aprojgd_first_two_are_projgd, _pin_aprojgd_two_pixel_unrolled, _pin_aprojgd_beck_teboulle]
+
+
+@pytest.mark.parametrize("pin", PINS_APROJGD, ids=lambda f: f.__name__[5:])
+def test_aprojgd_pins(pin):
+    pin(solvers.dual_rof_aprojgd)
+
+
+def test_projgd_breaks_the_accelerated_rate_on_dual_rof():
+    with pytest.raises(AssertionError):
+        _pin_aprojgd_beck_teboulle(lambda b, a, g, K, eps=0.0: solvers.dual_rof_projgd(b, a, g, K, eps=eps))
+
+
+APROJGD_MUTANTS = {
+    "beta_t_over_tnew": ("((t - 1.0) / t_new)", "(t / t_new)"),
+    "no_momentum": ("((t - 1.0) / t_new)", "0.0"),
+    "extrapolation_sign": ("(q_new - q)", "(q - q_new)"),
+    "t_frozen": ("q, t = q_new, t_new", "q, t = q_new, t"),
+    "gradient_at_q": ("_dual_rof_grad(y, b", "_dual_rof_grad(q, b"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(APROJGD_MUTANTS))
+def test_aprojgd_mutants_fail_a_pin(name):
+    old, new = APROJGD_MUTANTS[name]
+    bad = _mutant(solvers.dual_rof_aprojgd, old, new)
+    failed = []
+    for pin in PINS_APROJGD:
+        try:
+            pin(bad)
+        except AssertionError:
+            failed.append(pin.__name__)
+    assert failed, f"planted mistake {name} passes every AProjGD pin"
