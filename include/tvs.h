@@ -42,12 +42,23 @@ typedef enum {
   TVS_ENOMEM = 2,        /* a device or pinned-host allocation failed        */
   TVS_ECUDA = 3,         /* a CUDA runtime call failed (message has details) */
   TVS_ENUMERIC = 4,      /* non-finite value in an input or in the objective */
-  TVS_ETIMEDOUT = 5,     /* a bounded device wait gave up                     */
+  TVS_ETIMEDOUT = 5,     /* a solve passed its wall-clock limit (the
+                            TVS_SOLVE_TIMEOUT_MS environment variable, in ms;
+                            PGD, FISTA, ProxSkip, PDHG, PDHGSkip-2): it stopped
+                            launching iterations and cleaned up                */
   TVS_EUNSUPPORTED = 6   /* valid request this build does not implement       */
 } tvs_status;
 
 typedef enum { TVS_OP_IDENTITY = 0, TVS_OP_GAUSS_BLUR = 1, TVS_OP_PARALLEL_BEAM = 2 } tvs_op_kind;
-typedef enum { TVS_DUAL_F32 = 0, TVS_DUAL_BF16 = 1, TVS_DUAL_F16 = 2 } tvs_dual_dtype;
+/* Storage type of the TV dual field (the inner iterations always compute in
+ * float32; stores round to nearest).  TVS_DUAL_Q15 is signed 16-bit fixed point
+ * for values in [-1, 1] -- the range of every stored dual component, each being a
+ * component of a vector projected onto the unit ball: integer i stands for
+ * i / 32767, stores clamp to [-1, 1].  Not in the paper: at the two bytes of
+ * bfloat16 and half it resolves 2^-15 over the whole range (64x bfloat16's and 8x
+ * half's step near 1), which keeps the prox result within 2e-3 of an FP64 dual
+ * at prox steps lambda where bfloat16 does not. */
+typedef enum { TVS_DUAL_F32 = 0, TVS_DUAL_BF16 = 1, TVS_DUAL_F16 = 2, TVS_DUAL_Q15 = 3 } tvs_dual_dtype;
 typedef enum { TVS_MEM_DEVICE = 0, TVS_MEM_HOST = 1 } tvs_mem;
 
 typedef struct tvs_ctx tvs_ctx;
@@ -315,9 +326,9 @@ tvs_status proxskip_solve_batch(tvs_ctx* ctx, int n, tvs_problem* const* probs,
 /* ---- the light-prox case: Dual-ROF (Section 2.1, Eq. 6) and Dual-Huber-ROF
  * (Section 2.2, Eq. 8) -------------------------------------------------------- */
 /* min over |q_i| <= alpha of F(q) = 1/2 ||div q + b||^2 + (eps/(2 alpha)) ||q||^2
- * (eps = 0: Dual-ROF), by projected gradient (p = 1) or ProxSkip with the
- * pointwise alpha-ball projection (Eq. 7) as the prox (p < 1), step gamma
- * (Section 2.1 uses 1/8).  dims = {nx, ny}; b is a 2D image; q_inout holds the
+ * (eps = 0: Dual-ROF), by projected gradient (p = 1), its accelerated form
+ * AProjGD (p = 1, accelerated = 1) or ProxSkip with the pointwise alpha-ball
+ * projection (Eq. 7) as the prox (p < 1), step gamma (Section 2.1 uses 1/8).  dims = {nx, ny}; b is a 2D image; q_inout holds the
  * two dual planes (vertical, horizontal), initial value in, final out; u_out
  * (may be NULL) receives u = b + div q.  The trace's objective[k] = F(q_{k+1});
  * f_star > 0 stops at the relative-gap target as for the other solvers. */
@@ -330,6 +341,14 @@ typedef struct {
   int max_iter;
   double f_star;
   double target_rel_gap;
+  int accelerated;  /* 1 (with p = 1): AProjGD -- each projected gradient step is
+                       taken from the extrapolated point y_k = q_k + ((t_{k-1} - 1)/t_k)
+                       (q_k - q_{k-1}) of Algorithm 3 (t_0 = 1), Section 2.2 */
+  const float* u_ref;      /* NULL, or a reference solution u* (image size, in the
+                              memory `mem` names): the trace's rel_dist[k] then holds
+                              ||u_{k+1} - u*|| / ||u*|| with u = b + div q, the
+                              error measure of Sections 2.1 and 2.2             */
+  double target_rel_dist;  /* > 0 (with u_ref): also stop once rel_dist <= this   */
 } tvs_rof_params;
 tvs_status dual_rof_solve(tvs_ctx* ctx, const int dims[2], const float* b, const tvs_rof_params* prm,
                           float* q_inout, float* u_out, tvs_mem mem, tvs_trace* trace);

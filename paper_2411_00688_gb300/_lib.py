@@ -17,7 +17,7 @@ TVS_OK, TVS_EINVAL, TVS_ENOMEM, TVS_ECUDA, TVS_ENUMERIC, TVS_ETIMEDOUT, TVS_EUNS
 STATUS_NAMES = {0: "TVS_OK", 1: "TVS_EINVAL", 2: "TVS_ENOMEM", 3: "TVS_ECUDA", 4: "TVS_ENUMERIC",
                 5: "TVS_ETIMEDOUT", 6: "TVS_EUNSUPPORTED"}
 OP_IDENTITY, OP_GAUSS_BLUR, OP_PARALLEL_BEAM = 0, 1, 2
-DUAL = {"f32": 0, "bf16": 1, "f16": 2}
+DUAL = {"f32": 0, "bf16": 1, "f16": 2, "q15": 3}
 MEM_DEVICE, MEM_HOST = 0, 1
 
 
@@ -57,7 +57,8 @@ class PDXParams(C.Structure):
 class RofParams(C.Structure):
     _fields_ = [("alpha", C.c_double), ("eps", C.c_double), ("gamma", C.c_double), ("p", C.c_double),
                 ("seed", C.c_uint64), ("max_iter", C.c_int), ("f_star", C.c_double),
-                ("target_rel_gap", C.c_double)]
+                ("target_rel_gap", C.c_double), ("accelerated", C.c_int), ("u_ref", C.c_void_p),
+                ("target_rel_dist", C.c_double)]
 
 
 class Trace(C.Structure):

@@ -209,7 +209,7 @@ def tvs_objective(prob: Problem, x) -> float:
     return out.value
 
 
-_DUAL_TORCH = {"f32": "float32", "bf16": "bfloat16", "f16": "float16"}
+_DUAL_TORCH = {"f32": "float32", "bf16": "bfloat16", "f16": "float16", "q15": "int16"}
 
 
 def _prox_args(z, u, dual, dual_state):
@@ -426,21 +426,28 @@ def pdhg_explicit_solve(prob, x, y, q=None, max_iter=100, sigma=1.0, tau=1.0, f_
 
 
 def dual_rof_solve(ctx: Context, b, q, alpha, gamma, max_iter, p=1.0, seed=0, eps=0.0, u=None,
-                   f_star=0.0, target=0.0):
-    """Projected gradient (p = 1) or ProxSkip on Dual-ROF / Dual-Huber-ROF.
+                   f_star=0.0, target=0.0, accelerated=False, u_ref=None, target_dist=0.0):
+    """Projected gradient (p = 1), AProjGD (p = 1, accelerated) or ProxSkip on
+    Dual-ROF / Dual-Huber-ROF.
 
     b: image (H, W); q: dual field (2, H, W), initial value in, final out; u: optional
-    output for b + div q.  All CUDA tensors or all numpy float32 arrays."""
+    output for b + div q; u_ref: optional reference solution (the trace then records
+    ||u_k - u*|| / ||u*||, and target_dist > 0 stops on it).  All CUDA tensors or all
+    numpy float32 arrays."""
+    pr, mem_r = (None, None)
+    if u_ref is not None:
+        pr, mem_r, kr = _arr(u_ref, "u_ref")
     prm = L.RofParams(alpha=float(alpha), eps=float(eps), gamma=float(gamma), p=float(p),
                       seed=int(seed) & ((1 << 64) - 1), max_iter=int(max_iter), f_star=float(f_star),
-                      target_rel_gap=float(target))
+                      target_rel_gap=float(target), accelerated=int(bool(accelerated)),
+                      u_ref=C.c_void_p(pr) if pr is not None else None, target_rel_dist=float(target_dist))
     pb, mem, kb = _arr(b, "b")
     pq, mem_q, kq = _arr(q, "q")
     pu, mem_u = (None, mem)
     if u is not None:
         pu, mem_u, ku = _arr(u, "u")
-    if len({mem, mem_q, mem_u}) != 1:
-        raise ValueError("b, q and u must live in the same memory")
+    if len({mem, mem_q, mem_u} | ({mem_r} if mem_r is not None else set())) != 1:
+        raise ValueError("b, q, u and u_ref must live in the same memory")
     if mem == L.MEM_DEVICE:
         _sync_torch()
     H, W = b.shape

@@ -19,10 +19,13 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -65,6 +68,30 @@ constexpr int LAG = 8;  // outer iterations the host may run ahead of the device
 bool is_fin(double v) { return std::isfinite(v); }
 
 }  // namespace
+
+// The CUDA graphs of one solve: one outer iteration each, by coin and by the
+// parity of the iterate buffers.
+struct GraphSet {
+  cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [coin][parity]
+  GraphSet() = default;
+  GraphSet(const GraphSet&) = delete;
+  GraphSet& operator=(const GraphSet&) = delete;
+  ~GraphSet() {
+    for (auto& row : exec)
+      for (auto& e : row)
+        if (e) cudaGraphExecDestroy(e);
+  }
+};
+
+// Graphs of one solver family kept in a problem between solves: `key` lists
+// every value the captured launches bake in (scalars, kernel configuration, and
+// the problem's buffer generation), so a later solve with the same key replays
+// them instead of capturing and instantiating them again.
+struct GraphCache {
+  std::vector<double> key;
+  std::unique_ptr<GraphSet> G;
+};
+enum GraphSlot { GS_FB = 0, GS_PD = 1, GS_PD1 = 2, GS_PDX = 3, GS_COUNT = 4 };
 
 struct tvs_ctx {
   int device = 0;
@@ -126,13 +153,40 @@ struct tvs_problem {
   double* dist_dev = nullptr;   // relative distance per trace entry
   float* aux = nullptr;         // m floats, allocated by the first explicit PDHG solve
   size_t bytes = 0;
+  // bumped whenever a buffer that captured graphs name is allocated anew
+  unsigned long long gen = 0;
+  GraphCache graphs[GS_COUNT];
 };
 
 namespace {
 
+// Host-side fault injection for tests, off unless asked for: with
+// TVS_FAULT_INJECT=alloc:N in the environment, the N-th device allocation after
+// the variable took that value fails as if the device had run out of memory (no
+// CUDA call is made for it), so the cleanup of every TVS_ENOMEM path can be
+// exercised without touching the GPU's real state.
+bool inject_alloc_failure() {
+  static std::mutex mu;
+  static std::string last;
+  static long count = 0;
+  const char* e = getenv("TVS_FAULT_INJECT");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!e || strncmp(e, "alloc:", 6) != 0) {
+    last.clear();
+    count = 0;
+    return false;
+  }
+  if (last != e) {
+    last = e;
+    count = 0;
+  }
+  return ++count == atol(e + 6);
+}
+
 tvs_status dalloc(tvs_ctx* ctx, size_t* owner_bytes, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) return TVS_OK;
+  if (inject_alloc_failure()) return fail(TVS_ENOMEM, "cudaMalloc(%zu bytes) failed: injected", bytes);
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     *p = nullptr;
@@ -153,7 +207,9 @@ void dfree(void* p) {
   if (p) cudaFree(p);
 }
 
-bool valid_dual(int d) { return d == TVS_DUAL_F32 || d == TVS_DUAL_BF16 || d == TVS_DUAL_F16; }
+bool valid_dual(int d) {
+  return d == TVS_DUAL_F32 || d == TVS_DUAL_BF16 || d == TVS_DUAL_F16 || d == TVS_DUAL_Q15;
+}
 
 std::vector<float> fgp_betas(int n_iter) {
   // beta of inner iteration i (1-based): 0 for i = 1, (t_{i-1} - 1) / t_i after,
@@ -343,6 +399,7 @@ tvs_status ensure_trace(tvs_problem* P, int K) {
   P->fgp_ts = nullptr;
   P->beta_dev = nullptr;
   const int cap = K + 1;
+  ++P->gen;
   TVS_TRY(palloc(P, &P->obj_dev, cap));
   TVS_TRY(palloc(P, &P->ts_dev, cap + 1));
   TVS_TRY(palloc(P, &P->fgp_ts, 2 * (size_t)cap));
@@ -485,15 +542,6 @@ tvs_status pd_forward(tvs_problem* P, const float* x, float tau, bool init, cuda
   return TVS_OK;
 }
 
-struct GraphSet {
-  cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [coin][parity]
-  ~GraphSet() {
-    for (auto& row : exec)
-      for (auto& e : row)
-        if (e) cudaGraphExecDestroy(e);
-  }
-};
-
 template <typename F>
 tvs_status capture(cudaStream_t s, cudaGraphExec_t* exec, F&& body) {
   cudaGraph_t g = nullptr;
@@ -511,20 +559,56 @@ tvs_status capture(cudaStream_t s, cudaGraphExec_t* exec, F&& body) {
   return TVS_OK;
 }
 
+// The problem's cached graphs of `slot` when they were captured under `key`
+// (*fresh = false); otherwise an empty set, now cached under `key`, to capture
+// into (*fresh = true).  The key is completed with the problem's buffer
+// generation and the presence of a reference solution.
+GraphSet& cached_graphs(tvs_problem* P, GraphSlot slot, std::vector<double> key, bool* fresh) {
+  key.push_back((double)P->gen);
+  key.push_back(P->uref ? 1.0 : 0.0);
+  GraphCache& c = P->graphs[slot];
+  if (c.G && c.key == key) {
+    *fresh = false;
+    return *c.G;
+  }
+  c.G.reset(new GraphSet());
+  c.key = std::move(key);
+  *fresh = true;
+  return *c.G;
+}
+
 // Shared outer-loop machinery: pacing, trace readback.
 struct LoopState {
   int iters = 0;
   int prox = 0;
+  bool timed_out = false;
 };
+
+// Wall-clock limit of a solve's host loop (TVS_SOLVE_TIMEOUT_MS, none by
+// default): once it has passed, no further iteration is launched and the solve
+// returns TVS_ETIMEDOUT after its usual clean-up, with the trace of the
+// iterations that ran.
+double solve_timeout_ms() {
+  const char* e = getenv("TVS_SOLVE_TIMEOUT_MS");
+  const double v = e ? atof(e) : 0.0;
+  return v > 0.0 ? v : 0.0;
+}
 
 tvs_status run_loop(tvs_problem* P, int K, const std::vector<unsigned char>& coins, GraphSet& G,
                     LoopState* ls) {
   tvs_ctx* C = P->ctx;
   cudaStream_t s = C->stream;
+  const double limit = solve_timeout_ms();
+  const auto t0 = std::chrono::steady_clock::now();
   for (int k = 0; k < K; ++k) {
     if (k >= LAG) {
       CUDA_TRY(cudaEventSynchronize(C->ring[k % LAG]));
       if (*(volatile int*)P->done_host) break;
+    }
+    if (limit > 0.0 &&
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() > limit) {
+      ls->timed_out = true;
+      break;
     }
     const int c = coins[k] ? 1 : 0;
     CUDA_TRY(cudaGraphLaunch(G.exec[c][k & 1], s));
@@ -621,6 +705,7 @@ tvs_status finish_solve(tvs_problem* P, int K, const LoopState& ls,
     }
   }
   if (bad) return fail(TVS_ENUMERIC, "non-finite objective during the solve");
+  if (ls.timed_out) return fail(TVS_ETIMEDOUT, "solve stopped at its time limit after %d iterations", iters);
   return TVS_OK;
 }
 
@@ -688,57 +773,71 @@ tvs_status fb_solve(tvs_problem* P, const tvs_fb_params* prm, float* x_io, tvs_m
   const float fgamma = (float)gamma;
   const float h_coef = (float)(p / gamma);
 
-  GraphSet G;
-  for (int c = 0; c < 2; ++c) {
-    if (c == 0 && kind != FB_PROXSKIP) continue;
-    for (int par = 0; par < 2; ++par) {
-      float* xc = P->x[par];
-      float* xn = P->x[par ^ 1];
-      TVS_TRY(capture(s, &G.exec[c][par], [&]() -> tvs_status {
-        if (kind == FB_PROXSKIP) {
-          if (c == 0) {
-            TVS_TRY(fb_step(P, xc, xn, P->h, fgamma, fgamma, s));
-          } else {
-            TVS_TRY(fb_step(P, xc, P->z, P->h, fgamma, (float)(gamma - gamma / p), s));
-          }
-        } else {
-          TVS_TRY(fb_step(P, kind == FB_FISTA ? aux : xc, P->z, nullptr, fgamma, 0.f, s));
+  bool fresh = false;
+  GraphSet& G = cached_graphs(P, GS_FB,
+                              {(double)kind, gamma, p, alpha, nonneg ? 1.0 : 0.0, (double)dtype, (double)N,
+                               (double)every, prm->f_star, prm->target_rel_gap, prm->target_rel_dist,
+                               (double)fcfg.tb, (double)fcfg.cpl, (double)fcfg.rpw},
+                              &fresh);
+  if (fresh) {
+    const tvs_status cst = [&]() -> tvs_status {
+      for (int c = 0; c < 2; ++c) {
+        if (c == 0 && kind != FB_PROXSKIP) continue;
+        for (int par = 0; par < 2; ++par) {
+          float* xc = P->x[par];
+          float* xn = P->x[par ^ 1];
+          TVS_TRY(capture(s, &G.exec[c][par], [&]() -> tvs_status {
+            if (kind == FB_PROXSKIP) {
+              if (c == 0) {
+                TVS_TRY(fb_step(P, xc, xn, P->h, fgamma, fgamma, s));
+              } else {
+                TVS_TRY(fb_step(P, xc, P->z, P->h, fgamma, (float)(gamma - gamma / p), s));
+              }
+            } else {
+              TVS_TRY(fb_step(P, kind == FB_FISTA ? aux : xc, P->z, nullptr, fgamma, 0.f, s));
+            }
+            const bool branch = kind != FB_FISTA && c == 1;  // overlap the record with the prox
+            if (kind != FB_FISTA) {
+              cudaStream_t rs = s;
+              if (branch) {
+                CUDA_TRY(cudaEventRecord(C->fork_ev, s));
+                CUDA_TRY(cudaStreamWaitEvent(C->side, C->fork_ev, 0));
+                rs = C->side;
+              }
+              CUDA_TRY(launch_reduce_record(P->part_a, na, P->part_b, nb, alpha, every, P->obj_dev,
+                                            P->ts_dev, prm->f_star, prm->target_rel_gap, P->flags,
+                                            P->done_host_dev, nullptr, rs));
+              TVS_TRY(track_distance(P, xc, prm->target_rel_dist, rs));
+              if (branch) CUDA_TRY(cudaEventRecord(C->join_ev, C->side));
+            }
+            if (c == 1) {
+              int fin = 0;
+              CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 0, s));
+              if (use_prox) TVS_TRY(launch_fgp_sequence(fcfg, d, P->z, P->dual, N, betas, lam, dtype, nonneg, s, &fin));
+              CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 1, s));
+              CUDA_TRY(launch_fgp_finalize(d, P->z, P->dual[fin], dtype, use_prox ? lam : 0.f, nonneg, xn,
+                                           kind == FB_PROXSKIP ? P->h : nullptr, h_coef,
+                                           fin != 0 ? P->dual[0] : nullptr, xc,
+                                           kind == FB_FISTA ? aux : nullptr, P->beta_dev, P->flags + 2, s));
+            }
+            if (branch) CUDA_TRY(cudaStreamWaitEvent(s, C->join_ev, 0));
+            if (kind == FB_FISTA) {
+              int a = 0, b = 0;
+              TVS_TRY(objective_parts(P, xn, P->part_a, P->part_b, &a, &b, s));
+              CUDA_TRY(launch_reduce_record(P->part_a, a, P->part_b, b, alpha, every, P->obj_dev,
+                                            P->ts_dev, prm->f_star, prm->target_rel_gap, P->flags,
+                                            P->done_host_dev, nullptr, s));
+              TVS_TRY(track_distance(P, xn, prm->target_rel_dist, s));
+            }
+            return TVS_OK;
+          }));
         }
-        const bool branch = kind != FB_FISTA && c == 1;  // overlap the record with the prox
-        if (kind != FB_FISTA) {
-          cudaStream_t rs = s;
-          if (branch) {
-            CUDA_TRY(cudaEventRecord(C->fork_ev, s));
-            CUDA_TRY(cudaStreamWaitEvent(C->side, C->fork_ev, 0));
-            rs = C->side;
-          }
-          CUDA_TRY(launch_reduce_record(P->part_a, na, P->part_b, nb, alpha, every, P->obj_dev,
-                                        P->ts_dev, prm->f_star, prm->target_rel_gap, P->flags,
-                                        P->done_host_dev, nullptr, rs));
-          TVS_TRY(track_distance(P, xc, prm->target_rel_dist, rs));
-          if (branch) CUDA_TRY(cudaEventRecord(C->join_ev, C->side));
-        }
-        if (c == 1) {
-          int fin = 0;
-          CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 0, s));
-          if (use_prox) TVS_TRY(launch_fgp_sequence(fcfg, d, P->z, P->dual, N, betas, lam, dtype, nonneg, s, &fin));
-          CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 1, s));
-          CUDA_TRY(launch_fgp_finalize(d, P->z, P->dual[fin], dtype, use_prox ? lam : 0.f, nonneg, xn,
-                                       kind == FB_PROXSKIP ? P->h : nullptr, h_coef,
-                                       fin != 0 ? P->dual[0] : nullptr, xc,
-                                       kind == FB_FISTA ? aux : nullptr, P->beta_dev, P->flags + 2, s));
-        }
-        if (branch) CUDA_TRY(cudaStreamWaitEvent(s, C->join_ev, 0));
-        if (kind == FB_FISTA) {
-          int a = 0, b = 0;
-          TVS_TRY(objective_parts(P, xn, P->part_a, P->part_b, &a, &b, s));
-          CUDA_TRY(launch_reduce_record(P->part_a, a, P->part_b, b, alpha, every, P->obj_dev,
-                                        P->ts_dev, prm->f_star, prm->target_rel_gap, P->flags,
-                                        P->done_host_dev, nullptr, s));
-          TVS_TRY(track_distance(P, xn, prm->target_rel_dist, s));
-        }
-        return TVS_OK;
-      }));
+      }
+      return TVS_OK;
+    }();
+    if (cst != TVS_OK) {
+      P->graphs[GS_FB].G.reset();
+      return cst;
     }
   }
   LoopState ls;
@@ -796,45 +895,59 @@ tvs_status pd_solve(tvs_problem* P, const tvs_pd_params* prm, float* x_io, float
   TVS_TRY(fgp_config_for(C, d, dtype, P->x[0], P->dual[0], P->dual[2], P->dual[3], &fcfg));
   const int na = pd_parts_a(P), nb = pd_parts_b(P);
   const float fs = (float)sigma, ft = (float)tau;
-  GraphSet G;
-  for (int c = 0; c < 2; ++c) {
-    if (c == 0 && !skip) continue;
-    for (int par = 0; par < 2; ++par) {
-      float* xc = P->x[par];
-      float* xn = P->x[par ^ 1];
-      TVS_TRY(capture(s, &G.exec[c][par], [&]() -> tvs_status {
-        if (skip) {
-          if (c == 0) TVS_TRY(pd_backward(P, xc, xn, P->h, fs, fs, s));
-          else TVS_TRY(pd_backward(P, xc, P->z, P->h, fs, (float)(sigma - sigma / p), s));
-        } else {
-          TVS_TRY(pd_backward(P, xc, P->z, nullptr, fs, 0.f, s));
+  bool fresh = false;
+  GraphSet& G = cached_graphs(P, GS_PD,
+                              {skip ? 1.0 : 0.0, sigma, tau, p, alpha, nonneg ? 1.0 : 0.0, (double)dtype,
+                               (double)N, (double)every, prm->f_star, prm->target_rel_gap, prm->target_rel_dist,
+                               (double)fcfg.tb, (double)fcfg.cpl, (double)fcfg.rpw},
+                              &fresh);
+  if (fresh) {
+    const tvs_status cst = [&]() -> tvs_status {
+      for (int c = 0; c < 2; ++c) {
+        if (c == 0 && !skip) continue;
+        for (int par = 0; par < 2; ++par) {
+          float* xc = P->x[par];
+          float* xn = P->x[par ^ 1];
+          TVS_TRY(capture(s, &G.exec[c][par], [&]() -> tvs_status {
+            if (skip) {
+              if (c == 0) TVS_TRY(pd_backward(P, xc, xn, P->h, fs, fs, s));
+              else TVS_TRY(pd_backward(P, xc, P->z, P->h, fs, (float)(sigma - sigma / p), s));
+            } else {
+              TVS_TRY(pd_backward(P, xc, P->z, nullptr, fs, 0.f, s));
+            }
+            // on prox iterations the objective record runs beside the inner iterations
+            cudaStream_t rs = s;
+            if (c == 1) {
+              CUDA_TRY(cudaEventRecord(C->fork_ev, s));
+              CUDA_TRY(cudaStreamWaitEvent(C->side, C->fork_ev, 0));
+              rs = C->side;
+            }
+            CUDA_TRY(launch_reduce_record(P->part_a, na, P->part_b, nb, alpha, every, P->obj_dev,
+                                          P->ts_dev, prm->f_star, prm->target_rel_gap, P->flags,
+                                          P->done_host_dev, nullptr, rs));
+            TVS_TRY(track_distance(P, xc, prm->target_rel_dist, rs));
+            if (c == 1) CUDA_TRY(cudaEventRecord(C->join_ev, C->side));
+            if (c == 1) {
+              int fin = 0;
+              CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 0, s));
+              if (use_prox) TVS_TRY(launch_fgp_sequence(fcfg, d, P->z, P->dual, N, betas, lam, dtype, nonneg, s, &fin));
+              CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 1, s));
+              CUDA_TRY(launch_fgp_finalize(d, P->z, P->dual[fin], dtype, use_prox ? lam : 0.f, nonneg, xn,
+                                           skip ? P->h : nullptr, (float)(p / sigma),
+                                           fin != 0 ? P->dual[0] : nullptr, nullptr, nullptr, nullptr,
+                                           nullptr, s));
+              CUDA_TRY(cudaStreamWaitEvent(s, C->join_ev, 0));  // the record read part_a
+            }
+            TVS_TRY(pd_forward(P, xn, ft, false, s));
+            return TVS_OK;
+          }));
         }
-        // on prox iterations the objective record runs beside the inner iterations
-        cudaStream_t rs = s;
-        if (c == 1) {
-          CUDA_TRY(cudaEventRecord(C->fork_ev, s));
-          CUDA_TRY(cudaStreamWaitEvent(C->side, C->fork_ev, 0));
-          rs = C->side;
-        }
-        CUDA_TRY(launch_reduce_record(P->part_a, na, P->part_b, nb, alpha, every, P->obj_dev,
-                                      P->ts_dev, prm->f_star, prm->target_rel_gap, P->flags,
-                                      P->done_host_dev, nullptr, rs));
-        TVS_TRY(track_distance(P, xc, prm->target_rel_dist, rs));
-        if (c == 1) CUDA_TRY(cudaEventRecord(C->join_ev, C->side));
-        if (c == 1) {
-          int fin = 0;
-          CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 0, s));
-          if (use_prox) TVS_TRY(launch_fgp_sequence(fcfg, d, P->z, P->dual, N, betas, lam, dtype, nonneg, s, &fin));
-          CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 1, s));
-          CUDA_TRY(launch_fgp_finalize(d, P->z, P->dual[fin], dtype, use_prox ? lam : 0.f, nonneg, xn,
-                                       skip ? P->h : nullptr, (float)(p / sigma),
-                                       fin != 0 ? P->dual[0] : nullptr, nullptr, nullptr, nullptr,
-                                       nullptr, s));
-          CUDA_TRY(cudaStreamWaitEvent(s, C->join_ev, 0));  // the record read part_a
-        }
-        TVS_TRY(pd_forward(P, xn, ft, false, s));
-        return TVS_OK;
-      }));
+      }
+      return TVS_OK;
+    }();
+    if (cst != TVS_OK) {
+      P->graphs[GS_PD].G.reset();
+      return cst;
     }
   }
   LoopState ls;
@@ -900,27 +1013,41 @@ tvs_status pd1_solve(tvs_problem* P, const tvs_pd_params* prm, float* x_io, floa
   TVS_TRY(fgp_config_for(C, d, dtype, P->x[0], P->dual[0], P->dual[2], P->dual[3], &fcfg));
   const int na = pd_parts_a(P), nb = pointwise_blocks(P->n);
   float* x = P->x[0];
-  GraphSet G;
-  for (int c = 0; c < 2; ++c) {
-    TVS_TRY(capture(s, &G.exec[c][0], [&]() -> tvs_status {
-      CUDA_TRY(launch_reduce_record(P->part_a, na, P->part_b, nb, alpha, every, P->obj_dev, P->ts_dev,
-                                    prm->f_star, prm->target_rel_gap, P->flags, P->done_host_dev, nullptr, s));
-      TVS_TRY(track_distance(P, x, prm->target_rel_dist, s));
-      if (c == 0) {
-        CUDA_TRY(launch_pd1_dual_pointwise(P->m, nullptr, P->axp, P->y, P->b, (float)p, (float)tau, nullptr, s));
-        return TVS_OK;
+  bool fresh = false;
+  GraphSet& G = cached_graphs(P, GS_PD1,
+                              {sigma, tau, p, alpha, nonneg ? 1.0 : 0.0, (double)dtype, (double)N, (double)every,
+                               prm->f_star, prm->target_rel_gap, prm->target_rel_dist, (double)fcfg.tb,
+                               (double)fcfg.cpl, (double)fcfg.rpw},
+                              &fresh);
+  if (fresh) {
+    const tvs_status cst = [&]() -> tvs_status {
+      for (int c = 0; c < 2; ++c) {
+        TVS_TRY(capture(s, &G.exec[c][0], [&]() -> tvs_status {
+          CUDA_TRY(launch_reduce_record(P->part_a, na, P->part_b, nb, alpha, every, P->obj_dev, P->ts_dev,
+                                        prm->f_star, prm->target_rel_gap, P->flags, P->done_host_dev, nullptr, s));
+          TVS_TRY(track_distance(P, x, prm->target_rel_dist, s));
+          if (c == 0) {
+            CUDA_TRY(launch_pd1_dual_pointwise(P->m, nullptr, P->axp, P->y, P->b, (float)p, (float)tau, nullptr, s));
+            return TVS_OK;
+          }
+          TVS_TRY(pd_backward(P, x, P->z, nullptr, (float)sigma, 0.f, s, false));
+          int fin = 0;
+          CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 0, s));
+          if (use_prox) TVS_TRY(launch_fgp_sequence(fcfg, d, P->z, P->dual, N, betas, lam, dtype, nonneg, s, &fin));
+          CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 1, s));
+          CUDA_TRY(launch_fgp_finalize_pd1(d, P->z, P->dual[fin], dtype, use_prox ? lam : 0.f, nonneg, (float)p, x,
+                                           P->h, fin != 0 ? P->dual[0] : nullptr, s));
+          TVS_TRY(pd1_forward(P, P->h, (float)p, (float)tau, s));
+          CUDA_TRY(launch_tv_partials(d, x, P->part_b, s));
+          return TVS_OK;
+        }));
       }
-      TVS_TRY(pd_backward(P, x, P->z, nullptr, (float)sigma, 0.f, s, false));
-      int fin = 0;
-      CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 0, s));
-      if (use_prox) TVS_TRY(launch_fgp_sequence(fcfg, d, P->z, P->dual, N, betas, lam, dtype, nonneg, s, &fin));
-      CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 1, s));
-      CUDA_TRY(launch_fgp_finalize_pd1(d, P->z, P->dual[fin], dtype, use_prox ? lam : 0.f, nonneg, (float)p, x,
-                                       P->h, fin != 0 ? P->dual[0] : nullptr, s));
-      TVS_TRY(pd1_forward(P, P->h, (float)p, (float)tau, s));
-      CUDA_TRY(launch_tv_partials(d, x, P->part_b, s));
       return TVS_OK;
-    }));
+    }();
+    if (cst != TVS_OK) {
+      P->graphs[GS_PD1].G.reset();
+      return cst;
+    }
   }
   LoopState ls;
   for (int k = 0; k < K; ++k) {
@@ -1367,19 +1494,29 @@ extern "C" tvs_status dual_rof_solve(tvs_ctx* C, const int dims[2], const float*
   if (!(prm->p > 0.0 && prm->p <= 1.0)) return fail(TVS_EINVAL, "p must lie in (0, 1]");
   if (prm->max_iter < 0) return fail(TVS_EINVAL, "max_iter must be >= 0");
   if (!is_fin(prm->f_star) || !(prm->target_rel_gap >= 0)) return fail(TVS_EINVAL, "invalid f_star/target");
+  if (prm->accelerated != 0 && prm->accelerated != 1) return fail(TVS_EINVAL, "accelerated must be 0 or 1");
+  if (prm->accelerated && prm->p < 1.0) return fail(TVS_EINVAL, "the accelerated solver takes p = 1");
+  if (!(prm->target_rel_dist >= 0) || !is_fin(prm->target_rel_dist)) return fail(TVS_EINVAL, "invalid target_rel_dist");
   const int K = prm->max_iter;
   const size_t n = (size_t)H * W;
   const bool skip = prm->p < 1.0;
+  const bool accel = prm->accelerated != 0;
   cudaStream_t s = C->stream;
   BatchScratch S;
-  float *q0, *q1, *h = nullptr, *bd;
-  Partial *pa, *pb;
+  float *q0, *q1, *q2 = nullptr, *h = nullptr, *bd, *beta_tab = nullptr, *uref = nullptr;
+  Partial *pa, *pb, *pc = nullptr;
+  double* dist = nullptr;
+  double uref_norm2 = 0.0;
   double* obj;
   unsigned long long* ts;
   int* flags;
   const int nparts = std::max(dual_rof_blocks(H, W), pointwise_blocks(n));
   TVS_TRY(S.zeros<float>(2 * n, &q0, s));
   TVS_TRY(S.zeros<float>(2 * n, &q1, s));
+  if (accel) {
+    TVS_TRY(S.zeros<float>(2 * n, &q2, s));
+    TVS_TRY(S.zeros<float>((size_t)K + 1, &beta_tab, s));
+  }
   if (skip) TVS_TRY(S.zeros<float>(2 * n, &h, s));
   TVS_TRY(S.zeros<float>(n, &bd, s));
   TVS_TRY(S.zeros<Partial>(nparts, &pa, s));
@@ -1401,6 +1538,25 @@ extern "C" tvs_status dual_rof_solve(tvs_ctx* C, const int dims[2], const float*
   }
   TVS_TRY(copy_in(bd, b, n, mem, s));
   TVS_TRY(copy_in(q0, q_io, 2 * n, mem, s));
+  if (prm->u_ref) {
+    // the reference: a device copy, and its squared norm (FP64, on the host)
+    std::vector<float> host(n);
+    if (mem == TVS_MEM_HOST)
+      memcpy(host.data(), prm->u_ref, n * sizeof(float));
+    else
+      CUDA_TRY(cudaMemcpy(host.data(), prm->u_ref, n * sizeof(float), cudaMemcpyDeviceToHost));
+    for (float v : host) {
+      if (!std::isfinite(v)) return fail(TVS_ENUMERIC, "u_ref holds a non-finite value");
+      uref_norm2 += (double)v * (double)v;
+    }
+    if (!(uref_norm2 > 0.0)) return fail(TVS_EINVAL, "u_ref must be nonzero");
+    TVS_TRY(S.zeros<float>(n, &uref, s));
+    TVS_TRY(S.zeros<Partial>(nparts, &pc, s));
+    TVS_TRY(S.zeros<double>((size_t)K + 1, &dist, s));
+    CUDA_TRY(cudaMemcpyAsync(uref, host.data(), n * sizeof(float), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemsetAsync(dist, 0xff, sizeof(double) * (K + 1), s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+  }
   int f0[4] = {0, -1, -1, 0};
   CUDA_TRY(cudaMemcpyAsync(flags, f0, sizeof(f0), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemsetAsync(obj, 0xff, sizeof(double) * (K + 1), s));
@@ -1410,19 +1566,52 @@ extern "C" tvs_status dual_rof_solve(tvs_ctx* C, const int dims[2], const float*
   const float alpha = (float)prm->alpha, eps = (float)prm->eps, gamma = (float)prm->gamma, p = (float)prm->p;
   const double ea = prm->eps / prm->alpha;
   const int nb = dual_rof_blocks(H, W);
-  float* q[2] = {q0, q1};
+  float* q[3] = {q0, q1, q2};
+  std::vector<float> bt;
+  if (accel) {
+    // beta_tab[k]: the extrapolation coefficient of iteration k, (t_{k-1} - 1) / t_k
+    // with t_0 = 1 (0 for k = 0); the step kernel of iteration k finds the record
+    // counter at k - 1
+    bt.assign((size_t)K + 1, 0.f);
+    double t = 1.0;
+    for (int k = 1; k <= K; ++k) {
+      const double tn = (1.0 + std::sqrt(1.0 + 4.0 * t * t)) / 2.0;
+      bt[k] = (float)((t - 1.0) / tn);
+      t = tn;
+    }
+    CUDA_TRY(cudaMemcpyAsync(beta_tab, bt.data(), sizeof(float) * bt.size(), cudaMemcpyHostToDevice, s));
+  }
   CUDA_TRY(cudaEventRecord(C->ev_start, s));
   CUDA_TRY(launch_timestamp(ts + K + 1, s));
-  GraphSet G;
-  for (int c = 0; c < 2; ++c) {
-    if (c == 0 && !skip) continue;
-    for (int par = 0; par < 2; ++par) {
-      TVS_TRY(capture(s, &G.exec[c][par], [&]() -> tvs_status {
-        CUDA_TRY(launch_dual_rof_step(H, W, q[par], q[par ^ 1], h, bd, alpha, eps, gamma, p, c == 1, pa, pb, s));
+  // plain / ProxSkip iterations: graph [coin][k mod 2]; accelerated: [k mod 3]
+  GraphSet G, G3;
+  if (accel) {
+    for (int r = 0; r < 3; ++r) {
+      cudaGraphExec_t* slot = r < 2 ? &G.exec[1][r] : &G3.exec[1][0];
+      TVS_TRY(capture(s, slot, [&]() -> tvs_status {
+        CUDA_TRY(launch_dual_rof_accel_step(H, W, q[r], q[(r + 2) % 3], q[(r + 1) % 3], bd, alpha, eps, gamma,
+                                            beta_tab, flags + 2, pa, pb, uref, pc, s));
         CUDA_TRY(launch_reduce_record(pa, nb, pb, nb, ea, 1, obj, ts, prm->f_star, prm->target_rel_gap, flags,
                                       done_dev, nullptr, s));
+        if (uref)
+          CUDA_TRY(launch_dist_record(pc, nb, uref_norm2, dist, prm->target_rel_dist, flags, done_dev, s));
         return TVS_OK;
       }));
+    }
+  } else {
+    for (int c = 0; c < 2; ++c) {
+      if (c == 0 && !skip) continue;
+      for (int par = 0; par < 2; ++par) {
+        TVS_TRY(capture(s, &G.exec[c][par], [&]() -> tvs_status {
+          CUDA_TRY(launch_dual_rof_step(H, W, q[par], q[par ^ 1], h, bd, alpha, eps, gamma, p, c == 1, pa, pb,
+                                        uref, pc, s));
+          CUDA_TRY(launch_reduce_record(pa, nb, pb, nb, ea, 1, obj, ts, prm->f_star, prm->target_rel_gap, flags,
+                                        done_dev, nullptr, s));
+          if (uref)
+            CUDA_TRY(launch_dist_record(pc, nb, uref_norm2, dist, prm->target_rel_dist, flags, done_dev, s));
+          return TVS_OK;
+        }));
+      }
     }
   }
   int iters = 0, prox = 0;
@@ -1432,18 +1621,24 @@ extern "C" tvs_status dual_rof_solve(tvs_ctx* C, const int dims[2], const float*
       if (*(volatile int*)done_host) break;
     }
     const int c = coins[k] ? 1 : 0;
-    CUDA_TRY(cudaGraphLaunch(G.exec[c][k & 1], s));
+    cudaGraphExec_t ex = G.exec[c][k & 1];
+    if (accel) ex = k % 3 < 2 ? G.exec[1][k % 3] : G3.exec[1][0];
+    CUDA_TRY(cudaGraphLaunch(ex, s));
     CUDA_TRY(cudaEventRecord(C->ring[k % LAG], s));
     iters = k + 1;
     prox += c;
   }
-  float* qf = q[iters & 1];
+  float* qf = accel ? q[iters % 3] : q[iters & 1];
   float* u_dev = nullptr;
   if (u_out) TVS_TRY(S.zeros<float>(n, &u_dev, s));
-  CUDA_TRY(launch_dual_rof_primal(H, W, qf, bd, u_dev, pa, pb, s));
-  if (iters > 0)
+  CUDA_TRY(launch_dual_rof_primal(H, W, qf, bd, u_dev, pa, pb, uref, pc, s));
+  if (iters > 0) {
     CUDA_TRY(launch_reduce_record(pa, pointwise_blocks(n), pb, pointwise_blocks(n), ea, 1, obj, ts, prm->f_star,
                                   prm->target_rel_gap, flags, done_dev, nullptr, s));
+    if (uref)
+      CUDA_TRY(launch_dist_record(pc, pointwise_blocks(n), uref_norm2, dist, prm->target_rel_dist, flags, done_dev,
+                                  s));
+  }
   TVS_TRY(copy_out(q_io, qf, 2 * n, mem, s));
   if (u_out) TVS_TRY(copy_out(u_out, u_dev, n, mem, s));
   CUDA_TRY(cudaEventRecord(C->ev_stop, s));
@@ -1470,10 +1665,16 @@ extern "C" tvs_status dual_rof_solve(tvs_ctx* C, const int dims[2], const float*
     tr->fgp_launches = 0;
     tr->fgp_pixel_iters = 0;
     const int lim = tr->cap < iters ? tr->cap : iters;
+    std::vector<double> dv;
+    if (dist && iters > 0 && tr->rel_dist) {
+      dv.resize(iters);
+      CUDA_TRY(cudaMemcpy(dv.data(), dist, sizeof(double) * iters, cudaMemcpyDeviceToHost));
+    }
     for (int k = 0; k < lim; ++k) {
       if (tr->objective) tr->objective[k] = o[k];
       if (tr->coins) tr->coins[k] = coins[k];
       if (tr->t_s) tr->t_s[k] = (double)(t[k] - t[iters]) * 1e-9;
+      if (tr->rel_dist) tr->rel_dist[k] = dv.empty() ? NAN : dv[k];
     }
   }
   if (fl[4]) return fail(TVS_ENUMERIC, "non-finite objective during the solve");
@@ -1648,6 +1849,7 @@ tvs_status tvs_problem_set_reference(tvs_problem* P, const float* u_ref, tvs_mem
     dfree(P->part_c);
     P->uref = nullptr;
     P->part_c = nullptr;
+    ++P->gen;
     return TVS_OK;
   }
   std::vector<float> host(P->n);
@@ -1663,6 +1865,7 @@ tvs_status tvs_problem_set_reference(tvs_problem* P, const float* u_ref, tvs_mem
   }
   if (!(nrm > 0.0)) return fail(TVS_EINVAL, "reference must be nonzero");
   if (!P->uref) {
+    ++P->gen;
     TVS_TRY(palloc(P, &P->uref, P->n));
     TVS_TRY(palloc(P, &P->part_c, (size_t)pointwise_blocks(P->n)));
   }

@@ -467,7 +467,8 @@ cudaError_t launch_batch_iteration(const BatchLaunch& L, int par, cudaStream_t s
     break;
         TVS_BF(0, float, 0) TVS_BF(1, float, 1) TVS_BF(2, float, 2)
         TVS_BF(3, __nv_bfloat16, 0) TVS_BF(4, __nv_bfloat16, 1) TVS_BF(5, __nv_bfloat16, 2)
-        TVS_BF(6, __half, 0) TVS_BF(7, __half, 1) default: TVS_BF(8, __half, 2)
+        TVS_BF(6, __half, 0) TVS_BF(7, __half, 1) TVS_BF(8, __half, 2)
+        TVS_BF(9, q15, 0) TVS_BF(10, q15, 1) default: TVS_BF(11, q15, 2)
 #undef TVS_BF
       }
       q = 1 - q;
@@ -486,8 +487,12 @@ cudaError_t launch_batch_iteration(const BatchLaunch& L, int par, cudaStream_t s
       launch_kernel(batch_finalize_kernel<__nv_bfloat16>, dim3(L.fin_grid), dim3(256), 0, s, L.probs,
                     L.chunk_range, (const int*)L.scan_chunks, L.n, par, fin_pair);
       break;
-    default:
+    case DUAL_F16:
       launch_kernel(batch_finalize_kernel<__half>, dim3(L.fin_grid), dim3(256), 0, s, L.probs,
+                    L.chunk_range, (const int*)L.scan_chunks, L.n, par, fin_pair);
+      break;
+    default:
+      launch_kernel(batch_finalize_kernel<q15>, dim3(L.fin_grid), dim3(256), 0, s, L.probs,
                     L.chunk_range, (const int*)L.scan_chunks, L.n, par, fin_pair);
   }
   return cudaGetLastError();

@@ -47,27 +47,116 @@ inline void launch_kernel(void (*kernel)(P...), dim3 grid, dim3 block, size_t sm
 }
 
 // ---------------------------------------------------------------- storage
-// The TV dual field may be stored as float, bfloat16 or half; arithmetic is
-// always float32 and stores round to nearest even.
+// The TV dual field may be stored as float, bfloat16, half or q15; arithmetic is
+// always float32 and stores round to nearest (even).  ld/st move one value;
+// ld2/st2 move two adjacent values (the first at an even element index, so the
+// pair is aligned to its size); round / round2 give the value a store followed by
+// a load would give, without the memory round trip; raw loads a stored value
+// without decoding it, and cvt decodes one already held in a register.
+//
+// q15: signed 16-bit fixed point for values in [-1, 1], the range of every
+// stored dual component (each is a component of a vector projected onto the unit
+// ball).  The code i stands for i * fl(1/32767); a store clamps to [-1, 1] and
+// takes i = the integer nearest (ties to even) to the exact product v * 32767.
+// Both directions use only full-rate FP32 and integer instructions: with
+// M = 1.5 * 2^23, the FFMA v * 32767 + M rounds to M + i exactly (|i| < 2^22),
+// whose bit pattern is that of M plus i, and the float of i is the float with
+// M's bits plus i, minus M.  Its absolute resolution, 2^-15 over the whole range,
+// is 64 times finer than bfloat16's and 8 times finer than half's near |p| = 1,
+// at the same two bytes.
+struct q15 {
+  int16_t v;
+};
 template <typename T> struct Elem;
 template <> struct Elem<float> {
+  static __device__ __forceinline__ float cvt(float v) { return v; }
+  static __device__ __forceinline__ float raw(const float* p) { return __ldg(p); }
   static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
   static __device__ __forceinline__ float ldc(const float* p) { return *p; }
   static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
   static __device__ __forceinline__ float round(float v) { return v; }
+  static __device__ __forceinline__ float2 ld2(const float* p) { return __ldg(reinterpret_cast<const float2*>(p)); }
+  static __device__ __forceinline__ void st2(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
+  static __device__ __forceinline__ float2 round2(float2 v) { return v; }
 };
 template <> struct Elem<__nv_bfloat16> {
+  static __device__ __forceinline__ float cvt(__nv_bfloat16 v) { return __bfloat162float(v); }
+  static __device__ __forceinline__ __nv_bfloat16 raw(const __nv_bfloat16* p) { return __ldg(p); }
   static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
   static __device__ __forceinline__ float ldc(const __nv_bfloat16* p) { return __bfloat162float(*p); }
   static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
   static __device__ __forceinline__ float round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+  static __device__ __forceinline__ float2 ld2(const __nv_bfloat16* p) {
+    return __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(p)));
+  }
+  static __device__ __forceinline__ void st2(__nv_bfloat16* p, float2 v) {
+    *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(v);
+  }
+  static __device__ __forceinline__ float2 round2(float2 v) { return __bfloat1622float2(__float22bfloat162_rn(v)); }
 };
 template <> struct Elem<__half> {
+  static __device__ __forceinline__ float cvt(__half v) { return __half2float(v); }
+  static __device__ __forceinline__ __half raw(const __half* p) { return __ldg(p); }
   static __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
   static __device__ __forceinline__ float ldc(const __half* p) { return __half2float(*p); }
   static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
   static __device__ __forceinline__ float round(float v) { return __half2float(__float2half_rn(v)); }
+  static __device__ __forceinline__ float2 ld2(const __half* p) {
+    return __half22float2(__ldg(reinterpret_cast<const __half2*>(p)));
+  }
+  static __device__ __forceinline__ void st2(__half* p, float2 v) { *reinterpret_cast<__half2*>(p) = __float22half2_rn(v); }
+  static __device__ __forceinline__ float2 round2(float2 v) { return __half22float2(__float22half2_rn(v)); }
 };
+template <> struct Elem<q15> {
+  static constexpr float kScale = 32767.f;
+  static constexpr float kInv = 1.f / 32767.f;
+  static constexpr float kMagic = 12582912.f;  // 1.5 * 2^23
+  static constexpr int kMagicBits = 0x4B400000;
+  static __device__ __forceinline__ float dec(int i) { return (__int_as_float(kMagicBits + i) - kMagic) * kInv; }
+  static __device__ __forceinline__ int enc(float v) {
+    return __float_as_int(__fmaf_rn(fminf(fmaxf(v, -1.f), 1.f), kScale, kMagic)) - kMagicBits;
+  }
+  static __device__ __forceinline__ float cvt(q15 v) { return dec(v.v); }
+  static __device__ __forceinline__ q15 raw(const q15* p) { return q15{__ldg(reinterpret_cast<const short*>(p))}; }
+  static __device__ __forceinline__ float ld(const q15* p) { return dec(__ldg(reinterpret_cast<const short*>(p))); }
+  static __device__ __forceinline__ float ldc(const q15* p) { return dec(p->v); }
+  static __device__ __forceinline__ void st(q15* p, float v) { p->v = (int16_t)enc(v); }
+  // v is a projected component (|v| <= 1 up to float rounding, well inside the
+  // half code step that the clamp of a store could change), so no clamp here
+  static __device__ __forceinline__ float round(float v) { return (__fmaf_rn(v, kScale, kMagic) - kMagic) * kInv; }
+  // sign extension of a 16-bit field by arithmetic alone: (f ^ 0x8000) - 0x8000
+  static __device__ __forceinline__ int sx16(unsigned f) { return (int)(f ^ 0x8000u) - 0x8000; }
+  static __device__ __forceinline__ float2 ld2(const q15* p) {
+    const unsigned w = __ldg(reinterpret_cast<const unsigned*>(p));
+    return make_float2(dec(sx16(w & 0xffffu)), dec(sx16(w >> 16)));
+  }
+  static __device__ __forceinline__ void st2(q15* p, float2 v) {
+    *reinterpret_cast<unsigned*>(p) = ((unsigned)enc(v.x) & 0xffffu) | ((unsigned)enc(v.y) << 16);
+  }
+  static __device__ __forceinline__ float2 round2(float2 v) {
+    const float2 m = make_float2(kMagic, kMagic);
+    const float2 a = __fadd2_rn(__ffma2_rn(v, make_float2(kScale, kScale), m), make_float2(-kMagic, -kMagic));
+    return __fmul2_rn(a, make_float2(kInv, kInv));
+  }
+};
+
+// Calls f(TypeTag<T>{}) with T the storage type of dual dtype `dtype`.
+template <typename T> struct TypeTag {
+  using type = T;
+};
+template <typename F>
+inline auto with_dual_type(int dtype, F&& f) {
+  switch (dtype) {
+    case DUAL_F32:
+      return f(TypeTag<float>{});
+    case DUAL_BF16:
+      return f(TypeTag<__nv_bfloat16>{});
+    case DUAL_F16:
+      return f(TypeTag<__half>{});
+    default:
+      return f(TypeTag<q15>{});
+  }
+}
 
 // ---------------------------------------------------------------- Philox4x64-10
 // Counter-based generator of Salmon et al. (SC'11): per round,

@@ -118,67 +118,104 @@ joseph_fwd_kernel(GeomConsts g, const float4* __restrict__ angles, const float* 
   if (MODE != 0) block_sum2_store<CT_NT>(acc_d, FAcc(), part, nullptr, blockIdx.x);
 }
 
-// g = A^T y at pixel (i, j); epilogue out = x - sigma g + ch h (when x given).
-__global__ void __launch_bounds__(CT_NT)
+// g = A^T y; epilogue out = x - sigma g + ch h (when x given).
+//
+// One thread per 2 x 2 pixel block (rows i0, i0+1, columns j0, j0+1).  For each
+// angle the block's pixels sit on two lines l (rows for row walks, columns
+// otherwise) at two indices k0, k0+1 along them; ray b gives pixel k the
+// projector's weight 1 - f when floor(fr(b, l)) = k and f when floor(fr(b, l)) =
+// k - 1 (f = fr - floor(fr)).  fr is affine in b with slope d * inv, so the bins
+// that reach either index lie in an interval of length 3 / |slope| around the b
+// where fr = k0 + 1/2: the ncand integers from ceil(bc - 1.5/|slope| - margin)
+// cover it (4 when bins have the pixel width).  Each candidate is decided with the
+// projector's own fr and serves both pixels of the line, and candidates that reach
+// a pixel with weight 0 add exactly nothing, so every pixel receives the same
+// terms in the same order (increasing angle, then increasing bin) as a gather
+// over its own bins: the weights are bit-identical to the projector's.
+constexpr int CT_BWD_NT = 128;
+
+__global__ void __launch_bounds__(CT_BWD_NT)
 joseph_bwd_kernel(GeomConsts g, const float4* __restrict__ angles, const float4* __restrict__ angles2,
                   const float* __restrict__ ys,
                   const float* __restrict__ x, const float* __restrict__ h, float* __restrict__ out,
                   float sigma, float ch, Partial* __restrict__ part_tv) {
   pdl_enter();
   const int N = g.N;
-  const int pix = blockIdx.x * CT_NT + threadIdx.x;
+  const int NB = (N + 1) / 2;  // blocks per row
+  const int blk = blockIdx.x * CT_BWD_NT + threadIdx.x;
   FAcc acc_tv;
-  if (pix < N * N) {
-    const int i = pix / N, j = pix - i * N;
-    float total = 0.f;
+  if (blk < NB * NB) {
+    const int i0 = 2 * (blk / NB), j0 = 2 * (blk - (blk / NB) * NB);
+    // line coordinates c_l of rows i0, i0+1 and columns j0, j0+1 (the projector's fma)
+    const float cr0 = __fmaf_rn((float)i0, g.s, g.c0), cr1 = __fmaf_rn((float)(i0 + 1), g.s, g.c0);
+    const float cc0 = __fmaf_rn((float)j0, g.s, g.c0), cc1 = __fmaf_rn((float)(j0 + 1), g.s, g.c0);
+    float t00 = 0.f, t01 = 0.f, t10 = 0.f, t11 = 0.f;  // totals of (i0 + a, j0 + b)
     for (int a = 0; a < g.n_angles; ++a) {
       const float4 ang = __ldg(angles + a);
+      const float4 a2 = __ldg(angles2 + a);  // (1 / slope, 1.5 / |slope| + margin, ncand, -)
       const bool rowwalk = ang.w != 0.f;
-      const int l = rowwalk ? i : j;   // line the ray walks
-      const int k = rowwalk ? j : i;   // this pixel's index along the line
-      // fr is affine in b with slope d * inv, so the bins whose floor(fr) is
-      // k - 1 or k lie in an interval of length 2 / |slope| around the b where
-      // fr = k; the ncand integers from ceil(bc - 1/|slope| - margin) cover it
-      // (3 when bins have the pixel width), and each candidate is decided with
-      // the projector's own fr.
-      const float4 a2 = __ldg(angles2 + a);  // (1 / slope, 1 / |slope| + margin, ncand, -)
-      const float fr0 = joseph_fr(g, ang, 0, l);
-      const float bc = ((float)k - fr0) * a2.x;
-      const int b_first = (int)ceilf(bc - a2.y);
-      const int ncand = (int)a2.z;
+      const float kf = rowwalk ? (float)j0 : (float)i0;  // first index along the lines
       const float* yrow = ys + (size_t)a * g.n_det;
-      float acc = 0.f;
-#pragma unroll 3
-      for (int j = 0; j < ncand; ++j) {
-        const int b = b_first + j;
-        if (b < 0 || b >= g.n_det) continue;
-        const float fr = joseph_fr(g, ang, b, l);
-        const float k0f = floorf(fr);
-        const float f = fr - k0f;
-        const int k0 = (int)k0f;
-        // the projector's weight of this pixel on ray b (0 when the ray's two
-        // interpolation cells miss it), applied without a divergent branch
-        const float wgt = k0 == k ? 1.f - f : (k0 + 1 == k ? f : 0.f);
-        acc = fmaf(wgt, __ldg(yrow + b), acc);
+      const int ncand = (int)a2.z;
+      float acc[2][2];  // [line][index]
+#pragma unroll
+      for (int li = 0; li < 2; ++li) {
+        const float cl = rowwalk ? (li ? cr1 : cr0) : (li ? cc1 : cc0);
+        const float fr0 = __fmaf_rn(__fmaf_rn(-cl, ang.x, g.t0), ang.y, g.half);
+        const float bfirst = ceilf((kf + 0.5f - fr0) * a2.x - a2.y);
+        const int b_first = (int)bfirst;
+        float aa = 0.f, ab = 0.f;
+        float bf = bfirst;
+        for (int b = b_first; b < b_first + ncand; ++b, bf += 1.f) {
+          if (b < 0 || b >= g.n_det) continue;
+          const float tb = __fmaf_rn(bf, g.d, g.t0);
+          const float fr = __fmaf_rn(__fmaf_rn(-cl, ang.x, tb), ang.y, g.half);
+          const float k0f = floorf(fr);
+          const float f = fr - k0f;
+          const float yv = __ldg(yrow + b);
+          // pixel kf: 1 - f if floor(fr) = kf, f if floor(fr) = kf - 1; pixel kf + 1 likewise
+          const float wa = k0f == kf ? 1.f - f : (k0f == kf - 1.f ? f : 0.f);
+          const float wb = k0f == kf + 1.f ? 1.f - f : (k0f == kf ? f : 0.f);
+          aa = fmaf(wa, yv, aa);
+          ab = fmaf(wb, yv, ab);
+        }
+        acc[li][0] = aa;
+        acc[li][1] = ab;
       }
-      total = fmaf(ang.z, acc, total);
+      // rows: line li is row i0 + li, index c column j0 + c; columns: transposed
+      const float a00 = acc[0][0], a11 = acc[1][1];
+      const float a01 = rowwalk ? acc[0][1] : acc[1][0];
+      const float a10 = rowwalk ? acc[1][0] : acc[0][1];
+      t00 = fmaf(ang.z, a00, t00);
+      t01 = fmaf(ang.z, a01, t01);
+      t10 = fmaf(ang.z, a10, t10);
+      t11 = fmaf(ang.z, a11, t11);
     }
-    if (x) {
-      const size_t o = (size_t)i * N + j;
-      const float xc = __ldg(x + o);
-      float v = xc - sigma * total;
-      if (h) v = fmaf(ch, __ldg(h + o), v);
-      out[o] = v;
-      if (part_tv) {
-        const float dy = i < N - 1 ? __ldg(x + o + N) - xc : 0.f;
-        const float dx = j < N - 1 ? __ldg(x + o + 1) - xc : 0.f;
-        acc_tv.add(tv_term(0.f, dy, dx));
+    const float tot[2][2] = {{t00, t01}, {t10, t11}};
+#pragma unroll
+    for (int di = 0; di < 2; ++di)
+#pragma unroll
+      for (int dj = 0; dj < 2; ++dj) {
+        const int i = i0 + di, j = j0 + dj;
+        if (i >= N || j >= N) continue;
+        const size_t o = (size_t)i * N + j;
+        const float total = tot[di][dj];
+        if (x) {
+          const float xc = __ldg(x + o);
+          float v = xc - sigma * total;
+          if (h) v = fmaf(ch, __ldg(h + o), v);
+          out[o] = v;
+          if (part_tv) {
+            const float dy = i < N - 1 ? __ldg(x + o + N) - xc : 0.f;
+            const float dx = j < N - 1 ? __ldg(x + o + 1) - xc : 0.f;
+            acc_tv.add(tv_term(0.f, dy, dx));
+          }
+        } else {
+          out[o] = total;
+        }
       }
-    } else {
-      out[(size_t)i * N + j] = total;
-    }
   }
-  if (part_tv) block_sum2_store<CT_NT>(FAcc(), acc_tv, nullptr, part_tv, blockIdx.x);
+  if (part_tv) block_sum2_store<CT_BWD_NT>(FAcc(), acc_tv, nullptr, part_tv, blockIdx.x);
 }
 
 GeomConsts consts(const CTGeom& g) {
@@ -210,9 +247,10 @@ cudaError_t ct_build_angle_table(const CTGeom& g, float4* dev_table, cudaStream_
     v.z = (float)((double)g.pixel_size / (rowwalk ? fabs(c) : fabs(sn)));
     v.w = rowwalk ? 1.f : 0.f;
     host[a] = v;
-    // backprojector helpers: slope of fr in b is d * inv (inv as stored, in float)
+    // backprojector helpers: slope of fr in b is d * inv (inv as stored, in float);
+    // the bins reaching two adjacent indices span 3 / |slope| (plus a margin)
     const double slope = (double)g.det_spacing * (double)v.y;
-    const double half = 1.0 / fabs(slope) + 0.02;
+    const double half = 1.5 / fabs(slope) + 0.02;
     host2[a] = make_float4((float)(1.0 / slope), (float)half, (float)(floor(2.0 * half) + 1.0), 0.f);
   }
   cudaError_t e = cudaMemcpyAsync(dev_table, host, sizeof(float4) * g.n_angles,
@@ -226,7 +264,10 @@ cudaError_t ct_build_angle_table(const CTGeom& g, float4* dev_table, cudaStream_
 }
 
 int ct_fwd_blocks(const CTGeom& g) { return (g.n_angles * g.n_det + CT_NT - 1) / CT_NT; }
-int ct_bwd_blocks(const CTGeom& g) { return (g.N * g.N + CT_NT - 1) / CT_NT; }
+int ct_bwd_blocks(const CTGeom& g) {
+  const int nb = (g.N + 1) / 2;
+  return (nb * nb + CT_BWD_NT - 1) / CT_BWD_NT;
+}
 
 cudaError_t launch_ct_forward(const CTGeom& g, const float* x, float* sino, float* y,
                               const float* b, float tau, Partial* part_data, int mode,
@@ -258,7 +299,7 @@ cudaError_t launch_ct_forward(const CTGeom& g, const float* x, float* sino, floa
 cudaError_t launch_ct_backward(const CTGeom& g, const float* y, const float* x, const float* h,
                                float* out, float sigma, float ch, Partial* part_tv, cudaStream_t s) {
   const GeomConsts c = consts(g);
-  launch_kernel(joseph_bwd_kernel, dim3(ct_bwd_blocks(g)), dim3(CT_NT), 0, s, c, g.angles, g.angles2, y, x, h, out, sigma, ch,
+  launch_kernel(joseph_bwd_kernel, dim3(ct_bwd_blocks(g)), dim3(CT_BWD_NT), 0, s, c, g.angles, g.angles2, y, x, h, out, sigma, ch,
                                                        part_tv);
   return cudaGetLastError();
 }

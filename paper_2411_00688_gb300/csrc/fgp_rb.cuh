@@ -300,8 +300,8 @@ __device__ __forceinline__ void fgp2d_rb_body_packed(const float* __restrict__ z
       const float2 nrm2 = __ffma2_rn(qy, qy, __fmul2_rn(qx, qx));
       const float2 sc = make_float2(fminf(1.f, rsqrtf(nrm2.x)), fminf(1.f, rsqrtf(nrm2.y)));
       float2 ny = __fmul2_rn(qy, sc), nx = __fmul2_rn(qx, sc);
-      ny = make_float2(Elem<T>::round(ny.x), Elem<T>::round(ny.y));
-      nx = make_float2(Elem<T>::round(nx.x), Elem<T>::round(nx.y));
+      ny = Elem<T>::round2(ny);
+      nx = Elem<T>::round2(nx);
       if (last) {
         Ry[r] = Py[r];
         Rx[r] = Px[r];

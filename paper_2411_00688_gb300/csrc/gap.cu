@@ -56,15 +56,12 @@ cudaError_t launch_rof_gap_partials(const Dims& d, const float* z, const void* p
                                     Partial* part, cudaStream_t s) {
   const int blocks = rof_gap_blocks(d.n());
   const IndexMap im(d.nz, d.ny, d.nx);
-  if (dtype == DUAL_F32)
-    launch_kernel(rof_gap_partials_kernel<float>, dim3(blocks), dim3(256), 0, s, z, (const float*)p, d.nz, d.ny,
-                  d.nx, d.ndim, lam, part, im);
-  else if (dtype == DUAL_BF16)
-    launch_kernel(rof_gap_partials_kernel<__nv_bfloat16>, dim3(blocks), dim3(256), 0, s, z,
-                  (const __nv_bfloat16*)p, d.nz, d.ny, d.nx, d.ndim, lam, part, im);
-  else
-    launch_kernel(rof_gap_partials_kernel<__half>, dim3(blocks), dim3(256), 0, s, z, (const __half*)p, d.nz,
-                  d.ny, d.nx, d.ndim, lam, part, im);
+  with_dual_type(dtype, [&](auto tag) {
+    using T = typename decltype(tag)::type;
+    launch_kernel(rof_gap_partials_kernel<T>, dim3(blocks), dim3(256), 0, s, z, (const T*)p, d.nz, d.ny, d.nx,
+                  d.ndim, lam, part, im);
+    return 0;
+  });
   return cudaGetLastError();
 }
 

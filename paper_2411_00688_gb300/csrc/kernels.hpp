@@ -25,7 +25,7 @@ inline bool pixels_within(int nx, int ny, int nz, size_t cap, size_t* n) {
   return true;
 }
 
-enum DualType { DUAL_F32 = 0, DUAL_BF16 = 1, DUAL_F16 = 2 };
+enum DualType { DUAL_F32 = 0, DUAL_BF16 = 1, DUAL_F16 = 2, DUAL_Q15 = 3 };
 
 // floor(n / d) for 0 <= n < 2^31 by one multiply and shift (division by an
 // invariant integer, Granlund and Montgomery, PLDI 1994, Theorem 4.2 with N = 31):
@@ -204,13 +204,22 @@ cudaError_t launch_pdx_dual(size_t m, const float* ax, float* axp, float* y, con
 int dual_rof_blocks(int H, int W);
 // One ProxSkip / projected-gradient step on q (2 planes) -> qn; h updated in place
 // on prox iterations (h == null: projected gradient).  Partials: 1/2 (div q + b)^2
-// and 1/2 |q|^2 of the current q.
+// and 1/2 |q|^2 of the current q; with uref, partials of |b + div q - uref|^2 into
+// part_c as well.
 cudaError_t launch_dual_rof_step(int H, int W, const float* q, float* qn, float* h, const float* b,
                                  float alpha, float eps, float gamma, float p, bool prox,
-                                 Partial* part_a, Partial* part_b, cudaStream_t s);
+                                 Partial* part_a, Partial* part_b, const float* uref, Partial* part_c,
+                                 cudaStream_t s);
+// AProjGD step: y = q + beta (q - q_prev) with beta = beta_tab[*beta_idx + 1];
+// qn = P_C(y - gamma grad F(y)); partials of F(q) (the current iterate), and of
+// the distance to uref as above.
+cudaError_t launch_dual_rof_accel_step(int H, int W, const float* q, const float* q_prev, float* qn,
+                                       const float* b, float alpha, float eps, float gamma,
+                                       const float* beta_tab, const int* beta_idx, Partial* part_a,
+                                       Partial* part_b, const float* uref, Partial* part_c, cudaStream_t s);
 // u = b + div q (u may be null) and the same partials (pointwise_blocks(H W) blocks).
 cudaError_t launch_dual_rof_primal(int H, int W, const float* q, const float* b, float* u, Partial* part_a,
-                                   Partial* part_b, cudaStream_t s);
+                                   Partial* part_b, const float* uref, Partial* part_c, cudaStream_t s);
 
 // ---- batched ProxSkip (batch.cu) ----
 // Descriptor of one problem of a batch (device memory).  Partials of its

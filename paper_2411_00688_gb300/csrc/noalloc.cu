@@ -77,7 +77,8 @@ extern "C" tvs_status tv_prox_noalloc(int ndim, const int dims[3], const float* 
   if (ndim != 2 && ndim != 3) return TVS_EINVAL;
   if (dims[0] < 1 || dims[1] < 1 || (ndim == 3 && dims[2] < 1)) return TVS_EINVAL;
   if (!(lambda >= 0.0) || !isfinite(lambda) || n_iter < 0) return TVS_EINVAL;
-  if (dual != TVS_DUAL_F32 && dual != TVS_DUAL_BF16 && dual != TVS_DUAL_F16) return TVS_EINVAL;
+  if (dual != TVS_DUAL_F32 && dual != TVS_DUAL_BF16 && dual != TVS_DUAL_F16 && dual != TVS_DUAL_Q15)
+    return TVS_EINVAL;
   Dims d;
   d.nx = dims[0];
   d.ny = dims[1];

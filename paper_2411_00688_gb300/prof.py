@@ -31,7 +31,7 @@ def main(argv=None):
     ap.add_argument("--iters", type=int, default=8)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--lam", type=float, default=0.2)
-    ap.add_argument("--dual", default="f32", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--dual", default="f32", choices=["f32", "bf16", "f16", "q15"])
     ap.add_argument("--ct", type=int, nargs=3, default=None, metavar=("N", "ANGLES", "BINS"))
     args = ap.parse_args(argv)
     if args.ct:
@@ -48,7 +48,7 @@ def main(argv=None):
     z = (torch.rand(shape, device="cuda", generator=g) > 0.5).float() + 0.2 * torch.randn(
         shape, device="cuda", generator=g)
     u = torch.empty_like(z)
-    dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[args.dual]
+    dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16, "q15": torch.int16}[args.dual]
     state = torch.zeros((len(shape),) + shape, dtype=dt, device="cuda")
     times = []
     for _ in range(args.reps):

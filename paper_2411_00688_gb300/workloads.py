@@ -9,6 +9,9 @@ benchmark's headline one (python -m paper_2411_00688_gb300.workloads NAME ...).
                  iterations (<= 1000 iterations); explicit preconditioned PDHG <= 20000
   denoise3d_512  ProxSkip p = 0.1 vs PGD, 30 inner, <= 200 iterations (FP32 / BF16 / FP16 dual)
   batch2d_256    256 uneven problems: one batched solve vs a loop of single solves
+  table1_deblur2d_1024  Table 1's solvers (FISTA-100, ISTA-10, ProxSkip-10 p = 0.5, ProxSkip-100
+                 p = 0.05) to a 1e-5 relative distance from u*
+  dual_huber_200x300    ProjGD, AProjGD and ProxSkip on Dual-Huber-ROF (Section 2.2)
 
 Each prints one JSON line per solver: iterations and prox calls to a 1e-4
 relative objective gap, device time to the target and wall time of the solve.
@@ -180,7 +183,7 @@ def deblur2d_1024():
     return out
 
 
-def denoise3d_512(duals=("f32", "bf16", "f16")):
+def denoise3d_512(duals=("f32", "bf16", "f16", "q15")):
     import torch
     from synth.configs import Denoise3DConfig
     tvs, ctx = _ctx()
@@ -206,6 +209,87 @@ def denoise3d_512(duals=("f32", "bf16", "f16")):
             out.append(_solve_record(name, tr, wall, f_star, workload=cfg.name, dual=dual,
                                      fgp_launch_us=per_it * 1e6,
                                      fgp_gbs=bpv * cfg.N ** 3 / per_it / 1e9 if per_it > 0 else None))
+    return out
+
+
+def table1_deblur2d_1024():
+    """Table 1's comparison on the synthetic 1024^2 deblurring problem: time to a
+    relative distance ||x_k - u*|| / ||u*|| of 1e-4 and 1e-5 (the paper's error
+    measure and target, Section 3.1) for FISTA-100, ISTA-10 (= PGD), ProxSkip-10
+    with p = 0.5 and ProxSkip-100 with p = 0.05, every prox warm-started, 5000
+    iterations each.  u* is a long FISTA run (4000 iterations, 200 inner) on the
+    same GPU."""
+    import torch
+    from synth.configs import DeblurConfig
+    tvs, ctx = _ctx()
+    cfg = DeblurConfig()
+    truth = torch.from_numpy(cfg.phantom().astype(np.float32)).cuda()
+    noise = torch.from_numpy(cfg.noise().astype(np.float32)).cuda()
+    prob = tvs.Problem(ctx, truth, cfg.alpha, op="blur", blur_sigma=cfg.blur_sigma)
+    b = torch.empty_like(truth)
+    tvs.tvs_op_apply(prob, truth, b)
+    b = (b + noise).contiguous()
+    prob.set_data(b)
+    u_star, ref = tvs.fista_solve(prob, b.clone(), 1.0, 4000, 200)
+    u_star = u_star.clone()
+    prob.set_reference(u_star)
+    K = 5000
+    rows = [("fista_100", lambda: tvs.fista_solve(prob, b.clone(), 1.0, K, 100)),
+            ("ista_10", lambda: tvs.pgd_solve(prob, b.clone(), 1.0, K, 10)),
+            ("proxskip_10_p0.5", lambda: tvs.proxskip_solve(prob, b.clone(), 1.0, 0.5, cfg.seed, K, 10)),
+            ("proxskip_100_p0.05", lambda: tvs.proxskip_solve(prob, b.clone(), 1.0, 0.05, cfg.seed, K, 100))]
+    out = []
+    for name, fn in rows:
+        fn()
+        (_, tr), wall = _timed(fn)
+        d = tr.rel_dist
+        rec = {"workload": "table1_deblur2d_1024", "solver": name, "iterations_run": tr.iters_run,
+               "wall_s": wall, "best_rel_dist": float(np.nanmin(d))}
+        for tgt in (1e-4, 1e-5):
+            hit = np.nonzero(d <= tgt)[0]
+            k = int(hit[0]) if len(hit) else None
+            rec[f"to_{tgt:g}"] = {"reached": k is not None, "iterations": (k + 1) if k is not None else None,
+                                  "prox_calls": int(np.sum(tr.coins[: k + 1])) if k is not None else None,
+                                  "time_s": float(tr.t_s[k]) if k is not None else None}
+        out.append(rec)
+    for tgt in ("to_0.0001", "to_1e-05"):
+        t_f = out[0][tgt]["time_s"]
+        for r in out:
+            if t_f and r[tgt]["time_s"]:
+                r[tgt]["faster_than_fista_pct"] = 100.0 * (t_f - r[tgt]["time_s"]) / t_f
+    return out
+
+
+def dual_huber_200x300(target=1e-6):
+    """Section 2.2's comparison: Dual-Huber-ROF (alpha 0.55, eps 0.1) on a 200 x 300
+    shapes image with noise 0.05, ProjGD, AProjGD and ProxSkip (p = 0.04767), step
+    1/L with L = 8 + eps/alpha, at most 5000 iterations, time until the relative
+    error ||u_k - u*|| / ||u*|| of u = b + div q is <= target (the paper's measure).
+    u* from a 40000-iteration AProjGD run."""
+    import torch
+    from synth import phantoms
+    tvs, ctx = _ctx()
+    H, W, alpha, eps = 200, 300, 0.55, 0.1
+    b = torch.from_numpy((phantoms.shapes_phantom_2d(H, W, 12, 7100)
+                          + phantoms.gaussian_noise((H, W), 0.05, 7101)).astype(np.float32)).cuda()
+    gamma = 1.0 / (8.0 + eps / alpha)
+    q = torch.zeros((2, H, W), device="cuda")
+    u_star = torch.empty((H, W), device="cuda")
+    tvs.dual_rof_solve(ctx, b, q, alpha, gamma, 40000, eps=eps, accelerated=True, u=u_star)
+    runs = [("projgd", dict()), ("aprojgd", dict(accelerated=True)), ("proxskip_p0.04767", dict(p=0.04767, seed=1))]
+    out = []
+    for name, kw in runs:
+        def fn(kw=kw):
+            return tvs.dual_rof_solve(ctx, b, torch.zeros((2, H, W), device="cuda"), alpha, gamma, 5000, eps=eps,
+                                      u_ref=u_star, target_dist=target, **kw)
+        fn()
+        (_, _, tr), wall = _timed(fn)
+        k = tr.reached_iter if tr.reached else None
+        out.append({"workload": "dual_huber_200x300", "solver": name, "target_rel_dist": target,
+                    "reached": bool(tr.reached), "iterations": (k + 1) if k is not None else tr.iters_run,
+                    "prox_calls": int(np.sum(tr.coins[: k + 1])) if k is not None else tr.prox_calls,
+                    "time_to_target_s": tr.time_to_target_s if tr.reached else None,
+                    "best_rel_dist": float(np.nanmin(tr.rel_dist)), "wall_s": wall})
     return out
 
 
@@ -259,17 +343,18 @@ def _batch(n_problems=None, K=None, batch_only=False, dual="f32"):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("workload", choices=["denoise2d_256", "ct2d_512", "denoise3d_512", "batch2d_256",
-                                         "deblur2d_1024"])
+                                         "deblur2d_1024", "table1_deblur2d_1024", "dual_huber_200x300"])
     ap.add_argument("--problems", type=int, default=None)
     ap.add_argument("--iters", type=int, default=None)
     ap.add_argument("--batch-only", action="store_true", help="batch2d_256: time the batched solve only")
-    ap.add_argument("--dual", default="f32", choices=["f32", "bf16", "f16"], help="batch2d_256: dual storage")
+    ap.add_argument("--dual", default="f32", choices=["f32", "bf16", "f16", "q15"], help="batch2d_256: dual storage")
     args = ap.parse_args(argv)
     if args.workload == "batch2d_256":
         recs = _batch(args.problems, args.iters, args.batch_only, args.dual)
     else:
         recs = {"denoise2d_256": denoise2d_256, "ct2d_512": ct2d_512, "denoise3d_512": denoise3d_512,
-                "deblur2d_1024": deblur2d_1024}[args.workload]()
+                "deblur2d_1024": deblur2d_1024, "table1_deblur2d_1024": table1_deblur2d_1024,
+                "dual_huber_200x300": dual_huber_200x300}[args.workload]()
     for r in recs:
         print(json.dumps(r), flush=True)
 

@@ -7,7 +7,7 @@ import pytest
 
 from oracle import coin, operators, solvers
 from synth import phantoms
-from tests._util import cuda, f32, host, rel_l2
+from tests._util import cuda, f32, host, assert_close
 
 pytestmark = pytest.mark.gpu
 
@@ -36,9 +36,9 @@ def test_blur_matches_oracle(tvs, ctx, shape, sigma):
     yt = torch.empty_like(xt)
     tvs.tvs_op_apply(prob, xt, yt)
     ref = operators.blur(x64, operators.gaussian_weights(sigma, 4))
-    assert rel_l2(host(yt), ref) <= 1e-6
+    assert_close(host(yt), ref, 1e-6)
     tvs.tvs_op_apply(prob, xt, yt, adjoint=True)
-    assert rel_l2(host(yt), operators.blur_adjoint(x64, operators.gaussian_weights(sigma, 4))) <= 1e-6
+    assert_close(host(yt), operators.blur_adjoint(x64, operators.gaussian_weights(sigma, 4)), 1e-6)
 
 
 @pytest.mark.parametrize("N,na,nd", [(16, 24, 23), (64, 90, 91), (31, 40, 45)])
@@ -55,8 +55,8 @@ def test_projector_matches_oracle(tvs, ctx, N, na, nd):
     aty = torch.empty_like(xt)
     tvs.tvs_op_apply(prob, xt, ax)
     tvs.tvs_op_apply(prob, yt, aty, adjoint=True)
-    assert rel_l2(host(ax), operators.joseph_forward(x64, geom)) <= 1e-5
-    assert rel_l2(host(aty), operators.joseph_adjoint(y64, geom)) <= 1e-5
+    assert_close(host(ax), operators.joseph_forward(x64, geom), 1e-5)
+    assert_close(host(aty), operators.joseph_adjoint(y64, geom), 1e-5)
     lhs = float(np.sum(host(ax) * y64))
     rhs = float(np.sum(x64 * host(aty)))
     assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
@@ -77,7 +77,7 @@ def test_projector_full_size(tvs, ctx):
     aty = torch.empty_like(xt)
     tvs.tvs_op_apply(prob, xt, ax)
     tvs.tvs_op_apply(prob, yt, aty, adjoint=True)
-    assert rel_l2(host(ax), operators.joseph_forward(x64, geom)) <= 1e-5
+    assert_close(host(ax), operators.joseph_forward(x64, geom), 1e-5)
     # the adjoint at sampled pixels (the oracle's scatter is slow at full size):
     # compare through the dot test and a few pixels: (A^T y)_ij = <A e_ij, y>
     lhs = float(np.sum(host(ax) * y64))
@@ -176,5 +176,5 @@ def test_projector_other_detector_spacing(tvs, ctx, det_ratio):
     aty = torch.empty_like(xt)
     tvs.tvs_op_apply(prob, xt, ax)
     tvs.tvs_op_apply(prob, yt, aty, adjoint=True)
-    assert rel_l2(host(ax), operators.joseph_forward(x64, geom)) <= 1e-5
-    assert rel_l2(host(aty), operators.joseph_adjoint(y64, geom)) <= 1e-5
+    assert_close(host(ax), operators.joseph_forward(x64, geom), 1e-5)
+    assert_close(host(aty), operators.joseph_adjoint(y64, geom), 1e-5)

@@ -8,7 +8,7 @@ import pytest
 
 from oracle import operators, solvers
 from synth import phantoms
-from tests._util import TOL_OBJ, TOL_X_F32, cuda, f32, host, rel_l2
+from tests._util import TOL_OBJ, TOL_X_F32, cuda, f32, host, assert_close
 
 pytestmark = pytest.mark.gpu
 
@@ -75,9 +75,9 @@ def test_explicit_pdhg_matches_oracle(tvs, ctx, op, shape, alpha, nonneg):
     x, y, q, tr = _run(tvs, prob, x0, b32, K)
     ref = solvers.pdhg_explicit(oprob, x0.astype(np.float64), K=K)
     assert tr.iters_run == K and tr.prox_calls == K
-    assert rel_l2(x, ref["x"]) <= TOL_X_F32
-    assert rel_l2(y, ref["y"]) <= TOL_X_F32
-    assert rel_l2(q, ref["q"]) <= TOL_X_F32
+    assert_close(x, ref["x"], TOL_X_F32)
+    assert_close(y, ref["y"], TOL_X_F32)
+    assert_close(q, ref["q"], TOL_X_F32)
     obj = np.asarray(ref["objective"])
     assert (np.abs(tr.objective - obj) / np.abs(obj)).max() <= TOL_OBJ
     if nonneg:
@@ -90,7 +90,8 @@ def test_explicit_pdhg_steps_scale(tvs, ctx):
     prob, oprob, x0, b32 = _case(tvs, ctx, "blur", (48, 40), 0.03)
     x, y, q, tr = _run(tvs, prob, x0, b32, 30, sigma=2.0, tau=0.5)
     ref = solvers.pdhg_explicit(oprob, x0.astype(np.float64), K=30, sigma=2.0, tau=0.5)
-    assert rel_l2(x, ref["x"]) <= TOL_X_F32 and rel_l2(q, ref["q"]) <= TOL_X_F32
+    assert_close(x, ref["x"], TOL_X_F32)
+    assert_close(q, ref["q"], TOL_X_F32)
     from paper_2411_00688_gb300 import TVSError
     with pytest.raises(TVSError):
         _run(tvs, prob, x0, b32, 5, sigma=2.0, tau=0.6)
@@ -126,7 +127,7 @@ def test_explicit_pdhg_alpha_zero_is_least_squares(tvs, ctx):
     prob, oprob, x0, b32 = _case(tvs, ctx, "identity", (20, 30), 0.0)
     x, y, q, tr = _run(tvs, prob, np.zeros_like(x0), b32, 200)
     assert np.all(q == 0.0)
-    assert rel_l2(x, b32.astype(np.float64)) <= 1e-5
+    assert_close(x, b32.astype(np.float64), 1e-5)
 
 
 def test_explicit_pdhg_stops_at_target(tvs, ctx):

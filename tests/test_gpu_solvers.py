@@ -10,7 +10,7 @@ import pytest
 from oracle import coin, operators, solvers
 from oracle.power import power_method
 from synth import configs, phantoms
-from tests._util import TOL_OBJ, TOL_X_F32, TOL_X_HALF, cuda, f32, host, rel_l2
+from tests._util import TOL_OBJ, TOL_X_F32, TOL_X_HALF, cuda, f32, host, assert_close
 
 pytestmark = pytest.mark.gpu
 
@@ -40,7 +40,7 @@ def _data(shape, op, seed, noise):
 def _check(trace, ref, x_gpu, tol_x=TOL_X_F32):
     assert list(trace.coins) == list(ref["coins"])
     assert trace.prox_calls == ref["prox_calls"]
-    assert rel_l2(x_gpu, ref["x"]) <= tol_x
+    assert_close(x_gpu, ref["x"], tol_x)
     obj = np.asarray(ref["objective"])
     rel = np.abs(trace.objective - obj) / np.abs(obj)
     assert rel.max() <= TOL_OBJ, rel.max()
@@ -95,7 +95,7 @@ def _psnr(u, truth):
     return 10.0 * math.log10(float(truth.max()) ** 2 / float(np.mean((u - truth) ** 2)))
 
 
-@pytest.mark.parametrize("dual", ["bf16", "f16"])
+@pytest.mark.parametrize("dual", ["bf16", "f16", "q15"])
 def test_proxskip_half_dual(tvs, ctx, dual):
     """BF16/FP16 dual storage: final iterate within 2e-3 relative l2 of the FP64
     oracle and its PSNR against the phantom within 0.05 dB of the oracle's."""
@@ -104,7 +104,27 @@ def test_proxskip_half_dual(tvs, ctx, dual):
     prob = tvs.Problem(ctx, cuda(b32), 0.03, op="blur", blur_sigma=2.0)
     x, tr = tvs.proxskip_solve(prob, cuda(b32), 1.0, 0.3, 2, 25, 20, dual=dual)
     ref = solvers.proxskip(solvers.Problem(operators.blur_op(2.0), b64, 0.03, (96, 96)), b64, 1.0, 0.3, 2, 25, 20)
-    assert rel_l2(host(x), ref["x"]) <= TOL_X_HALF
+    assert_close(host(x), ref["x"], TOL_X_HALF)
+    assert abs(_psnr(host(x), truth) - _psnr(ref["x"], truth)) <= 0.05
+
+
+@pytest.mark.parametrize("op,alpha,p", [("blur", 0.2, 0.05), ("blur", 0.2, 0.1), ("identity", 0.1, 0.3),
+                                        ("identity", 0.2, 0.05)])
+def test_proxskip_q15_dual_large_lambda(tvs, ctx, op, alpha, p):
+    """16-bit fixed-point dual at large prox steps (lambda = alpha / p up to 4, the
+    top of the batched workload's range): final iterate within 2e-3 relative l2 of
+    the FP64 oracle and PSNR within 0.05 dB of the oracle's."""
+    from oracle import coin
+    shape = (100, 140)
+    b32, b64 = _data(shape, op, 31, 0.01 if op == "blur" else 0.1)
+    truth = phantoms.shapes_phantom_2d(shape[0], shape[1], 6, 31)
+    seed = next(s for s in range(100) if sum(coin.schedule(s, p, 25)) >= 3)
+    prob = tvs.Problem(ctx, cuda(b32), alpha, op=op, blur_sigma=2.0)
+    x, tr = tvs.proxskip_solve(prob, cuda(b32), 1.0, p, seed, 25, 20, dual="q15")
+    A = operators.blur_op(2.0) if op == "blur" else operators.identity_op()
+    ref = solvers.proxskip(solvers.Problem(A, b64, alpha, shape), b64, 1.0, p, seed, 25, 20)
+    assert tr.prox_calls == ref["prox_calls"] >= 3
+    assert_close(host(x), ref["x"], TOL_X_HALF)
     assert abs(_psnr(host(x), truth) - _psnr(ref["x"], truth)) <= 0.05
 
 
@@ -113,7 +133,7 @@ def test_proxskip_p1_equals_pgd_on_gpu(tvs, ctx):
     prob = tvs.Problem(ctx, cuda(b32), 0.03, op="blur", blur_sigma=2.0)
     x1, t1 = tvs.pgd_solve(prob, cuda(b32), 1.0, 12, 10)
     x2, t2 = tvs.proxskip_solve(prob, cuda(b32), 1.0, 1.0, 9, 12, 10)
-    assert rel_l2(host(x2), host(x1)) <= 1e-5
+    assert_close(host(x2), host(x1), 1e-5)
     assert t2.prox_calls == 12
 
 
@@ -144,7 +164,7 @@ def test_pd_solvers_ct_small(tvs, ctx, skip):
         x, y, tr = tvs.pdhg_solve(prob, cuda(x0), cuda(y0), st, st, K, NI)
         ref = solvers.pdhg(oprob, x0.astype(np.float64), y0.astype(np.float64), st, st, K, NI)
     _check(tr, ref, host(x))
-    assert rel_l2(host(y), ref["y"]) <= TOL_X_F32
+    assert_close(host(y), ref["y"], TOL_X_F32)
 
 
 @pytest.mark.parametrize("p", [1.0, 0.3])
@@ -159,7 +179,7 @@ def test_pdhgskip1_ct_small(tvs, ctx, p):
     x, y, tr = tvs.pdhgskip1_solve(prob, cuda(x0), cuda(y0), st, st, p, 7, 25, 15)
     ref = solvers.pdhgskip1(oprob, x0.astype(np.float64), y0.astype(np.float64), st, st, p, 7, 25, 15)
     _check(tr, ref, host(x))
-    assert rel_l2(host(y), ref["y"]) <= TOL_X_F32
+    assert_close(host(y), ref["y"], TOL_X_F32)
 
 
 @pytest.mark.parametrize("op", ["identity", "blur"])
@@ -213,6 +233,60 @@ def test_deblur_full_size_prefix(tvs, ctx):
     ref = solvers.proxskip(solvers.Problem(operators.blur_op(cfg.blur_sigma), b64, cfg.alpha, b64.shape),
                            b64, 1.0, 0.5, cfg.seed, K, cfg.n_inner)
     _check(tr, ref, host(x))
+
+
+def test_pdhgskip_ct_full_size_prefix(tvs, ctx):
+    """The CT workload at its full size -- 512^2 image, 720 angles x 725 bins,
+    alpha 0.5, sigma = tau/4 with sigma tau ||A||^2 = 0.98 -- in the configuration
+    the benchmark times: PDHGSkip-2 (p = 0.2, a seed whose first iterations evaluate
+    the prox), 2 outer iterations of 10 inner iterations, every iterate compared
+    whole with the oracle (its projector pair takes most of a minute here)."""
+    from oracle import coin
+    cfg = configs.CTConfig()
+    N = cfg.N
+    geom = operators.ParallelBeam.unit_square(N, cfg.n_angles, cfg.n_det)
+    truth = cfg.phantom()
+    clean = operators.joseph_forward(truth, geom)
+    counts = cfg.counts(clean)
+    b32, b64 = f32(-np.log(np.maximum(counts, 1.0) / cfg.photons))
+    st = 0.99 / math.sqrt(1.3578)            # ||A||^2 of this geometry by the power method
+    sg, ta = 0.5 * st, 2.0 * st
+    p, K, NI = 0.2, 2, 10
+    seed = next(s for s in range(100) if coin.schedule(s, p, K) == [1, 1])
+    prob = tvs.Problem(ctx, cuda(b32), cfg.alpha, op="ct", shape=(N, N), n_angles=cfg.n_angles, n_det=cfg.n_det,
+                       pixel_size=1.0 / N, det_spacing=1.0 / N)
+    x0 = np.zeros((N, N), dtype=np.float32)
+    y0 = np.zeros((cfg.n_angles, cfg.n_det), dtype=np.float32)
+    x, y, tr = tvs.pdhgskip_solve(prob, cuda(x0), cuda(y0), sg, ta, p, seed, K, NI)
+    oprob = solvers.Problem(operators.ct_op(geom), b64, cfg.alpha, (N, N))
+    ref = solvers.pdhgskip2(oprob, x0.astype(np.float64), y0.astype(np.float64), sg, ta, p, seed, K, NI,
+                            record=False)
+    assert list(tr.coins) == [1, 1] and tr.prox_calls == 2
+    assert_close(host(x), ref["x"], TOL_X_F32)
+    assert_close(host(y), ref["y"], TOL_X_F32)
+    prob.close()
+
+
+def test_proxskip_3d_prefix_256(tvs, ctx):
+    """3D denoising at 256^3 (60 ellipsoids on the volume's grid, noise 0.05, alpha
+    0.05, p 0.1, 30 inner iterations as the 512^3 workload): 3 outer iterations with
+    a seed whose coins evaluate the prox, compared whole with the oracle's C
+    transcription (the numpy oracle would take minutes at this size)."""
+    from oracle import c as oc
+    from oracle import coin
+    N, alpha, p, K, NI = 256, 0.05, 0.1, 3, 30
+    vol = phantoms.ellipsoids_phantom_3d(N, 60, 4000) + phantoms.gaussian_noise((N,) * 3, 0.05, 4001,
+                                                                                 dtype=np.float32)
+    b32 = np.ascontiguousarray(vol.astype(np.float32))
+    seed = next(s for s in range(1000) if coin.schedule(s, p, K) == [1, 0, 1])
+    prob = tvs.Problem(ctx, cuda(b32), alpha)
+    x, tr = tvs.proxskip_solve(prob, cuda(b32), 1.0, p, seed, K, NI)
+    ref = oc.fb_solve("proxskip", b32.astype(np.float64), alpha, 1.0, K, NI, p=p, coins=coin.schedule(seed, p, K))
+    assert list(tr.coins) == [1, 0, 1]
+    assert_close(host(x), ref["x"], TOL_X_F32)
+    obj = np.asarray(ref["objective"])
+    assert (np.abs(tr.objective - obj) / np.abs(obj)).max() <= TOL_OBJ
+    prob.close()
 
 
 def test_denoise_full_size(tvs, ctx):

@@ -14,7 +14,7 @@ last so that a run stopping at its first failure has run every other test.
 import numpy as np
 import pytest
 
-from tests._util import TOL_X_F32, rel_l2
+from tests._util import TOL_X_F32, assert_close
 
 pytestmark = pytest.mark.gpu
 
@@ -51,7 +51,7 @@ def test_noalloc_matches_tv_prox_on_consecutive_calls(tvs):
             u = torch.full_like(z, float("nan"))
             assert tvs.tv_prox_noalloc(z, u, lam, n_iter) == 0
             torch.cuda.synchronize()
-            assert rel_l2(u.cpu().numpy(), ref.cpu().numpy()) <= TOL_X_F32, (shape, lam, n_iter)
+            assert_close(u.cpu().numpy(), ref.cpu().numpy(), TOL_X_F32, (shape, lam, n_iter))
     finally:
         ctx.close()
 
@@ -70,8 +70,8 @@ def test_noalloc_warm_start_two_calls(tvs):
             u = torch.empty_like(z)
             assert tvs.tv_prox_noalloc(z, u, 0.2, 13 + call, dual_state=s_new) == 0
             torch.cuda.synchronize()
-            assert rel_l2(u.cpu().numpy(), ref.cpu().numpy()) <= TOL_X_F32
-            assert rel_l2(s_new.cpu().numpy(), s_ref.cpu().numpy()) <= TOL_X_F32
+            assert_close(u.cpu().numpy(), ref.cpu().numpy(), TOL_X_F32)
+            assert_close(s_new.cpu().numpy(), s_ref.cpu().numpy(), TOL_X_F32)
     finally:
         ctx.close()
 
