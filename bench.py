@@ -441,8 +441,10 @@ def run_gpu(args):
         f_star, f_from = float(golden["f_star"]), "FP64 oracle (tests/golden/fstar_deblur2d_1024.json)"
     else:
         f_star, f_from = f_gpu, "GPU FISTA, 3000 iterations, 100 inner (no oracle value committed)"
+    # the FP32 iterates floor the GPU's objective about 1.5e-6 above the FP64
+    # optimum (rounding spreads values of flat regions, which TV then counts)
     f_check = {"f_star": f_star, "from": f_from, "gpu_fista_min": f_gpu,
-               "rel_diff": abs(f_gpu - f_star) / f_star}
+               "rel_diff": abs(f_gpu - f_star) / f_star, "agree_to_1e-5": abs(f_gpu - f_star) <= 1e-5 * f_star}
 
     def solve(kind, x, p=P_SKIP):
         if kind == "proxskip":

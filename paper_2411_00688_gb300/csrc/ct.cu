@@ -120,19 +120,23 @@ joseph_fwd_kernel(GeomConsts g, const float4* __restrict__ angles, const float* 
 
 // g = A^T y; epilogue out = x - sigma g + ch h (when x given).
 //
-// One thread per 2 x 2 pixel block (rows i0, i0+1, columns j0, j0+1).  For each
-// angle the block's pixels sit on two lines l (rows for row walks, columns
-// otherwise) at two indices k0, k0+1 along them; ray b gives pixel k the
+// Four threads per 2 x 2 pixel block (rows i0, i0+1, columns j0, j0+1), each
+// summing a quarter of the angles (enough threads to keep the SMs' warp slots
+// busy); the four partial sums are added in a fixed order, so the result is
+// deterministic.  For each angle the block's pixels sit on two lines l (rows for
+// row walks, columns otherwise) at two indices k0, k0+1 along them; ray b gives pixel k the
 // projector's weight 1 - f when floor(fr(b, l)) = k and f when floor(fr(b, l)) =
 // k - 1 (f = fr - floor(fr)).  fr is affine in b with slope d * inv, so the bins
 // that reach either index lie in an interval of length 3 / |slope| around the b
 // where fr = k0 + 1/2: the ncand integers from ceil(bc - 1.5/|slope| - margin)
 // cover it (4 when bins have the pixel width).  Each candidate is decided with the
 // projector's own fr and serves both pixels of the line, and candidates that reach
-// a pixel with weight 0 add exactly nothing, so every pixel receives the same
-// terms in the same order (increasing angle, then increasing bin) as a gather
-// over its own bins: the weights are bit-identical to the projector's.
-constexpr int CT_BWD_NT = 128;
+// a pixel with weight 0 add exactly nothing, so within each quarter of the angles
+// every pixel receives the same terms in the same order (increasing angle, then
+// increasing bin) as a gather over its own bins: the weights are bit-identical to
+// the projector's.
+constexpr int CT_BWD_NT = 128;  // 32 pixel blocks x 4 angle groups
+constexpr int CT_BWD_AG = 4;
 
 __global__ void __launch_bounds__(CT_BWD_NT)
 joseph_bwd_kernel(GeomConsts g, const float4* __restrict__ angles, const float4* __restrict__ angles2,
@@ -140,9 +144,13 @@ joseph_bwd_kernel(GeomConsts g, const float4* __restrict__ angles, const float4*
                   const float* __restrict__ x, const float* __restrict__ h, float* __restrict__ out,
                   float sigma, float ch, Partial* __restrict__ part_tv) {
   pdl_enter();
+  __shared__ float s_part[CT_BWD_AG][CT_BWD_NT / CT_BWD_AG][4];
   const int N = g.N;
   const int NB = (N + 1) / 2;  // blocks per row
-  const int blk = blockIdx.x * CT_BWD_NT + threadIdx.x;
+  constexpr int PB = CT_BWD_NT / CT_BWD_AG;  // pixel blocks per CTA
+  const int grp = threadIdx.x / PB, slot = threadIdx.x - grp * PB;
+  const int blk = blockIdx.x * PB + slot;
+  const int a_lo = (g.n_angles * grp) / CT_BWD_AG, a_hi = (g.n_angles * (grp + 1)) / CT_BWD_AG;
   FAcc acc_tv;
   if (blk < NB * NB) {
     const int i0 = 2 * (blk / NB), j0 = 2 * (blk - (blk / NB) * NB);
@@ -150,7 +158,7 @@ joseph_bwd_kernel(GeomConsts g, const float4* __restrict__ angles, const float4*
     const float cr0 = __fmaf_rn((float)i0, g.s, g.c0), cr1 = __fmaf_rn((float)(i0 + 1), g.s, g.c0);
     const float cc0 = __fmaf_rn((float)j0, g.s, g.c0), cc1 = __fmaf_rn((float)(j0 + 1), g.s, g.c0);
     float t00 = 0.f, t01 = 0.f, t10 = 0.f, t11 = 0.f;  // totals of (i0 + a, j0 + b)
-    for (int a = 0; a < g.n_angles; ++a) {
+    for (int a = a_lo; a < a_hi; ++a) {
       const float4 ang = __ldg(angles + a);
       const float4 a2 = __ldg(angles2 + a);  // (1 / slope, 1.5 / |slope| + margin, ncand, -)
       const bool rowwalk = ang.w != 0.f;
@@ -191,7 +199,23 @@ joseph_bwd_kernel(GeomConsts g, const float4* __restrict__ angles, const float4*
       t10 = fmaf(ang.z, a10, t10);
       t11 = fmaf(ang.z, a11, t11);
     }
-    const float tot[2][2] = {{t00, t01}, {t10, t11}};
+    s_part[grp][slot][0] = t00;
+    s_part[grp][slot][1] = t01;
+    s_part[grp][slot][2] = t10;
+    s_part[grp][slot][3] = t11;
+  }
+  __syncthreads();
+  // group 0 adds the four quarters in angle order and writes the block
+  if (grp == 0 && blk < NB * NB) {
+    const int i0 = 2 * (blk / NB), j0 = 2 * (blk - (blk / NB) * NB);
+    float tot[2][2];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float v = s_part[0][slot][e];
+#pragma unroll
+      for (int q = 1; q < CT_BWD_AG; ++q) v += s_part[q][slot][e];
+      tot[e >> 1][e & 1] = v;
+    }
 #pragma unroll
     for (int di = 0; di < 2; ++di)
 #pragma unroll
@@ -265,8 +289,8 @@ cudaError_t ct_build_angle_table(const CTGeom& g, float4* dev_table, cudaStream_
 
 int ct_fwd_blocks(const CTGeom& g) { return (g.n_angles * g.n_det + CT_NT - 1) / CT_NT; }
 int ct_bwd_blocks(const CTGeom& g) {
-  const int nb = (g.N + 1) / 2;
-  return (nb * nb + CT_BWD_NT - 1) / CT_BWD_NT;
+  const int nb = (g.N + 1) / 2, per = CT_BWD_NT / CT_BWD_AG;
+  return (nb * nb + per - 1) / per;
 }
 
 cudaError_t launch_ct_forward(const CTGeom& g, const float* x, float* sino, float* y,

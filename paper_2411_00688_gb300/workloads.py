@@ -140,6 +140,52 @@ def ct2d_512():
     return out
 
 
+def ct2d_512_sweep():
+    """PDHG against PDHGSkip-2 and PDHGSkip-1 (p = 0.2, 0.05) on the CT workload over
+    the step split sigma = tau * ratio (sigma tau ||A||^2 = 0.98) and the inner
+    iteration count: time to the 1e-4 gap (F* from a long PDHG run), iterations and
+    prox calls; the projector pair's time beside it."""
+    import torch
+    from synth.configs import CTConfig
+    tvs, ctx = _ctx()
+    cfg = CTConfig()
+    N = cfg.N
+    truth = torch.from_numpy(cfg.phantom().astype(np.float32)).cuda()
+    mk = dict(op="ct", shape=(N, N), n_angles=cfg.n_angles, n_det=cfg.n_det, pixel_size=1.0 / N,
+              det_spacing=1.0 / N)
+    zeros_sino = torch.zeros((cfg.n_angles, cfg.n_det), device="cuda")
+    op = tvs.Problem(ctx, zeros_sino, cfg.alpha, **mk)
+    clean = torch.empty_like(zeros_sino)
+    tvs.tvs_op_apply(op, truth, clean)
+    counts = cfg.counts(clean.cpu().numpy().astype(np.float64))
+    b = torch.from_numpy((-np.log(np.maximum(counts, 1.0) / cfg.photons)).astype(np.float32)).cuda()
+    prob = tvs.Problem(ctx, b, cfg.alpha, **mk)
+    L = _power_norm_sq(tvs, prob, (N, N), (cfg.n_angles, cfg.n_det))
+    st = 0.99 / math.sqrt(L)
+    x0 = torch.zeros((N, N), device="cuda")
+    _, _, ref = tvs.pdhg_solve(prob, x0.clone(), zeros_sino.clone(), st, st, 6000, 100)
+    f_star = float(np.nanmin(ref.objective))
+    out = []
+    for ratio in (1.0, 0.25, 0.0625):
+        sg, ta = st * math.sqrt(ratio), st / math.sqrt(ratio)
+        for n_inner in (50, 200, 500):
+            runs = [("pdhg", lambda: tvs.pdhg_solve(prob, x0.clone(), zeros_sino.clone(), sg, ta, cfg.max_iter,
+                                                    n_inner, f_star=f_star, target=TARGET))]
+            for p in cfg.ps:
+                runs.append((f"pdhgskip2_p{p}", lambda p=p: tvs.pdhgskip_solve(
+                    prob, x0.clone(), zeros_sino.clone(), sg, ta, p, cfg.seed, cfg.max_iter, n_inner,
+                    f_star=f_star, target=TARGET)))
+                runs.append((f"pdhgskip1_p{p}", lambda p=p: tvs.pdhgskip1_solve(
+                    prob, x0.clone(), zeros_sino.clone(), sg, ta, p, cfg.seed, cfg.max_iter, n_inner,
+                    f_star=f_star, target=TARGET)))
+            for name, fn in runs:
+                fn()
+                (_, _, tr), wall = _timed(fn)
+                out.append(_solve_record(name, tr, wall, f_star, workload="ct2d_512", ratio=ratio,
+                                         n_inner=n_inner))
+    return out
+
+
 def _explicit(tvs, prob, x0, y0, f_star, name, K=20000):
     def run():
         return tvs.pdhg_explicit_solve(prob, x0.clone(), y0.clone(), None, K, f_star=f_star, target=TARGET)
@@ -343,7 +389,8 @@ def _batch(n_problems=None, K=None, batch_only=False, dual="f32"):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("workload", choices=["denoise2d_256", "ct2d_512", "denoise3d_512", "batch2d_256",
-                                         "deblur2d_1024", "table1_deblur2d_1024", "dual_huber_200x300"])
+                                         "deblur2d_1024", "table1_deblur2d_1024", "dual_huber_200x300",
+                                         "ct2d_512_sweep"])
     ap.add_argument("--problems", type=int, default=None)
     ap.add_argument("--iters", type=int, default=None)
     ap.add_argument("--batch-only", action="store_true", help="batch2d_256: time the batched solve only")
@@ -354,7 +401,7 @@ def main(argv=None):
     else:
         recs = {"denoise2d_256": denoise2d_256, "ct2d_512": ct2d_512, "denoise3d_512": denoise3d_512,
                 "deblur2d_1024": deblur2d_1024, "table1_deblur2d_1024": table1_deblur2d_1024,
-                "dual_huber_200x300": dual_huber_200x300}[args.workload]()
+                "dual_huber_200x300": dual_huber_200x300, "ct2d_512_sweep": ct2d_512_sweep}[args.workload]()
     for r in recs:
         print(json.dumps(r), flush=True)
 
