@@ -43,8 +43,8 @@ TARGET = 1e-4
 P_SKIP = 0.5
 P_OTHERS = (0.1, 0.05)
 F_STAR_ITERS, F_STAR_INNER = 3000, 100
-FGP_BYTES_PER_PX = 28        # read z (4) + p_k (8) + p_{k-1} (8), write p_{k+1} (8), FP32 dual, 2D
-FGP3_BYTES = {"f32": 40, "bf16": 22, "f16": 22, "q15": 22}   # per voxel and inner iteration, 3D
+# Bytes of one dual component per pixel for each dual storage type.
+DUAL_BYTES = {"f32": 4, "bf16": 2, "f16": 2, "q15": 2}
 WORKLOAD = ("deblur2d_1024: 1024x1024, 40 ellipses, 9x9 Gaussian sigma 2, noise 0.01, alpha 0.02, gamma 1, "
             "ProxSkip p 0.5 seed 0, 50 FGP iterations per prox, stop at relative objective gap 1e-4 "
             "(max 1000 iterations)")
@@ -52,9 +52,9 @@ WORKLOAD = ("deblur2d_1024: 1024x1024, 40 ellipses, 9x9 Gaussian sigma 2, noise 
 # capture of `dram__bytes_read.sum + dram__bytes_write.sum`.  Each record describes
 # only the kernel sources and launch configuration it was taken on: the bench line
 # carries it only while the hash of those sources (and the configuration) match.
-FGP_TRAFFIC = {"config": [4, 2, 104], "bytes": 20388923,
+FGP_TRAFFIC = {"config": [4, 2, 104], "bytes": 20390558,
                "sources": ["common.cuh", "fgp_rb.cuh", "fgp.cu"],
-               "sha256": "9400c3397cae3c57988378ed31992c99ddbed0ba82af16c2e3bad042fc8cb953"}
+               "sha256": "cec4d58a47436f50a6bb7c3c1f99a6e37b18bdfd7ffdac64826c06ccd55debcc"}
 FGP3_TRAFFIC = {}   # dual -> {"bytes": per launch at 512^3, "sources": [...], "sha256": ...}
 # Iterations this workload's ProxSkip solve needs to reach the target on the GPU
 # (its trace: 261 iterations); the reference arm extrapolates the oracle to them,
@@ -110,6 +110,17 @@ def _fgp3_traffic(dual):
     if not rec or _sources_hash(rec["sources"]) != rec["sha256"]:
         return None
     return rec["bytes"]
+
+
+def fgp_algo_bytes(n_iter, units, ndim, dual="f32"):
+    """Algorithmic HBM bytes of n_iter FGP iterations over `units` pixels or voxels
+    (nothing cached between iterations): each reads z (FP32) and p_k and writes
+    p_{k+1} (ndim components each); from the third on it also reads p_{k-1} for
+    the momentum term, whose weight is zero in the first two because t restarts
+    at 1 with every prox call.  2D FP32: 20 and 28 B per pixel; 3D FP32: 28 and
+    40 B per voxel; 3D 16-bit: 16 and 22 B per voxel."""
+    p = ndim * DUAL_BYTES[dual]
+    return units * (n_iter * (4 + 2 * p) + max(n_iter - 2, 0) * p)
 
 
 def _golden_f_star():
@@ -232,7 +243,8 @@ def extra_denoise3d(tvs, ctx, stream, hbm_peak, peak_kind):
     """512^3 TV denoising (alpha 0.05): FGP time per inner iteration and its
     bandwidth against the HBM peak for each dual storage (the volume and its duals,
     3.5-9.7 GB, are far larger than L2), from tv_prox on the benchmark's stream with
-    n inner iterations minus none."""
+    n + 2 inner iterations minus 2, so that every timed iteration carries the
+    momentum read."""
     import torch
     from synth.configs import Denoise3DConfig
     cfg = Denoise3DConfig()
@@ -266,10 +278,12 @@ def extra_denoise3d(tvs, ctx, stream, hbm_peak, peak_kind):
                 torch.cuda.synchronize()
                 ts.append(e0.elapsed_time(e1) * 1e-3)
             return statistics.median(ts)
-        per_it = (med(n_it) - med(0)) / n_it
-        achieved = FGP3_BYTES[dual] * N ** 3 / per_it / 1e9
+        # iterations 3 .. n_it + 2, all with momentum: prox(n_it + 2) minus prox(2)
+        per_it = (med(n_it + 2) - med(2)) / n_it
+        per_launch = (fgp_algo_bytes(n_it + 2, N ** 3, 3, dual) - fgp_algo_bytes(2, N ** 3, 3, dual)) / n_it
+        achieved = per_launch / per_it / 1e9
         out[dual] = {"kernel": "fgp3d_zm_kernel", "us_per_inner_iteration": per_it * 1e6,
-                     "bytes_per_launch": FGP3_BYTES[dual] * N ** 3, "achieved_gbs": achieved,
+                     "bytes_per_launch": per_launch, "achieved_gbs": achieved,
                      "frac": achieved / hbm_peak, "traffic": _fgp3_traffic(dual)}
         del state
         torch.cuda.empty_cache()
@@ -537,7 +551,7 @@ def run_gpu(args):
     in_solve = [t.fgp_ms / t.fgp_launches for t in ps_tr if t.fgp_launches > 0]
     fgp_in_solve_s = statistics.median(in_solve) * 1e-3 if in_solve else None
     hbm_peak, peak_kind = _peaks()
-    bytes_per_launch = FGP_BYTES_PER_PX * H * W * n_fgp / launches_per_prox
+    bytes_per_launch = fgp_algo_bytes(n_fgp, H * W, 2) / launches_per_prox
     achieved = bytes_per_launch / fgp_launch_s / 1e9
 
     # end to end through the C ABI with pinned host buffers: H2D of b and x_0,
