@@ -53,7 +53,7 @@ WORKLOAD = ("deblur2d_1024: 1024x1024, 40 ellipses, 9x9 Gaussian sigma 2, noise 
 # only the kernel sources and launch configuration it was taken on: the bench line
 # carries it only while the hash of those sources (and the configuration) match.
 FGP_TRAFFIC = {"config": [4, 2, 104], "bytes": 20390558,
-               "sources": ["common.cuh", "fgp_rb.cuh", "fgp.cu"],
+               "sources": ["common.cuh", "fgp_rb.cuh", "fgp_tb.cu"],
                "sha256": "cec4d58a47436f50a6bb7c3c1f99a6e37b18bdfd7ffdac64826c06ccd55debcc"}
 FGP3_TRAFFIC = {}   # dual -> {"bytes": per launch at 512^3, "sources": [...], "sha256": ...}
 # Iterations this workload's ProxSkip solve needs to reach the target on the GPU

@@ -45,7 +45,9 @@ typedef enum {
   TVS_ETIMEDOUT = 5,     /* a solve passed its wall-clock limit (the
                             TVS_SOLVE_TIMEOUT_MS environment variable, in ms;
                             PGD, FISTA, ProxSkip, PDHG, PDHGSkip-2): it stopped
-                            launching iterations and cleaned up                */
+                            launching iterations and cleaned up; or a 3D inner
+                            kernel gave up (after 2 s) waiting for a tile load
+                            and left part of its output unwritten              */
   TVS_EUNSUPPORTED = 6   /* valid request this build does not implement       */
 } tvs_status;
 
@@ -210,8 +212,16 @@ tvs_status tv_prox(tvs_ctx* ctx, int ndim, const int dims[3], const float* z, fl
  * iteration per launch (3D).  The first query (or the first prox / solve) of a
  * 2D shape times the candidates on the device and caches the fastest;
  * TVS_FGP_CONFIG="tb,cpl,rpw" in the environment forces one, and
- * TVS_TUNE_CACHE=path keeps the choices in a text file across processes.  Not in the paper:
- * a performance knob only (every configuration computes identical iterates). */
+ * TVS_TUNE_CACHE=path keeps the choices in a text file across processes.  3D volumes
+ * large enough to fill the GPU with (x-y tile, z chunk) pairs take a z-marching
+ * kernel (with a 16-bit dual the one whose planes arrive by TMA tile loads, with
+ * an FP32 dual the one with register loads), smaller ones the tiled kernel;
+ * TVS_FGP3D=tma, zm or tile forces one (tma falls back to zm where the row pitch or
+ * a buffer is not 16-byte aligned), TVS_FGP3D_CFG="cpl,rpw,zc" picks a z-marching
+ * variant and TVS_FGP3D_STAGES=3 a three-stage TMA ring (all read at each launch).
+ * Not in the paper: a performance knob only (with an FP32, BF16 or FP16 dual every
+ * configuration computes identical iterates; with the 16-bit fixed point the
+ * stored codes may differ by a few units, see TVS_DUAL_Q15). */
 tvs_status tvs_fgp_config(tvs_ctx* ctx, int ndim, const int dims[3], tvs_dual_dtype dual, int out[3]);
 
 /* ---- allocation-free TV prox -------------------------------------------------- */

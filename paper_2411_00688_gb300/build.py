@@ -20,7 +20,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build", platform.machine())  # objects per host architecture
 LIB = os.path.join(PKG, "libtvs.so")
-SOURCES = ["api.cu", "fgp.cu", "ops.cu", "ct.cu", "noalloc.cu", "batch.cu", "rof.cu", "pdx.cu", "gap.cu"]
+SOURCES = ["api.cu", "fgp.cu", "fgp_tb.cu", "fgp3d.cu", "ops.cu", "ct.cu", "noalloc.cu", "batch.cu", "rof.cu", "pdx.cu", "gap.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -706,6 +706,8 @@ tvs_status finish_solve(tvs_problem* P, int K, const LoopState& ls,
   }
   if (bad) return fail(TVS_ENUMERIC, "non-finite objective during the solve");
   if (ls.timed_out) return fail(TVS_ETIMEDOUT, "solve stopped at its time limit after %d iterations", iters);
+  if (P->dims.ndim == 3 && fgp3d_take_wait_timeouts())
+    return fail(TVS_ETIMEDOUT, "a 3D inner kernel gave up waiting for a TMA tile load; the result is incomplete");
   return TVS_OK;
 }
 
@@ -1984,6 +1986,8 @@ tvs_status tv_prox(tvs_ctx* C, int ndim, const int dims[3], const float* z, floa
                                nullptr, 0.f, (fin != 0 && dual_state) ? dual_state : nullptr,
                                nullptr, nullptr, nullptr, nullptr, s));
   CUDA_TRY(cudaStreamSynchronize(s));
+  if (ndim == 3 && use && n_iter > 0 && fgp3d_take_wait_timeouts())
+    return fail(TVS_ETIMEDOUT, "a 3D inner kernel gave up waiting for a TMA tile load; the result is incomplete");
   return TVS_OK;
 }
 

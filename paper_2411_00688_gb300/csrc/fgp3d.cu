@@ -1,0 +1,788 @@
+// 3D TV-prox kernels: one accelerated dual projected-gradient (FGP) iteration
+// per launch (the iteration of fgp.cu with the three-component dual and
+// step 1/(12 lam)), either over (x, y, z) tiles staged in shared memory
+// (fgp3d_kernel) or marching through z (fgp3d_zm_kernel with register loads,
+// fgp3d_tma_kernel with TMA tile loads; the default for volumes large enough
+// to fill the GPU).
+#include <cudaTypedefs.h>
+
+#include <atomic>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "common.cuh"
+#include "kernels.hpp"
+#include "tma.cuh"
+
+namespace tvs {
+
+namespace {
+
+constexpr int TX3 = 32, TY3 = 8, TZ3 = 4, NT3 = 256;
+
+template <typename T, bool NONNEG>
+__global__ void __launch_bounds__(NT3)
+fgp3d_kernel(const float* __restrict__ z, const T* __restrict__ pc, const T* __restrict__ pp,
+             T* __restrict__ pn, int D, int H, int W, float lam, float inv_step, float beta) {
+  pdl_enter();
+  __shared__ float sr[3][TZ3 + 2][TY3 + 2][TX3 + 2];
+  __shared__ float su[TZ3 + 1][TY3 + 1][TX3 + 1];
+  const int j0 = blockIdx.x * TX3, i0 = blockIdx.y * TY3, k0 = blockIdx.z * TZ3;
+  const size_t n = (size_t)D * H * W;
+  constexpr int RX = TX3 + 2, RY = TY3 + 2, RZ = TZ3 + 2;
+  for (int e = threadIdx.x; e < RZ * RY * RX; e += NT3) {
+    const int c = e / (RY * RX), rem = e - c * (RY * RX);
+    const int a = rem / RX, b = rem - a * RX;
+    const int gk = k0 - 1 + c, gi = i0 - 1 + a, gj = j0 - 1 + b;
+    float r0 = 0.f, r1 = 0.f, r2 = 0.f;
+    if (gk >= 0 && gk < D && gi >= 0 && gi < H && gj >= 0 && gj < W) {
+      const size_t o = ((size_t)gk * H + gi) * W + gj;
+      const float c0 = Elem<T>::ld(pc + o), c1 = Elem<T>::ld(pc + n + o), c2 = Elem<T>::ld(pc + 2 * n + o);
+      if (beta != 0.f) {
+        r0 = c0 + beta * (c0 - Elem<T>::ld(pp + o));
+        r1 = c1 + beta * (c1 - Elem<T>::ld(pp + n + o));
+        r2 = c2 + beta * (c2 - Elem<T>::ld(pp + 2 * n + o));
+      } else {
+        r0 = c0; r1 = c1; r2 = c2;
+      }
+    }
+    sr[0][c][a][b] = r0;
+    sr[1][c][a][b] = r1;
+    sr[2][c][a][b] = r2;
+  }
+  __syncthreads();
+  constexpr int UX = TX3 + 1, UY = TY3 + 1, UZ = TZ3 + 1;
+  for (int e = threadIdx.x; e < UZ * UY * UX; e += NT3) {
+    const int c = e / (UY * UX), rem = e - c * (UY * UX);
+    const int a = rem / UX, b = rem - a * UX;
+    const int gk = k0 + c, gi = i0 + a, gj = j0 + b;
+    float u = 0.f;
+    if (gk < D && gi < H && gj < W) {
+      float dv = 0.f;
+      if (gk < D - 1) dv += sr[0][c + 1][a + 1][b + 1];
+      if (gk > 0) dv -= sr[0][c][a + 1][b + 1];
+      if (gi < H - 1) dv += sr[1][c + 1][a + 1][b + 1];
+      if (gi > 0) dv -= sr[1][c + 1][a][b + 1];
+      if (gj < W - 1) dv += sr[2][c + 1][a + 1][b + 1];
+      if (gj > 0) dv -= sr[2][c + 1][a + 1][b];
+      u = __ldg(z + ((size_t)gk * H + gi) * W + gj) + lam * dv;
+      if (NONNEG) u = fmaxf(u, 0.f);
+    }
+    su[c][a][b] = u;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < TZ3 * TY3 * TX3; e += NT3) {
+    const int c = e / (TY3 * TX3), rem = e - c * (TY3 * TX3);
+    const int a = rem / TX3, b = rem - a * TX3;
+    const int gk = k0 + c, gi = i0 + a, gj = j0 + b;
+    if (gk < D && gi < H && gj < W) {
+      const float uc = su[c][a][b];
+      const float g0 = gk < D - 1 ? su[c + 1][a][b] - uc : 0.f;
+      const float g1 = gi < H - 1 ? su[c][a + 1][b] - uc : 0.f;
+      const float g2 = gj < W - 1 ? su[c][a][b + 1] - uc : 0.f;
+      const float q0 = sr[0][c + 1][a + 1][b + 1] + inv_step * g0;
+      const float q1 = sr[1][c + 1][a + 1][b + 1] + inv_step * g1;
+      const float q2 = sr[2][c + 1][a + 1][b + 1] + inv_step * g2;
+      const float nrm2 = q0 * q0 + q1 * q1 + q2 * q2;
+      const float sc = nrm2 > 1.f ? rsqrtf(nrm2) : 1.f;
+      const size_t o = ((size_t)gk * H + gi) * W + gj;
+      Elem<T>::st(pn + o, q0 * sc);
+      Elem<T>::st(pn + n + o, q1 * sc);
+      Elem<T>::st(pn + 2 * n + o, q2 * sc);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 3D, one inner iteration per launch, marching through z ("2.5D").  A CTA owns an
+// x-y region of 32*CPL x 8*RPW cells (warp w: RPW consecutive rows, lane: CPL
+// adjacent columns) and a chunk of ZC planes.  Per plane k it loads r(k+1)
+// (from z, p_k, p_{k-1}), forms u(k+1), then writes p_{k+1} at plane k from
+// r(k), u(k), u(k+1): each voxel is read once (z, p_k, p_{k-1}) and written once,
+// plus one warm-up plane per chunk and a one-cell x-y halo.  x neighbours come
+// from warp shuffles, y neighbours from registers or, across warps, from a
+// double-buffered shared row (one barrier per plane).
+//
+// (A variant that compiled a second, mask-free body for CTAs whose region lies
+// inside the volume measured no faster with an FP32 dual and 1.5x slower with
+// BF16 at 512^3, so every CTA runs this one body.)
+template <typename T, bool NONNEG, int CPL, int RPW, int ZC>
+__global__ void __launch_bounds__(256)
+fgp3d_zm_kernel(const float* __restrict__ z, const T* __restrict__ pc, const T* __restrict__ pp,
+                T* __restrict__ pn, int D, int H, int W, float lam, float inv_step, float beta) {
+  pdl_enter();
+  constexpr int NW = 8;
+  constexpr int RW = 32 * CPL, RH = NW * RPW;
+  constexpr int TW = RW - 2, TH = RH - 2;
+  __shared__ float sh_ry[2][NW][RW];   // bottom row of r_y(k+1) of each warp block
+  __shared__ float sh_u[2][NW][RW];    // top row of u(k+1) of each warp block
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gi0 = blockIdx.y * TH - 1 + warp * RPW;
+  const int gj0 = blockIdx.x * TW - 1 + lane * CPL;
+  const int k0 = blockIdx.z * ZC;
+  const int k1 = min(k0 + ZC, D);
+  const size_t HW = (size_t)H * W, n = (size_t)D * HW;
+  bool row_in[RPW], row_dn[RPW], row_up[RPW], col_in[CPL], col_rt[CPL], col_lf[CPL];
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) {
+    const int gi = gi0 + r;
+    row_in[r] = gi >= 0 && gi < H;
+    row_dn[r] = gi < H - 1;
+    row_up[r] = gi > 0;
+  }
+#pragma unroll
+  for (int q = 0; q < CPL; ++q) {
+    const int gj = gj0 + q;
+    col_in[q] = gj >= 0 && gj < W;
+    col_rt[q] = gj < W - 1;
+    col_lf[q] = gj > 0;
+  }
+  // r(k) (three components), r_z(k-1), u(k) of the thread's cells
+  float Rz[RPW][CPL], Ry[RPW][CPL], Rx[RPW][CPL], Rzm[RPW][CPL], Uk[RPW][CPL];
+
+  auto load_r = [&](int k, float (&rz)[RPW][CPL], float (&ry)[RPW][CPL], float (&rx)[RPW][CPL],
+                    float (&zz)[RPW][CPL], bool need_all) {
+#pragma unroll
+    for (int r = 0; r < RPW; ++r)
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, zv = 0.f;
+        if (k >= 0 && k < D && row_in[r] && col_in[q]) {
+          const size_t o = (size_t)k * HW + (size_t)(gi0 + r) * W + (gj0 + q);
+          const float c0 = Elem<T>::ld(pc + o);
+          a0 = beta != 0.f ? c0 + beta * (c0 - Elem<T>::ld(pp + o)) : c0;
+          if (need_all) {
+            const float c1 = Elem<T>::ld(pc + n + o), c2 = Elem<T>::ld(pc + 2 * n + o);
+            if (beta != 0.f) {
+              a1 = c1 + beta * (c1 - Elem<T>::ld(pp + n + o));
+              a2 = c2 + beta * (c2 - Elem<T>::ld(pp + 2 * n + o));
+            } else {
+              a1 = c1;
+              a2 = c2;
+            }
+            zv = __ldg(z + o);
+          }
+        }
+        rz[r][q] = a0;
+        ry[r][q] = a1;
+        rx[r][q] = a2;
+        zz[r][q] = zv;
+      }
+  };
+  // u at plane k from r(k) (Rz/Ry/Rx), r_z(k-1) and the staged r_y row above.
+  auto form_u = [&](int k, const float (&rz)[RPW][CPL], const float (&ry)[RPW][CPL],
+                    const float (&rx)[RPW][CPL], const float (&rzm)[RPW][CPL],
+                    const float (&zz)[RPW][CPL], const float* ry_above, float (&u)[RPW][CPL]) {
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+      const float rx_left = __shfl_up_sync(0xffffffffu, rx[r][CPL - 1], 1);
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) {
+        const float up = r > 0 ? ry[r - 1][q] : ry_above[q];
+        const float lf = q > 0 ? rx[r][q - 1] : rx_left;
+        float dv = 0.f;
+        if (k < D - 1) dv += rz[r][q];
+        if (k > 0) dv -= rzm[r][q];
+        if (row_dn[r]) dv += ry[r][q];
+        if (row_up[r]) dv -= up;
+        if (col_rt[q]) dv += rx[r][q];
+        if (col_lf[q]) dv -= lf;
+        float v = zz[r][q] + lam * dv;
+        if (NONNEG) v = fmaxf(v, 0.f);
+        u[r][q] = (k < D && row_in[r] && col_in[q]) ? v : 0.f;
+      }
+    }
+  };
+
+  // FP32 duals: plane k+2's stored values are fetched into registers while plane
+  // k is computed, so their loads are in flight for a whole plane before make_r
+  // forms r(k+2) from them (measured at 512^3: 1.08 -> 0.98 ms per iteration).
+  // With 16-bit duals the extra registers cost more occupancy than the overlap
+  // gains, so those load each plane when they need it.
+  constexpr bool kPrefetch = sizeof(T) == 4;
+  T Pc[RPW][CPL][3], Pp[RPW][CPL][3];
+  float Zr[RPW][CPL];
+  auto fetch = [&](int k) {
+#pragma unroll
+    for (int r = 0; r < RPW; ++r)
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) {
+        const bool in = k >= 0 && k < D && row_in[r] && col_in[q];
+        const size_t o = in ? (size_t)k * HW + (size_t)(gi0 + r) * W + (gj0 + q) : 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          Pc[r][q][c] = in ? Elem<T>::raw(pc + (size_t)c * n + o) : T();
+          Pp[r][q][c] = (in && beta != 0.f) ? Elem<T>::raw(pp + (size_t)c * n + o) : T();
+        }
+        Zr[r][q] = in ? __ldg(z + o) : 0.f;
+      }
+  };
+  // r = p_k + beta (p_k - p_{k-1}) and z from the fetched values (cells outside
+  // the volume were fetched as zero, which decodes to 0)
+  auto make_r = [&](float (&rz)[RPW][CPL], float (&ry)[RPW][CPL], float (&rx)[RPW][CPL],
+                    float (&zz)[RPW][CPL]) {
+#pragma unroll
+    for (int r = 0; r < RPW; ++r)
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) {
+        float a[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float cc = Elem<T>::cvt(Pc[r][q][c]);
+          a[c] = beta != 0.f ? cc + beta * (cc - Elem<T>::cvt(Pp[r][q][c])) : cc;
+        }
+        rz[r][q] = a[0];
+        ry[r][q] = a[1];
+        rx[r][q] = a[2];
+        zz[r][q] = Zr[r][q];
+      }
+  };
+
+  float Zt[RPW][CPL], Dy[RPW][CPL], Dx[RPW][CPL];
+  // warm-up: r_z(k0-1) and r(k0), then u(k0)
+  load_r(k0 - 1, Rzm, Dy, Dx, Zt, false);
+  load_r(k0, Rz, Ry, Rx, Zt, true);
+  if constexpr (kPrefetch) fetch(k0 + 1);
+  int buf = 0;
+#pragma unroll
+  for (int q = 0; q < CPL; ++q) sh_ry[buf][warp][lane * CPL + q] = Ry[RPW - 1][q];
+  __syncthreads();
+  {
+    float above[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) above[q] = warp > 0 ? sh_ry[buf][warp - 1][lane * CPL + q] : 0.f;
+    form_u(k0, Rz, Ry, Rx, Rzm, Zt, above, Uk);
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) sh_u[buf][warp][lane * CPL + q] = Uk[0][q];
+  }
+  for (int k = k0; k < k1; ++k) {
+    // next plane: r(k+1), u(k+1)
+    float Rz1[RPW][CPL], Ry1[RPW][CPL], Rx1[RPW][CPL], U1[RPW][CPL];
+    if constexpr (kPrefetch) {
+      make_r(Rz1, Ry1, Rx1, Zt);
+      fetch(k + 2);
+    } else {
+      load_r(k + 1, Rz1, Ry1, Rx1, Zt, true);
+    }
+    const int nb = buf ^ 1;
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) sh_ry[nb][warp][lane * CPL + q] = Ry1[RPW - 1][q];
+    __syncthreads();
+    float above[CPL], below_u[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+      above[q] = warp > 0 ? sh_ry[nb][warp - 1][lane * CPL + q] : 0.f;
+      below_u[q] = warp < NW - 1 ? sh_u[buf][warp + 1][lane * CPL + q] : 0.f;
+    }
+    form_u(k + 1, Rz1, Ry1, Rx1, Rz, Zt, above, U1);
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) sh_u[nb][warp][lane * CPL + q] = U1[0][q];
+    // p_{k+1} at plane k
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+      const float u_right = __shfl_down_sync(0xffffffffu, Uk[r][0], 1);
+      const int a = warp * RPW + r;
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) {
+        const float uc = Uk[r][q];
+        const float dn = r < RPW - 1 ? Uk[r + 1][q] : below_u[q];
+        const float rt = q < CPL - 1 ? Uk[r][q + 1] : u_right;
+        const float g0 = k < D - 1 ? U1[r][q] - uc : 0.f;
+        const float g1 = row_dn[r] ? dn - uc : 0.f;
+        const float g2 = col_rt[q] ? rt - uc : 0.f;
+        const float q0 = Rz[r][q] + inv_step * g0;
+        const float q1 = Ry[r][q] + inv_step * g1;
+        const float q2 = Rx[r][q] + inv_step * g2;
+        const float nrm2 = q0 * q0 + q1 * q1 + q2 * q2;
+        const float sc = nrm2 > 1.f ? rsqrtf(nrm2) : 1.f;
+        const int c = lane * CPL + q;
+        if (a >= 1 && a <= TH && c >= 1 && c <= TW && row_in[r] && col_in[q]) {
+          const size_t o = (size_t)k * HW + (size_t)(gi0 + r) * W + (gj0 + q);
+          Elem<T>::st(pn + o, q0 * sc);
+          Elem<T>::st(pn + n + o, q1 * sc);
+          Elem<T>::st(pn + 2 * n + o, q2 * sc);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RPW; ++r)
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) {
+        Rzm[r][q] = Rz[r][q];
+        Rz[r][q] = Rz1[r][q];
+        Ry[r][q] = Ry1[r][q];
+        Rx[r][q] = Rx1[r][q];
+        Uk[r][q] = U1[r][q];
+      }
+    buf = nb;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// z-marching with TMA staging: the decomposition, arithmetic and order of
+// fgp3d_zm_kernel, but the planes come from shared memory.  One thread issues
+// tiled TMA loads of whole planes of the CTA's region -- z, the three
+// components of p_k and, when the momentum weight is non-zero, of p_{k-1} --
+// into a ring of NS stages completed on mbarriers, NS planes ahead of the
+// plane being consumed; the other threads neither compute addresses nor hold
+// loads in flight.  A box starts at the region's first column rounded down to
+// the 16-byte boundary TMA requires (x may be -1 .. -8 at the left face, where
+// the box reads zeros, as it does past every face), so each box is 16 bytes
+// wider than the region and the cells are read at that offset.
+template <typename T, int CPL, int RPW, int NS_>
+struct ZmTma {
+  static constexpr int RW = 32 * CPL, RH = 8 * RPW;
+  static constexpr int AP = 16 / (int)sizeof(T), AZ = 4;  // x alignment of p and z boxes (elements)
+  static constexpr int BXP = RW + AP, BXZ = RW + AZ;       // box widths
+  static constexpr uint32_t ZB = RH * BXZ * 4;            // bytes of a z box
+  static constexpr uint32_t PB = 3 * RH * BXP * sizeof(T);  // bytes of a dual box (3 components)
+  static constexpr uint32_t ZB_AL = (ZB + 127) / 128 * 128, PB_AL = (PB + 127) / 128 * 128;
+  static constexpr int NS = NS_;                          // stages
+  static constexpr uint32_t STAGE = ZB_AL + 2 * PB_AL;
+  static constexpr uint32_t SMEM = NS * STAGE + 128;      // dynamic, with room to align to 128 B
+};
+
+__device__ unsigned int g_tma_wait_timeouts = 0;
+std::atomic<bool> g_tma_launched{false};
+
+template <typename T, bool NONNEG, int CPL, int RPW, int ZC, int NS_>
+__global__ void __launch_bounds__(256)
+fgp3d_tma_kernel(const __grid_constant__ CUtensorMap tm_z, const __grid_constant__ CUtensorMap tm_p,
+                 const __grid_constant__ CUtensorMap tm_q, T* __restrict__ pn, int D, int H, int W, float lam,
+                 float inv_step, float beta) {
+  pdl_enter();
+  using L = ZmTma<T, CPL, RPW, NS_>;
+  constexpr int NW = 8, NS = L::NS;
+  constexpr int RW = L::RW, RH = L::RH;
+  constexpr int TW = RW - 2, TH = RH - 2;
+  extern __shared__ unsigned char tma_dyn[];
+  __shared__ float sh_ry[2][NW][RW];   // bottom row of r_y(k+1) of each warp block
+  __shared__ float sh_u[2][NW][RW];    // top row of u(k+1) of each warp block
+  __shared__ __align__(8) uint64_t bar[NS];
+  __shared__ int s_abort;
+  unsigned char* const sbase = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(tma_dyn) + 127) & ~static_cast<uintptr_t>(127));
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int xr = blockIdx.x * TW - 1, yr = blockIdx.y * TH - 1;  // region origin
+  const int xz = xr - ((xr % L::AZ) + L::AZ) % L::AZ;           // box origins (x)
+  const int xp = xr - ((xr % L::AP) + L::AP) % L::AP;
+  const int oz = xr - xz, op = xr - xp;
+  const int gi0 = yr + warp * RPW;
+  const int gj0 = xr + lane * CPL;
+  const int k0 = blockIdx.z * ZC;
+  const int k1 = min(k0 + ZC, D);
+  const int nplanes = k1 - k0 + 2;  // local plane j is k = k0 - 1 + j
+  const size_t HW = (size_t)H * W, n = (size_t)D * HW;
+  const bool mom = beta != 0.f;
+  bool row_in[RPW], row_dn[RPW], row_up[RPW], col_in[CPL], col_rt[CPL], col_lf[CPL];
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) {
+    const int gi = gi0 + r;
+    row_in[r] = gi >= 0 && gi < H;
+    row_dn[r] = gi < H - 1;
+    row_up[r] = gi > 0;
+  }
+#pragma unroll
+  for (int q = 0; q < CPL; ++q) {
+    const int gj = gj0 + q;
+    col_in[q] = gj >= 0 && gj < W;
+    col_rt[q] = gj < W - 1;
+    col_lf[q] = gj > 0;
+  }
+  auto zs = [&](int st) { return reinterpret_cast<const float*>(sbase + st * L::STAGE); };
+  auto ps = [&](int st) { return reinterpret_cast<const T*>(sbase + st * L::STAGE + L::ZB_AL); };
+  auto qs = [&](int st) { return reinterpret_cast<const T*>(sbase + st * L::STAGE + L::ZB_AL + L::PB_AL); };
+
+  // thread 0: plane j into stage j % NS (planes outside the volume are not
+  // loaded; their cells read as zero below)
+  int issued_end = 0;      // thread 0: planes [0, issued_end) were issued
+  int first_pending = -1;  // first plane whose wait gave up (its load may still land)
+  auto issue = [&](int j) {
+    const int k = k0 - 1 + j;
+    if (j >= nplanes) return;
+    issued_end = j + 1;
+    if (k < 0 || k >= D) return;
+    const int st = j % NS;
+    const bool wz = j > 0;  // plane k0 - 1 contributes only r_z
+    unsigned char* stage = sbase + st * L::STAGE;
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&bar[st], (wz ? L::ZB : 0u) + L::PB + (mom ? L::PB : 0u));
+    if (wz) tma_load_3d(stage, &tm_z, xz, yr, k, &bar[st]);
+    tma_load_4d(stage + L::ZB_AL, &tm_p, xp, yr, k, 0, &bar[st]);
+    if (mom) tma_load_4d(stage + L::ZB_AL + L::PB_AL, &tm_q, xp, yr, k, 0, &bar[st]);
+  };
+
+  uint32_t ph = 0;  // parity of the next phase of each stage's barrier
+  // r(k) (and z) of plane j from its stage; cells outside the volume are zero
+  auto take = [&](int j, float (&rz)[RPW][CPL], float (&ry)[RPW][CPL], float (&rx)[RPW][CPL],
+                  float (&zz)[RPW][CPL], bool need_all) {
+    const int k = k0 - 1 + j;
+    const bool in = k >= 0 && k < D;
+    const int st = j % NS;
+    if (in) {
+      if (mbar_wait_bounded(&bar[st], (ph >> st) & 1u, &g_tma_wait_timeouts)) {
+        ph ^= 1u << st;
+      } else {
+        s_abort = 1;
+        if (first_pending < 0) first_pending = j;
+      }
+    }
+    const T* P = ps(st);
+    const T* Q = qs(st);
+    const float* Z = zs(st);
+#pragma unroll
+    for (int r = 0; r < RPW; ++r)
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) {
+        const int cell = (warp * RPW + r) * L::BXP + lane * CPL + q + op;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, zv = 0.f;
+        if (in) {
+          const float c0 = Elem<T>::cvt(P[cell]);
+          a0 = mom ? c0 + beta * (c0 - Elem<T>::cvt(Q[cell])) : c0;
+          if (need_all) {
+            const float c1 = Elem<T>::cvt(P[RH * L::BXP + cell]), c2 = Elem<T>::cvt(P[2 * RH * L::BXP + cell]);
+            if (mom) {
+              a1 = c1 + beta * (c1 - Elem<T>::cvt(Q[RH * L::BXP + cell]));
+              a2 = c2 + beta * (c2 - Elem<T>::cvt(Q[2 * RH * L::BXP + cell]));
+            } else {
+              a1 = c1;
+              a2 = c2;
+            }
+            zv = Z[(warp * RPW + r) * L::BXZ + lane * CPL + q + oz];
+          }
+        }
+        rz[r][q] = a0;
+        ry[r][q] = a1;
+        rx[r][q] = a2;
+        zz[r][q] = zv;
+      }
+  };
+  // u at plane k from r(k), r_z(k-1) and the staged r_y row above
+  auto form_u = [&](int k, const float (&rz)[RPW][CPL], const float (&ry)[RPW][CPL],
+                    const float (&rx)[RPW][CPL], const float (&rzm)[RPW][CPL],
+                    const float (&zz)[RPW][CPL], const float* ry_above, float (&u)[RPW][CPL]) {
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+      const float rx_left = __shfl_up_sync(0xffffffffu, rx[r][CPL - 1], 1);
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) {
+        const float up = r > 0 ? ry[r - 1][q] : ry_above[q];
+        const float lf = q > 0 ? rx[r][q - 1] : rx_left;
+        float dv = 0.f;
+        if (k < D - 1) dv += rz[r][q];
+        if (k > 0) dv -= rzm[r][q];
+        if (row_dn[r]) dv += ry[r][q];
+        if (row_up[r]) dv -= up;
+        if (col_rt[q]) dv += rx[r][q];
+        if (col_lf[q]) dv -= lf;
+        float v = zz[r][q] + lam * dv;
+        if (NONNEG) v = fmaxf(v, 0.f);
+        u[r][q] = (k < D && row_in[r] && col_in[q]) ? v : 0.f;
+      }
+    }
+  };
+
+  if (tid == 0) {
+    for (int st = 0; st < NS; ++st) mbar_init(&bar[st], 1);
+    s_abort = 0;
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    issue(0);
+    issue(1);
+  }
+  float Rz[RPW][CPL], Ry[RPW][CPL], Rx[RPW][CPL], Rzm[RPW][CPL], Uk[RPW][CPL];
+  float Zt[RPW][CPL], Dy[RPW][CPL], Dx[RPW][CPL];
+  take(0, Rzm, Dy, Dx, Zt, false);
+  take(1, Rz, Ry, Rx, Zt, true);
+  int buf = 0;
+#pragma unroll
+  for (int q = 0; q < CPL; ++q) sh_ry[buf][warp][lane * CPL + q] = Ry[RPW - 1][q];
+  __syncthreads();
+  bool aborted = s_abort != 0;
+  if (tid == 0 && !aborted)
+    for (int j = 2; j < 2 + NS; ++j) issue(j);
+  {
+    float above[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) above[q] = warp > 0 ? sh_ry[buf][warp - 1][lane * CPL + q] : 0.f;
+    form_u(k0, Rz, Ry, Rx, Rzm, Zt, above, Uk);
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) sh_u[buf][warp][lane * CPL + q] = Uk[0][q];
+  }
+  int consumed = 2;  // planes taken so far (thread 0 uses it to drain after an abort)
+  for (int k = k0; k < k1 && !aborted; ++k) {
+    const int j = k - k0 + 2;  // plane k + 1
+    float Rz1[RPW][CPL], Ry1[RPW][CPL], Rx1[RPW][CPL], U1[RPW][CPL];
+    take(j, Rz1, Ry1, Rx1, Zt, true);
+    consumed = j + 1;
+    const int nb = buf ^ 1;
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) sh_ry[nb][warp][lane * CPL + q] = Ry1[RPW - 1][q];
+    __syncthreads();
+    // every thread reads the flag after the same barrier: all leave together
+    aborted = s_abort != 0;
+    if (aborted) break;
+    if (tid == 0) issue(j + NS);  // the stage plane j came from is free again
+    float above[CPL], below_u[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+      above[q] = warp > 0 ? sh_ry[nb][warp - 1][lane * CPL + q] : 0.f;
+      below_u[q] = warp < NW - 1 ? sh_u[buf][warp + 1][lane * CPL + q] : 0.f;
+    }
+    form_u(k + 1, Rz1, Ry1, Rx1, Rz, Zt, above, U1);
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) sh_u[nb][warp][lane * CPL + q] = U1[0][q];
+    // p_{k+1} at plane k
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+      const float u_right = __shfl_down_sync(0xffffffffu, Uk[r][0], 1);
+      const int a = warp * RPW + r;
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) {
+        const float uc = Uk[r][q];
+        const float dn = r < RPW - 1 ? Uk[r + 1][q] : below_u[q];
+        const float rt = q < CPL - 1 ? Uk[r][q + 1] : u_right;
+        const float g0 = k < D - 1 ? U1[r][q] - uc : 0.f;
+        const float g1 = row_dn[r] ? dn - uc : 0.f;
+        const float g2 = col_rt[q] ? rt - uc : 0.f;
+        const float q0 = Rz[r][q] + inv_step * g0;
+        const float q1 = Ry[r][q] + inv_step * g1;
+        const float q2 = Rx[r][q] + inv_step * g2;
+        const float nrm2 = q0 * q0 + q1 * q1 + q2 * q2;
+        const float sc = nrm2 > 1.f ? rsqrtf(nrm2) : 1.f;
+        const int c = lane * CPL + q;
+        if (a >= 1 && a <= TH && c >= 1 && c <= TW && row_in[r] && col_in[q]) {
+          const size_t o = (size_t)k * HW + (size_t)(gi0 + r) * W + (gj0 + q);
+          Elem<T>::st(pn + o, q0 * sc);
+          Elem<T>::st(pn + n + o, q1 * sc);
+          Elem<T>::st(pn + 2 * n + o, q2 * sc);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RPW; ++r)
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) {
+        Rzm[r][q] = Rz[r][q];
+        Rz[r][q] = Rz1[r][q];
+        Ry[r][q] = Ry1[r][q];
+        Rx[r][q] = Rx1[r][q];
+        Uk[r][q] = U1[r][q];
+      }
+    buf = nb;
+  }
+  // After a wait gave up, nothing more is stored; thread 0 lets the loads still
+  // in flight (the one it gave up on, if any, and those issued after the last
+  // plane taken) land, each wait bounded again, so that none writes shared
+  // memory after the CTA has exited.
+  if (aborted && tid == 0) {
+    for (int j = consumed - 1; j < issued_end; ++j) {
+      const int jj = j < consumed ? first_pending : j;  // first the plane given up on
+      const int k = k0 - 1 + jj;
+      if (jj < 0 || k < 0 || k >= D) continue;
+      const int st = jj % NS;
+      if (!mbar_wait_bounded(&bar[st], (ph >> st) & 1u, &g_tma_wait_timeouts)) break;
+      ph ^= 1u << st;
+    }
+  }
+}
+
+// z-marching variants: (columns per lane, rows per warp, planes per chunk);
+// TVS_FGP3D_CFG="cpl,rpw,zc" selects one.
+template <typename T, bool NN, int CPL, int RPW, int ZC>
+cudaError_t fgp3d_zm_launch(const Dims& d, const float* z, const void* pc, const void* pp, void* pn, float lam,
+                            float inv_step, float beta, cudaStream_t s) {
+  constexpr int TW = 32 * CPL - 2, TH = 8 * RPW - 2;
+  dim3 grid((d.nx + TW - 1) / TW, (d.ny + TH - 1) / TH, (d.nz + ZC - 1) / ZC);
+  launch_kernel(fgp3d_zm_kernel<T, NN, CPL, RPW, ZC>, dim3(grid), dim3(256), 0, s, z, (const T*)pc, (const T*)pp,
+                (T*)pn, d.nz, d.ny, d.nx, lam, inv_step, beta);
+  return cudaGetLastError();
+}
+
+// The TMA variant of a z-marching configuration; *used = false (nothing
+// launched) when the buffers or the row pitch do not meet TMA's 16-byte rules or
+// the driver refuses a tensor map, so that the caller falls back.
+template <typename T, bool NN, int CPL, int RPW, int ZC, int NS>
+cudaError_t fgp3d_tma_launch(const Dims& d, const float* z, const void* pc, const void* pp, void* pn, float lam,
+                             float inv_step, float beta, cudaStream_t s, bool* used) {
+  using L = ZmTma<T, CPL, RPW, NS>;
+  *used = false;
+  if constexpr (L::SMEM + 128u * L::RW + 64u > 227u * 1024u) return cudaSuccess;
+  // the ring may pass the 48 KB a launch gets without opting in, and the SM's
+  // shared/L1 split is asked to favour shared memory so that the resident CTAs
+  // are set by registers, not by a small carveout (attributes of the function,
+  // not stream work: also valid while a stream is being captured)
+  static const cudaError_t attr = [] {
+    auto k = fgp3d_tma_kernel<T, NN, CPL, RPW, ZC, NS>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    return e;
+  }();
+  if (attr != cudaSuccess) return attr;
+  const uint64_t es = sizeof(T), nx = d.nx, ny = d.ny, nz = d.nz;
+  if (!pp) pp = pc;
+  if (((uintptr_t)z | (uintptr_t)pc | (uintptr_t)pp) & 15) return cudaSuccess;
+  if ((nx * 4) % 16 || (nx * es) % 16) return cudaSuccess;
+  CUtensorMap mz, mp, mq;
+  const uint64_t dz[3] = {nx, ny, nz}, sz[2] = {nx * 4, nx * ny * 4};
+  const uint32_t bz[3] = {(uint32_t)L::BXZ, (uint32_t)L::RH, 1};
+  const uint64_t dp[4] = {nx, ny, nz, 3}, sp[3] = {nx * es, nx * ny * es, nx * ny * nz * es};
+  const uint32_t bp[4] = {(uint32_t)L::BXP, (uint32_t)L::RH, 1, 3};
+  const CUtensorMapDataType tp = es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+  if (!encode_tensor_map(&mz, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, z, dz, sz, bz) ||
+      !encode_tensor_map(&mp, tp, 4, pc, dp, sp, bp) || !encode_tensor_map(&mq, tp, 4, pp, dp, sp, bp))
+    return cudaSuccess;
+  constexpr int TW = L::RW - 2, TH = L::RH - 2;
+  dim3 grid((d.nx + TW - 1) / TW, (d.ny + TH - 1) / TH, (d.nz + ZC - 1) / ZC);
+  launch_kernel(fgp3d_tma_kernel<T, NN, CPL, RPW, ZC, NS>, grid, dim3(256), (size_t)L::SMEM, s, mz, mp, mq,
+                (T*)pn, d.nz, d.ny, d.nx, lam, inv_step, beta);
+  g_tma_launched.store(true, std::memory_order_relaxed);
+  *used = true;
+  return cudaGetLastError();
+}
+
+struct ZmCfg {
+  int cpl = 0, rpw = 0, zc = 0;
+};
+// Defaults: the fastest variant measured at 512^3 for each dual width (FP32,
+// register loads: 1,2,64; 16-bit, TMA staging: 2,2,32); TVS_FGP3D_CFG overrides
+// both.  The environment is read at every launch (and so fixed in a captured
+// graph), so that a process can compare the variants one after another.
+ZmCfg fgp3d_zm_cfg(bool half_dual) {
+  if (const char* e = getenv("TVS_FGP3D_CFG")) {
+    ZmCfg t;
+    if (sscanf(e, "%d,%d,%d", &t.cpl, &t.rpw, &t.zc) == 3 && t.cpl > 0) return t;
+  }
+  ZmCfg c;
+  c.cpl = half_dual ? 2 : 1;
+  c.rpw = 2;
+  c.zc = half_dual ? 32 : 64;
+  return c;
+}
+
+// Stages of the TMA ring: 2, or 3 with TVS_FGP3D_STAGES=3 (read at every launch).
+int fgp3d_tma_stages() {
+  const char* e = getenv("TVS_FGP3D_STAGES");
+  return (e && e[0] == '3') ? 3 : 2;
+}
+
+enum class Fgp3dKind { Auto, Tile, Zm, Tma };
+// TVS_FGP3D=tile / zm / tma forces the tiled kernel, the z-marching kernel with
+// register loads, or the z-marching kernel with TMA staging (read at every
+// launch, and so fixed in a captured graph).
+Fgp3dKind fgp3d_kind_env() {
+  const char* e = getenv("TVS_FGP3D");
+  if (!e) return Fgp3dKind::Auto;
+  if (strcmp(e, "tile") == 0) return Fgp3dKind::Tile;
+  if (strcmp(e, "zm") == 0) return Fgp3dKind::Zm;
+  if (strcmp(e, "tma") == 0) return Fgp3dKind::Tma;
+  return Fgp3dKind::Auto;
+}
+
+template <typename T, bool NN>
+cudaError_t fgp3d_zm_dispatch(const Dims& d, const float* z, const void* pc, const void* pp, void* pn, float lam,
+                              float inv_step, float beta, bool tma, cudaStream_t s) {
+  const ZmCfg c = fgp3d_zm_cfg(sizeof(T) == 2);
+  bool used = false;
+#define TVS_ZM(C_, R_, Z_)                                                                                \
+  if (c.cpl == C_ && c.rpw == R_ && c.zc == Z_) {                                                        \
+    if (tma) {                                                                                           \
+      const cudaError_t e =                                                                              \
+          fgp3d_tma_stages() == 3                                                                        \
+              ? fgp3d_tma_launch<T, NN, C_, R_, Z_, 3>(d, z, pc, pp, pn, lam, inv_step, beta, s, &used)  \
+              : fgp3d_tma_launch<T, NN, C_, R_, Z_, 2>(d, z, pc, pp, pn, lam, inv_step, beta, s, &used); \
+      if (e != cudaSuccess || used) return e;                                                            \
+    }                                                                                                    \
+    return fgp3d_zm_launch<T, NN, C_, R_, Z_>(d, z, pc, pp, pn, lam, inv_step, beta, s);                  \
+  }
+  TVS_ZM(1, 2, 64)
+  TVS_ZM(1, 4, 64)
+  TVS_ZM(2, 2, 64)
+  TVS_ZM(1, 2, 32)
+  TVS_ZM(2, 2, 32)
+  TVS_ZM(2, 4, 32)
+#undef TVS_ZM
+  return fgp3d_zm_launch<T, NN, 1, 2, 64>(d, z, pc, pp, pn, lam, inv_step, beta, s);
+}
+
+template <typename T, bool NN>
+cudaError_t fgp3d_iter_t(const Dims& d, const float* z, const void* pc, const void* pp, void* pn,
+                         float lam, float inv_step, float beta, cudaStream_t s) {
+  Fgp3dKind kind = fgp3d_kind_env();
+  if (kind == Fgp3dKind::Auto) {
+    // z-marching needs enough (x-y tile, z chunk) pairs to fill the GPU.  With a
+    // 16-bit dual the TMA-staged kernel is the faster (512^3, BF16: 906 -> 650
+    // us per iteration; Q15: 950 -> 737 us); with an FP32 dual the kernel with
+    // register loads and its prefetch of the next plane (950 us) is at least as
+    // fast as every TMA variant measured (944 - 1415 us).
+    const bool big = (long long)((d.nx + 29) / 30) * ((d.ny + 13) / 14) * ((d.nz + 63) / 64) >= 4 * 152;
+    kind = !big ? Fgp3dKind::Tile : (sizeof(T) == 2 ? Fgp3dKind::Tma : Fgp3dKind::Zm);
+  }
+  if (kind != Fgp3dKind::Tile)
+    return fgp3d_zm_dispatch<T, NN>(d, z, pc, pp, pn, lam, inv_step, beta, kind == Fgp3dKind::Tma, s);
+  dim3 grid((d.nx + TX3 - 1) / TX3, (d.ny + TY3 - 1) / TY3, (d.nz + TZ3 - 1) / TZ3);
+  launch_kernel(fgp3d_kernel<T, NN>, dim3(grid), dim3(NT3), 0, s, z, (const T*)pc, (const T*)pp, (T*)pn, d.nz, d.ny,
+                d.nx, lam, inv_step, beta);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool encode_tensor_map(CUtensorMap* map, CUtensorMapDataType type, int rank, const void* base,
+                       const uint64_t* dims, const uint64_t* strides_bytes, const uint32_t* box) {
+  static const PFN_cuTensorMapEncodeTiled_v12000 encode = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      (void)cudaGetLastError();
+      return nullptr;
+    }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  if (!encode || rank < 1 || rank > 5) return false;
+  cuuint64_t gd[5], gs[4];
+  cuuint32_t bx[5], es[5];
+  for (int i = 0; i < rank; ++i) {
+    gd[i] = dims[i];
+    bx[i] = box[i];
+    es[i] = 1;
+    if (i + 1 < rank) gs[i] = strides_bytes[i];
+  }
+  // 128-byte L2 promotion: 256 measured 6 % slower on the FP32 boxes (rows of
+  // 144 B) and no different on the 16-bit ones
+  return encode(map, type, (cuuint32_t)rank, const_cast<void*>(base), gd, gs, bx, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool fgp3d_take_wait_timeouts() {
+  if (!g_tma_launched.load(std::memory_order_relaxed)) return false;
+  unsigned int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_tma_wait_timeouts, sizeof(v)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  if (v == 0) return false;
+  const unsigned int zero = 0;
+  (void)cudaMemcpyToSymbol(g_tma_wait_timeouts, &zero, sizeof(zero));
+  return true;
+}
+
+cudaError_t launch_fgp3d_iter(const Dims& d, const float* z, const void* pc, const void* pp, void* pn,
+                              float lam, float inv_step, float beta, int dtype, bool nonneg, cudaStream_t s) {
+  if (d.n() == 0) return cudaSuccess;
+  if (d.ndim != 3) return cudaErrorInvalidValue;
+  return with_dual_type(dtype, [&](auto tag) {
+    using T = typename decltype(tag)::type;
+    return nonneg ? fgp3d_iter_t<T, true>(d, z, pc, pp, pn, lam, inv_step, beta, s)
+                  : fgp3d_iter_t<T, false>(d, z, pc, pp, pn, lam, inv_step, beta, s);
+  });
+}
+
+}  // namespace tvs

@@ -1,5 +1,5 @@
 // Register-blocked temporally blocked FGP body for 2D images, shared by the
-// single-problem kernel (fgp.cu) and the batched kernel (batch.cu).
+// single-problem kernel (fgp_tb.cu) and the batched kernel (batch.cu).
 #pragma once
 
 #include "common.cuh"

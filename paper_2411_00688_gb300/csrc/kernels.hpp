@@ -76,12 +76,18 @@ struct Partial {
 };
 inline size_t dual_elem_bytes(int t) { return t == DUAL_F32 ? 4 : 2; }
 
-// ---- TV prox (fgp.cu) ----
+// ---- TV prox (fgp.cu, fgp_tb.cu, fgp3d.cu) ----
 // One inner iteration: r = pc + beta (pc - pp); u = P_X(z + lam div r);
 // pn = P_B(r + inv_step * D u).  pp may equal pc when beta == 0.
 cudaError_t launch_fgp_iter(const Dims& d, const float* z, const void* pc, const void* pp, void* pn,
                             float lam, float inv_step, float beta, int dtype, bool nonneg,
                             cudaStream_t s);
+// One 3D iteration (fgp3d.cu); launch_fgp_iter forwards 3D volumes here.
+cudaError_t launch_fgp3d_iter(const Dims& d, const float* z, const void* pc, const void* pp, void* pn,
+                              float lam, float inv_step, float beta, int dtype, bool nonneg, cudaStream_t s);
+// True (and the count cleared) when a bounded wait of a TMA-staged 3D kernel
+// gave up since the last call; call only after the stream has been synchronised.
+bool fgp3d_take_wait_timeouts();
 // PDHGSkip-1 finalisation: u = P_X(z + lam div p); xh = (u - x)/prob_p; x += prob_p xh.
 cudaError_t launch_fgp_finalize_pd1(const Dims& d, const float* z, const void* p, int dtype, float lam,
                                     bool nonneg, float prob_p, float* x, float* xh, void* p_home,
