@@ -52,10 +52,16 @@ WORKLOAD = ("deblur2d_1024: 1024x1024, 40 ellipses, 9x9 Gaussian sigma 2, noise 
 # capture of `dram__bytes_read.sum + dram__bytes_write.sum`.  Each record describes
 # only the kernel sources and launch configuration it was taken on: the bench line
 # carries it only while the hash of those sources (and the configuration) match.
-FGP_TRAFFIC = {"config": [4, 2, 104], "bytes": 20390558,
+FGP_TRAFFIC = {"config": [4, 2, 104], "bytes": 20388825,
                "sources": ["common.cuh", "fgp_rb.cuh", "fgp_tb.cu"],
-               "sha256": "cec4d58a47436f50a6bb7c3c1f99a6e37b18bdfd7ffdac64826c06ccd55debcc"}
-FGP3_TRAFFIC = {}   # dual -> {"bytes": per launch at 512^3, "sources": [...], "sha256": ...}
+               "sha256": "871296a6d16aaf315d36acd9e5dc8a38b9425cd90064afab3d11cc83cfa6414c"}
+# 3D: per momentum launch of the default kernel, captured on a 320^3 volume
+# (inputs larger than L2) and scaled by the voxel count to 512^3.
+_FGP3_SRC = {"sources": ["common.cuh", "tma.cuh", "fgp3d.cu"],
+             "sha256": "a1b97d35a7dc4796545baeae0ae49d0b26052b4aada2ef1e28d868c9e88d94de"}
+FGP3_TRAFFIC = {"f32": dict(_FGP3_SRC, bytes=5401626018),
+                "bf16": dict(_FGP3_SRC, bytes=2957804306),
+                "q15": dict(_FGP3_SRC, bytes=2959729492)}
 # Iterations this workload's ProxSkip solve needs to reach the target on the GPU
 # (its trace: 261 iterations); the reference arm extrapolates the oracle to them,
 # counting the prox calls among them from the coin schedule.
@@ -282,7 +288,8 @@ def extra_denoise3d(tvs, ctx, stream, hbm_peak, peak_kind):
         per_it = (med(n_it + 2) - med(2)) / n_it
         per_launch = (fgp_algo_bytes(n_it + 2, N ** 3, 3, dual) - fgp_algo_bytes(2, N ** 3, 3, dual)) / n_it
         achieved = per_launch / per_it / 1e9
-        out[dual] = {"kernel": "fgp3d_zm_kernel", "us_per_inner_iteration": per_it * 1e6,
+        out[dual] = {"kernel": "fgp3d_tma2_kernel (z-marching, planes by TMA tile loads, packed FP32x2, "
+                               "2 columns x 4 rows per lane)", "us_per_inner_iteration": per_it * 1e6,
                      "bytes_per_launch": per_launch, "achieved_gbs": achieved,
                      "frac": achieved / hbm_peak, "traffic": _fgp3_traffic(dual)}
         del state

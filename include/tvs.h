@@ -213,9 +213,9 @@ tvs_status tv_prox(tvs_ctx* ctx, int ndim, const int dims[3], const float* z, fl
  * 2D shape times the candidates on the device and caches the fastest;
  * TVS_FGP_CONFIG="tb,cpl,rpw" in the environment forces one, and
  * TVS_TUNE_CACHE=path keeps the choices in a text file across processes.  3D volumes
- * large enough to fill the GPU with (x-y tile, z chunk) pairs take a z-marching
- * kernel (with a 16-bit dual the one whose planes arrive by TMA tile loads, with
- * an FP32 dual the one with register loads), smaller ones the tiled kernel;
+ * large enough to fill the GPU with (x-y tile, z chunk) pairs take the z-marching
+ * kernel whose planes arrive by TMA tile loads (register loads where a buffer or
+ * the row pitch is not 16-byte aligned), smaller ones the tiled kernel;
  * TVS_FGP3D=tma, zm or tile forces one (tma falls back to zm where the row pitch or
  * a buffer is not 16-byte aligned), TVS_FGP3D_CFG="cpl,rpw,zc" picks a z-marching
  * variant and TVS_FGP3D_STAGES=3 a three-stage TMA ring (all read at each launch).

@@ -2,8 +2,21 @@
 // per launch (the iteration of fgp.cu with the three-component dual and
 // step 1/(12 lam)), either over (x, y, z) tiles staged in shared memory
 // (fgp3d_kernel) or marching through z (fgp3d_zm_kernel with register loads,
-// fgp3d_tma_kernel with TMA tile loads; the default for volumes large enough
-// to fill the GPU).
+// fgp3d_tma_kernel with TMA tile loads, fgp3d_tma2_kernel the same with two
+// columns per lane in packed FP32x2 arithmetic; the default for volumes large
+// enough to fill the GPU).
+//
+// Every kernel here evaluates each step in one fixed order with explicit
+// round-to-nearest operations (no contraction left to the compiler):
+//   r   = fma(beta, c - p_prev, c)
+//   dv  = ((((((0 + r_z) - r_z(k-1)) + r_y) - r_y(i-1)) + r_x) - r_x(j-1)),
+//         each term only where the Neumann rule keeps it
+//   u   = fma(lam, dv, z)                      (then max(., 0) when nonneg)
+//   q_c = fma(inv_step, g_c, r_c),  g_c the forward difference of u (0 at the
+//         last index of the axis)
+//   |q|^2 = fma(q_x, q_x, fma(q_y, q_y, q_z * q_z))
+//   p   = q * (|q|^2 > 1 ? rsqrt(|q|^2) : 1)
+// so that every variant stores the same bits.
 #include <cudaTypedefs.h>
 
 #include <atomic>
@@ -40,9 +53,9 @@ fgp3d_kernel(const float* __restrict__ z, const T* __restrict__ pc, const T* __r
       const size_t o = ((size_t)gk * H + gi) * W + gj;
       const float c0 = Elem<T>::ld(pc + o), c1 = Elem<T>::ld(pc + n + o), c2 = Elem<T>::ld(pc + 2 * n + o);
       if (beta != 0.f) {
-        r0 = c0 + beta * (c0 - Elem<T>::ld(pp + o));
-        r1 = c1 + beta * (c1 - Elem<T>::ld(pp + n + o));
-        r2 = c2 + beta * (c2 - Elem<T>::ld(pp + 2 * n + o));
+        r0 = __fmaf_rn(beta, __fsub_rn(c0, Elem<T>::ld(pp + o)), c0);
+        r1 = __fmaf_rn(beta, __fsub_rn(c1, Elem<T>::ld(pp + n + o)), c1);
+        r2 = __fmaf_rn(beta, __fsub_rn(c2, Elem<T>::ld(pp + 2 * n + o)), c2);
       } else {
         r0 = c0; r1 = c1; r2 = c2;
       }
@@ -60,13 +73,13 @@ fgp3d_kernel(const float* __restrict__ z, const T* __restrict__ pc, const T* __r
     float u = 0.f;
     if (gk < D && gi < H && gj < W) {
       float dv = 0.f;
-      if (gk < D - 1) dv += sr[0][c + 1][a + 1][b + 1];
-      if (gk > 0) dv -= sr[0][c][a + 1][b + 1];
-      if (gi < H - 1) dv += sr[1][c + 1][a + 1][b + 1];
-      if (gi > 0) dv -= sr[1][c + 1][a][b + 1];
-      if (gj < W - 1) dv += sr[2][c + 1][a + 1][b + 1];
-      if (gj > 0) dv -= sr[2][c + 1][a + 1][b];
-      u = __ldg(z + ((size_t)gk * H + gi) * W + gj) + lam * dv;
+      if (gk < D - 1) dv = __fadd_rn(dv, sr[0][c + 1][a + 1][b + 1]);
+      if (gk > 0) dv = __fsub_rn(dv, sr[0][c][a + 1][b + 1]);
+      if (gi < H - 1) dv = __fadd_rn(dv, sr[1][c + 1][a + 1][b + 1]);
+      if (gi > 0) dv = __fsub_rn(dv, sr[1][c + 1][a][b + 1]);
+      if (gj < W - 1) dv = __fadd_rn(dv, sr[2][c + 1][a + 1][b + 1]);
+      if (gj > 0) dv = __fsub_rn(dv, sr[2][c + 1][a + 1][b]);
+      u = __fmaf_rn(lam, dv, __ldg(z + ((size_t)gk * H + gi) * W + gj));
       if (NONNEG) u = fmaxf(u, 0.f);
     }
     su[c][a][b] = u;
@@ -78,18 +91,18 @@ fgp3d_kernel(const float* __restrict__ z, const T* __restrict__ pc, const T* __r
     const int gk = k0 + c, gi = i0 + a, gj = j0 + b;
     if (gk < D && gi < H && gj < W) {
       const float uc = su[c][a][b];
-      const float g0 = gk < D - 1 ? su[c + 1][a][b] - uc : 0.f;
-      const float g1 = gi < H - 1 ? su[c][a + 1][b] - uc : 0.f;
-      const float g2 = gj < W - 1 ? su[c][a][b + 1] - uc : 0.f;
-      const float q0 = sr[0][c + 1][a + 1][b + 1] + inv_step * g0;
-      const float q1 = sr[1][c + 1][a + 1][b + 1] + inv_step * g1;
-      const float q2 = sr[2][c + 1][a + 1][b + 1] + inv_step * g2;
-      const float nrm2 = q0 * q0 + q1 * q1 + q2 * q2;
+      const float g0 = gk < D - 1 ? __fsub_rn(su[c + 1][a][b], uc) : 0.f;
+      const float g1 = gi < H - 1 ? __fsub_rn(su[c][a + 1][b], uc) : 0.f;
+      const float g2 = gj < W - 1 ? __fsub_rn(su[c][a][b + 1], uc) : 0.f;
+      const float q0 = __fmaf_rn(inv_step, g0, sr[0][c + 1][a + 1][b + 1]);
+      const float q1 = __fmaf_rn(inv_step, g1, sr[1][c + 1][a + 1][b + 1]);
+      const float q2 = __fmaf_rn(inv_step, g2, sr[2][c + 1][a + 1][b + 1]);
+      const float nrm2 = __fmaf_rn(q2, q2, __fmaf_rn(q1, q1, __fmul_rn(q0, q0)));
       const float sc = nrm2 > 1.f ? rsqrtf(nrm2) : 1.f;
       const size_t o = ((size_t)gk * H + gi) * W + gj;
-      Elem<T>::st(pn + o, q0 * sc);
-      Elem<T>::st(pn + n + o, q1 * sc);
-      Elem<T>::st(pn + 2 * n + o, q2 * sc);
+      Elem<T>::st(pn + o, __fmul_rn(q0, sc));
+      Elem<T>::st(pn + n + o, __fmul_rn(q1, sc));
+      Elem<T>::st(pn + 2 * n + o, __fmul_rn(q2, sc));
     }
   }
 }
@@ -151,12 +164,12 @@ fgp3d_zm_kernel(const float* __restrict__ z, const T* __restrict__ pc, const T* 
         if (k >= 0 && k < D && row_in[r] && col_in[q]) {
           const size_t o = (size_t)k * HW + (size_t)(gi0 + r) * W + (gj0 + q);
           const float c0 = Elem<T>::ld(pc + o);
-          a0 = beta != 0.f ? c0 + beta * (c0 - Elem<T>::ld(pp + o)) : c0;
+          a0 = beta != 0.f ? __fmaf_rn(beta, __fsub_rn(c0, Elem<T>::ld(pp + o)), c0) : c0;
           if (need_all) {
             const float c1 = Elem<T>::ld(pc + n + o), c2 = Elem<T>::ld(pc + 2 * n + o);
             if (beta != 0.f) {
-              a1 = c1 + beta * (c1 - Elem<T>::ld(pp + n + o));
-              a2 = c2 + beta * (c2 - Elem<T>::ld(pp + 2 * n + o));
+              a1 = __fmaf_rn(beta, __fsub_rn(c1, Elem<T>::ld(pp + n + o)), c1);
+              a2 = __fmaf_rn(beta, __fsub_rn(c2, Elem<T>::ld(pp + 2 * n + o)), c2);
             } else {
               a1 = c1;
               a2 = c2;
@@ -182,13 +195,13 @@ fgp3d_zm_kernel(const float* __restrict__ z, const T* __restrict__ pc, const T* 
         const float up = r > 0 ? ry[r - 1][q] : ry_above[q];
         const float lf = q > 0 ? rx[r][q - 1] : rx_left;
         float dv = 0.f;
-        if (k < D - 1) dv += rz[r][q];
-        if (k > 0) dv -= rzm[r][q];
-        if (row_dn[r]) dv += ry[r][q];
-        if (row_up[r]) dv -= up;
-        if (col_rt[q]) dv += rx[r][q];
-        if (col_lf[q]) dv -= lf;
-        float v = zz[r][q] + lam * dv;
+        if (k < D - 1) dv = __fadd_rn(dv, rz[r][q]);
+        if (k > 0) dv = __fsub_rn(dv, rzm[r][q]);
+        if (row_dn[r]) dv = __fadd_rn(dv, ry[r][q]);
+        if (row_up[r]) dv = __fsub_rn(dv, up);
+        if (col_rt[q]) dv = __fadd_rn(dv, rx[r][q]);
+        if (col_lf[q]) dv = __fsub_rn(dv, lf);
+        float v = __fmaf_rn(lam, dv, zz[r][q]);
         if (NONNEG) v = fmaxf(v, 0.f);
         u[r][q] = (k < D && row_in[r] && col_in[q]) ? v : 0.f;
       }
@@ -230,7 +243,7 @@ fgp3d_zm_kernel(const float* __restrict__ z, const T* __restrict__ pc, const T* 
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           const float cc = Elem<T>::cvt(Pc[r][q][c]);
-          a[c] = beta != 0.f ? cc + beta * (cc - Elem<T>::cvt(Pp[r][q][c])) : cc;
+          a[c] = beta != 0.f ? __fmaf_rn(beta, __fsub_rn(cc, Elem<T>::cvt(Pp[r][q][c])), cc) : cc;
         }
         rz[r][q] = a[0];
         ry[r][q] = a[1];
@@ -288,20 +301,20 @@ fgp3d_zm_kernel(const float* __restrict__ z, const T* __restrict__ pc, const T* 
         const float uc = Uk[r][q];
         const float dn = r < RPW - 1 ? Uk[r + 1][q] : below_u[q];
         const float rt = q < CPL - 1 ? Uk[r][q + 1] : u_right;
-        const float g0 = k < D - 1 ? U1[r][q] - uc : 0.f;
-        const float g1 = row_dn[r] ? dn - uc : 0.f;
-        const float g2 = col_rt[q] ? rt - uc : 0.f;
-        const float q0 = Rz[r][q] + inv_step * g0;
-        const float q1 = Ry[r][q] + inv_step * g1;
-        const float q2 = Rx[r][q] + inv_step * g2;
-        const float nrm2 = q0 * q0 + q1 * q1 + q2 * q2;
+        const float g0 = k < D - 1 ? __fsub_rn(U1[r][q], uc) : 0.f;
+        const float g1 = row_dn[r] ? __fsub_rn(dn, uc) : 0.f;
+        const float g2 = col_rt[q] ? __fsub_rn(rt, uc) : 0.f;
+        const float q0 = __fmaf_rn(inv_step, g0, Rz[r][q]);
+        const float q1 = __fmaf_rn(inv_step, g1, Ry[r][q]);
+        const float q2 = __fmaf_rn(inv_step, g2, Rx[r][q]);
+        const float nrm2 = __fmaf_rn(q2, q2, __fmaf_rn(q1, q1, __fmul_rn(q0, q0)));
         const float sc = nrm2 > 1.f ? rsqrtf(nrm2) : 1.f;
         const int c = lane * CPL + q;
         if (a >= 1 && a <= TH && c >= 1 && c <= TW && row_in[r] && col_in[q]) {
           const size_t o = (size_t)k * HW + (size_t)(gi0 + r) * W + (gj0 + q);
-          Elem<T>::st(pn + o, q0 * sc);
-          Elem<T>::st(pn + n + o, q1 * sc);
-          Elem<T>::st(pn + 2 * n + o, q2 * sc);
+          Elem<T>::st(pn + o, __fmul_rn(q0, sc));
+          Elem<T>::st(pn + n + o, __fmul_rn(q1, sc));
+          Elem<T>::st(pn + 2 * n + o, __fmul_rn(q2, sc));
         }
       }
     }
@@ -439,12 +452,12 @@ fgp3d_tma_kernel(const __grid_constant__ CUtensorMap tm_z, const __grid_constant
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, zv = 0.f;
         if (in) {
           const float c0 = Elem<T>::cvt(P[cell]);
-          a0 = mom ? c0 + beta * (c0 - Elem<T>::cvt(Q[cell])) : c0;
+          a0 = mom ? __fmaf_rn(beta, __fsub_rn(c0, Elem<T>::cvt(Q[cell])), c0) : c0;
           if (need_all) {
             const float c1 = Elem<T>::cvt(P[RH * L::BXP + cell]), c2 = Elem<T>::cvt(P[2 * RH * L::BXP + cell]);
             if (mom) {
-              a1 = c1 + beta * (c1 - Elem<T>::cvt(Q[RH * L::BXP + cell]));
-              a2 = c2 + beta * (c2 - Elem<T>::cvt(Q[2 * RH * L::BXP + cell]));
+              a1 = __fmaf_rn(beta, __fsub_rn(c1, Elem<T>::cvt(Q[RH * L::BXP + cell])), c1);
+              a2 = __fmaf_rn(beta, __fsub_rn(c2, Elem<T>::cvt(Q[2 * RH * L::BXP + cell])), c2);
             } else {
               a1 = c1;
               a2 = c2;
@@ -470,13 +483,13 @@ fgp3d_tma_kernel(const __grid_constant__ CUtensorMap tm_z, const __grid_constant
         const float up = r > 0 ? ry[r - 1][q] : ry_above[q];
         const float lf = q > 0 ? rx[r][q - 1] : rx_left;
         float dv = 0.f;
-        if (k < D - 1) dv += rz[r][q];
-        if (k > 0) dv -= rzm[r][q];
-        if (row_dn[r]) dv += ry[r][q];
-        if (row_up[r]) dv -= up;
-        if (col_rt[q]) dv += rx[r][q];
-        if (col_lf[q]) dv -= lf;
-        float v = zz[r][q] + lam * dv;
+        if (k < D - 1) dv = __fadd_rn(dv, rz[r][q]);
+        if (k > 0) dv = __fsub_rn(dv, rzm[r][q]);
+        if (row_dn[r]) dv = __fadd_rn(dv, ry[r][q]);
+        if (row_up[r]) dv = __fsub_rn(dv, up);
+        if (col_rt[q]) dv = __fadd_rn(dv, rx[r][q]);
+        if (col_lf[q]) dv = __fsub_rn(dv, lf);
+        float v = __fmaf_rn(lam, dv, zz[r][q]);
         if (NONNEG) v = fmaxf(v, 0.f);
         u[r][q] = (k < D && row_in[r] && col_in[q]) ? v : 0.f;
       }
@@ -545,20 +558,20 @@ fgp3d_tma_kernel(const __grid_constant__ CUtensorMap tm_z, const __grid_constant
         const float uc = Uk[r][q];
         const float dn = r < RPW - 1 ? Uk[r + 1][q] : below_u[q];
         const float rt = q < CPL - 1 ? Uk[r][q + 1] : u_right;
-        const float g0 = k < D - 1 ? U1[r][q] - uc : 0.f;
-        const float g1 = row_dn[r] ? dn - uc : 0.f;
-        const float g2 = col_rt[q] ? rt - uc : 0.f;
-        const float q0 = Rz[r][q] + inv_step * g0;
-        const float q1 = Ry[r][q] + inv_step * g1;
-        const float q2 = Rx[r][q] + inv_step * g2;
-        const float nrm2 = q0 * q0 + q1 * q1 + q2 * q2;
+        const float g0 = k < D - 1 ? __fsub_rn(U1[r][q], uc) : 0.f;
+        const float g1 = row_dn[r] ? __fsub_rn(dn, uc) : 0.f;
+        const float g2 = col_rt[q] ? __fsub_rn(rt, uc) : 0.f;
+        const float q0 = __fmaf_rn(inv_step, g0, Rz[r][q]);
+        const float q1 = __fmaf_rn(inv_step, g1, Ry[r][q]);
+        const float q2 = __fmaf_rn(inv_step, g2, Rx[r][q]);
+        const float nrm2 = __fmaf_rn(q2, q2, __fmaf_rn(q1, q1, __fmul_rn(q0, q0)));
         const float sc = nrm2 > 1.f ? rsqrtf(nrm2) : 1.f;
         const int c = lane * CPL + q;
         if (a >= 1 && a <= TH && c >= 1 && c <= TW && row_in[r] && col_in[q]) {
           const size_t o = (size_t)k * HW + (size_t)(gi0 + r) * W + (gj0 + q);
-          Elem<T>::st(pn + o, q0 * sc);
-          Elem<T>::st(pn + n + o, q1 * sc);
-          Elem<T>::st(pn + 2 * n + o, q2 * sc);
+          Elem<T>::st(pn + o, __fmul_rn(q0, sc));
+          Elem<T>::st(pn + n + o, __fmul_rn(q1, sc));
+          Elem<T>::st(pn + 2 * n + o, __fmul_rn(q2, sc));
         }
       }
     }
@@ -581,6 +594,266 @@ fgp3d_tma_kernel(const __grid_constant__ CUtensorMap tm_z, const __grid_constant
   if (aborted && tid == 0) {
     for (int j = consumed - 1; j < issued_end; ++j) {
       const int jj = j < consumed ? first_pending : j;  // first the plane given up on
+      const int k = k0 - 1 + jj;
+      if (jj < 0 || k < 0 || k >= D) continue;
+      const int st = jj % NS;
+      if (!mbar_wait_bounded(&bar[st], (ph >> st) & 1u, &g_tma_wait_timeouts)) break;
+      ph ^= 1u << st;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Packed variant of fgp3d_tma_kernel: each lane owns two adjacent columns as one
+// float2 and runs every step above as paired FP32x2 FMA/ADD/MUL instructions
+// (the masks that the Neumann rule and the volume's faces impose become 0/+-1
+// multipliers of the paired FMAs, or selects where a masked value must be
+// exactly +0); the plane data come from the TMA ring as 8-byte (FP32) or
+// 4-byte (16-bit) pairs.  For the pairs to be aligned the region starts two
+// columns left of its first output column: 64 columns give 60 outputs.
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
+template <typename T> struct Pair;
+template <> struct Pair<float> {
+  static __device__ __forceinline__ float2 ld(const float* p) { return *reinterpret_cast<const float2*>(p); }
+};
+template <> struct Pair<__nv_bfloat16> {
+  static __device__ __forceinline__ float2 ld(const __nv_bfloat16* p) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+  }
+};
+template <> struct Pair<__half> {
+  static __device__ __forceinline__ float2 ld(const __half* p) {
+    return __half22float2(*reinterpret_cast<const __half2*>(p));
+  }
+};
+template <> struct Pair<q15> {
+  static __device__ __forceinline__ float2 ld(const q15* p) {
+    const short2 v = *reinterpret_cast<const short2*>(p);
+    return make_float2(Elem<q15>::cvt(q15{v.x}), Elem<q15>::cvt(q15{v.y}));
+  }
+};
+
+template <typename T, int RPW, int NS_>
+struct ZmTma2 {
+  static constexpr int RW = 64, RH = 8 * RPW, TW = 60, TH = RH - 2;
+  static constexpr int AP = 16 / (int)sizeof(T), AZ = 4;
+  static constexpr int BXP = RW + AP, BXZ = RW + AZ;
+  static constexpr uint32_t ZB = RH * BXZ * 4;
+  static constexpr uint32_t PB = 3 * RH * BXP * sizeof(T);
+  static constexpr uint32_t ZB_AL = (ZB + 127) / 128 * 128, PB_AL = (PB + 127) / 128 * 128;
+  static constexpr int NS = NS_;
+  static constexpr uint32_t STAGE = ZB_AL + 2 * PB_AL;
+  static constexpr uint32_t SMEM = NS * STAGE + 128;
+};
+
+template <typename T, bool NONNEG, int RPW, int ZC, int NS_>
+__global__ void __launch_bounds__(256)
+fgp3d_tma2_kernel(const __grid_constant__ CUtensorMap tm_z, const __grid_constant__ CUtensorMap tm_p,
+                  const __grid_constant__ CUtensorMap tm_q, T* __restrict__ pn, int D, int H, int W, float lam,
+                  float inv_step, float beta) {
+  pdl_enter();
+  using L = ZmTma2<T, RPW, NS_>;
+  constexpr int NW = 8, NS = L::NS, RH = L::RH, TH = L::TH;
+  extern __shared__ unsigned char tma_dyn[];
+  __shared__ float2 sh_ry[2][NW][32];  // bottom row of r_y(k+1) of each warp block
+  __shared__ float2 sh_u[2][NW][32];   // top row of u(k+1) of each warp block
+  __shared__ __align__(8) uint64_t bar[NS];
+  __shared__ int s_abort;
+  unsigned char* const sbase = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(tma_dyn) + 127) & ~static_cast<uintptr_t>(127));
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int xr = blockIdx.x * L::TW - 2, yr = blockIdx.y * TH - 1;  // region origin (xr even)
+  const int xz = xr - ((xr % L::AZ) + L::AZ) % L::AZ;
+  const int xp = xr - ((xr % L::AP) + L::AP) % L::AP;
+  const int oz = xr - xz, op = xr - xp;  // both even: pairs stay aligned
+  const int gi0 = yr + warp * RPW;
+  const int gj = xr + 2 * lane;  // this lane's columns: gj, gj + 1
+  const int k0 = blockIdx.z * ZC;
+  const int k1 = min(k0 + ZC, D);
+  const int nplanes = k1 - k0 + 2;
+  const size_t HW = (size_t)H * W, n = (size_t)D * HW;
+  const bool mom = beta != 0.f;
+  const float2 beta2 = make_float2(beta, beta), lam2 = make_float2(lam, lam), inv2 = make_float2(inv_step, inv_step);
+  // Neumann multipliers of the in-plane divergence terms and the in-volume masks
+  const bool in_x = gj >= 0 && gj < W, in_y = gj + 1 >= 0 && gj + 1 < W;
+  const float2 m_rt = make_float2(gj < W - 1 ? 1.f : 0.f, gj + 1 < W - 1 ? 1.f : 0.f);
+  const float2 m_lf = make_float2(gj > 0 ? -1.f : 0.f, gj + 1 > 0 ? -1.f : 0.f);
+  const bool rt_x = gj < W - 1, rt_y = gj + 1 < W - 1;
+  bool row_in[RPW], row_dn[RPW];
+  float2 m_dn[RPW], m_up[RPW];
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) {
+    const int gi = gi0 + r;
+    row_in[r] = gi >= 0 && gi < H;
+    row_dn[r] = gi < H - 1;
+    m_dn[r] = row_dn[r] ? make_float2(1.f, 1.f) : make_float2(0.f, 0.f);
+    m_up[r] = gi > 0 ? make_float2(-1.f, -1.f) : make_float2(0.f, 0.f);
+  }
+  auto zs = [&](int st) { return reinterpret_cast<const float*>(sbase + st * L::STAGE); };
+  auto ps = [&](int st) { return reinterpret_cast<const T*>(sbase + st * L::STAGE + L::ZB_AL); };
+  auto qs = [&](int st) { return reinterpret_cast<const T*>(sbase + st * L::STAGE + L::ZB_AL + L::PB_AL); };
+
+  int issued_end = 0;
+  int first_pending = -1;
+  auto issue = [&](int j) {
+    const int k = k0 - 1 + j;
+    if (j >= nplanes) return;
+    issued_end = j + 1;
+    if (k < 0 || k >= D) return;
+    const int st = j % NS;
+    const bool wz = j > 0;
+    unsigned char* stage = sbase + st * L::STAGE;
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&bar[st], (wz ? L::ZB : 0u) + L::PB + (mom ? L::PB : 0u));
+    if (wz) tma_load_3d(stage, &tm_z, xz, yr, k, &bar[st]);
+    tma_load_4d(stage + L::ZB_AL, &tm_p, xp, yr, k, 0, &bar[st]);
+    if (mom) tma_load_4d(stage + L::ZB_AL + L::PB_AL, &tm_q, xp, yr, k, 0, &bar[st]);
+  };
+
+  uint32_t ph = 0;
+  auto take = [&](int j, float2 (&rz)[RPW], float2 (&ry)[RPW], float2 (&rx)[RPW], float2 (&zz)[RPW],
+                  bool need_all) {
+    const int k = k0 - 1 + j;
+    const bool in = k >= 0 && k < D;
+    const int st = j % NS;
+    if (in) {
+      if (mbar_wait_bounded(&bar[st], (ph >> st) & 1u, &g_tma_wait_timeouts)) {
+        ph ^= 1u << st;
+      } else {
+        s_abort = 1;
+        if (first_pending < 0) first_pending = j;
+      }
+    }
+    const T* P = ps(st);
+    const T* Q = qs(st);
+    const float* Z = zs(st);
+    const float2 zero = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+      const int cell = (warp * RPW + r) * L::BXP + 2 * lane + op;
+      float2 a0 = zero, a1 = zero, a2 = zero, zv = zero;
+      if (in) {
+        const float2 c0 = Pair<T>::ld(P + cell);
+        a0 = mom ? __ffma2_rn(beta2, f2_sub(c0, Pair<T>::ld(Q + cell)), c0) : c0;
+        if (need_all) {
+          const float2 c1 = Pair<T>::ld(P + RH * L::BXP + cell), c2 = Pair<T>::ld(P + 2 * RH * L::BXP + cell);
+          if (mom) {
+            a1 = __ffma2_rn(beta2, f2_sub(c1, Pair<T>::ld(Q + RH * L::BXP + cell)), c1);
+            a2 = __ffma2_rn(beta2, f2_sub(c2, Pair<T>::ld(Q + 2 * RH * L::BXP + cell)), c2);
+          } else {
+            a1 = c1;
+            a2 = c2;
+          }
+          zv = *reinterpret_cast<const float2*>(Z + (warp * RPW + r) * L::BXZ + 2 * lane + oz);
+        }
+      }
+      rz[r] = a0;
+      ry[r] = a1;
+      rx[r] = a2;
+      zz[r] = zv;
+    }
+  };
+  // u at plane k (the fixed order of the file header, as paired FMAs whose
+  // multipliers are +-1 where a term is kept and 0 where it is not)
+  auto form_u = [&](int k, const float2 (&rz)[RPW], const float2 (&ry)[RPW], const float2 (&rx)[RPW],
+                    const float2 (&rzm)[RPW], const float2 (&zz)[RPW], float2 ry_above, float2 (&u)[RPW]) {
+    const float2 m_zf = k < D - 1 ? make_float2(1.f, 1.f) : make_float2(0.f, 0.f);
+    const float2 m_zb = k > 0 ? make_float2(-1.f, -1.f) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+      const float rx_left = __shfl_up_sync(0xffffffffu, rx[r].y, 1);
+      const float2 up = r > 0 ? ry[r - 1] : ry_above;
+      const float2 lf = make_float2(rx_left, rx[r].x);
+      float2 dv = __ffma2_rn(m_zf, rz[r], make_float2(0.f, 0.f));
+      dv = __ffma2_rn(m_zb, rzm[r], dv);
+      dv = __ffma2_rn(m_dn[r], ry[r], dv);
+      dv = __ffma2_rn(m_up[r], up, dv);
+      dv = __ffma2_rn(m_rt, rx[r], dv);
+      dv = __ffma2_rn(m_lf, lf, dv);
+      float2 v = __ffma2_rn(lam2, dv, zz[r]);
+      if (NONNEG) v = make_float2(fmaxf(v.x, 0.f), fmaxf(v.y, 0.f));
+      const bool ok = k < D && row_in[r];
+      u[r] = make_float2(ok && in_x ? v.x : 0.f, ok && in_y ? v.y : 0.f);
+    }
+  };
+
+  if (tid == 0) {
+    for (int st = 0; st < NS; ++st) mbar_init(&bar[st], 1);
+    s_abort = 0;
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    issue(0);
+    issue(1);
+  }
+  float2 Rz[RPW], Ry[RPW], Rx[RPW], Rzm[RPW], Uk[RPW], Zt[RPW], Dy[RPW], Dx[RPW];
+  take(0, Rzm, Dy, Dx, Zt, false);
+  take(1, Rz, Ry, Rx, Zt, true);
+  int buf = 0;
+  sh_ry[buf][warp][lane] = Ry[RPW - 1];
+  __syncthreads();
+  bool aborted = s_abort != 0;
+  if (tid == 0 && !aborted)
+    for (int j = 2; j < 2 + NS; ++j) issue(j);
+  form_u(k0, Rz, Ry, Rx, Rzm, Zt, warp > 0 ? sh_ry[buf][warp - 1][lane] : make_float2(0.f, 0.f), Uk);
+  sh_u[buf][warp][lane] = Uk[0];
+  int consumed = 2;
+  for (int k = k0; k < k1 && !aborted; ++k) {
+    const int j = k - k0 + 2;
+    float2 Rz1[RPW], Ry1[RPW], Rx1[RPW], U1[RPW];
+    take(j, Rz1, Ry1, Rx1, Zt, true);
+    consumed = j + 1;
+    const int nb = buf ^ 1;
+    sh_ry[nb][warp][lane] = Ry1[RPW - 1];
+    __syncthreads();
+    aborted = s_abort != 0;
+    if (aborted) break;
+    if (tid == 0) issue(j + NS);
+    const float2 above = warp > 0 ? sh_ry[nb][warp - 1][lane] : make_float2(0.f, 0.f);
+    const float2 below_u = warp < NW - 1 ? sh_u[buf][warp + 1][lane] : make_float2(0.f, 0.f);
+    form_u(k + 1, Rz1, Ry1, Rx1, Rz, Zt, above, U1);
+    sh_u[nb][warp][lane] = U1[0];
+    // p_{k+1} at plane k
+    const bool zf = k < D - 1;
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+      const float u_right = __shfl_down_sync(0xffffffffu, Uk[r].x, 1);
+      const int a = warp * RPW + r;
+      const float2 uc = Uk[r];
+      const float2 dn = r < RPW - 1 ? Uk[r + 1] : below_u;
+      const float2 rt = make_float2(uc.y, u_right);
+      const float2 d0 = f2_sub(U1[r], uc), d1 = f2_sub(dn, uc), d2 = f2_sub(rt, uc);
+      const float2 g0 = zf ? d0 : make_float2(0.f, 0.f);
+      const float2 g1 = row_dn[r] ? d1 : make_float2(0.f, 0.f);
+      const float2 g2 = make_float2(rt_x ? d2.x : 0.f, rt_y ? d2.y : 0.f);
+      const float2 q0 = __ffma2_rn(inv2, g0, Rz[r]);
+      const float2 q1 = __ffma2_rn(inv2, g1, Ry[r]);
+      const float2 q2 = __ffma2_rn(inv2, g2, Rx[r]);
+      const float2 nrm2 = __ffma2_rn(q2, q2, __ffma2_rn(q1, q1, __fmul2_rn(q0, q0)));
+      const float2 sc = make_float2(nrm2.x > 1.f ? rsqrtf(nrm2.x) : 1.f, nrm2.y > 1.f ? rsqrtf(nrm2.y) : 1.f);
+      // outputs: region columns 2 .. 61 (lanes 1 .. 30, whole pairs) and rows 1 .. TH
+      if (lane >= 1 && lane <= 30 && a >= 1 && a <= TH && row_in[r] && in_x) {
+        const size_t o = (size_t)k * HW + (size_t)(gi0 + r) * W + gj;
+        Elem<T>::st2(pn + o, __fmul2_rn(q0, sc));
+        Elem<T>::st2(pn + n + o, __fmul2_rn(q1, sc));
+        Elem<T>::st2(pn + 2 * n + o, __fmul2_rn(q2, sc));
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+      Rzm[r] = Rz[r];
+      Rz[r] = Rz1[r];
+      Ry[r] = Ry1[r];
+      Rx[r] = Rx1[r];
+      Uk[r] = U1[r];
+    }
+    buf = nb;
+  }
+  if (aborted && tid == 0) {
+    for (int j = consumed - 1; j < issued_end; ++j) {
+      const int jj = j < consumed ? first_pending : j;
       const int k = k0 - 1 + jj;
       if (jj < 0 || k < 0 || k >= D) continue;
       const int st = jj % NS;
@@ -645,22 +918,68 @@ cudaError_t fgp3d_tma_launch(const Dims& d, const float* z, const void* pc, cons
   return cudaGetLastError();
 }
 
+// The packed TMA variant (two columns per lane); *used as for fgp3d_tma_launch.
+template <typename T, bool NN, int RPW, int ZC, int NS>
+cudaError_t fgp3d_tma2_launch(const Dims& d, const float* z, const void* pc, const void* pp, void* pn, float lam,
+                              float inv_step, float beta, cudaStream_t s, bool* used) {
+  using L = ZmTma2<T, RPW, NS>;
+  *used = false;
+  if constexpr (L::SMEM + 2u * 2u * 8u * 32u * 8u + 64u > 227u * 1024u) return cudaSuccess;
+  static const cudaError_t attr = [] {
+    auto k = fgp3d_tma2_kernel<T, NN, RPW, ZC, NS>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    return e;
+  }();
+  if (attr != cudaSuccess) return attr;
+  const uint64_t es = sizeof(T), nx = d.nx, ny = d.ny, nz = d.nz;
+  if (!pp) pp = pc;
+  if (((uintptr_t)z | (uintptr_t)pc | (uintptr_t)pp | (uintptr_t)pn) & 15) return cudaSuccess;
+  if ((nx * 4) % 16 || (nx * es) % 16) return cudaSuccess;  // also makes every row start even
+  CUtensorMap mz, mp, mq;
+  const uint64_t dz[3] = {nx, ny, nz}, sz[2] = {nx * 4, nx * ny * 4};
+  const uint32_t bz[3] = {(uint32_t)L::BXZ, (uint32_t)L::RH, 1};
+  const uint64_t dp[4] = {nx, ny, nz, 3}, sp[3] = {nx * es, nx * ny * es, nx * ny * nz * es};
+  const uint32_t bp[4] = {(uint32_t)L::BXP, (uint32_t)L::RH, 1, 3};
+  const CUtensorMapDataType tp = es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+  if (!encode_tensor_map(&mz, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, z, dz, sz, bz) ||
+      !encode_tensor_map(&mp, tp, 4, pc, dp, sp, bp) || !encode_tensor_map(&mq, tp, 4, pp, dp, sp, bp))
+    return cudaSuccess;
+  dim3 grid((d.nx + L::TW - 1) / L::TW, (d.ny + L::TH - 1) / L::TH, (d.nz + ZC - 1) / ZC);
+  launch_kernel(fgp3d_tma2_kernel<T, NN, RPW, ZC, NS>, grid, dim3(256), (size_t)L::SMEM, s, mz, mp, mq, (T*)pn,
+                d.nz, d.ny, d.nx, lam, inv_step, beta);
+  g_tma_launched.store(true, std::memory_order_relaxed);
+  *used = true;
+  return cudaGetLastError();
+}
+
 struct ZmCfg {
   int cpl = 0, rpw = 0, zc = 0;
 };
-// Defaults: the fastest variant measured at 512^3 for each dual width (FP32,
-// register loads: 1,2,64; 16-bit, TMA staging: 2,2,32); TVS_FGP3D_CFG overrides
-// both.  The environment is read at every launch (and so fixed in a captured
-// graph), so that a process can compare the variants one after another.
-ZmCfg fgp3d_zm_cfg(bool half_dual) {
+// Defaults: the fastest variant measured at 512^3 -- with TMA staging two
+// columns and four rows per lane in packed arithmetic, 32 planes per chunk, for
+// every dual type (FP32 840 us, BF16 515 us, Q15 638 us per iteration); with
+// register loads (the fallback where TMA's alignment rules fail) one column and
+// two rows, 64 planes, for FP32 and two columns for the 16-bit types.
+// TVS_FGP3D_CFG overrides them.  The environment is read at every launch (and
+// so fixed in a captured graph), so that a process can compare the variants one
+// after another.
+ZmCfg fgp3d_zm_cfg(bool half_dual, bool tma) {
   if (const char* e = getenv("TVS_FGP3D_CFG")) {
     ZmCfg t;
     if (sscanf(e, "%d,%d,%d", &t.cpl, &t.rpw, &t.zc) == 3 && t.cpl > 0) return t;
   }
   ZmCfg c;
-  c.cpl = half_dual ? 2 : 1;
-  c.rpw = 2;
-  c.zc = half_dual ? 32 : 64;
+  if (tma) {
+    c.cpl = 2;
+    c.rpw = 4;
+    c.zc = 32;
+  } else {
+    c.cpl = half_dual ? 2 : 1;
+    c.rpw = 2;
+    c.zc = half_dual ? 32 : 64;
+  }
   return c;
 }
 
@@ -683,22 +1002,38 @@ Fgp3dKind fgp3d_kind_env() {
   return Fgp3dKind::Auto;
 }
 
+// With tma, the TMA variant of the configuration (packed where it has two
+// columns per lane); where TMA's alignment rules fail, or without tma, the
+// register-load variant of the register-load configuration.
 template <typename T, bool NN>
 cudaError_t fgp3d_zm_dispatch(const Dims& d, const float* z, const void* pc, const void* pp, void* pn, float lam,
                               float inv_step, float beta, bool tma, cudaStream_t s) {
-  const ZmCfg c = fgp3d_zm_cfg(sizeof(T) == 2);
-  bool used = false;
-#define TVS_ZM(C_, R_, Z_)                                                                                \
-  if (c.cpl == C_ && c.rpw == R_ && c.zc == Z_) {                                                        \
-    if (tma) {                                                                                           \
-      const cudaError_t e =                                                                              \
-          fgp3d_tma_stages() == 3                                                                        \
-              ? fgp3d_tma_launch<T, NN, C_, R_, Z_, 3>(d, z, pc, pp, pn, lam, inv_step, beta, s, &used)  \
-              : fgp3d_tma_launch<T, NN, C_, R_, Z_, 2>(d, z, pc, pp, pn, lam, inv_step, beta, s, &used); \
-      if (e != cudaSuccess || used) return e;                                                            \
-    }                                                                                                    \
-    return fgp3d_zm_launch<T, NN, C_, R_, Z_>(d, z, pc, pp, pn, lam, inv_step, beta, s);                  \
+  if (tma) {
+    const ZmCfg c = fgp3d_zm_cfg(sizeof(T) == 2, true);
+    const bool three = fgp3d_tma_stages() == 3;
+    bool used = false;
+    cudaError_t e = cudaSuccess;
+#define TVS_TMA(C_, R_, Z_)                                                                                    \
+  if (c.cpl == C_ && c.rpw == R_ && c.zc == Z_) {                                                             \
+    if constexpr (C_ == 2)                                                                                    \
+      e = three ? fgp3d_tma2_launch<T, NN, R_, Z_, 3>(d, z, pc, pp, pn, lam, inv_step, beta, s, &used)        \
+                : fgp3d_tma2_launch<T, NN, R_, Z_, 2>(d, z, pc, pp, pn, lam, inv_step, beta, s, &used);       \
+    else                                                                                                      \
+      e = three ? fgp3d_tma_launch<T, NN, C_, R_, Z_, 3>(d, z, pc, pp, pn, lam, inv_step, beta, s, &used)     \
+                : fgp3d_tma_launch<T, NN, C_, R_, Z_, 2>(d, z, pc, pp, pn, lam, inv_step, beta, s, &used);    \
+    if (e != cudaSuccess || used) return e;                                                                   \
   }
+    TVS_TMA(1, 2, 64)
+    TVS_TMA(1, 4, 64)
+    TVS_TMA(2, 2, 64)
+    TVS_TMA(1, 2, 32)
+    TVS_TMA(2, 2, 32)
+    TVS_TMA(2, 4, 32)
+#undef TVS_TMA
+  }
+  const ZmCfg c = fgp3d_zm_cfg(sizeof(T) == 2, false);
+#define TVS_ZM(C_, R_, Z_) \
+  if (c.cpl == C_ && c.rpw == R_ && c.zc == Z_) return fgp3d_zm_launch<T, NN, C_, R_, Z_>(d, z, pc, pp, pn, lam, inv_step, beta, s);
   TVS_ZM(1, 2, 64)
   TVS_ZM(1, 4, 64)
   TVS_ZM(2, 2, 64)
@@ -714,13 +1049,12 @@ cudaError_t fgp3d_iter_t(const Dims& d, const float* z, const void* pc, const vo
                          float lam, float inv_step, float beta, cudaStream_t s) {
   Fgp3dKind kind = fgp3d_kind_env();
   if (kind == Fgp3dKind::Auto) {
-    // z-marching needs enough (x-y tile, z chunk) pairs to fill the GPU.  With a
-    // 16-bit dual the TMA-staged kernel is the faster (512^3, BF16: 906 -> 650
-    // us per iteration; Q15: 950 -> 737 us); with an FP32 dual the kernel with
-    // register loads and its prefetch of the next plane (950 us) is at least as
-    // fast as every TMA variant measured (944 - 1415 us).
+    // z-marching needs enough (x-y tile, z chunk) pairs to fill the GPU; there
+    // the TMA-staged packed kernel is the faster for every dual type (512^3,
+    // per iteration: FP32 953 -> 840 us, BF16 906 -> 515 us, Q15 950 -> 638 us
+    // against register loads)
     const bool big = (long long)((d.nx + 29) / 30) * ((d.ny + 13) / 14) * ((d.nz + 63) / 64) >= 4 * 152;
-    kind = !big ? Fgp3dKind::Tile : (sizeof(T) == 2 ? Fgp3dKind::Tma : Fgp3dKind::Zm);
+    kind = big ? Fgp3dKind::Tma : Fgp3dKind::Tile;
   }
   if (kind != Fgp3dKind::Tile)
     return fgp3d_zm_dispatch<T, NN>(d, z, pc, pp, pn, lam, inv_step, beta, kind == Fgp3dKind::Tma, s);
