@@ -115,6 +115,7 @@ struct tvs_ctx {
   };
   std::vector<Tuned> tuned;  // autotuner cache, one entry per 2D shape and dual type
   std::vector<tvs_problem*> problems;  // live problems, destroyed with the context
+  struct BatchCache* batch = nullptr;  // set-up and graphs of the last batched solve
 };
 
 struct tvs_problem {
@@ -1229,41 +1230,66 @@ struct BatchScratch {
   }
 };
 
+
+bool same_fb_params(const tvs_fb_params& a, const tvs_fb_params& b) {
+  return a.gamma == b.gamma && a.p == b.p && a.seed == b.seed && a.max_iter == b.max_iter &&
+         a.n_inner == b.n_inner && a.dual == b.dual && a.f_star == b.f_star &&
+         a.target_rel_gap == b.target_rel_gap && a.objective_every == b.objective_every && a.resume == b.resume &&
+         a.k0 == b.k0 && a.target_rel_dist == b.target_rel_dist;
+}
+
 }  // namespace
 
-extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const* probs,
-                                           const tvs_fb_params* prm, float* const* x_io, tvs_mem mem,
-                                           tvs_trace* traces) {
-  if (!C || n < 1 || !probs || !prm || !x_io) return fail(TVS_EINVAL, "null argument or n < 1");
-  if (mem != TVS_MEM_DEVICE && mem != TVS_MEM_HOST) return fail(TVS_EINVAL, "invalid mem kind");
-  const int K = prm[0].max_iter, N = prm[0].n_inner, dtype = prm[0].dual;
-  for (int i = 0; i < n; ++i) {
-    tvs_problem* P = probs[i];
-    if (!P || P->ctx != C) return fail(TVS_EINVAL, "problem %d is null or from another context", i);
-    if (!x_io[i]) return fail(TVS_EINVAL, "x_inout[%d] is null", i);
-    if (P->dims.ndim != 2 || P->desc.op.kind == TVS_OP_PARALLEL_BEAM)
-      return fail(TVS_EUNSUPPORTED, "batched solves take 2D identity or blur problems (problem %d)", i);
-    if (P->n >= ((size_t)1 << 31)) return fail(TVS_EUNSUPPORTED, "batched problems have fewer than 2^31 pixels");
-    TVS_TRY(check_common(P, prm[i].max_iter, prm[i].n_inner, prm[i].dual, prm[i].f_star,
-                         prm[i].target_rel_gap, prm[i].objective_every, x_io[i]));
-    if (prm[i].max_iter != K || prm[i].n_inner != N || prm[i].dual != dtype)
-      return fail(TVS_EINVAL, "max_iter, n_inner and dual must agree across the batch");
-    if (!(prm[i].gamma > 0) || !is_fin(prm[i].gamma)) return fail(TVS_EINVAL, "gamma must be > 0");
-    if (!(prm[i].p > 0.0 && prm[i].p <= 1.0)) return fail(TVS_EINVAL, "p must lie in (0, 1]");
-    if (prm[i].resume) return fail(TVS_EUNSUPPORTED, "batched solves do not resume");
-    for (int j = 0; j < i; ++j)
-      if (probs[j] == P) return fail(TVS_EINVAL, "problem %d appears twice", i);
-  }
-  int blur_radius = 0;
-  for (int i = 0; i < n; ++i)
-    if (probs[i]->desc.op.kind == TVS_OP_GAUSS_BLUR) {
-      if (blur_radius && probs[i]->bw.R != blur_radius)
-        return fail(TVS_EUNSUPPORTED, "blur problems of a batch must share the blur radius");
-      blur_radius = probs[i]->bw.R;
-    }
-  cudaStream_t s = C->stream;
+// The set-up of a batched solve -- descriptors, work lists, coins, scratch and
+// the two captured iteration graphs -- kept in the context for the next batched
+// solve of the same problems (same buffer generations), parameters and memory
+// kind, which then only resets the per-solve state.  Destroying any of its
+// problems, or the context, drops it.
+struct BatchCache {
+  std::vector<tvs_problem*> probs;
+  std::vector<unsigned long long> gens;
+  std::vector<tvs_fb_params> prm;
+  tvs_mem mem = TVS_MEM_DEVICE;
   BatchScratch S;
-  // per-problem state, descriptors and work lists
+  BatchLaunch L{};
+  GraphSet G;
+  std::vector<BatchState> st0;
+  std::vector<float> betas;  // L.betas points here
+  unsigned long long* t0_dev = nullptr;
+  double* obj_pack = nullptr;
+  unsigned long long* ts_pack = nullptr;
+  float** x_dev_list = nullptr;  // the caller's device iterates (set-up and trace kernels)
+  size_t rows = 0;
+  bool matches(int n, tvs_problem* const* P, const tvs_fb_params* p, tvs_mem m) const {
+    if ((int)probs.size() != n || m != mem) return false;
+    for (int i = 0; i < n; ++i)
+      if (probs[i] != P[i] || gens[i] != P[i]->gen || !same_fb_params(prm[i], p[i])) return false;
+    return true;
+  }
+  bool uses(const tvs_problem* P) const { return std::find(probs.begin(), probs.end(), P) != probs.end(); }
+};
+
+void drop_batch_cache(tvs_ctx* C) {
+  if (!C->batch) return;
+  cudaStreamSynchronize(C->stream);
+  delete C->batch;
+  C->batch = nullptr;
+}
+
+namespace {
+
+tvs_status build_batch(tvs_ctx* C, int n, tvs_problem* const* probs, const tvs_fb_params* prm, tvs_mem mem,
+                       int blur_radius, BatchCache* B) {
+  const int K = prm[0].max_iter, N = prm[0].n_inner, dtype = prm[0].dual;
+  cudaStream_t s = C->stream;
+  B->probs.assign(probs, probs + n);
+  B->gens.resize(n);
+  for (int i = 0; i < n; ++i) B->gens[i] = probs[i]->gen;
+  B->prm.assign(prm, prm + n);
+  B->mem = mem;
+  BatchScratch& S = B->S;
+  BatchLaunch& L = B->L;
+  // per-problem descriptors and work lists
   std::vector<BatchProb> desc(n);
   std::vector<int4> blur_tiles;
   std::vector<int2> ident_chunks, tile_range(n), chunk_range(n);
@@ -1271,9 +1297,6 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
   const int chunk = batch_chunk(), ftw = batch_fgp_tile_w(), fth = batch_fgp_tile_h();
   for (int i = 0; i < n; ++i) {
     tvs_problem* P = probs[i];
-    TVS_TRY(ensure_trace(P, K));
-    // host iterates are copied in here; device iterates by the set-up kernel below
-    if (mem == TVS_MEM_HOST) TVS_TRY(copy_in(P->x[0], x_io[i], P->n, mem, s));
     const int H = P->dims.ny, W = P->dims.nx;
     const double gamma = prm[i].gamma, p = prm[i].p, alpha = P->desc.alpha;
     BatchProb& D = desc[i];
@@ -1328,18 +1351,16 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
   const int n_blur = (int)blur_tiles.size();
   for (auto& D : desc)
     if (D.part_off < 0) D.part_off = n_blur + (-1 - D.part_off);
-  std::vector<BatchState> st0(n, BatchState{0, -1, 0, 0});
+  B->st0.assign(n, BatchState{0, -1, 0, 0});
   std::vector<unsigned long long> seeds(n);
   std::vector<double> pvals(n);
   for (int i = 0; i < n; ++i) {
     seeds[i] = prm[i].seed;
     pvals[i] = prm[i].p;
   }
-
-  BatchLaunch L{};
   L.n = n;
   TVS_TRY(S.upload(desc, (BatchProb**)&L.probs, s));
-  TVS_TRY(S.upload(st0, &L.state, s));
+  TVS_TRY(S.upload(B->st0, &L.state, s));
   TVS_TRY(S.upload(blur_tiles, (int4**)&L.blur_tiles, s));
   TVS_TRY(S.upload(ident_chunks, (int2**)&L.ident_chunks, s));
   {
@@ -1379,8 +1400,7 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
   TVS_TRY(S.zeros<int>((size_t)L.n_work, &L.work, s));
   TVS_TRY(S.zeros<Partial>((size_t)n_blur + ident_chunks.size(), &L.part_a, s));
   TVS_TRY(S.zeros<Partial>((size_t)n_blur + ident_chunks.size(), &L.part_b, s));
-  unsigned long long* t0_dev = nullptr;
-  TVS_TRY(S.zeros<unsigned long long>(1, &t0_dev, s));
+  TVS_TRY(S.zeros<unsigned long long>(1, &B->t0_dev, s));
   {
     cudaError_t e = cudaHostAlloc((void**)&S.done_host, sizeof(int) * n, cudaHostAllocMapped);
     if (e != cudaSuccess) {
@@ -1390,27 +1410,97 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
     memset(S.done_host, 0, sizeof(int) * n);
     CUDA_TRY(cudaHostGetDevicePointer((void**)&L.done_host, S.done_host, 0));
   }
-  const std::vector<float> betas = fgp_betas(N);
-  L.betas = betas.data();
+  B->betas = fgp_betas(N);
+  L.betas = B->betas.data();
   L.n_inner = N;
   L.dtype = dtype;
   L.blur_radius = blur_radius;
   L.use_prox = N > 0;
-  float** x_dev_list = nullptr;  // the caller's device iterates, for the set-up and trace kernels
-  if (mem == TVS_MEM_DEVICE) {
-    std::vector<float*> xs(x_io, x_io + n);
-    TVS_TRY(S.upload(xs, &x_dev_list, s));
-  }
-  CUDA_TRY(launch_batch_init(L, (const float* const*)x_dev_list, K, s));
-  CUDA_TRY(cudaEventRecord(C->ev_start, s));
-  CUDA_TRY(launch_timestamp(t0_dev, s));
-  GraphSet G;
+  if (mem == TVS_MEM_DEVICE) TVS_TRY(S.zeros<float*>((size_t)n, &B->x_dev_list, s));
+  B->rows = (size_t)n * (K > 0 ? K : 1);
+  TVS_TRY(S.zeros<double>(B->rows, &B->obj_pack, s));
+  TVS_TRY(S.zeros<unsigned long long>(B->rows, &B->ts_pack, s));
   for (int par = 0; par < 2; ++par) {
-    TVS_TRY(capture(s, &G.exec[1][par], [&]() -> tvs_status {
+    TVS_TRY(capture(s, &B->G.exec[1][par], [&]() -> tvs_status {
       CUDA_TRY(launch_batch_iteration(L, par, s));
       return TVS_OK;
     }));
   }
+  return TVS_OK;
+}
+
+}  // namespace
+
+extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const* probs,
+                                           const tvs_fb_params* prm, float* const* x_io, tvs_mem mem,
+                                           tvs_trace* traces) {
+  if (!C || n < 1 || !probs || !prm || !x_io) return fail(TVS_EINVAL, "null argument or n < 1");
+  if (mem != TVS_MEM_DEVICE && mem != TVS_MEM_HOST) return fail(TVS_EINVAL, "invalid mem kind");
+  const int K = prm[0].max_iter, N = prm[0].n_inner, dtype = prm[0].dual;
+  for (int i = 0; i < n; ++i) {
+    tvs_problem* P = probs[i];
+    if (!P || P->ctx != C) return fail(TVS_EINVAL, "problem %d is null or from another context", i);
+    if (!x_io[i]) return fail(TVS_EINVAL, "x_inout[%d] is null", i);
+    if (P->dims.ndim != 2 || P->desc.op.kind == TVS_OP_PARALLEL_BEAM)
+      return fail(TVS_EUNSUPPORTED, "batched solves take 2D identity or blur problems (problem %d)", i);
+    if (P->n >= ((size_t)1 << 31)) return fail(TVS_EUNSUPPORTED, "batched problems have fewer than 2^31 pixels");
+    TVS_TRY(check_common(P, prm[i].max_iter, prm[i].n_inner, prm[i].dual, prm[i].f_star,
+                         prm[i].target_rel_gap, prm[i].objective_every, x_io[i]));
+    if (prm[i].max_iter != K || prm[i].n_inner != N || prm[i].dual != dtype)
+      return fail(TVS_EINVAL, "max_iter, n_inner and dual must agree across the batch");
+    if (!(prm[i].gamma > 0) || !is_fin(prm[i].gamma)) return fail(TVS_EINVAL, "gamma must be > 0");
+    if (!(prm[i].p > 0.0 && prm[i].p <= 1.0)) return fail(TVS_EINVAL, "p must lie in (0, 1]");
+    if (prm[i].resume) return fail(TVS_EUNSUPPORTED, "batched solves do not resume");
+    for (int j = 0; j < i; ++j)
+      if (probs[j] == P) return fail(TVS_EINVAL, "problem %d appears twice", i);
+  }
+  int blur_radius = 0;
+  for (int i = 0; i < n; ++i)
+    if (probs[i]->desc.op.kind == TVS_OP_GAUSS_BLUR) {
+      if (blur_radius && probs[i]->bw.R != blur_radius)
+        return fail(TVS_EUNSUPPORTED, "blur problems of a batch must share the blur radius");
+      blur_radius = probs[i]->bw.R;
+    }
+  cudaStream_t s = C->stream;
+  for (int i = 0; i < n; ++i) TVS_TRY(ensure_trace(probs[i], K));
+  // A batch solved again with the same problems (same buffers), parameters and
+  // memory kind reuses the work lists, scratch and captured graphs of the last
+  // one: only the per-solve state is reset.
+  BatchCache* B = C->batch;
+  if (!B || !B->matches(n, probs, prm, mem)) {
+    drop_batch_cache(C);
+    std::unique_ptr<BatchCache> nb(new BatchCache);
+    TVS_TRY(build_batch(C, n, probs, prm, mem, blur_radius, nb.get()));
+    C->batch = nb.release();
+    B = C->batch;
+  }
+  BatchLaunch& L = B->L;
+  BatchScratch& S = B->S;
+  // per-solve state: iterates, counters, work lists of the iteration, records
+  for (int i = 0; i < n; ++i)
+    if (mem == TVS_MEM_HOST) TVS_TRY(copy_in(probs[i]->x[0], x_io[i], probs[i]->n, mem, s));
+  CUDA_TRY(cudaMemcpyAsync(L.state, B->st0.data(), sizeof(BatchState) * n, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemsetAsync(L.scan_tiles, 0, sizeof(int) * (n + 1), s));
+  CUDA_TRY(cudaMemsetAsync(L.scan_chunks, 0, sizeof(int) * (n + 1), s));
+  CUDA_TRY(cudaMemsetAsync(L.kctr, 0, sizeof(int), s));
+  CUDA_TRY(cudaMemsetAsync(L.work, 0, sizeof(int) * L.n_work, s));
+  const size_t nparts = (size_t)L.n_blur_tiles + L.n_ident_chunks;
+  if (nparts) {
+    CUDA_TRY(cudaMemsetAsync(L.part_a, 0, sizeof(Partial) * nparts, s));
+    CUDA_TRY(cudaMemsetAsync(L.part_b, 0, sizeof(Partial) * nparts, s));
+  }
+  CUDA_TRY(cudaMemsetAsync(B->t0_dev, 0, sizeof(unsigned long long), s));
+  CUDA_TRY(cudaMemsetAsync(B->obj_pack, 0, sizeof(double) * B->rows, s));
+  CUDA_TRY(cudaMemsetAsync(B->ts_pack, 0, sizeof(unsigned long long) * B->rows, s));
+  memset(S.done_host, 0, sizeof(int) * n);
+  if (mem == TVS_MEM_DEVICE) {
+    std::vector<float*> xs(x_io, x_io + n);
+    CUDA_TRY(cudaMemcpyAsync(B->x_dev_list, xs.data(), sizeof(float*) * n, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));  // xs is a local vector
+  }
+  CUDA_TRY(launch_batch_init(L, mem == TVS_MEM_DEVICE ? (const float* const*)B->x_dev_list : nullptr, K, s));
+  CUDA_TRY(cudaEventRecord(C->ev_start, s));
+  CUDA_TRY(launch_timestamp(B->t0_dev, s));
   int launched = 0;
   for (int k = 0; k < K; ++k) {
     if (k >= LAG) {
@@ -1419,7 +1509,7 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
       for (int i = 0; i < n; ++i) ndone += ((volatile int*)S.done_host)[i];
       if (ndone == n) break;
     }
-    CUDA_TRY(cudaGraphLaunch(G.exec[1][k & 1], s));
+    CUDA_TRY(cudaGraphLaunch(B->G.exec[1][k & 1], s));
     CUDA_TRY(cudaEventRecord(C->ring[k % LAG], s));
     launched = k + 1;
   }
@@ -1427,23 +1517,19 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
   CUDA_TRY(cudaEventRecord(C->ev_stop, s));
   // records of every problem packed on the device (and device results copied
   // out), then brought back in four copies
-  double* obj_pack = nullptr;
-  unsigned long long* ts_pack = nullptr;
-  const size_t rows = (size_t)n * (K > 0 ? K : 1);
-  TVS_TRY(S.zeros<double>(rows, &obj_pack, s));
-  TVS_TRY(S.zeros<unsigned long long>(rows, &ts_pack, s));
-  CUDA_TRY(launch_batch_trace(L, K, obj_pack, ts_pack, mem == TVS_MEM_DEVICE ? x_dev_list : nullptr, s));
+  const size_t rows = B->rows;
+  CUDA_TRY(launch_batch_trace(L, K, B->obj_pack, B->ts_pack, mem == TVS_MEM_DEVICE ? B->x_dev_list : nullptr, s));
   std::vector<BatchState> st(n);
   std::vector<double> obj_all(rows);
   std::vector<unsigned long long> ts_all(rows);
   std::vector<unsigned char> coins((size_t)K * n);
   unsigned long long t0 = 0;
   CUDA_TRY(cudaMemcpyAsync(st.data(), L.state, sizeof(BatchState) * n, cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaMemcpyAsync(obj_all.data(), obj_pack, sizeof(double) * rows, cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaMemcpyAsync(ts_all.data(), ts_pack, sizeof(unsigned long long) * rows, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(obj_all.data(), B->obj_pack, sizeof(double) * rows, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(ts_all.data(), B->ts_pack, sizeof(unsigned long long) * rows, cudaMemcpyDeviceToHost, s));
   if (!coins.empty())
     CUDA_TRY(cudaMemcpyAsync(coins.data(), L.coins, coins.size(), cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaMemcpyAsync(&t0, t0_dev, sizeof(t0), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(&t0, B->t0_dev, sizeof(t0), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   float solve_ms = 0.f;
   CUDA_TRY(cudaEventElapsedTime(&solve_ms, C->ev_start, C->ev_stop));
@@ -1730,6 +1816,7 @@ tvs_status tvs_destroy(tvs_ctx* C) {
   if (!C) return TVS_OK;
   cudaSetDevice(C->device);
   if (C->stream) cudaStreamSynchronize(C->stream);
+  drop_batch_cache(C);
   while (!C->problems.empty()) tvs_problem_destroy(C->problems.back());
   dfree(C->prox_scratch);
   dfree(C->red_out);
@@ -1896,6 +1983,7 @@ tvs_status tvs_problem_destroy(tvs_problem* P) {
   tvs_ctx* C = P->ctx;
   cudaSetDevice(C->device);
   cudaStreamSynchronize(C->stream);
+  if (C->batch && C->batch->uses(P)) drop_batch_cache(C);
   void* bufs[] = {P->b, P->x[0], P->x[1], P->z, P->h, P->r, P->y, P->axp, P->dual[0], P->dual[1],
                   P->dual[2], P->dual[3], P->part_a, P->part_b, P->obj_dev, P->ts_dev, P->fgp_ts, P->beta_dev,
                   P->flags, P->count, P->angle_tab, P->angle_tab2, P->xt, P->uref, P->part_c, P->dist_dev,

@@ -243,3 +243,56 @@ def test_batch_many_problems_uses_global_scan(tvs, ctx):
     for p in probs:
         p.close()
     torch.cuda.synchronize()
+
+
+def test_batch_setup_reused_and_rebuilt(tvs):
+    """A repeated batched solve (same problems and parameters) replays the kept
+    set-up and graphs and gives the same bits; a changed parameter, a different
+    memory kind or a destroyed problem makes it build a new set-up, whose result
+    equals a solve in a fresh context."""
+    import torch
+    K, N = 15, 8
+    ctx = tvs.Context(0)
+    try:
+        probs, xs0, data = _build(tvs, ctx)
+        gam = [1.0] * len(SPECS)
+        ps = [s[4] for s in SPECS]
+        seeds = [s[5] for s in SPECS]
+
+        def run(ps_, dev=True):
+            xs = [x.clone() for x in xs0] if dev else [np.ascontiguousarray(host(x), dtype=np.float32) for x in xs0]
+            out, trs = tvs.proxskip_solve_batch(ctx, probs, xs, gam, ps_, seeds, K, N)
+            return [host(x) if dev else x for x in out], [list(t.objective) for t in trs]
+
+        a_x, a_obj = run(ps)
+        b_x, b_obj = run(ps)
+        for u, v in zip(a_x, b_x):
+            np.testing.assert_array_equal(u, v)
+        assert a_obj == b_obj
+        h_x, _ = run(ps, dev=False)
+        for u, v in zip(a_x, h_x):
+            np.testing.assert_array_equal(u, v)
+        ps2 = list(ps)
+        ps2[2] = 0.6
+        c_x, c_obj = run(ps2)
+        fresh = tvs.Context(0)
+        try:
+            fprobs = [tvs.Problem(fresh, cuda(data[k][0]), s[3], op=s[2], blur_sigma=s[6])
+                      for k, s in enumerate(SPECS)]
+            fx = [x.clone() for x in xs0]
+            f_out, f_trs = tvs.proxskip_solve_batch(fresh, fprobs, fx, gam, ps2, seeds, K, N)
+            for u, v in zip(c_x, f_out):
+                np.testing.assert_array_equal(u, host(v))
+            assert c_obj == [list(t.objective) for t in f_trs]
+        finally:
+            fresh.close()
+        # a destroyed problem drops the kept set-up; a batch of new problems still solves
+        probs[0].close()
+        probs[0] = tvs.Problem(ctx, cuda(data[0][0]), SPECS[0][3], op=SPECS[0][2], blur_sigma=SPECS[0][6])
+        d_x, d_obj = run(ps)
+        for u, v in zip(a_x, d_x):
+            np.testing.assert_array_equal(u, v)
+        assert d_obj == a_obj
+        torch.cuda.synchronize()
+    finally:
+        ctx.close()
