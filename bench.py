@@ -58,10 +58,10 @@ FGP_TRAFFIC = {"config": [4, 2, 104], "bytes": 20388825,
 # 3D: per momentum launch of the default kernel, captured on a 320^3 volume
 # (inputs larger than L2) and scaled by the voxel count to 512^3.
 _FGP3_SRC = {"sources": ["common.cuh", "tma.cuh", "fgp3d.cu"],
-             "sha256": "a1b97d35a7dc4796545baeae0ae49d0b26052b4aada2ef1e28d868c9e88d94de"}
-FGP3_TRAFFIC = {"f32": dict(_FGP3_SRC, bytes=5401626018),
-                "bf16": dict(_FGP3_SRC, bytes=2957804306),
-                "q15": dict(_FGP3_SRC, bytes=2959729492)}
+             "sha256": "cf831402f604485ec8c42bd514da6902281b4a93b3b78c8ce0754a2e0158cbbf"}
+FGP3_TRAFFIC = {"f32": dict(_FGP3_SRC, bytes=5397339439),
+                "bf16": dict(_FGP3_SRC, bytes=2951982612),
+                "q15": dict(_FGP3_SRC, bytes=2961351639)}
 # Iterations this workload's ProxSkip solve needs to reach the target on the GPU
 # (its trace: 261 iterations); the reference arm extrapolates the oracle to them,
 # counting the prox calls among them from the coin schedule.
@@ -360,9 +360,11 @@ def extra_batch(tvs, ctx, stream, rank, world):
 
 def extra_ct(tvs, ctx, stream):
     """ct2d_512: 512^2 phantom, 720 angles x 725 bins, Poisson counts, alpha 0.5.
-    PDHG against PDHGSkip-2 and PDHGSkip-1 (p 0.2, 0.05), time to the 1e-4 gap with
-    F* from a long PDHG run on the same GPU, at sigma = tau / 4 (sigma tau ||A||^2 =
-    0.98) with 200 inner iterations; and the projector pair's time."""
+    PDHG against PDHGSkip-2 (p 0.7, 0.5, 0.2) and PDHGSkip-1 (p 0.7, 0.2), time to
+    the 1e-4 gap with F* from a long PDHG run on the same GPU, at the step sizes
+    and inner iteration count where PDHG is fastest in a sweep of sigma/tau in
+    {1, 1/2, 1/4, 1/16} and 100 / 200 / 500 inner iterations (sigma = tau,
+    sigma tau ||A||^2 = 0.98, 200 inner); and the projector pair's time."""
     import torch
     from synth.configs import CTConfig
     cfg = CTConfig()
@@ -397,19 +399,20 @@ def extra_ct(tvs, ctx, stream):
     _, t_fwd = _timed_once(stream, lambda: tvs.tvs_op_apply(prob, x0, y))
     _, t_bwd = _timed_once(stream, lambda: tvs.tvs_op_apply(prob, y, z, adjoint=True))
     st = 0.99 / math.sqrt(L)
-    sg, ta = st * 0.5, st * 2.0
+    sg = ta = st
     _, _, ref = tvs.pdhg_solve(prob, x0.clone(), zeros_sino.clone(), st, st, 4000, 100)
     f_star = float(np.nanmin(ref.objective))
     runs = {"pdhg": lambda: tvs.pdhg_solve(prob, x0.clone(), zeros_sino.clone(), sg, ta, cfg.max_iter, 200,
                                            f_star=f_star, target=TARGET)}
-    for p in cfg.ps:
+    for p in (0.7, 0.5, 0.2):
         runs[f"pdhgskip2_p{p}"] = (lambda p=p: tvs.pdhgskip_solve(
             prob, x0.clone(), zeros_sino.clone(), sg, ta, p, cfg.seed, cfg.max_iter, 200, f_star=f_star,
             target=TARGET))
+    for p in (0.7, 0.2):
         runs[f"pdhgskip1_p{p}"] = (lambda p=p: tvs.pdhgskip1_solve(
             prob, x0.clone(), zeros_sino.clone(), sg, ta, p, cfg.seed, cfg.max_iter, 200, f_star=f_star,
             target=TARGET))
-    out = {"workload": "ct2d_512: 512^2, 720 angles, 725 bins, 1e4 photons, alpha 0.5; sigma = tau/4 "
+    out = {"workload": "ct2d_512: 512^2, 720 angles, 725 bins, 1e4 photons, alpha 0.5; sigma = tau "
                        "(sigma tau ||A||^2 = 0.98), 200 inner iterations",
            "norm_A_sq": L, "f_star": f_star, "f_star_from": "PDHG, 4000 iterations, 100 inner, same GPU",
            "projector_us": t_fwd * 1e6, "backprojector_us": t_bwd * 1e6}

@@ -613,24 +613,46 @@ fgp3d_tma_kernel(const __grid_constant__ CUtensorMap tm_z, const __grid_constant
 // columns left of its first output column: 64 columns give 60 outputs.
 __device__ __forceinline__ float2 f2_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 
-template <typename T> struct Pair;
+// Two adjacent stored values (the first at an even index) to / from a float2:
+// ld reads shared memory, st writes global memory; each gives the values and
+// the bits of the scalar Elem<T> operations.
+template <typename T> struct Pair {
+  static __device__ __forceinline__ void st(T* p, float2 v) { Elem<T>::st2(p, v); }
+};
 template <> struct Pair<float> {
   static __device__ __forceinline__ float2 ld(const float* p) { return *reinterpret_cast<const float2*>(p); }
+  static __device__ __forceinline__ void st(float* p, float2 v) { Elem<float>::st2(p, v); }
 };
 template <> struct Pair<__nv_bfloat16> {
   static __device__ __forceinline__ float2 ld(const __nv_bfloat16* p) {
     return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
   }
+  static __device__ __forceinline__ void st(__nv_bfloat16* p, float2 v) { Elem<__nv_bfloat16>::st2(p, v); }
 };
 template <> struct Pair<__half> {
   static __device__ __forceinline__ float2 ld(const __half* p) {
     return __half22float2(*reinterpret_cast<const __half2*>(p));
   }
+  static __device__ __forceinline__ void st(__half* p, float2 v) { Elem<__half>::st2(p, v); }
 };
+// q15: a code c is decoded as ((M + c) - M) * (1/32767) with M = 1.5 * 2^23,
+// whose bit pattern is 0x4B400000 + c; the subtraction and the scaling of the
+// pair run as one paired ADD and one paired MUL.  A store forms M + 32767 v by
+// one paired FMA and keeps the low 16 bits of each result's bit pattern, which
+// are the code (0x4B400000 has none set).
 template <> struct Pair<q15> {
   static __device__ __forceinline__ float2 ld(const q15* p) {
-    const short2 v = *reinterpret_cast<const short2*>(p);
-    return make_float2(Elem<q15>::cvt(q15{v.x}), Elem<q15>::cvt(q15{v.y}));
+    const unsigned w = *reinterpret_cast<const unsigned*>(p);
+    const int lo = (int)(short)(w & 0xffffu), hi = (int)w >> 16;
+    const float2 m = make_float2(__int_as_float(Elem<q15>::kMagicBits + lo), __int_as_float(Elem<q15>::kMagicBits + hi));
+    return __fmul2_rn(__fadd2_rn(m, make_float2(-Elem<q15>::kMagic, -Elem<q15>::kMagic)),
+                      make_float2(Elem<q15>::kInv, Elem<q15>::kInv));
+  }
+  static __device__ __forceinline__ void st(q15* p, float2 v) {
+    const float2 c = make_float2(fminf(fmaxf(v.x, -1.f), 1.f), fminf(fmaxf(v.y, -1.f), 1.f));
+    const float2 m = __ffma2_rn(c, make_float2(Elem<q15>::kScale, Elem<q15>::kScale),
+                                make_float2(Elem<q15>::kMagic, Elem<q15>::kMagic));
+    *reinterpret_cast<unsigned*>(p) = __byte_perm(__float_as_uint(m.x), __float_as_uint(m.y), 0x5410);
   }
 };
 
@@ -836,9 +858,9 @@ fgp3d_tma2_kernel(const __grid_constant__ CUtensorMap tm_z, const __grid_constan
       // outputs: region columns 2 .. 61 (lanes 1 .. 30, whole pairs) and rows 1 .. TH
       if (lane >= 1 && lane <= 30 && a >= 1 && a <= TH && row_in[r] && in_x) {
         const size_t o = (size_t)k * HW + (size_t)(gi0 + r) * W + gj;
-        Elem<T>::st2(pn + o, __fmul2_rn(q0, sc));
-        Elem<T>::st2(pn + n + o, __fmul2_rn(q1, sc));
-        Elem<T>::st2(pn + 2 * n + o, __fmul2_rn(q2, sc));
+        Pair<T>::st(pn + o, __fmul2_rn(q0, sc));
+        Pair<T>::st(pn + n + o, __fmul2_rn(q1, sc));
+        Pair<T>::st(pn + 2 * n + o, __fmul2_rn(q2, sc));
       }
     }
 #pragma unroll
