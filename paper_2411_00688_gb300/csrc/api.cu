@@ -1333,7 +1333,7 @@ tvs_status build_batch(tvs_ctx* C, int n, tvs_problem* const* probs, const tvs_f
     if (P->desc.op.kind == TVS_OP_GAUSS_BLUR) {
       D.part_off = (int)blur_tiles.size();
       const int fx = fb_step_tile_w(P->bw.R);  // tiles of the fused blur step
-      const int tx = (W + fx - 1) / fx, ty = (H + fb_step_tile_h() - 1) / fb_step_tile_h();
+      const int tx = (W + fx - 1) / fx, ty = (H + fb_step_tile_h(P->bw.R) - 1) / fb_step_tile_h(P->bw.R);
       for (int y = 0; y < ty; ++y)
         for (int x = 0; x < tx; ++x) blur_tiles.push_back(make_int4(i, x, y, 0));
       D.part_n = tx * ty;

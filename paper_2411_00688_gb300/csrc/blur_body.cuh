@@ -109,9 +109,13 @@ __device__ __forceinline__ void blur_tile_body(const float* __restrict__ src, in
 // Layout: every lane owns two adjacent columns (one float2) in every pass, so a
 // tap is one packed FP32x2 FMA and a horizontal pass reads R + 1 float2 per two
 // outputs; the staged region is 64 columns wide, the tile fb_tile_w(R) =
-// 64 - 4R columns by FY rows.
-constexpr int FY = 32, FNT = 256;
+// 64 - 4R columns by fb_tile_h(R) rows: 40 rows up to radius 6 (a 1024^2 image is
+// then 572 tiles of radius 4, one wave of four CTAs per SM, where 32 rows gave
+// 704 tiles and a second wave of 96), 32 beyond (the staged rows of 40 would
+// pass the 48 KB of static shared memory).
+constexpr int FNT = 256;
 __host__ __device__ constexpr int fb_tile_w(int R) { return 64 - 4 * R; }
+__host__ __device__ constexpr int fb_tile_h(int R) { return R <= 6 ? 40 : 32; }
 
 // Two adjacent taps positions: (v[c], v[c + 1]) for even c is one float2; for odd
 // c it straddles two.
@@ -135,7 +139,7 @@ __device__ __forceinline__ void blur_fb_step_body(const float* __restrict__ x, c
                                                   int W, const BlurW& w, float gamma, float ch,
                                                   Partial* __restrict__ part_a, Partial* __restrict__ part_b,
                                                   int tile_x, int tile_y, int part_index) {
-  constexpr int FX = fb_tile_w(R);
+  constexpr int FX = fb_tile_w(R), FY = fb_tile_h(R);
   constexpr int XR = FY + 4 * R;                   // staged x: rows i0-2R .., columns j0-2R .. j0-2R+63
   constexpr int RR = FY + 2 * R;                   // residual region rows i0-R .., columns j0-R .. j0+FX+R
   constexpr int NW = FNT / 32;                     // warps; lane = column pair, warp = row phase

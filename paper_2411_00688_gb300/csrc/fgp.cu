@@ -136,6 +136,50 @@ __global__ void fgp_finalize_kernel(const float* __restrict__ z, const T* __rest
   }
 }
 
+// 2D finalisation over a (row, column-pair) grid: the arithmetic of
+// fgp_finalize_kernel without its index division and grid-stride loop, two
+// adjacent pixels of a row per thread (the generic kernel held 124 registers
+// and two CTAs per SM; this one needs a few dozen).
+template <typename T, bool NONNEG>
+__global__ void __launch_bounds__(256)
+fgp_finalize2d_kernel(const float* __restrict__ z, const T* __restrict__ p, int H, int W, float lam,
+                      float* __restrict__ x_out, float* __restrict__ h_out, float h_coef, T* __restrict__ p_home,
+                      const float* __restrict__ x_prev, float* __restrict__ fista_y,
+                      const float* __restrict__ beta_tab, const int* __restrict__ beta_idx) {
+  pdl_enter();
+  const int gi = blockIdx.y * blockDim.y + threadIdx.y;
+  const int gj0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (gi >= H) return;
+  const float beta_x = fista_y ? beta_tab[*beta_idx] : 0.f;
+  const size_t n = (size_t)H * W;
+  const T* py = p;
+  const T* px = p + n;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int gj = gj0 + q;
+    if (gj >= W) break;
+    const size_t o = (size_t)gi * W + gj;
+    float dv = 0.f;
+    if (gi < H - 1) dv += Elem<T>::ld(py + o);
+    if (gi > 0) dv -= Elem<T>::ld(py + o - W);
+    if (gj < W - 1) dv += Elem<T>::ld(px + o);
+    if (gj > 0) dv -= Elem<T>::ld(px + o - 1);
+    const float zz = __ldg(z + o);
+    float u = zz + lam * dv;
+    if (NONNEG) u = fmaxf(u, 0.f);
+    if (fista_y) {
+      const float xp = __ldg(x_prev + o);
+      fista_y[o] = u + beta_x * (u - xp);
+    }
+    x_out[o] = u;
+    if (h_out) h_out[o] = h_coef * (u - zz);
+    if (p_home) {
+      p_home[o] = py[o];
+      p_home[n + o] = px[o];
+    }
+  }
+}
+
 // PDHGSkip-1 finalisation (Algorithm 5 with omega + 1 = 1/p):
 // u = P_X(z + lam div p_N); x^ = (u - x) / p; x <- x + p x^ (in place).
 template <typename T, bool NONNEG>
@@ -178,6 +222,12 @@ template <typename T, bool NN>
 cudaError_t fgp_finalize_t(const Dims& d, const float* z, const void* p, float lam, float* x_out,
                            float* h_out, float h_coef, void* p_home, const float* x_prev,
                            float* fista_y, const float* beta_tab, const int* beta_idx, cudaStream_t s) {
+  if (d.ndim == 2 && d.ny <= 65535 * 8) {
+    const dim3 grid((d.nx + 63) / 64, (d.ny + 7) / 8);
+    launch_kernel(fgp_finalize2d_kernel<T, NN>, grid, dim3(32, 8), 0, s, z, (const T*)p, d.ny, d.nx, lam, x_out,
+                  h_out, h_coef, (T*)p_home, x_prev, fista_y, beta_tab, beta_idx);
+    return cudaGetLastError();
+  }
   const size_t n = d.n();
   int blocks = (int)((n + 255) / 256);
   if (blocks > 152 * 16) blocks = 152 * 16;

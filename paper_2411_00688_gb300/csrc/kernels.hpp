@@ -128,8 +128,8 @@ struct BlurW {
 };
 int tile_blocks_2d(int H, int W);        // blocks of the 2D tile kernels
 int fb_step_blocks_2d(int H, int W, int R);  // blocks of launch_blur_fb_step (blur radius R)
-int fb_step_tile_w(int R);                   // its tile: fb_step_tile_w(R) x fb_step_tile_h()
-int fb_step_tile_h();
+int fb_step_tile_w(int R);                   // its tile: fb_step_tile_w(R) x fb_step_tile_h(R)
+int fb_step_tile_h(int R);
 // Fused forward-backward step: out = x - gamma A (A x - b) + ch h (h may be null),
 // partials of 1/2 ||A x - b||^2 and TV(x) (fb_step_blocks_2d of each).
 cudaError_t launch_blur_fb_step(int H, int W, const float* x, const float* b, const float* h, float* out,

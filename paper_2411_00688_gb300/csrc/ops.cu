@@ -272,16 +272,16 @@ bool pdl_enabled() {
 
 int tile_blocks_2d(int H, int W) { return ((W + BX - 1) / BX) * ((H + BY - 1) / BY); }
 int fb_step_tile_w(int R) { return fb_tile_w(R); }
-int fb_step_tile_h() { return FY; }
+int fb_step_tile_h(int R) { return fb_tile_h(R); }
 int fb_step_blocks_2d(int H, int W, int R) {
-  const int fx = fb_tile_w(R);
-  return ((W + fx - 1) / fx) * ((H + FY - 1) / FY);
+  const int fx = fb_tile_w(R), fy = fb_tile_h(R);
+  return ((W + fx - 1) / fx) * ((H + fy - 1) / fy);
 }
 
 cudaError_t launch_blur_fb_step(int H, int W, const float* x, const float* b, const float* h, float* out,
                                 const BlurW& w, float gamma, float ch, Partial* part_data, Partial* part_tv,
                                 cudaStream_t s) {
-  dim3 grid((W + fb_tile_w(w.R) - 1) / fb_tile_w(w.R), (H + FY - 1) / FY);
+  dim3 grid((W + fb_tile_w(w.R) - 1) / fb_tile_w(w.R), (H + fb_tile_h(w.R) - 1) / fb_tile_h(w.R));
   switch (w.R) {
 #define TVS_FB_R(R_) \
   case R_: launch_kernel(blur_fb_step_kernel<R_>, dim3(grid), dim3(FNT), 0, s, x, b, h, out, H, W, w, gamma, ch, part_data, part_tv); break;
