@@ -314,16 +314,18 @@ tvs_status fgp_config_for(tvs_ctx* C, const Dims& d, int dtype, const float* z, 
       }
     }
   }
-  const int cands[][3] = {{4, 1, 105}, {4, 2, 104}, {4, 2, 105}, {4, 1, 5}};
-  const float betas[4] = {0.f, 0.f, 0.2f, 0.4f};
+  const int cands[][3] = {{4, 1, 105}, {4, 2, 104}, {4, 2, 105}, {4, 1, 5}, {5, 2, 104}};
+  const float betas[8] = {0.f, 0.f, 0.2f, 0.4f, 0.5f, 0.55f, 0.6f, 0.65f};
   cudaStream_t s = C->stream;
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));
   CUDA_TRY(cudaEventCreate(&e1));
   FgpConfig best;
   float best_ms = 1e30f;
-  // three rounds over the candidates, each timing 6 launches after a warm-up;
-  // a candidate's score is its best round (robust against clock ramps and noise)
+  // three rounds over the candidates, each timing 6 launches of as many
+  // iterations as the candidate blocks after a warm-up; a candidate's score is
+  // its best round's time per inner iteration (robust against clock ramps and
+  // noise, and comparable across depths)
   const int ncand = (int)(sizeof(cands) / sizeof(cands[0]));
   std::vector<float> score(ncand, 1e30f);
   for (int round = 0; round < 3; ++round) {
@@ -333,11 +335,11 @@ tvs_status fgp_config_for(tvs_ctx* C, const Dims& d, int dtype, const float* z, 
       c.cpl = cands[ci][1];
       c.rpw = cands[ci][2];
       float ms = 0.f;
-      cudaError_t e = launch_fgp_block(c, d, z, home, home, scratch0, scratch1, 0.1f, 1.25f, betas, 4, dtype,
+      cudaError_t e = launch_fgp_block(c, d, z, home, home, scratch0, scratch1, 0.1f, 1.25f, betas, c.tb, dtype,
                                        false, s);
       if (e == cudaSuccess) e = cudaEventRecord(e0, s);
       for (int r = 0; r < 6 && e == cudaSuccess; ++r)
-        e = launch_fgp_block(c, d, z, home, home, scratch0, scratch1, 0.1f, 1.25f, betas, 4, dtype, false, s);
+        e = launch_fgp_block(c, d, z, home, home, scratch0, scratch1, 0.1f, 1.25f, betas, c.tb, dtype, false, s);
       if (e == cudaSuccess) e = cudaEventRecord(e1, s);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
@@ -346,7 +348,7 @@ tvs_status fgp_config_for(tvs_ctx* C, const Dims& d, int dtype, const float* z, 
         cudaEventDestroy(e1);
         return fail(TVS_ECUDA, "fgp autotune: %s", cudaGetErrorString(e));
       }
-      score[ci] = std::min(score[ci], ms);
+      score[ci] = std::min(score[ci], ms / c.tb);
     }
   }
   for (int ci = 0; ci < ncand; ++ci)

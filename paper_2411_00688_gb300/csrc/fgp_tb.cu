@@ -238,6 +238,7 @@ cudaError_t fgp_tb_dispatch(const FgpConfig& c, const Dims& d, const float* z, c
   TVS_RB_CASE(3, 2, 6)
   TVS_RB_CASE(4, 2, 4)
   TVS_RB_CASE(4, 1, 6)
+  TVS_RB_CASE(5, 2, 4)
 #undef TVS_RB_CASE
   return cudaErrorInvalidValue;
 }
@@ -248,7 +249,7 @@ bool fgp_config_valid(const FgpConfig& c) {
   if (c.tb <= 1) return true;
   const int ok[][3] = {{2, 2, 4},   {3, 2, 4},   {4, 2, 4},   {4, 2, 5},   {4, 1, 5},   {6, 2, 6},
                        {8, 2, 6},   {2, 2, 104}, {4, 1, 105}, {4, 2, 105}, {4, 2, 108}, {4, 1, 108},
-                       {6, 2, 108}, {3, 2, 106}, {4, 2, 104}, {4, 1, 106}};
+                       {6, 2, 108}, {3, 2, 106}, {4, 2, 104}, {4, 1, 106}, {5, 2, 104}};
   for (const auto& k : ok)
     if (k[0] == c.tb && k[1] == c.cpl && k[2] == c.rpw) return true;
   return false;

@@ -28,7 +28,7 @@ from tests._util import TOL_X_F32, TOL_X_HALF, assert_close, cuda, f32, host
 pytestmark = pytest.mark.gpu
 
 CFG_2D = ["1", "2,2,4", "3,2,4", "4,2,4", "4,2,5", "4,1,5", "6,2,6", "8,2,6", "2,2,104", "4,1,105", "4,2,105",
-          "4,2,108", "4,1,108", "6,2,108", "3,2,106", "4,2,104", "4,1,106"]
+          "4,2,108", "4,1,108", "6,2,108", "3,2,106", "4,2,104", "4,1,106", "5,2,104"]
 CFG_3D = ["1,2,64", "1,4,64", "2,2,64", "1,2,32", "2,2,32", "2,4,32", "tma:1,2,64", "tma:1,2,32", "tma:1,4,64",
           "tma:2,2,64", "tma:2,2,32", "tma:2,4,32", "tma3:1,2,64", "tma3:2,2,32", "tile"]
 DUALS = ["f32", "bf16", "f16", "q15"]
