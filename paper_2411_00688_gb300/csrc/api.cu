@@ -1433,10 +1433,47 @@ tvs_status build_batch(tvs_ctx* C, int n, tvs_problem* const* probs, const tvs_f
 
 }  // namespace
 
+namespace {
+tvs_status validate_batch(tvs_ctx* C, int n, tvs_problem* const* probs, const tvs_fb_params* prm,
+                          float* const* x_io, tvs_mem mem);
+tvs_status batch_solve_in_order(tvs_ctx* C, int n, tvs_problem* const* probs, const tvs_fb_params* prm,
+                                float* const* x_io, tvs_mem mem, tvs_trace* traces);
+}  // namespace
+
+// The batch is solved with its problems ordered by pixel count, smallest first:
+// each inner launch hands out the tiles of the active problems in that order, so
+// its last tiles are interior tiles of large images, the cheapest per tile (no
+// edge masks), and the launch's tail is shorter.  Results and traces are
+// returned in the caller's order.
 extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const* probs,
                                            const tvs_fb_params* prm, float* const* x_io, tvs_mem mem,
                                            tvs_trace* traces) {
   if (!C || n < 1 || !probs || !prm || !x_io) return fail(TVS_EINVAL, "null argument or n < 1");
+  TVS_TRY(validate_batch(C, n, probs, prm, x_io, mem));
+  std::vector<int> ord(n);
+  for (int i = 0; i < n; ++i) ord[i] = i;
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return probs[a]->n < probs[b]->n; });
+  std::vector<tvs_problem*> pp(n);
+  std::vector<tvs_fb_params> pm(n);
+  std::vector<float*> px(n);
+  std::vector<tvs_trace> pt(traces ? n : 0);
+  for (int j = 0; j < n; ++j) {
+    pp[j] = probs[ord[j]];
+    pm[j] = prm[ord[j]];
+    px[j] = x_io[ord[j]];
+    if (traces) pt[j] = traces[ord[j]];
+  }
+  const tvs_status st = batch_solve_in_order(C, n, pp.data(), pm.data(), px.data(), mem, traces ? pt.data() : nullptr);
+  if (traces)
+    for (int j = 0; j < n; ++j) traces[ord[j]] = pt[j];
+  return st;
+}
+
+namespace {
+// Arguments as for proxskip_solve_batch, checked (messages give the caller's
+// problem indices).
+tvs_status validate_batch(tvs_ctx* C, int n, tvs_problem* const* probs, const tvs_fb_params* prm,
+                          float* const* x_io, tvs_mem mem) {
   if (mem != TVS_MEM_DEVICE && mem != TVS_MEM_HOST) return fail(TVS_EINVAL, "invalid mem kind");
   const int K = prm[0].max_iter, N = prm[0].n_inner, dtype = prm[0].dual;
   for (int i = 0; i < n; ++i) {
@@ -1456,6 +1493,17 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
     for (int j = 0; j < i; ++j)
       if (probs[j] == P) return fail(TVS_EINVAL, "problem %d appears twice", i);
   }
+  for (int i = 1; i < n; ++i)
+    if (probs[i]->desc.op.kind == TVS_OP_GAUSS_BLUR)
+      for (int j = 0; j < i; ++j)
+        if (probs[j]->desc.op.kind == TVS_OP_GAUSS_BLUR && probs[j]->bw.R != probs[i]->bw.R)
+          return fail(TVS_EUNSUPPORTED, "blur problems of a batch must share the blur radius");
+  return TVS_OK;
+}
+
+tvs_status batch_solve_in_order(tvs_ctx* C, int n, tvs_problem* const* probs, const tvs_fb_params* prm,
+                                float* const* x_io, tvs_mem mem, tvs_trace* traces) {
+  const int K = prm[0].max_iter, N = prm[0].n_inner;
   int blur_radius = 0;
   for (int i = 0; i < n; ++i)
     if (probs[i]->desc.op.kind == TVS_OP_GAUSS_BLUR) {
@@ -1569,6 +1617,8 @@ extern "C" tvs_status proxskip_solve_batch(tvs_ctx* C, int n, tvs_problem* const
   if (bad) return fail(TVS_ENUMERIC, "non-finite objective in the batch");
   return TVS_OK;
 }
+
+}  // namespace
 
 // ---------------------------------------------------------------- Dual-ROF (light prox)
 extern "C" tvs_status dual_rof_solve(tvs_ctx* C, const int dims[2], const float* b,

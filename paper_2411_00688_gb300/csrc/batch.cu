@@ -16,15 +16,19 @@ namespace tvs {
 
 namespace {
 
-// Blocked inner kernel of the batch: 4 iterations per launch over a 64 x 40
-// region (56 x 32 outputs), two columns per lane.  On the 256-problem workload
-// (sides 64..1024) the taller region does 5 % less halo work than 64 x 32 and
-// still fits three CTAs per SM without spilling: batched solve 0.308 -> 0.296 s;
-// 64 x 64 (one CTA per SM) took 0.438 s.
+// Blocked inner kernel of the batch: 5 iterations per launch over a 64 x 40
+// region (54 x 30 outputs), two columns per lane, three CTAs per SM without
+// spilling.  On the 256-problem workload (sides 64..1024), batched solve:
+// 4 iterations on 64 x 32 0.308 s, on 64 x 40 0.291 s, 5 on 64 x 32 0.286 s,
+// 5 on 64 x 40 0.267 s (10 launches per 50-iteration prox instead of 13);
+// 4 on 64 x 64 (one CTA per SM) 0.438 s.
 #ifndef TVS_BATCH_RPW
 #define TVS_BATCH_RPW 5
 #endif
-constexpr int BT_TB = 4, BT_CPL = 2, BT_RPW = TVS_BATCH_RPW;
+#ifndef TVS_BATCH_TB
+#define TVS_BATCH_TB 5
+#endif
+constexpr int BT_TB = TVS_BATCH_TB, BT_CPL = 2, BT_RPW = TVS_BATCH_RPW;
 constexpr int BT_TW = 32 * BT_CPL - 2 * BT_TB, BT_TH = 8 * BT_RPW - 2 * BT_TB;
 constexpr int CHUNK = 2048;                        // pixels per pointwise work item
 
