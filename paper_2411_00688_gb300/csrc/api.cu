@@ -24,6 +24,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -64,15 +65,24 @@ tvs_status fail(tvs_status st, const char* fmt, ...) {
   } while (0)
 
 constexpr int LAG = 8;  // outer iterations the host may run ahead of the device
+// Outer iterations per chunk graph: CHUNK iterations from a multiple of CHUNK run
+// as one graph launch, captured for their coin pattern the first time it occurs,
+// so the programmatic launch chain continues across those iterations instead of
+// ending at a graph boundary (which drains the device and costs a full launch).
+// CHUNK_DEPTH chunk launches may be queued ahead of the device.
+constexpr int CHUNK = 4;
+constexpr int CHUNK_DEPTH = 2;
 
 bool is_fin(double v) { return std::isfinite(v); }
 
 }  // namespace
 
 // The CUDA graphs of one solve: one outer iteration each, by coin and by the
-// parity of the iterate buffers.
+// parity of the iterate buffers, and runs of CHUNK iterations from an even
+// iteration, by their coins (bit i: the coin of the run's i-th iteration).
 struct GraphSet {
   cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [coin][parity]
+  cudaGraphExec_t chunk[1 << CHUNK] = {};                                 // [coin pattern]
   GraphSet() = default;
   GraphSet(const GraphSet&) = delete;
   GraphSet& operator=(const GraphSet&) = delete;
@@ -80,6 +90,8 @@ struct GraphSet {
     for (auto& row : exec)
       for (auto& e : row)
         if (e) cudaGraphExecDestroy(e);
+    for (auto& e : chunk)
+      if (e) cudaGraphExecDestroy(e);
   }
 };
 
@@ -447,6 +459,8 @@ tvs_status fb_step(tvs_problem* P, const float* src, float* out, const float* h,
   return TVS_OK;
 }
 
+InnerStamp inner_stamp(tvs_problem* P) { return InnerStamp{P->fgp_ts, P->flags + 3}; }
+
 // Partials of F(x) only; returns their counts.
 tvs_status objective_parts(tvs_problem* P, const float* x, Partial* pa, Partial* pb, int* na, int* nb,
                            cudaStream_t s) {
@@ -597,15 +611,26 @@ double solve_timeout_ms() {
   return v > 0.0 ? v : 0.0;
 }
 
+// Captures the stream work of one outer iteration with the given coin, reading
+// the iterate buffer of the given parity.
+using IterBody = std::function<tvs_status(int coin, int parity)>;
+
+// Launches the outer iterations: with `body`, runs of CHUNK iterations from a
+// multiple of CHUNK as one chunk graph each (captured on first use of its coin
+// pattern) and the remaining iterations one graph each, at most CHUNK_DEPTH
+// launches ahead of the device; without it, one graph per iteration, LAG ahead.
+// The host stops launching once the device has raised done_host.
 tvs_status run_loop(tvs_problem* P, int K, const std::vector<unsigned char>& coins, GraphSet& G,
-                    LoopState* ls) {
+                    LoopState* ls, const IterBody* body = nullptr) {
   tvs_ctx* C = P->ctx;
   cudaStream_t s = C->stream;
   const double limit = solve_timeout_ms();
   const auto t0 = std::chrono::steady_clock::now();
-  for (int k = 0; k < K; ++k) {
-    if (k >= LAG) {
-      CUDA_TRY(cudaEventSynchronize(C->ring[k % LAG]));
+  const int depth = body ? CHUNK_DEPTH : LAG;
+  int k = 0;
+  for (int j = 0; k < K; ++j) {
+    if (j >= depth) {
+      CUDA_TRY(cudaEventSynchronize(C->ring[(j - depth) % LAG]));
       if (*(volatile int*)P->done_host) break;
     }
     if (limit > 0.0 &&
@@ -613,11 +638,34 @@ tvs_status run_loop(tvs_problem* P, int K, const std::vector<unsigned char>& coi
       ls->timed_out = true;
       break;
     }
-    const int c = coins[k] ? 1 : 0;
-    CUDA_TRY(cudaGraphLaunch(G.exec[c][k & 1], s));
-    CUDA_TRY(cudaEventRecord(C->ring[k % LAG], s));
-    ls->iters = k + 1;
-    ls->prox += c;
+    if (body && k % CHUNK == 0 && K - k >= CHUNK) {
+      int pat = 0, np = 0;
+      for (int i = 0; i < CHUNK; ++i) {
+        const int c = coins[k + i] ? 1 : 0;
+        pat |= c << i;
+        np += c;
+      }
+      if (!G.chunk[pat]) {
+        const tvs_status st = capture(s, &G.chunk[pat], [&]() -> tvs_status {
+          for (int i = 0; i < CHUNK; ++i) TVS_TRY((*body)((pat >> i) & 1, i & 1));
+          return TVS_OK;
+        });
+        if (st != TVS_OK) {
+          G.chunk[pat] = nullptr;
+          return st;
+        }
+      }
+      CUDA_TRY(cudaGraphLaunch(G.chunk[pat], s));
+      k += CHUNK;
+      ls->prox += np;
+    } else {
+      const int c = coins[k] ? 1 : 0;
+      CUDA_TRY(cudaGraphLaunch(G.exec[c][k & 1], s));
+      k += 1;
+      ls->prox += c;
+    }
+    CUDA_TRY(cudaEventRecord(C->ring[j % LAG], s));
+    ls->iters = k;
   }
   return TVS_OK;
 }
@@ -784,59 +832,60 @@ tvs_status fb_solve(tvs_problem* P, const tvs_fb_params* prm, float* x_io, tvs_m
                                (double)every, prm->f_star, prm->target_rel_gap, prm->target_rel_dist,
                                (double)fcfg.tb, (double)fcfg.cpl, (double)fcfg.rpw},
                               &fresh);
+  // one outer iteration from x[par] to x[par ^ 1]
+  const IterBody body = [&](int c, int par) -> tvs_status {
+    float* xc = P->x[par];
+    float* xn = P->x[par ^ 1];
+    if (kind == FB_PROXSKIP) {
+      if (c == 0) {
+        TVS_TRY(fb_step(P, xc, xn, P->h, fgamma, fgamma, s));
+      } else {
+        TVS_TRY(fb_step(P, xc, P->z, P->h, fgamma, (float)(gamma - gamma / p), s));
+      }
+    } else {
+      TVS_TRY(fb_step(P, kind == FB_FISTA ? aux : xc, P->z, nullptr, fgamma, 0.f, s));
+    }
+    const bool branch = kind != FB_FISTA && c == 1;  // overlap the record with the prox
+    if (kind != FB_FISTA) {
+      cudaStream_t rs = s;
+      if (branch) {
+        CUDA_TRY(cudaEventRecord(C->fork_ev, s));
+        CUDA_TRY(cudaStreamWaitEvent(C->side, C->fork_ev, 0));
+        rs = C->side;
+      }
+      CUDA_TRY(launch_reduce_record(P->part_a, na, P->part_b, nb, alpha, every, P->obj_dev,
+                                    P->ts_dev, prm->f_star, prm->target_rel_gap, P->flags,
+                                    P->done_host_dev, nullptr, rs));
+      TVS_TRY(track_distance(P, xc, prm->target_rel_dist, rs));
+      if (branch) CUDA_TRY(cudaEventRecord(C->join_ev, C->side));
+    }
+    if (c == 1) {
+      int fin = 0;
+      CUDA_TRY(launch_inner_start_stamp(inner_stamp(P), s));
+      if (use_prox) TVS_TRY(launch_fgp_sequence(fcfg, d, P->z, P->dual, N, betas, lam, dtype, nonneg, s, &fin));
+      CUDA_TRY(launch_fgp_finalize(d, P->z, P->dual[fin], dtype, use_prox ? lam : 0.f, nonneg, xn,
+                                   kind == FB_PROXSKIP ? P->h : nullptr, h_coef,
+                                   fin != 0 ? P->dual[0] : nullptr, xc,
+                                   kind == FB_FISTA ? aux : nullptr, P->beta_dev, P->flags + 2,
+                                   inner_stamp(P), s));
+    }
+    if (branch) CUDA_TRY(cudaStreamWaitEvent(s, C->join_ev, 0));
+    if (kind == FB_FISTA) {
+      int a = 0, b = 0;
+      TVS_TRY(objective_parts(P, xn, P->part_a, P->part_b, &a, &b, s));
+      CUDA_TRY(launch_reduce_record(P->part_a, a, P->part_b, b, alpha, every, P->obj_dev,
+                                    P->ts_dev, prm->f_star, prm->target_rel_gap, P->flags,
+                                    P->done_host_dev, nullptr, s));
+      TVS_TRY(track_distance(P, xn, prm->target_rel_dist, s));
+    }
+    return TVS_OK;
+  };
   if (fresh) {
     const tvs_status cst = [&]() -> tvs_status {
       for (int c = 0; c < 2; ++c) {
         if (c == 0 && kind != FB_PROXSKIP) continue;
-        for (int par = 0; par < 2; ++par) {
-          float* xc = P->x[par];
-          float* xn = P->x[par ^ 1];
-          TVS_TRY(capture(s, &G.exec[c][par], [&]() -> tvs_status {
-            if (kind == FB_PROXSKIP) {
-              if (c == 0) {
-                TVS_TRY(fb_step(P, xc, xn, P->h, fgamma, fgamma, s));
-              } else {
-                TVS_TRY(fb_step(P, xc, P->z, P->h, fgamma, (float)(gamma - gamma / p), s));
-              }
-            } else {
-              TVS_TRY(fb_step(P, kind == FB_FISTA ? aux : xc, P->z, nullptr, fgamma, 0.f, s));
-            }
-            const bool branch = kind != FB_FISTA && c == 1;  // overlap the record with the prox
-            if (kind != FB_FISTA) {
-              cudaStream_t rs = s;
-              if (branch) {
-                CUDA_TRY(cudaEventRecord(C->fork_ev, s));
-                CUDA_TRY(cudaStreamWaitEvent(C->side, C->fork_ev, 0));
-                rs = C->side;
-              }
-              CUDA_TRY(launch_reduce_record(P->part_a, na, P->part_b, nb, alpha, every, P->obj_dev,
-                                            P->ts_dev, prm->f_star, prm->target_rel_gap, P->flags,
-                                            P->done_host_dev, nullptr, rs));
-              TVS_TRY(track_distance(P, xc, prm->target_rel_dist, rs));
-              if (branch) CUDA_TRY(cudaEventRecord(C->join_ev, C->side));
-            }
-            if (c == 1) {
-              int fin = 0;
-              CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 0, s));
-              if (use_prox) TVS_TRY(launch_fgp_sequence(fcfg, d, P->z, P->dual, N, betas, lam, dtype, nonneg, s, &fin));
-              CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 1, s));
-              CUDA_TRY(launch_fgp_finalize(d, P->z, P->dual[fin], dtype, use_prox ? lam : 0.f, nonneg, xn,
-                                           kind == FB_PROXSKIP ? P->h : nullptr, h_coef,
-                                           fin != 0 ? P->dual[0] : nullptr, xc,
-                                           kind == FB_FISTA ? aux : nullptr, P->beta_dev, P->flags + 2, s));
-            }
-            if (branch) CUDA_TRY(cudaStreamWaitEvent(s, C->join_ev, 0));
-            if (kind == FB_FISTA) {
-              int a = 0, b = 0;
-              TVS_TRY(objective_parts(P, xn, P->part_a, P->part_b, &a, &b, s));
-              CUDA_TRY(launch_reduce_record(P->part_a, a, P->part_b, b, alpha, every, P->obj_dev,
-                                            P->ts_dev, prm->f_star, prm->target_rel_gap, P->flags,
-                                            P->done_host_dev, nullptr, s));
-              TVS_TRY(track_distance(P, xn, prm->target_rel_dist, s));
-            }
-            return TVS_OK;
-          }));
-        }
+        for (int par = 0; par < 2; ++par)
+          TVS_TRY(capture(s, &G.exec[c][par], [&]() -> tvs_status { return body(c, par); }));
       }
       return TVS_OK;
     }();
@@ -846,7 +895,7 @@ tvs_status fb_solve(tvs_problem* P, const tvs_fb_params* prm, float* x_io, tvs_m
     }
   }
   LoopState ls;
-  TVS_TRY(run_loop(P, K, coins, G, &ls));
+  TVS_TRY(run_loop(P, K, coins, G, &ls, &body));
   float* xfin = P->x[ls.iters & 1];
   if (kind != FB_FISTA && ls.iters > 0) {
     int a = 0, b = 0;
@@ -906,47 +955,47 @@ tvs_status pd_solve(tvs_problem* P, const tvs_pd_params* prm, float* x_io, float
                                (double)N, (double)every, prm->f_star, prm->target_rel_gap, prm->target_rel_dist,
                                (double)fcfg.tb, (double)fcfg.cpl, (double)fcfg.rpw},
                               &fresh);
+  // one outer iteration from x[par] to x[par ^ 1]
+  const IterBody body = [&](int c, int par) -> tvs_status {
+    float* xc = P->x[par];
+    float* xn = P->x[par ^ 1];
+    if (skip) {
+      if (c == 0) TVS_TRY(pd_backward(P, xc, xn, P->h, fs, fs, s));
+      else TVS_TRY(pd_backward(P, xc, P->z, P->h, fs, (float)(sigma - sigma / p), s));
+    } else {
+      TVS_TRY(pd_backward(P, xc, P->z, nullptr, fs, 0.f, s));
+    }
+    // on prox iterations the objective record runs beside the inner iterations
+    cudaStream_t rs = s;
+    if (c == 1) {
+      CUDA_TRY(cudaEventRecord(C->fork_ev, s));
+      CUDA_TRY(cudaStreamWaitEvent(C->side, C->fork_ev, 0));
+      rs = C->side;
+    }
+    CUDA_TRY(launch_reduce_record(P->part_a, na, P->part_b, nb, alpha, every, P->obj_dev,
+                                  P->ts_dev, prm->f_star, prm->target_rel_gap, P->flags,
+                                  P->done_host_dev, nullptr, rs));
+    TVS_TRY(track_distance(P, xc, prm->target_rel_dist, rs));
+    if (c == 1) CUDA_TRY(cudaEventRecord(C->join_ev, C->side));
+    if (c == 1) {
+      int fin = 0;
+      CUDA_TRY(launch_inner_start_stamp(inner_stamp(P), s));
+      if (use_prox) TVS_TRY(launch_fgp_sequence(fcfg, d, P->z, P->dual, N, betas, lam, dtype, nonneg, s, &fin));
+      CUDA_TRY(launch_fgp_finalize(d, P->z, P->dual[fin], dtype, use_prox ? lam : 0.f, nonneg, xn,
+                                   skip ? P->h : nullptr, (float)(p / sigma),
+                                   fin != 0 ? P->dual[0] : nullptr, nullptr, nullptr, nullptr,
+                                   nullptr, inner_stamp(P), s));
+      CUDA_TRY(cudaStreamWaitEvent(s, C->join_ev, 0));  // the record read part_a
+    }
+    TVS_TRY(pd_forward(P, xn, ft, false, s));
+    return TVS_OK;
+  };
   if (fresh) {
     const tvs_status cst = [&]() -> tvs_status {
       for (int c = 0; c < 2; ++c) {
         if (c == 0 && !skip) continue;
-        for (int par = 0; par < 2; ++par) {
-          float* xc = P->x[par];
-          float* xn = P->x[par ^ 1];
-          TVS_TRY(capture(s, &G.exec[c][par], [&]() -> tvs_status {
-            if (skip) {
-              if (c == 0) TVS_TRY(pd_backward(P, xc, xn, P->h, fs, fs, s));
-              else TVS_TRY(pd_backward(P, xc, P->z, P->h, fs, (float)(sigma - sigma / p), s));
-            } else {
-              TVS_TRY(pd_backward(P, xc, P->z, nullptr, fs, 0.f, s));
-            }
-            // on prox iterations the objective record runs beside the inner iterations
-            cudaStream_t rs = s;
-            if (c == 1) {
-              CUDA_TRY(cudaEventRecord(C->fork_ev, s));
-              CUDA_TRY(cudaStreamWaitEvent(C->side, C->fork_ev, 0));
-              rs = C->side;
-            }
-            CUDA_TRY(launch_reduce_record(P->part_a, na, P->part_b, nb, alpha, every, P->obj_dev,
-                                          P->ts_dev, prm->f_star, prm->target_rel_gap, P->flags,
-                                          P->done_host_dev, nullptr, rs));
-            TVS_TRY(track_distance(P, xc, prm->target_rel_dist, rs));
-            if (c == 1) CUDA_TRY(cudaEventRecord(C->join_ev, C->side));
-            if (c == 1) {
-              int fin = 0;
-              CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 0, s));
-              if (use_prox) TVS_TRY(launch_fgp_sequence(fcfg, d, P->z, P->dual, N, betas, lam, dtype, nonneg, s, &fin));
-              CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 1, s));
-              CUDA_TRY(launch_fgp_finalize(d, P->z, P->dual[fin], dtype, use_prox ? lam : 0.f, nonneg, xn,
-                                           skip ? P->h : nullptr, (float)(p / sigma),
-                                           fin != 0 ? P->dual[0] : nullptr, nullptr, nullptr, nullptr,
-                                           nullptr, s));
-              CUDA_TRY(cudaStreamWaitEvent(s, C->join_ev, 0));  // the record read part_a
-            }
-            TVS_TRY(pd_forward(P, xn, ft, false, s));
-            return TVS_OK;
-          }));
-        }
+        for (int par = 0; par < 2; ++par)
+          TVS_TRY(capture(s, &G.exec[c][par], [&]() -> tvs_status { return body(c, par); }));
       }
       return TVS_OK;
     }();
@@ -956,7 +1005,7 @@ tvs_status pd_solve(tvs_problem* P, const tvs_pd_params* prm, float* x_io, float
     }
   }
   LoopState ls;
-  TVS_TRY(run_loop(P, K, coins, G, &ls));
+  TVS_TRY(run_loop(P, K, coins, G, &ls, &body));
   float* xfin = P->x[ls.iters & 1];
   if (ls.iters > 0) {
     CUDA_TRY(launch_tv_partials(d, xfin, P->part_b, s));
@@ -1037,11 +1086,10 @@ tvs_status pd1_solve(tvs_problem* P, const tvs_pd_params* prm, float* x_io, floa
           }
           TVS_TRY(pd_backward(P, x, P->z, nullptr, (float)sigma, 0.f, s, false));
           int fin = 0;
-          CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 0, s));
+          CUDA_TRY(launch_inner_start_stamp(inner_stamp(P), s));
           if (use_prox) TVS_TRY(launch_fgp_sequence(fcfg, d, P->z, P->dual, N, betas, lam, dtype, nonneg, s, &fin));
-          CUDA_TRY(launch_timestamp_pair(P->fgp_ts, P->flags + 3, 1, s));
           CUDA_TRY(launch_fgp_finalize_pd1(d, P->z, P->dual[fin], dtype, use_prox ? lam : 0.f, nonneg, (float)p, x,
-                                           P->h, fin != 0 ? P->dual[0] : nullptr, s));
+                                           P->h, fin != 0 ? P->dual[0] : nullptr, inner_stamp(P), s));
           TVS_TRY(pd1_forward(P, P->h, (float)p, (float)tau, s));
           CUDA_TRY(launch_tv_partials(d, x, P->part_b, s));
           return TVS_OK;
@@ -1151,33 +1199,34 @@ tvs_status pdx_solve(tvs_problem* P, const tvs_pdx_params* prm, float* x_io, flo
   const int na = pointwise_blocks(P->m), nb = pdx_tv_blocks(d.ny, d.nx);
   const float s_d = (float)(0.5 * prm->tau);
   GraphSet G;
-  for (int par = 0; par < 2; ++par) {
+  // one iteration from (x, q)[par] to (x, q)[par ^ 1]
+  const IterBody body = [&](int, int par) -> tvs_status {
     float* xc = P->x[par];
     float* xn = P->x[par ^ 1];
     const float* qc = (const float*)P->dual[par];
     float* qn = (float*)P->dual[par ^ 1];
-    TVS_TRY(capture(s, &G.exec[1][par], [&]() -> tvs_status {
-      const float* g = P->y;
-      if (!ident) {
-        TVS_TRY(apply_At(P, P->y, P->z, s));
-        g = P->z;
-      }
-      CUDA_TRY(launch_pdx_tv_step(d.ny, d.nx, xc, g, T, qc, xn, qn, (float)alpha, s_d, nonneg, P->part_b, s));
-      CUDA_TRY(launch_reduce_record(P->part_a, na, P->part_b, nb, alpha, every, P->obj_dev, P->ts_dev,
-                                    prm->f_star, prm->target_rel_gap, P->flags, P->done_host_dev, nullptr, s));
-      TVS_TRY(track_distance(P, xc, prm->target_rel_dist, s));
-      const float* ax = xn;
-      if (!ident) {
-        TVS_TRY(apply_A(P, xn, P->aux, s));
-        ax = P->aux;
-      }
-      CUDA_TRY(launch_pdx_dual(P->m, ax, P->axp, P->y, P->b, S, false, P->part_a, s));
-      return TVS_OK;
-    }));
-  }
+    const float* g = P->y;
+    if (!ident) {
+      TVS_TRY(apply_At(P, P->y, P->z, s));
+      g = P->z;
+    }
+    CUDA_TRY(launch_pdx_tv_step(d.ny, d.nx, xc, g, T, qc, xn, qn, (float)alpha, s_d, nonneg, P->part_b, s));
+    CUDA_TRY(launch_reduce_record(P->part_a, na, P->part_b, nb, alpha, every, P->obj_dev, P->ts_dev,
+                                  prm->f_star, prm->target_rel_gap, P->flags, P->done_host_dev, nullptr, s));
+    TVS_TRY(track_distance(P, xc, prm->target_rel_dist, s));
+    const float* ax = xn;
+    if (!ident) {
+      TVS_TRY(apply_A(P, xn, P->aux, s));
+      ax = P->aux;
+    }
+    CUDA_TRY(launch_pdx_dual(P->m, ax, P->axp, P->y, P->b, S, false, P->part_a, s));
+    return TVS_OK;
+  };
+  for (int par = 0; par < 2; ++par)
+    TVS_TRY(capture(s, &G.exec[1][par], [&]() -> tvs_status { return body(1, par); }));
   std::vector<unsigned char> coins(K, 1);
   LoopState ls;
-  TVS_TRY(run_loop(P, K, coins, G, &ls));
+  TVS_TRY(run_loop(P, K, coins, G, &ls, &body));
   float* xfin = P->x[ls.iters & 1];
   const float* qfin = (const float*)P->dual[ls.iters & 1];
   if (ls.iters > 0) {
@@ -2124,7 +2173,7 @@ tvs_status tv_prox(tvs_ctx* C, int ndim, const int dims[3], const float* z, floa
                                        dual, nonneg != 0, s, &fin));
   CUDA_TRY(launch_fgp_finalize(d, z, buf[fin], dual, use ? (float)lambda : 0.f, nonneg != 0, u,
                                nullptr, 0.f, (fin != 0 && dual_state) ? dual_state : nullptr,
-                               nullptr, nullptr, nullptr, nullptr, s));
+                               nullptr, nullptr, nullptr, nullptr, InnerStamp{}, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   if (ndim == 3 && use && n_iter > 0 && fgp3d_take_wait_timeouts())
     return fail(TVS_ETIMEDOUT, "a 3D inner kernel gave up waiting for a TMA tile load; the result is incomplete");

@@ -99,8 +99,9 @@ __global__ void fgp_finalize_kernel(const float* __restrict__ z, const T* __rest
                                     float* __restrict__ h_out, float h_coef, T* __restrict__ p_home,
                                     const float* __restrict__ x_prev, float* __restrict__ fista_y,
                                     const float* __restrict__ beta_tab, const int* __restrict__ beta_idx,
-                                    IndexMap im) {
+                                    IndexMap im, InnerStamp st) {
   pdl_enter();
+  stamp_inner_end(st);
   const float beta_x = fista_y ? beta_tab[*beta_idx] : 0.f;
   const size_t n = (size_t)D * H * W;
   const size_t HW = (size_t)H * W;
@@ -145,8 +146,9 @@ __global__ void __launch_bounds__(256)
 fgp_finalize2d_kernel(const float* __restrict__ z, const T* __restrict__ p, int H, int W, float lam,
                       float* __restrict__ x_out, float* __restrict__ h_out, float h_coef, T* __restrict__ p_home,
                       const float* __restrict__ x_prev, float* __restrict__ fista_y,
-                      const float* __restrict__ beta_tab, const int* __restrict__ beta_idx) {
+                      const float* __restrict__ beta_tab, const int* __restrict__ beta_idx, InnerStamp st) {
   pdl_enter();
+  stamp_inner_end(st);
   const int gi = blockIdx.y * blockDim.y + threadIdx.y;
   const int gj0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   if (gi >= H) return;
@@ -185,8 +187,10 @@ fgp_finalize2d_kernel(const float* __restrict__ z, const T* __restrict__ p, int 
 template <typename T, bool NONNEG>
 __global__ void fgp_finalize_pd1_kernel(const float* __restrict__ z, const T* __restrict__ p, int H, int W,
                                         float lam, float prob_p, float* __restrict__ x,
-                                        float* __restrict__ xh, T* __restrict__ p_home, IndexMap im) {
+                                        float* __restrict__ xh, T* __restrict__ p_home, IndexMap im,
+                                        InnerStamp st) {
   pdl_enter();
+  stamp_inner_end(st);
   const size_t n = (size_t)H * W;
   for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
     int gk, gi, gj;
@@ -221,11 +225,12 @@ cudaError_t fgp_iter_t(const Dims& d, const float* z, const void* pc, const void
 template <typename T, bool NN>
 cudaError_t fgp_finalize_t(const Dims& d, const float* z, const void* p, float lam, float* x_out,
                            float* h_out, float h_coef, void* p_home, const float* x_prev,
-                           float* fista_y, const float* beta_tab, const int* beta_idx, cudaStream_t s) {
+                           float* fista_y, const float* beta_tab, const int* beta_idx, InnerStamp st,
+                           cudaStream_t s) {
   if (d.ndim == 2 && d.ny <= 65535 * 8) {
     const dim3 grid((d.nx + 63) / 64, (d.ny + 7) / 8);
     launch_kernel(fgp_finalize2d_kernel<T, NN>, grid, dim3(32, 8), 0, s, z, (const T*)p, d.ny, d.nx, lam, x_out,
-                  h_out, h_coef, (T*)p_home, x_prev, fista_y, beta_tab, beta_idx);
+                  h_out, h_coef, (T*)p_home, x_prev, fista_y, beta_tab, beta_idx, st);
     return cudaGetLastError();
   }
   const size_t n = d.n();
@@ -233,7 +238,7 @@ cudaError_t fgp_finalize_t(const Dims& d, const float* z, const void* p, float l
   if (blocks > 152 * 16) blocks = 152 * 16;
   launch_kernel(fgp_finalize_kernel<T, NN>, dim3(blocks), dim3(256), 0, s, z, (const T*)p, d.nz, d.ny, d.nx, d.ndim, lam,
                                                     x_out, h_out, h_coef, (T*)p_home, x_prev,
-                                                    fista_y, beta_tab, beta_idx, IndexMap(d.nz, d.ny, d.nx));
+                                                    fista_y, beta_tab, beta_idx, IndexMap(d.nz, d.ny, d.nx), st);
   return cudaGetLastError();
 }
 
@@ -253,7 +258,7 @@ cudaError_t launch_fgp_iter(const Dims& d, const float* z, const void* pc, const
 
 cudaError_t launch_fgp_finalize_pd1(const Dims& d, const float* z, const void* p, int dtype, float lam,
                                     bool nonneg, float prob_p, float* x, float* xh, void* p_home,
-                                    cudaStream_t s) {
+                                    InnerStamp st, cudaStream_t s) {
   const size_t n = d.n();
   if (n == 0) return cudaSuccess;
   int blocks = (int)((n + 255) / 256);
@@ -261,10 +266,10 @@ cudaError_t launch_fgp_finalize_pd1(const Dims& d, const float* z, const void* p
 #define TVS_PD1(T_)                                                                                   \
   if (nonneg)                                                                                         \
     launch_kernel(fgp_finalize_pd1_kernel<T_, true>, dim3(blocks), dim3(256), 0, s, z, (const T_*)p, d.ny, d.nx, lam, prob_p, x, xh, \
-                                                             (T_*)p_home, IndexMap(1, d.ny, d.nx));   \
+                                                             (T_*)p_home, IndexMap(1, d.ny, d.nx), st); \
   else                                                                                                \
     launch_kernel(fgp_finalize_pd1_kernel<T_, false>, dim3(blocks), dim3(256), 0, s, z, (const T_*)p, d.ny, d.nx, lam, prob_p, x, xh, \
-                                                              (T_*)p_home, IndexMap(1, d.ny, d.nx));
+                                                              (T_*)p_home, IndexMap(1, d.ny, d.nx), st);
   if (dtype == DUAL_F32) {
     TVS_PD1(float)
   } else if (dtype == DUAL_BF16) {
@@ -281,12 +286,12 @@ cudaError_t launch_fgp_finalize_pd1(const Dims& d, const float* z, const void* p
 cudaError_t launch_fgp_finalize(const Dims& d, const float* z, const void* p, int dtype, float lam,
                                 bool nonneg, float* x_out, float* h_out, float h_coef,
                                 void* p_home, const float* x_prev, float* fista_y,
-                                const float* beta_tab, const int* beta_idx, cudaStream_t s) {
+                                const float* beta_tab, const int* beta_idx, InnerStamp st, cudaStream_t s) {
   if (d.n() == 0) return cudaSuccess;
   return with_dual_type(dtype, [&](auto tag) {
     using T = typename decltype(tag)::type;
-    return nonneg ? fgp_finalize_t<T, true>(d, z, p, lam, x_out, h_out, h_coef, p_home, x_prev, fista_y, beta_tab, beta_idx, s)
-                  : fgp_finalize_t<T, false>(d, z, p, lam, x_out, h_out, h_coef, p_home, x_prev, fista_y, beta_tab, beta_idx, s);
+    return nonneg ? fgp_finalize_t<T, true>(d, z, p, lam, x_out, h_out, h_coef, p_home, x_prev, fista_y, beta_tab, beta_idx, st, s)
+                  : fgp_finalize_t<T, false>(d, z, p, lam, x_out, h_out, h_coef, p_home, x_prev, fista_y, beta_tab, beta_idx, st, s);
   });
 }
 

@@ -74,6 +74,14 @@ struct IndexMap {
 struct Partial {
   float s, c;
 };
+// Timing of the inner iterations of a solve's prox calls: a pair of device times
+// per call, arr[2c] at the start of the inner iterations and arr[2c + 1] at their
+// end, c = *ctr, which the end stamp advances.  arr == null: no stamp.
+struct InnerStamp {
+  unsigned long long* arr;
+  int* ctr;
+};
+
 inline size_t dual_elem_bytes(int t) { return t == DUAL_F32 ? 4 : 2; }
 
 // ---- TV prox (fgp.cu, fgp_tb.cu, fgp3d.cu) ----
@@ -91,7 +99,7 @@ bool fgp3d_take_wait_timeouts();
 // PDHGSkip-1 finalisation: u = P_X(z + lam div p); xh = (u - x)/prob_p; x += prob_p xh.
 cudaError_t launch_fgp_finalize_pd1(const Dims& d, const float* z, const void* p, int dtype, float lam,
                                     bool nonneg, float prob_p, float* x, float* xh, void* p_home,
-                                    cudaStream_t s);
+                                    InnerStamp st, cudaStream_t s);
 // Temporally blocked inner iterations (2D): tile-shape / depth configuration.
 // tb <= 1 selects the one-iteration kernel.  A launch of the blocked kernel runs
 // `iters` <= tb iterations from (pc = p_k, pp = p_{k-1}) and writes
@@ -108,18 +116,19 @@ cudaError_t fgp_prepare_device();
 cudaError_t launch_fgp_block(const FgpConfig& c, const Dims& d, const float* z, const void* pc,
                              const void* pp, void* pn, void* pnp, float lam, float inv_step,
                              const float* betas, int iters, int dtype, bool nonneg, cudaStream_t s);
-// x_out = P_X(z + lam div p); if h_out: h_out = h_coef (x_out - z);
-// if p_home: p_home = p.  When fista_y is set: fista_y = x_out + beta (x_out - x_prev) with
-// beta = beta_tab[*beta_idx] (FISTA extrapolation, read on the device).
 // ROF duality-gap partials of a unit-ball dual p (rof_gap_blocks(n) of them):
 // lam * their sum = P(u) - D(p) at u = z + lam div p.
 int rof_gap_blocks(size_t n);
 cudaError_t launch_rof_gap_partials(const Dims& d, const float* z, const void* p, int dtype, float lam,
                                     Partial* part, cudaStream_t s);
+// x_out = P_X(z + lam div p); if h_out: h_out = h_coef (x_out - z);
+// if p_home: p_home = p.  When fista_y is set: fista_y = x_out + beta (x_out - x_prev) with
+// beta = beta_tab[*beta_idx] (FISTA extrapolation, read on the device).
+// st: the end stamp of the inner iterations before it (InnerStamp).
 cudaError_t launch_fgp_finalize(const Dims& d, const float* z, const void* p, int dtype, float lam,
                                 bool nonneg, float* x_out, float* h_out, float h_coef,
                                 void* p_home, const float* x_prev, float* fista_y,
-                                const float* beta_tab, const int* beta_idx, cudaStream_t s);
+                                const float* beta_tab, const int* beta_idx, InnerStamp st, cudaStream_t s);
 
 // ---- objective pieces and pointwise steps (ops.cu) ----
 struct BlurW {
@@ -189,8 +198,8 @@ cudaError_t launch_dist_partials(size_t n, const float* x, const float* u_ref, P
 cudaError_t launch_dist_record(const Partial* part, int n_part, double ref_norm2, double* dist, double target,
                                int* flags, int* done_host, cudaStream_t s);
 cudaError_t launch_timestamp(unsigned long long* ts, cudaStream_t s);
-// arr[2 * (*ctr) + which] = now; when which == 1 also (*ctr)++.
-cudaError_t launch_timestamp_pair(unsigned long long* arr, int* ctr, int which, cudaStream_t s);
+// The start stamp of an InnerStamp as a launch of its own (st.arr[2 * *st.ctr] = now).
+cudaError_t launch_inner_start_stamp(const InnerStamp& st, cudaStream_t s);
 cudaError_t launch_count_nonfinite(const float* x, size_t n, int* count, cudaStream_t s);
 cudaError_t launch_coin_schedule(uint64_t seed, double p, int64_t k0, int K, unsigned char* out,
                                  cudaStream_t s);

@@ -144,7 +144,7 @@ extern "C" tvs_status tv_prox_noalloc(int ndim, const int dims[3], const float* 
   }
   if (launch_fgp_finalize(d, z, buf[fin], dual, use ? lam : 0.f, nonneg != 0, u, nullptr, 0.f,
                           (fin != 0 && dual_state) ? dual_state : nullptr, nullptr, nullptr, nullptr,
-                          nullptr, s) != cudaSuccess)
+                          nullptr, InnerStamp{}, s) != cudaSuccess)
     return TVS_ECUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return TVS_ECUDA;
   return TVS_OK;

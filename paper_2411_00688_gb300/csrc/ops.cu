@@ -222,11 +222,11 @@ dist_record_kernel(const Partial* __restrict__ part, int n_part, double ref_norm
 __global__ void timestamp_kernel(unsigned long long* ts) {
   pdl_enter(); *ts = globaltimer_ns(); }
 
-__global__ void timestamp_pair_kernel(unsigned long long* arr, int* ctr, int which) {
+// Start stamp of an InnerStamp; the finalisation after the inner iterations
+// writes the end stamp.
+__global__ void inner_start_stamp_kernel(unsigned long long* arr, const int* ctr) {
   pdl_enter();
-  const int c = *ctr;
-  arr[2 * c + which] = globaltimer_ns();
-  if (which == 1) *ctr = c + 1;
+  arr[2 * *ctr] = globaltimer_ns();
 }
 
 __global__ void count_nonfinite_kernel(const float* __restrict__ x, size_t n, int* count) {
@@ -390,8 +390,8 @@ cudaError_t launch_timestamp(unsigned long long* ts, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_timestamp_pair(unsigned long long* arr, int* ctr, int which, cudaStream_t s) {
-  launch_kernel(timestamp_pair_kernel, dim3(1), dim3(1), 0, s, arr, ctr, which);
+cudaError_t launch_inner_start_stamp(const InnerStamp& st, cudaStream_t s) {
+  launch_kernel(inner_start_stamp_kernel, dim3(1), dim3(1), 0, s, st.arr, (const int*)st.ctr);
   return cudaGetLastError();
 }
 
