@@ -292,16 +292,6 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   return t;
 }
 
-// End stamp of an InnerStamp, by the first thread of the first block of the kernel
-// that follows the inner iterations (after pdl_enter(): they have completed).
-__device__ __forceinline__ void stamp_inner_end(const InnerStamp& st) {
-  if (st.arr && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
-    const int c = *st.ctr;
-    st.arr[2 * c + 1] = globaltimer_ns();
-    *st.ctr = c + 1;
-  }
-}
-
 // Isotropic TV term of one pixel, |(D x)_i| = sqrt(dz^2 + dy^2 + dx^2), with one
 // fixed rounding sequence so that every kernel produces identical per-pixel terms
 // (dz = 0 for images: fma(0, 0, t) = t exactly).

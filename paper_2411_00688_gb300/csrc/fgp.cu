@@ -23,6 +23,17 @@ namespace tvs {
 
 namespace {
 
+// End stamp of an InnerStamp, by the first thread of the first block of the kernel
+// that follows the inner iterations (after pdl_enter(): they have completed).
+__device__ __forceinline__ void stamp_inner_end(const InnerStamp& st) {
+  if (st.arr && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+    const int c = *st.ctr;
+    st.arr[2 * c + 1] = globaltimer_ns();
+    *st.ctr = c + 1;
+  }
+}
+
+
 constexpr int TX2 = 32, TY2 = 16, NT2 = 256;
 
 template <typename T, bool NONNEG>

@@ -348,6 +348,43 @@ def test_resume_equals_uninterrupted_proxskip(tvs, ctx):
     np.testing.assert_allclose(np.concatenate([tb.objective, tc.objective]), ta.objective, rtol=1e-12)
 
 
+def test_chunk_graphs_equal_single_iteration_graphs(tvs, ctx):
+    """A solve of 13 iterations runs three four-iteration chunk graphs and one
+    single-iteration graph; 13 resumed solves of one iteration each run only
+    single-iteration graphs.  Both give the same iterates, bit for bit, for every
+    solver family whose outer loop launches chunks."""
+    b32, _ = _data((48, 56), "blur", 102, 0.02)
+    prob = tvs.Problem(ctx, cuda(b32), 0.03, op="blur", blur_sigma=2.0)
+    K, N = 13, 6
+    xa, ta = tvs.proxskip_solve(prob, cuda(b32), 1.0, 0.4, 23, K, N)
+    x = cuda(b32)
+    coins = []
+    for k in range(K):
+        x, t = tvs.proxskip_solve(prob, x, 1.0, 0.4, 23, 1, N, resume=k > 0, k0=k)
+        coins += list(t.coins)
+    np.testing.assert_array_equal(host(x), host(xa))
+    assert coins == list(ta.coins)
+    # PGD (every coin 1) against PGD in pieces: the warm dual carries over as resume keeps it
+    xa, _ = tvs.pgd_solve(prob, cuda(b32), 1.0, K, N)
+    x = cuda(b32)
+    for k in range(K):
+        x, _ = tvs.pgd_solve(prob, x, 1.0, 1, N, resume=k > 0, k0=k)
+    np.testing.assert_array_equal(host(x), host(xa))
+    Nc, na, nd = 32, 40, 45
+    geom, c32, c64, oprob, L = _ct_setup(Nc, na, nd, 56, 0.002)
+    st = 0.99 / math.sqrt(L)
+    cprob = tvs.Problem(ctx, cuda(c32), 0.002, op="ct", shape=(Nc, Nc), n_angles=na, n_det=nd,
+                        pixel_size=1.0 / Nc, det_spacing=1.0 / Nc)
+    z = np.zeros((Nc, Nc), dtype=np.float32)
+    y0 = np.zeros((na, nd), dtype=np.float32)
+    xa, ya, _ = tvs.pdhgskip_solve(cprob, cuda(z), cuda(y0), st, st, 0.5, 4, K, N)
+    x, y = cuda(z), cuda(y0)
+    for k in range(K):
+        x, y, _ = tvs.pdhgskip_solve(cprob, x, y, st, st, 0.5, 4, 1, N, resume=k > 0, k0=k)
+    np.testing.assert_array_equal(host(x), host(xa))
+    np.testing.assert_array_equal(host(y), host(ya))
+
+
 def test_resume_equals_uninterrupted_pdhgskip(tvs, ctx):
     N, na, nd = 40, 48, 57
     geom, b32, b64, oprob, L = _ct_setup(N, na, nd, 55, 0.002)
