@@ -63,9 +63,10 @@ FGP3_TRAFFIC = {"f32": dict(_FGP3_SRC, bytes=5397339439),
                 "bf16": dict(_FGP3_SRC, bytes=2951982612),
                 "q15": dict(_FGP3_SRC, bytes=2961351639)}
 # Iterations this workload's ProxSkip solve needs to reach the target on the GPU
-# (its trace: 261 iterations); the reference arm extrapolates the oracle to them,
-# counting the prox calls among them from the coin schedule.
-REF_ITERS_DEFAULT = 261
+# (its trace: 265 iterations to the 1e-4 gap against the oracle's F*); the reference
+# arm extrapolates the oracle to them, counting the prox calls among them from the
+# coin schedule.
+REF_ITERS_DEFAULT = 265
 FSTAR_GOLDEN = os.path.join(ROOT, "tests", "golden", "fstar_deblur2d_1024.json")
 
 

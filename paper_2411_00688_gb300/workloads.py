@@ -12,6 +12,8 @@ benchmark's headline one (python -m paper_2411_00688_gb300.workloads NAME ...).
   table1_deblur2d_1024  Table 1's solvers (FISTA-100, ISTA-10, ProxSkip-10 p = 0.5, ProxSkip-100
                  p = 0.05) to a 1e-5 relative distance from u*
   dual_huber_200x300    ProjGD, AProjGD and ProxSkip on Dual-Huber-ROF (Section 2.2)
+  iteration_split_deblur2d_1024  device time of skipped and prox outer iterations of the
+                 ProxSkip solve (trace timestamps), p = 0.5 and 0.02
 
 Each prints one JSON line per solver: iterations and prox calls to a 1e-4
 relative objective gap, device time to the target and wall time of the solve.
@@ -229,6 +231,40 @@ def deblur2d_1024():
     return out
 
 
+def iteration_split_deblur2d_1024():
+    """Where an outer iteration's time goes in the ProxSkip solve of the deblurring
+    workload (50 inner iterations, no stopping target): from the trace's device
+    timestamps, the median time between the objective records of two consecutive
+    skipped iterations, and between the record of a prox iteration and the next
+    one, with the inner iterations' share of a prox call; at p = 0.5 (the
+    benchmark's probability) and at p = 0.02 (almost every iteration skipped)."""
+    import statistics
+    import torch
+    from synth.configs import DeblurConfig
+    tvs, ctx = _ctx()
+    cfg = DeblurConfig()
+    truth = torch.from_numpy(cfg.phantom().astype(np.float32)).cuda()
+    noise = torch.from_numpy(cfg.noise().astype(np.float32)).cuda()
+    prob = tvs.Problem(ctx, truth, cfg.alpha, op="blur", blur_sigma=cfg.blur_sigma)
+    b = torch.empty_like(truth)
+    tvs.tvs_op_apply(prob, truth, b)
+    b = (b + noise).contiguous()
+    prob.set_data(b)
+    out = []
+    for p, K in ((0.5, 300), (0.02, 600)):
+        for _ in range(3):  # the last of three solves (graphs captured, clocks up)
+            _, tr = tvs.proxskip_solve(prob, b.clone(), 1.0, p, cfg.seed, K, cfg.n_inner)
+        t, c, n = tr.t_s, tr.coins, tr.iters_run
+        skip = [t[k + 1] - t[k] for k in range(n - 1) if c[k] == 0 and c[k + 1] == 0]
+        prox = [t[k + 1] - t[k] for k in range(n - 1) if c[k] == 1]
+        out.append({"workload": cfg.name, "p": p, "iterations": n, "prox_calls": tr.prox_calls,
+                    "solve_ms": tr.solve_ms,
+                    "skipped_iteration_us": statistics.median(skip) * 1e6 if skip else None,
+                    "prox_iteration_us": statistics.median(prox) * 1e6 if prox else None,
+                    "inner_us_per_prox": tr.fgp_ms / max(tr.prox_calls, 1) * 1e3})
+    return out
+
+
 def denoise3d_512(duals=("f32", "bf16", "f16", "q15")):
     import torch
     from synth.configs import Denoise3DConfig
@@ -390,7 +426,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("workload", choices=["denoise2d_256", "ct2d_512", "denoise3d_512", "batch2d_256",
                                          "deblur2d_1024", "table1_deblur2d_1024", "dual_huber_200x300",
-                                         "ct2d_512_sweep"])
+                                         "ct2d_512_sweep", "iteration_split_deblur2d_1024"])
     ap.add_argument("--problems", type=int, default=None)
     ap.add_argument("--iters", type=int, default=None)
     ap.add_argument("--batch-only", action="store_true", help="batch2d_256: time the batched solve only")
@@ -401,7 +437,8 @@ def main(argv=None):
     else:
         recs = {"denoise2d_256": denoise2d_256, "ct2d_512": ct2d_512, "denoise3d_512": denoise3d_512,
                 "deblur2d_1024": deblur2d_1024, "table1_deblur2d_1024": table1_deblur2d_1024,
-                "dual_huber_200x300": dual_huber_200x300, "ct2d_512_sweep": ct2d_512_sweep}[args.workload]()
+                "dual_huber_200x300": dual_huber_200x300, "ct2d_512_sweep": ct2d_512_sweep,
+                "iteration_split_deblur2d_1024": iteration_split_deblur2d_1024}[args.workload]()
     for r in recs:
         print(json.dumps(r), flush=True)
 
