@@ -1073,28 +1073,30 @@ tvs_status pd1_solve(tvs_problem* P, const tvs_pd_params* prm, float* x_io, floa
                                prm->f_star, prm->target_rel_gap, prm->target_rel_dist, (double)fcfg.tb,
                                (double)fcfg.cpl, (double)fcfg.rpw},
                               &fresh);
+  // one outer iteration (x is updated in place: both parities are the same work)
+  const IterBody body = [&](int c, int) -> tvs_status {
+    CUDA_TRY(launch_reduce_record(P->part_a, na, P->part_b, nb, alpha, every, P->obj_dev, P->ts_dev,
+                                  prm->f_star, prm->target_rel_gap, P->flags, P->done_host_dev, nullptr, s));
+    TVS_TRY(track_distance(P, x, prm->target_rel_dist, s));
+    if (c == 0) {
+      CUDA_TRY(launch_pd1_dual_pointwise(P->m, nullptr, P->axp, P->y, P->b, (float)p, (float)tau, nullptr, s));
+      return TVS_OK;
+    }
+    TVS_TRY(pd_backward(P, x, P->z, nullptr, (float)sigma, 0.f, s, false));
+    int fin = 0;
+    CUDA_TRY(launch_inner_start_stamp(inner_stamp(P), s));
+    if (use_prox) TVS_TRY(launch_fgp_sequence(fcfg, d, P->z, P->dual, N, betas, lam, dtype, nonneg, s, &fin));
+    CUDA_TRY(launch_fgp_finalize_pd1(d, P->z, P->dual[fin], dtype, use_prox ? lam : 0.f, nonneg, (float)p, x,
+                                     P->h, fin != 0 ? P->dual[0] : nullptr, inner_stamp(P), s));
+    TVS_TRY(pd1_forward(P, P->h, (float)p, (float)tau, s));
+    CUDA_TRY(launch_tv_partials(d, x, P->part_b, s));
+    return TVS_OK;
+  };
   if (fresh) {
     const tvs_status cst = [&]() -> tvs_status {
-      for (int c = 0; c < 2; ++c) {
-        TVS_TRY(capture(s, &G.exec[c][0], [&]() -> tvs_status {
-          CUDA_TRY(launch_reduce_record(P->part_a, na, P->part_b, nb, alpha, every, P->obj_dev, P->ts_dev,
-                                        prm->f_star, prm->target_rel_gap, P->flags, P->done_host_dev, nullptr, s));
-          TVS_TRY(track_distance(P, x, prm->target_rel_dist, s));
-          if (c == 0) {
-            CUDA_TRY(launch_pd1_dual_pointwise(P->m, nullptr, P->axp, P->y, P->b, (float)p, (float)tau, nullptr, s));
-            return TVS_OK;
-          }
-          TVS_TRY(pd_backward(P, x, P->z, nullptr, (float)sigma, 0.f, s, false));
-          int fin = 0;
-          CUDA_TRY(launch_inner_start_stamp(inner_stamp(P), s));
-          if (use_prox) TVS_TRY(launch_fgp_sequence(fcfg, d, P->z, P->dual, N, betas, lam, dtype, nonneg, s, &fin));
-          CUDA_TRY(launch_fgp_finalize_pd1(d, P->z, P->dual[fin], dtype, use_prox ? lam : 0.f, nonneg, (float)p, x,
-                                           P->h, fin != 0 ? P->dual[0] : nullptr, inner_stamp(P), s));
-          TVS_TRY(pd1_forward(P, P->h, (float)p, (float)tau, s));
-          CUDA_TRY(launch_tv_partials(d, x, P->part_b, s));
-          return TVS_OK;
-        }));
-      }
+      for (int c = 0; c < 2; ++c)
+        for (int par = 0; par < 2; ++par)
+          TVS_TRY(capture(s, &G.exec[c][par], [&]() -> tvs_status { return body(c, par); }));
       return TVS_OK;
     }();
     if (cst != TVS_OK) {
@@ -1103,17 +1105,7 @@ tvs_status pd1_solve(tvs_problem* P, const tvs_pd_params* prm, float* x_io, floa
     }
   }
   LoopState ls;
-  for (int k = 0; k < K; ++k) {
-    if (k >= LAG) {
-      CUDA_TRY(cudaEventSynchronize(C->ring[k % LAG]));
-      if (*(volatile int*)P->done_host) break;
-    }
-    const int cc = coins[k] ? 1 : 0;
-    CUDA_TRY(cudaGraphLaunch(G.exec[cc][0], s));
-    CUDA_TRY(cudaEventRecord(C->ring[k % LAG], s));
-    ls.iters = k + 1;
-    ls.prox += cc;
-  }
+  TVS_TRY(run_loop(P, K, coins, G, &ls, &body));
   if (ls.iters > 0) {
     CUDA_TRY(launch_reduce_record(P->part_a, na, P->part_b, nb, alpha, 1, P->obj_dev, P->ts_dev, prm->f_star,
                                   prm->target_rel_gap, P->flags, P->done_host_dev, nullptr, s));
@@ -1600,17 +1592,34 @@ tvs_status batch_solve_in_order(tvs_ctx* C, int n, tvs_problem* const* probs, co
   CUDA_TRY(launch_batch_init(L, mem == TVS_MEM_DEVICE ? (const float* const*)B->x_dev_list : nullptr, K, s));
   CUDA_TRY(cudaEventRecord(C->ev_start, s));
   CUDA_TRY(launch_timestamp(B->t0_dev, s));
+  // iterations in runs of CHUNK per graph launch (one chunk graph: the batch's
+  // coins are drawn on the device), CHUNK_DEPTH launches ahead of the device
   int launched = 0;
-  for (int k = 0; k < K; ++k) {
-    if (k >= LAG) {
-      CUDA_TRY(cudaEventSynchronize(C->ring[k % LAG]));
+  for (int j = 0; launched < K; ++j) {
+    if (j >= CHUNK_DEPTH) {
+      CUDA_TRY(cudaEventSynchronize(C->ring[(j - CHUNK_DEPTH) % LAG]));
       int ndone = 0;
       for (int i = 0; i < n; ++i) ndone += ((volatile int*)S.done_host)[i];
       if (ndone == n) break;
     }
-    CUDA_TRY(cudaGraphLaunch(B->G.exec[1][k & 1], s));
-    CUDA_TRY(cudaEventRecord(C->ring[k % LAG], s));
-    launched = k + 1;
+    if (launched % CHUNK == 0 && K - launched >= CHUNK) {
+      if (!B->G.chunk[0]) {
+        const tvs_status st = capture(s, &B->G.chunk[0], [&]() -> tvs_status {
+          for (int i = 0; i < CHUNK; ++i) CUDA_TRY(launch_batch_iteration(L, i & 1, s));
+          return TVS_OK;
+        });
+        if (st != TVS_OK) {
+          B->G.chunk[0] = nullptr;
+          return st;
+        }
+      }
+      CUDA_TRY(cudaGraphLaunch(B->G.chunk[0], s));
+      launched += CHUNK;
+    } else {
+      CUDA_TRY(cudaGraphLaunch(B->G.exec[1][launched & 1], s));
+      launched += 1;
+    }
+    CUDA_TRY(cudaEventRecord(C->ring[j % LAG], s));
   }
   CUDA_TRY(launch_batch_final_objective(L, launched & 1, s));
   CUDA_TRY(cudaEventRecord(C->ev_stop, s));

@@ -352,7 +352,8 @@ def test_chunk_graphs_equal_single_iteration_graphs(tvs, ctx):
     """A solve of 13 iterations runs three four-iteration chunk graphs and one
     single-iteration graph; 13 resumed solves of one iteration each run only
     single-iteration graphs.  Both give the same iterates, bit for bit, for every
-    solver family whose outer loop launches chunks."""
+    solver family whose outer loop launches chunks (ProxSkip, PGD, PDHGSkip-2,
+    PDHGSkip-1)."""
     b32, _ = _data((48, 56), "blur", 102, 0.02)
     prob = tvs.Problem(ctx, cuda(b32), 0.03, op="blur", blur_sigma=2.0)
     K, N = 13, 6
@@ -377,12 +378,13 @@ def test_chunk_graphs_equal_single_iteration_graphs(tvs, ctx):
                         pixel_size=1.0 / Nc, det_spacing=1.0 / Nc)
     z = np.zeros((Nc, Nc), dtype=np.float32)
     y0 = np.zeros((na, nd), dtype=np.float32)
-    xa, ya, _ = tvs.pdhgskip_solve(cprob, cuda(z), cuda(y0), st, st, 0.5, 4, K, N)
-    x, y = cuda(z), cuda(y0)
-    for k in range(K):
-        x, y, _ = tvs.pdhgskip_solve(cprob, x, y, st, st, 0.5, 4, 1, N, resume=k > 0, k0=k)
-    np.testing.assert_array_equal(host(x), host(xa))
-    np.testing.assert_array_equal(host(y), host(ya))
+    for fn in (tvs.pdhgskip_solve, tvs.pdhgskip1_solve):
+        xa, ya, _ = fn(cprob, cuda(z), cuda(y0), st, st, 0.5, 4, K, N)
+        x, y = cuda(z), cuda(y0)
+        for k in range(K):
+            x, y, _ = fn(cprob, x, y, st, st, 0.5, 4, 1, N, resume=k > 0, k0=k)
+        np.testing.assert_array_equal(host(x), host(xa))
+        np.testing.assert_array_equal(host(y), host(ya))
 
 
 def test_resume_equals_uninterrupted_pdhgskip(tvs, ctx):
