@@ -88,7 +88,7 @@ def test_prox_scratch_failure_then_success(tvs, clean_env):
         ctx.close()
 
 
-@pytest.mark.parametrize("solver", ["proxskip", "pdhg"])
+@pytest.mark.parametrize("solver", ["proxskip", "pdhg", "pdhgskip1"])
 def test_solve_time_limit(tvs, clean_env, solver):
     ctx = tvs.Context(0)
     try:
@@ -98,9 +98,12 @@ def test_solve_time_limit(tvs, clean_env, solver):
         with pytest.raises(tvs.TVSError) as ei:
             if solver == "proxskip":
                 tvs.proxskip_solve(prob, b.clone(), 1.0, 0.5, 1, 200000, 20)
-            else:
+            elif solver == "pdhg":
                 import torch
                 tvs.pdhg_solve(prob, b.clone(), torch.zeros_like(b), 0.9, 0.9, 200000, 20)
+            else:
+                import torch
+                tvs.pdhgskip1_solve(prob, b.clone(), torch.zeros_like(b), 0.9, 0.9, 0.5, 1, 200000, 20)
         assert ei.value.status == 5      # TVS_ETIMEDOUT
         os.environ.pop("TVS_SOLVE_TIMEOUT_MS")
         x, tr = tvs.proxskip_solve(prob, b.clone(), 1.0, 0.5, 1, 10, 5)
