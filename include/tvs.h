@@ -44,7 +44,8 @@ typedef enum {
   TVS_ENUMERIC = 4,      /* non-finite value in an input or in the objective */
   TVS_ETIMEDOUT = 5,     /* a solve passed its wall-clock limit (the
                             TVS_SOLVE_TIMEOUT_MS environment variable, in ms;
-                            PGD, FISTA, ProxSkip, PDHG, PDHGSkip-2): it stopped
+                            PGD, FISTA, ProxSkip, PDHG, PDHGSkip-2,
+                            PDHGSkip-1, explicit PDHG): it stopped
                             launching iterations and cleaned up; or a 3D inner
                             kernel gave up (after 2 s) waiting for a tile load
                             and left part of its output unwritten              */
