@@ -235,8 +235,9 @@ def iteration_split_deblur2d_1024():
     """Where an outer iteration's time goes in the ProxSkip solve of the deblurring
     workload (50 inner iterations, no stopping target): from the trace's device
     timestamps, the median time between the objective records of two consecutive
-    skipped iterations, and between the record of a prox iteration and the next
-    one, with the inner iterations' share of a prox call; at p = 0.5 (the
+    skipped iterations and of two consecutive prox iterations (whose records run
+    beside the inner iterations, so only two records made the same way are
+    compared), with the inner iterations' time per prox call; at p = 0.5 (the
     benchmark's probability) and at p = 0.02 (almost every iteration skipped)."""
     import statistics
     import torch
@@ -256,7 +257,7 @@ def iteration_split_deblur2d_1024():
             _, tr = tvs.proxskip_solve(prob, b.clone(), 1.0, p, cfg.seed, K, cfg.n_inner)
         t, c, n = tr.t_s, tr.coins, tr.iters_run
         skip = [t[k + 1] - t[k] for k in range(n - 1) if c[k] == 0 and c[k + 1] == 0]
-        prox = [t[k + 1] - t[k] for k in range(n - 1) if c[k] == 1]
+        prox = [t[k + 1] - t[k] for k in range(n - 1) if c[k] == 1 and c[k + 1] == 1]
         out.append({"workload": cfg.name, "p": p, "iterations": n, "prox_calls": tr.prox_calls,
                     "solve_ms": tr.solve_ms,
                     "skipped_iteration_us": statistics.median(skip) * 1e6 if skip else None,
