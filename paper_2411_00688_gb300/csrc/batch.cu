@@ -39,7 +39,7 @@ __device__ __forceinline__ bool active(const BatchState& st) { return st.done ==
 // skip), partials of 1/2 ||A x - b||^2 and TV(x).  write_out = 0: partials only
 // (the final objective; the coin is not read).
 template <int R>
-__global__ void __launch_bounds__(FNT)
+__global__ void __launch_bounds__(FNT, 4)
 batch_blur_fb_kernel(const BatchProb* __restrict__ probs, BatchState* __restrict__ state,
                      const int4* __restrict__ tiles, const unsigned char* __restrict__ coins, int n,
                      const int* __restrict__ kctr, int par, int write_out, Partial* part_a, Partial* part_b) {

@@ -133,12 +133,18 @@ __device__ __forceinline__ float2 fb_taps(const float2* v, const float* wk, floa
   }
 }
 
-template <int R>
-__device__ __forceinline__ void blur_fb_step_body(const float* __restrict__ x, const float* __restrict__ b,
-                                                  const float* __restrict__ h, float* __restrict__ out, int H,
-                                                  int W, const BlurW& w, float gamma, float ch,
-                                                  Partial* __restrict__ part_a, Partial* __restrict__ part_b,
-                                                  int tile_x, int tile_y, int part_index) {
+// IN: the staged region (rows i0 - 2R .. i0 + FY + 2R, columns j0 - 2R ..
+// j0 - 2R + 63) lies inside the image, so no index is reflected, every residual
+// cell is in the image and no Neumann mask of the TV term applies; the checks are
+// dropped and the arithmetic is unchanged.
+template <int R, bool IN>
+__device__ __forceinline__ void blur_fb_step_body_impl(const float* __restrict__ x, const float* __restrict__ b,
+                                                       const float* __restrict__ h, float* __restrict__ out, int H,
+                                                       int W, const BlurW& w, float gamma, float ch,
+                                                       Partial* __restrict__ part_a, Partial* __restrict__ part_b,
+                                                       int tile_x, int tile_y, int part_index,
+                                                       float2 (*__restrict__ sx)[32], float2 (*__restrict__ sh)[32],
+                                                       float2 (*__restrict__ sr)[32]) {
   constexpr int FX = fb_tile_w(R), FY = fb_tile_h(R);
   constexpr int XR = FY + 4 * R;                   // staged x: rows i0-2R .., columns j0-2R .. j0-2R+63
   constexpr int RR = FY + 2 * R;                   // residual region rows i0-R .., columns j0-R .. j0+FX+R
@@ -147,21 +153,21 @@ __device__ __forceinline__ void blur_fb_step_body(const float* __restrict__ x, c
   constexpr int VR = (RR + NW - 1) / NW;           // residual rows per warp (vertical pass)
   constexpr int VO = FY / NW;                      // output rows per warp (final pass)
   static_assert(FY % NW == 0 && R >= 1 && R <= 8, "tile layout");
-  __shared__ float2 sx[XR][32];
-  __shared__ float2 sh[XR][32];  // horizontal pass of x, later of r
-  __shared__ float2 sr[RR][32];
+  // shared memory (the caller's): sx[XR] staged x, sh[XR] horizontal pass of x and
+  // later of r, sr[RR] the residual
   float wk[2 * R + 1];
 #pragma unroll
   for (int k = 0; k <= 2 * R; ++k) wk[k] = w.w[k];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int j0 = tile_x * FX, i0 = tile_y * FY;
   {
-    const int gj0 = reflect_index(j0 - 2 * R + 2 * lane, W), gj1 = reflect_index(j0 - 2 * R + 2 * lane + 1, W);
+    const int gj0 = IN ? j0 - 2 * R + 2 * lane : reflect_index(j0 - 2 * R + 2 * lane, W);
+    const int gj1 = IN ? gj0 + 1 : reflect_index(j0 - 2 * R + 2 * lane + 1, W);
 #pragma unroll
     for (int t = 0; t < (XR + NW - 1) / NW; ++t) {
       const int a = wp + NW * t;
       if (a < XR) {
-        const float* row = x + (size_t)reflect_index(i0 - 2 * R + a, H) * W;
+        const float* row = x + (size_t)(IN ? i0 - 2 * R + a : reflect_index(i0 - 2 * R + a, H)) * W;
         sx[a][lane] = make_float2(__ldg(row + gj0), __ldg(row + gj1));
       }
     }
@@ -171,11 +177,11 @@ __device__ __forceinline__ void blur_fb_step_body(const float* __restrict__ x, c
   float2 bv[VR];
   {
     const int a0 = wp * VR, gj = j0 - R + 2 * lane;
-    const bool cin0 = gj >= 0 && gj < W, cin1 = gj + 1 >= 0 && gj + 1 < W;
+    const bool cin0 = IN || (gj >= 0 && gj < W), cin1 = IN || (gj + 1 >= 0 && gj + 1 < W);
 #pragma unroll
     for (int t = 0; t < VR; ++t) {
       const int gi = i0 - R + a0 + t;
-      const bool rin = lane < RP && a0 + t < RR && gi >= 0 && gi < H;
+      const bool rin = lane < RP && a0 + t < RR && (IN || (gi >= 0 && gi < H));
       const float* brow = b + (size_t)(rin ? gi : 0) * W;
       bv[t] = make_float2(rin && cin0 ? __ldg(brow + gj) : 0.f, rin && cin1 ? __ldg(brow + gj + 1) : 0.f);
     }
@@ -202,13 +208,13 @@ __device__ __forceinline__ void blur_fb_step_body(const float* __restrict__ x, c
 #pragma unroll
     for (int t = 0; t < VR + 2 * R; ++t) win[t] = a0 + t < XR ? sh[a0 + t][lane] : make_float2(0.f, 0.f);
     const int gj = j0 - R + 2 * lane;  // global column of the pair's left cell
-    const bool cin0 = gj >= 0 && gj < W, cin1 = gj + 1 >= 0 && gj + 1 < W;
+    const bool cin0 = IN || (gj >= 0 && gj < W), cin1 = IN || (gj + 1 >= 0 && gj + 1 < W);
     const bool own0 = 2 * lane >= R && 2 * lane < R + FX, own1 = 2 * lane + 1 >= R && 2 * lane + 1 < R + FX;
 #pragma unroll
     for (int t = 0; t < VR; ++t) {
       const int a = a0 + t;
       const int gi = i0 - R + a;
-      if (a >= RR || gi < 0 || gi >= H) continue;
+      if (a >= RR || (!IN && (gi < 0 || gi >= H))) continue;
       float2 v = make_float2(0.f, 0.f);
 #pragma unroll
       for (int k = 0; k <= 2 * R; ++k) v = __ffma2_rn(make_float2(wk[k], wk[k]), win[t + k], v);
@@ -224,7 +230,7 @@ __device__ __forceinline__ void blur_fb_step_body(const float* __restrict__ x, c
   }
   __syncthreads();
   // ring cells outside the image take their mirror cell's residual
-  if (i0 < R || j0 < R || i0 + FY + R > H || j0 + FX + R > W) {
+  if (!IN && (i0 < R || j0 < R || i0 + FY + R > H || j0 + FX + R > W)) {
     float* srf = &sr[0][0].x;  // row stride 64 floats
     for (int a = wp; a < RR; a += NW) {
       const int gi = i0 - R + a;
@@ -261,15 +267,15 @@ __device__ __forceinline__ void blur_fb_step_body(const float* __restrict__ x, c
 #pragma unroll
     for (int t = 0; t < VO; ++t) {
       const int gi = i0 + a0 + t;
-      const size_t o = (size_t)(gi < H ? gi : 0) * W + gj;
-      hv[t] = make_float2(h && out && gi < H && gj < W ? __ldg(h + o) : 0.f,
-                          h && out && gi < H && gj + 1 < W ? __ldg(h + o + 1) : 0.f);
+      const size_t o = (size_t)(IN || gi < H ? gi : 0) * W + gj;
+      hv[t] = make_float2(h && out && (IN || (gi < H && gj < W)) ? __ldg(h + o) : 0.f,
+                          h && out && (IN || (gi < H && gj + 1 < W)) ? __ldg(h + o + 1) : 0.f);
     }
 #pragma unroll
     for (int t = 0; t < VO; ++t) {
       const int a = a0 + t;
       const int gi = i0 + a;
-      if (gi >= H) continue;
+      if (!IN && gi >= H) continue;
       float2 v = make_float2(0.f, 0.f);
 #pragma unroll
       for (int k = 0; k <= 2 * R; ++k) v = __ffma2_rn(make_float2(wk[k], wk[k]), win[t + k], v);
@@ -279,20 +285,40 @@ __device__ __forceinline__ void blur_fb_step_body(const float* __restrict__ x, c
       const size_t o = (size_t)gi * W + gj;
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
-        if (gj + q >= W) continue;
+        if (!IN && gj + q >= W) continue;
         const float xq = q ? xc.y : xc.x, vq = q ? v.y : v.x;
         if (out) {
           float o_v = xq - gamma * vq;
           if (h) o_v = fmaf(ch, q ? hv[t].y : hv[t].x, o_v);
           out[o + q] = o_v;
         }
-        const float dy = gi < H - 1 ? (q ? xd.y : xd.x) - xq : 0.f;
-        const float dx = gj + q < W - 1 ? (q ? xr : xc.y) - xq : 0.f;
+        const float dy = IN || gi < H - 1 ? (q ? xd.y : xd.x) - xq : 0.f;
+        const float dx = IN || gj + q < W - 1 ? (q ? xr : xc.y) - xq : 0.f;
         acc_b.add(tv_term(0.f, dy, dx));
       }
     }
   }
   block_sum2_store<FNT>(acc_a, acc_b, part_a, part_b, part_index);
+}
+
+template <int R>
+__device__ __forceinline__ void blur_fb_step_body(const float* __restrict__ x, const float* __restrict__ b,
+                                                  const float* __restrict__ h, float* __restrict__ out, int H,
+                                                  int W, const BlurW& w, float gamma, float ch,
+                                                  Partial* __restrict__ part_a, Partial* __restrict__ part_b,
+                                                  int tile_x, int tile_y, int part_index) {
+  constexpr int FY = fb_tile_h(R), XR = FY + 4 * R, RR = FY + 2 * R;
+  __shared__ float2 sx[XR][32];
+  __shared__ float2 sh[XR][32];
+  __shared__ float2 sr[RR][32];
+  const int i0 = tile_y * FY, j0 = tile_x * fb_tile_w(R);
+  const bool in = i0 >= 2 * R && i0 + FY + 2 * R <= H && j0 >= 2 * R && j0 - 2 * R + 64 <= W;
+  if (in)
+    blur_fb_step_body_impl<R, true>(x, b, h, out, H, W, w, gamma, ch, part_a, part_b, tile_x, tile_y, part_index,
+                                    sx, sh, sr);
+  else
+    blur_fb_step_body_impl<R, false>(x, b, h, out, H, W, w, gamma, ch, part_a, part_b, tile_x, tile_y, part_index,
+                                     sx, sh, sr);
 }
 
 }  // namespace tvs

@@ -34,7 +34,7 @@ blur_kernel(const float* __restrict__ src, int H, int W, BlurW w, const float* _
 }
 
 template <int R>
-__global__ void __launch_bounds__(FNT)
+__global__ void __launch_bounds__(FNT, 4)  // four CTAs per SM: 572 tiles of a 1024^2 image in one wave
 blur_fb_step_kernel(const float* __restrict__ x, const float* __restrict__ b, const float* __restrict__ h,
                     float* __restrict__ out, int H, int W, BlurW w, float gamma, float ch,
                     Partial* __restrict__ part_a, Partial* __restrict__ part_b) {

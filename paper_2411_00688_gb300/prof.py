@@ -7,10 +7,15 @@ single launches of the kernel of interest:
     python -m paper_2411_00688_gb300.prof --shape 4096 4096 --iters 8 --reps 3
     python -m paper_2411_00688_gb300.prof --shape 256 256 256 --iters 4 --dual bf16
     python -m paper_2411_00688_gb300.prof --ct 512 720 725 --reps 3
+    python -m paper_2411_00688_gb300.prof --step 1024 1024 --iters 64 --reps 3
 
 It prints the per-iteration time measured with CUDA events on the launching
 stream (not meaningful under a profiler).  --ct N ANGLES BINS instead applies the
 parallel-beam projector and backprojector of an N x N unit-square geometry.
+--step H W runs PGD without inner iterations on an H x W 9x9-blur problem, so that
+the fused forward-backward step kernel (one launch per iteration, with the
+objective reduction beside it) can be captured, and prints the device time per
+outer iteration.
 """
 
 from __future__ import annotations
@@ -33,9 +38,12 @@ def main(argv=None):
     ap.add_argument("--lam", type=float, default=0.2)
     ap.add_argument("--dual", default="f32", choices=["f32", "bf16", "f16", "q15"])
     ap.add_argument("--ct", type=int, nargs=3, default=None, metavar=("N", "ANGLES", "BINS"))
+    ap.add_argument("--step", type=int, nargs=2, default=None, metavar=("H", "W"))
     args = ap.parse_args(argv)
     if args.ct:
         return _ct(args, tvs, L)
+    if args.step:
+        return _step(args, tvs, L)
 
     stream = torch.cuda.Stream()
     ctx = tvs.Context.__new__(tvs.Context)
@@ -91,6 +99,27 @@ def _ct(args, tvs, L):
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
         print(f"{name} {N}^2, {na} angles, {nd} bins: {statistics.median(times) * 1e3:.1f} us")
+    prob.close()
+    ctx.close()
+
+
+def _step(args, tvs, L):
+    import torch
+    H, W = args.step
+    stream = torch.cuda.Stream()
+    ctx = tvs.Context.__new__(tvs.Context)
+    ctx._h = C.c_void_p()
+    L.check(L.lib().tvs_create(C.byref(ctx._h), torch.cuda.current_device(), C.c_void_p(stream.cuda_stream)))
+    ctx.device = torch.cuda.current_device()
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    b = torch.rand((H, W), device="cuda", generator=g)
+    prob = tvs.Problem(ctx, b, 0.02, op="blur", blur_sigma=2.0)
+    per_it = []
+    for _ in range(args.reps):
+        _, tr = tvs.pgd_solve(prob, b.clone(), 1.0, args.iters, 0)
+        per_it.append(tr.solve_ms / max(tr.iters_run, 1))
+    print(f"blur step {H}x{W}: {statistics.median(per_it) * 1e3:.2f} us per outer iteration")
     prob.close()
     ctx.close()
 
