@@ -154,13 +154,56 @@ pd_dual_pointwise_kernel(size_t m, const float* __restrict__ ax, float* __restri
   block_sum2_store<PW_NT>(acc, FAcc(), part_a, nullptr, blockIdx.x);
 }
 
+// block_sum_partials<NT> of two arrays at once: the loads of both are issued in the
+// same pass and the two block reductions share their barriers.  Each sum is formed
+// in the order block_sum_partials<NT> forms it (per thread, per warp, then over the
+// warps), so the results are the same bits.
+template <int NT>
+__device__ __forceinline__ void block_sum_partials2(const Partial* __restrict__ pa, int na,
+                                                    const Partial* __restrict__ pb, int nb, double* sum_a,
+                                                    double* sum_b) {
+  __shared__ Partial spa[NT / 32], spb[NT / 32];
+  __shared__ double ta, tb;
+  FAcc a, b;
+  const int n = na > nb ? na : nb;
+  for (int i = threadIdx.x; i < n; i += NT) {
+    if (i < na) a.add(pa[i]);
+    if (i < nb) b.add(pb[i]);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  warp_sum<32>(a);
+  warp_sum<32>(b);
+  if (lane == 0) {
+    spa[warp] = Partial{a.s, a.c};
+    spb[warp] = Partial{b.s, b.c};
+  }
+  __syncthreads();
+  if (warp == 0) {
+    a = FAcc();
+    b = FAcc();
+    if (lane < NT / 32) {
+      a.s = spa[lane].s; a.c = spa[lane].c;
+      b.s = spb[lane].s; b.c = spb[lane].c;
+    }
+    warp_sum<32>(a);
+    warp_sum<32>(b);
+    if (lane == 0) {
+      ta = (double)a.s + (double)a.c;
+      tb = (double)b.s + (double)b.c;
+    }
+  }
+  __syncthreads();
+  *sum_a = ta;
+  *sum_b = tb;
+}
+
 __global__ void __launch_bounds__(512)
 reduce_record_kernel(const Partial* __restrict__ part_a, int n_a, const Partial* __restrict__ part_b,
                      int n_b, double alpha, int every, double* obj, unsigned long long* ts,
                      double f_star, double target, int* flags, int* done_host, double* f_out) {
   pdl_enter();
-  const double sum_a = block_sum_partials<512>(part_a, n_a);
-  const double sum_b = block_sum_partials<512>(part_b, n_b);
+  double sum_a, sum_b;
+  block_sum_partials2<512>(part_a, n_a, part_b, n_b, &sum_a, &sum_b);
   if (threadIdx.x == 0) {
     const double F = sum_a + alpha * sum_b;
     if (f_out) *f_out = F;
