@@ -14,6 +14,8 @@ benchmark's headline one (python -m paper_2411_00688_gb300.workloads NAME ...).
   dual_huber_200x300    ProjGD, AProjGD and ProxSkip on Dual-Huber-ROF (Section 2.2)
   iteration_split_deblur2d_1024  device time of skipped and prox outer iterations of the
                  ProxSkip solve (trace timestamps), p = 0.5 and 0.02
+  batch_dual_error      the batched workload with each 16-bit dual storage against FP32:
+                 problems over 2e-3 relative l2, worst cases, largest PSNR change
 
 Each prints one JSON line per solver: iterations and prox calls to a 1e-4
 relative objective gap, device time to the target and wall time of the solve.
@@ -423,11 +425,72 @@ def _batch(n_problems=None, K=None, batch_only=False, dual="f32"):
              "n_inner": cfg.n_inner, "batched_s": t_batch, "loop_s": t_loop, "speedup": t_loop / t_batch}]
 
 
+def batch_dual_error():
+    """The batched workload (256 problems, 200 iterations, 50 inner) solved with each
+    16-bit dual storage and with FP32: per storage, how many problems' iterates are
+    more than 2e-3 (relative l2) from the FP32 ones, the two worst with their prox
+    step lambda = gamma alpha / p, and the largest PSNR change against the phantom."""
+    import torch
+    from synth.configs import BatchConfig
+    tvs, ctx = _ctx()
+    cfg = BatchConfig()
+    specs = cfg.specs()
+    probs, bs, truths = [], [], []
+    for sp in specs:
+        truth = torch.from_numpy(cfg.phantom(sp).astype(np.float32)).cuda()
+        noise = torch.from_numpy(cfg.noise(sp).astype(np.float32)).cuda()
+        if sp["kind"] == "deblur":
+            opp = tvs.Problem(ctx, truth, sp["alpha"], op="blur", blur_sigma=sp["blur_sigma"])
+            clean = torch.empty_like(truth)
+            tvs.tvs_op_apply(opp, truth, clean)
+            opp.close()
+            b = (clean + noise).contiguous()
+            probs.append(tvs.Problem(ctx, b, sp["alpha"], op="blur", blur_sigma=sp["blur_sigma"]))
+        else:
+            b = (truth + noise).contiguous()
+            probs.append(tvs.Problem(ctx, b, sp["alpha"]))
+        bs.append(b)
+        truths.append(truth)
+    ps = [sp["p"] for sp in specs]
+    seeds = [sp["seed"] for sp in specs]
+
+    def solve(dual):
+        xs = [b.clone() for b in bs]
+        tvs.proxskip_solve_batch(ctx, probs, xs, [1.0] * len(probs), ps, seeds, cfg.max_iter, cfg.n_inner,
+                                 dual=dual)
+        return [x.double() for x in xs]
+
+    def psnr(x, t):
+        mse = float(((x - t.double()) ** 2).mean())
+        peak = float(t.abs().max())
+        return 10.0 * math.log10(peak * peak / mse) if mse > 0 and peak > 0 else float("inf")
+
+    ref = solve("f32")
+    ref_psnr = [psnr(x, t) for x, t in zip(ref, truths)]
+    out = []
+    for dual in ("bf16", "f16", "q15"):
+        xs = solve(dual)
+        rows = []
+        for i, (x, r) in enumerate(zip(xs, ref)):
+            rel = float(torch.linalg.norm(x - r) / torch.linalg.norm(r))
+            dpsnr = abs(psnr(x, truths[i]) - ref_psnr[i])
+            rows.append((rel, specs[i]["alpha"] / ps[i], specs[i]["H"], specs[i]["W"], dpsnr))
+        worst = sorted(rows, reverse=True)[:2]
+        out.append({"workload": cfg.name, "dual": dual, "problems": len(rows),
+                    "over_2e-3": sum(1 for r in rows if r[0] > 2e-3),
+                    "worst": [{"rel_l2": w[0], "lambda": w[1], "shape": [w[2], w[3]]} for w in worst],
+                    "max_dpsnr_db": max(r[4] for r in rows)})
+    for pr in probs:
+        pr.close()
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("workload", choices=["denoise2d_256", "ct2d_512", "denoise3d_512", "batch2d_256",
                                          "deblur2d_1024", "table1_deblur2d_1024", "dual_huber_200x300",
-                                         "ct2d_512_sweep", "iteration_split_deblur2d_1024"])
+                                         "ct2d_512_sweep", "iteration_split_deblur2d_1024",
+                                         "batch_dual_error"])
     ap.add_argument("--problems", type=int, default=None)
     ap.add_argument("--iters", type=int, default=None)
     ap.add_argument("--batch-only", action="store_true", help="batch2d_256: time the batched solve only")
@@ -439,7 +502,8 @@ def main(argv=None):
         recs = {"denoise2d_256": denoise2d_256, "ct2d_512": ct2d_512, "denoise3d_512": denoise3d_512,
                 "deblur2d_1024": deblur2d_1024, "table1_deblur2d_1024": table1_deblur2d_1024,
                 "dual_huber_200x300": dual_huber_200x300, "ct2d_512_sweep": ct2d_512_sweep,
-                "iteration_split_deblur2d_1024": iteration_split_deblur2d_1024}[args.workload]()
+                "iteration_split_deblur2d_1024": iteration_split_deblur2d_1024,
+                "batch_dual_error": batch_dual_error}[args.workload]()
     for r in recs:
         print(json.dumps(r), flush=True)
 
