@@ -2,8 +2,9 @@
 measurement infrastructure only, like the rest of this package).
 
 ``tvo.c`` restates in plain FP64 C, with OpenMP over image rows, what ``tv.py``
-(D, div, TV, the AProjGD TV prox), ``operators.py`` (the Gaussian blur and its
-scattered adjoint) and ``solvers.py`` (PGD, FISTA, ProxSkip) compute; the tests in
+(D, div, TV, the AProjGD TV prox), ``operators.py`` (the Gaussian blur and the
+Joseph projector, each with its scattered adjoint) and ``solvers.py`` (PGD, FISTA,
+ProxSkip, with the blur, the identity or the projector as A) compute; the tests in
 ``tests/test_oracle_c.py`` hold it to the numpy oracle at 1e-12.  It exists for the
 full-size runs the numpy code is too slow for.  ``build()`` compiles it with gcc
 into ``oracle/_build/<machine>/libtvo.so``.
@@ -61,6 +62,12 @@ def lib():
                                       _D, _D, C.c_double, C.c_double, C.POINTER(C.c_int)]
         _lib.tvo_fb_solve.restype = C.c_int
         _lib.tvo_max_threads.restype = C.c_int
+        _lib.tvo_joseph.argtypes = [C.c_long, C.c_long, C.c_long, C.c_double, C.c_double, _D, _D, C.c_int]
+        _lib.tvo_ct_fb_solve.argtypes = [C.c_int, C.c_long, C.c_long, C.c_long, C.c_double, C.c_double, _D,
+                                         C.c_double, C.c_int, C.c_double, C.c_double, C.POINTER(C.c_ubyte),
+                                         C.c_int, C.c_int, _D, _D, _D, C.c_double, C.c_double,
+                                         C.POINTER(C.c_int)]
+        _lib.tvo_ct_fb_solve.restype = C.c_int
     return _lib
 
 
@@ -121,6 +128,17 @@ def blur(u, w, adjoint=False):
     return out
 
 
+def joseph(u, geom, adjoint=False):
+    """A u (sinogram, n_angles x n_det) or A^T y (image) for an ``operators.ParallelBeam``
+    geometry, as ``operators.joseph_forward`` / ``joseph_adjoint``."""
+    u = _f64(u)
+    N, na, nd = geom.N, geom.n_angles, geom.n_det
+    out = np.empty((N, N) if adjoint else (na, nd))
+    lib().tvo_joseph(N, na, nd, float(geom.pixel_size), float(geom.det_spacing), _ptr(u), _ptr(out),
+                     int(bool(adjoint)))
+    return out
+
+
 def objective(b, alpha, x, w=None):
     """1/2 ||A x - b||^2 + alpha TV(x), A the blur with taps w (identity when None)."""
     b, x = _f64(b), _f64(x)
@@ -153,5 +171,27 @@ def fb_solve(kind, b, alpha, gamma, K, n_inner, x0=None, w=None, p=1.0, coins=No
                              float(f_star), float(target), C.byref(nprox))
     if ran < 0:
         raise MemoryError("tvo_fb_solve")
+    return dict(x=x, dual=d, objective=list(obj[:ran]) if record else [], coins=list(c[:ran]),
+                prox_calls=int(nprox.value), iters_run=int(ran))
+
+
+def ct_fb_solve(kind, b, alpha, gamma, K, n_inner, geom, x0=None, p=1.0, coins=None, nonneg=False,
+                f_star=0.0, target=0.0, dual=None, record=True):
+    """``fb_solve`` with A the parallel-beam projector of ``geom`` (b: the sinogram;
+    x_0 = 0 unless given)."""
+    b = _f64(b)
+    N = geom.N
+    x = np.zeros((N, N)) if x0 is None else _f64(x0).copy()
+    d = np.zeros((2, N, N)) if dual is None else np.array(dual, dtype=np.float64, order="C")
+    c = np.ones(max(K, 1), dtype=np.uint8) if coins is None else np.ascontiguousarray(coins, dtype=np.uint8)
+    obj = np.full(max(K, 1), np.nan)
+    nprox = C.c_int(0)
+    ran = lib().tvo_ct_fb_solve(_KIND[kind], N, geom.n_angles, geom.n_det, float(geom.pixel_size),
+                                float(geom.det_spacing), _ptr(b), float(alpha), int(bool(nonneg)), float(gamma),
+                                float(p), c.ctypes.data_as(C.POINTER(C.c_ubyte)), int(K), int(n_inner), _ptr(x),
+                                _ptr(d), _ptr(obj) if record else None, float(f_star), float(target),
+                                C.byref(nprox))
+    if ran < 0:
+        raise MemoryError("tvo_ct_fb_solve")
     return dict(x=x, dual=d, objective=list(obj[:ran]) if record else [], coins=list(c[:ran]),
                 prox_calls=int(nprox.value), iters_run=int(ran))

@@ -22,6 +22,8 @@
  * and returns u = P_X(z + lam div p_N) with p_N as the next warm start.
  * The blur is the separable, unit-sum sampled Gaussian with half-sample
  * symmetric extension (Section 3.1); its adjoint is formed by scattering.
+ * The CT operator is the parallel-beam projector in Joseph's discretisation of
+ * operators.py (Section 3.3), its adjoint the scatter of the same weights.
  */
 #include <math.h>
 #include <stdint.h>
@@ -241,29 +243,137 @@ void tvo_blur(long H, long W, const double* w, int R, const double* u, double* o
   free(tmp);
 }
 
+/* ------------------------------------------------------------------ projector */
+/* Parallel-beam geometry (Section 3.3): an N x N image of pixel size s centred at
+ * the origin, angle a at theta = a pi / n_angles, bin b on the line
+ * x cos + y sin = t_b with t_b = (b - (n_det - 1)/2) d.  Joseph's discretisation,
+ * as operators.py states it: a ray with |cos| >= |sin| is walked over the image
+ * rows (line l = row l, at y_l = (l - (N-1)/2) s), otherwise over the columns
+ * (line l = column l, at x_l); on line l it crosses the position
+ * pos = (t_b - y_l sin) / cos (rows) or (t_b - x_l cos) / sin (columns), i.e.
+ * the fractional pixel index c = pos / s + (N-1)/2 along the line; the sample is
+ * (1 - f) u[k0] + f u[k0 + 1] with k0 = floor(c), f = c - k0, pixels outside the
+ * image counting zero, and the ray sum is weighted by s / max(|cos|, |sin|). */
+typedef struct {
+  long N, na, nd;
+  double s, d;
+} tvo_geom;
+
+static const double TVO_PI = 3.14159265358979323846;
+
+typedef struct {
+  int row;       /* walked over rows */
+  double c, sn;  /* cos, sin of the angle */
+  double weight; /* s / max(|cos|, |sin|) */
+} ray_dir;
+
+static ray_dir ray_direction(const tvo_geom* g, long a) {
+  ray_dir r;
+  const double th = (double)a * TVO_PI / (double)g->na;
+  r.c = cos(th);
+  r.sn = sin(th);
+  r.row = fabs(r.c) >= fabs(r.sn);
+  r.weight = r.row ? g->s / fabs(r.c) : g->s / fabs(r.sn);
+  return r;
+}
+
+/* k0 and f of the crossing of bin b's ray with line l */
+static void crossing(const tvo_geom* g, const ray_dir* r, long b, long l, long* k0, double* f) {
+  const double t = ((double)b - (double)(g->nd - 1) / 2.0) * g->d;
+  const double coord = ((double)l - (double)(g->N - 1) / 2.0) * g->s;
+  const double pos = r->row ? (t - coord * r->sn) / r->c : (t - coord * r->c) / r->sn;
+  const double frac = pos / g->s + (double)(g->N - 1) / 2.0;
+  const double i0 = floor(frac);
+  *k0 = (long)i0;
+  *f = frac - i0;
+}
+
+/* y = A u: y[a][b] = weight_a sum_l ((1 - f) u_l[k0] + f u_l[k0 + 1]), u_l the
+ * image line l (a row or a column). */
+static void joseph_fwd(const tvo_geom* g, const double* u, double* y) {
+  const long N = g->N;
+#pragma omp parallel for schedule(dynamic)
+  for (long a = 0; a < g->na; ++a) {
+    const ray_dir r = ray_direction(g, a);
+    for (long b = 0; b < g->nd; ++b) {
+      double acc = 0.0;
+      for (long l = 0; l < N; ++l) {
+        long k0;
+        double f;
+        crossing(g, &r, b, l, &k0, &f);
+        if (k0 < -1 || k0 > N - 1) continue; /* both terms outside the image */
+        double term = 0.0;
+        if (k0 >= 0) term += (1.0 - f) * (r.row ? u[l * N + k0] : u[k0 * N + l]);
+        if (k0 + 1 <= N - 1) term += f * (r.row ? u[l * N + k0 + 1] : u[(k0 + 1) * N + l]);
+        acc += term;
+      }
+      y[a * g->nd + b] = r.weight * acc;
+    }
+  }
+}
+
+/* out = A^T y: every sample's weights scattered back, angle by angle, each
+ * sample adding (1 - f) y to pixel k0 and f y to pixel k0 + 1 of its line.  The
+ * lines of one angle touch disjoint pixels, so they are spread over the threads. */
+static void joseph_adj(const tvo_geom* g, const double* y, double* out) {
+  const long N = g->N;
+  memset(out, 0, sizeof(double) * N * N);
+  for (long a = 0; a < g->na; ++a) {
+    const ray_dir r = ray_direction(g, a);
+#pragma omp parallel for schedule(static)
+    for (long l = 0; l < N; ++l)
+      for (long b = 0; b < g->nd; ++b) {
+        long k0;
+        double f;
+        crossing(g, &r, b, l, &k0, &f);
+        if (k0 < -1 || k0 > N - 1) continue;
+        const double ya = y[a * g->nd + b];
+        double* line = r.row ? out + l * N : out + l;
+        const long step = r.row ? 1 : N;
+        if (k0 >= 0) line[k0 * step] += r.weight * (1.0 - f) * ya;
+        if (k0 + 1 <= N - 1) line[(k0 + 1) * step] += r.weight * f * ya;
+      }
+  }
+}
+
+void tvo_joseph(long N, long n_angles, long n_det, double s, double d, const double* in, double* out,
+                int adjoint) {
+  tvo_geom g = {N, n_angles, n_det, s, d};
+  if (adjoint)
+    joseph_adj(&g, in, out);
+  else
+    joseph_fwd(&g, in, out);
+}
+
 /* ------------------------------------------------------------------ solvers */
-/* min_x 1/2 ||A x - b||^2 + alpha TV(x) with A the identity (R = 0) or the blur
- * with taps w[0..2R] (2D only); 3D problems take the identity. */
+/* min_x 1/2 ||A x - b||^2 + alpha TV(x) with A the identity (R = 0, geom null),
+ * the blur with taps w[0..2R] (2D only; 3D problems take the identity) or the
+ * CT projector of geom (2D, b of n_angles x n_det). */
 typedef struct {
   tvo_shape sh;
-  long n;
+  long n, m; /* image size, data size */
   const double* w;
   int R;
+  const tvo_geom* geom;
   const double* b;
   double alpha;
   int nonneg;
-  double *t1, *t2, *t3, *g; /* scratch: 3 images, ndim planes */
+  double *t1, *t2, *t3, *g; /* scratch: t1 of the data size, t2 and t3 images, ndim planes */
 } prob_t;
 
 static void op_fwd(prob_t* P, const double* x, double* y) {
-  if (P->R == 0)
+  if (P->geom)
+    joseph_fwd(P->geom, x, y);
+  else if (P->R == 0)
     memcpy(y, x, sizeof(double) * P->n);
   else
     blur_fwd(P->sh.n1, P->sh.n2, P->w, P->R, x, P->t3, y);
 }
 
 static void op_adj(prob_t* P, const double* x, double* y) {
-  if (P->R == 0)
+  if (P->geom)
+    joseph_adj(P->geom, x, y);
+  else if (P->R == 0)
     memcpy(y, x, sizeof(double) * P->n);
   else
     blur_adj(P->sh.n1, P->sh.n2, P->w, P->R, x, P->t3, y);
@@ -272,7 +382,7 @@ static void op_adj(prob_t* P, const double* x, double* y) {
 /* grad f(x) = A^T (A x - b) into out. */
 static void grad_f(prob_t* P, const double* x, double* out) {
   op_fwd(P, x, P->t1);
-  for (long o = 0; o < P->n; ++o) P->t1[o] -= P->b[o];
+  for (long o = 0; o < P->m; ++o) P->t1[o] -= P->b[o];
   op_adj(P, P->t1, out);
 }
 
@@ -280,7 +390,7 @@ static double objective(prob_t* P, const double* x) {
   op_fwd(P, x, P->t1);
   double s = 0.0;
 #pragma omp parallel for reduction(+ : s) schedule(static)
-  for (long o = 0; o < P->n; ++o) {
+  for (long o = 0; o < P->m; ++o) {
     const double r = P->t1[o] - P->b[o];
     s += r * r;
   }
@@ -291,9 +401,10 @@ double tvo_objective(int ndim, const long* shape, const double* w, int R, const 
                      const double* x) {
   prob_t P;
   P.sh = mk_shape(ndim, shape);
-  P.n = P.sh.n0 * P.sh.n1 * P.sh.n2;
+  P.n = P.m = P.sh.n0 * P.sh.n1 * P.sh.n2;
   P.w = w;
   P.R = ndim == 2 ? R : 0;
+  P.geom = NULL;
   P.b = b;
   P.alpha = alpha;
   P.nonneg = 0;
@@ -316,20 +427,13 @@ double tvo_objective(int ndim, const long* shape, const double* w, int R, const 
  * iteration whose (F - f_star)/f_star <= target.  Returns the number of
  * iterations run (>= 0), or -1 if memory ran out; *prox_calls receives the prox
  * evaluations among them. */
-int tvo_fb_solve(int kind, int ndim, const long* shape, const double* w, int R, const double* b,
-                 double alpha, int nonneg, double gamma, double p, const unsigned char* coins, int K,
-                 int n_inner, double* x, double* dual, double* obj, double f_star, double target,
-                 int* prox_calls) {
-  prob_t P;
-  P.sh = mk_shape(ndim, shape);
-  P.n = P.sh.n0 * P.sh.n1 * P.sh.n2;
-  P.w = w;
-  P.R = ndim == 2 ? R : 0;
-  P.b = b;
-  P.alpha = alpha;
-  P.nonneg = nonneg;
+static int fb_core(prob_t* P_, int kind, int ndim, const long* shape, int nonneg, double gamma, double p,
+                   const unsigned char* coins, int K, int n_inner, double* x, double* dual, double* obj,
+                   double f_star, double target, int* prox_calls) {
+  prob_t P = *P_;
   const long n = P.n;
-  P.t1 = (double*)malloc(sizeof(double) * n);
+  const double alpha = P.alpha;
+  P.t1 = (double*)malloc(sizeof(double) * P.m);
   P.t2 = (double*)malloc(sizeof(double) * n);
   P.t3 = (double*)malloc(sizeof(double) * n);
   P.g = (double*)malloc(sizeof(double) * n * ndim);
@@ -393,6 +497,45 @@ done:
   free(xn);
   free(aux);
   return ran;
+}
+
+int tvo_fb_solve(int kind, int ndim, const long* shape, const double* w, int R, const double* b,
+                 double alpha, int nonneg, double gamma, double p, const unsigned char* coins, int K,
+                 int n_inner, double* x, double* dual, double* obj, double f_star, double target,
+                 int* prox_calls) {
+  prob_t P;
+  P.sh = mk_shape(ndim, shape);
+  P.n = P.m = P.sh.n0 * P.sh.n1 * P.sh.n2;
+  P.w = w;
+  P.R = ndim == 2 ? R : 0;
+  P.geom = NULL;
+  P.b = b;
+  P.alpha = alpha;
+  P.nonneg = nonneg;
+  return fb_core(&P, kind, ndim, shape, nonneg, gamma, p, coins, K, n_inner, x, dual, obj, f_star, target,
+                 prox_calls);
+}
+
+/* The same solvers with A the CT projector of an N x N image (pixel size s) onto
+ * n_angles x n_det bins of spacing d; b is the n_angles x n_det sinogram. */
+int tvo_ct_fb_solve(int kind, long N, long n_angles, long n_det, double s, double d, const double* b,
+                    double alpha, int nonneg, double gamma, double p, const unsigned char* coins, int K,
+                    int n_inner, double* x, double* dual, double* obj, double f_star, double target,
+                    int* prox_calls) {
+  const long shape[2] = {N, N};
+  tvo_geom g = {N, n_angles, n_det, s, d};
+  prob_t P;
+  P.sh = mk_shape(2, shape);
+  P.n = N * N;
+  P.m = n_angles * n_det;
+  P.w = NULL;
+  P.R = 0;
+  P.geom = &g;
+  P.b = b;
+  P.alpha = alpha;
+  P.nonneg = nonneg;
+  return fb_core(&P, kind, 2, shape, nonneg, gamma, p, coins, K, n_inner, x, dual, obj, f_star, target,
+                 prox_calls);
 }
 
 /* Threads the OpenMP passes use (1 without OpenMP). */

@@ -100,3 +100,40 @@ def test_fb_solver_3d_identity_and_stop():
     stop = c.fb_solve("proxskip", b, 0.1, 1.0, 12, 5, p=0.5, coins=coin.schedule(3, 0.5, 12),
                       f_star=f_star, target=1e-3)
     assert stop["iters_run"] == k_hit + 1
+
+
+@pytest.mark.parametrize("N,na,nd,spacing", [(24, 37, 31, None), (17, 20, 25, 0.6), (9, 8, 14, 1.7),
+                                             (32, 64, 46, None)])
+def test_joseph_and_adjoint(N, na, nd, spacing):
+    """The projector and its scattered adjoint equal the numpy oracle's (row and
+    column walks, the 45-degree switch, bins wider and narrower than a pixel)."""
+    g = operators.ParallelBeam(N, na, nd, 1.0 / N, (spacing or 1.0) / N)
+    rng = np.random.default_rng(N + na)
+    u, y = rng.random((N, N)), rng.standard_normal((na, nd))
+    np.testing.assert_allclose(c.joseph(u, g), operators.joseph_forward(u, g), rtol=0, atol=1e-13)
+    np.testing.assert_allclose(c.joseph(y, g, adjoint=True), operators.joseph_adjoint(y, g), rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("kind", ["pgd", "fista", "proxskip"])
+def test_ct_fb_solvers(kind):
+    """PGD / FISTA / ProxSkip with the CT projector as A, as the numpy solvers run them."""
+    N, na, nd = 20, 24, 29
+    g = operators.ParallelBeam.unit_square(N, na, nd)
+    rng = np.random.default_rng(3)
+    b = operators.joseph_forward(rng.random((N, N)), g) + 0.01 * rng.standard_normal((na, nd))
+    alpha, K, n_inner, p, seed = 0.002, 14, 6, 0.4, 11
+    gamma = 0.9 / 1.6  # below 1 / ||A||^2 for this geometry (||A||^2 = 1.157 by the power method)
+    prob = solvers.Problem(operators.ct_op(g), b, alpha, (N, N))
+    x0 = np.zeros((N, N))
+    if kind == "pgd":
+        ref = solvers.pgd(prob, x0, gamma, K, n_inner)
+    elif kind == "fista":
+        ref = solvers.fista(prob, x0, gamma, K, n_inner)
+    else:
+        ref = solvers.proxskip(prob, x0, gamma, p, seed, K, n_inner)
+    got = c.ct_fb_solve(kind, b, alpha, gamma, K, n_inner, g, p=p,
+                        coins=coin.schedule(seed, p, K) if kind == "proxskip" else None)
+    np.testing.assert_allclose(got["x"], ref["x"], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(got["dual"], ref["dual"], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(got["objective"], ref["objective"], rtol=1e-12)
+    assert got["prox_calls"] == ref["prox_calls"] and got["iters_run"] == K
