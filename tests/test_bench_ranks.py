@@ -59,3 +59,17 @@ def test_reference_arm_skips_nonzero_ranks(monkeypatch, capsys):
 
     bench.run_reference(Args())
     assert capsys.readouterr().out == ""
+
+
+def test_ct_f_star_prefers_the_oracle_value(tmp_path):
+    """The CT record takes the committed oracle F* when it exists and reports the
+    GPU's long-run minimum beside it; without the file it falls back to the GPU's."""
+    import json
+    import bench
+    path = tmp_path / "fstar.json"
+    fs, src, chk = bench.ct_f_star(352.9143, path=str(path))
+    assert fs == 352.9143 and "GPU" in src and chk is None
+    path.write_text(json.dumps({"f_star": 352.9142}))
+    fs, src, chk = bench.ct_f_star(352.9143, path=str(path))
+    assert fs == 352.9142 and "oracle" in src
+    assert chk["gpu_pdhg_min"] == 352.9143 and abs(chk["rel_diff"] - 0.0001 / 352.9142) < 1e-12
