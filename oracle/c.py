@@ -68,6 +68,9 @@ def lib():
                                          C.c_int, C.c_int, _D, _D, _D, C.c_double, C.c_double,
                                          C.POINTER(C.c_int)]
         _lib.tvo_ct_fb_solve.restype = C.c_int
+        _lib.tvo_ct_pdhg.argtypes = [C.c_long, C.c_long, C.c_long, C.c_double, C.c_double, _D, C.c_double,
+                                     C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, _D, _D, _D, _D]
+        _lib.tvo_ct_pdhg.restype = C.c_int
     return _lib
 
 
@@ -195,3 +198,20 @@ def ct_fb_solve(kind, b, alpha, gamma, K, n_inner, geom, x0=None, p=1.0, coins=N
         raise MemoryError("tvo_ct_fb_solve")
     return dict(x=x, dual=d, objective=list(obj[:ran]) if record else [], coins=list(c[:ran]),
                 prox_calls=int(nprox.value), iters_run=int(ran))
+
+
+def ct_pdhg(b, alpha, sigma, tau, K, n_inner, geom, x0=None, y0=None, nonneg=False, record=True):
+    """``solvers.pdhg`` with K the parallel-beam projector of ``geom`` (x_0 = 0 and
+    y_0 = 0 unless given).  Returns a dict like the numpy solver's."""
+    b = _f64(b)
+    N = geom.N
+    x = np.zeros((N, N)) if x0 is None else _f64(x0).copy()
+    y = np.zeros(b.shape) if y0 is None else _f64(y0).copy()
+    d = np.zeros((2, N, N))
+    obj = np.full(max(K, 1), np.nan)
+    ran = lib().tvo_ct_pdhg(N, geom.n_angles, geom.n_det, float(geom.pixel_size), float(geom.det_spacing),
+                            _ptr(b), float(alpha), int(bool(nonneg)), float(sigma), float(tau), int(K),
+                            int(n_inner), _ptr(x), _ptr(y), _ptr(d), _ptr(obj) if record else None)
+    if ran < 0:
+        raise MemoryError("tvo_ct_pdhg")
+    return dict(x=x, y=y, dual=d, objective=list(obj[:ran]) if record else [], iters_run=int(ran))

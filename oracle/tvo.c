@@ -538,6 +538,73 @@ int tvo_ct_fb_solve(int kind, long N, long n_angles, long n_det, double s, doubl
                  prox_calls);
 }
 
+/* Implicit PDHG (solvers.pdhg; Algorithm 6 at p = 1) with K = the CT projector,
+ * f = 1/2 ||. - b||^2, g = alpha TV (+ the indicator of x >= 0 with nonneg):
+ *   x_{k+1} = prox_{sigma g}(x_k - sigma K^T y_k),  x-bar = 2 x_{k+1} - x_k,
+ *   y_{k+1} = prox_{tau f*}(y_k + tau K x-bar),
+ * prox_{tau f*}(v) = v - tau (tau (v / tau) + b) / (tau + 1) (Moreau).  K x-bar is
+ * formed as 2 K x_{k+1} - K x_k from the K x_{k+1} the objective needs anyway.
+ * x, y: x_0, y_0 in, last iterates out; dual: the TV prox's warm start;
+ * obj (may be NULL): F(x_{k+1}).  Returns K, or -1 if memory ran out. */
+int tvo_ct_pdhg(long N, long n_angles, long n_det, double s, double d, const double* b, double alpha,
+                int nonneg, double sigma, double tau, int K, int n_inner, double* x, double* y, double* dual,
+                double* obj) {
+  const long shape[2] = {N, N};
+  const long n = N * N, m = n_angles * n_det;
+  tvo_geom g = {N, n_angles, n_det, s, d};
+  prob_t P;
+  P.sh = mk_shape(2, shape);
+  P.n = n;
+  P.m = m;
+  P.w = NULL;
+  P.R = 0;
+  P.geom = &g;
+  P.b = b;
+  P.alpha = alpha;
+  P.nonneg = nonneg;
+  P.g = (double*)malloc(sizeof(double) * n * 2);
+  double* aty = (double*)malloc(sizeof(double) * n);
+  double* v = (double*)malloc(sizeof(double) * n);
+  double* xn = (double*)malloc(sizeof(double) * n);
+  double* ax = (double*)malloc(sizeof(double) * m);
+  double* axn = (double*)malloc(sizeof(double) * m);
+  int ran = -1;
+  if (!P.g || !aty || !v || !xn || !ax || !axn) goto done;
+  joseph_fwd(&g, x, ax);
+  for (int k = 0; k < K; ++k) {
+    joseph_adj(&g, y, aty);
+    for (long o = 0; o < n; ++o) v[o] = x[o] - sigma * aty[o];
+    if (tvo_fgp_prox(2, shape, v, sigma * alpha, n_inner, dual, nonneg, xn)) goto done;
+    joseph_fwd(&g, xn, axn);
+    for (long o = 0; o < m; ++o) {
+      const double vv = y[o] + tau * (2.0 * axn[o] - ax[o]);
+      const double w = vv / tau;
+      y[o] = vv - tau * (tau * w + b[o]) / (tau + 1.0);
+    }
+    memcpy(x, xn, sizeof(double) * n);
+    memcpy(ax, axn, sizeof(double) * m);
+    if (obj) {
+      double r2 = 0.0;
+#pragma omp parallel for reduction(+ : r2) schedule(static)
+      for (long o = 0; o < m; ++o) {
+        const double r = ax[o] - b[o];
+        r2 += r * r;
+      }
+      obj[k] = 0.5 * r2 + alpha * tv_sh(P.sh, x, P.g);
+    }
+    ran = k + 1;
+  }
+  if (K == 0) ran = 0;
+done:
+  free(P.g);
+  free(aty);
+  free(v);
+  free(xn);
+  free(ax);
+  free(axn);
+  return ran;
+}
+
 /* Threads the OpenMP passes use (1 without OpenMP). */
 int tvo_max_threads(void) {
 #ifdef _OPENMP

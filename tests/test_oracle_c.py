@@ -137,3 +137,20 @@ def test_ct_fb_solvers(kind):
     np.testing.assert_allclose(got["dual"], ref["dual"], rtol=0, atol=1e-12)
     np.testing.assert_allclose(got["objective"], ref["objective"], rtol=1e-12)
     assert got["prox_calls"] == ref["prox_calls"] and got["iters_run"] == K
+
+
+@pytest.mark.parametrize("nonneg", [False, True])
+def test_ct_pdhg(nonneg):
+    """Implicit PDHG with the CT projector, as the numpy solver runs it (K x-bar is
+    formed from K x_{k+1} by linearity in C, directly in numpy)."""
+    N, na, nd = 18, 22, 27
+    g = operators.ParallelBeam.unit_square(N, na, nd)
+    rng = np.random.default_rng(5)
+    b = operators.joseph_forward(rng.random((N, N)), g) + 0.01 * rng.standard_normal((na, nd))
+    alpha, K, n_inner, st = 0.003, 12, 7, 0.99 / np.sqrt(1.2)
+    prob = solvers.Problem(operators.ct_op(g), b, alpha, (N, N), nonneg=nonneg)
+    ref = solvers.pdhg(prob, np.zeros((N, N)), np.zeros((na, nd)), st, st, K, n_inner)
+    got = c.ct_pdhg(b, alpha, st, st, K, n_inner, g, nonneg=nonneg)
+    np.testing.assert_allclose(got["x"], ref["x"], rtol=0, atol=1e-11)
+    np.testing.assert_allclose(got["y"], ref["y"], rtol=0, atol=1e-11)
+    np.testing.assert_allclose(got["objective"], ref["objective"], rtol=1e-12)
