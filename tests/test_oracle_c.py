@@ -154,3 +154,16 @@ def test_ct_pdhg(nonneg):
     np.testing.assert_allclose(got["x"], ref["x"], rtol=0, atol=1e-11)
     np.testing.assert_allclose(got["y"], ref["y"], rtol=0, atol=1e-11)
     np.testing.assert_allclose(got["objective"], ref["objective"], rtol=1e-12)
+
+
+def test_joseph_full_size_adjoint():
+    """At the CT workload's size (512^2, 720 x 725), the size of its F* run, the C
+    projector and its adjoint pass the dot test <A u, y> = <u, A^T y>."""
+    g = operators.ParallelBeam.unit_square(512, 720, 725)
+    rng = np.random.default_rng(7)
+    u, y = rng.random((512, 512)), rng.standard_normal((720, 725))
+    au = c.joseph(u, g)
+    lhs = float(np.sum(au * y))
+    rhs = float(np.sum(u * c.joseph(y, g, adjoint=True)))
+    # relative to the sum of the magnitudes of the terms (the sums cancel)
+    assert abs(lhs - rhs) <= 1e-12 * float(np.abs(au * y).sum())
